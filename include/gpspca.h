@@ -1,0 +1,174 @@
+/*
+ * gpspca.h - C ABI of the GB300 (sm_103a) generalized power method for sparse PCA.
+ *
+ * The operation (paper "Large-Scale Paralleled Sparse Principal Component
+ * Analysis", Section 2 and Table 1): A is a p x n data matrix (p samples of n
+ * variables, columns a_i).  For the four formulations
+ *
+ *   SL1  max_{x in S^p}   sum_i [ |a_i^T x| - gamma ]_+^2
+ *   SL0  max_{x in S^p}   sum_i [ (a_i^T x)^2 - gamma ]_+
+ *   BL1  max_{X in S^p_m} sum_j sum_i [ mu_j |a_i^T x_j| - gamma_j ]_+^2
+ *   BL0  max_{X in S^p_m} sum_j sum_i [ (mu_j a_i^T x_j)^2 - gamma_j ]_+
+ *
+ * the library runs the generalized power iteration: T = A^T X (column sweep),
+ * a per-entry soft (L1) or hard (L0) threshold at gamma that yields the
+ * gradient direction G, the rank update Y = A G, and the projection back onto
+ * the feasible set (x = y/||y|| on the sphere, X = Y (Y^T Y)^{-1/2} on the
+ * Stiefel manifold).  The sparse loadings Z of Table 1's "Original form"
+ * column are recovered from the last sweep.  Every step runs in this
+ * library's CUDA kernels; there is no host fallback.
+ *
+ * Conventions shared by all entry points
+ *  - Matrices are column-major.  Element (r, i) of A is data[i*ld + r].  A C
+ *    array or torch tensor of shape [n][ld] (rows = variables) is this layout.
+ *  - m is always the number of gamma values.  Block forms: m components,
+ *    gamma[j] and mu[j] belong to component j.  Single-unit forms: m
+ *    independent solves on the same A, one per gamma (a sparsity path), all
+ *    starting from the same x0; X then has m unit columns, not orthonormal.
+ *  - Return value: GPSPCA_OK (0) or a negative GPSPCA_E* code; the message of
+ *    the calling thread's last error is returned by gpspca_last_error().
+ *    Nothing aborts the process or traps the device.
+ *  - Memory: A, x0 and every output buffer belong to the caller.  The library
+ *    borrows them until gpspca_solve returns, or until gpspca_poll returns
+ *    GPSPCA_OK for the ticket; the caller must not free or modify them before.
+ *    The library allocates only its own workspace, counted against the
+ *    context's budget (GPSPCA_ENOMEM when a solve would exceed it).
+ */
+#ifndef GPSPCA_H
+#define GPSPCA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Formulations of Table 1. */
+typedef enum { GPSPCA_SL1 = 0, GPSPCA_SL0 = 1, GPSPCA_BL1 = 2, GPSPCA_BL0 = 3 } gpspca_form;
+
+/* Storage type of A.  F64 solves compute in double; the others compute in
+ * float with double objective, normalisation, Gram matrix and stopping test.
+ * FP8_E4M3 stores q_ri with a per-column float scale s_i: a_ri = q_ri * s_i. */
+typedef enum { GPSPCA_F32 = 0, GPSPCA_BF16 = 1, GPSPCA_FP8_E4M3 = 2, GPSPCA_F64 = 3 } gpspca_dtype;
+
+/* Where a caller buffer lives.  HOST buffers are copied by the library
+ * (host to device before the solve, device to host after it); pinned host
+ * memory makes those copies asynchronous. */
+typedef enum { GPSPCA_DEVICE = 0, GPSPCA_HOST = 1 } gpspca_location;
+
+/* Return codes. */
+#define GPSPCA_OK 0
+#define GPSPCA_PENDING 1          /* gpspca_poll: ticket not finished yet */
+#define GPSPCA_EINVAL (-1)        /* bad shape, pointer, gamma < 0, mu <= 0, m > p (block), m > 64 */
+#define GPSPCA_ENOMEM (-2)        /* workspace would exceed the context budget, or allocation failed */
+#define GPSPCA_ENONFINITE (-3)    /* A has a NaN/Inf entry (or one whose square overflows float) */
+#define GPSPCA_ETIMEDOUT (-4)     /* a device-side wait gave up; the context stays usable */
+#define GPSPCA_EDEGENERATE (-5)   /* block polar step met a rank-deficient Y; outputs hold the last valid X */
+#define GPSPCA_ECUDA (-6)         /* a CUDA runtime call failed */
+#define GPSPCA_ENOTFOUND (-7)     /* gpspca_poll: unknown or already collected ticket */
+
+/* Per-solve termination status, written to out->status[j]. */
+#define GPSPCA_CONVERGED 0   /* |f_k - f_{k-1}| < tol * f_{k-1} */
+#define GPSPCA_MAXIT 1       /* maxit sweeps done */
+#define GPSPCA_ZERO 2        /* f_k == 0: every entry thresholded (or A == 0) */
+#define GPSPCA_DEGENERATE 3  /* lambda_min(Y^T Y) <= 1e-12 lambda_max(Y^T Y) in the polar step */
+
+/* Flags for gpspca_solve / gpspca_submit. */
+#define GPSPCA_GAMMA_RELATIVE 1u  /* gamma[j] is relative: the device scales it to
+                                     gamma[j]*max_i||a_i|| (L1) or (gamma[j]*max_i||a_i||)^2 (L0) */
+
+/* Largest m (components, or gamma values of a path) one solve accepts. */
+#define GPSPCA_MAX_M 64
+
+/* The data matrix A (p x n, column-major, leading dimension ld >= p).
+ * The buffer must hold ld*n elements.  The fast load path wants the base
+ * address 16-byte aligned and ld*sizeof(element) a multiple of 16; other
+ * layouts run on a slower element-wise load path.  col_scale: FP8_E4M3 only,
+ * n floats in the same location as data (NULL otherwise). */
+typedef struct {
+  const void* data;
+  gpspca_dtype dtype;
+  gpspca_location location;
+  int64_t p, n, ld;
+  const float* col_scale;
+} gpspca_matrix;
+
+/* Caller-allocated results, all in `location`.  Element type of X and Z is
+ * double for F64 solves and float otherwise.
+ *   X          p x m column-major (ld p): the iterate that produced the objective
+ *   Z          n x m column-major (ld n): unit-norm (or all-zero) sparse loadings
+ *   support    ceil(n/32) x m uint32 words (may be NULL): bit (i % 32) of word
+ *              j*ceil(n/32) + i/32 is set iff Z[i, j] != 0
+ *   objective  m doubles: per gamma (single-unit) or per component f_j (block;
+ *              the block objective is their sum)
+ *   iters      m int32: sweeps t = A^T x performed
+ *   status     m int32: GPSPCA_CONVERGED / MAXIT / ZERO / DEGENERATE
+ *   gamma_abs  m doubles (may be NULL): the absolute gamma used */
+typedef struct {
+  gpspca_location location;
+  void* X;
+  void* Z;
+  uint32_t* support;
+  double* objective;
+  int32_t* iters;
+  int32_t* status;
+  double* gamma_abs;
+} gpspca_out;
+
+typedef struct gpspca_ctx gpspca_ctx;
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the
+ * library's own workspace (0 = 90% of the device's free memory).
+ * cuda_stream: a cudaStream_t to run on, or NULL for a stream the context
+ * creates.  Section 3's host/device flow: the context owns device workspace
+ * and launches every step on that stream. */
+int gpspca_create(gpspca_ctx** ctx, int device, size_t hbm_budget_bytes, void* cuda_stream);
+
+/* One synchronous solve (Section 2, Table 1).
+ *   A       data matrix descriptor (device or host)
+ *   form    GPSPCA_SL1 / SL0 / BL1 / BL0
+ *   gamma   host array of m values >= 0 (absolute unless GPSPCA_GAMMA_RELATIVE)
+ *   m       1 <= m <= GPSPCA_MAX_M; block forms also need m <= p
+ *   mu      host array of m weights > 0 (block forms), or NULL for all 1;
+ *           must be NULL or all 1 for single-unit forms
+ *   tol     stop when |f_k - f_{k-1}| < tol * f_{k-1} (k >= 1)
+ *   maxit   >= 1: at most maxit sweeps
+ *   x0      optional p x m starting iterate (same location as A; float, or
+ *           double for F64); projected on the feasible set (columns
+ *           normalised, or the polar factor for block forms).  NULL: the
+ *           largest-norm column (single-unit) or the polar factor of the m
+ *           largest-norm columns (block), ties to the lower index.
+ *   flags   GPSPCA_GAMMA_RELATIVE or 0
+ *   out     result buffers
+ * Returns GPSPCA_OK, GPSPCA_EDEGENERATE (outputs valid, see status), or an
+ * error code (outputs undefined). */
+int gpspca_solve(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form, const double* gamma, int32_t m,
+                 const double* mu, double tol, int32_t maxit, const void* x0, uint32_t flags, gpspca_out* out);
+
+/* Asynchronous form of gpspca_solve for many concurrent requests.  The
+ * request is queued; a scheduler thread admits it when its workspace fits the
+ * budget next to the solves already running, and advances every admitted
+ * solve one sweep per scheduling tick, so requests that arrive while others
+ * run join them on the device.  Same arguments and ownership as gpspca_solve
+ * (A and out must be in device memory); *ticket receives the request id. */
+int gpspca_submit(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form, const double* gamma, int32_t m,
+                  const double* mu, double tol, int32_t maxit, uint32_t flags, gpspca_out* out,
+                  uint64_t* ticket);
+
+/* Wait up to wait_us microseconds (0 = just look, < 0 = until done) for a
+ * ticket.  Returns GPSPCA_PENDING, or the ticket's result code (as
+ * gpspca_solve would return it) once, after which the ticket is forgotten. */
+int gpspca_poll(gpspca_ctx* ctx, uint64_t ticket, int32_t wait_us);
+
+/* Finish queued work, free every workspace buffer and the context. */
+int gpspca_destroy(gpspca_ctx* ctx);
+
+/* Message for the calling thread's last error ("" if none). */
+const char* gpspca_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GPSPCA_H */

@@ -19,5 +19,6 @@ from .gpower import (  # noqa: F401
     loadings,
     polar,
     initial_iterate,
+    project_start,
     gpower,
 )

@@ -184,6 +184,22 @@ def initial_iterate(A: np.ndarray, form: str, m: int):
     return X0, None
 
 
+def project_start(x0: np.ndarray, form: str):
+    """A caller's starting iterate, projected on the feasible set: columns
+    normalised (sphere, single-unit) or the polar factor (Stiefel, block).
+    Returns (X0, status) like ``initial_iterate``."""
+    p, m = x0.shape
+    if _is_block(form):
+        X0, degenerate = polar(x0)
+        if degenerate:
+            return np.zeros((p, m)), STATUS_DEGENERATE
+        return X0, None
+    norms = np.linalg.norm(x0, axis=0)
+    if np.any(norms == 0):
+        return np.zeros((p, m)), STATUS_DEGENERATE
+    return x0 / norms, None
+
+
 @dataclass
 class OracleResult:
     """Outcome of one oracle call.
@@ -296,8 +312,8 @@ def gpower(A, form: str, gamma, mu=None, tol: float = 1e-6, maxit: int = 1000, x
       component.
     mu: block weights mu_j > 0 (default all 1); must be all 1 (or None) for
       single-unit forms.
-    x0: optional p x m starting iterate (single-unit: columns normalised by
-      the caller; block: orthonormal).
+    x0: optional p x m starting iterate, projected on the feasible set
+      (``project_start``).
     """
     _check_form(form)
     A = np.asarray(A, dtype=np.float64)
@@ -335,8 +351,7 @@ def gpower(A, form: str, gamma, mu=None, tol: float = 1e-6, maxit: int = 1000, x
     if x0 is None:
         X0, st0 = initial_iterate(A, form, m)
     else:
-        X0 = np.asarray(x0, dtype=np.float64).reshape(p, m).copy()
-        st0 = None
+        X0, st0 = project_start(np.asarray(x0, dtype=np.float64).reshape(p, m), form)
     if st0 is not None:
         status[:] = st0
         return OracleResult(X, Z, objective, iters, status, gamma, mu, history, T_out)

@@ -459,3 +459,22 @@ def test_planted_spike_support_recovery():
         assert r.status[0] == oracle.STATUS_CONVERGED
         union = set(np.flatnonzero(np.any(r.Z != 0, axis=1)).tolist())
         assert set(meta.supports[0].tolist()) <= union
+
+
+def test_start_is_projected_on_the_feasible_set():
+    """A caller's x0 is projected on the sphere (single-unit) or the Stiefel
+    manifold (block): a scaled copy of the default start, or the raw m
+    largest columns, reproduce the default run exactly."""
+    A = _rand(20, 70, 31)
+    c = np.linalg.norm(A, axis=0)
+    g = oracle.gamma_from_rho(A, "SL1", 0.2)
+    ref = oracle.gpower(A, "SL1", g, tol=0.0, maxit=12)
+    i = int(np.argmax(c))
+    alt = oracle.gpower(A, "SL1", g, tol=0.0, maxit=12, x0=5.0 * A[:, i])
+    np.testing.assert_allclose(alt.X, ref.X, atol=1e-14)
+    mu = np.array([1.0, 0.8, 0.6])
+    gb = 0.2 * c.max() * mu
+    refb = oracle.gpower(A, "BL1", gb, mu=mu, tol=0.0, maxit=12)
+    order = np.argsort(-c, kind="stable")[:3]
+    altb = oracle.gpower(A, "BL1", gb, mu=mu, tol=0.0, maxit=12, x0=A[:, order])
+    np.testing.assert_allclose(altb.X, refb.X, atol=1e-13)
