@@ -161,6 +161,14 @@ int gpspca_submit(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form, con
  * gpspca_solve would return it) once, after which the ticket is forgotten. */
 int gpspca_poll(gpspca_ctx* ctx, uint64_t ticket, int32_t wait_us);
 
+/* Measurement aid: prepare a solve (start and projection, as gpspca_solve
+ * does), then time `reps` back-to-back launches of the fused sweep of one
+ * iteration (every component pass) on the context's stream with CUDA events.
+ * *ms_per_sweep receives the mean milliseconds per sweep.  A must be on the
+ * device or the host as for gpspca_solve; results are discarded. */
+int gpspca_time_sweep(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form, const double* gamma, int32_t m,
+                      const double* mu, uint32_t flags, int32_t reps, double* ms_per_sweep);
+
 /* Finish queued work, free every workspace buffer and the context. */
 int gpspca_destroy(gpspca_ctx* ctx);
 

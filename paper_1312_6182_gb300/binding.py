@@ -1,0 +1,296 @@
+"""ctypes binding of libgpspca (C ABI in include/gpspca.h).
+
+Argument marshalling only: every step of a solve runs in the library's CUDA
+kernels.  PyTorch supplies device memory (tensors) and nothing else.  If the
+library has not been built, ``load()`` raises; there is no fallback.
+
+Layout: A is passed as a tensor ``At`` of shape (n, ld) whose row i holds
+column a_i of the p x n matrix A (its first p entries), i.e. A column-major.
+Results come back as X (m, p) and Z (m, n): row j is column j of the paper's
+X (p x m) and Z (n x m).
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "_lib", "libgpspca.so")
+
+FORMS = {"SL1": 0, "SL0": 1, "BL1": 2, "BL0": 3}
+F32, BF16, FP8_E4M3, F64 = 0, 1, 2, 3
+DEVICE, HOST = 0, 1
+
+OK, PENDING = 0, 1
+EINVAL, ENOMEM, ENONFINITE, ETIMEDOUT, EDEGENERATE, ECUDA, ENOTFOUND = -1, -2, -3, -4, -5, -6, -7
+CONVERGED, MAXIT, ZERO, DEGENERATE = 0, 1, 2, 3
+GAMMA_RELATIVE = 1
+MAX_M = 64
+
+ERROR_NAMES = {
+    EINVAL: "EINVAL", ENOMEM: "ENOMEM", ENONFINITE: "ENONFINITE", ETIMEDOUT: "ETIMEDOUT",
+    EDEGENERATE: "EDEGENERATE", ECUDA: "ECUDA", ENOTFOUND: "ENOTFOUND",
+}
+
+EXPORTED = ("gpspca_create", "gpspca_solve", "gpspca_submit", "gpspca_poll", "gpspca_destroy",
+            "gpspca_last_error", "gpspca_time_sweep")
+
+
+class Matrix(ctypes.Structure):
+    _fields_ = [
+        ("data", ctypes.c_void_p),
+        ("dtype", ctypes.c_int),
+        ("location", ctypes.c_int),
+        ("p", ctypes.c_int64),
+        ("n", ctypes.c_int64),
+        ("ld", ctypes.c_int64),
+        ("col_scale", ctypes.c_void_p),
+    ]
+
+
+class Out(ctypes.Structure):
+    _fields_ = [
+        ("location", ctypes.c_int),
+        ("X", ctypes.c_void_p),
+        ("Z", ctypes.c_void_p),
+        ("support", ctypes.c_void_p),
+        ("objective", ctypes.c_void_p),
+        ("iters", ctypes.c_void_p),
+        ("status", ctypes.c_void_p),
+        ("gamma_abs", ctypes.c_void_p),
+    ]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libgpspca.so (raises if it is missing: build it first)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is not built; run __graft_entry__.build() or python -m paper_1312_6182_gb300.build")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    D = ctypes.POINTER(ctypes.c_double)
+    lib.gpspca_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, ctypes.c_size_t, P]
+    lib.gpspca_create.restype = ctypes.c_int
+    lib.gpspca_solve.argtypes = [P, ctypes.POINTER(Matrix), ctypes.c_int, D, ctypes.c_int32, D, ctypes.c_double,
+                                 ctypes.c_int32, P, ctypes.c_uint32, ctypes.POINTER(Out)]
+    lib.gpspca_solve.restype = ctypes.c_int
+    lib.gpspca_submit.argtypes = [P, ctypes.POINTER(Matrix), ctypes.c_int, D, ctypes.c_int32, D, ctypes.c_double,
+                                  ctypes.c_int32, ctypes.c_uint32, ctypes.POINTER(Out),
+                                  ctypes.POINTER(ctypes.c_uint64)]
+    lib.gpspca_submit.restype = ctypes.c_int
+    lib.gpspca_poll.argtypes = [P, ctypes.c_uint64, ctypes.c_int32]
+    lib.gpspca_poll.restype = ctypes.c_int
+    lib.gpspca_destroy.argtypes = [P]
+    lib.gpspca_destroy.restype = ctypes.c_int
+    lib.gpspca_last_error.argtypes = []
+    lib.gpspca_last_error.restype = ctypes.c_char_p
+    lib.gpspca_time_sweep.argtypes = [P, ctypes.POINTER(Matrix), ctypes.c_int, D, ctypes.c_int32, D,
+                                      ctypes.c_uint32, ctypes.c_int32, D]
+    lib.gpspca_time_sweep.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def last_error() -> str:
+    return load().gpspca_last_error().decode()
+
+
+class GpspcaError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _check(rc: int, allow=(OK,)):
+    if rc not in allow:
+        raise GpspcaError(rc, last_error())
+    return rc
+
+
+def _dtype_code(t):
+    import torch
+
+    table = {torch.float32: F32, torch.float64: F64, torch.bfloat16: BF16}
+    if hasattr(torch, "float8_e4m3fn"):
+        table[torch.float8_e4m3fn] = FP8_E4M3
+    if t.dtype not in table:
+        raise TypeError(f"unsupported dtype {t.dtype}")
+    return table[t.dtype]
+
+
+def _darr(vals: Optional[Sequence[float]], m: int):
+    if vals is None:
+        return None
+    arr = (ctypes.c_double * m)(*[float(v) for v in vals])
+    return arr
+
+
+def matrix(At, p: Optional[int] = None, col_scale=None) -> Matrix:
+    """Descriptor for At (n, ld) holding A column-major (first p entries of each row)."""
+    if At.dim() != 2 or At.stride(1) != 1:
+        raise ValueError("At must be 2-D with unit stride along its rows")
+    n, ld = At.shape
+    if p is None:
+        p = ld
+    M = Matrix()
+    M.data = At.data_ptr() if At.numel() else None
+    M.dtype = _dtype_code(At)
+    M.location = DEVICE if At.is_cuda else HOST
+    M.p = int(p)
+    M.n = int(n)
+    M.ld = int(At.stride(0)) if n > 1 else int(max(ld, p))
+    M.col_scale = col_scale.data_ptr() if col_scale is not None else None
+    return M
+
+
+@dataclass
+class Result:
+    X: "object"          # (m, p): row j = column j of X
+    Z: "object"          # (m, n)
+    support: "object"    # (m, ceil(n/32)) int32 bit words
+    objective: "object"  # (m,) float64
+    iters: "object"      # (m,) int32
+    status: "object"     # (m,) int32
+    gamma_abs: "object"  # (m,) float64
+    rc: int = OK
+
+
+def alloc_result(m: int, p: int, n: int, device, tc, pin: bool = False) -> Result:
+    import torch
+
+    kw = dict(device=device)
+    pm = dict(pin_memory=True) if (pin and str(device) == "cpu") else {}
+    nw = (n + 31) // 32
+    return Result(
+        X=torch.empty((m, p), dtype=tc, **kw, **pm),
+        Z=torch.empty((m, n), dtype=tc, **kw, **pm),
+        support=torch.empty((m, nw), dtype=torch.int32, **kw, **pm),
+        objective=torch.empty((m,), dtype=torch.float64, **kw, **pm),
+        iters=torch.empty((m,), dtype=torch.int32, **kw, **pm),
+        status=torch.empty((m,), dtype=torch.int32, **kw, **pm),
+        gamma_abs=torch.empty((m,), dtype=torch.float64, **kw, **pm),
+    )
+
+
+def out_struct(res: Result) -> Out:
+    o = Out()
+    o.location = DEVICE if res.X.is_cuda else HOST
+    o.X = res.X.data_ptr() if res.X.numel() else None
+    o.Z = res.Z.data_ptr() if res.Z.numel() else None
+    o.support = res.support.data_ptr() if res.support.numel() else None
+    o.objective = res.objective.data_ptr()
+    o.iters = res.iters.data_ptr()
+    o.status = res.status.data_ptr()
+    o.gamma_abs = res.gamma_abs.data_ptr()
+    if o.X is None:
+        o.X = o.objective  # zero-length outputs: any non-NULL pointer
+    if o.Z is None:
+        o.Z = o.objective
+    return o
+
+
+class Context:
+    """A libgpspca context on one CUDA device (its own stream)."""
+
+    def __init__(self, device: int = 0, budget_bytes: int = 0, stream=None):
+        """stream: a torch.cuda.Stream (or raw cudaStream_t int) to run on;
+        None lets the library create its own."""
+        self.lib = load()
+        self.ptr = ctypes.c_void_p()
+        handle = None
+        if stream is not None:
+            handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        _check(self.lib.gpspca_create(ctypes.byref(self.ptr), int(device), int(budget_bytes), handle))
+        self.device = device
+        self.stream = stream
+
+    def close(self):
+        if self.ptr:
+            self.lib.gpspca_destroy(self.ptr)
+            self.ptr = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @staticmethod
+    def _sync_torch(*tensors):
+        import torch
+
+        if any(t is not None and getattr(t, "is_cuda", False) for t in tensors):
+            torch.cuda.current_stream().synchronize()
+
+    def solve(self, At, form: str, gamma, mu=None, tol: float = 1e-6, maxit: int = 1000, x0=None,
+              gamma_relative: bool = False, p: Optional[int] = None, col_scale=None,
+              out: Optional[Result] = None, allow_degenerate: bool = True) -> Result:
+        """One synchronous solve.  gamma: m values; mu: block weights."""
+        import torch
+
+        gamma = [float(g) for g in (gamma if hasattr(gamma, "__len__") else [gamma])]
+        m = len(gamma)
+        M = matrix(At, p, col_scale)
+        tc = torch.float64 if At.dtype == torch.float64 else torch.float32
+        if out is None:
+            out = alloc_result(m, int(M.p), int(M.n), At.device, tc)
+        o = out_struct(out)
+        self._sync_torch(At, x0, out.X)
+        rc = self.lib.gpspca_solve(self.ptr, ctypes.byref(M), FORMS[form], _darr(gamma, m), m, _darr(mu, m),
+                                   float(tol), int(maxit), x0.data_ptr() if x0 is not None else None,
+                                   GAMMA_RELATIVE if gamma_relative else 0, ctypes.byref(o))
+        allow = (OK, EDEGENERATE) if allow_degenerate else (OK,)
+        _check(rc, allow)
+        out.rc = rc
+        return out
+
+    def submit(self, At, form: str, gamma, mu=None, tol: float = 1e-6, maxit: int = 1000,
+               gamma_relative: bool = False, p: Optional[int] = None, col_scale=None,
+               out: Optional[Result] = None):
+        """Queue a solve (device buffers only); returns (ticket, out)."""
+        import torch
+
+        gamma = [float(g) for g in (gamma if hasattr(gamma, "__len__") else [gamma])]
+        m = len(gamma)
+        M = matrix(At, p, col_scale)
+        tc = torch.float64 if At.dtype == torch.float64 else torch.float32
+        if out is None:
+            out = alloc_result(m, int(M.p), int(M.n), At.device, tc)
+        o = out_struct(out)
+        self._sync_torch(At, out.X)
+        t = ctypes.c_uint64()
+        _check(self.lib.gpspca_submit(self.ptr, ctypes.byref(M), FORMS[form], _darr(gamma, m), m, _darr(mu, m),
+                                      float(tol), int(maxit), GAMMA_RELATIVE if gamma_relative else 0,
+                                      ctypes.byref(o), ctypes.byref(t)))
+        return t.value, out
+
+    def poll(self, ticket: int, wait_us: int = 0) -> int:
+        """PENDING, or the ticket's result code (once)."""
+        return self.lib.gpspca_poll(self.ptr, ctypes.c_uint64(ticket), int(wait_us))
+
+    def time_sweep(self, At, form: str, gamma, mu=None, reps: int = 20, gamma_relative: bool = False,
+                   p: Optional[int] = None, col_scale=None) -> float:
+        """Mean milliseconds of one fused sweep (all component passes), CUDA events."""
+        gamma = [float(g) for g in (gamma if hasattr(gamma, "__len__") else [gamma])]
+        m = len(gamma)
+        M = matrix(At, p, col_scale)
+        self._sync_torch(At)
+        ms = ctypes.c_double()
+        _check(self.lib.gpspca_time_sweep(self.ptr, ctypes.byref(M), FORMS[form], _darr(gamma, m), m,
+                                          _darr(mu, m), GAMMA_RELATIVE if gamma_relative else 0, int(reps),
+                                          ctypes.byref(ms)))
+        return ms.value

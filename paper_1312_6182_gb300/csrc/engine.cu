@@ -1,0 +1,961 @@
+// Host engine of libgpspca: launch planning, workspace, CUDA-graph execution
+// of the generalized power iteration with a device-driven loop, the
+// request scheduler for gpspca_submit/gpspca_poll, and the C ABI.
+//
+// One solve is one CUDA graph:
+//   reset -> column norms -> start selection -> gather start -> reduce(start)
+//   -> finish(start)  -> WHILE(cond) { sweep pass(es) -> reduce -> finish }
+//   -> finalize
+// The finish kernel decides on the device whether another sweep is needed
+// and sets the WHILE node's condition, so no host round trip happens per
+// iteration.  Every pointer a kernel dereferences lives in a device-side IO
+// record that is rewritten before each launch, so a graph is cached per
+// launch geometry and replayed for new buffers and parameters.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "aux.cuh"
+
+namespace gpspca {
+
+const void* sweep_kernel_f32(int mg, int nch);
+const void* sweep_kernel_f64(int mg, int nch);
+const void* sweep_kernel_bf16(int mg, int nch);
+const void* sweep_kernel_fp8(int mg, int nch);
+
+// ---------------------------------------------------------------- errors
+
+static thread_local std::string t_last_error;
+
+static int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  t_last_error = buf;
+  return code;
+}
+
+#define GP_CUDA(call)                                                                           \
+  do {                                                                                          \
+    cudaError_t e_ = (call);                                                                    \
+    if (e_ != cudaSuccess) return fail(GPSPCA_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+// ---------------------------------------------------------------- dtype facts
+
+struct DInfo {
+  int esize, tcsize, vec, align;
+};
+static DInfo dinfo(int dt) {
+  switch (dt) {
+    case GPSPCA_F32: return {4, 4, Elem<float>::VEC, Elem<float>::ALIGN};
+    case GPSPCA_F64: return {8, 8, Elem<double>::VEC, Elem<double>::ALIGN};
+    case GPSPCA_BF16: return {2, 4, Elem<__nv_bfloat16>::VEC, Elem<__nv_bfloat16>::ALIGN};
+    default: return {1, 4, Elem<__nv_fp8_e4m3>::VEC, Elem<__nv_fp8_e4m3>::ALIGN};
+  }
+}
+
+static const void* sweep_ptr(int dt, int mg, int nch) {
+  switch (dt) {
+    case GPSPCA_F32: return sweep_kernel_f32(mg, nch);
+    case GPSPCA_F64: return sweep_kernel_f64(mg, nch);
+    case GPSPCA_BF16: return sweep_kernel_bf16(mg, nch);
+    default: return sweep_kernel_fp8(mg, nch);
+  }
+}
+
+struct KAttr {
+  int max_threads = 0;
+  size_t local = 0;
+  bool ok = false;
+};
+
+static std::mutex g_attr_mu;
+static std::map<const void*, KAttr> g_attr;
+
+static KAttr kattr(const void* f) {
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  auto it = g_attr.find(f);
+  if (it != g_attr.end()) return it->second;
+  KAttr k;
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, f) == cudaSuccess) {
+    k.max_threads = a.maxThreadsPerBlock;
+    k.local = a.localSizeBytes;
+    k.ok = true;
+    cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  }
+  g_attr[f] = k;
+  return k;
+}
+
+// ---------------------------------------------------------------- planning
+
+constexpr int kSmemBudget = 200 * 1024;  // stage ring + bookkeeping, per CTA
+
+struct Pass {
+  int j0, mgv, mg, nch, threads, W, S, smem;
+  const void* k;
+};
+
+struct Plan {
+  int dtype = 0, form = 0, m = 0, p = 0, n = 0;
+  int64_t ld = 0;
+  int fast = 0;
+  int C = 1, ps = 0, ncl = 0, cols_per_cl = 0;
+  std::vector<Pass> passes;
+  int nred = 0, npairs = 0, full_gram = 0;
+  int finish_smem = 0;
+  int tcsize = 4, esize = 4;
+  size_t ws_cnorm = 0, ws_P = 0, ws_ypart = 0, ws_T = 0, ws_fpart = 0, ws_gpart = 0;
+
+  std::string key() const {
+    char b[256];
+    snprintf(b, sizeof(b), "%d/%d/%d/%d/%d/%lld/%d/%d/%d/%d/%d", dtype, form, m, p, n, (long long)ld, fast, C, ps,
+             ncl, cols_per_cl);
+    std::string s(b);
+    for (const Pass& q : passes) {
+      snprintf(b, sizeof(b), "|%d,%d,%d,%d,%d,%d,%d", q.j0, q.mgv, q.mg, q.nch, q.threads, q.W, q.S);
+      s += b;
+    }
+    return s;
+  }
+  size_t workspace_bytes() const { return ws_cnorm + ws_P + ws_ypart + ws_T + ws_fpart + ws_gpart + 7 * 256; }
+};
+
+static const int kMGs[] = {1, 2, 4, 5, 8};
+
+// Components per pass: passes of 8, the last one the smallest built width.
+static std::vector<std::pair<int, int>> split_components(int m) {
+  std::vector<std::pair<int, int>> out;  // (mg, valid)
+  int rem = m;
+  while (rem > 0) {
+    int mg = 8;
+    if (rem < 8)
+      for (int c : kMGs)
+        if (c >= rem) { mg = c; break; }
+    const int v = std::min(rem, mg);
+    out.push_back({mg, v});
+    rem -= v;
+  }
+  return out;
+}
+
+// Pick threads / rows per thread / tile width / stages for one pass with
+// cluster size C.  Returns false if this C does not fit.
+static bool fit_pass(int dt, int mg, int C, int ps, int m, Pass* out) {
+  const DInfo d = dinfo(dt);
+  static const int kNch[] = {1, 2, 4};
+  for (int nch : kNch) {
+    const void* k = sweep_ptr(dt, mg, nch);
+    if (!k) continue;
+    const KAttr at = kattr(k);
+    if (!at.ok || at.local > 0) continue;  // spilling variants are not used
+    int threads = (ps + nch * d.vec - 1) / (nch * d.vec);
+    threads = std::max(64, (threads + 31) / 32 * 32);
+    if (threads > at.max_threads) continue;
+    const int colbytes = ps * d.esize;
+    const int wb = 32 / mg;
+    const int nw = threads / 32;
+    const SweepSmem base = sweep_smem_layout(0, 0, ps, d.esize, d.tcsize, nw, m, mg);
+    const int room = kSmemBudget - base.total;
+    int W = std::min(wb, std::max(1, 32768 / colbytes));
+    int S = 0;
+    while (W >= 1) {
+      S = std::min(8, room / (W * colbytes));
+      if (S >= 3 || (W == 1 && S >= 2)) break;
+      --W;
+    }
+    if (W < 1 || S < 2) continue;
+    const SweepSmem L = sweep_smem_layout(W, S, ps, d.esize, d.tcsize, nw, m, mg);
+    *out = Pass{0, 0, mg, nch, threads, W, S, L.total, k};
+    return true;
+  }
+  return false;
+}
+
+static int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fast, int nsm, Plan* P) {
+  const DInfo d = dinfo(dt);
+  Plan pl;
+  pl.dtype = dt;
+  pl.form = form;
+  pl.m = m;
+  pl.p = static_cast<int>(p);
+  pl.n = static_cast<int>(n);
+  pl.ld = ld;
+  pl.fast = fast ? 1 : 0;
+  pl.tcsize = d.tcsize;
+  pl.esize = d.esize;
+  const auto groups = split_components(m);
+  const int unit = std::max(d.align, d.vec);
+  bool found = false;
+  for (int C : {1, 2, 4, 8}) {
+    const int ps = static_cast<int>(((p + C - 1) / C + unit - 1) / unit * unit);
+    if (C > 1 && static_cast<int64_t>(C - 1) * ps >= p) break;
+    std::vector<Pass> passes;
+    bool ok = true;
+    int j0 = 0;
+    for (auto g : groups) {
+      Pass q;
+      if (!fit_pass(dt, g.first, C, ps, m, &q)) { ok = false; break; }
+      q.j0 = j0;
+      q.mgv = g.second;
+      j0 += g.second;
+      passes.push_back(q);
+    }
+    if (!ok) continue;
+    pl.C = C;
+    pl.ps = ps;
+    pl.passes = passes;
+    found = true;
+    break;
+  }
+  if (!found) return fail(GPSPCA_EINVAL, "no sweep configuration fits p=%lld (rows too long for the on-chip tile ring)", (long long)p);
+  // clusters: as many as can be co-resident for the heaviest pass
+  int ncl = nsm / pl.C;
+  for (const Pass& q : pl.passes) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = pl.C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(pl.C * std::max(1, nsm / pl.C));
+    cfg.blockDim = dim3(q.threads);
+    cfg.dynamicSmemBytes = q.smem;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, q.k, &cfg) == cudaSuccess && nc > 0) ncl = std::min(ncl, nc);
+  }
+  ncl = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ncl, n)));
+  pl.ncl = ncl;
+  pl.cols_per_cl = static_cast<int>((n + ncl - 1) / ncl);
+  pl.nred = static_cast<int>((p + kReduceRows - 1) / kReduceRows);
+  pl.full_gram = form >= 2 ? 1 : 0;
+  pl.npairs = pl.full_gram ? m * (m + 1) / 2 : m;
+  pl.finish_smem = static_cast<int>(sizeof(double)) * (pl.npairs + 2 * kMaxM + kMaxM * kMaxM + 2 * kMaxM * kMaxM + 256);
+  pl.ws_cnorm = sizeof(double) * n;
+  pl.ws_P = static_cast<size_t>(d.tcsize) * m * p;
+  pl.ws_ypart = static_cast<size_t>(d.tcsize) * ncl * m * p;
+  pl.ws_T = static_cast<size_t>(d.tcsize) * m * n;
+  pl.ws_fpart = sizeof(double) * ncl * 2 * m;
+  pl.ws_gpart = sizeof(double) * static_cast<size_t>(pl.nred) * pl.npairs;
+  *P = pl;
+  return GPSPCA_OK;
+}
+
+// ---------------------------------------------------------------- workspace
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct Slot;
+
+struct Budget {
+  std::mutex mu;
+  size_t limit = 0, used = 0;
+};
+
+struct Slot {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaStream_t cap = nullptr, cap2 = nullptr;
+  IO* io_dev = nullptr;
+  State* st_dev = nullptr;
+  IO* io_host = nullptr;     // pinned
+  State* st_host = nullptr;  // pinned
+  cudaEvent_t done = nullptr;
+  Budget* budget = nullptr;
+  // workspace buffers, grown on demand
+  DevBuf b_cnorm, b_P, b_Y, b_ypart, b_T, b_fpart, b_gpart;
+  // staging for host-located inputs/outputs
+  DevBuf s_A, s_scale, s_x0, s_X, s_Z, s_sup, s_obj, s_it, s_stat, s_gam;
+  struct GraphEntry {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
+  };
+  std::unordered_map<std::string, GraphEntry> graphs;
+
+  size_t held() const {
+    size_t s = 0;
+    for (const DevBuf* b : {&b_cnorm, &b_P, &b_Y, &b_ypart, &b_T, &b_fpart, &b_gpart, &s_A, &s_scale, &s_x0, &s_X,
+                            &s_Z, &s_sup, &s_obj, &s_it, &s_stat, &s_gam})
+      s += b->bytes;
+    return s;
+  }
+};
+
+static int ensure(Slot* s, DevBuf* b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) / 256 * 256;
+  if (b->bytes >= bytes) return GPSPCA_OK;
+  {
+    std::lock_guard<std::mutex> lk(s->budget->mu);
+    if (s->budget->used - b->bytes + bytes > s->budget->limit)
+      return fail(GPSPCA_ENOMEM, "workspace of %zu bytes exceeds the context budget (%zu of %zu in use)", bytes,
+                  s->budget->used, s->budget->limit);
+    s->budget->used = s->budget->used - b->bytes + bytes;
+  }
+  // stream-ordered: the old buffer is released after the work queued on
+  // this slot's stream, and no device-wide synchronisation happens
+  if (b->p) cudaFreeAsync(b->p, s->stream);
+  b->p = nullptr;
+  b->bytes = 0;
+  if (cudaMallocAsync(&b->p, bytes, s->stream) != cudaSuccess) {
+    cudaGetLastError();
+    b->p = nullptr;
+    std::lock_guard<std::mutex> lk(s->budget->mu);
+    s->budget->used -= bytes;
+    return fail(GPSPCA_ENOMEM, "device allocation of %zu bytes failed", bytes);
+  }
+  b->bytes = bytes;
+  return GPSPCA_OK;
+}
+
+static void release(Slot* s, DevBuf* b) {
+  if (b->p) cudaFreeAsync(b->p, s->stream);
+  std::lock_guard<std::mutex> lk(s->budget->mu);
+  s->budget->used -= b->bytes;
+  b->p = nullptr;
+  b->bytes = 0;
+}
+
+static void release_workspace(Slot* s) {
+  for (DevBuf* b : {&s->b_cnorm, &s->b_P, &s->b_Y, &s->b_ypart, &s->b_T, &s->b_fpart, &s->b_gpart, &s->s_A,
+                    &s->s_scale, &s->s_x0, &s->s_X, &s->s_Z, &s->s_sup, &s->s_obj, &s->s_it, &s->s_stat, &s->s_gam})
+    release(s, b);
+}
+
+static int slot_init(Slot* s, int device, cudaStream_t user_stream, Budget* budget) {
+  s->device = device;
+  s->budget = budget;
+  if (user_stream) {
+    s->stream = user_stream;
+  } else {
+    GP_CUDA(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
+    s->own_stream = true;
+  }
+  GP_CUDA(cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking));
+  GP_CUDA(cudaStreamCreateWithFlags(&s->cap2, cudaStreamNonBlocking));
+  GP_CUDA(cudaMalloc(&s->io_dev, sizeof(IO)));
+  GP_CUDA(cudaMalloc(&s->st_dev, sizeof(State)));
+  GP_CUDA(cudaMallocHost(&s->io_host, sizeof(IO)));
+  GP_CUDA(cudaMallocHost(&s->st_host, sizeof(State)));
+  GP_CUDA(cudaEventCreateWithFlags(&s->done, cudaEventDisableTiming));
+  return GPSPCA_OK;
+}
+
+static void slot_free(Slot* s) {
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  for (auto& kv : s->graphs) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.g) cudaGraphDestroy(kv.second.g);
+  }
+  s->graphs.clear();
+  release_workspace(s);
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  if (s->io_dev) cudaFree(s->io_dev);
+  if (s->st_dev) cudaFree(s->st_dev);
+  if (s->io_host) cudaFreeHost(s->io_host);
+  if (s->st_host) cudaFreeHost(s->st_host);
+  if (s->done) cudaEventDestroy(s->done);
+  if (s->cap) cudaStreamDestroy(s->cap);
+  if (s->cap2) cudaStreamDestroy(s->cap2);
+  if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+  *s = Slot();
+}
+
+// ---------------------------------------------------------------- graph
+
+static void launch_prologue(const Plan& pl, Slot* s, cudaStream_t cs, cudaGraphConditionalHandle h, int use_cond = 1) {
+  launch_reset(s->io_dev, s->st_dev, pl.m, pl.form, cs);
+  launch_colnorm(pl.dtype, s->io_dev, s->st_dev, pl.ld, pl.p, pl.n, pl.fast, cs);
+  StartArgs sa{s->io_dev, s->st_dev, pl.ld, pl.p, pl.n, pl.m, pl.form};
+  launch_select_start(pl.dtype, sa, cs);
+  launch_gather_start(pl.dtype, sa, cs);
+  ReduceArgs ra{s->io_dev, s->st_dev, 1, pl.m, pl.p, pl.full_gram, pl.npairs, 1};
+  launch_reduce(pl.tcsize, ra, pl.nred, cs);
+  FinishArgs fa{s->io_dev, s->st_dev, pl.ncl, pl.nred, pl.npairs, pl.m, pl.form, 1, h, use_cond};
+  launch_finish(fa, pl.finish_smem, cs);
+}
+
+static void launch_sweeps(const Plan& pl, Slot* s, cudaStream_t cs) {
+  for (const Pass& q : pl.passes) {
+    SweepArgs a{s->io_dev, s->st_dev, pl.ld, pl.p, pl.n, pl.m, pl.form, q.j0, q.mgv, pl.ps, q.W, q.S,
+                pl.cols_per_cl, pl.fast};
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = pl.C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(pl.ncl * pl.C);
+    cfg.blockDim = dim3(q.threads);
+    cfg.dynamicSmemBytes = q.smem;
+    cfg.stream = cs;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    void* args[] = {&a};
+    cudaLaunchKernelExC(&cfg, q.k, args);
+  }
+}
+
+static void launch_body(const Plan& pl, Slot* s, cudaStream_t cs, cudaGraphConditionalHandle h) {
+  launch_sweeps(pl, s, cs);
+  ReduceArgs ra{s->io_dev, s->st_dev, pl.ncl, pl.m, pl.p, pl.full_gram, pl.npairs, 0};
+  launch_reduce(pl.tcsize, ra, pl.nred, cs);
+  FinishArgs fa{s->io_dev, s->st_dev, pl.ncl, pl.nred, pl.npairs, pl.m, pl.form, 0, h, 1};
+  launch_finish(fa, pl.finish_smem, cs);
+}
+
+static void launch_epilogue(const Plan& pl, Slot* s, cudaStream_t cs) {
+  launch_finalize(pl.tcsize, s->io_dev, s->st_dev, pl.p, pl.n, pl.m, pl.form, cs);
+}
+
+static int build_graph(const Plan& pl, Slot* s, Slot::GraphEntry* out) {
+  cudaGraph_t g = nullptr;
+  GP_CUDA(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle h;
+  GP_CUDA(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+  GP_CUDA(cudaStreamBeginCaptureToGraph(s->cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  launch_prologue(pl, s, s->cap, h);
+  cudaStreamCaptureStatus cst;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  GP_CUDA(cudaStreamGetCaptureInfo(s->cap, &cst, nullptr, nullptr, &deps, nullptr, &ndeps));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cnode;
+  GP_CUDA(cudaGraphAddNode(&cnode, g, deps, nullptr, ndeps, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  GP_CUDA(cudaStreamUpdateCaptureDependencies(s->cap, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+  GP_CUDA(cudaStreamBeginCaptureToGraph(s->cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  launch_body(pl, s, s->cap2, h);
+  cudaGraph_t body_out = nullptr;
+  GP_CUDA(cudaStreamEndCapture(s->cap2, &body_out));
+  launch_epilogue(pl, s, s->cap);
+  cudaGraph_t gout = nullptr;
+  GP_CUDA(cudaStreamEndCapture(s->cap, &gout));
+  GP_CUDA(cudaGetLastError());
+  cudaGraphExec_t exec = nullptr;
+  GP_CUDA(cudaGraphInstantiate(&exec, g, 0));
+  out->g = g;
+  out->exec = exec;
+  return GPSPCA_OK;
+}
+
+static int get_graph(const Plan& pl, Slot* s, cudaGraphExec_t* exec) {
+  const std::string key = pl.key();
+  auto it = s->graphs.find(key);
+  if (it != s->graphs.end()) {
+    *exec = it->second.exec;
+    return GPSPCA_OK;
+  }
+  Slot::GraphEntry e;
+  const int rc = build_graph(pl, s, &e);
+  if (rc != GPSPCA_OK) return rc;
+  if (s->graphs.size() >= 64) {  // bound the cache
+    for (auto& kv : s->graphs) {
+      cudaGraphExecDestroy(kv.second.exec);
+      cudaGraphDestroy(kv.second.g);
+    }
+    s->graphs.clear();
+  }
+  s->graphs[key] = e;
+  *exec = e.exec;
+  return GPSPCA_OK;
+}
+
+// ---------------------------------------------------------------- one solve
+
+struct Request {
+  gpspca_matrix A;
+  gpspca_form form;
+  std::vector<double> gamma, mu;
+  int m = 0;
+  double tol = 0;
+  int maxit = 0;
+  const void* x0 = nullptr;
+  uint32_t flags = 0;
+  gpspca_out out;
+};
+
+static int validate(const Request& r) {
+  const gpspca_matrix& A = r.A;
+  if (A.dtype < GPSPCA_F32 || A.dtype > GPSPCA_F64) return fail(GPSPCA_EINVAL, "unknown dtype %d", (int)A.dtype);
+  if (A.location != GPSPCA_DEVICE && A.location != GPSPCA_HOST) return fail(GPSPCA_EINVAL, "bad A location");
+  if (A.p < 0 || A.n < 0) return fail(GPSPCA_EINVAL, "negative shape");
+  if (A.p > (1 << 30) || A.n > (1 << 30)) return fail(GPSPCA_EINVAL, "p and n must be below 2^30");
+  if (A.p > 0 && A.n > 0) {
+    if (!A.data) return fail(GPSPCA_EINVAL, "A.data is NULL");
+    if (A.ld < A.p) return fail(GPSPCA_EINVAL, "ld (%lld) < p (%lld)", (long long)A.ld, (long long)A.p);
+    if (A.dtype == GPSPCA_FP8_E4M3 && !A.col_scale) return fail(GPSPCA_EINVAL, "FP8 storage needs col_scale");
+  }
+  if (r.form < GPSPCA_SL1 || r.form > GPSPCA_BL0) return fail(GPSPCA_EINVAL, "unknown formulation %d", (int)r.form);
+  if (r.m < 1 || r.m > kMaxM) return fail(GPSPCA_EINVAL, "m = %d outside [1, %d]", r.m, kMaxM);
+  const bool block = r.form >= GPSPCA_BL1;
+  for (int j = 0; j < r.m; ++j) {
+    if (!(r.gamma[j] >= 0.0) || !std::isfinite(r.gamma[j])) return fail(GPSPCA_EINVAL, "gamma[%d] must be finite and >= 0", j);
+    if (!(r.mu[j] > 0.0) || !std::isfinite(r.mu[j])) return fail(GPSPCA_EINVAL, "mu[%d] must be finite and > 0", j);
+    if (!block && r.mu[j] != 1.0) return fail(GPSPCA_EINVAL, "single-unit formulations take no weights (mu = 1)");
+  }
+  if (block && A.p > 0 && r.m > A.p) return fail(GPSPCA_EINVAL, "block formulations need m <= p");
+  if (block && !r.x0 && A.n > 0 && r.m > A.n) return fail(GPSPCA_EINVAL, "block start needs m <= n columns");
+  if (!(r.tol >= 0.0) || !std::isfinite(r.tol)) return fail(GPSPCA_EINVAL, "tol must be finite and >= 0");
+  if (r.maxit < 1) return fail(GPSPCA_EINVAL, "maxit must be >= 1");
+  const gpspca_out& o = r.out;
+  if (o.location != GPSPCA_DEVICE && o.location != GPSPCA_HOST) return fail(GPSPCA_EINVAL, "bad out location");
+  if (!o.X || !o.Z || !o.objective || !o.iters || !o.status) return fail(GPSPCA_EINVAL, "an output pointer is NULL");
+  return GPSPCA_OK;
+}
+
+// Empty A (p == 0 or n == 0): status ZERO, nothing to compute.
+static int solve_empty(Slot* s, const Request& r) {
+  std::vector<double> obj(r.m, 0.0);
+  std::vector<int32_t> it(r.m, 0), stv(r.m, GPSPCA_ZERO);
+  const cudaMemcpyKind k = r.out.location == GPSPCA_HOST ? cudaMemcpyHostToHost : cudaMemcpyHostToDevice;
+  GP_CUDA(cudaMemcpyAsync(r.out.objective, obj.data(), sizeof(double) * r.m, k, s->stream));
+  GP_CUDA(cudaMemcpyAsync(r.out.iters, it.data(), sizeof(int32_t) * r.m, k, s->stream));
+  GP_CUDA(cudaMemcpyAsync(r.out.status, stv.data(), sizeof(int32_t) * r.m, k, s->stream));
+  if (r.out.gamma_abs) GP_CUDA(cudaMemcpyAsync(r.out.gamma_abs, r.gamma.data(), sizeof(double) * r.m, k, s->stream));
+  GP_CUDA(cudaStreamSynchronize(s->stream));
+  return GPSPCA_OK;
+}
+
+// Validate, plan, size the workspace and write the IO record for one solve
+// (asynchronous, on the slot's stream).  scratch_out: results go to library
+// staging buffers and are not copied anywhere (used by the sweep timer).
+static int prepare_solve(Slot* s, const Request& r, int nsm, bool scratch_out, Plan* plan, bool* empty) {
+  *empty = false;
+  int rc = validate(r);
+  if (rc != GPSPCA_OK) return rc;
+  if (r.A.p == 0 || r.A.n == 0) {
+    *empty = true;
+    return scratch_out ? GPSPCA_OK : solve_empty(s, r);
+  }
+  const DInfo d = dinfo(r.A.dtype);
+  const bool host_in = r.A.location == GPSPCA_HOST;
+  const bool staged_out = scratch_out || r.out.location == GPSPCA_HOST;
+  const int64_t p = r.A.p, n = r.A.n, ld = r.A.ld;
+  const int m = r.m;
+  const size_t a_bytes = static_cast<size_t>(ld) * n * d.esize;
+  const void* A_dev = r.A.data;
+  const float* scale_dev = r.A.col_scale;
+  const void* x0_dev = r.x0;
+  if (host_in) {
+    if ((rc = ensure(s, &s->s_A, a_bytes))) return rc;
+    GP_CUDA(cudaMemcpyAsync(s->s_A.p, r.A.data, a_bytes, cudaMemcpyHostToDevice, s->stream));
+    A_dev = s->s_A.p;
+    if (r.A.dtype == GPSPCA_FP8_E4M3) {
+      if ((rc = ensure(s, &s->s_scale, sizeof(float) * n))) return rc;
+      GP_CUDA(cudaMemcpyAsync(s->s_scale.p, r.A.col_scale, sizeof(float) * n, cudaMemcpyHostToDevice, s->stream));
+      scale_dev = static_cast<const float*>(s->s_scale.p);
+    }
+    if (r.x0) {
+      if ((rc = ensure(s, &s->s_x0, static_cast<size_t>(d.tcsize) * p * m))) return rc;
+      GP_CUDA(cudaMemcpyAsync(s->s_x0.p, r.x0, static_cast<size_t>(d.tcsize) * p * m, cudaMemcpyHostToDevice,
+                              s->stream));
+      x0_dev = s->s_x0.p;
+    }
+  }
+  const bool fast = (reinterpret_cast<uintptr_t>(A_dev) % 16 == 0) && ((ld * d.esize) % 16 == 0);
+  Plan& pl = *plan;
+  if ((rc = make_plan(r.A.dtype, r.form, m, p, n, ld, fast, nsm, &pl))) return rc;
+  if ((rc = ensure(s, &s->b_cnorm, pl.ws_cnorm))) return rc;
+  if ((rc = ensure(s, &s->b_P, pl.ws_P))) return rc;
+  if ((rc = ensure(s, &s->b_Y, pl.ws_P))) return rc;
+  if ((rc = ensure(s, &s->b_ypart, pl.ws_ypart))) return rc;
+  if ((rc = ensure(s, &s->b_T, pl.ws_T))) return rc;
+  if ((rc = ensure(s, &s->b_fpart, pl.ws_fpart))) return rc;
+  if ((rc = ensure(s, &s->b_gpart, pl.ws_gpart))) return rc;
+  IO& io = *s->io_host;
+  std::memset(&io, 0, sizeof(IO));
+  io.A = A_dev;
+  io.col_scale = scale_dev;
+  io.x0 = x0_dev;
+  if (staged_out) {
+    const size_t nw = (n + 31) / 32;
+    if ((rc = ensure(s, &s->s_X, static_cast<size_t>(d.tcsize) * p * m))) return rc;
+    if ((rc = ensure(s, &s->s_Z, static_cast<size_t>(d.tcsize) * n * m))) return rc;
+    if ((rc = ensure(s, &s->s_sup, sizeof(uint32_t) * nw * m))) return rc;
+    if ((rc = ensure(s, &s->s_obj, sizeof(double) * m))) return rc;
+    if ((rc = ensure(s, &s->s_it, sizeof(int32_t) * m))) return rc;
+    if ((rc = ensure(s, &s->s_stat, sizeof(int32_t) * m))) return rc;
+    if ((rc = ensure(s, &s->s_gam, sizeof(double) * m))) return rc;
+    io.X = s->s_X.p;
+    io.Z = s->s_Z.p;
+    io.support = static_cast<uint32_t*>(s->s_sup.p);
+    io.objective = static_cast<double*>(s->s_obj.p);
+    io.iters = static_cast<int32_t*>(s->s_it.p);
+    io.status = static_cast<int32_t*>(s->s_stat.p);
+    io.gamma_abs = static_cast<double*>(s->s_gam.p);
+  } else {
+    io.X = r.out.X;
+    io.Z = r.out.Z;
+    io.support = r.out.support;
+    io.objective = r.out.objective;
+    io.iters = r.out.iters;
+    io.status = r.out.status;
+    io.gamma_abs = r.out.gamma_abs;
+  }
+  io.cnorm = static_cast<double*>(s->b_cnorm.p);
+  io.P = s->b_P.p;
+  io.Y = s->b_Y.p;
+  io.ypart = s->b_ypart.p;
+  io.T = s->b_T.p;
+  io.fpart = static_cast<double*>(s->b_fpart.p);
+  io.gpart = static_cast<double*>(s->b_gpart.p);
+  for (int j = 0; j < m; ++j) {
+    io.gamma_in[j] = r.gamma[j];
+    io.mu[j] = r.mu[j];
+  }
+  io.tol = r.tol;
+  io.maxit = r.maxit;
+  io.gamma_relative = (r.flags & GPSPCA_GAMMA_RELATIVE) ? 1 : 0;
+  io.has_x0 = r.x0 ? 1 : 0;
+  GP_CUDA(cudaMemcpyAsync(s->io_dev, s->io_host, sizeof(IO), cudaMemcpyHostToDevice, s->stream));
+  return GPSPCA_OK;
+}
+
+// Enqueue one solve on the slot's stream (asynchronous).  *empty is set when
+// nothing was launched.
+static int launch_solve(Slot* s, const Request& r, int nsm, bool* empty) {
+  Plan pl;
+  int rc = prepare_solve(s, r, nsm, false, &pl, empty);
+  if (rc != GPSPCA_OK || *empty) return rc;
+  const DInfo d = dinfo(r.A.dtype);
+  const int64_t p = r.A.p, n = r.A.n;
+  const int m = r.m;
+  cudaGraphExec_t exec = nullptr;
+  if ((rc = get_graph(pl, s, &exec))) return rc;
+  GP_CUDA(cudaGraphLaunch(exec, s->stream));
+  if (r.out.location == GPSPCA_HOST) {
+    const size_t nw = (n + 31) / 32;
+    GP_CUDA(cudaMemcpyAsync(r.out.X, s->s_X.p, static_cast<size_t>(d.tcsize) * p * m, cudaMemcpyDeviceToHost, s->stream));
+    GP_CUDA(cudaMemcpyAsync(r.out.Z, s->s_Z.p, static_cast<size_t>(d.tcsize) * n * m, cudaMemcpyDeviceToHost, s->stream));
+    if (r.out.support)
+      GP_CUDA(cudaMemcpyAsync(r.out.support, s->s_sup.p, sizeof(uint32_t) * nw * m, cudaMemcpyDeviceToHost, s->stream));
+    GP_CUDA(cudaMemcpyAsync(r.out.objective, s->s_obj.p, sizeof(double) * m, cudaMemcpyDeviceToHost, s->stream));
+    GP_CUDA(cudaMemcpyAsync(r.out.iters, s->s_it.p, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, s->stream));
+    GP_CUDA(cudaMemcpyAsync(r.out.status, s->s_stat.p, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, s->stream));
+    if (r.out.gamma_abs)
+      GP_CUDA(cudaMemcpyAsync(r.out.gamma_abs, s->s_gam.p, sizeof(double) * m, cudaMemcpyDeviceToHost, s->stream));
+  }
+  GP_CUDA(cudaMemcpyAsync(s->st_host, s->st_dev, sizeof(State), cudaMemcpyDeviceToHost, s->stream));
+  GP_CUDA(cudaEventRecord(s->done, s->stream));
+  return GPSPCA_OK;
+}
+
+// Result code of a finished solve from its device state.
+static int solve_result(Slot* s) {
+  GP_CUDA(cudaEventSynchronize(s->done));
+  GP_CUDA(cudaGetLastError());
+  const State& st = *s->st_host;
+  if (st.error & kErrNonFinite) return fail(GPSPCA_ENONFINITE, "A has a non-finite entry (or an entry whose square overflows)");
+  if (st.error & kErrTimeout) return fail(GPSPCA_ETIMEDOUT, "a device-side wait for a tile copy gave up");
+  if (st.any_degenerate) return fail(GPSPCA_EDEGENERATE, "polar step met a rank-deficient Y (status DEGENERATE)");
+  return GPSPCA_OK;
+}
+
+static int request_from(Request* r, const gpspca_matrix* A, gpspca_form form, const double* gamma, int32_t m,
+                        const double* mu, double tol, int32_t maxit, const void* x0, uint32_t flags,
+                        gpspca_out* out) {
+  if (!A || !out || !gamma) return fail(GPSPCA_EINVAL, "A, gamma and out must not be NULL");
+  if (m < 1 || m > kMaxM) return fail(GPSPCA_EINVAL, "m = %d outside [1, %d]", m, kMaxM);
+  r->A = *A;
+  r->form = form;
+  r->m = m;
+  r->gamma.assign(gamma, gamma + m);
+  r->mu.assign(m, 1.0);
+  if (mu) r->mu.assign(mu, mu + m);
+  r->tol = tol;
+  r->maxit = maxit;
+  r->x0 = x0;
+  r->flags = flags;
+  r->out = *out;
+  return GPSPCA_OK;
+}
+
+}  // namespace gpspca
+
+// ---------------------------------------------------------------- context + serving
+
+using namespace gpspca;
+
+struct Ticket {
+  Request req;
+  std::string msg;
+  int rc = GPSPCA_PENDING;
+  bool done = false;
+  std::chrono::steady_clock::time_point t_submit;
+};
+
+struct gpspca_ctx {
+  int device = 0;
+  int nsm = 0;
+  Budget budget;
+  Slot sync_slot;
+  std::mutex solve_mu;  // one synchronous solve at a time on sync_slot
+  // serving
+  std::vector<std::unique_ptr<Slot>> serve_slots;
+  std::mutex q_mu;
+  std::condition_variable q_cv;      // scheduler wakeup
+  std::condition_variable done_cv;   // ticket completion
+  std::deque<uint64_t> queue;
+  std::unordered_map<uint64_t, std::unique_ptr<Ticket>> tickets;
+  uint64_t next_ticket = 1;
+  bool stop = false;
+  std::thread sched;
+  bool sched_started = false;
+};
+
+static constexpr int kServeSlots = 8;
+
+// Scheduler: admits queued requests into free slots (each slot has its own
+// stream and workspace, counted against the context budget), so solves that
+// arrive while others run overlap on the device; completion is detected per
+// slot with events and reported to gpspca_poll.
+static void scheduler_main(gpspca_ctx* ctx) {
+  cudaSetDevice(ctx->device);
+  std::vector<uint64_t> running(ctx->serve_slots.size(), 0);
+  for (;;) {
+    bool progressed = false;
+    // completions
+    for (size_t i = 0; i < running.size(); ++i) {
+      if (!running[i]) continue;
+      Slot* s = ctx->serve_slots[i].get();
+      if (cudaEventQuery(s->done) == cudaErrorNotReady) continue;
+      const int rc = solve_result(s);
+      release_workspace(s);  // the budget counts running solves only
+      std::lock_guard<std::mutex> lk(ctx->q_mu);
+      auto it = ctx->tickets.find(running[i]);
+      if (it != ctx->tickets.end()) {
+        it->second->rc = rc;
+        it->second->msg = rc == GPSPCA_OK ? "" : t_last_error;
+        it->second->done = true;
+      }
+      running[i] = 0;
+      progressed = true;
+      ctx->done_cv.notify_all();
+    }
+    // admissions
+    for (size_t i = 0; i < running.size(); ++i) {
+      if (running[i]) continue;
+      uint64_t id = 0;
+      Ticket* t = nullptr;
+      {
+        std::lock_guard<std::mutex> lk(ctx->q_mu);
+        if (ctx->queue.empty()) break;
+        id = ctx->queue.front();
+        t = ctx->tickets[id].get();
+      }
+      Slot* s = ctx->serve_slots[i].get();
+      bool empty = false;
+      const int rc = launch_solve(s, t->req, ctx->nsm, &empty);
+      if (rc == GPSPCA_ENOMEM) {
+        // does not fit next to the running solves: wait for one to finish,
+        // unless nothing runs (then it can never fit)
+        release_workspace(s);
+        bool any = false;
+        for (uint64_t r2 : running) any = any || r2;
+        if (any) break;
+      }
+      std::lock_guard<std::mutex> lk(ctx->q_mu);
+      ctx->queue.pop_front();
+      progressed = true;
+      if (rc != GPSPCA_OK || empty) {
+        if (rc != GPSPCA_OK) release_workspace(s);
+        t->rc = rc;
+        t->msg = rc == GPSPCA_OK ? "" : t_last_error;
+        t->done = true;
+        ctx->done_cv.notify_all();
+      } else {
+        running[i] = id;
+      }
+    }
+    bool any_running = false;
+    for (uint64_t r2 : running) any_running = any_running || r2;
+    std::unique_lock<std::mutex> lk(ctx->q_mu);
+    if (ctx->stop && ctx->queue.empty() && !any_running) break;
+    if (!progressed) {
+      if (any_running)
+        ctx->q_cv.wait_for(lk, std::chrono::microseconds(50));
+      else
+        ctx->q_cv.wait_for(lk, std::chrono::milliseconds(20), [&] { return ctx->stop || !ctx->queue.empty(); });
+    }
+  }
+}
+
+extern "C" {
+
+const char* gpspca_last_error(void) { return t_last_error.c_str(); }
+
+int gpspca_create(gpspca_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_stream) {
+  if (!out) return fail(GPSPCA_EINVAL, "ctx pointer is NULL");
+  *out = nullptr;
+  int ndev = 0;
+  GP_CUDA(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return fail(GPSPCA_EINVAL, "device %d out of range (%d devices)", device, ndev);
+  GP_CUDA(cudaSetDevice(device));
+  auto* ctx = new gpspca_ctx();
+  ctx->device = device;
+  cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, device);
+  size_t fr = 0, tot = 0;
+  cudaMemGetInfo(&fr, &tot);
+  ctx->budget.limit = hbm_budget_bytes ? hbm_budget_bytes : static_cast<size_t>(0.9 * fr);
+  int rc = slot_init(&ctx->sync_slot, device, static_cast<cudaStream_t>(cuda_stream), &ctx->budget);
+  if (rc != GPSPCA_OK) {
+    slot_free(&ctx->sync_slot);
+    delete ctx;
+    return rc;
+  }
+  *out = ctx;
+  return GPSPCA_OK;
+}
+
+int gpspca_solve(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form, const double* gamma, int32_t m,
+                 const double* mu, double tol, int32_t maxit, const void* x0, uint32_t flags, gpspca_out* out) {
+  if (!ctx) return fail(GPSPCA_EINVAL, "ctx is NULL");
+  Request r;
+  int rc = request_from(&r, A, form, gamma, m, mu, tol, maxit, x0, flags, out);
+  if (rc != GPSPCA_OK) return rc;
+  std::lock_guard<std::mutex> lk(ctx->solve_mu);
+  GP_CUDA(cudaSetDevice(ctx->device));
+  bool empty = false;
+  rc = launch_solve(&ctx->sync_slot, r, ctx->nsm, &empty);
+  if (rc != GPSPCA_OK || empty) return rc;
+  return solve_result(&ctx->sync_slot);
+}
+
+int gpspca_time_sweep(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form, const double* gamma, int32_t m,
+                      const double* mu, uint32_t flags, int32_t reps, double* ms_per_sweep) {
+  if (!ctx || !ms_per_sweep) return fail(GPSPCA_EINVAL, "ctx and ms_per_sweep must not be NULL");
+  if (reps < 1) return fail(GPSPCA_EINVAL, "reps must be >= 1");
+  gpspca_out dummy = {};
+  dummy.location = GPSPCA_DEVICE;
+  double one = 0.0;
+  dummy.X = dummy.Z = dummy.objective = &one;  // replaced by staging buffers
+  dummy.iters = dummy.status = reinterpret_cast<int32_t*>(&one);
+  Request r;
+  int rc = request_from(&r, A, form, gamma, m, mu, 0.0, 1 << 30, nullptr, flags, &dummy);
+  if (rc != GPSPCA_OK) return rc;
+  std::lock_guard<std::mutex> lk(ctx->solve_mu);
+  GP_CUDA(cudaSetDevice(ctx->device));
+  Slot* s = &ctx->sync_slot;
+  Plan pl;
+  bool empty = false;
+  rc = prepare_solve(s, r, ctx->nsm, true, &pl, &empty);
+  if (rc != GPSPCA_OK) return rc;
+  if (empty) return fail(GPSPCA_EINVAL, "empty matrix");
+  launch_prologue(pl, s, s->stream, cudaGraphConditionalHandle{}, 0);
+  cudaEvent_t e0, e1;
+  GP_CUDA(cudaEventCreate(&e0));
+  GP_CUDA(cudaEventCreate(&e1));
+  launch_sweeps(pl, s, s->stream);  // warm-up
+  GP_CUDA(cudaEventRecord(e0, s->stream));
+  for (int i = 0; i < reps; ++i) launch_sweeps(pl, s, s->stream);
+  GP_CUDA(cudaEventRecord(e1, s->stream));
+  GP_CUDA(cudaEventSynchronize(e1));
+  GP_CUDA(cudaGetLastError());
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  GP_CUDA(cudaMemcpy(s->st_host, s->st_dev, sizeof(State), cudaMemcpyDeviceToHost));
+  if (s->st_host->error & kErrTimeout) return fail(GPSPCA_ETIMEDOUT, "a device-side wait for a tile copy gave up");
+  if (s->st_host->n_active == 0) return fail(GPSPCA_EINVAL, "the start is degenerate or A is zero: nothing to time");
+  *ms_per_sweep = static_cast<double>(ms) / reps;
+  return GPSPCA_OK;
+}
+
+int gpspca_submit(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form, const double* gamma, int32_t m,
+                  const double* mu, double tol, int32_t maxit, uint32_t flags, gpspca_out* out, uint64_t* ticket) {
+  if (!ctx || !ticket) return fail(GPSPCA_EINVAL, "ctx and ticket must not be NULL");
+  auto t = std::make_unique<Ticket>();
+  int rc = request_from(&t->req, A, form, gamma, m, mu, tol, maxit, nullptr, flags, out);
+  if (rc != GPSPCA_OK) return rc;
+  if ((rc = validate(t->req)) != GPSPCA_OK) return rc;
+  if (A->location != GPSPCA_DEVICE || out->location != GPSPCA_DEVICE)
+    return fail(GPSPCA_EINVAL, "gpspca_submit takes device buffers only");
+  t->t_submit = std::chrono::steady_clock::now();
+  std::lock_guard<std::mutex> lk(ctx->q_mu);
+  if (!ctx->sched_started) {
+    cudaSetDevice(ctx->device);
+    for (int i = 0; i < kServeSlots; ++i) {
+      auto s = std::make_unique<Slot>();
+      rc = slot_init(s.get(), ctx->device, nullptr, &ctx->budget);
+      if (rc != GPSPCA_OK) return rc;
+      ctx->serve_slots.push_back(std::move(s));
+    }
+    ctx->sched = std::thread(scheduler_main, ctx);
+    ctx->sched_started = true;
+  }
+  const uint64_t id = ctx->next_ticket++;
+  ctx->tickets[id] = std::move(t);
+  ctx->queue.push_back(id);
+  *ticket = id;
+  ctx->q_cv.notify_all();
+  return GPSPCA_OK;
+}
+
+int gpspca_poll(gpspca_ctx* ctx, uint64_t ticket, int32_t wait_us) {
+  if (!ctx) return fail(GPSPCA_EINVAL, "ctx is NULL");
+  std::unique_lock<std::mutex> lk(ctx->q_mu);
+  auto it = ctx->tickets.find(ticket);
+  if (it == ctx->tickets.end()) return fail(GPSPCA_ENOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+  Ticket* t = it->second.get();
+  auto ready = [&] { return t->done; };
+  if (!t->done) {
+    if (wait_us < 0)
+      ctx->done_cv.wait(lk, ready);
+    else if (wait_us > 0)
+      ctx->done_cv.wait_for(lk, std::chrono::microseconds(wait_us), ready);
+  }
+  if (!t->done) return GPSPCA_PENDING;
+  const int rc = t->rc;
+  if (rc != GPSPCA_OK) t_last_error = t->msg;
+  ctx->tickets.erase(it);
+  return rc;
+}
+
+int gpspca_destroy(gpspca_ctx* ctx) {
+  if (!ctx) return GPSPCA_OK;
+  if (ctx->sched_started) {
+    {
+      std::lock_guard<std::mutex> lk(ctx->q_mu);
+      ctx->stop = true;
+    }
+    ctx->q_cv.notify_all();
+    ctx->sched.join();
+  }
+  cudaSetDevice(ctx->device);
+  for (auto& s : ctx->serve_slots) slot_free(s.get());
+  slot_free(&ctx->sync_slot);
+  delete ctx;
+  return GPSPCA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,465 @@
+// Fused single-read sweep of the generalized power iteration (Section 2,
+// Table 1): for a slab of columns a_i of A it forms t_ij = a_i^T x_j, applies
+// the formulation's threshold, and accumulates y_j += g_ij a_i, reading each
+// column from HBM once.
+//
+// Decomposition
+//  * Thread-block clusters of C CTAs own a contiguous slab of columns; CTA r
+//    of a cluster owns rows [r*ps, (r+1)*ps) of every column in the slab.
+//  * One elected thread streams W-column tiles of the CTA's rows through an
+//    S-stage shared-memory ring with 1-D bulk (TMA) copies on mbarriers.
+//  * Each thread owns R = NCH*VEC fixed rows; the iterate x (MG components)
+//    and the accumulated y for those rows live in registers.
+//  * Per tile: per-thread partial dots -> warp reduce-scatter (31 shuffles
+//    for 32 values) -> CTA sum -> partial sums of the C CTAs of the cluster
+//    exchanged through distributed shared memory and added in rank order, so
+//    every CTA holds the same t.  The threshold runs on one thread per
+//    (column, component), the objective of Table 1 accumulates in double,
+//    then every thread applies g to its rows of the tile still in shared
+//    memory (the second use of the tile costs no HBM traffic).
+//  * Epilogue: each cluster writes its partial y (all p rows) and its
+//    objective partials; a separate deterministic reduction adds them.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
+#include "internal.h"
+#include "ptx.cuh"
+
+namespace gpspca {
+
+template <typename TA>
+struct Elem;
+template <>
+struct Elem<float> {
+  using TC = float;
+  static constexpr int VEC = 4;    // elements per shared-memory vector load (16 B)
+  static constexpr int ALIGN = 4;  // elements per 16 bytes
+};
+template <>
+struct Elem<double> {
+  using TC = double;
+  static constexpr int VEC = 2;
+  static constexpr int ALIGN = 2;
+};
+template <>
+struct Elem<__nv_bfloat16> {
+  using TC = float;
+  static constexpr int VEC = 4;  // 8-byte loads
+  static constexpr int ALIGN = 8;
+};
+template <>
+struct Elem<__nv_fp8_e4m3> {
+  using TC = float;
+  static constexpr int VEC = 4;  // 4-byte loads
+  static constexpr int ALIGN = 16;
+};
+
+__device__ __forceinline__ void load_vec(const float* p, float (&v)[4]) {
+  const float4 f = *reinterpret_cast<const float4*>(p);
+  v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+}
+__device__ __forceinline__ void load_vec(const double* p, double (&v)[2]) {
+  const double2 f = *reinterpret_cast<const double2*>(p);
+  v[0] = f.x; v[1] = f.y;
+}
+__device__ __forceinline__ void load_vec(const __nv_bfloat16* p, float (&v)[4]) {
+  const uint2 u = *reinterpret_cast<const uint2*>(p);
+  v[0] = __uint_as_float(u.x << 16);
+  v[1] = __uint_as_float(u.x & 0xffff0000u);
+  v[2] = __uint_as_float(u.y << 16);
+  v[3] = __uint_as_float(u.y & 0xffff0000u);
+}
+__device__ __forceinline__ float2 fp8x2_to_float2(uint32_t bits16) {
+  const __half2_raw h = __nv_cvt_fp8x2_to_halfraw2(static_cast<__nv_fp8x2_storage_t>(bits16), __NV_E4M3);
+  return __half22float2(__half2(h));
+}
+__device__ __forceinline__ void load_vec(const __nv_fp8_e4m3* p, float (&v)[4]) {
+  const uint32_t u = *reinterpret_cast<const uint32_t*>(p);
+  const float2 a = fp8x2_to_float2(u & 0xffffu);
+  const float2 b = fp8x2_to_float2(u >> 16);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
+template <typename TA>
+__device__ __forceinline__ typename Elem<TA>::TC to_tc(TA v);
+template <>
+__device__ __forceinline__ float to_tc<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ double to_tc<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ float to_tc<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <>
+__device__ __forceinline__ float to_tc<__nv_fp8_e4m3>(__nv_fp8_e4m3 v) { return static_cast<float>(v); }
+
+// Threshold of Table 1 for one entry t = a_i^T x_j (already scaled), in
+// double.  term: the summand of the reformulated objective; g: the gradient
+// factor (the power step uses y_j = sum_i g_ij a_i); zr: the unnormalised
+// original-form loading.  Ties are inactive; sign(0) = 0.
+struct Thr {
+  double term, g, zr;
+};
+__device__ __forceinline__ Thr threshold(int form, double t, double gam, double mu) {
+  Thr r;
+  if ((form & 1) == 0) {  // SL1 / BL1
+    const double s = fmax(mu * fabs(t) - gam, 0.0);
+    const double sg = (t > 0.0) ? 1.0 : ((t < 0.0) ? -1.0 : 0.0);
+    r.term = s * s;
+    r.g = mu * sg * s;
+    r.zr = sg * s;
+  } else {  // SL0 / BL0
+    const double u = mu * t;
+    const bool act = u * u > gam;
+    r.term = act ? (u * u - gam) : 0.0;
+    r.g = act ? mu * mu * t : 0.0;
+    r.zr = act ? u : 0.0;
+  }
+  return r;
+}
+
+// Reduce 32 per-lane values over the warp; lane L returns the total of v[L].
+template <typename T>
+__device__ __forceinline__ T warp_reduce_scatter32(T (&v)[32], int lane) {
+#pragma unroll
+  for (int h = 16; h >= 1; h >>= 1) {
+    const bool up = (lane & h) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const T send = up ? v[i] : v[i + h];
+      const T keep = up ? v[i + h] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+    }
+  }
+  return v[0];
+}
+
+constexpr int kRingSlack = 33 * 4 * 4 * 8;  // 33 * NCHmax * VECmax * 8-byte elements
+
+// Shared-memory layout of the sweep kernel (host and device agree on it).
+struct SweepSmem {
+  int stage_bytes, bars, red, xch, gsm, wsm, gam, mu, facc, zacc, total;
+};
+__host__ __device__ inline int align_up(int v, int a) { return (v + a - 1) / a * a; }
+__host__ __device__ inline SweepSmem sweep_smem_layout(int W, int S, int ps, int esize, int tcsize, int nwarps, int m,
+                                                      int mg) {
+  SweepSmem L;
+  L.stage_bytes = W * ps * esize;  // ps*esize is a multiple of 16
+  // Threads own rows up to NCH*threads*VEC >= ps; rows past the CTA's slice
+  // are read (and masked) but must stay inside the allocation: the slack
+  // after the ring covers the largest overshoot (< 33 * NCH * VEC elements).
+  int o = align_up(S * L.stage_bytes + kRingSlack, 128);
+  L.bars = o; o += 8 * S;
+  o = align_up(o, 16);
+  L.red = o; o += nwarps * 32 * tcsize;
+  L.xch = o; o += 2 * 32 * tcsize;
+  L.gsm = o; o += 32 * tcsize;
+  L.wsm = o; o += m * mg * tcsize;
+  o = align_up(o, 8);
+  L.gam = o; o += 8 * mg;
+  L.mu = o; o += 8 * mg;
+  L.facc = o; o += 8 * 32;
+  L.zacc = o; o += 8 * 32;
+  L.total = align_up(o, 128);
+  return L;
+}
+
+template <typename TA, int MG, int NCH>
+struct SweepCfg {
+  using TC = typename Elem<TA>::TC;
+  static constexpr int VEC = Elem<TA>::VEC;
+  static constexpr int R = NCH * VEC;
+  static constexpr int WB = 32 / MG;  // most columns one tile can hold
+  static constexpr int REGS = static_cast<int>(sizeof(TC) / 4) * (2 * R * MG + 32) + 80;
+  // register arrays of x and y beyond this spill; such variants are not built
+  static constexpr bool kBuilt = static_cast<int>(sizeof(TC) / 4) * 2 * R * MG <= 160;
+  static constexpr int MAXT_RAW = 65536 / REGS;
+  // each of the 4 SM sub-partitions holds a quarter of the CTA's warps, so
+  // the thread bound is rounded down to a multiple of 4 warps
+  static constexpr int MAXT = MAXT_RAW >= 1024 ? 1024 : (MAXT_RAW < 128 ? 128 : (MAXT_RAW / 128) * 128);
+};
+
+template <typename TA, int MG, int NCH>
+__global__ void __launch_bounds__(SweepCfg<TA, MG, NCH>::MAXT, 1) sweep_kernel(const SweepArgs a) {
+  using Cfg = SweepCfg<TA, MG, NCH>;
+  using TC = typename Cfg::TC;
+  constexpr int VEC = Cfg::VEC;
+  constexpr int WB = Cfg::WB;
+  constexpr bool kFP8 = (sizeof(TA) == 1);
+
+  State* st = a.st;
+  if (st->n_active == 0) return;  // uniform across the grid
+
+  const IO* io = a.io;
+  const int tid = threadIdx.x;
+  const int nthr = blockDim.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+  const int nwarps = nthr >> 5;
+  uint32_t C;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(C));
+  const uint32_t cr = cluster_ctarank();
+  const int cl = blockIdx.x / static_cast<int>(C);
+  const int m = a.m;
+  const int p = a.p;
+  const int n = a.n;
+  const int ps = a.ps;
+  const int row0 = static_cast<int>(cr) * ps;
+  const int rows_valid = max(0, min(ps, p - row0));
+  const int col_begin = cl * a.cols_per_cl;
+  const int col_end = min(n, col_begin + a.cols_per_cl);
+  const int ncols = max(0, col_end - col_begin);
+  const int W = a.W;
+  const int S = a.S;
+  const int ntiles = (ncols + W - 1) / W;
+  const bool block = a.form >= 2;
+  const TA* __restrict__ A = static_cast<const TA*>(io->A);
+  const int64_t ld = a.ld;
+
+  extern __shared__ __align__(128) unsigned char smem[];
+  const SweepSmem L = sweep_smem_layout(W, S, ps, sizeof(TA), sizeof(TC), nwarps, m, MG);
+  TA* stage = reinterpret_cast<TA*>(smem);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bars);
+  TC* red = reinterpret_cast<TC*>(smem + L.red);
+  TC* xch = reinterpret_cast<TC*>(smem + L.xch);
+  TC* gsm = reinterpret_cast<TC*>(smem + L.gsm);
+  TC* wsm = reinterpret_cast<TC*>(smem + L.wsm);
+  double* gam = reinterpret_cast<double*>(smem + L.gam);
+  double* muv = reinterpret_cast<double*>(smem + L.mu);
+  double* fsm = reinterpret_cast<double*>(smem + L.facc);
+  double* zsm = reinterpret_cast<double*>(smem + L.zacc);
+  const int stage_elems = W * ps;
+
+  // ---- prologue: parameters, weights, barriers, first tiles
+  if (tid < MG) {
+    const bool v = tid < a.mg_valid;
+    gam[tid] = v ? st->gamma[a.j0 + tid] : 0.0;
+    muv[tid] = v ? io->mu[a.j0 + tid] : 1.0;
+  }
+  for (int idx = tid; idx < m * MG; idx += nthr) {
+    const int l = idx / MG, j = idx % MG;
+    wsm[idx] = (j < a.mg_valid) ? static_cast<TC>(st->W[l * m + a.j0 + j]) : TC(0);
+  }
+  const uint32_t bytes_per_col = static_cast<uint32_t>(align_up(rows_valid * static_cast<int>(sizeof(TA)), 16));
+  if (a.fast && tid == 0) {
+    for (int s = 0; s < S; ++s) mbar_init(smem_u32(&bars[s]), 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  auto issue_tile = [&](int tile, int buf) {
+    const int c0 = col_begin + tile * W;
+    const int wv = min(W, col_end - c0);
+    const uint32_t bar = smem_u32(&bars[buf]);
+    mbar_arrive_expect_tx(bar, bytes_per_col * static_cast<uint32_t>(wv));
+    for (int w = 0; w < wv; ++w) {
+      const TA* src = A + static_cast<int64_t>(c0 + w) * ld + row0;
+      bulk_g2s(smem_u32(stage + buf * stage_elems + w * ps), src, bytes_per_col, bar);
+    }
+  };
+  if (a.fast && tid == 0) {
+    const int pre = min(S, ntiles);
+    for (int s = 0; s < pre; ++s) issue_tile(s, s);
+  }
+
+  // ---- iterate rows in registers: X_k = Y_{k-1} W_{k-1}
+  const TC* __restrict__ Yp = static_cast<const TC*>(io->Y);
+  TC x[NCH][VEC][MG];
+  TC y[NCH][VEC][MG];
+  uint32_t vmask = 0;  // bit (c*VEC+v): row is inside this CTA's valid rows
+#pragma unroll
+  for (int c = 0; c < NCH; ++c) {
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) {
+      if ((c * nthr + tid) * VEC + v < rows_valid) vmask |= 1u << (c * VEC + v);
+#pragma unroll
+      for (int j = 0; j < MG; ++j) {
+        x[c][v][j] = 0;
+        y[c][v][j] = 0;
+      }
+    }
+  }
+  // block: all m columns of Y contribute; single-unit: only column j0+j
+  const int lbeg = block ? 0 : a.j0;
+  const int lend = block ? m : a.j0 + a.mg_valid;
+  for (int l = lbeg; l < lend; ++l) {
+    TC wl[MG];
+#pragma unroll
+    for (int j = 0; j < MG; ++j) wl[j] = (block || l == a.j0 + j) ? wsm[l * MG + j] : TC(0);
+    const TC* yl = Yp + static_cast<int64_t>(l) * p + row0;
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) {
+        const int rl = (c * nthr + tid) * VEC + v;
+        const TC yv = (vmask & (1u << (c * VEC + v))) ? yl[rl] : TC(0);
+#pragma unroll
+        for (int j = 0; j < MG; ++j) x[c][v][j] += yv * wl[j];
+      }
+    }
+  }
+  if (cl == 0) {  // the iterate that this sweep evaluates is an output
+    TC* Xo = static_cast<TC*>(io->X);
+#pragma unroll
+    for (int j = 0; j < MG; ++j) {
+      if (j < a.mg_valid && st->active[a.j0 + j]) {
+#pragma unroll
+        for (int c = 0; c < NCH; ++c)
+#pragma unroll
+          for (int v = 0; v < VEC; ++v)
+            if (vmask & (1u << (c * VEC + v)))
+              Xo[static_cast<int64_t>(a.j0 + j) * p + row0 + (c * nthr + tid) * VEC + v] = x[c][v][j];
+      }
+    }
+  }
+
+  double facc = 0.0, zacc = 0.0;
+  bool timed_out = false;
+  TC* Tout = static_cast<TC*>(io->T);
+  const float* cscale = io->col_scale;
+
+  for (int tile = 0; tile < ntiles; ++tile) {
+    const int buf = a.fast ? tile % S : 0;
+    const TA* sb = stage + buf * stage_elems;
+    const int c0 = col_begin + tile * W;
+    const int wv = min(W, col_end - c0);
+    if (a.fast) {
+      if (!mbar_wait_bounded(smem_u32(&bars[buf]), static_cast<uint32_t>((tile / S) & 1))) timed_out = true;
+    } else {
+      __syncthreads();  // previous tile fully consumed
+      TA* sbw = stage;
+      for (int w = 0; w < wv; ++w) {
+        const TA* src = A + static_cast<int64_t>(c0 + w) * ld + row0;
+        for (int r = tid; r < rows_valid; r += nthr) sbw[w * ps + r] = src[r];
+      }
+      __syncthreads();
+    }
+
+    // partial dots over this thread's rows
+    TC pd[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) pd[i] = 0;
+#pragma unroll
+    for (int w = 0; w < WB; ++w) {
+      if (w < wv) {
+        const TA* colp = sb + w * ps;
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+          TC av[VEC];
+          load_vec(colp + (c * nthr + tid) * VEC, av);
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) {
+            const TC aval = (vmask & (1u << (c * VEC + v))) ? av[v] : TC(0);
+#pragma unroll
+            for (int j = 0; j < MG; ++j) pd[w * MG + j] += aval * x[c][v][j];
+          }
+        }
+      }
+    }
+    const TC mine = warp_reduce_scatter32(pd, lane);
+    red[warp * 32 + lane] = mine;
+    __syncthreads();  // (1) partials visible; previous tile's buffer free
+    if (a.fast && tid == 0 && tile >= 1 && tile - 1 + S < ntiles) issue_tile(tile - 1 + S, (tile - 1) % S);
+    if (tid < 32) {
+      TC s = 0;
+      for (int w2 = 0; w2 < nwarps; ++w2) s += red[w2 * 32 + tid];
+      xch[(tile & 1) * 32 + tid] = s;
+    }
+    if (C > 1) {
+      cluster_sync_all();  // (2) every CTA's partial visible cluster-wide
+    } else {
+      __syncthreads();
+    }
+    if (tid < WB * MG) {
+      const int w = tid / MG, j = tid % MG;
+      TC t = 0;
+      if (C > 1) {
+        const uint32_t addr = smem_u32(&xch[(tile & 1) * 32 + tid]);
+        for (uint32_t r = 0; r < C; ++r) t += dsmem_ld(dsmem_map(addr, r), TC(0));
+      } else {
+        t = xch[(tile & 1) * 32 + tid];
+      }
+      TC g = 0;
+      if (w < wv && j < a.mg_valid) {
+        const int col = c0 + w;
+        double td = static_cast<double>(t);
+        double sc = 1.0;
+        if (kFP8) {
+          sc = static_cast<double>(cscale[col]);
+          td *= sc;
+        }
+        const Thr th = threshold(a.form, td, gam[j], muv[j]);
+        if (cr == 0) {
+          if (st->active[a.j0 + j]) Tout[static_cast<int64_t>(a.j0 + j) * n + col] = static_cast<TC>(td);
+          facc += th.term;
+          zacc += th.zr * th.zr;
+        }
+        g = static_cast<TC>(th.g * sc);
+      }
+      gsm[tid] = g;
+    }
+    __syncthreads();  // (3) g visible
+
+    // rank update y += g a over this thread's rows of the tile
+#pragma unroll
+    for (int w = 0; w < WB; ++w) {
+      if (w < wv) {
+        TC gw[MG];
+#pragma unroll
+        for (int j = 0; j < MG; ++j) gw[j] = gsm[w * MG + j];
+        const TA* colp = sb + w * ps;
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+          TC av[VEC];
+          load_vec(colp + (c * nthr + tid) * VEC, av);
+#pragma unroll
+          for (int v = 0; v < VEC; ++v)
+#pragma unroll
+            for (int j = 0; j < MG; ++j) y[c][v][j] += av[v] * gw[j];
+        }
+      }
+    }
+  }
+
+  // ---- epilogue: this cluster's partial of Y = A G and of the objective
+  TC* yp = static_cast<TC*>(io->ypart);
+#pragma unroll
+  for (int j = 0; j < MG; ++j) {
+    if (j < a.mg_valid) {
+      TC* dst = yp + (static_cast<int64_t>(cl) * m + a.j0 + j) * p + row0;
+#pragma unroll
+      for (int c = 0; c < NCH; ++c)
+#pragma unroll
+        for (int v = 0; v < VEC; ++v)
+          if (vmask & (1u << (c * VEC + v))) dst[(c * nthr + tid) * VEC + v] = y[c][v][j];
+    }
+  }
+  __syncthreads();
+  if (tid < 32) {
+    fsm[tid] = facc;
+    zsm[tid] = zacc;
+  }
+  __syncthreads();
+  if (cr == 0 && tid < a.mg_valid) {
+    double F = 0.0, Zs = 0.0;
+    for (int w = 0; w < WB; ++w) {
+      F += fsm[w * MG + tid];
+      Zs += zsm[w * MG + tid];
+    }
+    io->fpart[(static_cast<int64_t>(cl) * 2 + 0) * m + a.j0 + tid] = F;
+    io->fpart[(static_cast<int64_t>(cl) * 2 + 1) * m + a.j0 + tid] = Zs;
+  }
+  if (timed_out) atomicOr(&st->error, static_cast<int>(kErrTimeout));
+  if (C > 1) cluster_sync_all();  // no CTA leaves while a peer may read its shared memory
+}
+
+template <typename TA, int MG, int NCH>
+const void* sweep_kernel_ptr() {
+  if constexpr (SweepCfg<TA, MG, NCH>::kBuilt) {
+    return reinterpret_cast<const void*>(&sweep_kernel<TA, MG, NCH>);
+  } else {
+    return nullptr;
+  }
+}
+
+}  // namespace gpspca

@@ -1,0 +1,355 @@
+"""GPU path (through the C ABI) against the FP64 oracle, element by element.
+
+Sizes span several column tiles, several clusters and ragged tails in both p
+and n; the workload-sized cases (200 x 1000 FP64, 5000 x 20000 FP32) run in
+the launch configuration the benchmark uses.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1312_6182_gb300 import binding, synth
+from tests.compare import assert_matches, gpu_arrays
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    c = binding.Context(0)
+    yield c
+    c.close()
+
+
+def _dev(At, ld=None):
+    """Device copy of At (n x p); ld > p pads each row (aligned fast path)."""
+    n, p = At.shape
+    if ld is None or ld == p:
+        return torch.from_numpy(np.ascontiguousarray(At)).cuda()
+    buf = np.zeros((n, ld), dtype=At.dtype)
+    buf[:, :p] = At
+    return torch.from_numpy(buf).cuda()
+
+
+def _gammas(A64, form, rho):
+    c = oracle.column_norms(A64).max()
+    rho = np.atleast_1d(rho).astype(np.float64)
+    return rho * c if form.endswith("1") else (rho * c) ** 2
+
+
+def _run(ctx, At, form, gam, mu=None, tol=1e-6, maxit=1000, ld=None, x0=None, **kw):
+    dA = _dev(At, ld)
+    p = At.shape[1]
+    res = ctx.solve(dA, form, list(gam), mu=mu, tol=tol, maxit=maxit, p=p, x0=x0, **kw)
+    return gpu_arrays(res), res
+
+
+# ---------------------------------------------------------------- workload sizes
+
+def test_fp64_200x1000_single_unit_l1(ctx):
+    """200 x 1000 N(0,1), centred columns, FP64, SL1 at gamma = 0.1 max||a_i||,
+    x0 = largest column, tol 1e-6, maxit 1000: computed in double on the GPU."""
+    At = synth.workload_fp64_200x1000(0)
+    A = At.T
+    gam = _gammas(A, "SL1", 0.1)
+    ref = oracle.gpower(A, "SL1", gam, tol=1e-6, maxit=1000)
+    g, res = _run(ctx, At, "SL1", gam, tol=1e-6, maxit=1000)
+    assert res.X.dtype == torch.float64
+    assert_matches("SL1", g, ref, tol_z=1e-9, tol_f=1e-11, tol_x=1e-9, iters_slack=0)
+
+
+@pytest.fixture(scope="module")
+def spikes_full():
+    At = synth.workload_spikes_5000x20000(0)
+    return At, At.astype(np.float64).T
+
+
+FULL_CASES = [
+    ("SL1", None), ("SL0", None),
+    ("BL1", [1.0] * 5), ("BL0", [1.0] * 5),
+    ("BL1", [1.0, 0.9, 0.8, 0.7, 0.6]), ("BL0", [1.0, 0.9, 0.8, 0.7, 0.6]),
+]
+
+
+@pytest.mark.parametrize("form,mu", FULL_CASES)
+def test_spikes_5000x20000_fp32(ctx, spikes_full, form, mu):
+    """The four formulations on 5000 x 20000 planted spikes in FP32 against the
+    FP64 oracle: loadings 1e-5, objective 1e-6, support outside the band."""
+    At, A = spikes_full
+    m = 1 if mu is None else 5
+    gam = _gammas(A, form, [0.05] * m)
+    ref = oracle.gpower(A, form, gam, mu=mu, tol=1e-6, maxit=1000)
+    g, _ = _run(ctx, At, form, gam, mu=mu, tol=1e-6, maxit=1000)
+    assert_matches(form, g, ref, tol_z=1e-5, tol_f=1e-6, tol_x=1e-5)
+
+
+# ---------------------------------------------------------------- fixed sweep counts
+
+RAGGED = dict(p=1237, n=3001)
+
+
+@pytest.mark.parametrize("form", oracle.FORMS)
+@pytest.mark.parametrize("ld", [1240, 1237])  # padded (bulk-copy path) and unpadded (element path)
+def test_fixed_sweeps_ragged(ctx, form, ld):
+    """tol = 0, 15 sweeps, ragged p and n, all four forms: per-step drift stays
+    at float32 rounding.  ld = 1237 is not 16-byte aligned (element path)."""
+    At = synth.planted_spike(RAGGED["p"], RAGGED["n"], 3, [25.0, 12.0, 8.0], support_frac=0.04, seed=5,
+                             dtype=np.float32)
+    A = At.astype(np.float64).T
+    if form.startswith("S"):
+        gam, mu = _gammas(A, form, [0.02, 0.08, 0.2]), None
+    else:
+        mu = [1.0, 0.9, 0.8, 0.7, 0.6]
+        gam = _gammas(A, form, [0.03] * 5) * (np.array(mu) if form.endswith("1") else np.array(mu) ** 2)
+    ref = oracle.gpower(A, form, gam, mu=mu, tol=0.0, maxit=15)
+    g, _ = _run(ctx, At, form, gam, mu=mu, tol=0.0, maxit=15, ld=ld)
+    assert_matches(form, g, ref, tol_z=2e-5, tol_f=1e-6, tol_x=2e-5, iters_slack=0)
+
+
+@pytest.mark.parametrize("form", ["SL1", "SL0"])
+def test_gamma_path_64(ctx, form):
+    """A 64-value gamma path (log-spaced over [0.001, 0.5] max||a_i||) on one
+    A: 64 independent single-unit solves in 8 passes of the fused sweep."""
+    At = synth.planted_spike(1500, 6000, 3, [40.0, 20.0, 13.3], support_frac=0.02, seed=1, dtype=np.float32)
+    A = At.astype(np.float64).T
+    gam = _gammas(A, form, synth.log_spaced_rho(64))
+    ref = oracle.gpower(A, form, gam, tol=1e-6, maxit=300)
+    g, _ = _run(ctx, At, form, gam, tol=1e-6, maxit=300)
+    assert_matches(form, g, ref, tol_z=1e-4, tol_f=1e-6, tol_x=1e-4, iters_slack=2)
+
+
+@pytest.mark.parametrize("m", [16, 32])
+def test_block_many_components(ctx, m):
+    """Block L1 with m = 16 and 32 components (several component passes per
+    sweep, a 16x16 / 32x32 FP64 Jacobi polar step), fixed sweep count."""
+    At = synth.planted_spike(900, 4000, 4, [30.0, 20.0, 15.0, 10.0], support_frac=0.02, seed=7,
+                             dtype=np.float32)
+    A = At.astype(np.float64).T
+    gam = _gammas(A, "BL1", [0.02] * m)
+    ref = oracle.gpower(A, "BL1", gam, mu=[1.0] * m, tol=0.0, maxit=8)
+    g, _ = _run(ctx, At, "BL1", gam, mu=[1.0] * m, tol=0.0, maxit=8)
+    assert_matches("BL1", g, ref, tol_z=5e-5, tol_f=1e-6, tol_x=5e-5, iters_slack=0)
+
+
+# ---------------------------------------------------------------- storage precisions
+
+def _bf16(At):
+    t = torch.from_numpy(At).to(torch.bfloat16)
+    return t, t.float().numpy()
+
+
+def _fp8(At):
+    s = np.abs(At).max(axis=1).astype(np.float32) / 448.0
+    s[s == 0] = 1.0
+    q = torch.from_numpy(At / s[:, None]).to(torch.float8_e4m3fn)
+    deq = q.float().numpy() * s[:, None]
+    return q, torch.from_numpy(s), deq
+
+
+@pytest.mark.parametrize("form", oracle.FORMS)
+def test_bf16_storage_matches_oracle_on_stored_values(ctx, form):
+    """BF16 storage: the oracle runs on the exactly upcast BF16 values, so the
+    only differences are float32 accumulation."""
+    At = synth.planted_spike(2000, 7001, 3, [30.0, 15.0, 10.0], support_frac=0.03, seed=11, dtype=np.float32)
+    tb, deq = _bf16(At)
+    A = deq.astype(np.float64).T
+    m = 1 if form.startswith("S") else 3
+    mu = None if m == 1 else [1.0, 0.8, 0.6]
+    gam = _gammas(A, form, [0.05] * m)
+    ref = oracle.gpower(A, form, gam, mu=mu, tol=1e-6, maxit=500)
+    res = ctx.solve(tb.cuda(), form, list(gam), mu=mu, tol=1e-6, maxit=500)
+    assert_matches(form, gpu_arrays(res), ref, tol_z=1e-5, tol_f=1e-6, tol_x=1e-5)
+
+
+@pytest.mark.parametrize("form", ["SL0", "BL1"])
+def test_fp8_storage_matches_oracle_on_stored_values(ctx, form):
+    """FP8 E4M3 with per-column scales: oracle on the dequantised matrix."""
+    At = synth.planted_spike(1800, 6000, 3, [30.0, 15.0, 10.0], support_frac=0.03, seed=12, dtype=np.float32)
+    q, s, deq = _fp8(At)
+    A = deq.astype(np.float64).T
+    m = 1 if form.startswith("S") else 3
+    mu = None if m == 1 else [1.0, 1.0, 1.0]
+    gam = _gammas(A, form, [0.05] * m)
+    ref = oracle.gpower(A, form, gam, mu=mu, tol=1e-6, maxit=500)
+    res = ctx.solve(q.cuda(), form, list(gam), mu=mu, tol=1e-6, maxit=500, col_scale=s.cuda())
+    assert_matches(form, gpu_arrays(res), ref, tol_z=1e-5, tol_f=1e-6, tol_x=1e-5)
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "fp8"])
+def test_low_precision_then_fp32_refinement(ctx, fmt):
+    """Precision path: converge on BF16 / FP8 storage, then 3 FP32 sweeps from
+    the converged X on the FP32 matrix; against the oracle on the FP32 matrix
+    the loadings are within 1e-3."""
+    At = synth.planted_spike(2000, 8000, 4, [40.0, 28.0, 23.0, 20.0], support_frac=0.01, seed=2,
+                             dtype=np.float32)
+    A = At.astype(np.float64).T
+    mu = [1.0] * 4
+    gam = _gammas(A, "BL1", [0.05] * 4)
+    ref = oracle.gpower(A, "BL1", gam, mu=mu, tol=1e-6, maxit=1000)
+    if fmt == "bf16":
+        low = ctx.solve(_bf16(At)[0].cuda(), "BL1", list(gam), mu=mu, tol=1e-6, maxit=1000)
+    else:
+        q, s, _ = _fp8(At)
+        low = ctx.solve(q.cuda(), "BL1", list(gam), mu=mu, tol=1e-6, maxit=1000, col_scale=s.cuda())
+    x0 = low.X.contiguous()
+    fine = ctx.solve(torch.from_numpy(At).cuda(), "BL1", list(gam), mu=mu, tol=0.0, maxit=3, x0=x0)
+    g = gpu_arrays(fine)
+    for j in range(4):
+        err = np.linalg.norm(g["Z"][:, j] - ref.Z[:, j]) / np.linalg.norm(ref.Z[:, j])
+        assert err < 1e-3, (fmt, j, err)
+    assert abs(np.sum(g["objective"]) - ref.total) / ref.total < 1e-4
+
+
+# ---------------------------------------------------------------- API behaviour
+
+def test_host_buffers_equal_device_buffers(ctx):
+    """The C ABI with host (pinned) input and outputs gives the bit-identical
+    result of the device path."""
+    At = synth.planted_spike(1000, 4000, 2, [30.0, 15.0], support_frac=0.05, seed=4, dtype=np.float32)
+    gam = _gammas(At.astype(np.float64).T, "SL1", 0.05)
+    dev = ctx.solve(torch.from_numpy(At).cuda(), "SL1", list(gam))
+    hA = torch.from_numpy(At).pin_memory()
+    out = binding.alloc_result(1, 1000, 4000, "cpu", torch.float32, pin=True)
+    host = ctx.solve(hA, "SL1", list(gam), out=out)
+    assert torch.equal(host.Z, dev.Z.cpu()) and torch.equal(host.X, dev.X.cpu())
+    assert torch.equal(host.objective, dev.objective.cpu())
+
+
+def test_relative_gamma_is_scaled_on_device(ctx):
+    At = synth.planted_spike(800, 3000, 2, [30.0, 15.0], support_frac=0.05, seed=8, dtype=np.float32)
+    A = At.astype(np.float64).T
+    for form in ("SL1", "BL0"):
+        m = 1 if form.startswith("S") else 2
+        rho = [0.07] * m
+        res = ctx.solve(torch.from_numpy(At).cuda(), form, rho, mu=None if m == 1 else [1.0, 1.0],
+                        gamma_relative=True)
+        ga = res.gamma_abs.cpu().numpy()
+        np.testing.assert_allclose(ga, oracle.gamma_from_rho(A, form, rho), rtol=1e-12)
+        ref = oracle.gpower(A, form, ga, mu=None if m == 1 else [1.0, 1.0])
+        assert_matches(form, gpu_arrays(res), ref)
+
+
+def test_warm_start_x0(ctx):
+    At = synth.planted_spike(700, 2500, 2, [25.0, 12.0], support_frac=0.05, seed=9, dtype=np.float32)
+    A = At.astype(np.float64).T
+    gam = _gammas(A, "BL0", [0.05, 0.05])
+    rng = np.random.default_rng(0)
+    x0 = rng.standard_normal((700, 2))
+    ref = oracle.gpower(A, "BL0", gam, mu=[1.0, 1.0], tol=0.0, maxit=10, x0=x0)
+    g, _ = _run(ctx, At, "BL0", gam, mu=[1.0, 1.0], tol=0.0, maxit=10,
+                x0=torch.from_numpy(x0.T.astype(np.float32).copy()).cuda())
+    assert_matches("BL0", g, ref, tol_z=2e-5, tol_x=2e-5, iters_slack=0)
+
+
+def test_deterministic(ctx):
+    At = synth.planted_spike(1500, 5000, 3, [30.0, 15.0, 10.0], support_frac=0.03, seed=10, dtype=np.float32)
+    dA = torch.from_numpy(At).cuda()
+    gam = list(_gammas(At.astype(np.float64).T, "BL1", [0.04] * 3))
+    a = ctx.solve(dA, "BL1", gam, mu=[1.0, 1.0, 1.0])
+    b = ctx.solve(dA, "BL1", gam, mu=[1.0, 1.0, 1.0])
+    assert torch.equal(a.Z, b.Z) and torch.equal(a.X, b.X) and torch.equal(a.objective, b.objective)
+
+
+# ---------------------------------------------------------------- edge cases
+
+def test_tiny_shapes(ctx):
+    rng = np.random.default_rng(3)
+    for p, n, form in ((1, 9, "SL0"), (9, 1, "SL1"), (3, 5, "BL1"), (5, 40, "BL0")):
+        At = rng.standard_normal((n, p)).astype(np.float32)
+        A = At.astype(np.float64).T
+        m = 1 if form.startswith("S") else min(2, p, n)
+        mu = None if m == 1 else [1.0] * m
+        gam = _gammas(A, form, [0.1] * m)
+        ref = oracle.gpower(A, form, gam, mu=mu, tol=0.0, maxit=6)
+        g, _ = _run(ctx, At, form, gam, mu=mu, tol=0.0, maxit=6)
+        assert_matches(form, g, ref, tol_z=1e-5, tol_x=1e-5, iters_slack=0)
+
+
+def test_zero_matrix_and_large_gamma(ctx):
+    At = np.zeros((50, 30), dtype=np.float32)
+    g, res = _run(ctx, At, "SL1", [0.1])
+    assert g["status"][0] == binding.ZERO and g["iters"][0] == 0 and np.all(g["Z"] == 0)
+    At = np.random.default_rng(1).standard_normal((200, 64)).astype(np.float32)
+    A = At.astype(np.float64).T
+    for form in oracle.FORMS:
+        m = 1 if form.startswith("S") else 2
+        c = oracle.column_norms(A).max()
+        gam = [c] * m if form.endswith("1") else [c * c] * m
+        g, _ = _run(ctx, At, form, gam, mu=None if m == 1 else [1.0, 1.0])
+        assert np.all(g["status"] == binding.ZERO) and np.all(g["iters"] == 1)
+        assert np.all(g["Z"] == 0) and np.all(g["objective"] == 0)
+
+
+def test_empty_matrix(ctx):
+    At = torch.zeros((0, 16), device="cuda")
+    res = ctx.solve(At, "SL1", [0.1], p=16)
+    assert res.status.item() == binding.ZERO and res.iters.item() == 0
+
+
+def test_nonfinite_input_is_reported(ctx):
+    At = np.random.default_rng(2).standard_normal((100, 40)).astype(np.float32)
+    At[17, 3] = np.nan
+    with pytest.raises(binding.GpspcaError) as e:
+        ctx.solve(torch.from_numpy(At).cuda(), "SL1", [0.1])
+    assert e.value.code == binding.ENONFINITE
+    # the context stays usable
+    At[17, 3] = 0.0
+    ctx.solve(torch.from_numpy(At).cuda(), "SL1", [0.1])
+
+
+def test_degenerate_polar_status(ctx):
+    At = np.random.default_rng(20).standard_normal((30, 12)).astype(np.float32)
+    A = At.astype(np.float64).T
+    c = oracle.column_norms(A).max()
+    gam = [0.1 * c, 2.0 * c]
+    ref = oracle.gpower(A, "BL1", gam, mu=[1.0, 1.0])
+    res = ctx.solve(torch.from_numpy(At).cuda(), "BL1", gam, mu=[1.0, 1.0])
+    assert res.rc == binding.EDEGENERATE
+    g = gpu_arrays(res)
+    assert_matches("BL1", g, ref, iters_slack=0)
+
+
+def test_invalid_arguments(ctx):
+    dA = torch.randn(40, 8, device="cuda")
+    for kw in (dict(form="BL1", gamma=[0.1] * 9, mu=[1.0] * 9),   # m > p
+               dict(form="SL1", gamma=[-1.0]),
+               dict(form="BL0", gamma=[0.1, 0.1], mu=[1.0, 0.0]),
+               dict(form="SL1", gamma=[0.1] * 65)):
+        with pytest.raises(binding.GpspcaError) as e:
+            ctx.solve(dA, **kw)
+        assert e.value.code == binding.EINVAL
+
+
+def test_time_sweep(ctx):
+    At = synth.planted_spike(2000, 8000, 2, [30.0, 15.0], support_frac=0.05, seed=4, dtype=np.float32)
+    ms = ctx.time_sweep(torch.from_numpy(At).cuda(), "SL1", [0.05], gamma_relative=True, reps=5)
+    assert 0 < ms < 100
+
+
+# ---------------------------------------------------------------- serving
+
+def test_submitted_requests_equal_solo_solves(ctx):
+    """Requests of different shapes and formulations submitted together (and so
+    overlapping on the device) give the bit-identical results of solo solves."""
+    rng = np.random.default_rng(0)
+    reqs = []
+    for i in range(10):
+        p = int(rng.integers(200, 1500))
+        n = int(rng.integers(800, 5000))
+        form = oracle.FORMS[i % 4]
+        m = 1 if form.startswith("S") else int(rng.integers(2, 6))
+        At = synth.planted_spike(p, n, m, [30.0 / (j + 1) for j in range(m)], support_frac=0.05, seed=100 + i,
+                                 dtype=np.float32)
+        reqs.append((torch.from_numpy(At).cuda(), form, [float(rng.uniform(0.02, 0.2))] * m,
+                     None if m == 1 else [1.0] * m))
+    solo = [ctx.solve(dA, f, g, mu=mu, gamma_relative=True) for dA, f, g, mu in reqs]
+    tickets = [ctx.submit(dA, f, g, mu=mu, gamma_relative=True) for dA, f, g, mu in reqs]
+    for (t, out), ref in zip(tickets, solo):
+        rc = ctx.poll(t, wait_us=-1)
+        assert rc in (binding.OK, binding.EDEGENERATE)
+        assert torch.equal(out.Z, ref.Z) and torch.equal(out.X, ref.X)
+        assert torch.equal(out.objective, ref.objective) and torch.equal(out.iters, ref.iters)
+    assert ctx.poll(tickets[0][0], 0) == binding.ENOTFOUND
