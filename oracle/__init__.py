@@ -20,5 +20,9 @@ from .gpower import (  # noqa: F401
     polar,
     initial_iterate,
     project_start,
+    block_start,
+    sketch_signs,
+    splitmix64,
+    POWER_STEPS,
     gpower,
 )

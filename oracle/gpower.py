@@ -35,8 +35,11 @@ the project's design notes):
 * gamma is absolute here; ``gamma_from_rho`` converts the paper's unitless
   values, read as relative to max_i ||a_i|| (L1) and its square (L0).
 * Initialisation: single-unit x0 = a_{i*}/||a_{i*}|| with i* the first index of
-  the largest column norm; block X0 = polar factor of the m largest-norm
-  columns in decreasing norm order (ties -> lower index).
+  the largest column norm.  Block: a PCA start, X0 = the Rayleigh-Ritz
+  vectors of A A^T on the subspace reached by two block power steps from a
+  fixed Rademacher sketch (``block_start``); the m largest columns are a poor
+  start (on planted spikes they all come from the strongest spike and the
+  iteration stalls in degenerate local maxima).
 * Stopping: after computing f_k, stop if f_k == 0 (status ZERO), else if k > 0
   and |f_k - f_{k-1}| < tol * f_{k-1} (CONVERGED), else if k == maxit - 1
   (MAXIT).  The returned iterate is x_k, the one that produced f_k.
@@ -162,12 +165,68 @@ def polar(Y: np.ndarray):
     return U @ Vt, degenerate
 
 
+# SplitMix64 (Steele, Lea & Flood, "Fast splittable pseudorandom number
+# generators", OOPSLA 2014): the k-th output (k = 1, 2, ...) of the stream with
+# seed s is mix(s + k * GOLDEN).
+_GOLDEN = 0x9E3779B97F4A7C15
+_MIX1 = 0xBF58476D1CE4E5B9
+_MIX2 = 0x94D049BB133111EB
+SKETCH_SEED = 0x5EED5EED5EED5EED
+POWER_STEPS = 2
+
+
+def splitmix64(seed: int, k: np.ndarray) -> np.ndarray:
+    """k-th SplitMix64 output of the stream seeded with ``seed`` (uint64 arrays)."""
+    k = np.asarray(k, dtype=np.uint64)
+    z = np.uint64(seed) + k * np.uint64(_GOLDEN)
+    z = (z ^ (z >> np.uint64(30))) * np.uint64(_MIX1)
+    z = (z ^ (z >> np.uint64(27))) * np.uint64(_MIX2)
+    return z ^ (z >> np.uint64(31))
+
+
+def sketch_signs(p: int, m: int) -> np.ndarray:
+    """p x m Rademacher sketch: entry (r, j) is -1 if the top bit of output
+    k = j * 2^32 + r + 1 of SplitMix64(SKETCH_SEED) is set, else +1."""
+    r = np.arange(p, dtype=np.uint64)[:, None]
+    j = np.arange(m, dtype=np.uint64)[None, :]
+    z = splitmix64(SKETCH_SEED, (j << np.uint64(32)) + r + np.uint64(1))
+    return np.where((z >> np.uint64(63)) == np.uint64(1), -1.0, 1.0)
+
+
+def block_start(A: np.ndarray, m: int, steps: int = POWER_STEPS):
+    """PCA start for the block forms (reading of an unstated detail).
+
+    Q_0 = polar(Omega) for the Rademacher sketch Omega; Q_{s+1} = polar(A A^T Q_s)
+    for s < steps; then Rayleigh-Ritz on span(Q): B = sym(Q^T A A^T Q),
+    B = V diag(w) V^T with w in decreasing order and each column of V signed
+    so that its largest-magnitude entry (first on ties) is positive;
+    X0 = Q V.  Returns (X0, status) like ``initial_iterate``.
+    """
+    p = A.shape[0]
+    Q, degenerate = polar(sketch_signs(p, m))
+    if degenerate:
+        return np.zeros((p, m)), STATUS_DEGENERATE
+    for _ in range(steps):
+        Q, degenerate = polar(A @ (A.T @ Q))
+        if degenerate:
+            return np.zeros((p, m)), STATUS_DEGENERATE
+    B = Q.T @ (A @ (A.T @ Q))
+    B = 0.5 * (B + B.T)
+    w, V = np.linalg.eigh(B)
+    V = V[:, ::-1]
+    for j in range(m):
+        i = int(np.argmax(np.abs(V[:, j])))
+        if V[i, j] < 0:
+            V[:, j] = -V[:, j]
+    return Q @ V, None
+
+
 def initial_iterate(A: np.ndarray, form: str, m: int):
     """Starting point (reading of an unstated detail, see module docstring).
 
     Returns (X0 p x m, status) where status is None when X0 is usable, or
-    STATUS_ZERO (A == 0) / STATUS_DEGENERATE (block, the m largest-norm
-    columns are rank deficient).
+    STATUS_ZERO (A == 0) / STATUS_DEGENERATE (block, a rank-deficient step of
+    ``block_start``).
     """
     c = column_norms(A)
     p = A.shape[0]
@@ -177,11 +236,7 @@ def initial_iterate(A: np.ndarray, form: str, m: int):
         i_star = int(np.argmax(c))  # first index attaining the maximum
         x0 = A[:, i_star] / c[i_star]
         return np.repeat(x0[:, None], m, axis=1), None
-    order = np.argsort(-c, kind="stable")[:m]  # decreasing norm, ties -> lower index
-    X0, degenerate = polar(A[:, order])
-    if degenerate:
-        return np.zeros((p, m)), STATUS_DEGENERATE
-    return X0, None
+    return block_start(A, m)
 
 
 def project_start(x0: np.ndarray, form: str):

@@ -181,9 +181,11 @@ def test_start_at_fixed_point_stops_after_second_sweep():
     A[2, 1] = 0.5
     A[3, 3] = 0.25
     A[3, 4] = 0.25
+    e0 = np.zeros((4, 1))
+    e0[0, 0] = 1.0  # the largest column's direction; block forms take it as x0
     for form in oracle.FORMS:
-        m = 1
-        r = oracle.gpower(A, form, [0.1], mu=None if form[0] == "S" else [1.0], tol=1e-6)
+        block = form[0] == "B"
+        r = oracle.gpower(A, form, [0.1], mu=[1.0] if block else None, tol=1e-6, x0=e0 if block else None)
         assert r.status[0] == oracle.STATUS_CONVERGED and r.iters[0] == 2
         assert abs(r.X[0, 0]) == 1.0
         np.testing.assert_array_equal(np.flatnonzero(r.Z[:, 0]), [2])
@@ -270,7 +272,8 @@ def test_block_with_one_component_equals_single_unit(form):
     A = _rand(25, 70, 8)
     g = oracle.gamma_from_rho(A, form, 0.25)
     s = oracle.gpower(A, form, g, tol=1e-10)
-    b = oracle.gpower(A, "B" + form[1:], g, mu=[1.0], tol=1e-10)
+    x0 = oracle.initial_iterate(A, form, 1)[0]
+    b = oracle.gpower(A, "B" + form[1:], g, mu=[1.0], tol=1e-10, x0=x0)
     assert s.iters[0] == b.iters[0]
     sgn = np.sign(s.X[:, 0] @ b.X[:, 0])
     np.testing.assert_allclose(b.X[:, 0], sgn * s.X[:, 0], atol=1e-12)
@@ -297,8 +300,9 @@ def test_block_mu_scaling_invariance(form):
 
 @pytest.mark.parametrize("form", oracle.FORMS)
 def test_rotation_of_samples_is_equivariant(form):
-    """Replacing A by Q A (Q orthogonal p x p) maps X to Q X and leaves t = A^T x,
-    the objective and Z unchanged; a transposed operand anywhere breaks this."""
+    """Replacing A by Q A (Q orthogonal p x p) and x0 by Q x0 maps X to Q X and
+    leaves t = A^T x, the objective and Z unchanged; a transposed operand
+    anywhere breaks this.  (Single-unit forms pick x0 from A itself.)"""
     A = _rand(18, 45, 12)
     Q, _ = np.linalg.qr(np.random.default_rng(13).standard_normal((18, 18)))
     m = 2 if form in ("SL1", "SL0") else 3
@@ -308,8 +312,9 @@ def test_rotation_of_samples_is_equivariant(form):
     gam = rho * c if form in ("SL1", "BL1") else (rho * c) ** 2
     if mu is not None:
         gam = gam * (mu if form == "BL1" else mu * mu)
-    r1 = oracle.gpower(A, form, gam, mu=mu, tol=0.0, maxit=25)
-    r2 = oracle.gpower(Q @ A, form, gam, mu=mu, tol=0.0, maxit=25)
+    x0 = np.linalg.qr(np.random.default_rng(14).standard_normal((18, m)))[0] if mu is not None else None
+    r1 = oracle.gpower(A, form, gam, mu=mu, tol=0.0, maxit=25, x0=x0)
+    r2 = oracle.gpower(Q @ A, form, gam, mu=mu, tol=0.0, maxit=25, x0=None if x0 is None else Q @ x0)
     np.testing.assert_allclose(r2.X, Q @ r1.X, atol=1e-10)
     np.testing.assert_allclose(r2.Z, r1.Z, atol=1e-10)
     np.testing.assert_allclose(r2.objective, r1.objective, rtol=1e-10)
@@ -383,8 +388,7 @@ def test_degenerate_polar_keeps_last_valid_iterate():
     r = oracle.gpower(A, "BL1", gam, mu=[1.0, 1.0])
     assert np.all(r.status == oracle.STATUS_DEGENERATE)
     assert np.all(r.iters == 1)
-    order = np.argsort(-oracle.column_norms(A), kind="stable")[:2]
-    X0, _ = oracle.polar(A[:, order])
+    X0, _ = oracle.block_start(A, 2)
     np.testing.assert_allclose(r.X, X0, atol=1e-14)
     assert np.all(r.Z[:, 1] == 0)
 
@@ -440,10 +444,8 @@ def test_gamma_path_equals_independent_solves():
 
 def test_planted_spike_support_recovery():
     """Statistical sanity (not parity): on strong planted sparse spikes the
-    single-unit solutions recover the first spike's support exactly.  The block
-    solutions start from the m largest columns, which here all belong to the
-    first spike, so the method only promises a local maximum (Section 2); the
-    first spike's support must still appear inside the block supports."""
+    single-unit solutions recover the first spike's support exactly and the
+    block solutions (PCA start) recover all three supports, one per component."""
     At, meta = synth.planted_spike(400, 3000, 3, [40.0, 20.0, 13.3], support_frac=0.05,
                                    seed=0, dtype=np.float64, with_meta=True)
     A = At.T
@@ -454,27 +456,50 @@ def test_planted_spike_support_recovery():
         assert set(np.flatnonzero(r.Z[:, 0])) == set(meta.supports[0].tolist())
     c = oracle.column_norms(A).max()
     for form in ("BL1", "BL0"):
-        g = np.full(3, 0.1 * c) if form == "BL1" else np.full(3, (0.1 * c) ** 2)
-        r = oracle.gpower(A, form, g, mu=np.ones(3))
-        assert r.status[0] == oracle.STATUS_CONVERGED
-        union = set(np.flatnonzero(np.any(r.Z != 0, axis=1)).tolist())
-        assert set(meta.supports[0].tolist()) <= union
+        for mu in (np.ones(3), np.array([1.0, 0.8, 0.6])):
+            g = np.full(3, 0.1 * c) if form == "BL1" else np.full(3, (0.1 * c) ** 2)
+            r = oracle.gpower(A, form, g, mu=mu)
+            assert r.status[0] == oracle.STATUS_CONVERGED
+            found = [set(np.flatnonzero(r.Z[:, j]).tolist()) for j in range(3)]
+            assert found == [set(sp.tolist()) for sp in meta.supports]
 
 
-def test_start_is_projected_on_the_feasible_set():
-    """A caller's x0 is projected on the sphere (single-unit) or the Stiefel
-    manifold (block): a scaled copy of the default start, or the raw m
-    largest columns, reproduce the default run exactly."""
-    A = _rand(20, 70, 31)
-    c = np.linalg.norm(A, axis=0)
-    g = oracle.gamma_from_rho(A, "SL1", 0.2)
-    ref = oracle.gpower(A, "SL1", g, tol=0.0, maxit=12)
-    i = int(np.argmax(c))
-    alt = oracle.gpower(A, "SL1", g, tol=0.0, maxit=12, x0=5.0 * A[:, i])
-    np.testing.assert_allclose(alt.X, ref.X, atol=1e-14)
-    mu = np.array([1.0, 0.8, 0.6])
-    gb = 0.2 * c.max() * mu
-    refb = oracle.gpower(A, "BL1", gb, mu=mu, tol=0.0, maxit=12)
-    order = np.argsort(-c, kind="stable")[:3]
-    altb = oracle.gpower(A, "BL1", gb, mu=mu, tol=0.0, maxit=12, x0=A[:, order])
-    np.testing.assert_allclose(altb.X, refb.X, atol=1e-13)
+# ---------------------------------------------------------------- block start
+
+def test_splitmix64_published_outputs():
+    """SplitMix64 seeded with 0: the published first outputs of the generator."""
+    out = oracle.splitmix64(0, np.arange(1, 4, dtype=np.uint64))
+    assert [int(v) for v in out] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_sketch_is_balanced_rademacher():
+    S = oracle.sketch_signs(4000, 8)
+    assert set(np.unique(S)) == {-1.0, 1.0}
+    assert abs(S.mean()) < 0.03
+    np.testing.assert_array_equal(S, oracle.sketch_signs(4000, 8))
+    np.testing.assert_array_equal(S[:100, :3], oracle.sketch_signs(100, 3))  # entries depend on (r, j) only
+
+
+def test_block_start_rayleigh_ritz_and_svd_limit():
+    """The start X0 = Q V is orthonormal and diagonalises A A^T on its span
+    with non-increasing Ritz values; with many power steps it is the top-m
+    left singular vectors of A (independent SVD), signed by the rule."""
+    A, U, V = _low_rank_plus_noise(30, 80, [12.0, 8.0, 5.0, 3.0], seed=5, noise=0.1)
+    X0, st = oracle.block_start(A, 3)
+    assert st is None
+    np.testing.assert_allclose(X0.T @ X0, np.eye(3), atol=1e-13)
+    R = X0.T @ A @ A.T @ X0
+    np.testing.assert_allclose(R - np.diag(np.diag(R)), 0.0, atol=1e-9 * np.abs(R).max())
+    assert np.all(np.diff(np.diag(R)) <= 1e-9 * np.abs(R).max())
+    Xl, _ = oracle.block_start(A, 3, steps=300)
+    Us = np.linalg.svd(A)[0][:, :3]
+    for j in range(3):
+        assert abs(Xl[:, j] @ Us[:, j]) == pytest.approx(1.0, abs=1e-10)
+
+
+def test_block_start_rank_deficient_is_degenerate():
+    A = np.outer(np.arange(1.0, 7.0), np.ones(10))  # rank one, m = 2
+    X0, st = oracle.block_start(A, 2)
+    assert st == oracle.STATUS_DEGENERATE
+    r = oracle.gpower(A, "BL1", [0.1, 0.1], mu=[1, 1])
+    assert np.all(r.status == oracle.STATUS_DEGENERATE) and np.all(r.iters == 0)
