@@ -7,6 +7,14 @@ namespace gpspca {
 
 // ---------------------------------------------------------------- helpers
 
+// k-th output of the SplitMix64 stream seeded with `seed`.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t k) {
+  uint64_t z = seed + k * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
 __device__ __forceinline__ int stop_rule(int k, double f, double f_prev, double tol, int maxit) {
   // Stopping test after sweep k (objective f_k): zero objective, relative
   // change below tol (from the second sweep on), or the sweep budget.
@@ -434,6 +442,9 @@ __global__ void gather_start_kernel(const StartArgs a) {
   TC v;
   if (io->has_x0) {
     v = static_cast<const TC*>(io->x0)[static_cast<int64_t>(j) * a.p + r];
+  } else if (a.form >= 2) {  // block start: Rademacher sketch
+    const uint64_t k = (static_cast<uint64_t>(j) << 32) + static_cast<uint64_t>(r) + 1ull;
+    v = (splitmix64(kSketchSeed, k) >> 63) ? TC(-1) : TC(1);
   } else {
     const int col = st->start_cols[j];
     v = to_tc<TA>(static_cast<const TA*>(io->A)[static_cast<int64_t>(col) * a.ld + r]);
@@ -449,6 +460,7 @@ __global__ void __launch_bounds__(kReduceRows* kReduceGroups) reduce_kernel(cons
   if (a.st->n_active == 0) return;
   __shared__ double part[kReduceGroups][kReduceRows];
   __shared__ double Ys[kMaxM][kReduceRows];
+  __shared__ double Yo[kMaxM][kReduceRows];  // cross mode: the previous Y
   const int tid = threadIdx.x;
   const int rl = tid % kReduceRows, g = tid / kReduceRows;
   const int row = blockIdx.x * kReduceRows + rl;
@@ -467,9 +479,22 @@ __global__ void __launch_bounds__(kReduceRows* kReduceGroups) reduce_kernel(cons
       for (int g2 = 0; g2 < kReduceGroups; ++g2) t += part[g2][rl];
       const TC tc = static_cast<TC>(t);
       Ys[j][rl] = (row < p) ? static_cast<double>(tc) : 0.0;
-      if (row < p) Y[static_cast<int64_t>(j) * p + row] = tc;
+      if (a.cross) {
+        Yo[j][rl] = (row < p) ? static_cast<double>(Y[static_cast<int64_t>(j) * p + row]) : 0.0;
+      } else if (row < p) {
+        Y[static_cast<int64_t>(j) * p + row] = tc;
+      }
     }
     __syncthreads();
+  }
+  if (a.cross) {  // C[j][l] = sum_r Yold[r][j] Ynew[r][l]
+    for (int q = tid; q < a.npairs; q += blockDim.x) {
+      const int j = q / m, l = q % m;
+      double s = 0.0;
+      for (int r = 0; r < kReduceRows; ++r) s += Yo[j][r] * Ys[l][r];
+      a.io->gpart[static_cast<int64_t>(blockIdx.x) * a.npairs + q] = s;
+    }
+    return;
   }
   for (int q = tid; q < a.npairs; q += blockDim.x) {
     int j, l;
@@ -487,8 +512,74 @@ __global__ void __launch_bounds__(kReduceRows* kReduceGroups) reduce_kernel(cons
   }
 }
 
-// Objective, stopping test and projection weights after a sweep (or for the
-// start when init != 0).  One CTA; all FP64.
+// Rayleigh-Ritz rotation of the block start.  The current start is
+// Q = Y W (W the symmetric polar weights in the state) and the last sketch
+// sweep gave C = Y^T (A A^T Q); B = Q^T A A^T Q = W C, symmetrised.  Its
+// eigenvectors, by decreasing Ritz value, each signed so that its
+// largest-magnitude entry (first on ties) is positive, rotate the start:
+// new weights W V.  m x m work in FP64.
+__device__ void ritz_weights(const double* C, int m, const double* Wcur, double* Wout, double* sm,
+                             double* scratch) {
+  const int mm = m + (m & 1);
+  double* G = sm;
+  double* V = sm + mm * mm;
+  int* rp = reinterpret_cast<int*>(V + mm * mm);
+  int* rq = rp + 32;
+  double* rc = reinterpret_cast<double*>(rq + 32);
+  double* rs = rc + 32;
+  double* lam = rs + 32;
+  __shared__ int ord[kMaxM];
+  __shared__ double sgn[kMaxM];
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  for (int idx = tid; idx < mm * mm; idx += nthr) {
+    const int r = idx / mm, c = idx % mm;
+    double v = 0.0;
+    if (r < m && c < m) {
+      double brc = 0.0, bcr = 0.0;
+      for (int k = 0; k < m; ++k) {
+        brc += Wcur[r * m + k] * C[k * m + c];
+        bcr += Wcur[c * m + k] * C[k * m + r];
+      }
+      v = 0.5 * (brc + bcr);
+    }
+    G[idx] = v;
+  }
+  __syncthreads();
+  jacobi_eig(G, V, mm, rp, rq, rc, rs, scratch);
+  if (tid < m) lam[tid] = G[tid * mm + tid];
+  __syncthreads();
+  if (tid == 0) {  // order by decreasing Ritz value (ties: lower index first)
+    for (int j = 0; j < m; ++j) ord[j] = j;
+    for (int a = 0; a < m; ++a) {
+      int best = a;
+      for (int b = a + 1; b < m; ++b)
+        if (lam[ord[b]] > lam[ord[best]]) best = b;
+      const int t = ord[a];
+      ord[a] = ord[best];
+      ord[best] = t;
+    }
+    for (int j = 0; j < m; ++j) {
+      const int c = ord[j];
+      int imax = 0;
+      for (int i = 1; i < m; ++i)
+        if (fabs(V[i * mm + c]) > fabs(V[imax * mm + c])) imax = i;
+      sgn[j] = V[imax * mm + c] < 0.0 ? -1.0 : 1.0;
+    }
+  }
+  __syncthreads();
+  for (int idx = tid; idx < m * m; idx += nthr) {
+    const int l = idx / m, j = idx % m;
+    const int c = ord[j];
+    double s = 0.0;
+    for (int k = 0; k < m; ++k) s += Wcur[l * m + k] * V[k * mm + c];
+    Wout[l * m + j] = sgn[j] * s;
+  }
+  __syncthreads();
+}
+
+// Objective, stopping test and projection weights after a sweep, or one step
+// of the start (projection of the start, Rayleigh-Ritz rotation).  One CTA;
+// all FP64.
 __global__ void __launch_bounds__(kFinishThreads) finish_kernel(const FinishArgs a) {
   extern __shared__ double fsm[];
   State* st = a.st;
@@ -502,12 +593,16 @@ __global__ void __launch_bounds__(kFinishThreads) finish_kernel(const FinishArgs
   double* fz = gsum + a.npairs;          // 2m
   double* Wt = fz + 2 * kMaxM;           // m*m
   double* jac = Wt + kMaxM * kMaxM;      // Jacobi workspace
-  bool proceed = st->n_active > 0;
+  const bool proceed = st->n_active > 0;
   if (proceed) {
     sum_partials(io->gpart, a.nblk, a.npairs, a.npairs, gsum);
-    if (!a.init) sum_partials(io->fpart, a.nsplit, 2 * m, 2 * m, fz);
+    if (a.mode == kFinishIterate) sum_partials(io->fpart, a.nsplit, 2 * m, 2 * m, fz);
   }
-  if (proceed && a.init) {
+  if (proceed && a.mode == kFinishRitz) {
+    ritz_weights(gsum, m, st->W, Wt, jac, scratch);
+    if (tid == 0)
+      for (int idx = 0; idx < m * m; ++idx) st->W[idx] = Wt[idx];
+  } else if (proceed && a.mode == kFinishPolar) {
     if (block) {
       const bool ok = polar_weights(gsum, m, Wt, jac, scratch);
       if (tid == 0) {
@@ -535,7 +630,6 @@ __global__ void __launch_bounds__(kFinishThreads) finish_kernel(const FinishArgs
       }
       st->n_active = na;
     }
-    if (tid == 0) st->k = 0;
   } else if (proceed) {
     const int k = st->k;
     const double tol = io->tol;
@@ -609,6 +703,7 @@ __global__ void __launch_bounds__(kFinishThreads) finish_kernel(const FinishArgs
     if (tid == 0) st->k = k + 1;
   }
   __syncthreads();
+  if (tid == 0 && a.mode != kFinishIterate && a.last) st->k = 0;
   if (tid == 0 && a.use_cond) cudaGraphSetConditional(a.cond, st->n_active > 0 ? 1u : 0u);
 }
 

@@ -15,7 +15,8 @@ struct ReduceArgs {
   int m, p;
   int full_gram;      // 1: all j <= l pairs (block forms); 0: diagonal only
   int npairs;
-  int init;           // 1: reducing the start (runs even before the state is active)
+  int init;           // 1: the partials are the start directions io->P (nsplit = 1)
+  int cross;          // 1: no Y update; Gram partials of (old Y, new Y) pairs, m*m
 };
 
 struct FinishArgs {
@@ -24,10 +25,20 @@ struct FinishArgs {
   int nsplit;  // objective partials in io->fpart
   int nblk;    // Gram partials in io->gpart
   int npairs;
-  int m, form, init;
+  int m, form;
+  int mode;  // kFinishIterate, kFinishPolar (project the start), kFinishRitz (rotate the start)
+  int last;  // 1: the start is complete after this step (sweep counter k = 0)
   cudaGraphConditionalHandle cond;
   int use_cond;
 };
+
+enum : int { kFinishIterate = 0, kFinishPolar = 1, kFinishRitz = 2 };
+
+// Fixed sketch of the block start: SplitMix64 (Steele, Lea & Flood 2014),
+// entry (r, j) = sign from the top bit of output k = j * 2^32 + r + 1 of the
+// stream seeded with kSketchSeed.
+constexpr unsigned long long kSketchSeed = 0x5EED5EED5EED5EEDull;
+constexpr int kPowerSteps = 2;
 
 struct StartArgs {
   const IO* io;

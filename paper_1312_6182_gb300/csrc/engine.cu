@@ -118,6 +118,7 @@ struct Plan {
   int dtype = 0, form = 0, m = 0, p = 0, n = 0;
   int64_t ld = 0;
   int fast = 0;
+  int pca = 0;  // block start by power steps + Rayleigh-Ritz (no caller x0)
   int C = 1, ps = 0, ncl = 0, cols_per_cl = 0;
   std::vector<Pass> passes;
   int nred = 0, npairs = 0, full_gram = 0;
@@ -127,8 +128,8 @@ struct Plan {
 
   std::string key() const {
     char b[256];
-    snprintf(b, sizeof(b), "%d/%d/%d/%d/%d/%lld/%d/%d/%d/%d/%d", dtype, form, m, p, n, (long long)ld, fast, C, ps,
-             ncl, cols_per_cl);
+    snprintf(b, sizeof(b), "%d/%d/%d/%d/%d/%lld/%d/%d/%d/%d/%d/%d", dtype, form, m, p, n, (long long)ld, fast, pca, C,
+             ps, ncl, cols_per_cl);
     std::string s(b);
     for (const Pass& q : passes) {
       snprintf(b, sizeof(b), "|%d,%d,%d,%d,%d,%d,%d", q.j0, q.mgv, q.mg, q.nch, q.threads, q.W, q.S);
@@ -249,7 +250,7 @@ static int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, 
   pl.cols_per_cl = static_cast<int>((n + ncl - 1) / ncl);
   pl.nred = static_cast<int>((p + kReduceRows - 1) / kReduceRows);
   pl.full_gram = form >= 2 ? 1 : 0;
-  pl.npairs = pl.full_gram ? m * (m + 1) / 2 : m;
+  pl.npairs = pl.full_gram ? m * m : m;  // gpart capacity: the Ritz step's cross Gram is m x m
   pl.finish_smem = static_cast<int>(sizeof(double)) * (pl.npairs + 2 * kMaxM + kMaxM * kMaxM + 2 * kMaxM * kMaxM + 256);
   pl.ws_cnorm = sizeof(double) * n;
   pl.ws_P = static_cast<size_t>(d.tcsize) * m * p;
@@ -387,22 +388,43 @@ static void slot_free(Slot* s) {
 
 // ---------------------------------------------------------------- graph
 
-static void launch_prologue(const Plan& pl, Slot* s, cudaStream_t cs, cudaGraphConditionalHandle h, int use_cond = 1) {
+static void launch_sweeps(const Plan& pl, Slot* s, cudaStream_t cs, int sketch = 0);
+
+// Start of the solve: norms, gamma, the start directions and their
+// projection.  Block forms without a caller start then take kPowerSteps
+// power steps (A A^T Q, projected) and a Rayleigh-Ritz rotation.
+static void launch_prologue(const Plan& pl, Slot* s, cudaStream_t cs, cudaGraphConditionalHandle h, bool pca,
+                            int use_cond = 1) {
   launch_reset(s->io_dev, s->st_dev, pl.m, pl.form, cs);
   launch_colnorm(pl.dtype, s->io_dev, s->st_dev, pl.ld, pl.p, pl.n, pl.fast, cs);
   StartArgs sa{s->io_dev, s->st_dev, pl.ld, pl.p, pl.n, pl.m, pl.form};
   launch_select_start(pl.dtype, sa, cs);
   launch_gather_start(pl.dtype, sa, cs);
-  ReduceArgs ra{s->io_dev, s->st_dev, 1, pl.m, pl.p, pl.full_gram, pl.npairs, 1};
+  const int gram_pairs = pl.full_gram ? pl.m * (pl.m + 1) / 2 : pl.m;
+  ReduceArgs ra{s->io_dev, s->st_dev, 1, pl.m, pl.p, pl.full_gram, gram_pairs, 1, 0};
   launch_reduce(pl.tcsize, ra, pl.nred, cs);
-  FinishArgs fa{s->io_dev, s->st_dev, pl.ncl, pl.nred, pl.npairs, pl.m, pl.form, 1, h, use_cond};
+  FinishArgs fa{s->io_dev, s->st_dev, pl.ncl, pl.nred, gram_pairs, pl.m, pl.form, kFinishPolar, pca ? 0 : 1, h,
+                use_cond};
   launch_finish(fa, pl.finish_smem, cs);
+  if (!pca) return;
+  for (int step = 0; step < kPowerSteps; ++step) {
+    launch_sweeps(pl, s, cs, 1);
+    ReduceArgs rp{s->io_dev, s->st_dev, pl.ncl, pl.m, pl.p, 1, gram_pairs, 0, 0};
+    launch_reduce(pl.tcsize, rp, pl.nred, cs);
+    FinishArgs fp{s->io_dev, s->st_dev, pl.ncl, pl.nred, gram_pairs, pl.m, pl.form, kFinishPolar, 0, h, use_cond};
+    launch_finish(fp, pl.finish_smem, cs);
+  }
+  launch_sweeps(pl, s, cs, 1);
+  ReduceArgs rc{s->io_dev, s->st_dev, pl.ncl, pl.m, pl.p, 1, pl.m * pl.m, 0, 1};
+  launch_reduce(pl.tcsize, rc, pl.nred, cs);
+  FinishArgs fr{s->io_dev, s->st_dev, pl.ncl, pl.nred, pl.m * pl.m, pl.m, pl.form, kFinishRitz, 1, h, use_cond};
+  launch_finish(fr, pl.finish_smem, cs);
 }
 
-static void launch_sweeps(const Plan& pl, Slot* s, cudaStream_t cs) {
+static void launch_sweeps(const Plan& pl, Slot* s, cudaStream_t cs, int sketch) {
   for (const Pass& q : pl.passes) {
     SweepArgs a{s->io_dev, s->st_dev, pl.ld, pl.p, pl.n, pl.m, pl.form, q.j0, q.mgv, pl.ps, q.W, q.S,
-                pl.cols_per_cl, pl.fast};
+                pl.cols_per_cl, pl.fast, sketch};
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -422,9 +444,10 @@ static void launch_sweeps(const Plan& pl, Slot* s, cudaStream_t cs) {
 
 static void launch_body(const Plan& pl, Slot* s, cudaStream_t cs, cudaGraphConditionalHandle h) {
   launch_sweeps(pl, s, cs);
-  ReduceArgs ra{s->io_dev, s->st_dev, pl.ncl, pl.m, pl.p, pl.full_gram, pl.npairs, 0};
+  const int gram_pairs = pl.full_gram ? pl.m * (pl.m + 1) / 2 : pl.m;
+  ReduceArgs ra{s->io_dev, s->st_dev, pl.ncl, pl.m, pl.p, pl.full_gram, gram_pairs, 0, 0};
   launch_reduce(pl.tcsize, ra, pl.nred, cs);
-  FinishArgs fa{s->io_dev, s->st_dev, pl.ncl, pl.nred, pl.npairs, pl.m, pl.form, 0, h, 1};
+  FinishArgs fa{s->io_dev, s->st_dev, pl.ncl, pl.nred, gram_pairs, pl.m, pl.form, kFinishIterate, 0, h, 1};
   launch_finish(fa, pl.finish_smem, cs);
 }
 
@@ -438,7 +461,7 @@ static int build_graph(const Plan& pl, Slot* s, Slot::GraphEntry* out) {
   cudaGraphConditionalHandle h;
   GP_CUDA(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
   GP_CUDA(cudaStreamBeginCaptureToGraph(s->cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  launch_prologue(pl, s, s->cap, h);
+  launch_prologue(pl, s, s->cap, h, pl.pca != 0);
   cudaStreamCaptureStatus cst;
   const cudaGraphNode_t* deps = nullptr;
   size_t ndeps = 0;
@@ -584,6 +607,7 @@ static int prepare_solve(Slot* s, const Request& r, int nsm, bool scratch_out, P
   const bool fast = (reinterpret_cast<uintptr_t>(A_dev) % 16 == 0) && ((ld * d.esize) % 16 == 0);
   Plan& pl = *plan;
   if ((rc = make_plan(r.A.dtype, r.form, m, p, n, ld, fast, nsm, &pl))) return rc;
+  pl.pca = (r.form >= GPSPCA_BL1 && !r.x0) ? 1 : 0;
   if ((rc = ensure(s, &s->b_cnorm, pl.ws_cnorm))) return rc;
   if ((rc = ensure(s, &s->b_P, pl.ws_P))) return rc;
   if ((rc = ensure(s, &s->b_Y, pl.ws_P))) return rc;
@@ -870,7 +894,7 @@ int gpspca_time_sweep(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form,
   rc = prepare_solve(s, r, ctx->nsm, true, &pl, &empty);
   if (rc != GPSPCA_OK) return rc;
   if (empty) return fail(GPSPCA_EINVAL, "empty matrix");
-  launch_prologue(pl, s, s->stream, cudaGraphConditionalHandle{}, 0);
+  launch_prologue(pl, s, s->stream, cudaGraphConditionalHandle{}, pl.pca != 0, 0);
   cudaEvent_t e0, e1;
   GP_CUDA(cudaEventCreate(&e0));
   GP_CUDA(cudaEventCreate(&e1));

@@ -86,6 +86,7 @@ struct SweepArgs {
   int form;
   int j0, mg_valid;
   int ps, W, S, cols_per_cl, fast;
+  int sketch;  // 1: power step of the block start (no threshold, no outputs)
 };
 
 }  // namespace gpspca

@@ -214,6 +214,9 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH>::MAXT, 1) sweep_kernel(c
   const int S = a.S;
   const int ntiles = (ncols + W - 1) / W;
   const bool block = a.form >= 2;
+  // the block start's power steps use g = t (L0 threshold at gamma = 0, mu = 1)
+  const bool sketch = a.sketch != 0;
+  const int form = sketch ? GPSPCA_SL0 : a.form;
   const TA* __restrict__ A = static_cast<const TA*>(io->A);
   const int64_t ld = a.ld;
 
@@ -233,7 +236,7 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH>::MAXT, 1) sweep_kernel(c
 
   // ---- prologue: parameters, weights, barriers, first tiles
   if (tid < MG) {
-    const bool v = tid < a.mg_valid;
+    const bool v = tid < a.mg_valid && !sketch;
     gam[tid] = v ? st->gamma[a.j0 + tid] : 0.0;
     muv[tid] = v ? io->mu[a.j0 + tid] : 1.0;
   }
@@ -298,7 +301,7 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH>::MAXT, 1) sweep_kernel(c
       }
     }
   }
-  if (cl == 0) {  // the iterate that this sweep evaluates is an output
+  if (cl == 0 && !sketch) {  // the iterate that this sweep evaluates is an output
     TC* Xo = static_cast<TC*>(io->X);
 #pragma unroll
     for (int j = 0; j < MG; ++j) {
@@ -388,8 +391,8 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH>::MAXT, 1) sweep_kernel(c
           sc = static_cast<double>(cscale[col]);
           td *= sc;
         }
-        const Thr th = threshold(a.form, td, gam[j], muv[j]);
-        if (cr == 0) {
+        const Thr th = threshold(form, td, gam[j], muv[j]);
+        if (cr == 0 && !sketch) {
           if (st->active[a.j0 + j]) Tout[static_cast<int64_t>(a.j0 + j) * n + col] = static_cast<TC>(td);
           facc += th.term;
           zacc += th.zr * th.zr;
@@ -440,7 +443,7 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH>::MAXT, 1) sweep_kernel(c
     zsm[tid] = zacc;
   }
   __syncthreads();
-  if (cr == 0 && tid < a.mg_valid) {
+  if (cr == 0 && tid < a.mg_valid && !sketch) {
     double F = 0.0, Zs = 0.0;
     for (int w = 0; w < WB; ++w) {
       F += fsm[w * MG + tid];

@@ -58,7 +58,8 @@ def test_fp64_200x1000_single_unit_l1(ctx):
     ref = oracle.gpower(A, "SL1", gam, tol=1e-6, maxit=1000)
     g, res = _run(ctx, At, "SL1", gam, tol=1e-6, maxit=1000)
     assert res.X.dtype == torch.float64
-    assert_matches("SL1", g, ref, tol_z=1e-9, tol_f=1e-11, tol_x=1e-9, iters_slack=0)
+    assert_matches("SL1", g, ref, oracle.column_norms(A), tol_z=1e-9, tol_f=1e-11, tol_x=1e-9, iters_slack=0,
+                   eps=2.0 ** -53)
 
 
 @pytest.fixture(scope="module")
@@ -83,7 +84,7 @@ def test_spikes_5000x20000_fp32(ctx, spikes_full, form, mu):
     gam = _gammas(A, form, [0.05] * m)
     ref = oracle.gpower(A, form, gam, mu=mu, tol=1e-6, maxit=1000)
     g, _ = _run(ctx, At, form, gam, mu=mu, tol=1e-6, maxit=1000)
-    assert_matches(form, g, ref, tol_z=1e-5, tol_f=1e-6, tol_x=1e-5)
+    assert_matches(form, g, ref, oracle.column_norms(A), tol_z=1e-5, tol_f=1e-6, tol_x=1e-5)
 
 
 # ---------------------------------------------------------------- fixed sweep counts
@@ -102,11 +103,11 @@ def test_fixed_sweeps_ragged(ctx, form, ld):
     if form.startswith("S"):
         gam, mu = _gammas(A, form, [0.02, 0.08, 0.2]), None
     else:
-        mu = [1.0, 0.9, 0.8, 0.7, 0.6]
-        gam = _gammas(A, form, [0.03] * 5) * (np.array(mu) if form.endswith("1") else np.array(mu) ** 2)
+        mu = [1.0, 0.8, 0.6]
+        gam = _gammas(A, form, [0.03] * 3) * (np.array(mu) if form.endswith("1") else np.array(mu) ** 2)
     ref = oracle.gpower(A, form, gam, mu=mu, tol=0.0, maxit=15)
     g, _ = _run(ctx, At, form, gam, mu=mu, tol=0.0, maxit=15, ld=ld)
-    assert_matches(form, g, ref, tol_z=2e-5, tol_f=1e-6, tol_x=2e-5, iters_slack=0)
+    assert_matches(form, g, ref, oracle.column_norms(A), tol_z=2e-5, tol_f=1e-6, tol_x=2e-5, iters_slack=0)
 
 
 @pytest.mark.parametrize("form", ["SL1", "SL0"])
@@ -118,20 +119,21 @@ def test_gamma_path_64(ctx, form):
     gam = _gammas(A, form, synth.log_spaced_rho(64))
     ref = oracle.gpower(A, form, gam, tol=1e-6, maxit=300)
     g, _ = _run(ctx, At, form, gam, tol=1e-6, maxit=300)
-    assert_matches(form, g, ref, tol_z=1e-4, tol_f=1e-6, tol_x=1e-4, iters_slack=2)
+    assert_matches(form, g, ref, oracle.column_norms(A), tol_z=1e-4, tol_f=1e-6, tol_x=1e-4, iters_slack=2)
 
 
-@pytest.mark.parametrize("m", [16, 32])
-def test_block_many_components(ctx, m):
-    """Block L1 with m = 16 and 32 components (several component passes per
-    sweep, a 16x16 / 32x32 FP64 Jacobi polar step), fixed sweep count."""
-    At = synth.planted_spike(900, 4000, 4, [30.0, 20.0, 15.0, 10.0], support_frac=0.02, seed=7,
+@pytest.mark.parametrize("p,n,m", [(1500, 8000, 16), (2000, 12000, 32)])
+def test_block_many_components(ctx, p, n, m):
+    """Block L1 with m = 16 and 32 components on as many planted spikes
+    (theta_j = 100/sqrt(j), 1% supports): several component passes per sweep,
+    a 16x16 / 32x32 FP64 Jacobi polar step, the PCA start; 8 sweeps."""
+    At = synth.planted_spike(p, n, m, [100.0 / np.sqrt(j) for j in range(1, m + 1)], support_frac=0.01, seed=7,
                              dtype=np.float32)
     A = At.astype(np.float64).T
     gam = _gammas(A, "BL1", [0.02] * m)
     ref = oracle.gpower(A, "BL1", gam, mu=[1.0] * m, tol=0.0, maxit=8)
     g, _ = _run(ctx, At, "BL1", gam, mu=[1.0] * m, tol=0.0, maxit=8)
-    assert_matches("BL1", g, ref, tol_z=5e-5, tol_f=1e-6, tol_x=5e-5, iters_slack=0)
+    assert_matches("BL1", g, ref, oracle.column_norms(A), tol_z=5e-5, tol_f=1e-6, tol_x=5e-5, iters_slack=0)
 
 
 # ---------------------------------------------------------------- storage precisions
@@ -161,7 +163,7 @@ def test_bf16_storage_matches_oracle_on_stored_values(ctx, form):
     gam = _gammas(A, form, [0.05] * m)
     ref = oracle.gpower(A, form, gam, mu=mu, tol=1e-6, maxit=500)
     res = ctx.solve(tb.cuda(), form, list(gam), mu=mu, tol=1e-6, maxit=500)
-    assert_matches(form, gpu_arrays(res), ref, tol_z=1e-5, tol_f=1e-6, tol_x=1e-5)
+    assert_matches(form, gpu_arrays(res), ref, oracle.column_norms(A), tol_z=1e-5, tol_f=1e-6, tol_x=1e-5)
 
 
 @pytest.mark.parametrize("form", ["SL0", "BL1"])
@@ -175,7 +177,7 @@ def test_fp8_storage_matches_oracle_on_stored_values(ctx, form):
     gam = _gammas(A, form, [0.05] * m)
     ref = oracle.gpower(A, form, gam, mu=mu, tol=1e-6, maxit=500)
     res = ctx.solve(q.cuda(), form, list(gam), mu=mu, tol=1e-6, maxit=500, col_scale=s.cuda())
-    assert_matches(form, gpu_arrays(res), ref, tol_z=1e-5, tol_f=1e-6, tol_x=1e-5)
+    assert_matches(form, gpu_arrays(res), ref, oracle.column_norms(A), tol_z=1e-5, tol_f=1e-6, tol_x=1e-5)
 
 
 @pytest.mark.parametrize("fmt", ["bf16", "fp8"])
@@ -229,7 +231,7 @@ def test_relative_gamma_is_scaled_on_device(ctx):
         ga = res.gamma_abs.cpu().numpy()
         np.testing.assert_allclose(ga, oracle.gamma_from_rho(A, form, rho), rtol=1e-12)
         ref = oracle.gpower(A, form, ga, mu=None if m == 1 else [1.0, 1.0])
-        assert_matches(form, gpu_arrays(res), ref)
+        assert_matches(form, gpu_arrays(res), ref, oracle.column_norms(A))
 
 
 def test_warm_start_x0(ctx):
@@ -241,7 +243,7 @@ def test_warm_start_x0(ctx):
     ref = oracle.gpower(A, "BL0", gam, mu=[1.0, 1.0], tol=0.0, maxit=10, x0=x0)
     g, _ = _run(ctx, At, "BL0", gam, mu=[1.0, 1.0], tol=0.0, maxit=10,
                 x0=torch.from_numpy(x0.T.astype(np.float32).copy()).cuda())
-    assert_matches("BL0", g, ref, tol_z=2e-5, tol_x=2e-5, iters_slack=0)
+    assert_matches("BL0", g, ref, oracle.column_norms(A), tol_z=2e-5, tol_x=2e-5, iters_slack=0)
 
 
 def test_deterministic(ctx):
@@ -265,7 +267,7 @@ def test_tiny_shapes(ctx):
         gam = _gammas(A, form, [0.1] * m)
         ref = oracle.gpower(A, form, gam, mu=mu, tol=0.0, maxit=6)
         g, _ = _run(ctx, At, form, gam, mu=mu, tol=0.0, maxit=6)
-        assert_matches(form, g, ref, tol_z=1e-5, tol_x=1e-5, iters_slack=0)
+        assert_matches(form, g, ref, oracle.column_norms(A), tol_z=1e-5, tol_x=1e-5, iters_slack=0)
 
 
 def test_zero_matrix_and_large_gamma(ctx):
@@ -309,7 +311,7 @@ def test_degenerate_polar_status(ctx):
     res = ctx.solve(torch.from_numpy(At).cuda(), "BL1", gam, mu=[1.0, 1.0])
     assert res.rc == binding.EDEGENERATE
     g = gpu_arrays(res)
-    assert_matches("BL1", g, ref, iters_slack=0)
+    assert_matches("BL1", g, ref, oracle.column_norms(A), iters_slack=0)
 
 
 def test_invalid_arguments(ctx):
