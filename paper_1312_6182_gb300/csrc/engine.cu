@@ -83,6 +83,7 @@ static const void* sweep_ptr(int dt, int mg, int nch) {
 struct KAttr {
   int max_threads = 0;
   size_t local = 0;
+  int max_dyn_smem = 0;  // dynamic shared memory this kernel may use
   bool ok = false;
 };
 
@@ -95,12 +96,20 @@ static KAttr kattr(const void* f) {
   if (it != g_attr.end()) return it->second;
   KAttr k;
   cudaFuncAttributes a;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (cudaFuncGetAttributes(&a, f) == cudaSuccess) {
-    k.max_threads = a.maxThreadsPerBlock;
-    k.local = a.localSizeBytes;
-    k.ok = true;
-    cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    // the opt-in limit covers static and dynamic shared memory together
+    const int dyn = optin - static_cast<int>(a.sharedSizeBytes);
+    if (dyn > 0 && cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) == cudaSuccess) {
+      k.max_threads = a.maxThreadsPerBlock;
+      k.local = a.localSizeBytes;
+      k.max_dyn_smem = dyn;
+      k.ok = true;
+    }
   }
+  cudaGetLastError();
   g_attr[f] = k;
   return k;
 }
@@ -162,7 +171,7 @@ static std::vector<std::pair<int, int>> split_components(int m) {
 // cluster size C.  Returns false if this C does not fit.
 static bool fit_pass(int dt, int mg, int C, int ps, int m, Pass* out) {
   const DInfo d = dinfo(dt);
-  static const int kNch[] = {1, 2, 4};
+  static const int kNch[] = {1, 2, 3, 4};
   for (int nch : kNch) {
     const void* k = sweep_ptr(dt, mg, nch);
     if (!k) continue;
@@ -176,7 +185,7 @@ static bool fit_pass(int dt, int mg, int C, int ps, int m, Pass* out) {
     const int nw = threads / 32;
     const SweepSmem base = sweep_smem_layout(0, 0, ps, d.esize, d.tcsize, nw, m, mg);
     const int room = kSmemBudget - base.total;
-    int W = std::min(wb, std::max(1, 32768 / colbytes));
+    int W = std::min(wb, std::max(1, 49152 / colbytes));
     int S = 0;
     while (W >= 1) {
       S = std::min(8, room / (W * colbytes));
@@ -185,6 +194,7 @@ static bool fit_pass(int dt, int mg, int C, int ps, int m, Pass* out) {
     }
     if (W < 1 || S < 2) continue;
     const SweepSmem L = sweep_smem_layout(W, S, ps, d.esize, d.tcsize, nw, m, mg);
+    if (L.total > at.max_dyn_smem) continue;
     *out = Pass{0, 0, mg, nch, threads, W, S, L.total, k};
     return true;
   }
@@ -380,21 +390,30 @@ static void slot_free(Slot* s) {
   if (s->io_host) cudaFreeHost(s->io_host);
   if (s->st_host) cudaFreeHost(s->st_host);
   if (s->done) cudaEventDestroy(s->done);
-  if (s->cap) cudaStreamDestroy(s->cap);
-  if (s->cap2) cudaStreamDestroy(s->cap2);
+  for (cudaStream_t c : {s->cap2, s->cap}) {  // never destroy a stream that is still capturing
+    if (!c) continue;
+    cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c, &cst) == cudaSuccess && cst != cudaStreamCaptureStatusNone) {
+      cudaGraph_t g = nullptr;
+      cudaStreamEndCapture(c, &g);
+      if (g) cudaGraphDestroy(g);
+    }
+    cudaGetLastError();
+    cudaStreamDestroy(c);
+  }
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
   *s = Slot();
 }
 
 // ---------------------------------------------------------------- graph
 
-static void launch_sweeps(const Plan& pl, Slot* s, cudaStream_t cs, int sketch = 0);
+static cudaError_t launch_sweeps(const Plan& pl, Slot* s, cudaStream_t cs, int sketch = 0);
 
 // Start of the solve: norms, gamma, the start directions and their
 // projection.  Block forms without a caller start then take kPowerSteps
 // power steps (A A^T Q, projected) and a Rayleigh-Ritz rotation.
-static void launch_prologue(const Plan& pl, Slot* s, cudaStream_t cs, cudaGraphConditionalHandle h, bool pca,
-                            int use_cond = 1) {
+static cudaError_t launch_prologue(const Plan& pl, Slot* s, cudaStream_t cs, cudaGraphConditionalHandle h, bool pca,
+                                   int use_cond = 1) {
   launch_reset(s->io_dev, s->st_dev, pl.m, pl.form, cs);
   launch_colnorm(pl.dtype, s->io_dev, s->st_dev, pl.ld, pl.p, pl.n, pl.fast, cs);
   StartArgs sa{s->io_dev, s->st_dev, pl.ld, pl.p, pl.n, pl.m, pl.form};
@@ -406,22 +425,24 @@ static void launch_prologue(const Plan& pl, Slot* s, cudaStream_t cs, cudaGraphC
   FinishArgs fa{s->io_dev, s->st_dev, pl.ncl, pl.nred, gram_pairs, pl.m, pl.form, kFinishPolar, pca ? 0 : 1, h,
                 use_cond};
   launch_finish(fa, pl.finish_smem, cs);
-  if (!pca) return;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !pca) return e;
   for (int step = 0; step < kPowerSteps; ++step) {
-    launch_sweeps(pl, s, cs, 1);
+    if ((e = launch_sweeps(pl, s, cs, 1)) != cudaSuccess) return e;
     ReduceArgs rp{s->io_dev, s->st_dev, pl.ncl, pl.m, pl.p, 1, gram_pairs, 0, 0};
     launch_reduce(pl.tcsize, rp, pl.nred, cs);
     FinishArgs fp{s->io_dev, s->st_dev, pl.ncl, pl.nred, gram_pairs, pl.m, pl.form, kFinishPolar, 0, h, use_cond};
     launch_finish(fp, pl.finish_smem, cs);
   }
-  launch_sweeps(pl, s, cs, 1);
+  if ((e = launch_sweeps(pl, s, cs, 1)) != cudaSuccess) return e;
   ReduceArgs rc{s->io_dev, s->st_dev, pl.ncl, pl.m, pl.p, 1, pl.m * pl.m, 0, 1};
   launch_reduce(pl.tcsize, rc, pl.nred, cs);
   FinishArgs fr{s->io_dev, s->st_dev, pl.ncl, pl.nred, pl.m * pl.m, pl.m, pl.form, kFinishRitz, 1, h, use_cond};
   launch_finish(fr, pl.finish_smem, cs);
+  return cudaGetLastError();
 }
 
-static void launch_sweeps(const Plan& pl, Slot* s, cudaStream_t cs, int sketch) {
+static cudaError_t launch_sweeps(const Plan& pl, Slot* s, cudaStream_t cs, int sketch) {
   for (const Pass& q : pl.passes) {
     SweepArgs a{s->io_dev, s->st_dev, pl.ld, pl.p, pl.n, pl.m, pl.form, q.j0, q.mgv, pl.ps, q.W, q.S,
                 pl.cols_per_cl, pl.fast, sketch};
@@ -438,53 +459,75 @@ static void launch_sweeps(const Plan& pl, Slot* s, cudaStream_t cs, int sketch) 
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     void* args[] = {&a};
-    cudaLaunchKernelExC(&cfg, q.k, args);
+    const cudaError_t e = cudaLaunchKernelExC(&cfg, q.k, args);
+    if (e != cudaSuccess) return e;
   }
+  return cudaSuccess;
 }
 
-static void launch_body(const Plan& pl, Slot* s, cudaStream_t cs, cudaGraphConditionalHandle h) {
-  launch_sweeps(pl, s, cs);
+static cudaError_t launch_body(const Plan& pl, Slot* s, cudaStream_t cs, cudaGraphConditionalHandle h) {
+  cudaError_t e = launch_sweeps(pl, s, cs);
+  if (e != cudaSuccess) return e;
   const int gram_pairs = pl.full_gram ? pl.m * (pl.m + 1) / 2 : pl.m;
   ReduceArgs ra{s->io_dev, s->st_dev, pl.ncl, pl.m, pl.p, pl.full_gram, gram_pairs, 0, 0};
   launch_reduce(pl.tcsize, ra, pl.nred, cs);
   FinishArgs fa{s->io_dev, s->st_dev, pl.ncl, pl.nred, gram_pairs, pl.m, pl.form, kFinishIterate, 0, h, 1};
   launch_finish(fa, pl.finish_smem, cs);
+  return cudaGetLastError();
 }
 
-static void launch_epilogue(const Plan& pl, Slot* s, cudaStream_t cs) {
+static cudaError_t launch_epilogue(const Plan& pl, Slot* s, cudaStream_t cs) {
   launch_finalize(pl.tcsize, s->io_dev, s->st_dev, pl.p, pl.n, pl.m, pl.form, cs);
+  return cudaGetLastError();
 }
 
 static int build_graph(const Plan& pl, Slot* s, Slot::GraphEntry* out) {
   cudaGraph_t g = nullptr;
   GP_CUDA(cudaGraphCreate(&g, 0));
+  bool outer = false, inner = false;
+  cudaGraph_t tmp = nullptr;
+  // on any failure: end the open captures (so the streams leave capture
+  // mode), drop the partial graph and report the first error
+  auto abort_with = [&](cudaError_t e, const char* what) {
+    if (inner) cudaStreamEndCapture(s->cap2, &tmp);
+    if (outer) cudaStreamEndCapture(s->cap, &tmp);
+    cudaGetLastError();
+    cudaGraphDestroy(g);
+    return fail(GPSPCA_ECUDA, "graph build (%s): %s", what, cudaGetErrorString(e));
+  };
   cudaGraphConditionalHandle h;
-  GP_CUDA(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
-  GP_CUDA(cudaStreamBeginCaptureToGraph(s->cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  launch_prologue(pl, s, s->cap, h, pl.pca != 0);
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) return abort_with(e, "conditional handle");
+  if ((e = cudaStreamBeginCaptureToGraph(s->cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)))
+    return abort_with(e, "begin capture");
+  outer = true;
+  if ((e = launch_prologue(pl, s, s->cap, h, pl.pca != 0))) return abort_with(e, "start kernels");
   cudaStreamCaptureStatus cst;
   const cudaGraphNode_t* deps = nullptr;
   size_t ndeps = 0;
-  GP_CUDA(cudaStreamGetCaptureInfo(s->cap, &cst, nullptr, nullptr, &deps, nullptr, &ndeps));
+  if ((e = cudaStreamGetCaptureInfo(s->cap, &cst, nullptr, nullptr, &deps, nullptr, &ndeps)))
+    return abort_with(e, "capture info");
   cudaGraphNodeParams cp = {};
   cp.type = cudaGraphNodeTypeConditional;
   cp.conditional.handle = h;
   cp.conditional.type = cudaGraphCondTypeWhile;
   cp.conditional.size = 1;
   cudaGraphNode_t cnode;
-  GP_CUDA(cudaGraphAddNode(&cnode, g, deps, nullptr, ndeps, &cp));
+  if ((e = cudaGraphAddNode(&cnode, g, deps, nullptr, ndeps, &cp))) return abort_with(e, "while node");
   cudaGraph_t body = cp.conditional.phGraph_out[0];
-  GP_CUDA(cudaStreamUpdateCaptureDependencies(s->cap, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
-  GP_CUDA(cudaStreamBeginCaptureToGraph(s->cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  launch_body(pl, s, s->cap2, h);
-  cudaGraph_t body_out = nullptr;
-  GP_CUDA(cudaStreamEndCapture(s->cap2, &body_out));
-  launch_epilogue(pl, s, s->cap);
-  cudaGraph_t gout = nullptr;
-  GP_CUDA(cudaStreamEndCapture(s->cap, &gout));
-  GP_CUDA(cudaGetLastError());
+  if ((e = cudaStreamUpdateCaptureDependencies(s->cap, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies)))
+    return abort_with(e, "capture dependencies");
+  if ((e = cudaStreamBeginCaptureToGraph(s->cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)))
+    return abort_with(e, "begin body capture");
+  inner = true;
+  if ((e = launch_body(pl, s, s->cap2, h))) return abort_with(e, "loop body kernels");
+  inner = false;
+  if ((e = cudaStreamEndCapture(s->cap2, &tmp))) return abort_with(e, "end body capture");
+  if ((e = launch_epilogue(pl, s, s->cap))) return abort_with(e, "loadings kernel");
+  outer = false;
+  if ((e = cudaStreamEndCapture(s->cap, &tmp))) return abort_with(e, "end capture");
   cudaGraphExec_t exec = nullptr;
-  GP_CUDA(cudaGraphInstantiate(&exec, g, 0));
+  if ((e = cudaGraphInstantiate(&exec, g, 0))) return abort_with(e, "instantiate");
   out->g = g;
   out->exec = exec;
   return GPSPCA_OK;
@@ -894,13 +937,13 @@ int gpspca_time_sweep(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form,
   rc = prepare_solve(s, r, ctx->nsm, true, &pl, &empty);
   if (rc != GPSPCA_OK) return rc;
   if (empty) return fail(GPSPCA_EINVAL, "empty matrix");
-  launch_prologue(pl, s, s->stream, cudaGraphConditionalHandle{}, pl.pca != 0, 0);
+  GP_CUDA(launch_prologue(pl, s, s->stream, cudaGraphConditionalHandle{}, pl.pca != 0, 0));
   cudaEvent_t e0, e1;
   GP_CUDA(cudaEventCreate(&e0));
   GP_CUDA(cudaEventCreate(&e1));
-  launch_sweeps(pl, s, s->stream);  // warm-up
+  GP_CUDA(launch_sweeps(pl, s, s->stream));  // warm-up
   GP_CUDA(cudaEventRecord(e0, s->stream));
-  for (int i = 0; i < reps; ++i) launch_sweeps(pl, s, s->stream);
+  for (int i = 0; i < reps; ++i) GP_CUDA(launch_sweeps(pl, s, s->stream));
   GP_CUDA(cudaEventRecord(e1, s->stream));
   GP_CUDA(cudaEventSynchronize(e1));
   GP_CUDA(cudaGetLastError());

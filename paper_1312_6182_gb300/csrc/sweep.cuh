@@ -119,11 +119,13 @@ __device__ __forceinline__ Thr threshold(int form, double t, double gam, double 
   return r;
 }
 
-// Reduce 32 per-lane values over the warp; lane L returns the total of v[L].
-template <typename T>
-__device__ __forceinline__ T warp_reduce_scatter32(T (&v)[32], int lane) {
+// Reduce K per-lane values over the warp (K a power of two <= 32): lane L
+// returns the warp total of v[L % K].  K - 1 shuffles halve the vector over
+// the low lane bits, then log2(32/K) more add the remaining lane groups.
+template <int K, typename T>
+__device__ __forceinline__ T warp_reduce_scatter(T (&v)[K], int lane) {
 #pragma unroll
-  for (int h = 16; h >= 1; h >>= 1) {
+  for (int h = K / 2; h >= 1; h >>= 1) {
     const bool up = (lane & h) != 0;
 #pragma unroll
     for (int i = 0; i < h; ++i) {
@@ -132,7 +134,22 @@ __device__ __forceinline__ T warp_reduce_scatter32(T (&v)[32], int lane) {
       v[i] = keep + __shfl_xor_sync(0xffffffffu, send, h);
     }
   }
+#pragma unroll
+  for (int o = K; o < 32; o <<= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
   return v[0];
+}
+
+// Gradient factor of Table 1 in the compute type (the threshold decision on
+// the critical path of a tile); the objective is recomputed in double off it.
+template <typename TC>
+__device__ __forceinline__ TC grad_factor(int form, TC t, TC gam, TC mu) {
+  if ((form & 1) == 0) {
+    const TC s = mu * (t < TC(0) ? -t : t) - gam;
+    if (!(s > TC(0))) return TC(0);
+    return t > TC(0) ? mu * s : -(mu * s);
+  }
+  const TC u = mu * t;
+  return (u * u > gam) ? mu * mu * t : TC(0);
 }
 
 constexpr int kRingSlack = 33 * 4 * 4 * 8;  // 33 * NCHmax * VECmax * 8-byte elements
@@ -170,8 +187,11 @@ struct SweepCfg {
   using TC = typename Elem<TA>::TC;
   static constexpr int VEC = Elem<TA>::VEC;
   static constexpr int R = NCH * VEC;
-  static constexpr int WB = 32 / MG;  // most columns one tile can hold
-  static constexpr int REGS = static_cast<int>(sizeof(TC) / 4) * (2 * R * MG + 32) + 80;
+  // (column, component) dot products reduced per tile; single-unit tiles
+  // hold at most 8 columns (long columns leave room for 1-3 anyway)
+  static constexpr int KB = MG == 1 ? 8 : 32;
+  static constexpr int WB = KB / MG;  // most columns one tile can hold
+  static constexpr int REGS = static_cast<int>(sizeof(TC) / 4) * (2 * R * MG + KB) + 72;
   // register arrays of x and y beyond this spill; such variants are not built
   static constexpr bool kBuilt = static_cast<int>(sizeof(TC) / 4) * 2 * R * MG <= 160;
   static constexpr int MAXT_RAW = 65536 / REGS;
@@ -186,6 +206,7 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH>::MAXT, 1) sweep_kernel(c
   using TC = typename Cfg::TC;
   constexpr int VEC = Cfg::VEC;
   constexpr int WB = Cfg::WB;
+  constexpr int KB = Cfg::KB;
   constexpr bool kFP8 = (sizeof(TA) == 1);
 
   State* st = a.st;
@@ -232,6 +253,8 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH>::MAXT, 1) sweep_kernel(c
   double* muv = reinterpret_cast<double*>(smem + L.mu);
   double* fsm = reinterpret_cast<double*>(smem + L.facc);
   double* zsm = reinterpret_cast<double*>(smem + L.zacc);
+  __shared__ TC gam_c[MG], mu_c[MG];
+  __shared__ int act[MG];
   const int stage_elems = W * ps;
 
   // ---- prologue: parameters, weights, barriers, first tiles
@@ -239,6 +262,9 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH>::MAXT, 1) sweep_kernel(c
     const bool v = tid < a.mg_valid && !sketch;
     gam[tid] = v ? st->gamma[a.j0 + tid] : 0.0;
     muv[tid] = v ? io->mu[a.j0 + tid] : 1.0;
+    gam_c[tid] = static_cast<TC>(gam[tid]);
+    mu_c[tid] = static_cast<TC>(muv[tid]);
+    act[tid] = (tid < a.mg_valid) ? st->active[a.j0 + tid] : 0;
   }
   for (int idx = tid; idx < m * MG; idx += nthr) {
     const int l = idx / MG, j = idx % MG;
@@ -305,7 +331,7 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH>::MAXT, 1) sweep_kernel(c
     TC* Xo = static_cast<TC*>(io->X);
 #pragma unroll
     for (int j = 0; j < MG; ++j) {
-      if (j < a.mg_valid && st->active[a.j0 + j]) {
+      if (j < a.mg_valid && act[j]) {
 #pragma unroll
         for (int c = 0; c < NCH; ++c)
 #pragma unroll
@@ -338,10 +364,16 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH>::MAXT, 1) sweep_kernel(c
       __syncthreads();
     }
 
+    // this thread's (column, component) of the tile, and the FP8 column scale
+    const int wq = tid / MG, jq = tid % MG;
+    const bool mine_valid = tid < WB * MG && wq < wv && jq < a.mg_valid;
+    TC scl = TC(1);
+    if (kFP8 && mine_valid) scl = static_cast<TC>(cscale[c0 + wq]);
+
     // partial dots over this thread's rows
-    TC pd[32];
+    TC pd[KB];
 #pragma unroll
-    for (int i = 0; i < 32; ++i) pd[i] = 0;
+    for (int i = 0; i < KB; ++i) pd[i] = 0;
 #pragma unroll
     for (int w = 0; w < WB; ++w) {
       if (w < wv) {
@@ -359,49 +391,40 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH>::MAXT, 1) sweep_kernel(c
         }
       }
     }
-    const TC mine = warp_reduce_scatter32(pd, lane);
-    red[warp * 32 + lane] = mine;
+    const TC mine = warp_reduce_scatter<KB>(pd, lane);
+    if (lane < KB) red[warp * KB + lane] = mine;
     __syncthreads();  // (1) partials visible; previous tile's buffer free
     if (a.fast && tid == 0 && tile >= 1 && tile - 1 + S < ntiles) issue_tile(tile - 1 + S, (tile - 1) % S);
-    if (tid < 32) {
-      TC s = 0;
-      for (int w2 = 0; w2 < nwarps; ++w2) s += red[w2 * 32 + tid];
-      xch[(tile & 1) * 32 + tid] = s;
+    TC t = 0;
+    if (tid < KB) {
+      for (int w2 = 0; w2 < nwarps; ++w2) t += red[w2 * KB + tid];
     }
     if (C > 1) {
+      if (tid < KB) xch[(tile & 1) * 32 + tid] = t;
       cluster_sync_all();  // (2) every CTA's partial visible cluster-wide
-    } else {
-      __syncthreads();
-    }
-    if (tid < WB * MG) {
-      const int w = tid / MG, j = tid % MG;
-      TC t = 0;
-      if (C > 1) {
+      if (tid < KB) {
         const uint32_t addr = smem_u32(&xch[(tile & 1) * 32 + tid]);
+        t = 0;
         for (uint32_t r = 0; r < C; ++r) t += dsmem_ld(dsmem_map(addr, r), TC(0));
-      } else {
-        t = xch[(tile & 1) * 32 + tid];
       }
+    }
+    if (tid < KB) {
       TC g = 0;
-      if (w < wv && j < a.mg_valid) {
-        const int col = c0 + w;
-        double td = static_cast<double>(t);
-        double sc = 1.0;
-        if (kFP8) {
-          sc = static_cast<double>(cscale[col]);
-          td *= sc;
-        }
-        const Thr th = threshold(form, td, gam[j], muv[j]);
-        if (cr == 0 && !sketch) {
-          if (st->active[a.j0 + j]) Tout[static_cast<int64_t>(a.j0 + j) * n + col] = static_cast<TC>(td);
-          facc += th.term;
-          zacc += th.zr * th.zr;
-        }
-        g = static_cast<TC>(th.g * sc);
+      if (mine_valid) {
+        t *= scl;
+        g = grad_factor<TC>(form, t, gam_c[jq], mu_c[jq]) * scl;
       }
       gsm[tid] = g;
     }
     __syncthreads();  // (3) g visible
+    // off the critical path: the Table 1 objective in double and T
+    if (mine_valid && cr == 0 && !sketch) {
+      const double td = static_cast<double>(t);
+      const Thr th = threshold(form, td, gam[jq], muv[jq]);
+      if (act[jq]) Tout[static_cast<int64_t>(a.j0 + jq) * n + c0 + wq] = t;
+      facc += th.term;
+      zacc += th.zr * th.zr;
+    }
 
     // rank update y += g a over this thread's rows of the tile
 #pragma unroll
