@@ -181,7 +181,7 @@ static bool fit_pass(int dt, int mg, int C, int ps, int m, Pass* out) {
     threads = std::max(64, (threads + 31) / 32 * 32);
     if (threads > at.max_threads) continue;
     const int colbytes = ps * d.esize;
-    const int wb = 32 / mg;
+    const int wb = sweep_kb(mg) / mg;  // the kernel's tile width limit
     const int nw = threads / 32;
     const SweepSmem base = sweep_smem_layout(0, 0, ps, d.esize, d.tcsize, nw, m, mg);
     const int room = kSmemBudget - base.total;

@@ -182,14 +182,18 @@ __host__ __device__ inline SweepSmem sweep_smem_layout(int W, int S, int ps, int
   return L;
 }
 
+// (column, component) dot products reduced per tile, one per lane of a warp
+// (single-unit tiles hold at most 8 columns; long columns leave room for 1-3
+// anyway).  The host caps the tile width at sweep_kb(mg) / mg with the same
+// function.
+__host__ __device__ constexpr int sweep_kb(int mg) { return mg == 1 ? 8 : 32; }
+
 template <typename TA, int MG, int NCH>
 struct SweepCfg {
   using TC = typename Elem<TA>::TC;
   static constexpr int VEC = Elem<TA>::VEC;
   static constexpr int R = NCH * VEC;
-  // (column, component) dot products reduced per tile; single-unit tiles
-  // hold at most 8 columns (long columns leave room for 1-3 anyway)
-  static constexpr int KB = MG == 1 ? 8 : 32;
+  static constexpr int KB = sweep_kb(MG);
   static constexpr int WB = KB / MG;  // most columns one tile can hold
   static constexpr int REGS = static_cast<int>(sizeof(TC) / 4) * (2 * R * MG + KB) + 72;
   // register arrays of x and y beyond this spill; such variants are not built
@@ -391,24 +395,28 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH>::MAXT, 1) sweep_kernel(c
         }
       }
     }
+    // Lane L holds the warp total of slot L % KB.  Every lane of a warp stores
+    // and the whole of warp 0 forms the CTA totals (slots >= KB repeat
+    // slots < KB and are ignored): control flow between the two block
+    // barriers stays uniform within each warp.
     const TC mine = warp_reduce_scatter<KB>(pd, lane);
-    if (lane < KB) red[warp * KB + lane] = mine;
+    red[warp * 32 + lane] = mine;
     __syncthreads();  // (1) partials visible; previous tile's buffer free
     if (a.fast && tid == 0 && tile >= 1 && tile - 1 + S < ntiles) issue_tile(tile - 1 + S, (tile - 1) % S);
     TC t = 0;
-    if (tid < KB) {
-      for (int w2 = 0; w2 < nwarps; ++w2) t += red[w2 * KB + tid];
+    if (warp == 0) {
+      for (int w2 = 0; w2 < nwarps; ++w2) t += red[w2 * 32 + lane];
     }
     if (C > 1) {
-      if (tid < KB) xch[(tile & 1) * 32 + tid] = t;
+      if (warp == 0) xch[(tile & 1) * 32 + lane] = t;
       cluster_sync_all();  // (2) every CTA's partial visible cluster-wide
-      if (tid < KB) {
-        const uint32_t addr = smem_u32(&xch[(tile & 1) * 32 + tid]);
+      if (warp == 0) {
+        const uint32_t addr = smem_u32(&xch[(tile & 1) * 32 + lane]);
         t = 0;
         for (uint32_t r = 0; r < C; ++r) t += dsmem_ld(dsmem_map(addr, r), TC(0));
       }
     }
-    if (tid < KB) {
+    if (warp == 0) {
       TC g = 0;
       if (mine_valid) {
         t *= scl;
