@@ -743,6 +743,7 @@ static int solve_result(Slot* s) {
   const State& st = *s->st_host;
   if (st.error & kErrNonFinite) return fail(GPSPCA_ENONFINITE, "A has a non-finite entry (or an entry whose square overflows)");
   if (st.error & kErrTimeout) return fail(GPSPCA_ETIMEDOUT, "a device-side wait for a tile copy gave up");
+  if (st.error & kErrLaunch) return fail(GPSPCA_ECUDA, "internal: sweep launched with a tile wider than it reduces");
   if (st.any_degenerate) return fail(GPSPCA_EDEGENERATE, "polar step met a rank-deficient Y (status DEGENERATE)");
   return GPSPCA_OK;
 }

@@ -42,7 +42,7 @@ struct IO {
 };
 
 // Error bits in State::error.
-enum : int32_t { kErrNonFinite = 1, kErrTimeout = 2 };
+enum : int32_t { kErrNonFinite = 1, kErrTimeout = 2, kErrLaunch = 4 };
 
 // Device-resident state of one solve.
 struct State {

@@ -215,6 +215,10 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH>::MAXT, 1) sweep_kernel(c
 
   State* st = a.st;
   if (st->n_active == 0) return;  // uniform across the grid
+  if (a.W > WB || a.W < 1) {      // a tile wider than this variant reduces: refuse, uniformly
+    if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(&st->error, static_cast<int>(kErrLaunch));
+    return;
+  }
 
   const IO* io = a.io;
   const int tid = threadIdx.x;
