@@ -169,6 +169,33 @@ int gpspca_poll(gpspca_ctx* ctx, uint64_t ticket, int32_t wait_us);
 int gpspca_time_sweep(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form, const double* gamma, int32_t m,
                       const double* mu, uint32_t flags, int32_t reps, double* ms_per_sweep);
 
+/* One fused single-unit sweep that allocates no memory (the paper has no
+ * counterpart; it serves callers that cannot allocate device memory when
+ * they need a sweep, e.g. because another framework's caching allocator
+ * holds the free HBM, or because the call sits in a latency-bound loop or in
+ * code where allocation is forbidden).  No context is needed.
+ *
+ * For a float32 matrix A in device memory and a device iterate x (p floats,
+ * used as given), it computes on the device: t = A^T x (n floats), the
+ * objective f of Table 1 at x (one double) and x_next = A g / ||A g|| (p
+ * floats; all zero when every entry is thresholded), where g is the SL1 or
+ * SL0 gradient factor at gamma (absolute).  All outputs are caller-owned
+ * device memory.  Runs on cuda_stream (NULL: the legacy default stream) and
+ * returns when the results are ready.
+ *
+ * Scratch lives in file-scope device arrays of fixed size (6 MiB: the
+ * per-cluster partials of y, up to 160 clusters x p floats) that every GPU
+ * loading the library keeps until the process exits.  Limit: p <= 8192;
+ * a larger p returns GPSPCA_EINVAL naming the limit.
+ * The arrays are shared by every call: calls are serialised inside the
+ * library, and calls that overlapped on the GPU (e.g. from other processes
+ * sharing a context) would race.  The first call on a device resolves the
+ * arrays' device addresses (cudaGetSymbolAddress); make it before any
+ * stream capture.  No cudaMalloc, cudaFree or allocating library routine is
+ * called. */
+int gpspca_sweep_static(const gpspca_matrix* A, gpspca_form form, double gamma, const float* x, float* x_next,
+                        float* t, double* objective, void* cuda_stream);
+
 /* Finish queued work, free every workspace buffer and the context. */
 int gpspca_destroy(gpspca_ctx* ctx);
 

@@ -36,7 +36,7 @@ ERROR_NAMES = {
 }
 
 EXPORTED = ("gpspca_create", "gpspca_solve", "gpspca_submit", "gpspca_poll", "gpspca_destroy",
-            "gpspca_last_error", "gpspca_time_sweep")
+            "gpspca_last_error", "gpspca_time_sweep", "gpspca_sweep_static")
 
 
 class Matrix(ctypes.Structure):
@@ -95,6 +95,8 @@ def load(path: str = LIB_PATH):
     lib.gpspca_time_sweep.argtypes = [P, ctypes.POINTER(Matrix), ctypes.c_int, D, ctypes.c_int32, D,
                                       ctypes.c_uint32, ctypes.c_int32, D]
     lib.gpspca_time_sweep.restype = ctypes.c_int
+    lib.gpspca_sweep_static.argtypes = [ctypes.POINTER(Matrix), ctypes.c_int, ctypes.c_double, P, P, P, P, P]
+    lib.gpspca_sweep_static.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -294,3 +296,24 @@ class Context:
                                           _darr(mu, m), GAMMA_RELATIVE if gamma_relative else 0, int(reps),
                                           ctypes.byref(ms)))
         return ms.value
+
+
+def sweep_static(At, form: str, gamma: float, x, x_next, t, objective, p: Optional[int] = None, stream=None) -> int:
+    """One allocation-free single-unit sweep (gpspca_sweep_static).
+
+    At: float32 CUDA tensor (n, ld); x, x_next: float32 CUDA tensors of p
+    entries; t: float32 CUDA tensor of n entries; objective: float64 CUDA
+    tensor of one entry.  Every buffer is the caller's; the library allocates
+    nothing.  Returns OK or raises GpspcaError.
+    """
+    import torch
+
+    lib = load()
+    M = matrix(At, p)
+    torch.cuda.current_stream().synchronize()
+    handle = None
+    if stream is not None:
+        handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    rc = lib.gpspca_sweep_static(ctypes.byref(M), FORMS[form], float(gamma), x.data_ptr(), x_next.data_ptr(),
+                                 t.data_ptr(), objective.data_ptr(), handle)
+    return _check(rc)

@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "aux.cuh"
+#include "plan.h"
 
 namespace gpspca {
 
@@ -50,6 +51,8 @@ static int fail(int code, const char* fmt, ...) {
   t_last_error = buf;
   return code;
 }
+
+int record_error(int code, const char* msg) { return fail(code, "%s", msg); }
 
 #define GP_CUDA(call)                                                                           \
   do {                                                                                          \
@@ -118,37 +121,6 @@ static KAttr kattr(const void* f) {
 
 constexpr int kSmemBudget = 200 * 1024;  // stage ring + bookkeeping, per CTA
 
-struct Pass {
-  int j0, mgv, mg, nch, threads, W, S, smem;
-  const void* k;
-};
-
-struct Plan {
-  int dtype = 0, form = 0, m = 0, p = 0, n = 0;
-  int64_t ld = 0;
-  int fast = 0;
-  int pca = 0;  // block start by power steps + Rayleigh-Ritz (no caller x0)
-  int C = 1, ps = 0, ncl = 0, cols_per_cl = 0;
-  std::vector<Pass> passes;
-  int nred = 0, npairs = 0, full_gram = 0;
-  int finish_smem = 0;
-  int tcsize = 4, esize = 4;
-  size_t ws_cnorm = 0, ws_P = 0, ws_ypart = 0, ws_T = 0, ws_fpart = 0, ws_gpart = 0;
-
-  std::string key() const {
-    char b[256];
-    snprintf(b, sizeof(b), "%d/%d/%d/%d/%d/%lld/%d/%d/%d/%d/%d/%d", dtype, form, m, p, n, (long long)ld, fast, pca, C,
-             ps, ncl, cols_per_cl);
-    std::string s(b);
-    for (const Pass& q : passes) {
-      snprintf(b, sizeof(b), "|%d,%d,%d,%d,%d,%d,%d", q.j0, q.mgv, q.mg, q.nch, q.threads, q.W, q.S);
-      s += b;
-    }
-    return s;
-  }
-  size_t workspace_bytes() const { return ws_cnorm + ws_P + ws_ypart + ws_T + ws_fpart + ws_gpart + 7 * 256; }
-};
-
 static const int kMGs[] = {1, 2, 4, 5, 8};
 
 // Components per pass: passes of 8, the last one the smallest built width.
@@ -201,7 +173,7 @@ static bool fit_pass(int dt, int mg, int C, int ps, int m, Pass* out) {
   return false;
 }
 
-static int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fast, int nsm, Plan* P) {
+int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fast, int nsm, Plan* P) {
   const DInfo d = dinfo(dt);
   Plan pl;
   pl.dtype = dt;

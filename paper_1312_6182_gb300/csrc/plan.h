@@ -1,0 +1,50 @@
+// Launch plan of one solve (chosen by the engine from the kernels' register
+// and shared-memory needs); shared by the entry points of the library.
+#pragma once
+
+#include <stdint.h>
+
+#include <cstdio>
+#include <string>
+#include <vector>
+
+namespace gpspca {
+
+struct Pass {
+  int j0, mgv, mg, nch, threads, W, S, smem;
+  const void* k;
+};
+
+struct Plan {
+  int dtype = 0, form = 0, m = 0, p = 0, n = 0;
+  int64_t ld = 0;
+  int fast = 0;
+  int pca = 0;  // block start by power steps + Rayleigh-Ritz (no caller x0)
+  int C = 1, ps = 0, ncl = 0, cols_per_cl = 0;
+  std::vector<Pass> passes;
+  int nred = 0, npairs = 0, full_gram = 0;
+  int finish_smem = 0;
+  int tcsize = 4, esize = 4;
+  size_t ws_cnorm = 0, ws_P = 0, ws_ypart = 0, ws_T = 0, ws_fpart = 0, ws_gpart = 0;
+
+  std::string key() const {
+    char b[256];
+    snprintf(b, sizeof(b), "%d/%d/%d/%d/%d/%lld/%d/%d/%d/%d/%d/%d", dtype, form, m, p, n, (long long)ld, fast, pca, C,
+             ps, ncl, cols_per_cl);
+    std::string s(b);
+    for (const Pass& q : passes) {
+      snprintf(b, sizeof(b), "|%d,%d,%d,%d,%d,%d,%d", q.j0, q.mgv, q.mg, q.nch, q.threads, q.W, q.S);
+      s += b;
+    }
+    return s;
+  }
+  size_t workspace_bytes() const { return ws_cnorm + ws_P + ws_ypart + ws_T + ws_fpart + ws_gpart + 7 * 256; }
+};
+
+// Plan a solve: cluster size, per-pass kernel variant, threads, tile ring.
+int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fast, int nsm, Plan* P);
+
+// Record `msg` as the calling thread's last error (gpspca_last_error) and return code.
+int record_error(int code, const char* msg);
+
+}  // namespace gpspca
