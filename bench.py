@@ -311,13 +311,43 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_sweep_only(args):
+    """The fused sweep alone on the benchmark matrix (profiling entry):
+    prints the mean time of one sweep and the algorithmic bandwidth."""
+    import torch
+
+    from paper_1312_6182_gb300 import binding, synth
+
+    At = synth.workload_spikes_5000x20000(0)
+    if args.sweep_dtype == "bf16":
+        dA = torch.from_numpy(At).cuda().to(torch.bfloat16)
+    else:
+        dA = torch.from_numpy(At).cuda()
+    form = args.sweep_only
+    m = 1 if form.startswith("S") else args.sweep_m
+    mu = None if m == 1 else [1.0] * m
+    with binding.Context(0) as ctx:
+        ms = ctx.time_sweep(dA, form, [RHO] * m, mu=mu, gamma_relative=True, reps=args.reps)
+    nbytes = P * N * dA.element_size()
+    print(json.dumps({"sweep": form, "m": m, "dtype": args.sweep_dtype, "ms": round(ms, 5),
+                      "GB/s": round(nbytes / (ms / 1e3) / 1e9, 1)}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--sweep-only", default=None, choices=["SL1", "SL0", "BL1", "BL0"],
+                    help="time the fused sweep alone on the benchmark matrix (profiling)")
+    ap.add_argument("--sweep-m", type=int, default=5)
+    ap.add_argument("--sweep-dtype", default="f32", choices=["f32", "bf16"])
+    ap.add_argument("--reps", type=int, default=20)
     args = ap.parse_args()
+    if args.sweep_only:
+        run_sweep_only(args)
+        return
     if args.warmup < 3 and args.impl == "gpu":
         args.warmup = 3
     if args.impl == "reference":

@@ -157,7 +157,7 @@ static bool fit_pass(int dt, int mg, int C, int ps, int m, Pass* out) {
     const int nw = threads / 32;
     const SweepSmem base = sweep_smem_layout(0, 0, ps, d.esize, d.tcsize, nw, m, mg);
     const int room = kSmemBudget - base.total;
-    int W = std::min(wb, std::max(1, 49152 / colbytes));
+    int W = std::min(wb, std::max(1, 65536 / colbytes));
     int S = 0;
     while (W >= 1) {
       S = std::min(8, room / (W * colbytes));

@@ -84,4 +84,18 @@ __device__ __forceinline__ double dsmem_ld(uint32_t addr, double) {
   return v;
 }
 
+// Store a value into shared memory of CTA `rank` of the cluster (address
+// already mapped with dsmem_map) and signal the byte count on that CTA's
+// mbarrier (also mapped): one-way, no cluster barrier.
+__device__ __forceinline__ void st_async_remote(uint32_t addr, float v, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(addr),
+               "r"(__float_as_uint(v)), "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void st_async_remote(uint32_t addr, double v, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];" ::"r"(addr),
+               "l"(__double_as_longlong(v)), "r"(bar)
+               : "memory");
+}
+
 }  // namespace gpspca

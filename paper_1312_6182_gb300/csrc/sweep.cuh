@@ -156,8 +156,9 @@ constexpr int kRingSlack = 33 * 4 * 4 * 8;  // 33 * NCHmax * VECmax * 8-byte ele
 
 // Shared-memory layout of the sweep kernel (host and device agree on it).
 struct SweepSmem {
-  int stage_bytes, bars, red, xch, gsm, wsm, gam, mu, facc, zacc, total;
+  int stage_bytes, bars, xbars, red, xrecv, wsm, gam, mu, facc, zacc, total;
 };
+constexpr int kMaxCluster = 8;
 __host__ __device__ inline int align_up(int v, int a) { return (v + a - 1) / a * a; }
 __host__ __device__ inline SweepSmem sweep_smem_layout(int W, int S, int ps, int esize, int tcsize, int nwarps, int m,
                                                       int mg) {
@@ -167,11 +168,11 @@ __host__ __device__ inline SweepSmem sweep_smem_layout(int W, int S, int ps, int
   // are read (and masked) but must stay inside the allocation: the slack
   // after the ring covers the largest overshoot (< 33 * NCH * VEC elements).
   int o = align_up(S * L.stage_bytes + kRingSlack, 128);
-  L.bars = o; o += 8 * S;
+  L.bars = o; o += 8 * S;         // tile-copy mbarriers
+  L.xbars = o; o += 8 * 2;        // cluster-exchange mbarriers (by tile parity)
   o = align_up(o, 16);
-  L.red = o; o += nwarps * 32 * tcsize;
-  L.xch = o; o += 2 * 32 * tcsize;
-  L.gsm = o; o += 32 * tcsize;
+  L.red = o; o += 2 * nwarps * 32 * tcsize;          // warp partials, by tile parity
+  L.xrecv = o; o += 2 * kMaxCluster * 32 * tcsize;   // partials pushed by cluster peers
   L.wsm = o; o += m * mg * tcsize;
   o = align_up(o, 8);
   L.gam = o; o += 8 * mg;
@@ -253,9 +254,9 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH>::MAXT, 1) sweep_kernel(c
   const SweepSmem L = sweep_smem_layout(W, S, ps, sizeof(TA), sizeof(TC), nwarps, m, MG);
   TA* stage = reinterpret_cast<TA*>(smem);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bars);
+  uint64_t* xbars = reinterpret_cast<uint64_t*>(smem + L.xbars);
   TC* red = reinterpret_cast<TC*>(smem + L.red);
-  TC* xch = reinterpret_cast<TC*>(smem + L.xch);
-  TC* gsm = reinterpret_cast<TC*>(smem + L.gsm);
+  TC* xrecv = reinterpret_cast<TC*>(smem + L.xrecv);
   TC* wsm = reinterpret_cast<TC*>(smem + L.wsm);
   double* gam = reinterpret_cast<double*>(smem + L.gam);
   double* muv = reinterpret_cast<double*>(smem + L.mu);
@@ -279,11 +280,15 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH>::MAXT, 1) sweep_kernel(c
     wsm[idx] = (j < a.mg_valid) ? static_cast<TC>(st->W[l * m + a.j0 + j]) : TC(0);
   }
   const uint32_t bytes_per_col = static_cast<uint32_t>(align_up(rows_valid * static_cast<int>(sizeof(TA)), 16));
-  if (a.fast && tid == 0) {
-    for (int s = 0; s < S; ++s) mbar_init(smem_u32(&bars[s]), 1);
+  if (tid == 0) {
+    if (a.fast)
+      for (int s = 0; s < S; ++s) mbar_init(smem_u32(&bars[s]), 1);
+    mbar_init(smem_u32(&xbars[0]), 1);
+    mbar_init(smem_u32(&xbars[1]), 1);
     fence_mbar_init();
   }
   __syncthreads();
+  if (C > 1) cluster_sync_all();  // peers' exchange barriers are initialised before any push
   auto issue_tile = [&](int tile, int buf) {
     const int c0 = col_begin + tile * W;
     const int wv = min(W, col_end - c0);
@@ -372,9 +377,9 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH>::MAXT, 1) sweep_kernel(c
       __syncthreads();
     }
 
-    // this thread's (column, component) of the tile, and the FP8 column scale
-    const int wq = tid / MG, jq = tid % MG;
-    const bool mine_valid = tid < WB * MG && wq < wv && jq < a.mg_valid;
+    // lane L of every warp owns slot L = (column w = L / MG, component j = L % MG)
+    const int wq = lane / MG, jq = lane % MG;
+    const bool mine_valid = lane < WB * MG && wq < wv && jq < a.mg_valid;
     TC scl = TC(1);
     if (kFP8 && mine_valid) scl = static_cast<TC>(cscale[c0 + wq]);
 
@@ -399,38 +404,42 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH>::MAXT, 1) sweep_kernel(c
         }
       }
     }
-    // Lane L holds the warp total of slot L % KB.  Every lane of a warp stores
-    // and the whole of warp 0 forms the CTA totals (slots >= KB repeat
-    // slots < KB and are ignored): control flow between the two block
-    // barriers stays uniform within each warp.
+    // Lane L holds the warp total of slot L % KB.  One block barrier per
+    // tile: afterwards every warp adds the warp totals itself (partials are
+    // double-buffered by tile parity), so no second barrier is needed to
+    // broadcast the thresholded values.
     const TC mine = warp_reduce_scatter<KB>(pd, lane);
-    red[warp * 32 + lane] = mine;
-    __syncthreads();  // (1) partials visible; previous tile's buffer free
+    TC* redp = red + (tile & 1) * nwarps * 32;
+    redp[warp * 32 + lane] = mine;
+    const int xp = tile & 1;
+    if (C > 1 && tid == 0)  // this tile's pushes from the C-1 peers
+      mbar_arrive_expect_tx(smem_u32(&xbars[xp]), static_cast<uint32_t>((C - 1) * KB * sizeof(TC)));
+    __syncthreads();  // (1) warp partials visible; the previous tile's buffer is free
     if (a.fast && tid == 0 && tile >= 1 && tile - 1 + S < ntiles) issue_tile(tile - 1 + S, (tile - 1) % S);
     TC t = 0;
-    if (warp == 0) {
-      for (int w2 = 0; w2 < nwarps; ++w2) t += red[w2 * 32 + lane];
-    }
+    for (int w2 = 0; w2 < nwarps; ++w2) t += redp[w2 * 32 + lane];
     if (C > 1) {
-      if (warp == 0) xch[(tile & 1) * 32 + lane] = t;
-      cluster_sync_all();  // (2) every CTA's partial visible cluster-wide
-      if (warp == 0) {
-        const uint32_t addr = smem_u32(&xch[(tile & 1) * 32 + lane]);
-        t = 0;
-        for (uint32_t r = 0; r < C; ++r) t += dsmem_ld(dsmem_map(addr, r), TC(0));
+      // push this CTA's partial to every peer (one-way), wait for theirs,
+      // add all C in rank order: every CTA of the cluster holds the same t
+      TC* slot = xrecv + xp * kMaxCluster * 32;
+      if (warp == 0 && lane < KB) {
+        const uint32_t src = smem_u32(&slot[cr * 32 + lane]);
+        const uint32_t bar = smem_u32(&xbars[xp]);
+        for (uint32_t r = 0; r < C; ++r)
+          if (r != cr) st_async_remote(dsmem_map(src, r), t, dsmem_map(bar, r));
       }
+      if (!mbar_wait_bounded(smem_u32(&xbars[xp]), static_cast<uint32_t>((tile >> 1) & 1))) timed_out = true;
+      TC tot = 0;
+      for (uint32_t r = 0; r < C; ++r) tot += (r == cr) ? t : slot[r * 32 + lane];
+      t = tot;
     }
-    if (warp == 0) {
-      TC g = 0;
-      if (mine_valid) {
-        t *= scl;
-        g = grad_factor<TC>(form, t, gam_c[jq], mu_c[jq]) * scl;
-      }
-      gsm[tid] = g;
+    TC g = 0;
+    if (mine_valid) {
+      t *= scl;
+      g = grad_factor<TC>(form, t, gam_c[jq], mu_c[jq]) * scl;
     }
-    __syncthreads();  // (3) g visible
-    // off the critical path: the Table 1 objective in double and T
-    if (mine_valid && cr == 0 && !sketch) {
+    // the Table 1 objective in double and T (one warp, off the other warps' path)
+    if (warp == 0 && mine_valid && cr == 0 && !sketch) {
       const double td = static_cast<double>(t);
       const Thr th = threshold(form, td, gam[jq], muv[jq]);
       if (act[jq]) Tout[static_cast<int64_t>(a.j0 + jq) * n + c0 + wq] = t;
@@ -444,7 +453,7 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH>::MAXT, 1) sweep_kernel(c
       if (w < wv) {
         TC gw[MG];
 #pragma unroll
-        for (int j = 0; j < MG; ++j) gw[j] = gsm[w * MG + j];
+        for (int j = 0; j < MG; ++j) gw[j] = __shfl_sync(0xffffffffu, g, w * MG + j);
         const TA* colp = sb + w * ps;
 #pragma unroll
         for (int c = 0; c < NCH; ++c) {
