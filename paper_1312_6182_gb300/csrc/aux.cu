@@ -487,6 +487,45 @@ __global__ void __launch_bounds__(kReduceRows* kReduceGroups) reduce_kernel(cons
     }
     __syncthreads();
   }
+  if (a.objective) {
+    // Table 1 objective f_j and the squared norm of the unnormalised
+    // loadings, in double, over this block's share of T (active components)
+    __shared__ double red2[2][kReduceGroups];
+    const int nb = gridDim.x;
+    const int chunk = (a.n + nb - 1) / nb;
+    const int i0 = blockIdx.x * chunk, i1 = min(a.n, i0 + chunk);
+    const TC* T = static_cast<const TC*>(a.io->T);
+    for (int j = 0; j < m; ++j) {
+      double f = 0.0, z2 = 0.0;
+      if (a.st->active[j]) {
+        const double gam = a.st->gamma[j], mu = a.io->mu[j];
+        for (int i = i0 + tid; i < i1; i += blockDim.x) {
+          const Thr th = threshold(a.form, static_cast<double>(T[static_cast<int64_t>(j) * a.n + i]), gam, mu);
+          f += th.term;
+          z2 += th.zr * th.zr;
+        }
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        f += __shfl_xor_sync(0xffffffffu, f, off);
+        z2 += __shfl_xor_sync(0xffffffffu, z2, off);
+      }
+      if ((tid & 31) == 0) {
+        red2[0][tid >> 5] = f;
+        red2[1][tid >> 5] = z2;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        double F = 0.0, Z2 = 0.0;
+        for (int w = 0; w < kReduceGroups; ++w) {
+          F += red2[0][w];
+          Z2 += red2[1][w];
+        }
+        a.io->fpart[(static_cast<int64_t>(blockIdx.x) * 2 + 0) * m + j] = F;
+        a.io->fpart[(static_cast<int64_t>(blockIdx.x) * 2 + 1) * m + j] = Z2;
+      }
+      __syncthreads();
+    }
+  }
   if (a.cross) {  // C[j][l] = sum_r Yold[r][j] Ynew[r][l]
     for (int q = tid; q < a.npairs; q += blockDim.x) {
       const int j = q / m, l = q % m;

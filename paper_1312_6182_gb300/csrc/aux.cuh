@@ -17,12 +17,14 @@ struct ReduceArgs {
   int npairs;
   int init;           // 1: the partials are the start directions io->P (nsplit = 1)
   int cross;          // 1: no Y update; Gram partials of (old Y, new Y) pairs, m*m
+  int objective;      // 1: also the Table 1 objective partials from io->T (n entries, form)
+  int n, form;
 };
 
 struct FinishArgs {
   const IO* io;
   State* st;
-  int nsplit;  // objective partials in io->fpart
+  int nsplit;  // objective partials in io->fpart (one set per reduction block)
   int nblk;    // Gram partials in io->gpart
   int npairs;
   int m, form;

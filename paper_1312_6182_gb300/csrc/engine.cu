@@ -238,7 +238,7 @@ int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fa
   pl.ws_P = static_cast<size_t>(d.tcsize) * m * p;
   pl.ws_ypart = static_cast<size_t>(d.tcsize) * ncl * m * p;
   pl.ws_T = static_cast<size_t>(d.tcsize) * m * n;
-  pl.ws_fpart = sizeof(double) * ncl * 2 * m;
+  pl.ws_fpart = sizeof(double) * static_cast<size_t>(pl.nred) * 2 * m;
   pl.ws_gpart = sizeof(double) * static_cast<size_t>(pl.nred) * pl.npairs;
   *P = pl;
   return GPSPCA_OK;
@@ -392,7 +392,7 @@ static cudaError_t launch_prologue(const Plan& pl, Slot* s, cudaStream_t cs, cud
   launch_select_start(pl.dtype, sa, cs);
   launch_gather_start(pl.dtype, sa, cs);
   const int gram_pairs = pl.full_gram ? pl.m * (pl.m + 1) / 2 : pl.m;
-  ReduceArgs ra{s->io_dev, s->st_dev, 1, pl.m, pl.p, pl.full_gram, gram_pairs, 1, 0};
+  ReduceArgs ra{s->io_dev, s->st_dev, 1, pl.m, pl.p, pl.full_gram, gram_pairs, 1, 0, 0, pl.n, pl.form};
   launch_reduce(pl.tcsize, ra, pl.nred, cs);
   FinishArgs fa{s->io_dev, s->st_dev, pl.ncl, pl.nred, gram_pairs, pl.m, pl.form, kFinishPolar, pca ? 0 : 1, h,
                 use_cond};
@@ -401,13 +401,13 @@ static cudaError_t launch_prologue(const Plan& pl, Slot* s, cudaStream_t cs, cud
   if (e != cudaSuccess || !pca) return e;
   for (int step = 0; step < kPowerSteps; ++step) {
     if ((e = launch_sweeps(pl, s, cs, 1)) != cudaSuccess) return e;
-    ReduceArgs rp{s->io_dev, s->st_dev, pl.ncl, pl.m, pl.p, 1, gram_pairs, 0, 0};
+    ReduceArgs rp{s->io_dev, s->st_dev, pl.ncl, pl.m, pl.p, 1, gram_pairs, 0, 0, 0, pl.n, pl.form};
     launch_reduce(pl.tcsize, rp, pl.nred, cs);
     FinishArgs fp{s->io_dev, s->st_dev, pl.ncl, pl.nred, gram_pairs, pl.m, pl.form, kFinishPolar, 0, h, use_cond};
     launch_finish(fp, pl.finish_smem, cs);
   }
   if ((e = launch_sweeps(pl, s, cs, 1)) != cudaSuccess) return e;
-  ReduceArgs rc{s->io_dev, s->st_dev, pl.ncl, pl.m, pl.p, 1, pl.m * pl.m, 0, 1};
+  ReduceArgs rc{s->io_dev, s->st_dev, pl.ncl, pl.m, pl.p, 1, pl.m * pl.m, 0, 1, 0, pl.n, pl.form};
   launch_reduce(pl.tcsize, rc, pl.nred, cs);
   FinishArgs fr{s->io_dev, s->st_dev, pl.ncl, pl.nred, pl.m * pl.m, pl.m, pl.form, kFinishRitz, 1, h, use_cond};
   launch_finish(fr, pl.finish_smem, cs);
@@ -441,9 +441,9 @@ static cudaError_t launch_body(const Plan& pl, Slot* s, cudaStream_t cs, cudaGra
   cudaError_t e = launch_sweeps(pl, s, cs);
   if (e != cudaSuccess) return e;
   const int gram_pairs = pl.full_gram ? pl.m * (pl.m + 1) / 2 : pl.m;
-  ReduceArgs ra{s->io_dev, s->st_dev, pl.ncl, pl.m, pl.p, pl.full_gram, gram_pairs, 0, 0};
+  ReduceArgs ra{s->io_dev, s->st_dev, pl.ncl, pl.m, pl.p, pl.full_gram, gram_pairs, 0, 0, 1, pl.n, pl.form};
   launch_reduce(pl.tcsize, ra, pl.nred, cs);
-  FinishArgs fa{s->io_dev, s->st_dev, pl.ncl, pl.nred, gram_pairs, pl.m, pl.form, kFinishIterate, 0, h, 1};
+  FinishArgs fa{s->io_dev, s->st_dev, pl.nred, pl.nred, gram_pairs, pl.m, pl.form, kFinishIterate, 0, h, 1};
   launch_finish(fa, pl.finish_smem, cs);
   return cudaGetLastError();
 }

@@ -65,14 +65,14 @@ static int static_setup(int dev, StaticPtrs** out) {
   return GPSPCA_OK;
 }
 
-// Sum of the cluster partials (fixed order): objective f and ||y||^2, then
+// Sum of the reduction blocks' partials (fixed order): objective f and ||y||^2, then
 // x_next = y / ||y|| (all zero when y = 0).  One block.
-__global__ void static_sweep_finish(const double* fpart, int ncl, const double* gpart, int nred, float* x_next,
-                                    int p, double* objective) {
+__global__ void static_sweep_finish(const double* fpart, const double* gpart, int nred, float* x_next, int p,
+                                    double* objective) {
   __shared__ double s_f, s_g;
   if (threadIdx.x == 0) {
     double f = 0.0, g = 0.0;
-    for (int c = 0; c < ncl; ++c) f += fpart[2 * c];
+    for (int b = 0; b < nred; ++b) f += fpart[2 * b];
     for (int b = 0; b < nred; ++b) g += gpart[b];
     s_f = f;
     s_g = g;
@@ -115,12 +115,12 @@ extern "C" int gpspca_sweep_static(const gpspca_matrix* A, gpspca_form form, dou
   Plan pl;
   if ((rc = make_plan(GPSPCA_F32, form, 1, A->p, A->n, A->ld, fast, sp->nsm, &pl))) return rc;
   const int p = pl.p, n = pl.n;
-  // scratch layout: ypart [ncl][p] | xcopy [p] | fpart [ncl][2] | gpart [nred]
+  // scratch layout: ypart [ncl][p] | xcopy [p] | fpart [nred][2] | gpart [nred]
   auto up = [](size_t v) { return (v + 255) / 256 * 256; };
   const size_t off_ypart = 0;
   const size_t off_x = up(off_ypart + sizeof(float) * static_cast<size_t>(pl.ncl) * p);
   const size_t off_f = up(off_x + sizeof(float) * static_cast<size_t>(p));
-  const size_t off_g = up(off_f + sizeof(double) * 2 * static_cast<size_t>(pl.ncl));
+  const size_t off_g = up(off_f + sizeof(double) * 2 * static_cast<size_t>(pl.nred));
   const size_t need = up(off_g + sizeof(double) * static_cast<size_t>(pl.nred));
   if (need > kStaticScratchBytes) {
     char msg[200];
@@ -175,9 +175,9 @@ extern "C" int gpspca_sweep_static(const gpspca_matrix* A, gpspca_form form, dou
     cudaGetLastError();
     return record_error(GPSPCA_ECUDA, "sweep launch failed");
   }
-  ReduceArgs ra{sp->io_reduce, sp->st, pl.ncl, 1, p, 0, 1, 0, 0};
+  ReduceArgs ra{sp->io_reduce, sp->st, pl.ncl, 1, p, 0, 1, 0, 0, 1, n, form};
   launch_reduce(4, ra, pl.nred, stream);
-  static_sweep_finish<<<1, 256, 0, stream>>>(reinterpret_cast<const double*>(sc + off_f), pl.ncl,
+  static_sweep_finish<<<1, 256, 0, stream>>>(reinterpret_cast<const double*>(sc + off_f),
                                               reinterpret_cast<const double*>(sc + off_g), pl.nred, x_next, p,
                                               objective);
   if (cudaGetLastError() != cudaSuccess) return record_error(GPSPCA_ECUDA, "reduction launch failed");

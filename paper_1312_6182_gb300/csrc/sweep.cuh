@@ -13,12 +13,13 @@
 //  * Per tile: per-thread partial dots -> warp reduce-scatter (31 shuffles
 //    for 32 values) -> CTA sum -> partial sums of the C CTAs of the cluster
 //    exchanged through distributed shared memory and added in rank order, so
-//    every CTA holds the same t.  The threshold runs on one thread per
-//    (column, component), the objective of Table 1 accumulates in double,
-//    then every thread applies g to its rows of the tile still in shared
-//    memory (the second use of the tile costs no HBM traffic).
-//  * Epilogue: each cluster writes its partial y (all p rows) and its
-//    objective partials; a separate deterministic reduction adds them.
+//    every CTA holds the same t.  The threshold runs on one lane per
+//    (column, component), then every thread applies g to its rows of the
+//    tile still in shared memory (the second use of the tile costs no HBM
+//    traffic).  The sweep stores t; the reduction forms the Table 1
+//    objective from it in double, off this kernel's critical path.
+//  * Epilogue: each cluster writes its partial y (all p rows); a separate
+//    deterministic reduction adds them.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -156,7 +157,7 @@ constexpr int kRingSlack = 33 * 4 * 4 * 8;  // 33 * NCHmax * VECmax * 8-byte ele
 
 // Shared-memory layout of the sweep kernel (host and device agree on it).
 struct SweepSmem {
-  int stage_bytes, bars, xbars, red, xrecv, wsm, gam, mu, facc, zacc, total;
+  int stage_bytes, bars, xbars, red, xrecv, wsm, total;
 };
 constexpr int kMaxCluster = 8;
 __host__ __device__ inline int align_up(int v, int a) { return (v + a - 1) / a * a; }
@@ -174,11 +175,6 @@ __host__ __device__ inline SweepSmem sweep_smem_layout(int W, int S, int ps, int
   L.red = o; o += 2 * nwarps * 32 * tcsize;          // warp partials, by tile parity
   L.xrecv = o; o += 2 * kMaxCluster * 32 * tcsize;   // partials pushed by cluster peers
   L.wsm = o; o += m * mg * tcsize;
-  o = align_up(o, 8);
-  L.gam = o; o += 8 * mg;
-  L.mu = o; o += 8 * mg;
-  L.facc = o; o += 8 * 32;
-  L.zacc = o; o += 8 * 32;
   L.total = align_up(o, 128);
   return L;
 }
@@ -258,10 +254,6 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH>::MAXT, 1) sweep_kernel(c
   TC* red = reinterpret_cast<TC*>(smem + L.red);
   TC* xrecv = reinterpret_cast<TC*>(smem + L.xrecv);
   TC* wsm = reinterpret_cast<TC*>(smem + L.wsm);
-  double* gam = reinterpret_cast<double*>(smem + L.gam);
-  double* muv = reinterpret_cast<double*>(smem + L.mu);
-  double* fsm = reinterpret_cast<double*>(smem + L.facc);
-  double* zsm = reinterpret_cast<double*>(smem + L.zacc);
   __shared__ TC gam_c[MG], mu_c[MG];
   __shared__ int act[MG];
   const int stage_elems = W * ps;
@@ -269,10 +261,8 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH>::MAXT, 1) sweep_kernel(c
   // ---- prologue: parameters, weights, barriers, first tiles
   if (tid < MG) {
     const bool v = tid < a.mg_valid && !sketch;
-    gam[tid] = v ? st->gamma[a.j0 + tid] : 0.0;
-    muv[tid] = v ? io->mu[a.j0 + tid] : 1.0;
-    gam_c[tid] = static_cast<TC>(gam[tid]);
-    mu_c[tid] = static_cast<TC>(muv[tid]);
+    gam_c[tid] = v ? static_cast<TC>(st->gamma[a.j0 + tid]) : TC(0);
+    mu_c[tid] = v ? static_cast<TC>(io->mu[a.j0 + tid]) : TC(1);
     act[tid] = (tid < a.mg_valid) ? st->active[a.j0 + tid] : 0;
   }
   for (int idx = tid; idx < m * MG; idx += nthr) {
@@ -355,7 +345,6 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH>::MAXT, 1) sweep_kernel(c
     }
   }
 
-  double facc = 0.0, zacc = 0.0;
   bool timed_out = false;
   TC* Tout = static_cast<TC*>(io->T);
   const float* cscale = io->col_scale;
@@ -438,14 +427,9 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH>::MAXT, 1) sweep_kernel(c
       t *= scl;
       g = grad_factor<TC>(form, t, gam_c[jq], mu_c[jq]) * scl;
     }
-    // the Table 1 objective in double and T (one warp, off the other warps' path)
-    if (warp == 0 && mine_valid && cr == 0 && !sketch) {
-      const double td = static_cast<double>(t);
-      const Thr th = threshold(form, td, gam[jq], muv[jq]);
-      if (act[jq]) Tout[static_cast<int64_t>(a.j0 + jq) * n + c0 + wq] = t;
-      facc += th.term;
-      zacc += th.zr * th.zr;
-    }
+    // T for the objective (formed in double by the reduction) and the loadings
+    if (warp == 0 && mine_valid && cr == 0 && !sketch && act[jq])
+      Tout[static_cast<int64_t>(a.j0 + jq) * n + c0 + wq] = t;
 
     // rank update y += g a over this thread's rows of the tile
 #pragma unroll
@@ -480,21 +464,6 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH>::MAXT, 1) sweep_kernel(c
         for (int v = 0; v < VEC; ++v)
           if (vmask & (1u << (c * VEC + v))) dst[(c * nthr + tid) * VEC + v] = y[c][v][j];
     }
-  }
-  __syncthreads();
-  if (tid < 32) {
-    fsm[tid] = facc;
-    zsm[tid] = zacc;
-  }
-  __syncthreads();
-  if (cr == 0 && tid < a.mg_valid && !sketch) {
-    double F = 0.0, Zs = 0.0;
-    for (int w = 0; w < WB; ++w) {
-      F += fsm[w * MG + tid];
-      Zs += zsm[w * MG + tid];
-    }
-    io->fpart[(static_cast<int64_t>(cl) * 2 + 0) * m + a.j0 + tid] = F;
-    io->fpart[(static_cast<int64_t>(cl) * 2 + 1) * m + a.j0 + tid] = Zs;
   }
   if (timed_out) atomicOr(&st->error, static_cast<int>(kErrTimeout));
   if (C > 1) cluster_sync_all();  // no CTA leaves while a peer may read its shared memory
