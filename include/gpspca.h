@@ -77,6 +77,11 @@ typedef enum { GPSPCA_DEVICE = 0, GPSPCA_HOST = 1 } gpspca_location;
 /* Flags for gpspca_solve / gpspca_submit. */
 #define GPSPCA_GAMMA_RELATIVE 1u  /* gamma[j] is relative: the device scales it to
                                      gamma[j]*max_i||a_i|| (L1) or (gamma[j]*max_i||a_i||)^2 (L0) */
+#define GPSPCA_EAGER 2u           /* launch the same kernels one by one with a host-driven loop
+                                     (one device->host read of the active count per sweep)
+                                     instead of the cached CUDA graph with its device-side WHILE
+                                     node: for profilers and debuggers that cannot follow
+                                     conditional graph nodes.  Results are identical. */
 
 /* Largest m (components, or gamma values of a path) one solve accepts. */
 #define GPSPCA_MAX_M 64
@@ -137,9 +142,11 @@ int gpspca_create(gpspca_ctx** ctx, int device, size_t hbm_budget_bytes, void* c
  *   x0      optional p x m starting iterate (same location as A; float, or
  *           double for F64); projected on the feasible set (columns
  *           normalised, or the polar factor for block forms).  NULL: the
- *           largest-norm column (single-unit) or the polar factor of the m
- *           largest-norm columns (block), ties to the lower index.
- *   flags   GPSPCA_GAMMA_RELATIVE or 0
+ *           largest-norm column (single-unit, ties to the lower index) or,
+ *           for block forms, the PCA start: a seeded Rademacher sketch of m
+ *           columns (SplitMix64, seed 0x5EED5EED5EED5EED), two projected
+ *           power steps with A A^T and a Rayleigh-Ritz rotation
+ *   flags   GPSPCA_GAMMA_RELATIVE | GPSPCA_EAGER, or 0
  *   out     result buffers
  * Returns GPSPCA_OK, GPSPCA_EDEGENERATE (outputs valid, see status), or an
  * error code (outputs undefined). */

@@ -28,6 +28,7 @@ OK, PENDING = 0, 1
 EINVAL, ENOMEM, ENONFINITE, ETIMEDOUT, EDEGENERATE, ECUDA, ENOTFOUND = -1, -2, -3, -4, -5, -6, -7
 CONVERGED, MAXIT, ZERO, DEGENERATE = 0, 1, 2, 3
 GAMMA_RELATIVE = 1
+EAGER = 2  # kernels launched one by one, host-driven loop (for profilers)
 MAX_M = 64
 
 ERROR_NAMES = {
@@ -240,8 +241,9 @@ class Context:
 
     def solve(self, At, form: str, gamma, mu=None, tol: float = 1e-6, maxit: int = 1000, x0=None,
               gamma_relative: bool = False, p: Optional[int] = None, col_scale=None,
-              out: Optional[Result] = None, allow_degenerate: bool = True) -> Result:
-        """One synchronous solve.  gamma: m values; mu: block weights."""
+              out: Optional[Result] = None, allow_degenerate: bool = True, eager: bool = False) -> Result:
+        """One synchronous solve.  gamma: m values; mu: block weights.  eager: launch
+        the kernels one by one with a host-driven loop instead of the CUDA graph."""
         import torch
 
         gamma = [float(g) for g in (gamma if hasattr(gamma, "__len__") else [gamma])]
@@ -254,7 +256,8 @@ class Context:
         self._sync_torch(At, x0, out.X)
         rc = self.lib.gpspca_solve(self.ptr, ctypes.byref(M), FORMS[form], _darr(gamma, m), m, _darr(mu, m),
                                    float(tol), int(maxit), x0.data_ptr() if x0 is not None else None,
-                                   GAMMA_RELATIVE if gamma_relative else 0, ctypes.byref(o))
+                                   (GAMMA_RELATIVE if gamma_relative else 0) | (EAGER if eager else 0),
+                                   ctypes.byref(o))
         allow = (OK, EDEGENERATE) if allow_degenerate else (OK,)
         _check(rc, allow)
         out.rc = rc

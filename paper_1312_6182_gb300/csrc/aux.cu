@@ -24,6 +24,18 @@ __device__ __forceinline__ int stop_rule(int k, double f, double f_prev, double 
   return -1;
 }
 
+// 1/sqrt(x) for x > 0 in double: float estimate, two Newton steps (each
+// squares the relative error: 1e-7 -> 1e-14 -> 1e-16).  Keeps the slow
+// double-precision division and square root off the serial paths of the
+// one-CTA kernels.
+__device__ __forceinline__ double rsqrt_refined(double x) {
+  if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x);  // outside float's comfortable range
+  double r = static_cast<double>(rsqrtf(static_cast<float>(x)));
+  r = r * (1.5 - 0.5 * x * r * r);
+  r = r * (1.5 - 0.5 * x * r * r);
+  return r;
+}
+
 // dst[q] = sum_{b < nb} src[b*stride + q] for q < nq, added in a fixed order
 // (per q: strided over tpp lanes, then a shuffle tree), so the result does not
 // depend on scheduling.  All threads of the block must call it.
@@ -89,11 +101,23 @@ __device__ void jacobi_eig(double* G, double* V, int mm, int* rp, int* rq, doubl
         const double apq = G[pp * mm + qq];
         double c = 1.0, s = 0.0;
         if (apq != 0.0) {
+          // tan(theta) of the rotation that zeroes G_pq, in float (its
+          // transcendentals are cheap; an angle good to 1e-7 still cuts G_pq
+          // by 1e-7), then cos/sin refined in double so the rotation is
+          // orthogonal to double rounding
           const double app = G[pp * mm + pp], aqq = G[qq * mm + qq];
-          const double tau = (aqq - app) / (2.0 * apq);
-          const double t = (tau >= 0.0) ? 1.0 / (tau + hypot(1.0, tau)) : -1.0 / (-tau + hypot(1.0, tau));
-          c = 1.0 / sqrt(1.0 + t * t);
-          s = t * c;
+          const double num = aqq - app, den = 2.0 * apq;
+          float tau;
+          if (fabs(den) > 1e-30 && fabs(den) < 1e30 && fabs(num) < 1e30) {
+            tau = static_cast<float>(num) / static_cast<float>(den);  // may round to +-inf: no rotation
+          } else {
+            tau = static_cast<float>(fmax(fmin(num / den, 1e30), -1e30));
+          }
+          const float at = fabsf(tau);
+          float t = (at > 1e18f) ? 0.5f / at : 1.0f / (at + sqrtf(1.0f + at * at));
+          if (tau < 0.0f) t = -t;
+          c = rsqrt_refined(1.0 + static_cast<double>(t) * t);
+          s = static_cast<double>(t) * c;
         }
         rp[k] = pp; rq[k] = qq; rc[k] = c; rs[k] = s;
       }
@@ -124,8 +148,12 @@ __device__ void jacobi_eig(double* G, double* V, int mm, int* rp, int* rq, doubl
 }
 
 // Polar weights W = (Y^T Y)^{-1/2} from the Gram matrix (packed j <= l).
+// With Vwarm (the eigenvectors of the previous iteration's Gram matrix) the
+// Jacobi sweeps run on Vwarm^T G Vwarm, which is nearly diagonal near
+// convergence; the eigenvectors found are written back to Vout.
 // Returns false (degenerate) if lambda_min <= 1e-12 lambda_max.
-__device__ bool polar_weights(const double* gsum, int m, double* W, double* sm, double* scratch) {
+__device__ bool polar_weights(const double* gsum, int m, double* W, double* sm, double* scratch,
+                              const double* Vwarm, double* Vout) {
   const int mm = m + (m & 1);
   double* G = sm;
   double* V = sm + mm * mm;
@@ -134,22 +162,57 @@ __device__ bool polar_weights(const double* gsum, int m, double* W, double* sm, 
   double* rc = reinterpret_cast<double*>(rq + 32);
   double* rs = rc + 32;
   double* lam = rs + 32;
+  double* Gf = lam + kMaxM;  // full G (m x m), for the warm start
   __shared__ int deg;
   const int tid = threadIdx.x, nthr = blockDim.x;
-  for (int idx = tid; idx < mm * mm; idx += nthr) {
-    const int r = idx / mm, c = idx % mm;
-    double v = 0.0;
-    if (r < m && c < m) {
-      const int j = min(r, c), l = max(r, c);
-      const int q = j * m - j * (j - 1) / 2 + (l - j);  // packed upper-triangle index
-      v = gsum[q];
+  for (int idx = tid; idx < m * m; idx += nthr) {
+    const int r = idx / m, c = idx % m;
+    const int j = min(r, c), l = max(r, c);
+    Gf[idx] = gsum[j * m - j * (j - 1) / 2 + (l - j)];  // packed upper-triangle index
+  }
+  __syncthreads();
+  if (Vwarm) {  // G <- Vwarm^T G Vwarm, via V as temporary for G Vwarm
+    for (int idx = tid; idx < m * m; idx += nthr) {
+      const int r = idx / m, c = idx % m;
+      double t = 0.0;
+      for (int k = 0; k < m; ++k) t += Gf[r * m + k] * Vwarm[k * m + c];
+      V[idx] = t;
     }
-    G[idx] = v;
+    __syncthreads();
+    for (int idx = tid; idx < mm * mm; idx += nthr) {
+      const int r = idx / mm, c = idx % mm;
+      double t = 0.0;
+      if (r < m && c < m)
+        for (int k = 0; k < m; ++k) t += Vwarm[k * m + r] * V[k * m + c];
+      G[idx] = t;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < mm * mm; idx += nthr) {  // exact symmetry
+      const int r = idx / mm, c = idx % mm;
+      if (r < c) G[c * mm + r] = G[idx];
+    }
+  } else {
+    for (int idx = tid; idx < mm * mm; idx += nthr) {
+      const int r = idx / mm, c = idx % mm;
+      G[idx] = (r < m && c < m) ? Gf[r * m + c] : 0.0;
+    }
   }
   __syncthreads();
   jacobi_eig(G, V, mm, rp, rq, rc, rs, scratch);
   if (tid < m) lam[tid] = G[tid * mm + tid];
   __syncthreads();
+  // eigenvectors of the Gram matrix: Vwarm * V (or V), kept in Gf
+  for (int idx = tid; idx < m * m; idx += nthr) {
+    const int r = idx / m, c = idx % m;
+    double t;
+    if (Vwarm) {
+      t = 0.0;
+      for (int k = 0; k < m; ++k) t += Vwarm[r * m + k] * V[k * mm + c];
+    } else {
+      t = V[r * mm + c];
+    }
+    Gf[idx] = t;
+  }
   if (tid == 0) {
     double lmax = 0.0, lmin = 1e308;
     for (int i = 0; i < m; ++i) {
@@ -163,8 +226,9 @@ __device__ bool polar_weights(const double* gsum, int m, double* W, double* sm, 
   for (int idx = tid; idx < m * m; idx += nthr) {
     const int a = idx / m, b = idx % m;
     double s = 0.0;
-    for (int i = 0; i < m; ++i) s += V[a * mm + i] * V[b * mm + i] / sqrt(lam[i]);
+    for (int i = 0; i < m; ++i) s += Gf[a * m + i] * Gf[b * m + i] * rsqrt_refined(lam[i]);
     W[a * m + b] = s;
+    if (Vout) Vout[idx] = Gf[idx];
   }
   __syncthreads();
   return true;
@@ -180,6 +244,7 @@ __global__ void reset_state_kernel(const IO* io, State* st, int m, int form) {
     st->error = 0;
     st->any_degenerate = 0;
     st->cmax = 0.0;
+    st->has_v = 0;
   }
   if (j < kMaxM) {
     const bool v = j < m;
@@ -292,11 +357,23 @@ template <typename TA>
 __device__ double exact_colnorm_warp(const IO* io, int64_t ld, int p, int i) {
   const TA* col = static_cast<const TA*>(io->A) + static_cast<int64_t>(i) * ld;
   const int lane = threadIdx.x & 31;
-  double s = 0.0;
-  for (int r = lane; r < p; r += 32) {
-    const double v = static_cast<double>(to_tc<TA>(col[r]));
-    s += v * v;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;  // independent chains
+  int r = lane;
+  for (; r + 96 < p; r += 128) {
+    const double v0 = static_cast<double>(to_tc<TA>(col[r]));
+    const double v1 = static_cast<double>(to_tc<TA>(col[r + 32]));
+    const double v2 = static_cast<double>(to_tc<TA>(col[r + 64]));
+    const double v3 = static_cast<double>(to_tc<TA>(col[r + 96]));
+    s0 += v0 * v0;
+    s1 += v1 * v1;
+    s2 += v2 * v2;
+    s3 += v3 * v3;
   }
+  for (; r < p; r += 32) {
+    const double v = static_cast<double>(to_tc<TA>(col[r]));
+    s0 += v * v;
+  }
+  double s = (s0 + s1) + (s2 + s3);
   for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
   double c = sqrt(s);
   if (sizeof(TA) == 1) c *= static_cast<double>(io->col_scale[i]);
@@ -353,7 +430,9 @@ __global__ void __launch_bounds__(kStartThreads) select_start_kernel(const Start
     return;
   }
   const bool block = a.form >= 2;
-  const int mt = (block && !io->has_x0) ? a.m : 1;  // how many leading columns are needed
+  // only the largest column is needed: it is the single-unit start, and
+  // max_i ||a_i|| scales a relative gamma (block forms start from the sketch)
+  const int mt = 1;
   // 1. the mt-th largest approximate norm, by mt rounds of arg-max below the previous pick
   double pv = 1e308;
   int pi = -1;
@@ -416,7 +495,7 @@ __global__ void __launch_bounds__(kStartThreads) select_start_kernel(const Start
         const double g = io->gamma_in[j] * cmax;
         st->gamma[j] = l1 ? g : g * g;
       }
-      st->start_cols[j] = io->has_x0 ? -1 : order[block ? j : 0];
+      st->start_cols[j] = (io->has_x0 || block) ? -1 : order[0];
     }
     if (!(cmax > 0.0)) {  // A == 0
       for (int j = 0; j < a.m; ++j) {
@@ -468,11 +547,20 @@ __global__ void __launch_bounds__(kReduceRows* kReduceGroups) reduce_kernel(cons
   TC* Y = static_cast<TC*>(a.io->Y);
   const int m = a.m, p = a.p;
   for (int j = 0; j < m; ++j) {
-    double s = 0.0;
-    if (row < p)
-      for (int sp = g; sp < a.nsplit; sp += kReduceGroups)
-        s += static_cast<double>(yp[(static_cast<int64_t>(sp) * m + j) * p + row]);
-    part[g][rl] = s;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;  // independent chains, fixed order
+    if (row < p) {
+      const int64_t stride = static_cast<int64_t>(m) * p;
+      const TC* src = yp + static_cast<int64_t>(j) * p + row;
+      int sp = g;
+      for (; sp + 3 * kReduceGroups < a.nsplit; sp += 4 * kReduceGroups) {
+        s0 += static_cast<double>(src[sp * stride]);
+        s1 += static_cast<double>(src[(sp + kReduceGroups) * stride]);
+        s2 += static_cast<double>(src[(sp + 2 * kReduceGroups) * stride]);
+        s3 += static_cast<double>(src[(sp + 3 * kReduceGroups) * stride]);
+      }
+      for (; sp < a.nsplit; sp += kReduceGroups) s0 += static_cast<double>(src[sp * stride]);
+    }
+    part[g][rl] = (s0 + s1) + (s2 + s3);
     __syncthreads();
     if (g == 0) {
       double t = 0.0;
@@ -630,8 +718,8 @@ __global__ void __launch_bounds__(kFinishThreads) finish_kernel(const FinishArgs
   __shared__ int s_stop;
   double* gsum = fsm;                    // npairs
   double* fz = gsum + a.npairs;          // 2m
-  double* Wt = fz + 2 * kMaxM;           // m*m
-  double* jac = Wt + kMaxM * kMaxM;      // Jacobi workspace
+  double* Wt = fz + 2 * m;               // m*m
+  double* jac = Wt + m * m;              // Jacobi workspace (finish_smem_doubles)
   const bool proceed = st->n_active > 0;
   if (proceed) {
     sum_partials(io->gpart, a.nblk, a.npairs, a.npairs, gsum);
@@ -643,9 +731,10 @@ __global__ void __launch_bounds__(kFinishThreads) finish_kernel(const FinishArgs
       for (int idx = 0; idx < m * m; ++idx) st->W[idx] = Wt[idx];
   } else if (proceed && a.mode == kFinishPolar) {
     if (block) {
-      const bool ok = polar_weights(gsum, m, Wt, jac, scratch);
+      const bool ok = polar_weights(gsum, m, Wt, jac, scratch, nullptr, st->V);
       if (tid == 0) {
         if (ok) {
+          st->has_v = 1;
           for (int idx = 0; idx < m * m; ++idx) st->W[idx] = Wt[idx];
         } else {
           for (int j = 0; j < m; ++j) { st->status[j] = GPSPCA_DEGENERATE; st->active[j] = 0; }
@@ -659,7 +748,7 @@ __global__ void __launch_bounds__(kFinishThreads) finish_kernel(const FinishArgs
         for (int l = 0; l < m; ++l) st->W[l * m + j] = 0.0;
         const double d = gsum[j];
         if (d > 0.0) {
-          st->W[j * m + j] = 1.0 / sqrt(d);
+          st->W[j * m + j] = rsqrt_refined(d);
           ++na;
         } else {
           st->status[j] = GPSPCA_DEGENERATE;
@@ -688,7 +777,7 @@ __global__ void __launch_bounds__(kFinishThreads) finish_kernel(const FinishArgs
       __syncthreads();
       bool deg = false;
       if (s_stop < 0) {
-        deg = !polar_weights(gsum, m, Wt, jac, scratch);
+        deg = !polar_weights(gsum, m, Wt, jac, scratch, st->has_v ? st->V : nullptr, st->V);
       }
       if (tid == 0) {
         if (s_stop >= 0 || deg) {
@@ -722,7 +811,7 @@ __global__ void __launch_bounds__(kFinishThreads) finish_kernel(const FinishArgs
         if (s < 0) {
           const double d = gsum[j];
           if (d > 0.0) {
-            st->W[j * m + j] = 1.0 / sqrt(d);
+            st->W[j * m + j] = rsqrt_refined(d);
             st->f_prev[j] = f;
             ++na;
             continue;

@@ -55,6 +55,13 @@ constexpr int kFinishThreads = 256;
 constexpr int kStartThreads = 1024;
 constexpr int kMaxCandidates = 256;
 
+// Shared memory (in doubles) of finish_kernel for m components and npairs
+// Gram entries: partial sums, objective parts, weights, Jacobi workspace.
+inline int finish_smem_doubles(int m, int npairs) {
+  const int mm = m + (m & 1);
+  return npairs + 2 * m + m * m + 2 * mm * mm + 64 + kMaxM + m * m + 32;
+}
+
 // Host-side launchers (each kernel is launched from the file that defines it).
 void launch_reset(const IO* io, State* st, int m, int form, cudaStream_t s);
 void launch_colnorm(int dtype, const IO* io, State* st, int64_t ld, int p, int n, int fast, cudaStream_t s);

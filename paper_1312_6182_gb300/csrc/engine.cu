@@ -233,7 +233,7 @@ int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fa
   pl.nred = static_cast<int>((p + kReduceRows - 1) / kReduceRows);
   pl.full_gram = form >= 2 ? 1 : 0;
   pl.npairs = pl.full_gram ? m * m : m;  // gpart capacity: the Ritz step's cross Gram is m x m
-  pl.finish_smem = static_cast<int>(sizeof(double)) * (pl.npairs + 2 * kMaxM + kMaxM * kMaxM + 2 * kMaxM * kMaxM + 256);
+  pl.finish_smem = static_cast<int>(sizeof(double)) * finish_smem_doubles(m, pl.npairs);
   pl.ws_cnorm = sizeof(double) * n;
   pl.ws_P = static_cast<size_t>(d.tcsize) * m * p;
   pl.ws_ypart = static_cast<size_t>(d.tcsize) * ncl * m * p;
@@ -437,13 +437,14 @@ static cudaError_t launch_sweeps(const Plan& pl, Slot* s, cudaStream_t cs, int s
   return cudaSuccess;
 }
 
-static cudaError_t launch_body(const Plan& pl, Slot* s, cudaStream_t cs, cudaGraphConditionalHandle h) {
+static cudaError_t launch_body(const Plan& pl, Slot* s, cudaStream_t cs, cudaGraphConditionalHandle h,
+                               int use_cond = 1) {
   cudaError_t e = launch_sweeps(pl, s, cs);
   if (e != cudaSuccess) return e;
   const int gram_pairs = pl.full_gram ? pl.m * (pl.m + 1) / 2 : pl.m;
   ReduceArgs ra{s->io_dev, s->st_dev, pl.ncl, pl.m, pl.p, pl.full_gram, gram_pairs, 0, 0, 1, pl.n, pl.form};
   launch_reduce(pl.tcsize, ra, pl.nred, cs);
-  FinishArgs fa{s->io_dev, s->st_dev, pl.nred, pl.nred, gram_pairs, pl.m, pl.form, kFinishIterate, 0, h, 1};
+  FinishArgs fa{s->io_dev, s->st_dev, pl.nred, pl.nred, gram_pairs, pl.m, pl.form, kFinishIterate, 0, h, use_cond};
   launch_finish(fa, pl.finish_smem, cs);
   return cudaGetLastError();
 }
@@ -688,9 +689,23 @@ static int launch_solve(Slot* s, const Request& r, int nsm, bool* empty) {
   const DInfo d = dinfo(r.A.dtype);
   const int64_t p = r.A.p, n = r.A.n;
   const int m = r.m;
-  cudaGraphExec_t exec = nullptr;
-  if ((rc = get_graph(pl, s, &exec))) return rc;
-  GP_CUDA(cudaGraphLaunch(exec, s->stream));
+  if (r.flags & GPSPCA_EAGER) {
+    // the graph's kernels, launched one by one; the host reads the active
+    // count after each finish step in place of the WHILE node
+    GP_CUDA(launch_prologue(pl, s, s->stream, 0, pl.pca != 0, 0));
+    for (int k = 0; k <= r.maxit; ++k) {
+      GP_CUDA(cudaMemcpyAsync(&s->st_host->n_active, &s->st_dev->n_active, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                              s->stream));
+      GP_CUDA(cudaStreamSynchronize(s->stream));
+      if (s->st_host->n_active <= 0) break;
+      GP_CUDA(launch_body(pl, s, s->stream, 0, 0));
+    }
+    GP_CUDA(launch_epilogue(pl, s, s->stream));
+  } else {
+    cudaGraphExec_t exec = nullptr;
+    if ((rc = get_graph(pl, s, &exec))) return rc;
+    GP_CUDA(cudaGraphLaunch(exec, s->stream));
+  }
   if (r.out.location == GPSPCA_HOST) {
     const size_t nw = (n + 31) / 32;
     GP_CUDA(cudaMemcpyAsync(r.out.X, s->s_X.p, static_cast<size_t>(d.tcsize) * p * m, cudaMemcpyDeviceToHost, s->stream));
@@ -724,6 +739,7 @@ static int request_from(Request* r, const gpspca_matrix* A, gpspca_form form, co
                         const double* mu, double tol, int32_t maxit, const void* x0, uint32_t flags,
                         gpspca_out* out) {
   if (!A || !out || !gamma) return fail(GPSPCA_EINVAL, "A, gamma and out must not be NULL");
+  if (flags & ~(GPSPCA_GAMMA_RELATIVE | GPSPCA_EAGER)) return fail(GPSPCA_EINVAL, "unknown flag bits 0x%x", flags);
   if (m < 1 || m > kMaxM) return fail(GPSPCA_EINVAL, "m = %d outside [1, %d]", m, kMaxM);
   r->A = *A;
   r->form = form;

@@ -58,6 +58,8 @@ struct State {
   double f[kMaxM];
   double znorm2[kMaxM];  // squared norm of the unnormalised loading column of the last sweep
   double W[kMaxM * kMaxM];  // projection weights: X_k = Y_{k-1} W, [l * m + j]
+  double V[kMaxM * kMaxM];  // eigenvectors of the last Gram matrix (warm start of the next eigensolve)
+  int32_t has_v;
   double cmax;              // max_i ||a_i||
   int32_t start_cols[kMaxM];
 };

@@ -69,12 +69,11 @@ static int static_setup(int dev, StaticPtrs** out) {
 // x_next = y / ||y|| (all zero when y = 0).  One block.
 __global__ void static_sweep_finish(const double* fpart, const double* gpart, int nred, float* x_next, int p,
                                     double* objective) {
-  __shared__ double s_f, s_g;
+  __shared__ double s_g;
   if (threadIdx.x == 0) {
     double f = 0.0, g = 0.0;
     for (int b = 0; b < nred; ++b) f += fpart[2 * b];
     for (int b = 0; b < nred; ++b) g += gpart[b];
-    s_f = f;
     s_g = g;
     *objective = f;
   }

@@ -192,13 +192,16 @@ struct SweepCfg {
   static constexpr int R = NCH * VEC;
   static constexpr int KB = sweep_kb(MG);
   static constexpr int WB = KB / MG;  // most columns one tile can hold
-  static constexpr int REGS = static_cast<int>(sizeof(TC) / 4) * (2 * R * MG + KB) + 72;
+  // registers per thread: x and y tiles, the reduction slots, and a fixed
+  // part (addresses, loop state, loads in flight) measured with -Xptxas -v
+  static constexpr int REGS = static_cast<int>(sizeof(TC) / 4) * (2 * R * MG + KB + (MG == 1 ? 64 : (MG == 2 ? 60 : 40)));
   // register arrays of x and y beyond this spill; such variants are not built
   static constexpr bool kBuilt = static_cast<int>(sizeof(TC) / 4) * 2 * R * MG <= 160;
-  static constexpr int MAXT_RAW = 65536 / REGS;
-  // each of the 4 SM sub-partitions holds a quarter of the CTA's warps, so
-  // the thread bound is rounded down to a multiple of 4 warps
-  static constexpr int MAXT = MAXT_RAW >= 1024 ? 1024 : (MAXT_RAW < 128 ? 128 : (MAXT_RAW / 128) * 128);
+  // each of the 4 SM sub-partitions holds a quarter of the CTA's warps in its
+  // own 16K-register file: whole warps per sub-partition, times four
+  static constexpr int WARPS_PER_SMSP = 16384 / (32 * REGS);
+  static constexpr int MAXT_RAW = WARPS_PER_SMSP * 4 * 32;
+  static constexpr int MAXT = MAXT_RAW >= 1024 ? 1024 : (MAXT_RAW < 128 ? 128 : MAXT_RAW);
 };
 
 template <typename TA, int MG, int NCH>

@@ -255,6 +255,20 @@ def test_deterministic(ctx):
     assert torch.equal(a.Z, b.Z) and torch.equal(a.X, b.X) and torch.equal(a.objective, b.objective)
 
 
+@pytest.mark.parametrize("form", ["SL1", "BL0"])
+def test_eager_launches_equal_graph(ctx, form):
+    """The host-driven launch mode (for profilers) runs the same kernels: bit-identical results."""
+    At = synth.planted_spike(1500, 5000, 3, [30.0, 15.0, 10.0], support_frac=0.03, seed=11, dtype=np.float32)
+    dA = torch.from_numpy(At).cuda()
+    m = 1 if form == "SL1" else 3
+    gam = list(_gammas(At.astype(np.float64).T, form, [0.04] * m))
+    mu = None if m == 1 else [1.0, 0.8, 0.6]
+    a = ctx.solve(dA, form, gam, mu=mu)
+    b = ctx.solve(dA, form, gam, mu=mu, eager=True)
+    for k in ("X", "Z", "support", "objective", "iters", "status"):
+        assert torch.equal(getattr(a, k), getattr(b, k)), k
+
+
 # ---------------------------------------------------------------- edge cases
 
 def test_tiny_shapes(ctx):
