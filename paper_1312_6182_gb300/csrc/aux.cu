@@ -2,6 +2,7 @@
 #include <algorithm>
 
 #include "aux.cuh"
+#include "smalleig.cuh"
 
 namespace gpspca {
 
@@ -37,201 +38,47 @@ __device__ __forceinline__ double rsqrt_refined(double x) {
 }
 
 // dst[q] = sum_{b < nb} src[b*stride + q] for q < nq, added in a fixed order
-// (per q: strided over tpp lanes, then a shuffle tree), so the result does not
-// depend on scheduling.  All threads of the block must call it.
-__device__ void sum_partials(const double* __restrict__ src, int nb, int stride, int nq, double* dst) {
+// (per q: strided over tpp lanes with the loads of four partials in flight,
+// then a shuffle tree), so the result does not depend on scheduling.  dd
+// partials are summed in double-float, double partials in double; dst is
+// written as double.  All threads of the block must call it.
+__device__ __forceinline__ dd sp_zero(const dd*) { return dd{0.0f, 0.0f}; }
+__device__ __forceinline__ double sp_zero(const double*) { return 0.0; }
+__device__ __forceinline__ dd sp_add(dd a, dd b) { return dd_add(a, b); }
+__device__ __forceinline__ double sp_add(double a, double b) { return a + b; }
+__device__ __forceinline__ double sp_out(dd a) { return dd_to_double(a); }
+__device__ __forceinline__ double sp_out(double a) { return a; }
+__device__ __forceinline__ dd sp_shfl(dd v, int off, int w) {
+  return dd{__shfl_down_sync(0xffffffffu, v.hi, off, w), __shfl_down_sync(0xffffffffu, v.lo, off, w)};
+}
+__device__ __forceinline__ double sp_shfl(double v, int off, int w) { return __shfl_down_sync(0xffffffffu, v, off, w); }
+
+template <typename P>
+__device__ void sum_partials(const P* __restrict__ src, int nb, int stride, int nq, double* dst) {
   int tpp = 32;
   while (tpp > 1 && tpp * nq > static_cast<int>(blockDim.x)) tpp >>= 1;
   const int groups = blockDim.x / tpp;
   const int sub = threadIdx.x % tpp;
   for (int q0 = 0; q0 < nq; q0 += groups) {
     const int q = q0 + static_cast<int>(threadIdx.x) / tpp;
-    double s = 0.0;
-    if (q < nq)
-      for (int b = sub; b < nb; b += tpp) s += src[static_cast<int64_t>(b) * stride + q];
-    for (int off = tpp / 2; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off, tpp);
-    if (q < nq && sub == 0) dst[q] = s;
-  }
-  __syncthreads();
-}
-
-__device__ double block_sum(double v, double* scratch) {
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) scratch[warp] = v;
-  __syncthreads();
-  double t = 0.0;
-  if (threadIdx.x == 0) {
-    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) t += scratch[w];
-    scratch[32] = t;
-  }
-  __syncthreads();
-  t = scratch[32];
-  __syncthreads();
-  return t;
-}
-
-// Cyclic Jacobi eigensolver for a symmetric mm x mm matrix G (mm even) in
-// shared memory, FP64.  Each round applies mm/2 disjoint rotations chosen by
-// the round-robin (tournament) ordering, rows then columns, accumulating the
-// eigenvectors in V.  On return diag(G) holds the eigenvalues.
-__device__ void jacobi_eig(double* G, double* V, int mm, int* rp, int* rq, double* rc, double* rs,
-                           double* scratch) {
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  for (int idx = tid; idx < mm * mm; idx += nthr) V[idx] = (idx / mm == idx % mm) ? 1.0 : 0.0;
-  __syncthreads();
-  const int half = mm / 2;
-  for (int sweep = 0; sweep < 40; ++sweep) {
-    double off = 0.0, dg = 0.0;
-    for (int idx = tid; idx < mm * mm; idx += nthr) {
-      const int r = idx / mm, c = idx % mm;
-      const double g = G[idx];
-      if (r < c) off += g * g;
-      if (r == c) dg += g * g;
-    }
-    off = block_sum(off, scratch);
-    dg = block_sum(dg, scratch);
-    if (!(off > 1e-32 * dg)) break;  // relative off-diagonal size below ~1e-16
-    for (int round = 0; round < mm - 1; ++round) {
-      if (tid < half) {
-        const int k = tid;
-        const int a = (k == 0) ? 0 : ((k - 1 + round) % (mm - 1)) + 1;
-        const int b = ((mm - 2 - k + round) % (mm - 1)) + 1;
-        const int pp = min(a, b), qq = max(a, b);
-        const double apq = G[pp * mm + qq];
-        double c = 1.0, s = 0.0;
-        if (apq != 0.0) {
-          // tan(theta) of the rotation that zeroes G_pq, in float (its
-          // transcendentals are cheap; an angle good to 1e-7 still cuts G_pq
-          // by 1e-7), then cos/sin refined in double so the rotation is
-          // orthogonal to double rounding
-          const double app = G[pp * mm + pp], aqq = G[qq * mm + qq];
-          const double num = aqq - app, den = 2.0 * apq;
-          float tau;
-          if (fabs(den) > 1e-30 && fabs(den) < 1e30 && fabs(num) < 1e30) {
-            tau = static_cast<float>(num) / static_cast<float>(den);  // may round to +-inf: no rotation
-          } else {
-            tau = static_cast<float>(fmax(fmin(num / den, 1e30), -1e30));
-          }
-          const float at = fabsf(tau);
-          float t = (at > 1e18f) ? 0.5f / at : 1.0f / (at + sqrtf(1.0f + at * at));
-          if (tau < 0.0f) t = -t;
-          c = rsqrt_refined(1.0 + static_cast<double>(t) * t);
-          s = static_cast<double>(t) * c;
-        }
-        rp[k] = pp; rq[k] = qq; rc[k] = c; rs[k] = s;
+    P s0 = sp_zero(src), s1 = sp_zero(src);
+    if (q < nq) {
+      int b = sub;
+      for (; b + 3 * tpp < nb; b += 4 * tpp) {
+        const P v0 = src[static_cast<int64_t>(b) * stride + q];
+        const P v1 = src[static_cast<int64_t>(b + tpp) * stride + q];
+        const P v2 = src[static_cast<int64_t>(b + 2 * tpp) * stride + q];
+        const P v3 = src[static_cast<int64_t>(b + 3 * tpp) * stride + q];
+        s0 = sp_add(s0, sp_add(v0, v2));
+        s1 = sp_add(s1, sp_add(v1, v3));
       }
-      __syncthreads();
-      for (int idx = tid; idx < half * mm; idx += nthr) {  // rows: G <- J^T G
-        const int k = idx / mm, l = idx % mm;
-        const int pp = rp[k], qq = rq[k];
-        const double c = rc[k], s = rs[k];
-        const double gp = G[pp * mm + l], gq = G[qq * mm + l];
-        G[pp * mm + l] = c * gp - s * gq;
-        G[qq * mm + l] = s * gp + c * gq;
-      }
-      __syncthreads();
-      for (int idx = tid; idx < half * mm; idx += nthr) {  // columns: G <- G J, V <- V J
-        const int k = idx / mm, l = idx % mm;
-        const int pp = rp[k], qq = rq[k];
-        const double c = rc[k], s = rs[k];
-        const double gp = G[l * mm + pp], gq = G[l * mm + qq];
-        G[l * mm + pp] = c * gp - s * gq;
-        G[l * mm + qq] = s * gp + c * gq;
-        const double vp = V[l * mm + pp], vq = V[l * mm + qq];
-        V[l * mm + pp] = c * vp - s * vq;
-        V[l * mm + qq] = s * vp + c * vq;
-      }
-      __syncthreads();
+      for (; b < nb; b += tpp) s0 = sp_add(s0, src[static_cast<int64_t>(b) * stride + q]);
     }
-  }
-}
-
-// Polar weights W = (Y^T Y)^{-1/2} from the Gram matrix (packed j <= l).
-// With Vwarm (the eigenvectors of the previous iteration's Gram matrix) the
-// Jacobi sweeps run on Vwarm^T G Vwarm, which is nearly diagonal near
-// convergence; the eigenvectors found are written back to Vout.
-// Returns false (degenerate) if lambda_min <= 1e-12 lambda_max.
-__device__ bool polar_weights(const double* gsum, int m, double* W, double* sm, double* scratch,
-                              const double* Vwarm, double* Vout) {
-  const int mm = m + (m & 1);
-  double* G = sm;
-  double* V = sm + mm * mm;
-  int* rp = reinterpret_cast<int*>(V + mm * mm);
-  int* rq = rp + 32;
-  double* rc = reinterpret_cast<double*>(rq + 32);
-  double* rs = rc + 32;
-  double* lam = rs + 32;
-  double* Gf = lam + kMaxM;  // full G (m x m), for the warm start
-  __shared__ int deg;
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  for (int idx = tid; idx < m * m; idx += nthr) {
-    const int r = idx / m, c = idx % m;
-    const int j = min(r, c), l = max(r, c);
-    Gf[idx] = gsum[j * m - j * (j - 1) / 2 + (l - j)];  // packed upper-triangle index
+    P s = sp_add(s0, s1);
+    for (int off = tpp / 2; off > 0; off >>= 1) s = sp_add(s, sp_shfl(s, off, tpp));
+    if (q < nq && sub == 0) dst[q] = sp_out(s);
   }
   __syncthreads();
-  if (Vwarm) {  // G <- Vwarm^T G Vwarm, via V as temporary for G Vwarm
-    for (int idx = tid; idx < m * m; idx += nthr) {
-      const int r = idx / m, c = idx % m;
-      double t = 0.0;
-      for (int k = 0; k < m; ++k) t += Gf[r * m + k] * Vwarm[k * m + c];
-      V[idx] = t;
-    }
-    __syncthreads();
-    for (int idx = tid; idx < mm * mm; idx += nthr) {
-      const int r = idx / mm, c = idx % mm;
-      double t = 0.0;
-      if (r < m && c < m)
-        for (int k = 0; k < m; ++k) t += Vwarm[k * m + r] * V[k * m + c];
-      G[idx] = t;
-    }
-    __syncthreads();
-    for (int idx = tid; idx < mm * mm; idx += nthr) {  // exact symmetry
-      const int r = idx / mm, c = idx % mm;
-      if (r < c) G[c * mm + r] = G[idx];
-    }
-  } else {
-    for (int idx = tid; idx < mm * mm; idx += nthr) {
-      const int r = idx / mm, c = idx % mm;
-      G[idx] = (r < m && c < m) ? Gf[r * m + c] : 0.0;
-    }
-  }
-  __syncthreads();
-  jacobi_eig(G, V, mm, rp, rq, rc, rs, scratch);
-  if (tid < m) lam[tid] = G[tid * mm + tid];
-  __syncthreads();
-  // eigenvectors of the Gram matrix: Vwarm * V (or V), kept in Gf
-  for (int idx = tid; idx < m * m; idx += nthr) {
-    const int r = idx / m, c = idx % m;
-    double t;
-    if (Vwarm) {
-      t = 0.0;
-      for (int k = 0; k < m; ++k) t += Vwarm[r * m + k] * V[k * mm + c];
-    } else {
-      t = V[r * mm + c];
-    }
-    Gf[idx] = t;
-  }
-  if (tid == 0) {
-    double lmax = 0.0, lmin = 1e308;
-    for (int i = 0; i < m; ++i) {
-      lmax = fmax(lmax, lam[i]);
-      lmin = fmin(lmin, lam[i]);
-    }
-    deg = !(lmax > 0.0) || !(lmin > 1e-12 * lmax);
-  }
-  __syncthreads();
-  if (deg) return false;
-  for (int idx = tid; idx < m * m; idx += nthr) {
-    const int a = idx / m, b = idx % m;
-    double s = 0.0;
-    for (int i = 0; i < m; ++i) s += Gf[a * m + i] * Gf[b * m + i] * rsqrt_refined(lam[i]);
-    W[a * m + b] = s;
-    if (Vout) Vout[idx] = Gf[idx];
-  }
-  __syncthreads();
-  return true;
 }
 
 // ---------------------------------------------------------------- kernels
@@ -302,9 +149,9 @@ struct Wide<__nv_fp8_e4m3> {
 
 // Column norms c_i = ||a_i||_2 (step a0).  Float storage: squares summed
 // with Kahan compensation per lane in float, lanes combined in double; the
-// exact FP64 norms of the leading candidates are recomputed by
-// select_start_kernel before any decision is taken on them.  One warp per
-// column.  A non-finite norm flags the solve.
+// accurate norms (double-float sums of exact products) of the leading
+// candidates are recomputed by select_start_kernel before any decision is
+// taken on them.  One warp per column.  A non-finite norm flags the solve.
 template <typename TA>
 __global__ void colnorm_kernel(const IO* io, State* st, int64_t ld, int p, int n, int fast) {
   double* cnorm = io->cnorm;
@@ -352,110 +199,137 @@ __global__ void colnorm_kernel(const IO* io, State* st, int64_t ld, int p, int n
   if (bad) atomicOr(&st->error, static_cast<int>(kErrNonFinite));
 }
 
-// Exact FP64 norm of column i (used for the start decision and gamma scale).
+// Squared norm of column i over the rows [r0, p) step `step`: float data in
+// double-float (products of floats are exact, the sum is good to ~1e-14),
+// double data in double.
+template <typename TA>
+__device__ __forceinline__ dd col_sumsq_part(const IO* io, int64_t ld, int p, int i, int r0, int step) {
+  const TA* col = static_cast<const TA*>(io->A) + static_cast<int64_t>(i) * ld;
+  if constexpr (sizeof(typename Elem<TA>::TC) == 8) {
+    double s0 = 0.0, s1 = 0.0;
+    int r = r0;
+    for (; r + step < p; r += 2 * step) {
+      const double v0 = static_cast<double>(to_tc<TA>(col[r]));
+      const double v1 = static_cast<double>(to_tc<TA>(col[r + step]));
+      s0 = fma(v0, v0, s0);
+      s1 = fma(v1, v1, s1);
+    }
+    if (r < p) {
+      const double v = static_cast<double>(to_tc<TA>(col[r]));
+      s0 = fma(v, v, s0);
+    }
+    return dd_from_double(s0 + s1);
+  } else {
+    dd s0{0.0f, 0.0f}, s1{0.0f, 0.0f};
+    int r = r0;
+    for (; r + step < p; r += 2 * step) {
+      const float v0 = to_tc<TA>(col[r]);
+      const float v1 = to_tc<TA>(col[r + step]);
+      s0 = dd_add(s0, two_prod(v0, v0));
+      s1 = dd_add(s1, two_prod(v1, v1));
+    }
+    if (r < p) {
+      const float v = to_tc<TA>(col[r]);
+      s0 = dd_add(s0, two_prod(v, v));
+    }
+    return dd_add(s0, s1);
+  }
+}
+
+__device__ __forceinline__ dd warp_sum_dd(dd v) {
+  for (int off = 16; off > 0; off >>= 1)
+    v = dd_add(v, dd{__shfl_xor_sync(0xffffffffu, v.hi, off), __shfl_xor_sync(0xffffffffu, v.lo, off)});
+  return v;
+}
+
+// Accurate norm of column i by one warp (scaled by the FP8 column scale).
 template <typename TA>
 __device__ double exact_colnorm_warp(const IO* io, int64_t ld, int p, int i) {
-  const TA* col = static_cast<const TA*>(io->A) + static_cast<int64_t>(i) * ld;
-  const int lane = threadIdx.x & 31;
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;  // independent chains
-  int r = lane;
-  for (; r + 96 < p; r += 128) {
-    const double v0 = static_cast<double>(to_tc<TA>(col[r]));
-    const double v1 = static_cast<double>(to_tc<TA>(col[r + 32]));
-    const double v2 = static_cast<double>(to_tc<TA>(col[r + 64]));
-    const double v3 = static_cast<double>(to_tc<TA>(col[r + 96]));
-    s0 += v0 * v0;
-    s1 += v1 * v1;
-    s2 += v2 * v2;
-    s3 += v3 * v3;
-  }
-  for (; r < p; r += 32) {
-    const double v = static_cast<double>(to_tc<TA>(col[r]));
-    s0 += v * v;
-  }
-  double s = (s0 + s1) + (s2 + s3);
-  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-  double c = sqrt(s);
+  const dd s = warp_sum_dd(col_sumsq_part<TA>(io, ld, p, i, threadIdx.x & 31, 32));
+  double c = sqrt(dd_to_double(s));
   if (sizeof(TA) == 1) c *= static_cast<double>(io->col_scale[i]);
   return c;
 }
 
-// (value desc, index asc) ordering helpers for the block-wide argmax.
+// Accurate norm of column i by the whole CTA (warp partials added in warp
+// order); every thread gets the value.
+template <typename TA>
+__device__ double exact_colnorm_cta(const IO* io, int64_t ld, int p, int i, dd* red) {
+  const dd s = warp_sum_dd(col_sumsq_part<TA>(io, ld, p, i, threadIdx.x, blockDim.x));
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if ((threadIdx.x & 31) == 0) red[warp] = s;
+  __syncthreads();
+  dd t = red[0];
+  for (int w = 1; w < nw; ++w) t = dd_add(t, red[w]);
+  __syncthreads();
+  double c = sqrt(dd_to_double(t));
+  if (sizeof(TA) == 1) c *= static_cast<double>(io->col_scale[i]);
+  return c;
+}
+
+// (value desc, index asc) ordering on non-negative doubles, compared through
+// their bit patterns (which order like the values) on the integer pipes.
+__device__ __forceinline__ bool better_bits(long long v, int i, long long bv, int bi) {
+  return (v > bv) || (v == bv && i < bi);
+}
 __device__ __forceinline__ bool better(double v, int i, double bv, int bi) {
   return (v > bv) || (v == bv && i < bi);
 }
 
-__device__ void block_argmax(double& v, int& i, double* sv, int* si) {
-  for (int off = 16; off > 0; off >>= 1) {
-    const double ov = __shfl_xor_sync(0xffffffffu, v, off);
-    const int oi = __shfl_xor_sync(0xffffffffu, i, off);
-    if (better(ov, oi, v, i)) { v = ov; i = oi; }
-  }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) { sv[warp] = v; si[warp] = i; }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double bv = sv[0];
-    int bi = si[0];
-    for (int w = 1; w < static_cast<int>(blockDim.x >> 5); ++w)
-      if (better(sv[w], si[w], bv, bi)) { bv = sv[w]; bi = si[w]; }
-    sv[32] = bv; si[32] = bi;
-  }
-  __syncthreads();
-  v = sv[32];
-  i = si[32];
-  __syncthreads();
-}
-
-// Start of the iteration (step a0): the largest-norm column (single-unit) or
-// the m largest-norm columns in decreasing order (block), ties to the lower
-// index, decided on exact FP64 norms; gamma scaled by max_i ||a_i|| when
-// relative.  One CTA.
+// Start of the iteration (step a0): the largest-norm column (single-unit),
+// ties to the lower index, decided on accurate norms; gamma scaled by
+// max_i ||a_i|| when relative.  One CTA.
 template <typename TA>
 __global__ void __launch_bounds__(kStartThreads) select_start_kernel(const StartArgs a) {
   const IO* io = a.io;
   State* st = a.st;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int warp = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
-  __shared__ double sv[33];
+  __shared__ long long sv[33];
   __shared__ int si[33];
+  __shared__ dd red[32];
   __shared__ int cand[kMaxCandidates];
   __shared__ double cexact[kMaxCandidates];
   __shared__ int ncand;
-  __shared__ int order[kMaxM];
-  __shared__ double vm;
-  __shared__ int picks[kMaxM];
+  __shared__ int order0;
   if (st->error) {
     if (tid == 0) st->n_active = 0;
     return;
   }
   const bool block = a.form >= 2;
-  // only the largest column is needed: it is the single-unit start, and
-  // max_i ||a_i|| scales a relative gamma (block forms start from the sketch)
-  const int mt = 1;
-  // 1. the mt-th largest approximate norm, by mt rounds of arg-max below the previous pick
-  double pv = 1e308;
-  int pi = -1;
-  for (int r = 0; r < mt; ++r) {
-    double bv = -1.0;
-    int bi = 0x7fffffff;
-    for (int i = tid; i < a.n; i += nthr) {
-      const double v = io->cnorm[i];
-      const bool below = (v < pv) || (v == pv && i > pi);
-      if (below && better(v, i, bv, bi)) { bv = v; bi = i; }
-    }
-    block_argmax(bv, bi, sv, si);
-    pv = bv;
-    pi = bi;
-    if (tid == 0) picks[r] = bi;
-  }
-  if (tid == 0) { vm = pv; ncand = 0; }
-  __syncthreads();
-  // 2. candidates within 1e-5 (relative) of it; the compensated norms are
-  //    accurate to ~1e-7, so the exact leading columns are all among them
-  const double thr = vm * (1.0 - 1e-5);
+  // 1. arg-max of the compensated norms (the start column of single-unit
+  //    forms; the largest norm also scales a relative gamma)
+  const long long* cb = reinterpret_cast<const long long*>(io->cnorm);
+  long long bv = -1;
+  int bi = 0x7fffffff;
   for (int i = tid; i < a.n; i += nthr) {
-    if (io->cnorm[i] >= thr) {
+    const long long v = cb[i];
+    if (better_bits(v, i, bv, bi)) { bv = v; bi = i; }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    const long long ov = __shfl_xor_sync(0xffffffffu, bv, off);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+    if (better_bits(ov, oi, bv, bi)) { bv = ov; bi = oi; }
+  }
+  if (lane == 0) { sv[warp] = bv; si[warp] = bi; }
+  __syncthreads();
+  if (tid == 0) {
+    long long b = sv[0];
+    int ib = si[0];
+    for (int w = 1; w < nwarps; ++w)
+      if (better_bits(sv[w], si[w], b, ib)) { b = sv[w]; ib = si[w]; }
+    sv[32] = b;
+    si[32] = ib;
+    ncand = 0;
+  }
+  __syncthreads();
+  const double vmax = __longlong_as_double(sv[32]);
+  const int pick = si[32];
+  // 2. candidates within 1e-5 (relative) of it; the compensated norms are
+  //    accurate to ~1e-7, so the exact leading column is among them
+  const long long thr = __double_as_longlong(vmax * (1.0 - 1e-5));
+  for (int i = tid; i < a.n; i += nthr) {
+    if (cb[i] >= thr) {
       const int slot = atomicAdd(&ncand, 1);
       if (slot < kMaxCandidates) cand[slot] = i;
     }
@@ -463,31 +337,39 @@ __global__ void __launch_bounds__(kStartThreads) select_start_kernel(const Start
   __syncthreads();
   const int nc = min(ncand, kMaxCandidates);
   const bool overflow = ncand > kMaxCandidates;
-  // 3. exact FP64 norms of the candidates (one warp each)
-  for (int c = warp; c < nc; c += nwarps) {
-    const double e = exact_colnorm_warp<TA>(io, a.ld, a.p, cand[c]);
-    if (lane == 0) cexact[c] = e;
+  // 3. accurate norms of the candidates: the whole CTA per candidate when
+  //    there are few (the usual case), one warp each otherwise
+  if (nc <= 4) {
+    for (int c = 0; c < nc; ++c) {
+      const double e = exact_colnorm_cta<TA>(io, a.ld, a.p, cand[c], red);
+      if (tid == 0) cexact[c] = e;
+    }
+  } else {
+    for (int c = warp; c < nc; c += nwarps) {
+      const double e = exact_colnorm_warp<TA>(io, a.ld, a.p, cand[c]);
+      if (lane == 0) cexact[c] = e;
+    }
   }
   __syncthreads();
-  // 4. rank candidates by (exact norm desc, index asc); if more than
-  //    kMaxCandidates columns tie within 1e-5, keep the approximate order
+  // 4. the best candidate by (accurate norm desc, index asc); if more than
+  //    kMaxCandidates columns tie within 1e-5, keep the approximate pick
   if (tid < nc && !overflow) {
     const double v = cexact[tid];
     const int i = cand[tid];
     int rank = 0;
     for (int c = 0; c < nc; ++c)
       if (better(cexact[c], cand[c], v, i)) ++rank;
-    if (rank < mt) order[rank] = cand[tid];
+    if (rank == 0) order0 = i;
   }
-  if (overflow && tid < mt) order[tid] = picks[tid];
+  if (overflow && tid == 0) order0 = pick;
   __syncthreads();
   double cmax0 = 0.0;
-  if (overflow && warp == 0) cmax0 = exact_colnorm_warp<TA>(io, a.ld, a.p, order[0]);
+  if (overflow) cmax0 = exact_colnorm_cta<TA>(io, a.ld, a.p, order0, red);
   if (tid == 0) {
     double cmax = cmax0;
     if (!overflow)
       for (int c = 0; c < nc; ++c)
-        if (cand[c] == order[0]) cmax = cexact[c];
+        if (cand[c] == order0) cmax = cexact[c];
     st->cmax = cmax;
     const bool l1 = (a.form & 1) == 0;
     for (int j = 0; j < a.m; ++j) {
@@ -495,7 +377,7 @@ __global__ void __launch_bounds__(kStartThreads) select_start_kernel(const Start
         const double g = io->gamma_in[j] * cmax;
         st->gamma[j] = l1 ? g : g * g;
       }
-      st->start_cols[j] = (io->has_x0 || block) ? -1 : order[0];
+      st->start_cols[j] = (io->has_x0 || block) ? -1 : order0;
     }
     if (!(cmax > 0.0)) {  // A == 0
       for (int j = 0; j < a.m; ++j) {
@@ -532,93 +414,177 @@ __global__ void gather_start_kernel(const StartArgs a) {
   P[static_cast<int64_t>(j) * a.p + r] = v;
 }
 
-// Y = sum of the per-cluster partials (fixed order), and this block's rows'
-// contribution to the Gram matrix Y^T Y (packed j <= l, or the diagonal).
+// Sum of partials along the split index: for float data a double-float sum
+// on the float pipes, rounded to float once; for double data plain double.
+template <typename TC>
+struct YAcc;
+template <>
+struct YAcc<float> {
+  dd v{0.0f, 0.0f};
+  __device__ __forceinline__ void add(float x) {
+    const dd s = two_sum(v.hi, x);
+    v = fast_two_sum(s.hi, s.lo + v.lo);
+  }
+  __device__ __forceinline__ void add(const YAcc& o) { v = dd_add(v, o.v); }
+  __device__ __forceinline__ float rounded() const { return v.hi + v.lo; }
+};
+template <>
+struct YAcc<double> {
+  double v = 0.0;
+  __device__ __forceinline__ void add(double x) { v += x; }
+  __device__ __forceinline__ void add(const YAcc& o) { v += o.v; }
+  __device__ __forceinline__ double rounded() const { return v; }
+};
+
+__device__ __forceinline__ dd shfl_xor_dd(dd v, int off) {
+  return dd{__shfl_xor_sync(0xffffffffu, v.hi, off), __shfl_xor_sync(0xffffffffu, v.lo, off)};
+}
+
+// Table 1 summand and squared unnormalised loading of one entry t: the rule
+// of threshold(), for float t evaluated in double-float against the double
+// gamma and mu given as dd (no double arithmetic), for double t in double.
+__device__ __forceinline__ void objective_terms(int form, float t, double, double, dd gam, dd mu, dd* term,
+                                                dd* z2) {
+  if ((form & 1) == 0) {  // L1: s = [mu |t| - gamma]_+, term = s^2 = z^2
+    const dd s = dd_sub(dd_mul_f(mu, fabsf(t)), gam);
+    const dd sq = dd_mul(s, s);
+    const bool act = s.hi > 0.0f;
+    *term = act ? sq : dd{0.0f, 0.0f};
+    *z2 = *term;
+  } else {  // L0: u = mu t, active when u^2 > gamma: term = u^2 - gamma, z = u
+    const dd u = dd_mul_f(mu, t);
+    const dd u2 = dd_mul(u, u);
+    const dd d = dd_sub(u2, gam);
+    const bool act = d.hi > 0.0f;
+    *term = act ? d : dd{0.0f, 0.0f};
+    *z2 = act ? u2 : dd{0.0f, 0.0f};
+  }
+}
+__device__ __forceinline__ void objective_terms(int form, double t, double gam, double mu, dd, dd, dd* term,
+                                                dd* z2) {
+  const Thr th = threshold(form, t, gam, mu);
+  *term = dd_from_double(th.term);
+  *z2 = dd_from_double(th.zr * th.zr);
+}
+
+// One reduction launch after a sweep.  Blocks [0, nyb): Y = sum of the
+// per-cluster partials (fixed order) for kReduceRows rows, and those rows'
+// contribution to the Gram matrix Y^T Y (packed j <= l, or the diagonal), in
+// double.  Blocks [nyb, nyb + nobj) (with `objective`): a share of the Table 1
+// objective and of the loadings' squared norms from T, in double-float.
 template <typename TC>
 __global__ void __launch_bounds__(kReduceRows* kReduceGroups) reduce_kernel(const ReduceArgs a) {
   if (a.st->n_active == 0) return;
-  __shared__ double part[kReduceGroups][kReduceRows];
-  __shared__ double Ys[kMaxM][kReduceRows];
-  __shared__ double Yo[kMaxM][kReduceRows];  // cross mode: the previous Y
   const int tid = threadIdx.x;
+  const int m = a.m, p = a.p;
+  if (static_cast<int>(blockIdx.x) >= a.nyb) {
+    // ---- objective share: entries [i0, i1) of every active column of T
+    constexpr int JB = 8;  // columns per pass
+    __shared__ dd red[kReduceGroups][2 * JB];
+    const int b = blockIdx.x - a.nyb;
+    const int chunk = (a.n + a.nobj - 1) / a.nobj;
+    const int i0 = b * chunk, i1 = min(a.n, i0 + chunk);
+    const TC* T = static_cast<const TC*>(a.io->T);
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int j0 = 0; j0 < m; j0 += JB) {
+      dd acc[2 * JB];
+#pragma unroll
+      for (int u = 0; u < 2 * JB; ++u) acc[u] = dd{0.0f, 0.0f};
+#pragma unroll
+      for (int u = 0; u < JB; ++u) {
+        const int j = j0 + u;
+        if (j >= m || !a.st->active[j]) continue;
+        const double gam = a.st->gamma[j], mu = a.io->mu[j];
+        const dd gam_d = dd_from_double(gam), mu_d = dd_from_double(mu);
+        const TC* col = T + static_cast<int64_t>(j) * a.n;
+        for (int i = i0 + tid; i < i1; i += blockDim.x) {
+          dd term, zz;
+          objective_terms(a.form, col[i], gam, mu, gam_d, mu_d, &term, &zz);
+          acc[u] = dd_add(acc[u], term);
+          acc[JB + u] = dd_add(acc[JB + u], zz);
+        }
+      }
+      // reduce-scatter over the warp: lane L ends with the warp total of acc[L % 16]
+#pragma unroll
+      for (int h = JB; h >= 1; h >>= 1) {
+        const bool up = (lane & h) != 0;
+#pragma unroll
+        for (int q = 0; q < h; ++q) {
+          const dd send = up ? acc[q] : acc[q + h];
+          const dd keep = up ? acc[q + h] : acc[q];
+          acc[q] = dd_add(keep, shfl_xor_dd(send, h));
+        }
+      }
+      acc[0] = dd_add(acc[0], shfl_xor_dd(acc[0], 16));
+      if (lane < 2 * JB) red[warp][lane] = acc[0];
+      __syncthreads();
+      if (tid < 2 * JB) {
+        dd t = red[0][tid];
+        for (int w = 1; w < kReduceGroups; ++w) t = dd_add(t, red[w][tid]);
+        const int u = tid % JB, which = tid / JB, j = j0 + u;
+        if (j < m) a.io->fpart[(static_cast<int64_t>(b) * 2 + which) * m + j] = t;
+      }
+      __syncthreads();
+    }
+    return;
+  }
+  // ---- Y rows and their Gram contribution
+  constexpr int JY = 4;  // columns whose partial loads are in flight together
+  __shared__ YAcc<TC> part[kReduceGroups][JY][kReduceRows];
+  __shared__ TC Ys[kMaxM][kReduceRows];
+  __shared__ TC Yo[kMaxM][kReduceRows];  // cross mode: the previous Y
   const int rl = tid % kReduceRows, g = tid / kReduceRows;
   const int row = blockIdx.x * kReduceRows + rl;
   const TC* yp = static_cast<const TC*>(a.init ? a.io->P : a.io->ypart);
   TC* Y = static_cast<TC*>(a.io->Y);
-  const int m = a.m, p = a.p;
-  for (int j = 0; j < m; ++j) {
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;  // independent chains, fixed order
+  const int64_t stride = static_cast<int64_t>(m) * p;
+  for (int j0 = 0; j0 < m; j0 += JY) {
+    YAcc<TC> s[JY];
     if (row < p) {
-      const int64_t stride = static_cast<int64_t>(m) * p;
-      const TC* src = yp + static_cast<int64_t>(j) * p + row;
-      int sp = g;
-      for (; sp + 3 * kReduceGroups < a.nsplit; sp += 4 * kReduceGroups) {
-        s0 += static_cast<double>(src[sp * stride]);
-        s1 += static_cast<double>(src[(sp + kReduceGroups) * stride]);
-        s2 += static_cast<double>(src[(sp + 2 * kReduceGroups) * stride]);
-        s3 += static_cast<double>(src[(sp + 3 * kReduceGroups) * stride]);
-      }
-      for (; sp < a.nsplit; sp += kReduceGroups) s0 += static_cast<double>(src[sp * stride]);
-    }
-    part[g][rl] = (s0 + s1) + (s2 + s3);
-    __syncthreads();
-    if (g == 0) {
-      double t = 0.0;
-      for (int g2 = 0; g2 < kReduceGroups; ++g2) t += part[g2][rl];
-      const TC tc = static_cast<TC>(t);
-      Ys[j][rl] = (row < p) ? static_cast<double>(tc) : 0.0;
-      if (a.cross) {
-        Yo[j][rl] = (row < p) ? static_cast<double>(Y[static_cast<int64_t>(j) * p + row]) : 0.0;
-      } else if (row < p) {
-        Y[static_cast<int64_t>(j) * p + row] = tc;
-      }
-    }
-    __syncthreads();
-  }
-  if (a.objective) {
-    // Table 1 objective f_j and the squared norm of the unnormalised
-    // loadings, in double, over this block's share of T (active components)
-    __shared__ double red2[2][kReduceGroups];
-    const int nb = gridDim.x;
-    const int chunk = (a.n + nb - 1) / nb;
-    const int i0 = blockIdx.x * chunk, i1 = min(a.n, i0 + chunk);
-    const TC* T = static_cast<const TC*>(a.io->T);
-    for (int j = 0; j < m; ++j) {
-      double f = 0.0, z2 = 0.0;
-      if (a.st->active[j]) {
-        const double gam = a.st->gamma[j], mu = a.io->mu[j];
-        for (int i = i0 + tid; i < i1; i += blockDim.x) {
-          const Thr th = threshold(a.form, static_cast<double>(T[static_cast<int64_t>(j) * a.n + i]), gam, mu);
-          f += th.term;
-          z2 += th.zr * th.zr;
+      // loads of JY columns x 2 splits issued before any of their adds
+      for (int sp = g; sp < a.nsplit; sp += 2 * kReduceGroups) {
+        const bool two = sp + kReduceGroups < a.nsplit;
+        TC v0[JY], v1[JY];
+#pragma unroll
+        for (int u = 0; u < JY; ++u) {
+          const int j = min(j0 + u, m - 1);
+          const TC* src = yp + static_cast<int64_t>(j) * p + row;
+          v0[u] = src[sp * stride];
+          v1[u] = two ? src[(sp + kReduceGroups) * stride] : TC(0);
+        }
+#pragma unroll
+        for (int u = 0; u < JY; ++u) {
+          s[u].add(v0[u]);
+          if (two) s[u].add(v1[u]);
         }
       }
-      for (int off = 16; off > 0; off >>= 1) {
-        f += __shfl_xor_sync(0xffffffffu, f, off);
-        z2 += __shfl_xor_sync(0xffffffffu, z2, off);
-      }
-      if ((tid & 31) == 0) {
-        red2[0][tid >> 5] = f;
-        red2[1][tid >> 5] = z2;
-      }
-      __syncthreads();
-      if (tid == 0) {
-        double F = 0.0, Z2 = 0.0;
-        for (int w = 0; w < kReduceGroups; ++w) {
-          F += red2[0][w];
-          Z2 += red2[1][w];
-        }
-        a.io->fpart[(static_cast<int64_t>(blockIdx.x) * 2 + 0) * m + j] = F;
-        a.io->fpart[(static_cast<int64_t>(blockIdx.x) * 2 + 1) * m + j] = Z2;
-      }
-      __syncthreads();
     }
+#pragma unroll
+    for (int u = 0; u < JY; ++u) part[g][u][rl] = s[u];
+    __syncthreads();
+    if (tid < JY * kReduceRows) {
+      const int u = tid / kReduceRows, j = j0 + u;
+      const int r2 = blockIdx.x * kReduceRows + rl;
+      if (j < m) {
+        YAcc<TC> t = part[0][u][rl];
+        for (int g2 = 1; g2 < kReduceGroups; ++g2) t.add(part[g2][u][rl]);
+        const TC tc = t.rounded();
+        Ys[j][rl] = (r2 < p) ? tc : TC(0);
+        if (a.cross) {
+          Yo[j][rl] = (r2 < p) ? Y[static_cast<int64_t>(j) * p + r2] : TC(0);
+        } else if (r2 < p) {
+          Y[static_cast<int64_t>(j) * p + r2] = tc;
+        }
+      }
+    }
+    __syncthreads();
   }
   if (a.cross) {  // C[j][l] = sum_r Yold[r][j] Ynew[r][l]
     for (int q = tid; q < a.npairs; q += blockDim.x) {
       const int j = q / m, l = q % m;
       double s = 0.0;
-      for (int r = 0; r < kReduceRows; ++r) s += Yo[j][r] * Ys[l][r];
+      for (int r = 0; r < kReduceRows; ++r)
+        s = fma(static_cast<double>(Yo[j][r]), static_cast<double>(Ys[l][r]), s);
       a.io->gpart[static_cast<int64_t>(blockIdx.x) * a.npairs + q] = s;
     }
     return;
@@ -634,79 +600,14 @@ __global__ void __launch_bounds__(kReduceRows* kReduceGroups) reduce_kernel(cons
       j = l = q;
     }
     double s = 0.0;
-    for (int r = 0; r < kReduceRows; ++r) s += Ys[j][r] * Ys[l][r];
+    for (int r = 0; r < kReduceRows; ++r) s = fma(static_cast<double>(Ys[j][r]), static_cast<double>(Ys[l][r]), s);
     a.io->gpart[static_cast<int64_t>(blockIdx.x) * a.npairs + q] = s;
   }
 }
 
-// Rayleigh-Ritz rotation of the block start.  The current start is
-// Q = Y W (W the symmetric polar weights in the state) and the last sketch
-// sweep gave C = Y^T (A A^T Q); B = Q^T A A^T Q = W C, symmetrised.  Its
-// eigenvectors, by decreasing Ritz value, each signed so that its
-// largest-magnitude entry (first on ties) is positive, rotate the start:
-// new weights W V.  m x m work in FP64.
-__device__ void ritz_weights(const double* C, int m, const double* Wcur, double* Wout, double* sm,
-                             double* scratch) {
-  const int mm = m + (m & 1);
-  double* G = sm;
-  double* V = sm + mm * mm;
-  int* rp = reinterpret_cast<int*>(V + mm * mm);
-  int* rq = rp + 32;
-  double* rc = reinterpret_cast<double*>(rq + 32);
-  double* rs = rc + 32;
-  double* lam = rs + 32;
-  __shared__ int ord[kMaxM];
-  __shared__ double sgn[kMaxM];
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  for (int idx = tid; idx < mm * mm; idx += nthr) {
-    const int r = idx / mm, c = idx % mm;
-    double v = 0.0;
-    if (r < m && c < m) {
-      double brc = 0.0, bcr = 0.0;
-      for (int k = 0; k < m; ++k) {
-        brc += Wcur[r * m + k] * C[k * m + c];
-        bcr += Wcur[c * m + k] * C[k * m + r];
-      }
-      v = 0.5 * (brc + bcr);
-    }
-    G[idx] = v;
-  }
-  __syncthreads();
-  jacobi_eig(G, V, mm, rp, rq, rc, rs, scratch);
-  if (tid < m) lam[tid] = G[tid * mm + tid];
-  __syncthreads();
-  if (tid == 0) {  // order by decreasing Ritz value (ties: lower index first)
-    for (int j = 0; j < m; ++j) ord[j] = j;
-    for (int a = 0; a < m; ++a) {
-      int best = a;
-      for (int b = a + 1; b < m; ++b)
-        if (lam[ord[b]] > lam[ord[best]]) best = b;
-      const int t = ord[a];
-      ord[a] = ord[best];
-      ord[best] = t;
-    }
-    for (int j = 0; j < m; ++j) {
-      const int c = ord[j];
-      int imax = 0;
-      for (int i = 1; i < m; ++i)
-        if (fabs(V[i * mm + c]) > fabs(V[imax * mm + c])) imax = i;
-      sgn[j] = V[imax * mm + c] < 0.0 ? -1.0 : 1.0;
-    }
-  }
-  __syncthreads();
-  for (int idx = tid; idx < m * m; idx += nthr) {
-    const int l = idx / m, j = idx % m;
-    const int c = ord[j];
-    double s = 0.0;
-    for (int k = 0; k < m; ++k) s += Wcur[l * m + k] * V[k * mm + c];
-    Wout[l * m + j] = sgn[j] * s;
-  }
-  __syncthreads();
-}
-
 // Objective, stopping test and projection weights after a sweep, or one step
-// of the start (projection of the start, Rayleigh-Ritz rotation).  One CTA;
-// all FP64.
+// of the start (projection of the start, Rayleigh-Ritz rotation).  One CTA:
+// sums and stopping test in double, the m x m eigenproblems in double-float.
 __global__ void __launch_bounds__(kFinishThreads) finish_kernel(const FinishArgs a) {
   extern __shared__ double fsm[];
   State* st = a.st;
@@ -714,7 +615,6 @@ __global__ void __launch_bounds__(kFinishThreads) finish_kernel(const FinishArgs
   const int tid = threadIdx.x;
   const int m = a.m;
   const bool block = a.form >= 2;
-  __shared__ double scratch[33];
   __shared__ int s_stop;
   double* gsum = fsm;                    // npairs
   double* fz = gsum + a.npairs;          // 2m
@@ -726,37 +626,37 @@ __global__ void __launch_bounds__(kFinishThreads) finish_kernel(const FinishArgs
     if (a.mode == kFinishIterate) sum_partials(io->fpart, a.nsplit, 2 * m, 2 * m, fz);
   }
   if (proceed && a.mode == kFinishRitz) {
-    ritz_weights(gsum, m, st->W, Wt, jac, scratch);
-    if (tid == 0)
-      for (int idx = 0; idx < m * m; ++idx) st->W[idx] = Wt[idx];
+    ritz_weights(gsum, m, st->W, Wt, jac);
+    for (int idx = tid; idx < m * m; idx += blockDim.x) st->W[idx] = Wt[idx];
   } else if (proceed && a.mode == kFinishPolar) {
     if (block) {
-      const bool ok = polar_weights(gsum, m, Wt, jac, scratch, nullptr, st->V);
+      const bool ok = polar_weights(gsum, m, st->W, jac, st->has_v ? st->V : nullptr, st->V);
       if (tid == 0) {
         if (ok) {
           st->has_v = 1;
-          for (int idx = 0; idx < m * m; ++idx) st->W[idx] = Wt[idx];
         } else {
           for (int j = 0; j < m; ++j) { st->status[j] = GPSPCA_DEGENERATE; st->active[j] = 0; }
           st->n_active = 0;
           st->any_degenerate = 1;
         }
       }
-    } else if (tid == 0) {
-      int na = 0;
-      for (int j = 0; j < m; ++j) {
+    } else {  // one thread per component
+      const int j = tid;
+      bool live = false;
+      if (j < m) {
         for (int l = 0; l < m; ++l) st->W[l * m + j] = 0.0;
         const double d = gsum[j];
         if (d > 0.0) {
           st->W[j * m + j] = rsqrt_refined(d);
-          ++na;
+          live = true;
         } else {
           st->status[j] = GPSPCA_DEGENERATE;
           st->active[j] = 0;
           st->any_degenerate = 1;
         }
       }
-      st->n_active = na;
+      const int na = __syncthreads_count(live);
+      if (tid == 0) st->n_active = na;
     }
   } else if (proceed) {
     const int k = st->k;
@@ -777,34 +677,30 @@ __global__ void __launch_bounds__(kFinishThreads) finish_kernel(const FinishArgs
       __syncthreads();
       bool deg = false;
       if (s_stop < 0) {
-        deg = !polar_weights(gsum, m, Wt, jac, scratch, st->has_v ? st->V : nullptr, st->V);
+        deg = !polar_weights(gsum, m, st->W, jac, st->has_v ? st->V : nullptr, st->V);
       }
-      if (tid == 0) {
-        if (s_stop >= 0 || deg) {
-          for (int j = 0; j < m; ++j) {
-            st->status[j] = deg ? GPSPCA_DEGENERATE : s_stop;
-            st->iters[j] = k + 1;
-            st->f[j] = fz[j];
-            st->znorm2[j] = fz[m + j];
-            st->active[j] = 0;
-          }
+      if (s_stop >= 0 || deg) {
+        const int j = tid;
+        if (j < m) {
+          st->status[j] = deg ? GPSPCA_DEGENERATE : s_stop;
+          st->iters[j] = k + 1;
+          st->f[j] = fz[j];
+          st->znorm2[j] = fz[m + j];
+          st->active[j] = 0;
+        }
+        if (tid == 0) {
           if (deg) st->any_degenerate = 1;
           st->n_active = 0;
-        } else {
-          for (int idx = 0; idx < m * m; ++idx) st->W[idx] = Wt[idx];
         }
       }
-    } else if (tid == 0) {
-      int na = 0;
-      for (int j = 0; j < m; ++j) {
-        if (!st->active[j]) {
-          st->W[j * m + j] = 0.0;
-          continue;
-        }
+    } else {  // one thread per component (gamma path: independent solves)
+      const int j = tid;
+      bool live = false;
+      if (j < m && st->active[j]) {
         const double f = fz[j];
         int s = stop_rule(k, f, st->f_prev[j], tol, maxit);
         if (!isfinite(f)) {
-          st->error |= kErrNonFinite;
+          atomicOr(&st->error, kErrNonFinite);
           s = GPSPCA_MAXIT;
         }
         bool deg = false;
@@ -813,20 +709,25 @@ __global__ void __launch_bounds__(kFinishThreads) finish_kernel(const FinishArgs
           if (d > 0.0) {
             st->W[j * m + j] = rsqrt_refined(d);
             st->f_prev[j] = f;
-            ++na;
-            continue;
+            live = true;
+          } else {
+            deg = true;
           }
-          deg = true;
         }
-        st->status[j] = deg ? GPSPCA_DEGENERATE : s;
-        st->iters[j] = k + 1;
-        st->f[j] = f;
-        st->znorm2[j] = fz[m + j];
-        st->active[j] = 0;
+        if (!live) {
+          st->status[j] = deg ? GPSPCA_DEGENERATE : s;
+          st->iters[j] = k + 1;
+          st->f[j] = f;
+          st->znorm2[j] = fz[m + j];
+          st->active[j] = 0;
+          st->W[j * m + j] = 0.0;
+          if (deg) st->any_degenerate = 1;
+        }
+      } else if (j < m) {
         st->W[j * m + j] = 0.0;
-        if (deg) st->any_degenerate = 1;
       }
-      st->n_active = na;
+      const int na = __syncthreads_count(live);
+      if (tid == 0) st->n_active = na;
     }
     if (tid == 0) st->k = k + 1;
   }
@@ -907,7 +808,8 @@ void launch_gather_start(int dtype, const StartArgs& a, cudaStream_t s) {
   }
 }
 
-void launch_reduce(int tcsize, const ReduceArgs& a, int nblk, cudaStream_t s) {
+void launch_reduce(int tcsize, const ReduceArgs& a, cudaStream_t s) {
+  const int nblk = a.nyb + (a.objective ? a.nobj : 0);
   if (tcsize == 8)
     reduce_kernel<double><<<nblk, kReduceRows * kReduceGroups, 0, s>>>(a);
   else

@@ -4,6 +4,7 @@
 // weights via a Jacobi eigensolve), and the recovery of the loadings.
 #pragma once
 
+#include "smalleig.cuh"
 #include "sweep.cuh"
 
 namespace gpspca {
@@ -19,12 +20,14 @@ struct ReduceArgs {
   int cross;          // 1: no Y update; Gram partials of (old Y, new Y) pairs, m*m
   int objective;      // 1: also the Table 1 objective partials from io->T (n entries, form)
   int n, form;
+  int nyb;            // blocks summing Y rows (kReduceRows each)
+  int nobj;           // blocks forming objective partials (after the Y blocks), when objective
 };
 
 struct FinishArgs {
   const IO* io;
   State* st;
-  int nsplit;  // objective partials in io->fpart (one set per reduction block)
+  int nsplit;  // objective partial sets in io->fpart (one per objective block)
   int nblk;    // Gram partials in io->gpart
   int npairs;
   int m, form;
@@ -55,19 +58,17 @@ constexpr int kFinishThreads = 256;
 constexpr int kStartThreads = 1024;
 constexpr int kMaxCandidates = 256;
 
-// Shared memory (in doubles) of finish_kernel for m components and npairs
-// Gram entries: partial sums, objective parts, weights, Jacobi workspace.
-inline int finish_smem_doubles(int m, int npairs) {
-  const int mm = m + (m & 1);
-  return npairs + 2 * m + m * m + 2 * mm * mm + 64 + kMaxM + m * m + 32;
-}
+// Shared memory (in 8-byte slots) of finish_kernel for m components and
+// npairs Gram entries: partial sums, objective parts, weights, eigensolver
+// workspace.
+inline int finish_smem_doubles(int m, int npairs) { return npairs + 2 * m + m * m + eig_ws_slots(m); }
 
 // Host-side launchers (each kernel is launched from the file that defines it).
 void launch_reset(const IO* io, State* st, int m, int form, cudaStream_t s);
 void launch_colnorm(int dtype, const IO* io, State* st, int64_t ld, int p, int n, int fast, cudaStream_t s);
 void launch_select_start(int dtype, const StartArgs& a, cudaStream_t s);
 void launch_gather_start(int dtype, const StartArgs& a, cudaStream_t s);
-void launch_reduce(int tcsize, const ReduceArgs& a, int nblk, cudaStream_t s);
+void launch_reduce(int tcsize, const ReduceArgs& a, cudaStream_t s);
 void launch_finish(const FinishArgs& a, int smem, cudaStream_t s);
 void launch_finalize(int tcsize, const IO* io, const State* st, int p, int n, int m, int form, cudaStream_t s);
 

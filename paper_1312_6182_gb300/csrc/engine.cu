@@ -231,6 +231,7 @@ int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fa
   pl.ncl = ncl;
   pl.cols_per_cl = static_cast<int>((n + ncl - 1) / ncl);
   pl.nred = static_cast<int>((p + kReduceRows - 1) / kReduceRows);
+  pl.nobj = static_cast<int>(std::min<int64_t>(std::max<int64_t>(1, (n + 1023) / 1024), 2 * nsm));
   pl.full_gram = form >= 2 ? 1 : 0;
   pl.npairs = pl.full_gram ? m * m : m;  // gpart capacity: the Ritz step's cross Gram is m x m
   pl.finish_smem = static_cast<int>(sizeof(double)) * finish_smem_doubles(m, pl.npairs);
@@ -238,7 +239,7 @@ int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fa
   pl.ws_P = static_cast<size_t>(d.tcsize) * m * p;
   pl.ws_ypart = static_cast<size_t>(d.tcsize) * ncl * m * p;
   pl.ws_T = static_cast<size_t>(d.tcsize) * m * n;
-  pl.ws_fpart = sizeof(double) * static_cast<size_t>(pl.nred) * 2 * m;
+  pl.ws_fpart = sizeof(dd) * static_cast<size_t>(pl.nobj) * 2 * m;
   pl.ws_gpart = sizeof(double) * static_cast<size_t>(pl.nred) * pl.npairs;
   *P = pl;
   return GPSPCA_OK;
@@ -392,8 +393,8 @@ static cudaError_t launch_prologue(const Plan& pl, Slot* s, cudaStream_t cs, cud
   launch_select_start(pl.dtype, sa, cs);
   launch_gather_start(pl.dtype, sa, cs);
   const int gram_pairs = pl.full_gram ? pl.m * (pl.m + 1) / 2 : pl.m;
-  ReduceArgs ra{s->io_dev, s->st_dev, 1, pl.m, pl.p, pl.full_gram, gram_pairs, 1, 0, 0, pl.n, pl.form};
-  launch_reduce(pl.tcsize, ra, pl.nred, cs);
+  ReduceArgs ra{s->io_dev, s->st_dev, 1, pl.m, pl.p, pl.full_gram, gram_pairs, 1, 0, 0, pl.n, pl.form, pl.nred, 0};
+  launch_reduce(pl.tcsize, ra, cs);
   FinishArgs fa{s->io_dev, s->st_dev, pl.ncl, pl.nred, gram_pairs, pl.m, pl.form, kFinishPolar, pca ? 0 : 1, h,
                 use_cond};
   launch_finish(fa, pl.finish_smem, cs);
@@ -401,14 +402,14 @@ static cudaError_t launch_prologue(const Plan& pl, Slot* s, cudaStream_t cs, cud
   if (e != cudaSuccess || !pca) return e;
   for (int step = 0; step < kPowerSteps; ++step) {
     if ((e = launch_sweeps(pl, s, cs, 1)) != cudaSuccess) return e;
-    ReduceArgs rp{s->io_dev, s->st_dev, pl.ncl, pl.m, pl.p, 1, gram_pairs, 0, 0, 0, pl.n, pl.form};
-    launch_reduce(pl.tcsize, rp, pl.nred, cs);
+    ReduceArgs rp{s->io_dev, s->st_dev, pl.ncl, pl.m, pl.p, 1, gram_pairs, 0, 0, 0, pl.n, pl.form, pl.nred, 0};
+    launch_reduce(pl.tcsize, rp, cs);
     FinishArgs fp{s->io_dev, s->st_dev, pl.ncl, pl.nred, gram_pairs, pl.m, pl.form, kFinishPolar, 0, h, use_cond};
     launch_finish(fp, pl.finish_smem, cs);
   }
   if ((e = launch_sweeps(pl, s, cs, 1)) != cudaSuccess) return e;
-  ReduceArgs rc{s->io_dev, s->st_dev, pl.ncl, pl.m, pl.p, 1, pl.m * pl.m, 0, 1, 0, pl.n, pl.form};
-  launch_reduce(pl.tcsize, rc, pl.nred, cs);
+  ReduceArgs rc{s->io_dev, s->st_dev, pl.ncl, pl.m, pl.p, 1, pl.m * pl.m, 0, 1, 0, pl.n, pl.form, pl.nred, 0};
+  launch_reduce(pl.tcsize, rc, cs);
   FinishArgs fr{s->io_dev, s->st_dev, pl.ncl, pl.nred, pl.m * pl.m, pl.m, pl.form, kFinishRitz, 1, h, use_cond};
   launch_finish(fr, pl.finish_smem, cs);
   return cudaGetLastError();
@@ -442,9 +443,10 @@ static cudaError_t launch_body(const Plan& pl, Slot* s, cudaStream_t cs, cudaGra
   cudaError_t e = launch_sweeps(pl, s, cs);
   if (e != cudaSuccess) return e;
   const int gram_pairs = pl.full_gram ? pl.m * (pl.m + 1) / 2 : pl.m;
-  ReduceArgs ra{s->io_dev, s->st_dev, pl.ncl, pl.m, pl.p, pl.full_gram, gram_pairs, 0, 0, 1, pl.n, pl.form};
-  launch_reduce(pl.tcsize, ra, pl.nred, cs);
-  FinishArgs fa{s->io_dev, s->st_dev, pl.nred, pl.nred, gram_pairs, pl.m, pl.form, kFinishIterate, 0, h, use_cond};
+  ReduceArgs ra{s->io_dev, s->st_dev, pl.ncl, pl.m, pl.p, pl.full_gram, gram_pairs, 0, 0, 1, pl.n, pl.form, pl.nred,
+                pl.nobj};
+  launch_reduce(pl.tcsize, ra, cs);
+  FinishArgs fa{s->io_dev, s->st_dev, pl.nobj, pl.nred, gram_pairs, pl.m, pl.form, kFinishIterate, 0, h, use_cond};
   launch_finish(fa, pl.finish_smem, cs);
   return cudaGetLastError();
 }
@@ -666,7 +668,7 @@ static int prepare_solve(Slot* s, const Request& r, int nsm, bool scratch_out, P
   io.Y = s->b_Y.p;
   io.ypart = s->b_ypart.p;
   io.T = s->b_T.p;
-  io.fpart = static_cast<double*>(s->b_fpart.p);
+  io.fpart = static_cast<dd*>(s->b_fpart.p);
   io.gpart = static_cast<double*>(s->b_gpart.p);
   for (int j = 0; j < m; ++j) {
     io.gamma_in[j] = r.gamma[j];

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "dd.cuh"
 #include "gpspca.h"
 
 namespace gpspca {
@@ -30,7 +31,7 @@ struct IO {
   void* Y;        // [m][p] last unnormalised direction
   void* ypart;    // [nsplit][m][p] per-cluster partials of Y = A G
   void* T;        // [m][n] dot products of the last sweep
-  double* fpart;  // [nsplit][2][m] objective / loading-norm partials
+  dd* fpart;      // [nobj][2][m] objective / loading-norm partials (double-float)
   double* gpart;  // [nred][npairs] Gram partials
   double gamma_in[kMaxM];  // as passed (absolute, or relative with the flag)
   double mu[kMaxM];
@@ -58,7 +59,7 @@ struct State {
   double f[kMaxM];
   double znorm2[kMaxM];  // squared norm of the unnormalised loading column of the last sweep
   double W[kMaxM * kMaxM];  // projection weights: X_k = Y_{k-1} W, [l * m + j]
-  double V[kMaxM * kMaxM];  // eigenvectors of the last Gram matrix (warm start of the next eigensolve)
+  dd V[kMaxM * kMaxM];      // eigenvectors of the last Gram matrix, double-float (warm start of the next eigensolve)
   int32_t has_v;
   double cmax;              // max_i ||a_i||
   int32_t start_cols[kMaxM];

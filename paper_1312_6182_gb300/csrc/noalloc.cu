@@ -67,15 +67,16 @@ static int static_setup(int dev, StaticPtrs** out) {
 
 // Sum of the reduction blocks' partials (fixed order): objective f and ||y||^2, then
 // x_next = y / ||y|| (all zero when y = 0).  One block.
-__global__ void static_sweep_finish(const double* fpart, const double* gpart, int nred, float* x_next, int p,
+__global__ void static_sweep_finish(const dd* fpart, int nobj, const double* gpart, int nred, float* x_next, int p,
                                     double* objective) {
   __shared__ double s_g;
   if (threadIdx.x == 0) {
-    double f = 0.0, g = 0.0;
-    for (int b = 0; b < nred; ++b) f += fpart[2 * b];
+    dd f{0.0f, 0.0f};
+    double g = 0.0;
+    for (int b = 0; b < nobj; ++b) f = dd_add(f, fpart[2 * b]);
     for (int b = 0; b < nred; ++b) g += gpart[b];
     s_g = g;
-    *objective = f;
+    *objective = dd_to_double(f);
   }
   __syncthreads();
   const float inv = s_g > 0.0 ? static_cast<float>(1.0 / sqrt(s_g)) : 0.0f;
@@ -114,12 +115,12 @@ extern "C" int gpspca_sweep_static(const gpspca_matrix* A, gpspca_form form, dou
   Plan pl;
   if ((rc = make_plan(GPSPCA_F32, form, 1, A->p, A->n, A->ld, fast, sp->nsm, &pl))) return rc;
   const int p = pl.p, n = pl.n;
-  // scratch layout: ypart [ncl][p] | xcopy [p] | fpart [nred][2] | gpart [nred]
+  // scratch layout: ypart [ncl][p] | xcopy [p] | fpart [nobj][2] | gpart [nred]
   auto up = [](size_t v) { return (v + 255) / 256 * 256; };
   const size_t off_ypart = 0;
   const size_t off_x = up(off_ypart + sizeof(float) * static_cast<size_t>(pl.ncl) * p);
   const size_t off_f = up(off_x + sizeof(float) * static_cast<size_t>(p));
-  const size_t off_g = up(off_f + sizeof(double) * 2 * static_cast<size_t>(pl.nred));
+  const size_t off_g = up(off_f + sizeof(dd) * 2 * static_cast<size_t>(pl.nobj));
   const size_t need = up(off_g + sizeof(double) * static_cast<size_t>(pl.nred));
   if (need > kStaticScratchBytes) {
     char msg[200];
@@ -135,7 +136,7 @@ extern "C" int gpspca_sweep_static(const gpspca_matrix* A, gpspca_form form, dou
   io.X = sc + off_x;             // the sweep's copy of the iterate it evaluated
   io.T = t;
   io.ypart = sc + off_ypart;
-  io.fpart = reinterpret_cast<double*>(sc + off_f);
+  io.fpart = reinterpret_cast<dd*>(sc + off_f);
   io.gpart = reinterpret_cast<double*>(sc + off_g);
   io.mu[0] = 1.0;
   io.gamma_in[0] = gamma;
@@ -174,9 +175,9 @@ extern "C" int gpspca_sweep_static(const gpspca_matrix* A, gpspca_form form, dou
     cudaGetLastError();
     return record_error(GPSPCA_ECUDA, "sweep launch failed");
   }
-  ReduceArgs ra{sp->io_reduce, sp->st, pl.ncl, 1, p, 0, 1, 0, 0, 1, n, form};
-  launch_reduce(4, ra, pl.nred, stream);
-  static_sweep_finish<<<1, 256, 0, stream>>>(reinterpret_cast<const double*>(sc + off_f),
+  ReduceArgs ra{sp->io_reduce, sp->st, pl.ncl, 1, p, 0, 1, 0, 0, 1, n, form, pl.nred, pl.nobj};
+  launch_reduce(4, ra, stream);
+  static_sweep_finish<<<1, 256, 0, stream>>>(reinterpret_cast<const dd*>(sc + off_f), pl.nobj,
                                               reinterpret_cast<const double*>(sc + off_g), pl.nred, x_next, p,
                                               objective);
   if (cudaGetLastError() != cudaSuccess) return record_error(GPSPCA_ECUDA, "reduction launch failed");

@@ -22,7 +22,7 @@ struct Plan {
   int pca = 0;  // block start by power steps + Rayleigh-Ritz (no caller x0)
   int C = 1, ps = 0, ncl = 0, cols_per_cl = 0;
   std::vector<Pass> passes;
-  int nred = 0, npairs = 0, full_gram = 0;
+  int nred = 0, nobj = 0, npairs = 0, full_gram = 0;
   int finish_smem = 0;
   int tcsize = 4, esize = 4;
   size_t ws_cnorm = 0, ws_P = 0, ws_ypart = 0, ws_T = 0, ws_fpart = 0, ws_gpart = 0;
