@@ -29,6 +29,7 @@ RHO = 0.05
 MU_W = [1.0, 0.9, 0.8, 0.7, 0.6]
 CASES = [("SL1", None), ("SL0", None), ("BL1", [1.0] * 5), ("BL0", [1.0] * 5), ("BL1", MU_W), ("BL0", MU_W)]
 TOL, MAXIT = 1e-6, 1000
+RHO32 = 0.01
 METRIC = "GPower iters/s"
 UNIT = "iters/s"
 WORKLOAD = "planted spikes 5000x20000 fp32 (5 spikes, theta_j=40/j, 5% supports), SL1+SL0+BL1+BL0 (m=5, mu=1 and mu=[1,.9,.8,.7,.6]), gamma=0.05*max||a_i||, tol 1e-6"
@@ -48,6 +49,24 @@ def _dist():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def reduce_over_ranks(ms, units, device="cpu"):
+    """Replicas: the slowest rank's timed region and the units all ranks did.
+
+    One process per GPU runs the whole step on its own copy of the workload
+    (the solves share nothing, so nothing is exchanged on the data path); the
+    job's time is the maximum over ranks and its work the sum."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms), float(units)
+    t_max = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    t_sum = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t_sum, op=dist.ReduceOp.SUM)
+    return float(t_max.item()), float(t_sum.item())
 
 
 class Clocks:
@@ -164,14 +183,9 @@ def run_gpu(args):
     ms = ev0.elapsed_time(ev1)
     clocks = clk.stop()
     if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-        sw = torch.tensor([total_sweeps], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(sw)
-        total_sweeps_all = float(sw.item())
-    else:
-        total_sweeps_all = float(total_sweeps)
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ms, total_sweeps_all = reduce_over_ranks(ms, total_sweeps, "cuda")
     value = total_sweeps_all / (ms / 1e3)
 
     # end to end through the C ABI with host (pinned) buffers: A copied in and
@@ -333,10 +347,218 @@ def run_sweep_only(args):
                       "GB/s": round(nbytes / (ms / 1e3) / 1e9, 1)}), flush=True)
 
 
+def _event_ms(stream, fn, reps):
+    """Mean milliseconds of fn() over reps runs (CUDA events on `stream`)."""
+    import torch
+
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = None
+    for _ in range(reps):
+        out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps, out
+
+
+def _base_line(metric, unit, value, ms_per_step, args, workload, dtype, extra):
+    line = {"metric": metric, "value": round(value, 3), "unit": unit, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "config": {"workload": workload}}
+    line.update(extra)
+    return line
+
+
+def run_gamma_path(args):
+    """Sparsity path: 64 gamma values log-spaced over [0.001, 0.5] max||a_i||,
+    single-unit L1 and L0 on a 10000 x 50000 FP32 planted-spike A (3 spikes,
+    2% supports), as one batched solve (all 64 columns advance in every
+    sweep) against 64 separate solves; plus block L1 with m = 32.  Units:
+    solve-iterations (one gamma value, one sweep) per second."""
+    import numpy as np
+    import torch
+
+    from paper_1312_6182_gb300 import binding, synth
+
+    p, n = 10000, 50000
+    At = synth.workload_spikes_10000x50000(1)
+    dA = torch.from_numpy(At).cuda()
+    del At
+    rho = [float(r) for r in synth.log_spaced_rho(64)]
+    stream = torch.cuda.Stream()
+    ctx = binding.Context(0, stream=stream)
+    res = {}
+    clk = Clocks(0)
+    for form in ("SL1", "SL0"):
+        out = binding.alloc_result(64, p, n, "cuda", torch.float32)
+        one = binding.alloc_result(1, p, n, "cuda", torch.float32)
+        for _ in range(args.warmup):
+            ctx.solve(dA, form, rho, gamma_relative=True, out=out)
+        if form == "SL1":
+            clk.start()
+        ms_b, r = _event_ms(stream, lambda: ctx.solve(dA, form, rho, gamma_relative=True, out=out), args.steps)
+        if form == "SL1":
+            clocks = clk.stop()
+        it_b = int(r.iters.sum().item())
+        sweeps_b = int(r.iters.max().item())
+
+        def separate():
+            tot = 0
+            for g in rho:
+                rr = ctx.solve(dA, form, [g], gamma_relative=True, out=one)
+                tot += int(rr.iters.item())
+            return tot
+
+        separate()
+        ms_s, it_s = _event_ms(stream, separate, 1)
+        res[form] = {"batched_iters_per_s": round(it_b / (ms_b / 1e3), 1), "batched_ms_per_solve": round(ms_b, 3),
+                     "batched_sweeps": sweeps_b, "separate_iters_per_s": round(it_s / (ms_s / 1e3), 1),
+                     "separate_ms_for_64": round(ms_s, 3), "iters_sum": it_b,
+                     "speedup_batched_vs_separate": round(ms_s / ms_b, 2)}
+    # block L1, m = 32, mu = 1 on the same A; gamma = 0.01 max||a_i|| (with
+    # only 3 spikes, larger gammas threshold whole noise components away)
+    rho32 = [RHO32] * 32
+    out32 = binding.alloc_result(32, p, n, "cuda", torch.float32)
+    for _ in range(args.warmup):
+        ctx.solve(dA, "BL1", rho32, mu=[1.0] * 32, gamma_relative=True, out=out32)
+    ms_32, r32 = _event_ms(stream, lambda: ctx.solve(dA, "BL1", rho32, mu=[1.0] * 32, gamma_relative=True,
+                                                    out=out32), max(1, args.steps // 2))
+    res["BL1_m32"] = {"iters_per_s": round(int(r32.iters.max().item()) / (ms_32 / 1e3), 1),
+                      "ms_per_solve": round(ms_32, 3), "iters": int(r32.iters.max().item()),
+                      "status": sorted(set(int(v) for v in r32.status.tolist())), "rho": RHO32}
+    # the sweep of the 64-column batch alone: one read of A is the algorithmic minimum
+    ms_sw = ctx.time_sweep(dA, "SL1", rho, gamma_relative=True, reps=10)
+    ms_sw32 = ctx.time_sweep(dA, "BL1", rho32, mu=[1.0] * 32, gamma_relative=True, reps=10)
+    peak, kind = _peaks()
+    nbytes = p * n * 4
+    flops = 4.0 * p * n * 64
+    ctx.close()
+    value = res["SL1"]["batched_iters_per_s"]
+    line = _base_line("gamma-path solve-iters/s (64 gammas batched)", "iters/s", value,
+                      res["SL1"]["batched_ms_per_solve"], args,
+                      "planted spikes 10000x50000 fp32 (3 spikes, theta_j=40/j, 2% supports), 64 gammas log-spaced "
+                      "[0.001,0.5]*max||a_i||, SL1/SL0 batched vs separate; BL1 m=32 gamma=0.01*max||a_i||", "f32",
+                      {"results": res,
+                       "roofline": {"bound": "hbm", "kernel": "sweep_kernel<float,8,*> x 8 passes (64 columns)",
+                                    "achieved": round(nbytes / (ms_sw / 1e3) / 1e9, 1), "peak": peak,
+                                    "unit": "GB/s", "frac": round(nbytes / (ms_sw / 1e3) / 1e9 / peak, 4),
+                                    "peak_source": kind, "traffic": None, "ms_per_sweep": round(ms_sw, 4),
+                                    "algorithmic_bytes_per_sweep": nbytes,
+                                    "tflops_achieved": round(flops / (ms_sw / 1e3) / 1e12, 2)},
+                       "block_m32_sweep_ms": round(ms_sw32, 4), "clocks": clocks})
+    print(json.dumps(line), flush=True)
+
+
+def _fp8_columns(dA32):
+    """FP8 E4M3 storage with per-column scales s_i = max_r |A_ri| / 448."""
+    import torch
+
+    s = dA32.abs().amax(dim=1) / 448.0
+    s = torch.where(s > 0, s, torch.ones_like(s))
+    q = (dA32 / s[:, None]).to(torch.float8_e4m3fn)
+    return q, s.float().contiguous()
+
+
+def run_precision(args):
+    """Precision path: block L1 and L0, m = 16, on a 20000 x 100000
+    planted-spike A (16 spikes, 1% supports, theta_j = 100/sqrt j) stored in
+    BF16 and in FP8 E4M3 with per-column scales, each solved to convergence
+    and then refined by 3 FP32 sweeps from the converged X on the FP32 copy;
+    against the plain FP32 solve.  With --oracle, errors of every variant
+    against the FP64 oracle on the FP32 matrix (objective, loadings, support)."""
+    import numpy as np
+    import torch
+
+    from paper_1312_6182_gb300 import binding, synth
+
+    p, n, m = 20000, 100000, 16
+    At = synth.workload_spikes_20000x100000(2)
+    d32 = torch.from_numpy(At).cuda()
+    if not args.oracle:
+        del At
+    dbf = d32.to(torch.bfloat16)
+    d8, s8 = _fp8_columns(d32)
+    stream = torch.cuda.Stream()
+    ctx = binding.Context(0, stream=stream)
+    mu = [1.0] * m
+    out = binding.alloc_result(m, p, n, "cuda", torch.float32)
+    out2 = binding.alloc_result(m, p, n, "cuda", torch.float32)
+    res = {}
+    keep = {}
+    clk = Clocks(0)
+    clocks = None
+    for form in ("BL1", "BL0"):
+        for fmt, dA, cs in (("f32", d32, None), ("bf16", dbf, None), ("fp8", d8, s8)):
+            def solve():
+                return ctx.solve(dA, form, [0.05] * m, mu=mu, gamma_relative=True, out=out, col_scale=cs)
+
+            for _ in range(args.warmup):
+                solve()
+            if clocks is None:
+                clk.start()
+            ms, r = _event_ms(stream, solve, max(1, args.steps // 4))
+            if clocks is None:
+                clocks = clk.stop()
+            iters = int(r.iters.max().item())
+            entry = {"ms_per_solve": round(ms, 3), "iters": iters, "iters_per_s": round(iters / (ms / 1e3), 1)}
+            if fmt != "f32":
+                x0 = r.X.contiguous().clone()
+
+                def refine():
+                    return ctx.solve(d32, form, [0.05] * m, mu=mu, gamma_relative=True, tol=0.0, maxit=3, x0=x0,
+                                     out=out2)
+
+                ms_r, rr = _event_ms(stream, refine, max(1, args.steps // 4))
+                entry["refine_ms"] = round(ms_r, 3)
+                entry["ms_total"] = round(ms + ms_r, 3)
+                keep[(form, fmt)] = {k: getattr(rr, k).clone() for k in ("X", "Z", "objective", "support")}
+            else:
+                entry["ms_total"] = round(ms, 3)
+                keep[(form, fmt)] = {k: getattr(r, k).clone() for k in ("X", "Z", "objective", "support")}
+            entry["solves_per_s"] = round(1e3 / entry["ms_total"], 2)
+            res[f"{form}_{fmt}"] = entry
+    sweep_ms = {fmt: ctx.time_sweep(dA, "BL1", [0.05] * m, mu=mu, gamma_relative=True, reps=5, col_scale=cs)
+                for fmt, dA, cs in (("f32", d32, None), ("bf16", dbf, None), ("fp8", d8, s8))}
+    ctx.close()
+    if args.oracle:
+        import oracle
+
+        A64 = At.astype(np.float64).T
+        del At
+        for form in ("BL1", "BL0"):
+            gam = oracle.gamma_from_rho(A64, form, [0.05] * m)
+            ref = oracle.gpower(A64, form, gam, mu=np.array(mu), tol=1e-6, maxit=1000)
+            for fmt in ("f32", "bf16", "fp8"):
+                g = keep[(form, fmt)]
+                Z = g["Z"].double().cpu().numpy().T
+                zerr = [float(np.linalg.norm(Z[:, j] - ref.Z[:, j]) / max(np.linalg.norm(ref.Z[:, j]), 1e-300))
+                        for j in range(m)]
+                ferr = abs(float(g["objective"].sum().item()) - ref.total) / ref.total
+                sup = (Z != 0) != (ref.Z != 0)
+                res[f"{form}_{fmt}"]["oracle"] = {"loadings_rel_err_max": max(zerr), "objective_rel_err": ferr,
+                                                 "support_mismatches": int(sup.sum()), "oracle_iters": int(ref.iters[0])}
+    peak, kind = _peaks()
+    bytes_of = {"f32": p * n * 4, "bf16": p * n * 2, "fp8": p * n + n * 4}
+    roof = {fmt: {"ms_per_sweep": round(ms_, 4), "GB/s": round(bytes_of[fmt] / (ms_ / 1e3) / 1e9, 1),
+                  "frac": round(bytes_of[fmt] / (ms_ / 1e3) / 1e9 / peak, 4)} for fmt, ms_ in sweep_ms.items()}
+    value = res["BL1_bf16"]["solves_per_s"]
+    line = _base_line("precision-path solves/s (BF16 + 3 FP32 refinement sweeps)", "solves/s", value,
+                      res["BL1_bf16"]["ms_total"], args,
+                      "planted spikes 20000x100000 (16 spikes, theta_j=100/sqrt(j), 1% supports), BL1/BL0 m=16 mu=1, "
+                      "gamma=0.05*max||a_i||; BF16 and FP8-E4M3 (per-column scales) storage + 3 FP32 sweeps vs FP32",
+                      "bf16",
+                      {"results": res, "roofline": {"bound": "hbm", "peak": peak, "peak_source": kind, "unit": "GB/s",
+                                                    "sweeps_m16": roof}, "clocks": clocks})
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=None, help="timed steps (default 100; 4 for the other workloads)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--sweep-only", default=None, choices=["SL1", "SL0", "BL1", "BL0"],
@@ -344,9 +566,19 @@ def main():
     ap.add_argument("--sweep-m", type=int, default=5)
     ap.add_argument("--sweep-dtype", default="f32", choices=["f32", "bf16"])
     ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--workload", default="spikes5000", choices=["spikes5000", "gamma-path", "precision"],
+                    help="spikes5000: the headline step; the others measure the sparsity-path batch and the "
+                         "BF16/FP8 precision path (one JSON line each)")
+    ap.add_argument("--oracle", action="store_true", help="precision workload: errors against the FP64 oracle")
     args = ap.parse_args()
     if args.sweep_only:
         run_sweep_only(args)
+        return
+    if args.steps is None:
+        args.steps = 100 if args.workload == "spikes5000" else 4
+    if args.workload != "spikes5000":
+        args.warmup = max(args.warmup, 1)
+        {"gamma-path": run_gamma_path, "precision": run_precision}[args.workload](args)
         return
     if args.warmup < 3 and args.impl == "gpu":
         args.warmup = 3

@@ -123,13 +123,14 @@ constexpr int kSmemBudget = 200 * 1024;  // stage ring + bookkeeping, per CTA
 
 static const int kMGs[] = {1, 2, 4, 5, 8};
 
-// Components per pass: passes of 8, the last one the smallest built width.
-static std::vector<std::pair<int, int>> split_components(int m) {
+// Components per pass: passes of gmax (a built width), the last one the
+// smallest built width that holds the rest.
+static std::vector<std::pair<int, int>> split_components(int m, int gmax) {
   std::vector<std::pair<int, int>> out;  // (mg, valid)
   int rem = m;
   while (rem > 0) {
-    int mg = 8;
-    if (rem < 8)
+    int mg = gmax;
+    if (rem < gmax)
       for (int c : kMGs)
         if (c >= rem) { mg = c; break; }
     const int v = std::min(rem, mg);
@@ -185,29 +186,34 @@ int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fa
   pl.fast = fast ? 1 : 0;
   pl.tcsize = d.tcsize;
   pl.esize = d.esize;
-  const auto groups = split_components(m);
   const int unit = std::max(d.align, d.vec);
   bool found = false;
-  for (int C : {1, 2, 4, 8}) {
-    const int ps = static_cast<int>(((p + C - 1) / C + unit - 1) / unit * unit);
-    if (C > 1 && static_cast<int64_t>(C - 1) * ps >= p) break;
-    std::vector<Pass> passes;
-    bool ok = true;
-    int j0 = 0;
-    for (auto g : groups) {
-      Pass q;
-      if (!fit_pass(dt, g.first, C, ps, m, &q)) { ok = false; break; }
-      q.j0 = j0;
-      q.mgv = g.second;
-      j0 += g.second;
-      passes.push_back(q);
+  // widest passes first (fewest reads of A); long columns (large p) may only
+  // fit narrower passes, whose per-thread register tiles are smaller
+  for (int gmax : {8, 4, 2, 1}) {
+    const auto groups = split_components(m, gmax);
+    for (int C : {1, 2, 4, 8}) {
+      const int ps = static_cast<int>(((p + C - 1) / C + unit - 1) / unit * unit);
+      if (C > 1 && static_cast<int64_t>(C - 1) * ps >= p) break;
+      std::vector<Pass> passes;
+      bool ok = true;
+      int j0 = 0;
+      for (auto g : groups) {
+        Pass q;
+        if (!fit_pass(dt, g.first, C, ps, m, &q)) { ok = false; break; }
+        q.j0 = j0;
+        q.mgv = g.second;
+        j0 += g.second;
+        passes.push_back(q);
+      }
+      if (!ok) continue;
+      pl.C = C;
+      pl.ps = ps;
+      pl.passes = passes;
+      found = true;
+      break;
     }
-    if (!ok) continue;
-    pl.C = C;
-    pl.ps = ps;
-    pl.passes = passes;
-    found = true;
-    break;
+    if (found) break;
   }
   if (!found) return fail(GPSPCA_EINVAL, "no sweep configuration fits p=%lld (rows too long for the on-chip tile ring)", (long long)p);
   // clusters: as many as can be co-resident for the heaviest pass
