@@ -555,6 +555,127 @@ def run_precision(args):
     print(json.dumps(line), flush=True)
 
 
+def _pct(xs, q):
+    import numpy as np
+
+    return float(np.percentile(np.asarray(xs, dtype=np.float64), q)) if len(xs) else None
+
+
+def run_serving(args):
+    """Serving: the request mix (Poisson arrivals at 200/s; p, n log-uniform
+    over [256, 8192] x [1024, 65536]; FP32 or BF16; the four forms; m in
+    1..16; rho ~ U(0.02, 0.2)); each request's planted-spike A is drawn on
+    the device (seed 1000 + id, timed as ingest) and submitted to the
+    context's continuous-batching scheduler (admission by workspace under a
+    150 GB budget, up to 8 solves overlapping).  Reported: served solves/s
+    and p50/p99 latency at the offered load, the saturated throughput, and the
+    serial plain per-request solves on the same requests (their latency at the
+    same arrivals from a single-server FIFO queue)."""
+    import numpy as np
+    import torch
+
+    from paper_1312_6182_gb300 import binding, synth
+
+    reqs = synth.serving_requests(count=args.requests, rate=200.0, seed=3)
+    gen_stream = torch.cuda.Stream()
+    ctx = binding.Context(0, budget_bytes=150 << 30)
+
+    def make_input(r):
+        tdt = torch.float32 if r.dtype == "f32" else torch.bfloat16
+        A = torch.empty((r.n, r.p), device="cuda", dtype=tdt)
+        binding.synth_spikes(A, max(r.m, 1), r.theta(), 0.05, r.seed, stream=gen_stream)
+        gen_stream.synchronize()
+        return A
+
+    def mu_of(r):
+        return [1.0] * r.m if r.form.startswith("B") else None
+
+    def serve(use_arrivals):
+        lat, lat_solve, ingest, results = [], [], [], {}
+        pending = {}
+        i, t0 = 0, time.perf_counter()
+        while i < len(reqs) or pending:
+            now = time.perf_counter() - t0
+            if i < len(reqs) and (not use_arrivals or reqs[i].arrival_s <= now) and len(pending) < 64:
+                r = reqs[i]
+                t_in = time.perf_counter()
+                A = make_input(r)
+                t_ready = time.perf_counter()
+                ingest.append(t_ready - t_in)
+                t, out = ctx.submit(A, r.form, r.gammas(), mu=mu_of(r), tol=TOL, maxit=MAXIT, gamma_relative=True)
+                pending[t] = (r, A, out, t0 + (r.arrival_s if use_arrivals else 0.0), t_ready)
+                i += 1
+                continue
+            idle = i >= len(reqs) or len(pending) >= 64 or (use_arrivals and reqs[i].arrival_s > now)
+            first = True
+            for t in list(pending):
+                # when there is nothing to submit, wait up to 20 us on the oldest request
+                rc = ctx.poll(t, 20 if (idle and first) else 0)
+                first = False
+                if rc == binding.PENDING:
+                    continue
+                tc = time.perf_counter()
+                r, A, out, t_arr, t_ready = pending.pop(t)
+                if rc not in (binding.OK, binding.EDEGENERATE):
+                    raise RuntimeError(f"request {r.id} failed: {rc} {binding.last_error()}")
+                lat.append(tc - t_arr)
+                lat_solve.append(tc - t_ready)
+                results[r.id] = out
+        return time.perf_counter() - t0, lat, lat_solve, ingest, results
+
+    # warm-up: a few requests through both paths (graph builds for common shapes are per shape)
+    for r in reqs[: args.warmup]:
+        A = make_input(r)
+        ctx.solve(A, r.form, r.gammas(), mu=mu_of(r), tol=TOL, maxit=MAXIT, gamma_relative=True)
+    clk = Clocks(0)
+    clk.start()
+    span, lat, lat_solve, ingest, served = serve(True)
+    clocks = clk.stop()
+    span_sat, lat_sat, _, _, _ = serve(False)
+    # serial plain per-request solves on the same requests
+    svc, serial_out = [], {}
+    sample = set(range(0, len(reqs), max(1, len(reqs) // 20)))
+    for r in reqs:
+        A = make_input(r)
+        torch.cuda.synchronize()
+        t_a = time.perf_counter()
+        res = ctx.solve(A, r.form, r.gammas(), mu=mu_of(r), tol=TOL, maxit=MAXIT, gamma_relative=True)
+        svc.append(time.perf_counter() - t_a)
+        if r.id in sample:
+            serial_out[r.id] = res
+    # the same results alone and in the mix
+    same = sum(1 for k, v in serial_out.items()
+               if torch.equal(v.Z, served[k].Z) and torch.equal(v.objective, served[k].objective))
+    # single-server FIFO latency of the serial path at the same arrivals (Lindley)
+    free_at, lat_serial = 0.0, []
+    for r, sv in zip(reqs, svc):
+        start = max(r.arrival_s, free_at)
+        free_at = start + sv
+        lat_serial.append(free_at - r.arrival_s)
+    ctx.close()
+    nreq = len(reqs)
+    line = _base_line("served solves/s", "solves/s", nreq / span, span * 1e3 / nreq, args,
+                      f"serving mix: {nreq} requests, Poisson 200/s, p in [256,8192], n in [1024,65536] "
+                      "log-uniform, fp32|bf16, SL1|SL0|BL1|BL0, m 1..16, rho U(0.02,0.2), device-generated "
+                      "planted spikes (Philox4x32-10, seed 1000+id)", "f32|bf16",
+                      {"serving": {
+                          "offered_rate": 200.0, "requests": nreq,
+                          "served_solves_per_s": round(nreq / span, 2),
+                          "p50_ms": round(_pct(lat, 50) * 1e3, 3), "p99_ms": round(_pct(lat, 99) * 1e3, 3),
+                          "p50_solve_ms": round(_pct(lat_solve, 50) * 1e3, 3),
+                          "p99_solve_ms": round(_pct(lat_solve, 99) * 1e3, 3),
+                          "ingest_ms_mean": round(float(np.mean(ingest)) * 1e3, 4),
+                          "saturated_solves_per_s": round(nreq / span_sat, 2),
+                          "saturated_p50_ms": round(_pct(lat_sat, 50) * 1e3, 3),
+                          "serial_solves_per_s": round(nreq / sum(svc), 2),
+                          "serial_p50_ms_at_offered": round(_pct(lat_serial, 50) * 1e3, 3),
+                          "serial_p99_ms_at_offered": round(_pct(lat_serial, 99) * 1e3, 3),
+                          "same_alone_and_in_mix": f"{same}/{len(serial_out)}",
+                          "mean_p_times_n": float(np.mean([r.p * r.n for r in reqs]))},
+                       "clocks": clocks})
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -566,10 +687,11 @@ def main():
     ap.add_argument("--sweep-m", type=int, default=5)
     ap.add_argument("--sweep-dtype", default="f32", choices=["f32", "bf16"])
     ap.add_argument("--reps", type=int, default=20)
-    ap.add_argument("--workload", default="spikes5000", choices=["spikes5000", "gamma-path", "precision"],
+    ap.add_argument("--workload", default="spikes5000", choices=["spikes5000", "gamma-path", "precision", "serving"],
                     help="spikes5000: the headline step; the others measure the sparsity-path batch and the "
                          "BF16/FP8 precision path (one JSON line each)")
     ap.add_argument("--oracle", action="store_true", help="precision workload: errors against the FP64 oracle")
+    ap.add_argument("--requests", type=int, default=2000, help="serving workload: number of requests")
     args = ap.parse_args()
     if args.sweep_only:
         run_sweep_only(args)
@@ -578,7 +700,7 @@ def main():
         args.steps = 100 if args.workload == "spikes5000" else 4
     if args.workload != "spikes5000":
         args.warmup = max(args.warmup, 1)
-        {"gamma-path": run_gamma_path, "precision": run_precision}[args.workload](args)
+        {"gamma-path": run_gamma_path, "precision": run_precision, "serving": run_serving}[args.workload](args)
         return
     if args.warmup < 3 and args.impl == "gpu":
         args.warmup = 3

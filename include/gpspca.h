@@ -200,6 +200,22 @@ int gpspca_time_sweep(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form,
  * arrays' device addresses (cudaGetSymbolAddress); make it before any
  * stream capture.  No cudaMalloc, cudaFree or allocating library routine is
  * called. */
+/* Seeded synthetic input (not part of the method): a planted-spike matrix
+ * drawn on the device, for workloads whose requests bring their own data
+ * (the serving benchmark).  Writes A (p x n, column-major, leading dimension
+ * ld >= p; float32 or bfloat16, device memory At) with
+ *   A[r, i] = z_ri + [column i in the support of spike j] s_i theta_j/sqrt(s) u_j[r],
+ * z and u_j standard normal, j < k <= 64 spikes on disjoint supports of
+ * expected size s = max(1, round(support_frac * n)) (k * support_frac <= 1),
+ * Rademacher signs s_i.  Every value comes from Philox4x32-10 (Salmon et al.,
+ * SC'11) under key = seed, with Box-Muller in float32: noise rows 4b..4b+3 of
+ * column i from counter (b, i_lo, i_hi, 0), u_j rows from (b, j, 0, 1), the
+ * spike and sign of column i from words 0 and 1 of (i_lo, i_hi, 0, 2).
+ * theta: host array of k values.  Asynchronous on cuda_stream.  Returns
+ * GPSPCA_OK or GPSPCA_EINVAL / GPSPCA_ECUDA. */
+int gpspca_synth_spikes(void* At, gpspca_dtype dtype, int64_t p, int64_t n, int64_t ld, int32_t k,
+                        const double* theta, double support_frac, uint64_t seed, void* cuda_stream);
+
 int gpspca_sweep_static(const gpspca_matrix* A, gpspca_form form, double gamma, const float* x, float* x_next,
                         float* t, double* objective, void* cuda_stream);
 

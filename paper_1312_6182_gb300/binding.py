@@ -37,7 +37,7 @@ ERROR_NAMES = {
 }
 
 EXPORTED = ("gpspca_create", "gpspca_solve", "gpspca_submit", "gpspca_poll", "gpspca_destroy",
-            "gpspca_last_error", "gpspca_time_sweep", "gpspca_sweep_static")
+            "gpspca_last_error", "gpspca_time_sweep", "gpspca_sweep_static", "gpspca_synth_spikes")
 
 
 class Matrix(ctypes.Structure):
@@ -98,6 +98,9 @@ def load(path: str = LIB_PATH):
     lib.gpspca_time_sweep.restype = ctypes.c_int
     lib.gpspca_sweep_static.argtypes = [ctypes.POINTER(Matrix), ctypes.c_int, ctypes.c_double, P, P, P, P, P]
     lib.gpspca_sweep_static.restype = ctypes.c_int
+    lib.gpspca_synth_spikes.argtypes = [P, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
+                                        D, ctypes.c_double, ctypes.c_uint64, P]
+    lib.gpspca_synth_spikes.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -319,4 +322,22 @@ def sweep_static(At, form: str, gamma: float, x, x_next, t, objective, p: Option
         handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
     rc = lib.gpspca_sweep_static(ctypes.byref(M), FORMS[form], float(gamma), x.data_ptr(), x_next.data_ptr(),
                                  t.data_ptr(), objective.data_ptr(), handle)
+    return _check(rc)
+
+
+def synth_spikes(At, k: int, theta, support_frac: float, seed: int, p: Optional[int] = None, stream=None) -> int:
+    """Fill the float32 / bfloat16 CUDA tensor At (n, ld) with the seeded
+    planted-spike matrix of gpspca_synth_spikes (rows = columns of A).
+    Asynchronous on `stream` (a torch.cuda.Stream; default: the current one)."""
+    import torch
+
+    lib = load()
+    n, ld = At.shape
+    p = ld if p is None else int(p)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    rc = lib.gpspca_synth_spikes(At.data_ptr(), _dtype_code(At), int(p), int(n), int(At.stride(0)), int(k),
+                                 _darr(theta, k) if k > 0 else None, float(support_frac), int(seed) & (2**64 - 1),
+                                 handle)
     return _check(rc)

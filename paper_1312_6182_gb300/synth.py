@@ -120,3 +120,148 @@ def workload_spikes_20000x100000(seed: int = 2, p: int = 20000, n: int = 100000,
 def log_spaced_rho(count: int = 64, lo: float = 1e-3, hi: float = 0.5) -> np.ndarray:
     """``count`` relative sparsity values log-spaced over [lo, hi]."""
     return np.geomspace(lo, hi, count)
+
+
+# ---------------------------------------------------------------- counter-based generator
+#
+# Per-request matrices of the serving workload are drawn on the device by a
+# counter-based generator so that no host-side RNG or copy sits in the
+# request path; this is its NumPy twin (same counters, same float32
+# arithmetic), used to regenerate any request's A on the host.
+#
+# Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
+# easy as 1, 2, 3", SC'11): a 4 x 32-bit counter and a 2 x 32-bit key; ten
+# rounds, each multiplying words 0 and 2 by fixed constants (high and low
+# halves of the 64-bit products) and mixing in the key, which is bumped by
+# two Weyl constants between rounds.
+
+PHILOX_M0, PHILOX_M1 = 0xD2511F53, 0xCD9E8D57
+PHILOX_W0, PHILOX_W1 = 0x9E3779B9, 0xBB67AE85
+TWO_PI_F32 = np.float32(6.2831855)
+
+
+def philox4x32_10(c0, c1, c2, c3, k0: int, k1: int):
+    """Philox4x32-10 of the counters (c0, c1, c2, c3) (uint32 arrays or
+    scalars, broadcast) under key (k0, k1); returns four uint32 arrays."""
+    c = [np.asarray(x, dtype=np.uint32) for x in (c0, c1, c2, c3)]
+    c = list(np.broadcast_arrays(*c))
+    k0 &= 0xFFFFFFFF
+    k1 &= 0xFFFFFFFF
+    m0, m1 = np.uint64(PHILOX_M0), np.uint64(PHILOX_M1)
+    lo_mask, sh = np.uint64(0xFFFFFFFF), np.uint64(32)
+    for _ in range(10):
+        p0 = m0 * c[0].astype(np.uint64)
+        p1 = m1 * c[2].astype(np.uint64)
+        hi0, lo0 = (p0 >> sh).astype(np.uint32), (p0 & lo_mask).astype(np.uint32)
+        hi1, lo1 = (p1 >> sh).astype(np.uint32), (p1 & lo_mask).astype(np.uint32)
+        c = [hi1 ^ c[1] ^ np.uint32(k0), lo1, hi0 ^ c[3] ^ np.uint32(k1), lo0]
+        k0 = (k0 + PHILOX_W0) & 0xFFFFFFFF
+        k1 = (k1 + PHILOX_W1) & 0xFFFFFFFF
+    return c
+
+
+def _uniform23(w):
+    """uint32 -> float32 in (0, 1): the top 23 bits plus one half, times 2^-23
+    (exact in float32, so 0 and 1 are never returned)."""
+    return ((w >> np.uint32(9)).astype(np.float32) + np.float32(0.5)) * np.float32(2.0 ** -23)
+
+
+def _box_muller(w0, w1, w2, w3):
+    """Four N(0,1) float32 values from four words (Box-Muller on two pairs)."""
+    out = []
+    for a, b in ((w0, w1), (w2, w3)):
+        u1, u2 = _uniform23(a), _uniform23(b)
+        rad = np.sqrt(np.float32(-2.0) * np.log(u1)).astype(np.float32)
+        ang = (TWO_PI_F32 * u2).astype(np.float32)
+        out += [(rad * np.cos(ang)).astype(np.float32), (rad * np.sin(ang)).astype(np.float32)]
+    return out
+
+
+def spike_coefficients(k: int, theta, support_frac: float, n: int) -> np.ndarray:
+    """theta_j / sqrt(s) in float32, s = max(1, round(support_frac * n)) the
+    expected support size (the scale both generators use)."""
+    s = max(1, int(round(support_frac * n)))
+    return (np.asarray(theta, dtype=np.float64)[:k] / np.sqrt(s)).astype(np.float32)
+
+
+def counter_spikes(p: int, n: int, k: int, theta, support_frac: float, seed: int, dtype=np.float32):
+    """The device generator's matrix, on the host: At (n x p).
+
+    Entry (r, i) = noise + [i in support of spike j] sign_i theta_j/sqrt(s) u_j[r]:
+    * noise: rows 4b..4b+3 of column i from counter (b, i_lo, i_hi, 0);
+    * u_j: rows 4b..4b+3 from counter (b, j, 0, 1);
+    * column i's spike: counter (i_lo, i_hi, 0, 2), word 0 as a uniform v,
+      j = floor(v / support_frac) if below k (disjoint supports of expected
+      size support_frac n), sign from the top bit of word 1;
+    key = (seed_lo, seed_hi).  float32 arithmetic, products and sums
+    rounded separately; bfloat16 output rounds to nearest even."""
+    P4 = (p + 3) // 4
+    k0, k1 = seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF
+    i = np.arange(n, dtype=np.uint64)
+    ilo, ihi = (i & np.uint64(0xFFFFFFFF)).astype(np.uint32), (i >> np.uint64(32)).astype(np.uint32)
+    b = np.arange(P4, dtype=np.uint32)
+    w = philox4x32_10(b[None, :], ilo[:, None], ihi[:, None], np.uint32(0), k0, k1)
+    z = _box_muller(*w)  # each n x P4
+    At = np.stack(z, axis=2).reshape(n, 4 * P4)[:, :p].astype(np.float32)
+    sw = philox4x32_10(ilo, ihi, np.uint32(0), np.uint32(2), k0, k1)
+    v = _uniform23(sw[0])
+    j = np.floor(v / np.float32(support_frac)).astype(np.int64) if support_frac > 0 else np.full(n, k)
+    sign = np.where(sw[1] >> np.uint32(31), np.float32(-1.0), np.float32(1.0)).astype(np.float32)
+    coef = spike_coefficients(k, theta, support_frac, n)
+    for jj in range(k):
+        cols = np.nonzero(j == jj)[0]
+        if cols.size == 0:
+            continue
+        uw = philox4x32_10(b, np.uint32(jj), np.uint32(0), np.uint32(1), k0, k1)
+        u = np.stack(_box_muller(*uw), axis=1).reshape(4 * P4)[:p].astype(np.float32)
+        c = (coef[jj] * sign[cols]).astype(np.float32)
+        At[cols] = (At[cols] + (c[:, None] * u[None, :]).astype(np.float32)).astype(np.float32)
+    if dtype == "bf16":
+        bits = At.view(np.uint32)
+        rnd = (bits + np.uint32(0x7FFF) + ((bits >> np.uint32(16)) & np.uint32(1))) & np.uint32(0xFFFF0000)
+        return rnd.view(np.float32)  # bfloat16 values, held in float32
+    return np.ascontiguousarray(At)
+
+
+@dataclass
+class Request:
+    """One request of the serving mix."""
+
+    id: int
+    arrival_s: float
+    p: int
+    n: int
+    dtype: str  # "f32" or "bf16"
+    form: str
+    m: int
+    rho: float
+    seed: int
+
+    def gammas(self):
+        """Relative gammas: one per component (block), or for single-unit
+        forms a path of m values linearly spaced over [rho/2, rho]."""
+        if self.form.startswith("B") or self.m == 1:
+            return [self.rho] * self.m
+        return [self.rho * (0.5 + 0.5 * j / (self.m - 1)) for j in range(self.m)]
+
+    def theta(self):
+        k = max(self.m, 1)
+        return [40.0 / (j + 1) for j in range(k)]
+
+
+def serving_requests(count: int = 2000, rate: float = 200.0, seed: int = 3):
+    """The serving mix: Poisson arrivals at `rate`, p and n log-uniform over
+    [256, 8192] and [1024, 65536], FP32 or BF16, the four forms, m in 1..16,
+    rho ~ U(0.02, 0.2); request i's matrix has seed 1000 + i."""
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, size=count)
+    arr = np.cumsum(gaps) - gaps[0]
+    ps = np.round(np.exp(rng.uniform(np.log(256), np.log(8192), size=count))).astype(int)
+    ns = np.round(np.exp(rng.uniform(np.log(1024), np.log(65536), size=count))).astype(int)
+    dts = rng.integers(0, 2, size=count)
+    forms = rng.integers(0, 4, size=count)
+    ms = rng.integers(1, 17, size=count)
+    rhos = rng.uniform(0.02, 0.2, size=count)
+    names = ["SL1", "SL0", "BL1", "BL0"]
+    return [Request(i, float(arr[i]), int(ps[i]), int(ns[i]), "bf16" if dts[i] else "f32", names[forms[i]],
+                    int(ms[i]), float(rhos[i]), 1000 + i) for i in range(count)]
