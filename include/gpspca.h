@@ -82,6 +82,8 @@ typedef enum { GPSPCA_DEVICE = 0, GPSPCA_HOST = 1 } gpspca_location;
                                      instead of the cached CUDA graph with its device-side WHILE
                                      node: for profilers and debuggers that cannot follow
                                      conditional graph nodes.  Results are identical. */
+#define GPSPCA_NO_TENSOR_CORES 4u /* run the CUDA-core fused sweep even where the tensor-core
+                                     (tcgen05) sweep applies (bf16 storage, m >= 16) */
 
 /* Largest m (components, or gamma values of a path) one solve accepts. */
 #define GPSPCA_MAX_M 64
@@ -146,7 +148,7 @@ int gpspca_create(gpspca_ctx** ctx, int device, size_t hbm_budget_bytes, void* c
  *           for block forms, the PCA start: a seeded Rademacher sketch of m
  *           columns (SplitMix64, seed 0x5EED5EED5EED5EED), two projected
  *           power steps with A A^T and a Rayleigh-Ritz rotation
- *   flags   GPSPCA_GAMMA_RELATIVE | GPSPCA_EAGER, or 0
+ *   flags   GPSPCA_GAMMA_RELATIVE | GPSPCA_EAGER | GPSPCA_NO_TENSOR_CORES, or 0
  *   out     result buffers
  * Returns GPSPCA_OK, GPSPCA_EDEGENERATE (outputs valid, see status), or an
  * error code (outputs undefined). */

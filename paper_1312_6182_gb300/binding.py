@@ -29,6 +29,7 @@ EINVAL, ENOMEM, ENONFINITE, ETIMEDOUT, EDEGENERATE, ECUDA, ENOTFOUND = -1, -2, -
 CONVERGED, MAXIT, ZERO, DEGENERATE = 0, 1, 2, 3
 GAMMA_RELATIVE = 1
 EAGER = 2  # kernels launched one by one, host-driven loop (for profilers)
+NO_TENSOR_CORES = 4  # CUDA-core fused sweep even where the tensor-core sweep applies
 MAX_M = 64
 
 ERROR_NAMES = {
@@ -244,9 +245,11 @@ class Context:
 
     def solve(self, At, form: str, gamma, mu=None, tol: float = 1e-6, maxit: int = 1000, x0=None,
               gamma_relative: bool = False, p: Optional[int] = None, col_scale=None,
-              out: Optional[Result] = None, allow_degenerate: bool = True, eager: bool = False) -> Result:
+              out: Optional[Result] = None, allow_degenerate: bool = True, eager: bool = False,
+              tensor_cores: bool = True) -> Result:
         """One synchronous solve.  gamma: m values; mu: block weights.  eager: launch
-        the kernels one by one with a host-driven loop instead of the CUDA graph."""
+        the kernels one by one with a host-driven loop instead of the CUDA graph.
+        tensor_cores=False keeps the CUDA-core sweep where the tcgen05 one applies."""
         import torch
 
         gamma = [float(g) for g in (gamma if hasattr(gamma, "__len__") else [gamma])]
@@ -259,8 +262,8 @@ class Context:
         self._sync_torch(At, x0, out.X)
         rc = self.lib.gpspca_solve(self.ptr, ctypes.byref(M), FORMS[form], _darr(gamma, m), m, _darr(mu, m),
                                    float(tol), int(maxit), x0.data_ptr() if x0 is not None else None,
-                                   (GAMMA_RELATIVE if gamma_relative else 0) | (EAGER if eager else 0),
-                                   ctypes.byref(o))
+                                   (GAMMA_RELATIVE if gamma_relative else 0) | (EAGER if eager else 0)
+                                   | (0 if tensor_cores else NO_TENSOR_CORES), ctypes.byref(o))
         allow = (OK, EDEGENERATE) if allow_degenerate else (OK,)
         _check(rc, allow)
         out.rc = rc
@@ -291,7 +294,7 @@ class Context:
         return self.lib.gpspca_poll(self.ptr, ctypes.c_uint64(ticket), int(wait_us))
 
     def time_sweep(self, At, form: str, gamma, mu=None, reps: int = 20, gamma_relative: bool = False,
-                   p: Optional[int] = None, col_scale=None) -> float:
+                   p: Optional[int] = None, col_scale=None, tensor_cores: bool = True) -> float:
         """Mean milliseconds of one fused sweep (all component passes), CUDA events."""
         gamma = [float(g) for g in (gamma if hasattr(gamma, "__len__") else [gamma])]
         m = len(gamma)
@@ -299,7 +302,8 @@ class Context:
         self._sync_torch(At)
         ms = ctypes.c_double()
         _check(self.lib.gpspca_time_sweep(self.ptr, ctypes.byref(M), FORMS[form], _darr(gamma, m), m,
-                                          _darr(mu, m), GAMMA_RELATIVE if gamma_relative else 0, int(reps),
+                                          _darr(mu, m), (GAMMA_RELATIVE if gamma_relative else 0)
+                                          | (0 if tensor_cores else NO_TENSOR_CORES), int(reps),
                                           ctypes.byref(ms)))
         return ms.value
 

@@ -30,6 +30,7 @@
 
 #include "aux.cuh"
 #include "plan.h"
+#include "tc_sweep.cuh"
 
 namespace gpspca {
 
@@ -174,7 +175,35 @@ static bool fit_pass(int dt, int mg, int C, int ps, int m, Pass* out) {
   return false;
 }
 
-int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fast, int nsm, Plan* P) {
+// Tensor-core sweep geometry: T pass over 128-column tiles, Y pass over
+// 128-row blocks with the columns split so that the grid fills whole waves.
+static void plan_tc(Plan* pl, int m, int64_t p, int64_t n, int nsm) {
+  pl->tc = 1;
+  pl->mpad = (m + 15) / 16 * 16;
+  pl->npad = 3 * pl->mpad;
+  pl->p_pad = static_cast<int>((p + 7) / 8 * 8);
+  pl->n_pad = static_cast<int>((n + 7) / 8 * 8);
+  pl->ntile1 = static_cast<int>((n + kTcTile1 - 1) / kTcTile1);
+  pl->kchunks1 = static_cast<int>((p + kTcBK - 1) / kTcBK);
+  pl->nchunks2 = static_cast<int>((n + kTcBK - 1) / kTcBK);
+  pl->nrow2 = static_cast<int>((p + kTcRows2 - 1) / kTcRows2);
+  int best = 1;
+  double best_eff = 0.0;
+  for (int sp = 1; sp <= 16 && sp <= pl->nchunks2; ++sp) {
+    const int ctas = pl->nrow2 * sp;
+    const int waves = (ctas + nsm - 1) / nsm;
+    const double eff = static_cast<double>(ctas) / (static_cast<double>(waves) * nsm);
+    if (eff > best_eff + 0.02) {
+      best_eff = eff;
+      best = sp;
+    }
+  }
+  pl->kps2 = (pl->nchunks2 + best - 1) / best;
+  pl->nsplit2 = (pl->nchunks2 + pl->kps2 - 1) / pl->kps2;
+}
+
+int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fast, int nsm, Plan* P,
+              bool allow_tc) {
   const DInfo d = dinfo(dt);
   Plan pl;
   pl.dtype = dt;
@@ -188,9 +217,18 @@ int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fa
   pl.esize = d.esize;
   const int unit = std::max(d.align, d.vec);
   bool found = false;
+  // the tensor-core sweep: bf16 storage, 16 or more components (or gamma
+  // values), TMA-compatible layout (16-byte aligned base and column stride)
+  if (allow_tc && dt == GPSPCA_BF16 && m >= 16 && fast && ld % 8 == 0 && p >= 1 && n >= 1) {
+    plan_tc(&pl, m, p, n, nsm);
+    pl.C = 1;
+    pl.ps = static_cast<int>(p);
+    found = true;
+  }
   // widest passes first (fewest reads of A); long columns (large p) may only
   // fit narrower passes, whose per-thread register tiles are smaller
   for (int gmax : {8, 4, 2, 1}) {
+    if (found) break;
     const auto groups = split_components(m, gmax);
     for (int C : {1, 2, 4, 8}) {
       const int ps = static_cast<int>(((p + C - 1) / C + unit - 1) / unit * unit);
@@ -216,8 +254,9 @@ int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fa
     if (found) break;
   }
   if (!found) return fail(GPSPCA_EINVAL, "no sweep configuration fits p=%lld (rows too long for the on-chip tile ring)", (long long)p);
-  // clusters: as many as can be co-resident for the heaviest pass
-  int ncl = nsm / pl.C;
+  // clusters: as many as can be co-resident for the heaviest pass (the
+  // tensor-core sweep's Y-pass splits play their part)
+  int ncl = pl.tc ? pl.nsplit2 : nsm / pl.C;
   for (const Pass& q : pl.passes) {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
@@ -233,7 +272,7 @@ int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fa
     int nc = 0;
     if (cudaOccupancyMaxActiveClusters(&nc, q.k, &cfg) == cudaSuccess && nc > 0) ncl = std::min(ncl, nc);
   }
-  ncl = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ncl, n)));
+  if (!pl.tc) ncl = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ncl, n)));
   pl.ncl = ncl;
   pl.cols_per_cl = static_cast<int>((n + ncl - 1) / ncl);
   pl.nred = static_cast<int>((p + kReduceRows - 1) / kReduceRows);
@@ -247,6 +286,10 @@ int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fa
   pl.ws_T = static_cast<size_t>(d.tcsize) * m * n;
   pl.ws_fpart = sizeof(dd) * static_cast<size_t>(pl.nobj) * 2 * m;
   pl.ws_gpart = sizeof(double) * static_cast<size_t>(pl.nred) * pl.npairs;
+  if (pl.tc) {
+    pl.ws_x3 = 2 * static_cast<size_t>(pl.npad) * pl.p_pad;
+    pl.ws_g3 = 2 * static_cast<size_t>(pl.npad) * pl.n_pad;
+  }
   *P = pl;
   return GPSPCA_OK;
 }
@@ -277,7 +320,8 @@ struct Slot {
   cudaEvent_t done = nullptr;
   Budget* budget = nullptr;
   // workspace buffers, grown on demand
-  DevBuf b_cnorm, b_P, b_Y, b_ypart, b_T, b_fpart, b_gpart;
+  DevBuf b_cnorm, b_P, b_Y, b_ypart, b_T, b_fpart, b_gpart, b_x3, b_g3, b_maps;
+  TcMaps* maps_host = nullptr;  // pinned: the tensor maps copied to b_maps before a solve
   // staging for host-located inputs/outputs
   DevBuf s_A, s_scale, s_x0, s_X, s_Z, s_sup, s_obj, s_it, s_stat, s_gam;
   struct GraphEntry {
@@ -288,7 +332,8 @@ struct Slot {
 
   size_t held() const {
     size_t s = 0;
-    for (const DevBuf* b : {&b_cnorm, &b_P, &b_Y, &b_ypart, &b_T, &b_fpart, &b_gpart, &s_A, &s_scale, &s_x0, &s_X,
+    for (const DevBuf* b : {&b_cnorm, &b_P, &b_Y, &b_ypart, &b_T, &b_fpart, &b_gpart, &b_x3, &b_g3, &b_maps, &s_A,
+                            &s_scale, &s_x0, &s_X,
                             &s_Z, &s_sup, &s_obj, &s_it, &s_stat, &s_gam})
       s += b->bytes;
     return s;
@@ -331,7 +376,8 @@ static void release(Slot* s, DevBuf* b) {
 }
 
 static void release_workspace(Slot* s) {
-  for (DevBuf* b : {&s->b_cnorm, &s->b_P, &s->b_Y, &s->b_ypart, &s->b_T, &s->b_fpart, &s->b_gpart, &s->s_A,
+  for (DevBuf* b : {&s->b_cnorm, &s->b_P, &s->b_Y, &s->b_ypart, &s->b_T, &s->b_fpart, &s->b_gpart, &s->b_x3,
+                    &s->b_g3, &s->b_maps, &s->s_A,
                     &s->s_scale, &s->s_x0, &s->s_X, &s->s_Z, &s->s_sup, &s->s_obj, &s->s_it, &s->s_stat, &s->s_gam})
     release(s, b);
 }
@@ -351,6 +397,7 @@ static int slot_init(Slot* s, int device, cudaStream_t user_stream, Budget* budg
   GP_CUDA(cudaMalloc(&s->st_dev, sizeof(State)));
   GP_CUDA(cudaMallocHost(&s->io_host, sizeof(IO)));
   GP_CUDA(cudaMallocHost(&s->st_host, sizeof(State)));
+  GP_CUDA(cudaMallocHost(&s->maps_host, sizeof(TcMaps)));
   GP_CUDA(cudaEventCreateWithFlags(&s->done, cudaEventDisableTiming));
   return GPSPCA_OK;
 }
@@ -368,6 +415,7 @@ static void slot_free(Slot* s) {
   if (s->st_dev) cudaFree(s->st_dev);
   if (s->io_host) cudaFreeHost(s->io_host);
   if (s->st_host) cudaFreeHost(s->st_host);
+  if (s->maps_host) cudaFreeHost(s->maps_host);
   if (s->done) cudaEventDestroy(s->done);
   for (cudaStream_t c : {s->cap2, s->cap}) {  // never destroy a stream that is still capturing
     if (!c) continue;
@@ -422,6 +470,12 @@ static cudaError_t launch_prologue(const Plan& pl, Slot* s, cudaStream_t cs, cud
 }
 
 static cudaError_t launch_sweeps(const Plan& pl, Slot* s, cudaStream_t cs, int sketch) {
+  if (pl.tc) {
+    TcArgs a{s->io_dev, s->st_dev, pl.p, pl.n, pl.m, pl.mpad, pl.form, sketch, pl.p_pad, pl.n_pad,
+             pl.ntile1, pl.kchunks1, pl.nchunks2, pl.kps2, pl.nsplit2, pl.nrow2};
+    launch_tc_sweep(a, pl.npad, cs);
+    return cudaGetLastError();
+  }
   for (const Pass& q : pl.passes) {
     SweepArgs a{s->io_dev, s->st_dev, pl.ld, pl.p, pl.n, pl.m, pl.form, q.j0, q.mgv, pl.ps, q.W, q.S,
                 pl.cols_per_cl, pl.fast, sketch};
@@ -630,7 +684,8 @@ static int prepare_solve(Slot* s, const Request& r, int nsm, bool scratch_out, P
   }
   const bool fast = (reinterpret_cast<uintptr_t>(A_dev) % 16 == 0) && ((ld * d.esize) % 16 == 0);
   Plan& pl = *plan;
-  if ((rc = make_plan(r.A.dtype, r.form, m, p, n, ld, fast, nsm, &pl))) return rc;
+  const bool allow_tc = !(r.flags & GPSPCA_NO_TENSOR_CORES) && tc_supported(s->device);
+  if ((rc = make_plan(r.A.dtype, r.form, m, p, n, ld, fast, nsm, &pl, allow_tc))) return rc;
   pl.pca = (r.form >= GPSPCA_BL1 && !r.x0) ? 1 : 0;
   if ((rc = ensure(s, &s->b_cnorm, pl.ws_cnorm))) return rc;
   if ((rc = ensure(s, &s->b_P, pl.ws_P))) return rc;
@@ -639,6 +694,16 @@ static int prepare_solve(Slot* s, const Request& r, int nsm, bool scratch_out, P
   if ((rc = ensure(s, &s->b_T, pl.ws_T))) return rc;
   if ((rc = ensure(s, &s->b_fpart, pl.ws_fpart))) return rc;
   if ((rc = ensure(s, &s->b_gpart, pl.ws_gpart))) return rc;
+  if (pl.tc) {
+    if ((rc = ensure(s, &s->b_x3, pl.ws_x3))) return rc;
+    if ((rc = ensure(s, &s->b_g3, pl.ws_g3))) return rc;
+    if ((rc = ensure(s, &s->b_maps, sizeof(TcMaps)))) return rc;
+    // the host copy of the maps is reused only after this solve's copy has run
+    GP_CUDA(cudaStreamSynchronize(s->stream));
+    if ((rc = tc_encode_maps(s->maps_host, A_dev, p, n, ld, s->b_x3.p, pl.p_pad, s->b_g3.p, pl.n_pad, pl.npad)))
+      return rc;
+    GP_CUDA(cudaMemcpyAsync(s->b_maps.p, s->maps_host, sizeof(TcMaps), cudaMemcpyHostToDevice, s->stream));
+  }
   IO& io = *s->io_host;
   std::memset(&io, 0, sizeof(IO));
   io.A = A_dev;
@@ -676,6 +741,11 @@ static int prepare_solve(Slot* s, const Request& r, int nsm, bool scratch_out, P
   io.T = s->b_T.p;
   io.fpart = static_cast<dd*>(s->b_fpart.p);
   io.gpart = static_cast<double*>(s->b_gpart.p);
+  if (pl.tc) {
+    io.tc_x3 = s->b_x3.p;
+    io.tc_g3 = s->b_g3.p;
+    io.tc_maps = s->b_maps.p;
+  }
   for (int j = 0; j < m; ++j) {
     io.gamma_in[j] = r.gamma[j];
     io.mu[j] = r.mu[j];
@@ -747,7 +817,8 @@ static int request_from(Request* r, const gpspca_matrix* A, gpspca_form form, co
                         const double* mu, double tol, int32_t maxit, const void* x0, uint32_t flags,
                         gpspca_out* out) {
   if (!A || !out || !gamma) return fail(GPSPCA_EINVAL, "A, gamma and out must not be NULL");
-  if (flags & ~(GPSPCA_GAMMA_RELATIVE | GPSPCA_EAGER)) return fail(GPSPCA_EINVAL, "unknown flag bits 0x%x", flags);
+  if (flags & ~(GPSPCA_GAMMA_RELATIVE | GPSPCA_EAGER | GPSPCA_NO_TENSOR_CORES))
+    return fail(GPSPCA_EINVAL, "unknown flag bits 0x%x", flags);
   if (m < 1 || m > kMaxM) return fail(GPSPCA_EINVAL, "m = %d outside [1, %d]", m, kMaxM);
   r->A = *A;
   r->form = form;

@@ -33,6 +33,9 @@ struct IO {
   void* T;        // [m][n] dot products of the last sweep
   dd* fpart;      // [nobj][2][m] objective / loading-norm partials (double-float)
   double* gpart;  // [nred][npairs] Gram partials
+  void* tc_x3;    // tensor-core path: [3 mpad][p_pad] bf16 split of the iterate X (transposed)
+  void* tc_g3;    // tensor-core path: [3 mpad][n_pad] bf16 split of the gradient factors G (transposed)
+  const void* tc_maps;  // tensor-core path: the TMA tensor maps of A, X3 and G3 (TcMaps)
   double gamma_in[kMaxM];  // as passed (absolute, or relative with the flag)
   double mu[kMaxM];
   double tol;

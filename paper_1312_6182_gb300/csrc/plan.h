@@ -25,24 +25,35 @@ struct Plan {
   int nred = 0, nobj = 0, npairs = 0, full_gram = 0;
   int finish_smem = 0;
   int tcsize = 4, esize = 4;
-  size_t ws_cnorm = 0, ws_P = 0, ws_ypart = 0, ws_T = 0, ws_fpart = 0, ws_gpart = 0;
+  // tensor-core wide sweep (tc_sweep.cuh) instead of the CUDA-core passes
+  int tc = 0, mpad = 0, npad = 0, p_pad = 0, n_pad = 0, ntile1 = 0, kchunks1 = 0, nchunks2 = 0, kps2 = 0,
+      nsplit2 = 0, nrow2 = 0;
+  size_t ws_cnorm = 0, ws_P = 0, ws_ypart = 0, ws_T = 0, ws_fpart = 0, ws_gpart = 0, ws_x3 = 0, ws_g3 = 0;
 
   std::string key() const {
     char b[256];
     snprintf(b, sizeof(b), "%d/%d/%d/%d/%d/%lld/%d/%d/%d/%d/%d/%d", dtype, form, m, p, n, (long long)ld, fast, pca, C,
              ps, ncl, cols_per_cl);
     std::string s(b);
+    if (tc) {
+      snprintf(b, sizeof(b), "|tc%d,%d,%d", npad, kps2, nsplit2);
+      s += b;
+    }
     for (const Pass& q : passes) {
       snprintf(b, sizeof(b), "|%d,%d,%d,%d,%d,%d,%d", q.j0, q.mgv, q.mg, q.nch, q.threads, q.W, q.S);
       s += b;
     }
     return s;
   }
-  size_t workspace_bytes() const { return ws_cnorm + ws_P + ws_ypart + ws_T + ws_fpart + ws_gpart + 7 * 256; }
+  size_t workspace_bytes() const {
+    return ws_cnorm + ws_P + ws_ypart + ws_T + ws_fpart + ws_gpart + ws_x3 + ws_g3 + 10 * 256 + 1024;
+  }
 };
 
-// Plan a solve: cluster size, per-pass kernel variant, threads, tile ring.
-int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fast, int nsm, Plan* P);
+// Plan a solve: cluster size, per-pass kernel variant, threads, tile ring;
+// or, with allow_tc and a wide bf16 problem, the tensor-core sweep.
+int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fast, int nsm, Plan* P,
+              bool allow_tc = false);
 
 // Record `msg` as the calling thread's last error (gpspca_last_error) and return code.
 int record_error(int code, const char* msg);

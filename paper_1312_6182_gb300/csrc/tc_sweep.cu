@@ -1,0 +1,460 @@
+// Tensor-core (tcgen05) wide sweep: see tc_sweep.cuh.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstdio>
+
+#include "plan.h"
+#include "ptx.cuh"
+#include "sweep.cuh"
+#include "tc_sweep.cuh"
+
+namespace gpspca {
+
+constexpr int kTcStages = 5;
+constexpr uint32_t kTcA = 128 * 128;  // A bytes per stage: 128 x 64 bf16 (both passes)
+
+// v = b0 + b1 + b2 exactly: each part is the bf16 rounding of what the
+// previous ones left (the residuals are exact in float).
+__device__ __forceinline__ void split3(float v, __nv_bfloat16& b0, __nv_bfloat16& b1, __nv_bfloat16& b2) {
+  b0 = __float2bfloat16_rn(v);
+  const float r1 = v - __bfloat162float(b0);
+  b1 = __float2bfloat16_rn(r1);
+  const float r2 = r1 - __bfloat162float(b1);
+  b2 = __float2bfloat16_rn(r2);
+}
+
+// X = Y W (the iterate this sweep evaluates, as the fused sweep forms it),
+// written out for the active components and split into X3^T for the T pass.
+__global__ void tc_prep_kernel(const TcArgs a) {
+  __shared__ float Ws[kMaxM * kMaxM];
+  __shared__ int act[kMaxM];
+  const IO* io = a.io;
+  const State* st = a.st;
+  const int m = a.m, p = a.p;
+  const bool block = a.form >= 2;
+  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) Ws[idx] = static_cast<float>(st->W[idx]);
+  if (threadIdx.x < kMaxM) act[threadIdx.x] = threadIdx.x < m ? st->active[threadIdx.x] : 0;
+  __syncthreads();
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= p) return;
+  const float* Y = static_cast<const float*>(io->Y);
+  float* Xo = static_cast<float*>(io->X);
+  __nv_bfloat16* X3 = static_cast<__nv_bfloat16*>(io->tc_x3);
+  const int64_t rs = a.p_pad;
+  for (int j = 0; j < a.mpad; ++j) {
+    float x = 0.0f;
+    if (j < m) {
+      if (block) {
+        for (int l = 0; l < m; ++l) x += Y[static_cast<int64_t>(l) * p + r] * Ws[l * m + j];
+      } else {
+        x = Y[static_cast<int64_t>(j) * p + r] * Ws[j * m + j];
+      }
+      if (!a.sketch && act[j]) Xo[static_cast<int64_t>(j) * p + r] = x;
+    }
+    __nv_bfloat16 b0, b1, b2;
+    split3(x, b0, b1, b2);
+    X3[(0 * a.mpad + j) * rs + r] = b0;
+    X3[(1 * a.mpad + j) * rs + r] = b1;
+    X3[(2 * a.mpad + j) * rs + r] = b2;
+  }
+}
+
+template <int NPAD>
+struct TcCfg {
+  static constexpr int MPAD = NPAD / 3;
+  static constexpr uint32_t kB = NPAD * 128;  // X3 / G3 bytes per stage: NPAD rows x 64 bf16
+  static constexpr uint32_t kStage = kTcA + kB;
+  // two accumulators (ping-pong): the MMAs of one 64-deep chunk fill one while
+  // the epilogue drains the other
+  static constexpr uint32_t kCols = 2 * NPAD <= 128 ? 128 : (2 * NPAD <= 256 ? 256 : 512);
+  static_assert(NPAD % 48 == 0 && NPAD <= 192, "N = 3 mpad, mpad a multiple of 16, at most 64");
+  static_assert(kStage % 1024 == 0, "stages keep the 1024-byte alignment of the swizzle atoms");
+};
+
+struct TcSmem {
+  uint32_t base;         // 1024-aligned shared address of stage 0
+  unsigned char* ptr;    // its generic pointer
+  uint64_t* full;        // [kTcStages] TMA -> MMA
+  uint64_t* empty;       // [kTcStages] MMA -> TMA
+  uint64_t* accf;        // [2] MMA -> epilogue: a chunk's accumulator is complete
+  uint64_t* acce;        // [2] epilogue -> MMA: it has been read
+  uint32_t* tslot;
+  int* abort_flag;
+};
+
+template <int NPAD>
+__device__ __forceinline__ TcSmem tc_smem(unsigned char* raw) {
+  TcSmem s;
+  const uint32_t r = smem_u32(raw);
+  s.base = (r + 1023u) & ~1023u;
+  s.ptr = raw + (s.base - r);
+  s.full = reinterpret_cast<uint64_t*>(s.ptr + kTcStages * TcCfg<NPAD>::kStage);
+  s.empty = s.full + kTcStages;
+  s.accf = s.empty + kTcStages;
+  s.acce = s.accf + 2;
+  s.tslot = reinterpret_cast<uint32_t*>(s.acce + 2);
+  s.abort_flag = reinterpret_cast<int*>(s.tslot + 1);
+  return s;
+}
+
+// Barriers, tensor memory; returns the accumulators' tensor-memory address.
+template <int NPAD>
+__device__ __forceinline__ uint32_t tc_setup(const TcSmem& S) {
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int s = 0; s < kTcStages; ++s) {
+      mbar_init(smem_u32(&S.full[s]), 1);
+      mbar_init(smem_u32(&S.empty[s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&S.accf[b]), 1);
+      mbar_init(smem_u32(&S.acce[b]), 128);
+    }
+    *S.abort_flag = 0;
+    fence_mbar_init();
+  }
+  if ((tid >> 5) == 0) {
+    tmem_alloc(smem_u32(S.tslot), TcCfg<NPAD>::kCols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  return *S.tslot;
+}
+
+template <int NPAD>
+__device__ __forceinline__ void tc_teardown(const TcSmem& S, uint32_t tmem, bool timed_out, State* st) {
+  if (timed_out) atomicOr(&st->error, static_cast<int>(kErrTimeout));
+  tc_fence_before();
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, TcCfg<NPAD>::kCols);
+  }
+}
+
+__device__ __forceinline__ bool tc_aborted(const TcSmem& S) {
+  return *reinterpret_cast<volatile int*>(S.abort_flag) != 0;
+}
+
+// TMA producer: chunk `it` of the launch goes to stage it % kTcStages once
+// the MMAs of its previous use have completed.  load(c, sa, bar) issues the
+// copies of chunk c; false on a timeout.
+template <int NPAD, typename Load>
+__device__ __forceinline__ bool tc_produce(const TcSmem& S, int it, int c, Load load) {
+  const int s = it % kTcStages;
+  const uint32_t u = static_cast<uint32_t>(it / kTcStages);
+  if (tc_aborted(S) || (u > 0 && !mbar_wait_bounded(smem_u32(&S.empty[s]), (u - 1) & 1))) {
+    *S.abort_flag = 1;
+    return false;
+  }
+  const uint32_t bar = smem_u32(&S.full[s]);
+  mbar_arrive_expect_tx(bar, TcCfg<NPAD>::kStage);
+  load(c, S.base + s * TcCfg<NPAD>::kStage, bar);
+  return true;
+}
+
+// MMA issuer: the 4 MMAs (K = 16 each) of chunk `it` into accumulator it % 2,
+// starting it afresh; then the stage is released and the accumulator handed
+// to the epilogue.  false on a timeout.
+template <int NPAD, typename Descs>
+__device__ __forceinline__ bool tc_mma_chunk(const TcSmem& S, uint32_t tmem, int it, uint32_t idesc, Descs descs) {
+  const int s = it % kTcStages, b = it & 1;
+  const uint32_t u = static_cast<uint32_t>(it / kTcStages), ub = static_cast<uint32_t>(it >> 1);
+  if (ub > 0 && !mbar_wait_bounded(smem_u32(&S.acce[b]), (ub - 1) & 1)) return false;
+  if (!mbar_wait_bounded(smem_u32(&S.full[s]), u & 1)) return false;
+  tc_fence_after();
+  const uint32_t sa = S.base + s * TcCfg<NPAD>::kStage;
+  const uint32_t d = tmem + static_cast<uint32_t>(b * NPAD);
+#pragma unroll
+  for (int kk = 0; kk < kTcBK / 16; ++kk) {
+    uint64_t ad, bd;
+    descs(sa, kk, &ad, &bd);
+    umma_f16(d, ad, bd, idesc, kk > 0 ? 1u : 0u);
+  }
+  umma_commit(smem_u32(&S.empty[s]));
+  umma_commit(smem_u32(&S.accf[b]));
+  return true;
+}
+
+// Epilogue: adds chunk `it`'s accumulator (this thread's lane, the three split
+// groups summed as x0 + (x1 + x2)) into acc[], then releases it.  IEEE float
+// adds per chunk keep the sum at float accuracy however long the reduction
+// dimension is.  false on a timeout.
+template <int NPAD>
+__device__ __forceinline__ bool tc_drain(const TcSmem& S, uint32_t tlane, int it, float (&acc)[TcCfg<NPAD>::MPAD]) {
+  constexpr int MPAD = TcCfg<NPAD>::MPAD;
+  const int b = it & 1;
+  if (!mbar_wait_bounded(smem_u32(&S.accf[b]), static_cast<uint32_t>((it >> 1) & 1))) return false;
+  tc_fence_after();
+  const uint32_t col = tlane + static_cast<uint32_t>(b * NPAD);
+#pragma unroll
+  for (int c0 = 0; c0 < MPAD; c0 += 16) {
+    uint32_t h[16], md[16], lo[16];
+    tmem_ld16(col + c0, h);
+    tmem_ld16(col + MPAD + c0, md);
+    tmem_ld16(col + 2 * MPAD + c0, lo);
+    tmem_wait_ld();
+#pragma unroll
+    for (int e = 0; e < 16; ++e)
+      acc[c0 + e] += __uint_as_float(h[e]) + (__uint_as_float(md[e]) + __uint_as_float(lo[e]));
+  }
+  tc_fence_before();
+  mbar_arrive(smem_u32(&S.acce[b]));
+  return true;
+}
+
+// ---- pass 1: T = A^T X for 128-column tiles (persistent CTAs), threshold,
+// G3^T for pass 2.  Tensor-memory lane = column of the tile.
+template <int NPAD>
+__global__ void __launch_bounds__(kTcThreads, 1) tc_t_kernel(const TcArgs a) {
+  using Cfg = TcCfg<NPAD>;
+  constexpr int MPAD = Cfg::MPAD;
+  constexpr uint32_t kIdesc = idesc_bf16_f32(NPAD, 0, 0);
+  extern __shared__ unsigned char smem_raw[];
+  const TcSmem S = tc_smem<NPAD>(smem_raw);
+  __shared__ float gam_s[kMaxM], mu_s[kMaxM];
+  __shared__ int act_s[kMaxM];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const IO* io = a.io;
+  State* st = a.st;
+  const TcMaps* maps = static_cast<const TcMaps*>(io->tc_maps);
+  const bool sketch = a.sketch != 0;
+  const int form = sketch ? GPSPCA_SL0 : a.form;
+  if (tid < kMaxM) {
+    const bool v = tid < a.m && !sketch;
+    gam_s[tid] = v ? static_cast<float>(st->gamma[tid]) : 0.0f;
+    mu_s[tid] = v ? static_cast<float>(io->mu[tid]) : 1.0f;
+    act_s[tid] = tid < a.m ? st->active[tid] : 0;
+  }
+  const uint32_t tmem = tc_setup<NPAD>(S);
+  bool timed_out = false;
+
+  if (warp == 4) {  // TMA producer
+    if (lane == 0) {
+      tmap_acquire(&maps->a1);
+      tmap_acquire(&maps->x3);
+      int it = 0;
+      for (int tile = blockIdx.x; tile < a.ntile1 && !timed_out; tile += gridDim.x) {
+        for (int c = 0; c < a.kchunks1; ++c, ++it) {
+          const bool ok = tc_produce<NPAD>(S, it, c, [&](int cc, uint32_t sa, uint32_t bar) {
+            tma_load_2d(sa, &maps->a1, cc * kTcBK, tile * kTcTile1, bar);
+            tma_load_2d(sa + kTcA, &maps->x3, cc * kTcBK, 0, bar);
+          });
+          if (!ok) {
+            timed_out = true;
+            break;
+          }
+        }
+      }
+    }
+  } else if (warp == 5) {  // MMA issuer
+    if (lane == 0) {
+      int it = 0;
+      for (int tile = blockIdx.x; tile < a.ntile1 && !timed_out; tile += gridDim.x) {
+        for (int c = 0; c < a.kchunks1; ++c, ++it) {
+          const bool ok = tc_mma_chunk<NPAD>(S, tmem, it, kIdesc, [](uint32_t sa, int kk, uint64_t* ad, uint64_t* bd) {
+            *ad = sdesc_sw128(sa + kk * 32, 16, 1024);
+            *bd = sdesc_sw128(sa + kTcA + kk * 32, 16, 1024);
+          });
+          if (!ok) {
+            timed_out = true;
+            *S.abort_flag = 1;
+            break;
+          }
+        }
+      }
+    }
+  } else {  // epilogue, warps 0-3: thread = tensor-memory lane = column of the tile
+    const uint32_t tlane = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+    float* Tout = static_cast<float*>(io->T);
+    __nv_bfloat16* G3 = static_cast<__nv_bfloat16*>(io->tc_g3);
+    const int64_t gs = a.n_pad;
+    int it = 0;
+    for (int tile = blockIdx.x; tile < a.ntile1 && !timed_out; tile += gridDim.x) {
+      float t[MPAD];
+#pragma unroll
+      for (int j = 0; j < MPAD; ++j) t[j] = 0.0f;
+      for (int c = 0; c < a.kchunks1; ++c, ++it) {
+        if (!tc_drain<NPAD>(S, tlane, it, t)) {
+          timed_out = true;
+          *S.abort_flag = 1;
+          break;
+        }
+      }
+      if (timed_out) break;
+      const int i = tile * kTcTile1 + warp * 32 + lane;
+      if (i < a.n) {
+#pragma unroll
+        for (int j = 0; j < MPAD; ++j) {
+          float g = 0.0f;
+          if (j < a.m) {
+            if (!sketch && act_s[j]) Tout[static_cast<int64_t>(j) * a.n + i] = t[j];
+            g = grad_factor<float>(form, t[j], gam_s[j], mu_s[j]);
+          }
+          __nv_bfloat16 b0, b1, b2;
+          split3(g, b0, b1, b2);
+          G3[(0 * MPAD + j) * gs + i] = b0;
+          G3[(1 * MPAD + j) * gs + i] = b1;
+          G3[(2 * MPAD + j) * gs + i] = b2;
+        }
+      }
+    }
+  }
+  tc_teardown<NPAD>(S, tmem, timed_out, st);
+}
+
+// ---- pass 2: Y = A G for 128-row blocks, the columns split over gridDim.y;
+// partial sums to ypart[split].  Tensor-memory lane = row of the block.  The
+// A tile is the operand in MN-major form (64 rows contiguous per column).
+template <int NPAD>
+__global__ void __launch_bounds__(kTcThreads, 1) tc_y_kernel(const TcArgs a) {
+  using Cfg = TcCfg<NPAD>;
+  constexpr int MPAD = Cfg::MPAD;
+  constexpr uint32_t kIdesc = idesc_bf16_f32(NPAD, 1, 0);
+  extern __shared__ unsigned char smem_raw[];
+  const TcSmem S = tc_smem<NPAD>(smem_raw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const IO* io = a.io;
+  State* st = a.st;
+  const TcMaps* maps = static_cast<const TcMaps*>(io->tc_maps);
+  const int rb = blockIdx.x, sp = blockIdx.y;
+  const int cb = sp * a.kps2, ce = min(a.nchunks2, cb + a.kps2);
+  const uint32_t tmem = tc_setup<NPAD>(S);
+  bool timed_out = false;
+
+  if (warp == 4) {  // TMA producer
+    if (lane == 0) {
+      tmap_acquire(&maps->a2);
+      tmap_acquire(&maps->g3);
+      for (int c = cb, it = 0; c < ce; ++c, ++it) {
+        const bool ok = tc_produce<NPAD>(S, it, c, [&](int cc, uint32_t sa, uint32_t bar) {
+          tma_load_2d(sa, &maps->a2, rb * kTcRows2, cc * kTcBK, bar);
+          tma_load_2d(sa + kTcA / 2, &maps->a2, rb * kTcRows2 + 64, cc * kTcBK, bar);
+          tma_load_2d(sa + kTcA, &maps->g3, cc * kTcBK, 0, bar);
+        });
+        if (!ok) {
+          timed_out = true;
+          break;
+        }
+      }
+    }
+  } else if (warp == 5) {  // MMA issuer
+    if (lane == 0) {
+      for (int c = cb, it = 0; c < ce; ++c, ++it) {
+        // A: rows 0-63 and 64-127 are the two MN atoms (LBO apart), 8 columns
+        // per 1024-byte atom (SBO); B: K-major as in pass 1
+        const bool ok = tc_mma_chunk<NPAD>(S, tmem, it, kIdesc, [](uint32_t sa, int kk, uint64_t* ad, uint64_t* bd) {
+          *ad = sdesc_sw128(sa + kk * 2048, kTcA / 2, 1024);
+          *bd = sdesc_sw128(sa + kTcA + kk * 32, 16, 1024);
+        });
+        if (!ok) {
+          timed_out = true;
+          *S.abort_flag = 1;
+          break;
+        }
+      }
+    }
+  } else {  // epilogue, warps 0-3
+    const uint32_t tlane = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+    float y[MPAD];
+#pragma unroll
+    for (int j = 0; j < MPAD; ++j) y[j] = 0.0f;
+    for (int c = cb, it = 0; c < ce; ++c, ++it) {
+      if (!tc_drain<NPAD>(S, tlane, it, y)) {
+        timed_out = true;
+        *S.abort_flag = 1;
+        break;
+      }
+    }
+    const int r = rb * kTcRows2 + warp * 32 + lane;
+    if (!timed_out && r < a.p) {
+      float* yp = static_cast<float*>(io->ypart);
+#pragma unroll
+      for (int j = 0; j < MPAD; ++j)
+        if (j < a.m) yp[(static_cast<int64_t>(sp) * a.m + j) * a.p + r] = y[j];
+    }
+  }
+  tc_teardown<NPAD>(S, tmem, timed_out, st);
+}
+
+// ---------------------------------------------------------------- host
+
+int tc_smem_bytes(int npad) { return kTcStages * (static_cast<int>(kTcA) + npad * 128) + 1024 + 512; }
+
+bool tc_supported(int device) {
+  int major = 0, minor = 0;
+  if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device) != cudaSuccess) return false;
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device);
+  return major == 10 && minor == 3;  // built for sm_103a only
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<EncodeTiledFn>(f);
+  }();
+  return fn;
+}
+
+// bf16 matrix with inner extent `inner` (contiguous) and `outer` rows of
+// `stride_elems`; box 64 x box_outer, 128-byte swizzle, zero fill outside.
+static bool encode_bf16(CUtensorMap* m, const void* base, int64_t inner, int64_t outer, int64_t stride_elems,
+                        int box_outer) {
+  const EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {static_cast<cuuint64_t>(inner), static_cast<cuuint64_t>(outer)};
+  const cuuint64_t strides[1] = {static_cast<cuuint64_t>(stride_elems) * 2};
+  const cuuint32_t box[2] = {64u, static_cast<cuuint32_t>(box_outer)};
+  const cuuint32_t estr[2] = {1u, 1u};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int tc_encode_maps(TcMaps* maps, const void* A, int64_t p, int64_t n, int64_t ld, const void* x3, int p_pad,
+                   const void* g3, int n_pad, int npad) {
+  if (!encode_bf16(&maps->a1, A, p, n, ld, kTcTile1) || !encode_bf16(&maps->x3, x3, p, npad, p_pad, npad) ||
+      !encode_bf16(&maps->a2, A, p, n, ld, 64) || !encode_bf16(&maps->g3, g3, n, npad, n_pad, npad))
+    return record_error(GPSPCA_ECUDA, "cuTensorMapEncodeTiled failed for the tensor-core sweep");
+  return GPSPCA_OK;
+}
+
+template <int NPAD>
+static void launch_tc_npad(const TcArgs& a, int nsm, cudaStream_t s) {
+  static bool once = [] {
+    cudaFuncSetAttribute(tc_t_kernel<NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem_bytes(NPAD));
+    cudaFuncSetAttribute(tc_y_kernel<NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem_bytes(NPAD));
+    return true;
+  }();
+  (void)once;
+  const int smem = tc_smem_bytes(NPAD);
+  tc_prep_kernel<<<(a.p + 255) / 256, 256, 0, s>>>(a);
+  tc_t_kernel<NPAD><<<std::max(1, std::min(a.ntile1, nsm)), kTcThreads, smem, s>>>(a);
+  tc_y_kernel<NPAD><<<dim3(a.nrow2, a.nsplit2), kTcThreads, smem, s>>>(a);
+}
+
+void launch_tc_sweep(const TcArgs& a, int npad, cudaStream_t s) {
+  int dev = 0, nsm = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  switch (npad) {
+    case 48: launch_tc_npad<48>(a, nsm, s); break;
+    case 96: launch_tc_npad<96>(a, nsm, s); break;
+    case 144: launch_tc_npad<144>(a, nsm, s); break;
+    default: launch_tc_npad<192>(a, nsm, s); break;
+  }
+}
+
+}  // namespace gpspca

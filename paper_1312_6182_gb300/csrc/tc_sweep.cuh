@@ -1,0 +1,69 @@
+// The wide sweep on the 5th-generation tensor cores (tcgen05): for m >= 16
+// components (or gamma values), one power iteration is two tall-skinny
+// contractions over A,
+//
+//   T = A^T X   (n x m; then the Table 1 threshold gives G, per entry)
+//   Y = A G     (p x m),
+//
+// the same three steps as the fused CUDA-core sweep (column sweep,
+// threshold, rank update), with the dot products and the rank update on the
+// tensor cores.  A (bf16) streams through shared memory by TMA in 128-byte
+// swizzled tiles; one thread issues tcgen05.mma, accumulators live in tensor
+// memory and are read back with tcgen05.ld.
+//
+// Accuracy: X and G are float; each is split into three bf16 parts
+// (x = x0 + x1 + x2 exactly, 24 significant bits), laid side by side as the
+// N = 3 mpad columns of one MMA, so the tensor cores form A x0, A x1, A x2 in
+// float accumulators and the epilogue adds them (x0 + (x1 + x2)): the
+// products are those of float X against the stored A.
+//
+// Why two passes and not one: the rank update's accumulator Y (p x 3 mpad
+// floats) must stay in tensor memory (256 KB per SM) across every column
+// tile of a CTA's share of A; for the shapes that need this path (m >= 16,
+// p in the thousands) it does not fit, while T's accumulator (128 columns x
+// 3 mpad) always does.  Each pass reads A once, at tensor-core rate instead
+// of CUDA-core rate.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "internal.h"
+
+namespace gpspca {
+
+constexpr int kTcThreads = 192;  // warps 0-3: epilogue (tensor-memory lanes 0-127), 4: TMA, 5: MMA
+constexpr int kTcBK = 64;        // elements of the reduction dimension per stage (one 128-byte row)
+constexpr int kTcTile1 = 128;    // columns of A per T-pass tile (the MMA's M)
+constexpr int kTcRows2 = 128;    // rows of A per Y-pass block (the MMA's M)
+
+// TMA descriptors of one solve (device memory, refreshed by the host before
+// each solve).
+struct TcMaps {
+  CUtensorMap a1;  // A, box 64 rows x 128 columns (T pass)
+  CUtensorMap x3;  // X3^T, box 64 x N
+  CUtensorMap a2;  // A, box 64 rows x 64 columns (Y pass)
+  CUtensorMap g3;  // G3^T, box 64 x N
+};
+
+struct TcArgs {
+  const IO* io;
+  State* st;
+  int p, n, m, mpad, form, sketch;
+  int p_pad, n_pad;   // row strides (elements) of X3^T and G3^T
+  int ntile1;         // ceil(n / 128)
+  int kchunks1;       // ceil(p / 64)
+  int nchunks2;       // ceil(n / 64)
+  int kps2;           // 64-column chunks per Y-pass split
+  int nsplit2;        // Y-pass splits of the columns
+  int nrow2;          // ceil(p / 128)
+};
+
+// Host side (tc_sweep.cu).
+int tc_smem_bytes(int npad);
+bool tc_supported(int device);
+int tc_encode_maps(TcMaps* maps, const void* A, int64_t p, int64_t n, int64_t ld, const void* x3, int p_pad,
+                   const void* g3, int n_pad, int npad);
+void launch_tc_sweep(const TcArgs& a, int npad, cudaStream_t s);
+
+}  // namespace gpspca

@@ -136,6 +136,56 @@ def test_block_many_components(ctx, p, n, m):
     assert_matches("BL1", g, ref, oracle.column_norms(A), tol_z=5e-5, tol_f=1e-6, tol_x=5e-5, iters_slack=0)
 
 
+# ---------------------------------------------------------------- tensor-core (tcgen05) sweep
+
+@pytest.mark.parametrize("form,p,n,m", [("BL1", 1496, 8008, 16), ("BL0", 2048, 6000, 16), ("BL1", 1504, 9000, 32)])
+def test_tensor_core_sweep_block_matches_oracle(ctx, form, p, n, m):
+    """BF16 storage with 16 or more components runs the two-pass tcgen05
+    sweep (p, n ragged against its 64-row and 128-column tiles); the oracle
+    runs on the stored values.  8 sweeps from the PCA start."""
+    At = synth.planted_spike(p, n, m, [100.0 / np.sqrt(j) for j in range(1, m + 1)], support_frac=0.01, seed=8,
+                             dtype=np.float32)
+    tb, deq = _bf16(At)
+    A = deq.astype(np.float64).T
+    gam = _gammas(A, form, [0.02] * m)
+    mu = [1.0] * m
+    ref = oracle.gpower(A, form, gam, mu=mu, tol=0.0, maxit=8)
+    res = ctx.solve(tb.cuda(), form, list(gam), mu=mu, tol=0.0, maxit=8)
+    assert_matches(form, gpu_arrays(res), ref, oracle.column_norms(A), tol_z=5e-5, tol_f=1e-6, tol_x=5e-5,
+                   iters_slack=0)
+
+
+@pytest.mark.parametrize("form", ["SL1", "SL0"])
+def test_tensor_core_gamma_path_64(ctx, form):
+    """A 64-value gamma path on BF16 storage: all 64 columns in one tcgen05
+    contraction per sweep (N = 3 x 64), against the oracle's 64 solves."""
+    At = synth.planted_spike(1504, 6000, 3, [40.0, 20.0, 13.3], support_frac=0.02, seed=1, dtype=np.float32)
+    tb, deq = _bf16(At)
+    A = deq.astype(np.float64).T
+    gam = _gammas(A, form, synth.log_spaced_rho(64))
+    ref = oracle.gpower(A, form, gam, tol=1e-6, maxit=300)
+    res = ctx.solve(tb.cuda(), form, list(gam), tol=1e-6, maxit=300)
+    assert_matches(form, gpu_arrays(res), ref, oracle.column_norms(A), tol_z=1e-4, tol_f=1e-6, tol_x=1e-4,
+                   iters_slack=2)
+
+
+def test_tensor_core_and_cuda_core_sweeps_agree(ctx):
+    """The same solve with and without the tensor cores: float-rounding
+    differences only, on the well-determined quantities (the objective, and
+    the components of the four planted spikes; the other twelve fit noise
+    with near-equal eigenvalues and move freely at rounding level)."""
+    At = synth.planted_spike(1024, 4096, 4, [40.0, 28.0, 23.0, 20.0], support_frac=0.02, seed=5, dtype=np.float32)
+    dA = _bf16(At)[0].cuda()
+    gam = [0.03] * 16
+    a = ctx.solve(dA, "BL1", gam, mu=[1.0] * 16, tol=0.0, maxit=4, gamma_relative=True, tensor_cores=False)
+    b = ctx.solve(dA, "BL1", gam, mu=[1.0] * 16, tol=0.0, maxit=4, gamma_relative=True)
+    assert ((a.objective - b.objective).abs() / a.objective.abs()).max().item() < 1e-5
+    assert abs(a.objective.sum().item() - b.objective.sum().item()) / a.objective.sum().item() < 1e-6
+    # the planted subspace: projector onto the leading four columns
+    Xa, Xb = a.X[:4].double(), b.X[:4].double()
+    assert (Xa.T @ Xa - Xb.T @ Xb).abs().max().item() < 1e-5
+
+
 # ---------------------------------------------------------------- storage precisions
 
 def _bf16(At):
