@@ -217,10 +217,15 @@ int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fa
   pl.esize = d.esize;
   const int unit = std::max(d.align, d.vec);
   bool found = false;
-  // the tensor-core sweep: bf16 storage, 16 or more components (or gamma
-  // values), TMA-compatible layout (16-byte aligned base and column stride)
-  if (allow_tc && dt == GPSPCA_BF16 && m >= 16 && fast && ld % 8 == 0 && p >= 1 && n >= 1) {
+  // the tensor-core sweep for 16 or more components (or gamma values): bf16
+  // storage read in place (TMA-compatible layout: 16-byte aligned base and
+  // column stride), float A as three bf16 planes and fp8 A as one, copied
+  // once per solve
+  const bool native_bf16 = dt == GPSPCA_BF16 && fast && ld % 8 == 0;
+  if (allow_tc && m >= 16 && p >= 1 && n >= 1 && (native_bf16 || dt == GPSPCA_F32 || dt == GPSPCA_FP8_E4M3)) {
     plan_tc(&pl, m, p, n, nsm);
+    pl.tc_na = dt == GPSPCA_F32 ? 3 : 1;
+    pl.tc_convert = native_bf16 ? 0 : 1;
     pl.C = 1;
     pl.ps = static_cast<int>(p);
     found = true;
@@ -289,6 +294,7 @@ int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fa
   if (pl.tc) {
     pl.ws_x3 = 2 * static_cast<size_t>(pl.npad) * pl.p_pad;
     pl.ws_g3 = 2 * static_cast<size_t>(pl.npad) * pl.n_pad;
+    if (pl.tc_convert) pl.ws_planes = 2 * static_cast<size_t>(pl.tc_na) * n * pl.p_pad;
   }
   *P = pl;
   return GPSPCA_OK;
@@ -320,7 +326,7 @@ struct Slot {
   cudaEvent_t done = nullptr;
   Budget* budget = nullptr;
   // workspace buffers, grown on demand
-  DevBuf b_cnorm, b_P, b_Y, b_ypart, b_T, b_fpart, b_gpart, b_x3, b_g3, b_maps;
+  DevBuf b_cnorm, b_P, b_Y, b_ypart, b_T, b_fpart, b_gpart, b_x3, b_g3, b_maps, b_planes;
   TcMaps* maps_host = nullptr;  // pinned: the tensor maps copied to b_maps before a solve
   // staging for host-located inputs/outputs
   DevBuf s_A, s_scale, s_x0, s_X, s_Z, s_sup, s_obj, s_it, s_stat, s_gam;
@@ -332,7 +338,8 @@ struct Slot {
 
   size_t held() const {
     size_t s = 0;
-    for (const DevBuf* b : {&b_cnorm, &b_P, &b_Y, &b_ypart, &b_T, &b_fpart, &b_gpart, &b_x3, &b_g3, &b_maps, &s_A,
+    for (const DevBuf* b : {&b_cnorm, &b_P, &b_Y, &b_ypart, &b_T, &b_fpart, &b_gpart, &b_x3, &b_g3, &b_maps,
+                            &b_planes, &s_A,
                             &s_scale, &s_x0, &s_X,
                             &s_Z, &s_sup, &s_obj, &s_it, &s_stat, &s_gam})
       s += b->bytes;
@@ -377,7 +384,7 @@ static void release(Slot* s, DevBuf* b) {
 
 static void release_workspace(Slot* s) {
   for (DevBuf* b : {&s->b_cnorm, &s->b_P, &s->b_Y, &s->b_ypart, &s->b_T, &s->b_fpart, &s->b_gpart, &s->b_x3,
-                    &s->b_g3, &s->b_maps, &s->s_A,
+                    &s->b_g3, &s->b_maps, &s->b_planes, &s->s_A,
                     &s->s_scale, &s->s_x0, &s->s_X, &s->s_Z, &s->s_sup, &s->s_obj, &s->s_it, &s->s_stat, &s->s_gam})
     release(s, b);
 }
@@ -441,6 +448,8 @@ static cudaError_t launch_sweeps(const Plan& pl, Slot* s, cudaStream_t cs, int s
 // power steps (A A^T Q, projected) and a Rayleigh-Ritz rotation.
 static cudaError_t launch_prologue(const Plan& pl, Slot* s, cudaStream_t cs, cudaGraphConditionalHandle h, bool pca,
                                    int use_cond = 1) {
+  if (pl.tc && pl.tc_convert)  // bf16 planes of a float / fp8 A for the tensor cores
+    launch_tc_convert(pl.dtype, s->io_dev, pl.p, pl.n, pl.ld, pl.p_pad, cs);
   launch_reset(s->io_dev, s->st_dev, pl.m, pl.form, cs);
   launch_colnorm(pl.dtype, s->io_dev, s->st_dev, pl.ld, pl.p, pl.n, pl.fast, cs);
   StartArgs sa{s->io_dev, s->st_dev, pl.ld, pl.p, pl.n, pl.m, pl.form};
@@ -471,8 +480,9 @@ static cudaError_t launch_prologue(const Plan& pl, Slot* s, cudaStream_t cs, cud
 
 static cudaError_t launch_sweeps(const Plan& pl, Slot* s, cudaStream_t cs, int sketch) {
   if (pl.tc) {
-    TcArgs a{s->io_dev, s->st_dev, pl.p, pl.n, pl.m, pl.mpad, pl.form, sketch, pl.p_pad, pl.n_pad,
-             pl.ntile1, pl.kchunks1, pl.nchunks2, pl.kps2, pl.nsplit2, pl.nrow2};
+    TcArgs a{s->io_dev, s->st_dev, pl.p,     pl.n,      pl.m,     pl.mpad,     pl.form,
+             sketch,    pl.tc_na,  pl.dtype == GPSPCA_FP8_E4M3 ? 1 : 0, pl.p_pad, pl.n_pad, pl.ntile1, pl.kchunks1,
+             pl.nchunks2, pl.kps2, pl.nsplit2, pl.nrow2};
     launch_tc_sweep(a, pl.npad, cs);
     return cudaGetLastError();
   }
@@ -698,9 +708,13 @@ static int prepare_solve(Slot* s, const Request& r, int nsm, bool scratch_out, P
     if ((rc = ensure(s, &s->b_x3, pl.ws_x3))) return rc;
     if ((rc = ensure(s, &s->b_g3, pl.ws_g3))) return rc;
     if ((rc = ensure(s, &s->b_maps, sizeof(TcMaps)))) return rc;
+    if (pl.tc_convert && (rc = ensure(s, &s->b_planes, pl.ws_planes))) return rc;
     // the host copy of the maps is reused only after this solve's copy has run
     GP_CUDA(cudaStreamSynchronize(s->stream));
-    if ((rc = tc_encode_maps(s->maps_host, A_dev, p, n, ld, s->b_x3.p, pl.p_pad, s->b_g3.p, pl.n_pad, pl.npad)))
+    const void* planes = pl.tc_convert ? s->b_planes.p : A_dev;
+    const int64_t pld = pl.tc_convert ? pl.p_pad : ld;
+    if ((rc = tc_encode_maps(s->maps_host, planes, pl.tc_na, pld * n, p, n, pld, s->b_x3.p, pl.p_pad, s->b_g3.p,
+                             pl.n_pad, pl.npad)))
       return rc;
     GP_CUDA(cudaMemcpyAsync(s->b_maps.p, s->maps_host, sizeof(TcMaps), cudaMemcpyHostToDevice, s->stream));
   }
@@ -745,6 +759,7 @@ static int prepare_solve(Slot* s, const Request& r, int nsm, bool scratch_out, P
     io.tc_x3 = s->b_x3.p;
     io.tc_g3 = s->b_g3.p;
     io.tc_maps = s->b_maps.p;
+    io.tc_planes = pl.tc_convert ? s->b_planes.p : nullptr;
   }
   for (int j = 0; j < m; ++j) {
     io.gamma_in[j] = r.gamma[j];

@@ -28,7 +28,10 @@ struct Plan {
   // tensor-core wide sweep (tc_sweep.cuh) instead of the CUDA-core passes
   int tc = 0, mpad = 0, npad = 0, p_pad = 0, n_pad = 0, ntile1 = 0, kchunks1 = 0, nchunks2 = 0, kps2 = 0,
       nsplit2 = 0, nrow2 = 0;
-  size_t ws_cnorm = 0, ws_P = 0, ws_ypart = 0, ws_T = 0, ws_fpart = 0, ws_gpart = 0, ws_x3 = 0, ws_g3 = 0;
+  int tc_na = 1;       // bf16 planes of A the contractions read (3 for float A)
+  int tc_convert = 0;  // the planes are a workspace copy made once per solve (float / fp8 A)
+  size_t ws_cnorm = 0, ws_P = 0, ws_ypart = 0, ws_T = 0, ws_fpart = 0, ws_gpart = 0, ws_x3 = 0, ws_g3 = 0,
+         ws_planes = 0;
 
   std::string key() const {
     char b[256];
@@ -36,7 +39,7 @@ struct Plan {
              ps, ncl, cols_per_cl);
     std::string s(b);
     if (tc) {
-      snprintf(b, sizeof(b), "|tc%d,%d,%d", npad, kps2, nsplit2);
+      snprintf(b, sizeof(b), "|tc%d,%d,%d,%d,%d", npad, kps2, nsplit2, tc_na, tc_convert);
       s += b;
     }
     for (const Pass& q : passes) {
@@ -46,7 +49,7 @@ struct Plan {
     return s;
   }
   size_t workspace_bytes() const {
-    return ws_cnorm + ws_P + ws_ypart + ws_T + ws_fpart + ws_gpart + ws_x3 + ws_g3 + 10 * 256 + 1024;
+    return ws_cnorm + ws_P + ws_ypart + ws_T + ws_fpart + ws_gpart + ws_x3 + ws_g3 + ws_planes + 11 * 256 + 1024;
   }
 };
 

@@ -11,8 +11,7 @@
 
 namespace gpspca {
 
-constexpr int kTcStages = 5;
-constexpr uint32_t kTcA = 128 * 128;  // A bytes per stage: 128 x 64 bf16 (both passes)
+constexpr uint32_t kTcA = 128 * 128;  // bytes of one A plane per stage: 128 x 64 bf16 (both passes)
 
 // v = b0 + b1 + b2 exactly: each part is the bf16 rounding of what the
 // previous ones left (the residuals are exact in float).
@@ -60,38 +59,42 @@ __global__ void tc_prep_kernel(const TcArgs a) {
   }
 }
 
-template <int NPAD>
+template <int NPAD, int NA>
 struct TcCfg {
   static constexpr int MPAD = NPAD / 3;
-  static constexpr uint32_t kB = NPAD * 128;  // X3 / G3 bytes per stage: NPAD rows x 64 bf16
-  static constexpr uint32_t kStage = kTcA + kB;
+  static constexpr uint32_t kAll = NA * kTcA;  // A planes per stage
+  static constexpr uint32_t kB = NPAD * 128;   // X3 / G3 bytes per stage: NPAD rows x 64 bf16
+  static constexpr uint32_t kStage = kAll + kB;
+  static constexpr int kStages = NA == 1 ? 5 : 3;
   // two accumulators (ping-pong): the MMAs of one 64-deep chunk fill one while
   // the epilogue drains the other
   static constexpr uint32_t kCols = 2 * NPAD <= 128 ? 128 : (2 * NPAD <= 256 ? 256 : 512);
   static_assert(NPAD % 48 == 0 && NPAD <= 192, "N = 3 mpad, mpad a multiple of 16, at most 64");
+  static_assert(NA == 1 || NA == 3, "one bf16 plane, or three for float A");
   static_assert(kStage % 1024 == 0, "stages keep the 1024-byte alignment of the swizzle atoms");
+  static_assert(kStages * kStage + 1536 <= 227 * 1024, "stage ring fits the shared memory");
 };
 
 struct TcSmem {
   uint32_t base;         // 1024-aligned shared address of stage 0
   unsigned char* ptr;    // its generic pointer
-  uint64_t* full;        // [kTcStages] TMA -> MMA
-  uint64_t* empty;       // [kTcStages] MMA -> TMA
+  uint64_t* full;        // [kStages] TMA -> MMA
+  uint64_t* empty;       // [kStages] MMA -> TMA
   uint64_t* accf;        // [2] MMA -> epilogue: a chunk's accumulator is complete
   uint64_t* acce;        // [2] epilogue -> MMA: it has been read
   uint32_t* tslot;
   int* abort_flag;
 };
 
-template <int NPAD>
+template <int NPAD, int NA>
 __device__ __forceinline__ TcSmem tc_smem(unsigned char* raw) {
   TcSmem s;
   const uint32_t r = smem_u32(raw);
   s.base = (r + 1023u) & ~1023u;
   s.ptr = raw + (s.base - r);
-  s.full = reinterpret_cast<uint64_t*>(s.ptr + kTcStages * TcCfg<NPAD>::kStage);
-  s.empty = s.full + kTcStages;
-  s.accf = s.empty + kTcStages;
+  s.full = reinterpret_cast<uint64_t*>(s.ptr + TcCfg<NPAD, NA>::kStages * TcCfg<NPAD, NA>::kStage);
+  s.empty = s.full + TcCfg<NPAD, NA>::kStages;
+  s.accf = s.empty + TcCfg<NPAD, NA>::kStages;
   s.acce = s.accf + 2;
   s.tslot = reinterpret_cast<uint32_t*>(s.acce + 2);
   s.abort_flag = reinterpret_cast<int*>(s.tslot + 1);
@@ -99,11 +102,11 @@ __device__ __forceinline__ TcSmem tc_smem(unsigned char* raw) {
 }
 
 // Barriers, tensor memory; returns the accumulators' tensor-memory address.
-template <int NPAD>
+template <int NPAD, int NA>
 __device__ __forceinline__ uint32_t tc_setup(const TcSmem& S) {
   const int tid = threadIdx.x;
   if (tid == 0) {
-    for (int s = 0; s < kTcStages; ++s) {
+    for (int s = 0; s < TcCfg<NPAD, NA>::kStages; ++s) {
       mbar_init(smem_u32(&S.full[s]), 1);
       mbar_init(smem_u32(&S.empty[s]), 1);
     }
@@ -115,7 +118,7 @@ __device__ __forceinline__ uint32_t tc_setup(const TcSmem& S) {
     fence_mbar_init();
   }
   if ((tid >> 5) == 0) {
-    tmem_alloc(smem_u32(S.tslot), TcCfg<NPAD>::kCols);
+    tmem_alloc(smem_u32(S.tslot), TcCfg<NPAD, NA>::kCols);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -124,14 +127,14 @@ __device__ __forceinline__ uint32_t tc_setup(const TcSmem& S) {
   return *S.tslot;
 }
 
-template <int NPAD>
+template <int NPAD, int NA>
 __device__ __forceinline__ void tc_teardown(const TcSmem& S, uint32_t tmem, bool timed_out, State* st) {
   if (timed_out) atomicOr(&st->error, static_cast<int>(kErrTimeout));
   tc_fence_before();
   __syncthreads();
   if ((threadIdx.x >> 5) == 0) {
     tc_fence_after();
-    tmem_dealloc(tmem, TcCfg<NPAD>::kCols);
+    tmem_dealloc(tmem, TcCfg<NPAD, NA>::kCols);
   }
 }
 
@@ -139,40 +142,47 @@ __device__ __forceinline__ bool tc_aborted(const TcSmem& S) {
   return *reinterpret_cast<volatile int*>(S.abort_flag) != 0;
 }
 
-// TMA producer: chunk `it` of the launch goes to stage it % kTcStages once
+// TMA producer: chunk `it` of the launch goes to stage it % kStages once
 // the MMAs of its previous use have completed.  load(c, sa, bar) issues the
 // copies of chunk c; false on a timeout.
-template <int NPAD, typename Load>
+template <int NPAD, int NA, typename Load>
 __device__ __forceinline__ bool tc_produce(const TcSmem& S, int it, int c, Load load) {
-  const int s = it % kTcStages;
-  const uint32_t u = static_cast<uint32_t>(it / kTcStages);
+  constexpr int kS = TcCfg<NPAD, NA>::kStages;
+  const int s = it % kS;
+  const uint32_t u = static_cast<uint32_t>(it / kS);
   if (tc_aborted(S) || (u > 0 && !mbar_wait_bounded(smem_u32(&S.empty[s]), (u - 1) & 1))) {
     *S.abort_flag = 1;
     return false;
   }
   const uint32_t bar = smem_u32(&S.full[s]);
-  mbar_arrive_expect_tx(bar, TcCfg<NPAD>::kStage);
-  load(c, S.base + s * TcCfg<NPAD>::kStage, bar);
+  mbar_arrive_expect_tx(bar, TcCfg<NPAD, NA>::kStage);
+  load(c, S.base + s * TcCfg<NPAD, NA>::kStage, bar);
   return true;
 }
 
 // MMA issuer: the 4 MMAs (K = 16 each) of chunk `it` into accumulator it % 2,
 // starting it afresh; then the stage is released and the accumulator handed
 // to the epilogue.  false on a timeout.
-template <int NPAD, typename Descs>
+template <int NPAD, int NA, typename Descs>
 __device__ __forceinline__ bool tc_mma_chunk(const TcSmem& S, uint32_t tmem, int it, uint32_t idesc, Descs descs) {
-  const int s = it % kTcStages, b = it & 1;
-  const uint32_t u = static_cast<uint32_t>(it / kTcStages), ub = static_cast<uint32_t>(it >> 1);
+  constexpr int kS = TcCfg<NPAD, NA>::kStages;
+  const int s = it % kS, b = it & 1;
+  const uint32_t u = static_cast<uint32_t>(it / kS), ub = static_cast<uint32_t>(it >> 1);
   if (ub > 0 && !mbar_wait_bounded(smem_u32(&S.acce[b]), (ub - 1) & 1)) return false;
   if (!mbar_wait_bounded(smem_u32(&S.full[s]), u & 1)) return false;
   tc_fence_after();
-  const uint32_t sa = S.base + s * TcCfg<NPAD>::kStage;
+  const uint32_t sa = S.base + s * TcCfg<NPAD, NA>::kStage;
   const uint32_t d = tmem + static_cast<uint32_t>(b * NPAD);
+  // smallest plane first, so the large terms are added last (the
+  // accumulator's rounding is relative to its magnitude)
 #pragma unroll
-  for (int kk = 0; kk < kTcBK / 16; ++kk) {
-    uint64_t ad, bd;
-    descs(sa, kk, &ad, &bd);
-    umma_f16(d, ad, bd, idesc, kk > 0 ? 1u : 0u);
+  for (int pl = NA - 1; pl >= 0; --pl) {
+#pragma unroll
+    for (int kk = 0; kk < kTcBK / 16; ++kk) {
+      uint64_t ad, bd;
+      descs(sa, pl, kk, &ad, &bd);
+      umma_f16(d, ad, bd, idesc, (pl < NA - 1 || kk > 0) ? 1u : 0u);
+    }
   }
   umma_commit(smem_u32(&S.empty[s]));
   umma_commit(smem_u32(&S.accf[b]));
@@ -183,9 +193,9 @@ __device__ __forceinline__ bool tc_mma_chunk(const TcSmem& S, uint32_t tmem, int
 // groups summed as x0 + (x1 + x2)) into acc[], then releases it.  IEEE float
 // adds per chunk keep the sum at float accuracy however long the reduction
 // dimension is.  false on a timeout.
-template <int NPAD>
-__device__ __forceinline__ bool tc_drain(const TcSmem& S, uint32_t tlane, int it, float (&acc)[TcCfg<NPAD>::MPAD]) {
-  constexpr int MPAD = TcCfg<NPAD>::MPAD;
+template <int NPAD, int NA>
+__device__ __forceinline__ bool tc_drain(const TcSmem& S, uint32_t tlane, int it, float (&acc)[TcCfg<NPAD, NA>::MPAD]) {
+  constexpr int MPAD = TcCfg<NPAD, NA>::MPAD;
   const int b = it & 1;
   if (!mbar_wait_bounded(smem_u32(&S.accf[b]), static_cast<uint32_t>((it >> 1) & 1))) return false;
   tc_fence_after();
@@ -208,13 +218,13 @@ __device__ __forceinline__ bool tc_drain(const TcSmem& S, uint32_t tlane, int it
 
 // ---- pass 1: T = A^T X for 128-column tiles (persistent CTAs), threshold,
 // G3^T for pass 2.  Tensor-memory lane = column of the tile.
-template <int NPAD>
+template <int NPAD, int NA>
 __global__ void __launch_bounds__(kTcThreads, 1) tc_t_kernel(const TcArgs a) {
-  using Cfg = TcCfg<NPAD>;
+  using Cfg = TcCfg<NPAD, NA>;
   constexpr int MPAD = Cfg::MPAD;
   constexpr uint32_t kIdesc = idesc_bf16_f32(NPAD, 0, 0);
   extern __shared__ unsigned char smem_raw[];
-  const TcSmem S = tc_smem<NPAD>(smem_raw);
+  const TcSmem S = tc_smem<NPAD, NA>(smem_raw);
   __shared__ float gam_s[kMaxM], mu_s[kMaxM];
   __shared__ int act_s[kMaxM];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -229,19 +239,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_t_kernel(const TcArgs a) {
     mu_s[tid] = v ? static_cast<float>(io->mu[tid]) : 1.0f;
     act_s[tid] = tid < a.m ? st->active[tid] : 0;
   }
-  const uint32_t tmem = tc_setup<NPAD>(S);
+  const uint32_t tmem = tc_setup<NPAD, NA>(S);
   bool timed_out = false;
 
   if (warp == 4) {  // TMA producer
     if (lane == 0) {
-      tmap_acquire(&maps->a1);
+      for (int pl = 0; pl < NA; ++pl) tmap_acquire(&maps->a1[pl]);
       tmap_acquire(&maps->x3);
       int it = 0;
       for (int tile = blockIdx.x; tile < a.ntile1 && !timed_out; tile += gridDim.x) {
         for (int c = 0; c < a.kchunks1; ++c, ++it) {
-          const bool ok = tc_produce<NPAD>(S, it, c, [&](int cc, uint32_t sa, uint32_t bar) {
-            tma_load_2d(sa, &maps->a1, cc * kTcBK, tile * kTcTile1, bar);
-            tma_load_2d(sa + kTcA, &maps->x3, cc * kTcBK, 0, bar);
+          const bool ok = tc_produce<NPAD, NA>(S, it, c, [&](int cc, uint32_t sa, uint32_t bar) {
+            for (int pl = 0; pl < NA; ++pl) tma_load_2d(sa + pl * kTcA, &maps->a1[pl], cc * kTcBK, tile * kTcTile1, bar);
+            tma_load_2d(sa + Cfg::kAll, &maps->x3, cc * kTcBK, 0, bar);
           });
           if (!ok) {
             timed_out = true;
@@ -255,10 +265,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_t_kernel(const TcArgs a) {
       int it = 0;
       for (int tile = blockIdx.x; tile < a.ntile1 && !timed_out; tile += gridDim.x) {
         for (int c = 0; c < a.kchunks1; ++c, ++it) {
-          const bool ok = tc_mma_chunk<NPAD>(S, tmem, it, kIdesc, [](uint32_t sa, int kk, uint64_t* ad, uint64_t* bd) {
-            *ad = sdesc_sw128(sa + kk * 32, 16, 1024);
-            *bd = sdesc_sw128(sa + kTcA + kk * 32, 16, 1024);
-          });
+          const bool ok =
+              tc_mma_chunk<NPAD, NA>(S, tmem, it, kIdesc, [](uint32_t sa, int pl, int kk, uint64_t* ad, uint64_t* bd) {
+                *ad = sdesc_sw128(sa + pl * kTcA + kk * 32, 16, 1024);
+                *bd = sdesc_sw128(sa + Cfg::kAll + kk * 32, 16, 1024);
+              });
           if (!ok) {
             timed_out = true;
             *S.abort_flag = 1;
@@ -278,7 +289,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_t_kernel(const TcArgs a) {
 #pragma unroll
       for (int j = 0; j < MPAD; ++j) t[j] = 0.0f;
       for (int c = 0; c < a.kchunks1; ++c, ++it) {
-        if (!tc_drain<NPAD>(S, tlane, it, t)) {
+        if (!tc_drain<NPAD, NA>(S, tlane, it, t)) {
           timed_out = true;
           *S.abort_flag = 1;
           break;
@@ -287,12 +298,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_t_kernel(const TcArgs a) {
       if (timed_out) break;
       const int i = tile * kTcTile1 + warp * 32 + lane;
       if (i < a.n) {
+        const float scl = a.scaled ? io->col_scale[i] : 1.0f;
 #pragma unroll
         for (int j = 0; j < MPAD; ++j) {
           float g = 0.0f;
           if (j < a.m) {
-            if (!sketch && act_s[j]) Tout[static_cast<int64_t>(j) * a.n + i] = t[j];
-            g = grad_factor<float>(form, t[j], gam_s[j], mu_s[j]);
+            const float tj = t[j] * scl;
+            if (!sketch && act_s[j]) Tout[static_cast<int64_t>(j) * a.n + i] = tj;
+            g = grad_factor<float>(form, tj, gam_s[j], mu_s[j]) * scl;
           }
           __nv_bfloat16 b0, b1, b2;
           split3(g, b0, b1, b2);
@@ -303,37 +316,39 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_t_kernel(const TcArgs a) {
       }
     }
   }
-  tc_teardown<NPAD>(S, tmem, timed_out, st);
+  tc_teardown<NPAD, NA>(S, tmem, timed_out, st);
 }
 
 // ---- pass 2: Y = A G for 128-row blocks, the columns split over gridDim.y;
 // partial sums to ypart[split].  Tensor-memory lane = row of the block.  The
 // A tile is the operand in MN-major form (64 rows contiguous per column).
-template <int NPAD>
+template <int NPAD, int NA>
 __global__ void __launch_bounds__(kTcThreads, 1) tc_y_kernel(const TcArgs a) {
-  using Cfg = TcCfg<NPAD>;
+  using Cfg = TcCfg<NPAD, NA>;
   constexpr int MPAD = Cfg::MPAD;
   constexpr uint32_t kIdesc = idesc_bf16_f32(NPAD, 1, 0);
   extern __shared__ unsigned char smem_raw[];
-  const TcSmem S = tc_smem<NPAD>(smem_raw);
+  const TcSmem S = tc_smem<NPAD, NA>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const IO* io = a.io;
   State* st = a.st;
   const TcMaps* maps = static_cast<const TcMaps*>(io->tc_maps);
   const int rb = blockIdx.x, sp = blockIdx.y;
   const int cb = sp * a.kps2, ce = min(a.nchunks2, cb + a.kps2);
-  const uint32_t tmem = tc_setup<NPAD>(S);
+  const uint32_t tmem = tc_setup<NPAD, NA>(S);
   bool timed_out = false;
 
   if (warp == 4) {  // TMA producer
     if (lane == 0) {
-      tmap_acquire(&maps->a2);
+      for (int pl = 0; pl < NA; ++pl) tmap_acquire(&maps->a2[pl]);
       tmap_acquire(&maps->g3);
       for (int c = cb, it = 0; c < ce; ++c, ++it) {
-        const bool ok = tc_produce<NPAD>(S, it, c, [&](int cc, uint32_t sa, uint32_t bar) {
-          tma_load_2d(sa, &maps->a2, rb * kTcRows2, cc * kTcBK, bar);
-          tma_load_2d(sa + kTcA / 2, &maps->a2, rb * kTcRows2 + 64, cc * kTcBK, bar);
-          tma_load_2d(sa + kTcA, &maps->g3, cc * kTcBK, 0, bar);
+        const bool ok = tc_produce<NPAD, NA>(S, it, c, [&](int cc, uint32_t sa, uint32_t bar) {
+          for (int pl = 0; pl < NA; ++pl) {
+            tma_load_2d(sa + pl * kTcA, &maps->a2[pl], rb * kTcRows2, cc * kTcBK, bar);
+            tma_load_2d(sa + pl * kTcA + kTcA / 2, &maps->a2[pl], rb * kTcRows2 + 64, cc * kTcBK, bar);
+          }
+          tma_load_2d(sa + Cfg::kAll, &maps->g3, cc * kTcBK, 0, bar);
         });
         if (!ok) {
           timed_out = true;
@@ -346,10 +361,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_y_kernel(const TcArgs a) {
       for (int c = cb, it = 0; c < ce; ++c, ++it) {
         // A: rows 0-63 and 64-127 are the two MN atoms (LBO apart), 8 columns
         // per 1024-byte atom (SBO); B: K-major as in pass 1
-        const bool ok = tc_mma_chunk<NPAD>(S, tmem, it, kIdesc, [](uint32_t sa, int kk, uint64_t* ad, uint64_t* bd) {
-          *ad = sdesc_sw128(sa + kk * 2048, kTcA / 2, 1024);
-          *bd = sdesc_sw128(sa + kTcA + kk * 32, 16, 1024);
-        });
+        const bool ok =
+            tc_mma_chunk<NPAD, NA>(S, tmem, it, kIdesc, [](uint32_t sa, int pl, int kk, uint64_t* ad, uint64_t* bd) {
+              *ad = sdesc_sw128(sa + pl * kTcA + kk * 2048, kTcA / 2, 1024);
+              *bd = sdesc_sw128(sa + Cfg::kAll + kk * 32, 16, 1024);
+            });
         if (!ok) {
           timed_out = true;
           *S.abort_flag = 1;
@@ -363,7 +379,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_y_kernel(const TcArgs a) {
 #pragma unroll
     for (int j = 0; j < MPAD; ++j) y[j] = 0.0f;
     for (int c = cb, it = 0; c < ce; ++c, ++it) {
-      if (!tc_drain<NPAD>(S, tlane, it, y)) {
+      if (!tc_drain<NPAD, NA>(S, tlane, it, y)) {
         timed_out = true;
         *S.abort_flag = 1;
         break;
@@ -377,12 +393,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_y_kernel(const TcArgs a) {
         if (j < a.m) yp[(static_cast<int64_t>(sp) * a.m + j) * a.p + r] = y[j];
     }
   }
-  tc_teardown<NPAD>(S, tmem, timed_out, st);
+  tc_teardown<NPAD, NA>(S, tmem, timed_out, st);
 }
 
 // ---------------------------------------------------------------- host
 
-int tc_smem_bytes(int npad) { return kTcStages * (static_cast<int>(kTcA) + npad * 128) + 1024 + 512; }
+int tc_smem_bytes(int npad, int na) {
+  const int stages = na == 1 ? 5 : 3;
+  return stages * (na * static_cast<int>(kTcA) + npad * 128) + 1024 + 512;
+}
 
 bool tc_supported(int device) {
   int major = 0, minor = 0;
@@ -423,38 +442,83 @@ static bool encode_bf16(CUtensorMap* m, const void* base, int64_t inner, int64_t
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-int tc_encode_maps(TcMaps* maps, const void* A, int64_t p, int64_t n, int64_t ld, const void* x3, int p_pad,
-                   const void* g3, int n_pad, int npad) {
-  if (!encode_bf16(&maps->a1, A, p, n, ld, kTcTile1) || !encode_bf16(&maps->x3, x3, p, npad, p_pad, npad) ||
-      !encode_bf16(&maps->a2, A, p, n, ld, 64) || !encode_bf16(&maps->g3, g3, n, npad, n_pad, npad))
-    return record_error(GPSPCA_ECUDA, "cuTensorMapEncodeTiled failed for the tensor-core sweep");
+int tc_encode_maps(TcMaps* maps, const void* planes, int na, int64_t plane, int64_t p, int64_t n, int64_t ld,
+                   const void* x3, int p_pad, const void* g3, int n_pad, int npad) {
+  bool ok = encode_bf16(&maps->x3, x3, p, npad, p_pad, npad) && encode_bf16(&maps->g3, g3, n, npad, n_pad, npad);
+  for (int pl = 0; pl < na && ok; ++pl) {
+    const void* base = static_cast<const __nv_bfloat16*>(planes) + pl * plane;
+    ok = encode_bf16(&maps->a1[pl], base, p, n, ld, kTcTile1) && encode_bf16(&maps->a2[pl], base, p, n, ld, 64);
+  }
+  if (!ok) return record_error(GPSPCA_ECUDA, "cuTensorMapEncodeTiled failed for the tensor-core sweep");
   return GPSPCA_OK;
 }
 
-template <int NPAD>
+// float A -> three bf16 planes (a = a0 + a1 + a2 exactly); fp8 -> its values
+// in bf16 (exact; the column scale stays separate).  Grid-stride over A.
+template <typename TA>
+__global__ void tc_convert_kernel(const IO* io, int64_t p, int64_t n, int64_t ld, int64_t ldc) {
+  const TA* A = static_cast<const TA*>(io->A);
+  __nv_bfloat16* planes = static_cast<__nv_bfloat16*>(io->tc_planes);
+  const int64_t plane = n * ldc;
+  const int64_t total = n * p;
+  for (int64_t q = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; q < total;
+       q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = q / p, r = q - i * p;
+    const float v = to_tc<TA>(A[i * ld + r]);
+    if constexpr (sizeof(TA) == 4) {
+      __nv_bfloat16 b0, b1, b2;
+      split3(v, b0, b1, b2);
+      planes[i * ldc + r] = b0;
+      planes[plane + i * ldc + r] = b1;
+      planes[2 * plane + i * ldc + r] = b2;
+    } else {
+      planes[i * ldc + r] = __float2bfloat16_rn(v);
+    }
+  }
+}
+
+void launch_tc_convert(int dtype, const IO* io, int64_t p, int64_t n, int64_t ld, int64_t ldc, cudaStream_t s) {
+  int dev = 0, nsm = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (dtype == GPSPCA_F32)
+    tc_convert_kernel<float><<<nsm * 8, 256, 0, s>>>(io, p, n, ld, ldc);
+  else if (dtype == GPSPCA_FP8_E4M3)
+    tc_convert_kernel<__nv_fp8_e4m3><<<nsm * 8, 256, 0, s>>>(io, p, n, ld, ldc);
+}
+
+template <int NPAD, int NA>
 static void launch_tc_npad(const TcArgs& a, int nsm, cudaStream_t s) {
   static bool once = [] {
-    cudaFuncSetAttribute(tc_t_kernel<NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem_bytes(NPAD));
-    cudaFuncSetAttribute(tc_y_kernel<NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem_bytes(NPAD));
+    cudaFuncSetAttribute(tc_t_kernel<NPAD, NA>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem_bytes(NPAD, NA));
+    cudaFuncSetAttribute(tc_y_kernel<NPAD, NA>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem_bytes(NPAD, NA));
     return true;
   }();
   (void)once;
-  const int smem = tc_smem_bytes(NPAD);
+  const int smem = tc_smem_bytes(NPAD, NA);
   tc_prep_kernel<<<(a.p + 255) / 256, 256, 0, s>>>(a);
-  tc_t_kernel<NPAD><<<std::max(1, std::min(a.ntile1, nsm)), kTcThreads, smem, s>>>(a);
-  tc_y_kernel<NPAD><<<dim3(a.nrow2, a.nsplit2), kTcThreads, smem, s>>>(a);
+  tc_t_kernel<NPAD, NA><<<std::max(1, std::min(a.ntile1, nsm)), kTcThreads, smem, s>>>(a);
+  tc_y_kernel<NPAD, NA><<<dim3(a.nrow2, a.nsplit2), kTcThreads, smem, s>>>(a);
+}
+
+template <int NA>
+static void launch_tc_na(const TcArgs& a, int npad, int nsm, cudaStream_t s) {
+  switch (npad) {
+    case 48: launch_tc_npad<48, NA>(a, nsm, s); break;
+    case 96: launch_tc_npad<96, NA>(a, nsm, s); break;
+    case 144: launch_tc_npad<144, NA>(a, nsm, s); break;
+    default: launch_tc_npad<192, NA>(a, nsm, s); break;
+  }
 }
 
 void launch_tc_sweep(const TcArgs& a, int npad, cudaStream_t s) {
   int dev = 0, nsm = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  switch (npad) {
-    case 48: launch_tc_npad<48>(a, nsm, s); break;
-    case 96: launch_tc_npad<96>(a, nsm, s); break;
-    case 144: launch_tc_npad<144>(a, nsm, s); break;
-    default: launch_tc_npad<192>(a, nsm, s); break;
-  }
+  if (a.na == 3)
+    launch_tc_na<3>(a, npad, nsm, s);
+  else
+    launch_tc_na<1>(a, npad, nsm, s);
 }
 
 }  // namespace gpspca

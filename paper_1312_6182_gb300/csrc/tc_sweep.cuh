@@ -15,7 +15,12 @@
 // (x = x0 + x1 + x2 exactly, 24 significant bits), laid side by side as the
 // N = 3 mpad columns of one MMA, so the tensor cores form A x0, A x1, A x2 in
 // float accumulators and the epilogue adds them (x0 + (x1 + x2)): the
-// products are those of float X against the stored A.
+// products are those of float X against the stored A.  A float A is split
+// the same way once per solve into three bf16 planes (a0 + a1 + a2 = a
+// exactly), whose MMAs go into the same accumulator smallest plane first;
+// fp8 values are exact in bf16 (one plane) with the column scale applied in
+// the epilogue.  Each 64-deep chunk's accumulator is drained into registers
+// (IEEE float adds), so the sum keeps float accuracy for any p or n.
 //
 // Why two passes and not one: the rank update's accumulator Y (p x 3 mpad
 // floats) must stay in tensor memory (256 KB per SM) across every column
@@ -40,16 +45,18 @@ constexpr int kTcRows2 = 128;    // rows of A per Y-pass block (the MMA's M)
 // TMA descriptors of one solve (device memory, refreshed by the host before
 // each solve).
 struct TcMaps {
-  CUtensorMap a1;  // A, box 64 rows x 128 columns (T pass)
-  CUtensorMap x3;  // X3^T, box 64 x N
-  CUtensorMap a2;  // A, box 64 rows x 64 columns (Y pass)
-  CUtensorMap g3;  // G3^T, box 64 x N
+  CUtensorMap a1[3];  // bf16 planes of A, box 64 rows x 128 columns (T pass)
+  CUtensorMap x3;     // X3^T, box 64 x N
+  CUtensorMap a2[3];  // bf16 planes of A, box 64 rows x 64 columns (Y pass)
+  CUtensorMap g3;     // G3^T, box 64 x N
 };
 
 struct TcArgs {
   const IO* io;
   State* st;
   int p, n, m, mpad, form, sketch;
+  int na;             // bf16 planes of A: 1 (bf16 storage, or the fp8 values), 3 (float A = a0 + a1 + a2)
+  int scaled;         // fp8 storage: a_i = s_i q_i, the column scale applied to t and g
   int p_pad, n_pad;   // row strides (elements) of X3^T and G3^T
   int ntile1;         // ceil(n / 128)
   int kchunks1;       // ceil(p / 64)
@@ -60,10 +67,13 @@ struct TcArgs {
 };
 
 // Host side (tc_sweep.cu).
-int tc_smem_bytes(int npad);
+int tc_smem_bytes(int npad, int na);
 bool tc_supported(int device);
-int tc_encode_maps(TcMaps* maps, const void* A, int64_t p, int64_t n, int64_t ld, const void* x3, int p_pad,
-                   const void* g3, int n_pad, int npad);
+// planes: na bf16 matrices (p x n, column stride ld elements, `plane` elements apart)
+int tc_encode_maps(TcMaps* maps, const void* planes, int na, int64_t plane, int64_t p, int64_t n, int64_t ld,
+                   const void* x3, int p_pad, const void* g3, int n_pad, int npad);
+// float / fp8 A -> bf16 planes in the workspace (once per solve); ldc = p_pad
+void launch_tc_convert(int dtype, const IO* io, int64_t p, int64_t n, int64_t ld, int64_t ldc, cudaStream_t s);
 void launch_tc_sweep(const TcArgs& a, int npad, cudaStream_t s);
 
 }  // namespace gpspca
