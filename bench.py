@@ -30,6 +30,11 @@ MU_W = [1.0, 0.9, 0.8, 0.7, 0.6]
 CASES = [("SL1", None), ("SL0", None), ("BL1", [1.0] * 5), ("BL0", [1.0] * 5), ("BL1", MU_W), ("BL0", MU_W)]
 TOL, MAXIT = 1e-6, 1000
 RHO32 = 0.01
+# dram bytes (read + write) of one launch of the fused sweeps on this matrix,
+# from an ncu capture of the current kernels (dram__bytes_read.sum +
+# dram__bytes_write.sum)
+TRAFFIC_SL1 = 403.49e6
+TRAFFIC_BL1 = 403.90e6
 METRIC = "GPower iters/s"
 UNIT = "iters/s"
 WORKLOAD = "planted spikes 5000x20000 fp32 (5 spikes, theta_j=40/j, 5% supports), SL1+SL0+BL1+BL0 (m=5, mu=1 and mu=[1,.9,.8,.7,.6]), gamma=0.05*max||a_i||, tol 1e-6"
@@ -155,11 +160,13 @@ def run_gpu(args):
             m = 1 if mu is None else len(mu)
             dres, hres = outs[(form, tuple(mu) if mu else None)]
             res = ctx.solve(hA if host else dA, form, [RHO] * m, mu=mu, tol=TOL, maxit=MAXIT,
-                            gamma_relative=True, out=hres if host else dres)
+                            gamma_relative=True, out=hres if host else dres, eager=args.eager)
             it = int(res.iters.max().item())
             sweeps += it
-            passes = 1
-            launches += 6 + it * (passes + 2) + 1
+            # reset, norms, selection, gather, reduction + finish of the start
+            # (+ 3 x {sketch sweep, reduction, finish} for the block start),
+            # one {sweep, reduction, finish} per iteration, the loadings
+            launches += 6 + (9 if form.startswith("B") else 0) + 3 * it + 1
         return sweeps, launches
 
     torch.cuda.synchronize()
@@ -233,11 +240,13 @@ def run_gpu(args):
                    "l2": "inputs larger than L2 (A is 400 MB)", "parallelism": "replicas" if ws > 1 else "1 gpu"},
         "roofline": {"bound": "hbm", "kernel": "sweep_kernel<float,1,*> (single-unit fused sweep)",
                      "achieved": round(ach_su, 1), "peak": peak, "unit": "GB/s", "frac": round(ach_su / peak, 4),
-                     "peak_source": peak_kind, "traffic": None, "ms_per_launch": round(ms_su, 5),
-                     "algorithmic_bytes_per_launch": bytes_a},
+                     "peak_source": peak_kind, "traffic": TRAFFIC_SL1, "ms_per_launch": round(ms_su, 5),
+                     "algorithmic_bytes_per_launch": bytes_a,
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch"},
         "roofline_block": {"bound": "hbm", "kernel": "sweep_kernel<float,5,*> (block m=5 fused sweep)",
                            "achieved": round(ach_blk, 1), "peak": peak, "unit": "GB/s",
-                           "frac": round(ach_blk / peak, 4), "ms_per_launch": round(ms_blk, 5)},
+                           "frac": round(ach_blk / peak, 4), "ms_per_launch": round(ms_blk, 5),
+                           "traffic": TRAFFIC_BL1},
         "e2e": {"value": round(e2e_sweeps / (e2e_ms / 1e3), 2), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": total_launches,
@@ -338,8 +347,8 @@ def run_sweep_only(args):
     else:
         dA = torch.from_numpy(At).cuda()
     form = args.sweep_only
-    m = 1 if form.startswith("S") else args.sweep_m
-    mu = None if m == 1 else [1.0] * m
+    m = args.sweep_m or (1 if form.startswith("S") else 5)
+    mu = [1.0] * m if form.startswith("B") else None
     with binding.Context(0) as ctx:
         ms = ctx.time_sweep(dA, form, [RHO] * m, mu=mu, gamma_relative=True, reps=args.reps)
     nbytes = P * N * dA.element_size()
@@ -684,7 +693,7 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--sweep-only", default=None, choices=["SL1", "SL0", "BL1", "BL0"],
                     help="time the fused sweep alone on the benchmark matrix (profiling)")
-    ap.add_argument("--sweep-m", type=int, default=5)
+    ap.add_argument("--sweep-m", type=int, default=None, help="sweep-only: components or gammas (default 1 / 5)")
     ap.add_argument("--sweep-dtype", default="f32", choices=["f32", "bf16"])
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--workload", default="spikes5000", choices=["spikes5000", "gamma-path", "precision", "serving"],
@@ -692,6 +701,9 @@ def main():
                          "BF16/FP8 precision path (one JSON line each)")
     ap.add_argument("--oracle", action="store_true", help="precision workload: errors against the FP64 oracle")
     ap.add_argument("--requests", type=int, default=2000, help="serving workload: number of requests")
+    ap.add_argument("--eager", action="store_true",
+                    help="launch each solve's kernels one by one (profilers cannot follow the CUDA graph's "
+                         "conditional node); slower, for launch lists only")
     args = ap.parse_args()
     if args.sweep_only:
         run_sweep_only(args)

@@ -83,7 +83,8 @@ typedef enum { GPSPCA_DEVICE = 0, GPSPCA_HOST = 1 } gpspca_location;
                                      node: for profilers and debuggers that cannot follow
                                      conditional graph nodes.  Results are identical. */
 #define GPSPCA_NO_TENSOR_CORES 4u /* run the CUDA-core fused sweep even where the tensor-core
-                                     (tcgen05) sweep applies (bf16 storage, m >= 16) */
+                                     (tcgen05) sweep applies (bf16 storage with m >= 6, float or
+                                     fp8 storage with m >= 9) */
 
 /* Largest m (components, or gamma values of a path) one solve accepts. */
 #define GPSPCA_MAX_M 64

@@ -217,12 +217,16 @@ int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fa
   pl.esize = d.esize;
   const int unit = std::max(d.align, d.vec);
   bool found = false;
-  // the tensor-core sweep for 16 or more components (or gamma values): bf16
-  // storage read in place (TMA-compatible layout: 16-byte aligned base and
-  // column stride), float A as three bf16 planes and fp8 A as one, copied
-  // once per solve
+  // the tensor-core sweep where the CUDA-core passes become compute-bound:
+  // bf16 storage read in place (TMA-compatible layout: 16-byte aligned base
+  // and column stride) from 6 components (or gamma values) on; float A as
+  // three bf16 planes and fp8 A as one, copied once per solve, from 9 on (one
+  // CUDA-core pass covers up to 8).  Crossovers measured on GB300 over
+  // p x n in {5000 x 20000, 2000 x 60000, 8000 x 8000}.
   const bool native_bf16 = dt == GPSPCA_BF16 && fast && ld % 8 == 0;
-  if (allow_tc && m >= 16 && p >= 1 && n >= 1 && (native_bf16 || dt == GPSPCA_F32 || dt == GPSPCA_FP8_E4M3)) {
+  const int tc_min_m = native_bf16 ? 6 : 9;
+  if (allow_tc && m >= tc_min_m && p >= 1 && n >= 1 &&
+      (native_bf16 || dt == GPSPCA_F32 || dt == GPSPCA_FP8_E4M3)) {
     plan_tc(&pl, m, p, n, nsm);
     pl.tc_na = dt == GPSPCA_F32 ? 3 : 1;
     pl.tc_convert = native_bf16 ? 0 : 1;

@@ -160,6 +160,7 @@ struct SweepSmem {
   int stage_bytes, bars, xbars, red, xrecv, wsm, total;
 };
 constexpr int kMaxCluster = 8;
+constexpr int kXSlots = 2;  // cluster-exchange slots, by tile parity
 __host__ __device__ inline int align_up(int v, int a) { return (v + a - 1) / a * a; }
 __host__ __device__ inline SweepSmem sweep_smem_layout(int W, int S, int ps, int esize, int tcsize, int nwarps, int m,
                                                       int mg) {
@@ -170,10 +171,10 @@ __host__ __device__ inline SweepSmem sweep_smem_layout(int W, int S, int ps, int
   // after the ring covers the largest overshoot (< 33 * NCH * VEC elements).
   int o = align_up(S * L.stage_bytes + kRingSlack, 128);
   L.bars = o; o += 8 * S;         // tile-copy mbarriers
-  L.xbars = o; o += 8 * 2;        // cluster-exchange mbarriers (by tile parity)
+  L.xbars = o; o += 8 * kXSlots;  // cluster-exchange mbarriers (tile mod kXSlots)
   o = align_up(o, 16);
   L.red = o; o += 2 * nwarps * 32 * tcsize;          // warp partials, by tile parity
-  L.xrecv = o; o += 2 * kMaxCluster * 32 * tcsize;   // partials pushed by cluster peers
+  L.xrecv = o; o += kXSlots * kMaxCluster * 32 * tcsize;  // partials pushed by cluster peers
   L.wsm = o; o += m * mg * tcsize;
   L.total = align_up(o, 128);
   return L;
@@ -276,8 +277,7 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH>::MAXT, 1) sweep_kernel(c
   if (tid == 0) {
     if (a.fast)
       for (int s = 0; s < S; ++s) mbar_init(smem_u32(&bars[s]), 1);
-    mbar_init(smem_u32(&xbars[0]), 1);
-    mbar_init(smem_u32(&xbars[1]), 1);
+    for (int xs = 0; xs < kXSlots; ++xs) mbar_init(smem_u32(&xbars[xs]), 1);
     fence_mbar_init();
   }
   __syncthreads();
@@ -351,30 +351,32 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH>::MAXT, 1) sweep_kernel(c
   bool timed_out = false;
   TC* Tout = static_cast<TC*>(io->T);
   const float* cscale = io->col_scale;
+  // lane L of every warp owns slot L = (column w = L / MG, component j = L % MG)
+  const int wq = lane / MG, jq = lane % MG;
 
-  for (int tile = 0; tile < ntiles; ++tile) {
-    const int buf = a.fast ? tile % S : 0;
+  // Tiles run in order: phase A (partial dots, CTA total, push to the
+  // cluster peers), then phase B (the peers' totals, threshold, rank update).
+  // Overlapping phase A of tile t+1 with phase B of tile t was measured
+  // slower on GB300 (it costs a stage of prefetch or narrower tiles, and
+  // full-width tiles with the deeper ring matter more).
+
+  // phase A: returns this CTA's total for its lane's slot of tile `tile`
+  auto phase_a = [&](int tile) -> TC {
+    const int buf = tile % S;
     const TA* sb = stage + buf * stage_elems;
     const int c0 = col_begin + tile * W;
     const int wv = min(W, col_end - c0);
     if (a.fast) {
       if (!mbar_wait_bounded(smem_u32(&bars[buf]), static_cast<uint32_t>((tile / S) & 1))) timed_out = true;
     } else {
-      __syncthreads();  // previous tile fully consumed
-      TA* sbw = stage;
+      __syncthreads();  // the buffer's previous tile (tile - S) is fully consumed
+      TA* sbw = stage + buf * stage_elems;
       for (int w = 0; w < wv; ++w) {
         const TA* src = A + static_cast<int64_t>(c0 + w) * ld + row0;
         for (int r = tid; r < rows_valid; r += nthr) sbw[w * ps + r] = src[r];
       }
       __syncthreads();
     }
-
-    // lane L of every warp owns slot L = (column w = L / MG, component j = L % MG)
-    const int wq = lane / MG, jq = lane % MG;
-    const bool mine_valid = lane < WB * MG && wq < wv && jq < a.mg_valid;
-    TC scl = TC(1);
-    if (kFP8 && mine_valid) scl = static_cast<TC>(cscale[c0 + wq]);
-
     // partial dots over this thread's rows
     TC pd[KB];
 #pragma unroll
@@ -398,42 +400,52 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH>::MAXT, 1) sweep_kernel(c
     }
     // Lane L holds the warp total of slot L % KB.  One block barrier per
     // tile: afterwards every warp adds the warp totals itself (partials are
-    // double-buffered by tile parity), so no second barrier is needed to
-    // broadcast the thresholded values.
+    // double-buffered by tile parity).
     const TC mine = warp_reduce_scatter<KB>(pd, lane);
     TC* redp = red + (tile & 1) * nwarps * 32;
     redp[warp * 32 + lane] = mine;
-    const int xp = tile & 1;
+    const int xs = tile % kXSlots;
     if (C > 1 && tid == 0)  // this tile's pushes from the C-1 peers
-      mbar_arrive_expect_tx(smem_u32(&xbars[xp]), static_cast<uint32_t>((C - 1) * KB * sizeof(TC)));
-    __syncthreads();  // (1) warp partials visible; the previous tile's buffer is free
+      mbar_arrive_expect_tx(smem_u32(&xbars[xs]), static_cast<uint32_t>((C - 1) * KB * sizeof(TC)));
+    __syncthreads();  // (1) warp partials visible; phase B of the previous tile is done everywhere
     if (a.fast && tid == 0 && tile >= 1 && tile - 1 + S < ntiles) issue_tile(tile - 1 + S, (tile - 1) % S);
     TC t = 0;
     for (int w2 = 0; w2 < nwarps; ++w2) t += redp[w2 * 32 + lane];
-    if (C > 1) {
-      // push this CTA's partial to every peer (one-way), wait for theirs,
-      // add all C in rank order: every CTA of the cluster holds the same t
-      TC* slot = xrecv + xp * kMaxCluster * 32;
-      if (warp == 0 && lane < KB) {
-        const uint32_t src = smem_u32(&slot[cr * 32 + lane]);
-        const uint32_t bar = smem_u32(&xbars[xp]);
-        for (uint32_t r = 0; r < C; ++r)
-          if (r != cr) st_async_remote(dsmem_map(src, r), t, dsmem_map(bar, r));
-      }
-      if (!mbar_wait_bounded(smem_u32(&xbars[xp]), static_cast<uint32_t>((tile >> 1) & 1))) timed_out = true;
+    if (C > 1 && warp == 0 && lane < KB) {  // push this CTA's total to every peer (one-way)
+      TC* slot = xrecv + xs * kMaxCluster * 32;
+      const uint32_t src = smem_u32(&slot[cr * 32 + lane]);
+      const uint32_t bar = smem_u32(&xbars[xs]);
+      for (uint32_t r = 0; r < C; ++r)
+        if (r != cr) st_async_remote(dsmem_map(src, r), t, dsmem_map(bar, r));
+    }
+    return t;
+  };
+
+  // phase B: the cluster total, threshold, T, rank update of tile `tile`
+  auto phase_b = [&](int tile, TC t) {
+    const int buf = tile % S;
+    const TA* sb = stage + buf * stage_elems;
+    const int c0 = col_begin + tile * W;
+    const int wv = min(W, col_end - c0);
+    const bool mine_valid = lane < WB * MG && wq < wv && jq < a.mg_valid;
+    if (C > 1) {  // wait for the peers' totals, add all C in rank order
+      const int xs = tile % kXSlots;
+      TC* slot = xrecv + xs * kMaxCluster * 32;
+      if (!mbar_wait_bounded(smem_u32(&xbars[xs]), static_cast<uint32_t>((tile / kXSlots) & 1))) timed_out = true;
       TC tot = 0;
       for (uint32_t r = 0; r < C; ++r) tot += (r == cr) ? t : slot[r * 32 + lane];
       t = tot;
     }
+    TC scl = TC(1);
+    if (kFP8 && mine_valid) scl = static_cast<TC>(cscale[c0 + wq]);
     TC g = 0;
     if (mine_valid) {
       t *= scl;
       g = grad_factor<TC>(form, t, gam_c[jq], mu_c[jq]) * scl;
     }
-    // T for the objective (formed in double by the reduction) and the loadings
+    // T for the objective (formed by the reduction) and the loadings
     if (warp == 0 && mine_valid && cr == 0 && !sketch && act[jq])
       Tout[static_cast<int64_t>(a.j0 + jq) * n + c0 + wq] = t;
-
     // rank update y += g a over this thread's rows of the tile
 #pragma unroll
     for (int w = 0; w < WB; ++w) {
@@ -453,7 +465,9 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH>::MAXT, 1) sweep_kernel(c
         }
       }
     }
-  }
+  };
+
+  for (int tile = 0; tile < ntiles; ++tile) phase_b(tile, phase_a(tile));
 
   // ---- epilogue: this cluster's partial of Y = A G and of the objective
   TC* yp = static_cast<TC*>(io->ypart);

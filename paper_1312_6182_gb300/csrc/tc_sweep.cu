@@ -59,13 +59,18 @@ __global__ void tc_prep_kernel(const TcArgs a) {
   }
 }
 
+__host__ __device__ constexpr int tc_stages(int npad, int na) { return na == 3 ? 3 : (npad <= 48 ? 4 : (npad <= 96 ? 3 : 5)); }
+__host__ __device__ constexpr int tc_ctas_per_sm(int npad, int na) { return na == 1 && npad <= 96 ? 2 : 1; }
+
 template <int NPAD, int NA>
 struct TcCfg {
   static constexpr int MPAD = NPAD / 3;
   static constexpr uint32_t kAll = NA * kTcA;  // A planes per stage
   static constexpr uint32_t kB = NPAD * 128;   // X3 / G3 bytes per stage: NPAD rows x 64 bf16
   static constexpr uint32_t kStage = kAll + kB;
-  static constexpr int kStages = NA == 1 ? 5 : 3;
+  // ring depth: small N keeps two CTAs per SM (shared memory and tensor
+  // memory both fit twice), which also absorbs the T pass's tile tail
+  static constexpr int kStages = tc_stages(NPAD, NA);
   // two accumulators (ping-pong): the MMAs of one 64-deep chunk fill one while
   // the epilogue drains the other
   static constexpr uint32_t kCols = 2 * NPAD <= 128 ? 128 : (2 * NPAD <= 256 ? 256 : 512);
@@ -219,7 +224,7 @@ __device__ __forceinline__ bool tc_drain(const TcSmem& S, uint32_t tlane, int it
 // ---- pass 1: T = A^T X for 128-column tiles (persistent CTAs), threshold,
 // G3^T for pass 2.  Tensor-memory lane = column of the tile.
 template <int NPAD, int NA>
-__global__ void __launch_bounds__(kTcThreads, 1) tc_t_kernel(const TcArgs a) {
+__global__ void __launch_bounds__(kTcThreads) tc_t_kernel(const TcArgs a) {
   using Cfg = TcCfg<NPAD, NA>;
   constexpr int MPAD = Cfg::MPAD;
   constexpr uint32_t kIdesc = idesc_bf16_f32(NPAD, 0, 0);
@@ -323,7 +328,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_t_kernel(const TcArgs a) {
 // partial sums to ypart[split].  Tensor-memory lane = row of the block.  The
 // A tile is the operand in MN-major form (64 rows contiguous per column).
 template <int NPAD, int NA>
-__global__ void __launch_bounds__(kTcThreads, 1) tc_y_kernel(const TcArgs a) {
+__global__ void __launch_bounds__(kTcThreads) tc_y_kernel(const TcArgs a) {
   using Cfg = TcCfg<NPAD, NA>;
   constexpr int MPAD = Cfg::MPAD;
   constexpr uint32_t kIdesc = idesc_bf16_f32(NPAD, 1, 0);
@@ -399,8 +404,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_y_kernel(const TcArgs a) {
 // ---------------------------------------------------------------- host
 
 int tc_smem_bytes(int npad, int na) {
-  const int stages = na == 1 ? 5 : 3;
-  return stages * (na * static_cast<int>(kTcA) + npad * 128) + 1024 + 512;
+  return tc_stages(npad, na) * (na * static_cast<int>(kTcA) + npad * 128) + 1024 + 512;
 }
 
 bool tc_supported(int device) {
@@ -497,7 +501,7 @@ static void launch_tc_npad(const TcArgs& a, int nsm, cudaStream_t s) {
   (void)once;
   const int smem = tc_smem_bytes(NPAD, NA);
   tc_prep_kernel<<<(a.p + 255) / 256, 256, 0, s>>>(a);
-  tc_t_kernel<NPAD, NA><<<std::max(1, std::min(a.ntile1, nsm)), kTcThreads, smem, s>>>(a);
+  tc_t_kernel<NPAD, NA><<<std::max(1, std::min(a.ntile1, tc_ctas_per_sm(NPAD, NA) * nsm)), kTcThreads, smem, s>>>(a);
   tc_y_kernel<NPAD, NA><<<dim3(a.nrow2, a.nsplit2), kTcThreads, smem, s>>>(a);
 }
 

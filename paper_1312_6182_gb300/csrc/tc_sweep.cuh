@@ -1,5 +1,6 @@
-// The wide sweep on the 5th-generation tensor cores (tcgen05): for m >= 16
-// components (or gamma values), one power iteration is two tall-skinny
+// The wide sweep on the 5th-generation tensor cores (tcgen05): for many
+// components (or gamma values; the planner's crossover is m >= 6 for bf16
+// storage, m >= 9 otherwise), one power iteration is two tall-skinny
 // contractions over A,
 //
 //   T = A^T X   (n x m; then the Table 1 threshold gives G, per entry)
@@ -24,8 +25,8 @@
 //
 // Why two passes and not one: the rank update's accumulator Y (p x 3 mpad
 // floats) must stay in tensor memory (256 KB per SM) across every column
-// tile of a CTA's share of A; for the shapes that need this path (m >= 16,
-// p in the thousands) it does not fit, while T's accumulator (128 columns x
+// tile of a CTA's share of A; for the shapes that need this path (many
+// components, p in the thousands) it does not fit, while T's accumulator (128 columns x
 // 3 mpad) always does.  Each pass reads A once, at tensor-core rate instead
 // of CUDA-core rate.
 #pragma once
