@@ -608,7 +608,7 @@ __global__ void __launch_bounds__(kReduceRows* kReduceGroups) reduce_kernel(cons
 // Objective, stopping test and projection weights after a sweep, or one step
 // of the start (projection of the start, Rayleigh-Ritz rotation).  One CTA:
 // sums and stopping test in double, the m x m eigenproblems in double-float.
-__global__ void __launch_bounds__(kFinishThreads) finish_kernel(const FinishArgs a) {
+__global__ void __launch_bounds__(kFinishThreads, 1) finish_kernel(const FinishArgs a) {
   extern __shared__ double fsm[];
   State* st = a.st;
   const IO* io = a.io;

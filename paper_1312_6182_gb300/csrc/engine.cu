@@ -218,15 +218,16 @@ int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fa
   const int unit = std::max(d.align, d.vec);
   bool found = false;
   // the tensor-core sweep where the CUDA-core passes become compute-bound:
-  // bf16 storage read in place (TMA-compatible layout: 16-byte aligned base
-  // and column stride) from 6 components (or gamma values) on; float A as
-  // three bf16 planes and fp8 A as one, copied once per solve, from 9 on (one
-  // CUDA-core pass covers up to 8).  Crossovers measured on GB300 over
-  // p x n in {5000 x 20000, 2000 x 60000, 8000 x 8000}.
+  // bf16 storage from 6 components (or gamma values) on, read in place when
+  // its layout suits TMA (16-byte aligned base and column stride) and copied
+  // once per solve into a padded layout otherwise; float A as three bf16
+  // planes and fp8 A as one, copied once per solve, from 9 on (one CUDA-core
+  // pass covers up to 8).  Crossovers measured on GB300 over p x n in
+  // {5000 x 20000, 2000 x 60000, 8000 x 8000}.
   const bool native_bf16 = dt == GPSPCA_BF16 && fast && ld % 8 == 0;
-  const int tc_min_m = native_bf16 ? 6 : 9;
+  const int tc_min_m = dt == GPSPCA_BF16 ? 6 : 9;
   if (allow_tc && m >= tc_min_m && p >= 1 && n >= 1 &&
-      (native_bf16 || dt == GPSPCA_F32 || dt == GPSPCA_FP8_E4M3)) {
+      (dt == GPSPCA_BF16 || dt == GPSPCA_F32 || dt == GPSPCA_FP8_E4M3)) {
     plan_tc(&pl, m, p, n, nsm);
     pl.tc_na = dt == GPSPCA_F32 ? 3 : 1;
     pl.tc_convert = native_bf16 ? 0 : 1;

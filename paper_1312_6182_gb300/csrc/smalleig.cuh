@@ -66,8 +66,8 @@ __device__ inline EigWs eig_ws(double* base, int m) {
   return w;
 }
 
-// Barrier of the group that runs the Jacobi sweeps: warp 0 alone for
-// mm <= 8 (every rotation round then fits one warp), else the whole CTA.
+// Barrier of the group that runs the generic Jacobi sweeps (mm > 16: the
+// whole CTA; the one-warp form for mm <= 16 is jacobi_small).
 template <bool kWarp>
 __device__ __forceinline__ void group_sync() {
   if (kWarp) {
@@ -119,22 +119,32 @@ __device__ __forceinline__ void rotation(dd app, dd aqq, dd apq, dd* c, dd* s) {
   *s = dd_mul_f(*c, t);
 }
 
-// Cyclic Jacobi for mm = MM <= 8 on warp 0 alone: every round's index
-// arithmetic divides by constants, each lane owns one (pair, index) slot of
-// the row and column updates, and the rotation of each pair, computed by
-// lane k, is broadcast by shuffles.  Same rotations, order and stopping rule
-// as jacobi_dd.  The kernel runs once per launch with a cold instruction
-// cache, so loops stay rolled: code size, not arithmetic, sets its time.
+// Stopping rule of the Jacobi sweeps: the off-diagonal Frobenius norm below
+// 1e-12 of the diagonal's (far below the float data path's accuracy; dd
+// rounding leaves ~1e-14 per entry, which larger matrices add up to), or a
+// sweep that no longer halves it (the rounding floor has been reached).
+__device__ __forceinline__ bool jacobi_done(float off, float dg, float off_prev) {
+  return !(off > 1e-24f * dg) || (off_prev >= 0.0f && off > 0.25f * off_prev && off < 1e-20f * dg);
+}
+
+// Cyclic Jacobi for mm = MM <= 16 on warp 0 alone: every round's index
+// arithmetic divides by constants, each lane owns (pair, index) slots of the
+// row and column updates (up to four), and the rotation of each pair,
+// computed by lane k, is broadcast by shuffles.  Same rotations, order and
+// stopping rule as jacobi_dd.  The kernel runs once per launch with a cold
+// instruction cache, so loops stay rolled: code size, not arithmetic, sets
+// its time.
 template <int MM>
 __device__ void jacobi_small(dd* H, dd* V) {
   constexpr int HALF = MM / 2;
   constexpr int NE = MM * MM;
+  constexpr int NSLOT = HALF * MM;            // (pair, index) slots of a round
+  constexpr int NQ = (NSLOT + 31) / 32;       // slots per lane
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  const int k = lane / MM, l = lane % MM;
-  const bool own = lane < HALF * MM;
   for (int e = lane; e < NE; e += 32) V[e] = dd{(e / MM == e % MM) ? 1.0f : 0.0f, 0.0f};
   __syncwarp();
+  float off_prev = -1.0f;
   for (int sweep = 0; sweep < 30; ++sweep) {
     float off = 0.0f, dg = 0.0f;
     for (int e = lane; e < NE; e += 32) {
@@ -147,7 +157,8 @@ __device__ void jacobi_small(dd* H, dd* V) {
       off += __shfl_xor_sync(full, off, o);
       dg += __shfl_xor_sync(full, dg, o);
     }
-    if (!(off > 1e-26f * dg)) break;
+    if (jacobi_done(off, dg, off_prev)) break;
+    off_prev = off;
 #pragma unroll 1
     for (int round = 0; round < MM - 1; ++round) {  // rolled: one copy of the body to fetch
       dd c{1.0f, 0.0f}, s{0.0f, 0.0f};
@@ -157,25 +168,42 @@ __device__ void jacobi_small(dd* H, dd* V) {
         const int pp = min(a, b), qq = max(a, b);
         rotation(H[pp * MM + pp], H[qq * MM + qq], H[pp * MM + qq], &c, &s);
       }
-      const int src = own ? k : 0;
-      const dd ck{__shfl_sync(full, c.hi, src), __shfl_sync(full, c.lo, src)};
-      const dd sk{__shfl_sync(full, s.hi, src), __shfl_sync(full, s.lo, src)};
-      const int a = (k == 0) ? 0 : ((k - 1 + round) % (MM - 1)) + 1;
-      const int b = ((MM - 2 - k + round) % (MM - 1)) + 1;
-      const int pp = min(a, b), qq = max(a, b);
-      if (own) {  // rows: H <- J^T H
-        const dd hp = H[pp * MM + l], hq = H[qq * MM + l];
-        H[pp * MM + l] = dd_sub(dd_mul(ck, hp), dd_mul(sk, hq));
-        H[qq * MM + l] = dd_add(dd_mul(sk, hp), dd_mul(ck, hq));
+      dd ck[NQ], sk[NQ];
+      int pq[NQ], qk[NQ];
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {  // every lane joins every shuffle
+        const int e = lane + 32 * q;
+        const int k = (e < NSLOT) ? e / MM : 0;
+        ck[q] = dd{__shfl_sync(full, c.hi, k), __shfl_sync(full, c.lo, k)};
+        sk[q] = dd{__shfl_sync(full, s.hi, k), __shfl_sync(full, s.lo, k)};
+        const int a = (k == 0) ? 0 : ((k - 1 + round) % (MM - 1)) + 1;
+        const int b = ((MM - 2 - k + round) % (MM - 1)) + 1;
+        pq[q] = min(a, b);
+        qk[q] = max(a, b);
+      }
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {  // rows: H <- J^T H
+        const int e = lane + 32 * q;
+        if (e < NSLOT) {
+          const int l = e % MM, pp = pq[q], qq = qk[q];
+          const dd hp = H[pp * MM + l], hq = H[qq * MM + l];
+          H[pp * MM + l] = dd_sub(dd_mul(ck[q], hp), dd_mul(sk[q], hq));
+          H[qq * MM + l] = dd_add(dd_mul(sk[q], hp), dd_mul(ck[q], hq));
+        }
       }
       __syncwarp();
-      if (own) {  // columns: H <- H J, V <- V J
-        const dd hp = H[l * MM + pp], hq = H[l * MM + qq];
-        const dd vp = V[l * MM + pp], vq = V[l * MM + qq];
-        H[l * MM + pp] = dd_sub(dd_mul(ck, hp), dd_mul(sk, hq));
-        H[l * MM + qq] = dd_add(dd_mul(sk, hp), dd_mul(ck, hq));
-        V[l * MM + pp] = dd_sub(dd_mul(ck, vp), dd_mul(sk, vq));
-        V[l * MM + qq] = dd_add(dd_mul(sk, vp), dd_mul(ck, vq));
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {  // columns: H <- H J, V <- V J
+        const int e = lane + 32 * q;
+        if (e < NSLOT) {
+          const int l = e % MM, pp = pq[q], qq = qk[q];
+          const dd hp = H[l * MM + pp], hq = H[l * MM + qq];
+          const dd vp = V[l * MM + pp], vq = V[l * MM + qq];
+          H[l * MM + pp] = dd_sub(dd_mul(ck[q], hp), dd_mul(sk[q], hq));
+          H[l * MM + qq] = dd_add(dd_mul(sk[q], hp), dd_mul(ck[q], hq));
+          V[l * MM + pp] = dd_sub(dd_mul(ck[q], vp), dd_mul(sk[q], vq));
+          V[l * MM + qq] = dd_add(dd_mul(sk[q], vp), dd_mul(ck[q], vq));
+        }
       }
       __syncwarp();
     }
@@ -183,9 +211,8 @@ __device__ void jacobi_small(dd* H, dd* V) {
 }
 
 // Cyclic Jacobi on the symmetric mm x mm dd matrix H (mm even); on return
-// diag(H) holds the eigenvalues and V the eigenvectors (columns).  Stops when
-// the off-diagonal Frobenius norm is below ~1e-13 of the diagonal's (a
-// little above dd rounding), or after 30 sweeps.
+// diag(H) holds the eigenvalues and V the eigenvectors (columns).  Stops by
+// jacobi_done, or after 30 sweeps.
 template <bool kWarp>
 __device__ void jacobi_dd(const EigWs& ws, int mm) {
   dd* H = ws.H;
@@ -195,7 +222,7 @@ __device__ void jacobi_dd(const EigWs& ws, int mm) {
   for (int idx = tid; idx < mm * mm; idx += nthr) V[idx] = dd{(idx / mm == idx % mm) ? 1.0f : 0.0f, 0.0f};
   group_sync<kWarp>();
   const int half = mm / 2;
-  const float tol2 = 1e-26f * fmaxf(1.0f, static_cast<float>(mm * mm) / 64.0f);
+  float off_prev = -1.0f;
   for (int sweep = 0; sweep < 30; ++sweep) {
     float off = 0.0f, dg = 0.0f;
     for (int idx = tid; idx < mm * mm; idx += nthr) {
@@ -206,7 +233,8 @@ __device__ void jacobi_dd(const EigWs& ws, int mm) {
     }
     off = group_sum<kWarp>(off, ws.red);
     dg = group_sum<kWarp>(dg, ws.red);
-    if (!(off > tol2 * dg)) break;
+    if (jacobi_done(off, dg, off_prev)) break;
+    off_prev = off;
 #pragma unroll 1
     for (int round = 0; round < mm - 1; ++round) {
       if (tid < half) {
@@ -250,13 +278,17 @@ __device__ void jacobi_dd(const EigWs& ws, int mm) {
 // Runs the Jacobi sweeps on the group that suits mm; all threads of the CTA
 // call it and leave it together.
 __device__ inline void jacobi_dd_cta(const EigWs& ws, int mm) {
-  if (mm <= 8) {
+  if (mm <= 16) {
     if (threadIdx.x < 32) {
       switch (mm) {
         case 2: jacobi_small<2>(ws.H, ws.V); break;
         case 4: jacobi_small<4>(ws.H, ws.V); break;
         case 6: jacobi_small<6>(ws.H, ws.V); break;
-        default: jacobi_small<8>(ws.H, ws.V); break;
+        case 8: jacobi_small<8>(ws.H, ws.V); break;
+        case 10: jacobi_small<10>(ws.H, ws.V); break;
+        case 12: jacobi_small<12>(ws.H, ws.V); break;
+        case 14: jacobi_small<14>(ws.H, ws.V); break;
+        default: jacobi_small<16>(ws.H, ws.V); break;
       }
     }
   } else {

@@ -458,7 +458,8 @@ int tc_encode_maps(TcMaps* maps, const void* planes, int na, int64_t plane, int6
 }
 
 // float A -> three bf16 planes (a = a0 + a1 + a2 exactly); fp8 -> its values
-// in bf16 (exact; the column scale stays separate).  Grid-stride over A.
+// in bf16 (exact; the column scale stays separate); bf16 with a layout TMA
+// cannot read -> a copy with the padded column stride.  Grid-stride over A.
 template <typename TA>
 __global__ void tc_convert_kernel(const IO* io, int64_t p, int64_t n, int64_t ld, int64_t ldc) {
   const TA* A = static_cast<const TA*>(io->A);
@@ -476,7 +477,7 @@ __global__ void tc_convert_kernel(const IO* io, int64_t p, int64_t n, int64_t ld
       planes[plane + i * ldc + r] = b1;
       planes[2 * plane + i * ldc + r] = b2;
     } else {
-      planes[i * ldc + r] = __float2bfloat16_rn(v);
+      planes[i * ldc + r] = __float2bfloat16_rn(v);  // exact for fp8 and bf16 values
     }
   }
 }
@@ -489,6 +490,8 @@ void launch_tc_convert(int dtype, const IO* io, int64_t p, int64_t n, int64_t ld
     tc_convert_kernel<float><<<nsm * 8, 256, 0, s>>>(io, p, n, ld, ldc);
   else if (dtype == GPSPCA_FP8_E4M3)
     tc_convert_kernel<__nv_fp8_e4m3><<<nsm * 8, 256, 0, s>>>(io, p, n, ld, ldc);
+  else if (dtype == GPSPCA_BF16)  // a layout TMA cannot read in place: padded copy
+    tc_convert_kernel<__nv_bfloat16><<<nsm * 8, 256, 0, s>>>(io, p, n, ld, ldc);
 }
 
 template <int NPAD, int NA>

@@ -73,7 +73,8 @@ bool tc_supported(int device);
 // planes: na bf16 matrices (p x n, column stride ld elements, `plane` elements apart)
 int tc_encode_maps(TcMaps* maps, const void* planes, int na, int64_t plane, int64_t p, int64_t n, int64_t ld,
                    const void* x3, int p_pad, const void* g3, int n_pad, int npad);
-// float / fp8 A -> bf16 planes in the workspace (once per solve); ldc = p_pad
+// float / fp8 / unaligned bf16 A -> bf16 planes in the workspace (once per
+// solve); ldc = p_pad
 void launch_tc_convert(int dtype, const IO* io, int64_t p, int64_t n, int64_t ld, int64_t ldc, cudaStream_t s);
 void launch_tc_sweep(const TcArgs& a, int npad, cudaStream_t s);
 
