@@ -818,7 +818,7 @@ void launch_reduce(int tcsize, const ReduceArgs& a, cudaStream_t s) {
 
 void launch_finish(const FinishArgs& a, int smem, cudaStream_t s) {
   static bool once = [] {
-    cudaFuncSetAttribute(finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kFinishMaxSmem);
     return true;
   }();
   (void)once;

@@ -55,6 +55,7 @@ struct StartArgs {
 constexpr int kReduceRows = 32;   // rows per reduction block
 constexpr int kReduceGroups = 8;  // partial groups per reduction block
 constexpr int kFinishThreads = 256;
+constexpr int kFinishMaxSmem = 220 * 1024;  // dynamic shared memory of finish_kernel (m = 64 needs ~195 KB)
 constexpr int kStartThreads = 1024;
 constexpr int kMaxCandidates = 256;
 

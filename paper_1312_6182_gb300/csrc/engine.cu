@@ -290,6 +290,9 @@ int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fa
   pl.full_gram = form >= 2 ? 1 : 0;
   pl.npairs = pl.full_gram ? m * m : m;  // gpart capacity: the Ritz step's cross Gram is m x m
   pl.finish_smem = static_cast<int>(sizeof(double)) * finish_smem_doubles(m, pl.npairs);
+  if (pl.finish_smem > kFinishMaxSmem)
+    return fail(GPSPCA_EINVAL, "m = %d needs %d bytes of shared memory in the projection step (at most %d)", m,
+                pl.finish_smem, kFinishMaxSmem);
   pl.ws_cnorm = sizeof(double) * n;
   pl.ws_P = static_cast<size_t>(d.tcsize) * m * p;
   pl.ws_ypart = static_cast<size_t>(d.tcsize) * ncl * m * p;

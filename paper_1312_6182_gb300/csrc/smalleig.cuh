@@ -31,7 +31,7 @@ struct EigWs {
   dd* H;      // mm x mm, the matrix being diagonalised
   dd* V;      // mm x mm, accumulated rotations
   dd* E;      // m x m, products / eigenvectors
-  dd* T;      // m x m, the scaled input matrix
+  dd* T;      // m x m, the scaled input matrix (in V's space: dead before the sweeps start V)
   dd* Vs;     // m x m, shared copy of the warm-start eigenvectors
   dd* rc;     // 32 rotation cosines
   dd* rs;     // 32 rotation sines
@@ -44,7 +44,7 @@ struct EigWs {
 
 __host__ __device__ inline int eig_ws_slots(int m) {
   const int mm = m + (m & 1);
-  return 2 * mm * mm + 3 * m * m + 32 + 32 + 2 * kMaxM + 32 + 16;
+  return 2 * mm * mm + 2 * m * m + 32 + 32 + 2 * kMaxM + 32 + 16;
 }
 
 __device__ inline EigWs eig_ws(double* base, int m) {
@@ -54,8 +54,8 @@ __device__ inline EigWs eig_ws(double* base, int m) {
   w.H = d;
   w.V = w.H + mm * mm;
   w.E = w.V + mm * mm;
-  w.T = w.E + m * m;
-  w.Vs = w.T + m * m;
+  w.T = w.V;
+  w.Vs = w.E + m * m;
   w.rc = w.Vs + m * m;
   w.rs = w.rc + 32;
   w.lam = w.rs + 32;

@@ -188,6 +188,40 @@ def test_tensor_core_sweep_fp8_storage(ctx, form):
                    iters_slack=0)
 
 
+@pytest.mark.parametrize("dtype,form,p,n,m", [
+    ("bf16", "BL1", 40, 100, 6),     # p below one 64-row chunk, n below one 128-column tile
+    ("bf16", "SL0", 37, 1000, 8),    # unaligned bf16 stride: padded copy for TMA
+    ("f32", "SL1", 70, 300, 9),      # float: three bf16 planes
+    ("f32", "BL0", 256, 2000, 64),   # N = 192, the largest tensor-memory layout
+])
+def test_tensor_core_sweep_edge_shapes(ctx, dtype, form, p, n, m):
+    """Shapes at the edges of the tensor-core sweep's tiles, layouts and
+    widths, against the oracle on the stored values (3 sweeps from the start)."""
+    k = min(m, 4)
+    At = synth.planted_spike(p, n, k, [30.0 / (j + 1) for j in range(k)], support_frac=0.05, seed=31 + m,
+                             dtype=np.float32)
+    if dtype == "bf16":
+        tA, deq = _bf16(At)
+        tA = tA.cuda()
+    else:
+        tA, deq = torch.from_numpy(At).cuda(), At
+    A = deq.astype(np.float64).T
+    block = form.startswith("B")
+    rho = [0.01] * m if block else list(synth.log_spaced_rho(m, 0.005, 0.2))
+    gam = _gammas(A, form, rho)
+    mu = [1.0] * m if block else None
+    ref = oracle.gpower(A, form, gam, mu=mu, tol=0.0, maxit=3)
+    res = ctx.solve(tA, form, list(gam), mu=mu, tol=0.0, maxit=3, allow_degenerate=True)
+    if block and m > 4:
+        # more components than spikes: compare only the well-determined objective
+        assert abs(res.objective.sum().item() - ref.total) / ref.total < 1e-5
+        X = res.X.double().cpu().numpy().T
+        assert np.abs(X.T @ X - np.eye(m)).max() < 1e-5
+    else:
+        assert_matches(form, gpu_arrays(res), ref, oracle.column_norms(A), tol_z=5e-5, tol_f=1e-6, tol_x=5e-5,
+                       iters_slack=0)
+
+
 def test_tensor_core_and_cuda_core_sweeps_agree(ctx):
     """The same solve with and without the tensor cores: float-rounding
     differences only, on the well-determined quantities (the objective, and
