@@ -155,12 +155,20 @@ def run_gpu(args):
         )
 
     def step(host=False):
-        sweeps, launches = 0, 0
+        # the six independent solves of a step as one batch: they run
+        # concurrently on their own streams, ordered on the context's stream
+        items = []
         for form, mu in CASES:
             m = 1 if mu is None else len(mu)
             dres, hres = outs[(form, tuple(mu) if mu else None)]
-            res = ctx.solve(hA if host else dA, form, [RHO] * m, mu=mu, tol=TOL, maxit=MAXIT,
-                            gamma_relative=True, out=hres if host else dres, eager=args.eager)
+            items.append(dict(At=hA if host else dA, form=form, gamma=[RHO] * m, mu=mu, tol=TOL, maxit=MAXIT,
+                              gamma_relative=True, out=hres if host else dres, eager=args.eager))
+        if args.eager:  # profiling: one by one
+            results = [ctx.solve(**it) for it in items]
+        else:
+            results = ctx.solve_batch(items)
+        sweeps, launches = 0, 0
+        for (form, mu), res in zip(CASES, results):
             it = int(res.iters.max().item())
             sweeps += it
             # reset, norms, selection, gather, reduction + finish of the start

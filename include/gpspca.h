@@ -156,6 +156,32 @@ int gpspca_create(gpspca_ctx** ctx, int device, size_t hbm_budget_bytes, void* c
 int gpspca_solve(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form, const double* gamma, int32_t m,
                  const double* mu, double tol, int32_t maxit, const void* x0, uint32_t flags, gpspca_out* out);
 
+/* One solve of a batch (gpspca_solve_batch): the arguments of gpspca_solve. */
+typedef struct {
+  gpspca_matrix A;
+  gpspca_form form;
+  const double* gamma;  /* m values */
+  int32_t m;
+  const double* mu;     /* NULL or m values */
+  double tol;
+  int32_t maxit;
+  const void* x0;       /* NULL or a starting iterate, as for gpspca_solve */
+  uint32_t flags;
+  gpspca_out out;
+} gpspca_request;
+
+/* count independent solves (same arguments, ownership and results as
+ * gpspca_solve, one request each) run concurrently: each on its own stream
+ * and workspace (up to 8 at a time, in request order beyond that), so that
+ * the latency-bound steps of one solve (reductions, the projection's small
+ * eigenproblem) overlap the sweeps of the others.  Stream-ordered with the
+ * context's stream: the batch starts after the work already enqueued on it,
+ * and work enqueued on it afterwards starts after the whole batch.  Returns
+ * when every solve has finished; rcs[i] (count entries, caller-owned)
+ * receives solve i's result code.  The return value is GPSPCA_OK when every
+ * solve returned GPSPCA_OK or GPSPCA_EDEGENERATE, else the first other code. */
+int gpspca_solve_batch(gpspca_ctx* ctx, int32_t count, const gpspca_request* reqs, int32_t* rcs);
+
 /* Asynchronous form of gpspca_solve for many concurrent requests.  The
  * request is queued; a scheduler thread admits it when its workspace fits the
  * budget next to the solves already running, and advances every admitted

@@ -38,7 +38,8 @@ ERROR_NAMES = {
 }
 
 EXPORTED = ("gpspca_create", "gpspca_solve", "gpspca_submit", "gpspca_poll", "gpspca_destroy",
-            "gpspca_last_error", "gpspca_time_sweep", "gpspca_sweep_static", "gpspca_synth_spikes")
+            "gpspca_last_error", "gpspca_time_sweep", "gpspca_sweep_static", "gpspca_synth_spikes",
+            "gpspca_solve_batch")
 
 
 class Matrix(ctypes.Structure):
@@ -63,6 +64,21 @@ class Out(ctypes.Structure):
         ("iters", ctypes.c_void_p),
         ("status", ctypes.c_void_p),
         ("gamma_abs", ctypes.c_void_p),
+    ]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [
+        ("A", Matrix),
+        ("form", ctypes.c_int),
+        ("gamma", ctypes.POINTER(ctypes.c_double)),
+        ("m", ctypes.c_int32),
+        ("mu", ctypes.POINTER(ctypes.c_double)),
+        ("tol", ctypes.c_double),
+        ("maxit", ctypes.c_int32),
+        ("x0", ctypes.c_void_p),
+        ("flags", ctypes.c_uint32),
+        ("out", Out),
     ]
 
 
@@ -102,6 +118,8 @@ def load(path: str = LIB_PATH):
     lib.gpspca_synth_spikes.argtypes = [P, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
                                         D, ctypes.c_double, ctypes.c_uint64, P]
     lib.gpspca_synth_spikes.restype = ctypes.c_int
+    lib.gpspca_solve_batch.argtypes = [P, ctypes.c_int32, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_int32)]
+    lib.gpspca_solve_batch.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -268,6 +286,47 @@ class Context:
         _check(rc, allow)
         out.rc = rc
         return out
+
+    def solve_batch(self, items, allow_degenerate: bool = True):
+        """Independent solves run concurrently (gpspca_solve_batch), stream-ordered
+        with the context's stream.  items: dicts with the keyword arguments of
+        solve (At, form, gamma; optional mu, tol, maxit, x0, gamma_relative, p,
+        col_scale, out, eager, tensor_cores).  Returns the list of Results."""
+        import torch
+
+        n = len(items)
+        reqs = (Request * n)()
+        keep, outs = [], []
+        for k, it in enumerate(items):
+            At = it["At"]
+            gamma = [float(g) for g in (it["gamma"] if hasattr(it["gamma"], "__len__") else [it["gamma"]])]
+            m = len(gamma)
+            M = matrix(At, it.get("p"), it.get("col_scale"))
+            tc = torch.float64 if At.dtype == torch.float64 else torch.float32
+            out = it.get("out") or alloc_result(m, int(M.p), int(M.n), At.device, tc)
+            g_arr, mu_arr = _darr(gamma, m), _darr(it.get("mu"), m)
+            keep += [g_arr, mu_arr]
+            x0 = it.get("x0")
+            reqs[k].A = M
+            reqs[k].form = FORMS[it["form"]]
+            reqs[k].gamma = ctypes.cast(g_arr, ctypes.POINTER(ctypes.c_double))
+            reqs[k].m = m
+            reqs[k].mu = ctypes.cast(mu_arr, ctypes.POINTER(ctypes.c_double)) if mu_arr is not None else None
+            reqs[k].tol = float(it.get("tol", 1e-6))
+            reqs[k].maxit = int(it.get("maxit", 1000))
+            reqs[k].x0 = x0.data_ptr() if x0 is not None else None
+            reqs[k].flags = ((GAMMA_RELATIVE if it.get("gamma_relative") else 0) | (EAGER if it.get("eager") else 0)
+                             | (0 if it.get("tensor_cores", True) else NO_TENSOR_CORES))
+            reqs[k].out = out_struct(out)
+            outs.append(out)
+            self._sync_torch(At, x0, out.X)
+        rcs = (ctypes.c_int32 * n)()
+        self.lib.gpspca_solve_batch(self.ptr, n, reqs, rcs)
+        allow = (OK, EDEGENERATE) if allow_degenerate else (OK,)
+        for k in range(n):
+            _check(rcs[k], allow)
+            outs[k].rc = rcs[k]
+        return outs
 
     def submit(self, At, form: str, gamma, mu=None, tol: float = 1e-6, maxit: int = 1000,
                gamma_relative: bool = False, p: Optional[int] = None, col_scale=None,

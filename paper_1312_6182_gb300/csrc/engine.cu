@@ -888,6 +888,9 @@ struct gpspca_ctx {
   bool stop = false;
   std::thread sched;
   bool sched_started = false;
+  // batches (gpspca_solve_batch), under solve_mu
+  std::vector<std::unique_ptr<Slot>> batch_slots;
+  cudaEvent_t batch_start = nullptr;
 };
 
 static constexpr int kServeSlots = 8;
@@ -991,6 +994,55 @@ int gpspca_create(gpspca_ctx** out, int device, size_t hbm_budget_bytes, void* c
     return rc;
   }
   *out = ctx;
+  return GPSPCA_OK;
+}
+
+static constexpr int kBatchSlots = 8;
+
+int gpspca_solve_batch(gpspca_ctx* ctx, int32_t count, const gpspca_request* reqs, int32_t* rcs) {
+  if (!ctx) return fail(GPSPCA_EINVAL, "ctx is NULL");
+  if (count < 0 || (count > 0 && (!reqs || !rcs))) return fail(GPSPCA_EINVAL, "bad batch arguments");
+  std::vector<Request> R(static_cast<size_t>(count));
+  for (int i = 0; i < count; ++i) {
+    gpspca_out o = reqs[i].out;
+    const int rc = request_from(&R[i], &reqs[i].A, reqs[i].form, reqs[i].gamma, reqs[i].m, reqs[i].mu, reqs[i].tol,
+                                reqs[i].maxit, reqs[i].x0, reqs[i].flags, &o);
+    if (rc != GPSPCA_OK) return fail(rc, "batch request %d: %s", i, t_last_error.c_str());
+  }
+  std::lock_guard<std::mutex> lk(ctx->solve_mu);
+  GP_CUDA(cudaSetDevice(ctx->device));
+  if (!ctx->batch_start) GP_CUDA(cudaEventCreateWithFlags(&ctx->batch_start, cudaEventDisableTiming));
+  const int nb = std::min(count, kBatchSlots);
+  while (static_cast<int>(ctx->batch_slots.size()) < nb) {
+    auto s = std::make_unique<Slot>();
+    const int rc = slot_init(s.get(), ctx->device, nullptr, &ctx->budget);
+    if (rc != GPSPCA_OK) {
+      slot_free(s.get());
+      return rc;
+    }
+    ctx->batch_slots.push_back(std::move(s));
+  }
+  cudaStream_t cs = ctx->sync_slot.stream;
+  GP_CUDA(cudaEventRecord(ctx->batch_start, cs));
+  std::vector<char> running(static_cast<size_t>(count), 0);
+  auto collect = [&](int i) {
+    rcs[i] = solve_result(ctx->batch_slots[i % kBatchSlots].get());
+    running[i] = 0;
+  };
+  for (int i = 0; i < count; ++i) {
+    Slot* s = ctx->batch_slots[i % kBatchSlots].get();
+    if (i >= kBatchSlots && running[i - kBatchSlots]) collect(i - kBatchSlots);  // the slot's previous solve
+    GP_CUDA(cudaStreamWaitEvent(s->stream, ctx->batch_start, 0));
+    bool empty = false;
+    const int rc = launch_solve(s, R[i], ctx->nsm, &empty);
+    rcs[i] = rc;
+    running[i] = (rc == GPSPCA_OK && !empty) ? 1 : 0;
+  }
+  for (int k = 0; k < nb; ++k) GP_CUDA(cudaStreamWaitEvent(cs, ctx->batch_slots[k]->done, 0));
+  for (int i = 0; i < count; ++i)
+    if (running[i]) collect(i);
+  for (int i = 0; i < count; ++i)
+    if (rcs[i] != GPSPCA_OK && rcs[i] != GPSPCA_EDEGENERATE) return fail(rcs[i], "batch request %d failed", i);
   return GPSPCA_OK;
 }
 
@@ -1111,6 +1163,8 @@ int gpspca_destroy(gpspca_ctx* ctx) {
   }
   cudaSetDevice(ctx->device);
   for (auto& s : ctx->serve_slots) slot_free(s.get());
+  for (auto& s : ctx->batch_slots) slot_free(s.get());
+  if (ctx->batch_start) cudaEventDestroy(ctx->batch_start);
   slot_free(&ctx->sync_slot);
   delete ctx;
   return GPSPCA_OK;

@@ -450,6 +450,33 @@ def test_time_sweep(ctx):
 
 # ---------------------------------------------------------------- serving
 
+def test_batch_equals_solo_solves(ctx):
+    """gpspca_solve_batch: independent solves of different shapes, forms and
+    storage (more than its 8 concurrent slots) give the bit-identical results
+    of solo solves, and the batch is ordered on the context's stream."""
+    rng = np.random.default_rng(5)
+    items = []
+    for i in range(11):
+        p = int(rng.integers(200, 1500))
+        n = int(rng.integers(800, 5000))
+        form = oracle.FORMS[i % 4]
+        m = 1 if form.startswith("S") else int(rng.integers(2, 7))
+        At = synth.planted_spike(p, n, m, [30.0 / (j + 1) for j in range(m)], support_frac=0.05, seed=200 + i,
+                                 dtype=np.float32)
+        dA = torch.from_numpy(At).cuda()
+        if i % 3 == 2:
+            dA = dA.to(torch.bfloat16)
+        items.append(dict(At=dA, form=form, gamma=[float(rng.uniform(0.02, 0.2))] * m,
+                          mu=None if m == 1 else [1.0] * m, gamma_relative=True))
+    solo = [ctx.solve(**{k: v for k, v in it.items()}) for it in items]
+    got = ctx.solve_batch(items)
+    for ref, out in zip(solo, got):
+        assert torch.equal(out.Z, ref.Z) and torch.equal(out.X, ref.X)
+        assert torch.equal(out.objective, ref.objective) and torch.equal(out.iters, ref.iters)
+    with pytest.raises(binding.GpspcaError):
+        ctx.solve_batch([dict(At=items[0]["At"], form="SL1", gamma=[-1.0])])
+
+
 def test_submitted_requests_equal_solo_solves(ctx):
     """Requests of different shapes and formulations submitted together (and so
     overlapping on the device) give the bit-identical results of solo solves."""
