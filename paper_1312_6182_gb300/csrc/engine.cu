@@ -230,7 +230,11 @@ int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fa
       (dt == GPSPCA_BF16 || dt == GPSPCA_F32 || dt == GPSPCA_FP8_E4M3)) {
     plan_tc(&pl, m, p, n, nsm);
     pl.tc_na = dt == GPSPCA_F32 ? 3 : 1;
-    pl.tc_convert = native_bf16 ? 0 : 1;
+    // float A that TMA can read (16-byte aligned base and column stride) is
+    // split into its planes in shared memory; other float / fp8 / bf16
+    // layouts are copied once per solve
+    pl.tc_fused = (dt == GPSPCA_F32 && fast && ld % 4 == 0) ? 1 : 0;
+    pl.tc_convert = (native_bf16 || pl.tc_fused) ? 0 : 1;
     pl.C = 1;
     pl.ps = static_cast<int>(p);
     found = true;
@@ -488,9 +492,9 @@ static cudaError_t launch_prologue(const Plan& pl, Slot* s, cudaStream_t cs, cud
 
 static cudaError_t launch_sweeps(const Plan& pl, Slot* s, cudaStream_t cs, int sketch) {
   if (pl.tc) {
-    TcArgs a{s->io_dev, s->st_dev, pl.p,     pl.n,      pl.m,     pl.mpad,     pl.form,
-             sketch,    pl.tc_na,  pl.dtype == GPSPCA_FP8_E4M3 ? 1 : 0, pl.p_pad, pl.n_pad, pl.ntile1, pl.kchunks1,
-             pl.nchunks2, pl.kps2, pl.nsplit2, pl.nrow2};
+    TcArgs a{s->io_dev,  s->st_dev, pl.p,     pl.n,       pl.m,        pl.mpad,     pl.form,
+             sketch,     pl.tc_na,  pl.tc_fused, pl.dtype == GPSPCA_FP8_E4M3 ? 1 : 0, pl.p_pad, pl.n_pad,
+             pl.ntile1,  pl.kchunks1, pl.nchunks2, pl.kps2, pl.nsplit2, pl.nrow2};
     launch_tc_sweep(a, pl.npad, cs);
     return cudaGetLastError();
   }
@@ -719,11 +723,17 @@ static int prepare_solve(Slot* s, const Request& r, int nsm, bool scratch_out, P
     if (pl.tc_convert && (rc = ensure(s, &s->b_planes, pl.ws_planes))) return rc;
     // the host copy of the maps is reused only after this solve's copy has run
     GP_CUDA(cudaStreamSynchronize(s->stream));
-    const void* planes = pl.tc_convert ? s->b_planes.p : A_dev;
-    const int64_t pld = pl.tc_convert ? pl.p_pad : ld;
-    if ((rc = tc_encode_maps(s->maps_host, planes, pl.tc_na, pld * n, p, n, pld, s->b_x3.p, pl.p_pad, s->b_g3.p,
-                             pl.n_pad, pl.npad)))
-      return rc;
+    if (pl.tc_fused) {
+      if ((rc = tc_encode_maps_f32(s->maps_host, A_dev, p, n, ld, s->b_x3.p, pl.p_pad, s->b_g3.p, pl.n_pad,
+                                   pl.npad)))
+        return rc;
+    } else {
+      const void* planes = pl.tc_convert ? s->b_planes.p : A_dev;
+      const int64_t pld = pl.tc_convert ? pl.p_pad : ld;
+      if ((rc = tc_encode_maps(s->maps_host, planes, pl.tc_na, pld * n, p, n, pld, s->b_x3.p, pl.p_pad, s->b_g3.p,
+                               pl.n_pad, pl.npad)))
+        return rc;
+    }
     GP_CUDA(cudaMemcpyAsync(s->b_maps.p, s->maps_host, sizeof(TcMaps), cudaMemcpyHostToDevice, s->stream));
   }
   IO& io = *s->io_host;

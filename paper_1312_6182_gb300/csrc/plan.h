@@ -30,6 +30,7 @@ struct Plan {
       nsplit2 = 0, nrow2 = 0;
   int tc_na = 1;       // bf16 planes of A the contractions read (3 for float A)
   int tc_convert = 0;  // the planes are a workspace copy made once per solve (float / fp8 A)
+  int tc_fused = 0;    // float A read in place, split into planes in shared memory
   size_t ws_cnorm = 0, ws_P = 0, ws_ypart = 0, ws_T = 0, ws_fpart = 0, ws_gpart = 0, ws_x3 = 0, ws_g3 = 0,
          ws_planes = 0;
 
@@ -39,7 +40,7 @@ struct Plan {
              ps, ncl, cols_per_cl);
     std::string s(b);
     if (tc) {
-      snprintf(b, sizeof(b), "|tc%d,%d,%d,%d,%d", npad, kps2, nsplit2, tc_na, tc_convert);
+      snprintf(b, sizeof(b), "|tc%d,%d,%d,%d,%d,%d", npad, kps2, nsplit2, tc_na, tc_convert, tc_fused);
       s += b;
     }
     for (const Pass& q : passes) {

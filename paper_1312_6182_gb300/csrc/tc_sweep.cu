@@ -401,6 +401,440 @@ __global__ void __launch_bounds__(kTcThreads) tc_y_kernel(const TcArgs a) {
   tc_teardown<NPAD, NA>(S, tmem, timed_out, st);
 }
 
+// ---------------------------------------------------------------- fused float passes
+//
+// Float A without a bf16 copy: TMA brings float tiles (128-byte swizzle, 32
+// floats per row) into ring 1; eight converter warps split each float into
+// its three bf16 parts (exact) and write them as the three planes of ring 2,
+// in the layout TMA gives bf16 tiles (row = one column of A, 64 rows of A per
+// 128 bytes, 16-byte chunks swizzled by row); after a proxy fence the MMA
+// reads them like the planes of the copied path.  A is read once per pass at
+// 4 bytes per element.
+//
+// Ring 1 stage: float A only (32 KB: two boxes of 32 x 128 for the T pass,
+// four of 32 x 64 for the Y pass), released by the converters as soon as
+// they have read it, so the float copies run ahead of the MMAs.
+// Ring 2 stage: the three bf16 planes (48 KB) + the X3 / G3 tile (NPAD rows x
+// 128 B), released by the MMAs' commit.
+
+constexpr int kTcFusedThreads = 448;  // warps 0-3 epilogue, 4 TMA, 5 MMA, 6-13 converters
+constexpr int kTcConverters = 256;
+constexpr uint32_t kTcF = 32 * 1024;  // float A bytes per stage
+
+__host__ __device__ constexpr int tc_fused_s1(int npad) { return npad <= 96 ? 3 : 2; }
+
+__host__ __device__ constexpr int tc_fused_smem(int npad) {
+  return tc_fused_s1(npad) * static_cast<int>(kTcF) + 2 * (3 * static_cast<int>(kTcA) + npad * 128) + 1024 + 512;
+}
+
+template <int NPAD>
+struct TcFusedCfg {
+  static constexpr int MPAD = NPAD / 3;
+  static constexpr uint32_t kB = NPAD * 128;
+  static constexpr uint32_t kStage1 = kTcF;
+  static constexpr uint32_t kStage2 = 3 * kTcA + kB;
+  static constexpr int S1 = tc_fused_s1(NPAD);
+  static constexpr int S2 = 2;
+  static constexpr uint32_t kCols = TcCfg<NPAD, 3>::kCols;
+  static_assert(kStage1 % 1024 == 0 && kStage2 % 1024 == 0, "1024-byte aligned stages");
+  static_assert(tc_fused_smem(NPAD) <= 227 * 1024, "rings fit the shared memory");
+};
+
+struct TcFusedSmem {
+  uint32_t base1, base2;  // shared addresses of ring 1 and ring 2
+  unsigned char* ptr1;    // generic pointers of the same
+  unsigned char* ptr2;
+  uint64_t *full1, *empty1, *full2, *empty2;
+  TcSmem acc;  // accf / acce / tensor-memory slot / abort flag (the drain uses these)
+};
+
+template <int NPAD>
+__device__ __forceinline__ TcFusedSmem tc_fused_smem(unsigned char* raw) {
+  using Cfg = TcFusedCfg<NPAD>;
+  TcFusedSmem s;
+  const uint32_t r = smem_u32(raw);
+  s.base1 = (r + 1023u) & ~1023u;
+  s.ptr1 = raw + (s.base1 - r);
+  s.base2 = s.base1 + Cfg::S1 * Cfg::kStage1;
+  s.ptr2 = s.ptr1 + Cfg::S1 * Cfg::kStage1;
+  uint64_t* b = reinterpret_cast<uint64_t*>(s.ptr2 + Cfg::S2 * Cfg::kStage2);
+  s.full1 = b;
+  s.empty1 = s.full1 + Cfg::S1;
+  s.full2 = s.empty1 + Cfg::S1;
+  s.empty2 = s.full2 + Cfg::S2;
+  s.acc.accf = s.empty2 + Cfg::S2;
+  s.acc.acce = s.acc.accf + 2;
+  s.acc.tslot = reinterpret_cast<uint32_t*>(s.acc.acce + 2);
+  s.acc.abort_flag = reinterpret_cast<int*>(s.acc.tslot + 1);
+  s.acc.full = s.acc.empty = nullptr;
+  s.acc.base = 0;
+  s.acc.ptr = nullptr;
+  return s;
+}
+
+template <int NPAD>
+__device__ __forceinline__ uint32_t tc_fused_setup(const TcFusedSmem& S) {
+  using Cfg = TcFusedCfg<NPAD>;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int k = 0; k < Cfg::S1; ++k) {
+      mbar_init(smem_u32(&S.full1[k]), 1);                   // the producer's expect_tx
+      mbar_init(smem_u32(&S.empty1[k]), kTcConverters / 32);  // one arrival per converter warp
+    }
+    for (int k = 0; k < Cfg::S2; ++k) {
+      mbar_init(smem_u32(&S.full2[k]), kTcConverters + 1);  // converters + the X3 / G3 copy
+      mbar_init(smem_u32(&S.empty2[k]), 1);
+    }
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(smem_u32(&S.acc.accf[k]), 1);
+      mbar_init(smem_u32(&S.acc.acce[k]), 128);
+    }
+    *S.acc.abort_flag = 0;
+    fence_mbar_init();
+  }
+  if ((tid >> 5) == 0) {
+    tmem_alloc(smem_u32(S.acc.tslot), Cfg::kCols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  return *S.acc.tslot;
+}
+
+// Exact three-way split by truncation: a0 = a with its low 16 bits cleared,
+// a1 the same of a - a0 (exact: at most 16 significant bits), a2 = what is
+// left (at most 8 significant bits, exact in bf16); a = a0 + a1 + a2.  Each
+// part's bf16 is the high half of its float.
+__device__ __forceinline__ void split3_trunc(float x, uint32_t& h0, uint32_t& h1, uint32_t& h2) {
+  const uint32_t b0 = __float_as_uint(x) & 0xFFFF0000u;
+  const float r1 = x - __uint_as_float(b0);
+  const uint32_t b1 = __float_as_uint(r1) & 0xFFFF0000u;
+  const float r2 = r1 - __uint_as_float(b1);
+  h0 = b0;
+  h1 = b1;
+  h2 = __float_as_uint(r2);
+}
+
+// One converter thread: rows [8 g0, 8 g0 + 8 ng) of the 64 rows of A held in
+// one 128-byte row of a bf16 plane (row `prow` of the plane area), from the
+// two float rows (32 rows of A each) at f0 / f1 in ring 1; all layouts
+// swizzle the 16-byte chunks of a row by (row % 8), the float rows by their
+// own index.
+__device__ __forceinline__ void tc_convert_row(const unsigned char* f0, int frow0, const unsigned char* f1,
+                                               int frow1, unsigned char* plane0, int prow, int g0, int ng) {
+#pragma unroll 4
+  for (int g = g0; g < g0 + ng; ++g) {  // 8 rows of A -> one 16-byte chunk per plane
+    const unsigned char* src = g < 4 ? f0 : f1;
+    const int fr = g < 4 ? frow0 : frow1;
+    const int c0 = (g & 3) * 2;
+    const uint4 v0 = *reinterpret_cast<const uint4*>(src + fr * 128 + ((c0 ^ (fr & 7)) * 16));
+    const uint4 v1 = *reinterpret_cast<const uint4*>(src + fr * 128 + (((c0 + 1) ^ (fr & 7)) * 16));
+    const uint32_t x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+    uint32_t w[3][4];
+#pragma unroll
+    for (int e = 0; e < 8; e += 2) {
+      uint32_t a0, a1, a2, b0, b1, b2;
+      split3_trunc(__uint_as_float(x[e]), a0, a1, a2);
+      split3_trunc(__uint_as_float(x[e + 1]), b0, b1, b2);
+      // high halves of (even, odd) -> one bf16x2 word, even element in the low half
+      w[0][e / 2] = __byte_perm(a0, b0, 0x7632);
+      w[1][e / 2] = __byte_perm(a1, b1, 0x7632);
+      w[2][e / 2] = __byte_perm(a2, b2, 0x7632);
+    }
+    const int off = prow * 128 + ((g ^ (prow & 7)) * 16);
+#pragma unroll
+    for (int pl = 0; pl < 3; ++pl)
+      *reinterpret_cast<uint4*>(plane0 + pl * kTcA + off) = make_uint4(w[pl][0], w[pl][1], w[pl][2], w[pl][3]);
+  }
+}
+
+// Converter warps: chunk `it` from ring 1 into ring 2.  kY: Y-pass layout
+// (two 64-row MN atoms of 64 columns) instead of the T pass's 128 columns.
+template <int NPAD, bool kY>
+__device__ __forceinline__ bool tc_convert_chunk(const TcFusedSmem& S, int it) {
+  using Cfg = TcFusedCfg<NPAD>;
+  const int s1 = it % Cfg::S1, s2 = it % Cfg::S2;
+  const uint32_t u1 = static_cast<uint32_t>(it / Cfg::S1), u2 = static_cast<uint32_t>(it / Cfg::S2);
+  if (!mbar_wait_bounded(smem_u32(&S.full1[s1]), u1 & 1)) return false;
+  if (u2 > 0 && !mbar_wait_bounded(smem_u32(&S.empty2[s2]), (u2 - 1) & 1)) return false;
+  const unsigned char* f = S.ptr1 + s1 * Cfg::kStage1;
+  unsigned char* b = S.ptr2 + s2 * Cfg::kStage2;
+  const int c = static_cast<int>(threadIdx.x) - 192;  // 0..255: (half of the 64 rows, plane row)
+  const int h = c >> 7, q = c & 127;
+  if (!kY) {  // row q = column q of the tile; float boxes: rows 0-31 | 32-63 of A
+    tc_convert_row(f, q, f + 16384, q, b, q, 4 * h, 4);
+  } else {    // atom a = rows 64a..64a+63 of A, row i = column i; float boxes of 32 rows x 64 columns
+    const int a = q >> 6, i = q & 63;
+    tc_convert_row(f + (2 * a) * 8192, i, f + (2 * a + 1) * 8192, i, b + a * 8192, i, 4 * h, 4);
+  }
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) mbar_arrive(smem_u32(&S.empty1[s1]));  // the float stage is read
+  fence_async_smem();
+  mbar_arrive(smem_u32(&S.full2[s2]));
+  return true;
+}
+
+template <int NPAD, bool kY>
+__device__ __forceinline__ bool tc_fused_mma(const TcFusedSmem& S, uint32_t tmem, int it, uint32_t idesc) {
+  using Cfg = TcFusedCfg<NPAD>;
+  const int s2 = it % Cfg::S2, b = it & 1;
+  const uint32_t u2 = static_cast<uint32_t>(it / Cfg::S2);
+  const uint32_t ub = static_cast<uint32_t>(it >> 1);
+  if (ub > 0 && !mbar_wait_bounded(smem_u32(&S.acc.acce[b]), (ub - 1) & 1)) return false;
+  if (!mbar_wait_bounded(smem_u32(&S.full2[s2]), u2 & 1)) return false;
+  tc_fence_after();
+  const uint32_t sa = S.base2 + s2 * Cfg::kStage2;
+  const uint32_t sb = sa + 3 * kTcA;
+  const uint32_t d = tmem + static_cast<uint32_t>(b * NPAD);
+#pragma unroll
+  for (int pl = 2; pl >= 0; --pl) {  // smallest plane first
+#pragma unroll
+    for (int kk = 0; kk < kTcBK / 16; ++kk) {
+      const uint64_t ad = kY ? sdesc_sw128(sa + pl * kTcA + kk * 2048, kTcA / 2, 1024)
+                             : sdesc_sw128(sa + pl * kTcA + kk * 32, 16, 1024);
+      const uint64_t bd = sdesc_sw128(sb + kk * 32, 16, 1024);
+      umma_f16(d, ad, bd, idesc, (pl < 2 || kk > 0) ? 1u : 0u);
+    }
+  }
+  umma_commit(smem_u32(&S.empty2[s2]));
+  umma_commit(smem_u32(&S.acc.accf[b]));
+  return true;
+}
+
+// TMA producer of both rings: the float tile of chunk `it` once the
+// converters have read the stage's previous tile, the X3 / G3 tile once the
+// MMAs of the ring-2 stage's previous chunk have completed.  The two streams
+// are polled without blocking, so neither waits behind the other.
+// coord(it, &c, &tr): the chunk's 64-deep index c and its tile (T pass) or
+// 128-row block (Y pass).  false on a timeout or an abort.
+template <int NPAD, typename Coord>
+__device__ __forceinline__ bool tc_fused_producer(const TcFusedSmem& S, int total, Coord coord, const TcMaps* maps,
+                                                  bool y_pass) {
+  using Cfg = TcFusedCfg<NPAD>;
+  int itf = 0, itb = 0;
+  uint32_t idle = 0;
+  while (itf < total || itb < total) {
+    if (tc_aborted(S.acc)) return false;
+    bool progressed = false;
+    if (itf < total) {
+      const int s1 = itf % Cfg::S1;
+      const uint32_t u1 = static_cast<uint32_t>(itf / Cfg::S1);
+      if (u1 == 0 || mbar_test(smem_u32(&S.empty1[s1]), (u1 - 1) & 1)) {
+        int c, tr;
+        coord(itf, &c, &tr);
+        const uint32_t sa = S.base1 + s1 * Cfg::kStage1;
+        const uint32_t bar = smem_u32(&S.full1[s1]);
+        mbar_arrive_expect_tx(bar, kTcF);
+        if (!y_pass) {
+          tma_load_2d(sa, &maps->a1f, c * kTcBK, tr * kTcTile1, bar);
+          tma_load_2d(sa + 16384, &maps->a1f, c * kTcBK + 32, tr * kTcTile1, bar);
+        } else {
+          for (int q = 0; q < 4; ++q) tma_load_2d(sa + q * 8192, &maps->a2f, tr * kTcRows2 + 32 * q, c * kTcBK, bar);
+        }
+        ++itf;
+        progressed = true;
+      }
+    }
+    if (itb < total) {
+      const int s2 = itb % Cfg::S2;
+      const uint32_t u2 = static_cast<uint32_t>(itb / Cfg::S2);
+      if (u2 == 0 || mbar_test(smem_u32(&S.empty2[s2]), (u2 - 1) & 1)) {
+        int c, tr;
+        coord(itb, &c, &tr);
+        const uint32_t bar = smem_u32(&S.full2[s2]);
+        mbar_arrive_expect_tx(bar, Cfg::kB);
+        tma_load_2d(S.base2 + s2 * Cfg::kStage2 + 3 * kTcA, y_pass ? &maps->g3 : &maps->x3, c * kTcBK, 0, bar);
+        ++itb;
+        progressed = true;
+      }
+    }
+    if (progressed) {
+      idle = 0;
+    } else {
+      if (++idle > (1u << 25)) return false;
+      __nanosleep(32);
+    }
+  }
+  return true;
+}
+
+// fused T pass (float A)
+template <int NPAD>
+__global__ void __launch_bounds__(kTcFusedThreads, 1) tc_t_fused_kernel(const TcArgs a) {
+  using Cfg = TcFusedCfg<NPAD>;
+  constexpr int MPAD = Cfg::MPAD;
+  constexpr uint32_t kIdesc = idesc_bf16_f32(NPAD, 0, 0);
+  extern __shared__ unsigned char smem_raw[];
+  const TcFusedSmem S = tc_fused_smem<NPAD>(smem_raw);
+  __shared__ float gam_s[kMaxM], mu_s[kMaxM];
+  __shared__ int act_s[kMaxM];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const IO* io = a.io;
+  State* st = a.st;
+  const TcMaps* maps = static_cast<const TcMaps*>(io->tc_maps);
+  const bool sketch = a.sketch != 0;
+  const int form = sketch ? GPSPCA_SL0 : a.form;
+  if (tid < kMaxM) {
+    const bool v = tid < a.m && !sketch;
+    gam_s[tid] = v ? static_cast<float>(st->gamma[tid]) : 0.0f;
+    mu_s[tid] = v ? static_cast<float>(io->mu[tid]) : 1.0f;
+    act_s[tid] = tid < a.m ? st->active[tid] : 0;
+  }
+  const uint32_t tmem = tc_fused_setup<NPAD>(S);
+  bool timed_out = false;
+  if (warp == 4) {
+    if (lane == 0) {
+      tmap_acquire(&maps->a1f);
+      tmap_acquire(&maps->x3);
+      const int ntiles = blockIdx.x < a.ntile1 ? (a.ntile1 - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+      const int kc = a.kchunks1;
+      if (!tc_fused_producer<NPAD>(
+              S, ntiles * kc,
+              [&](int it, int* c, int* tr) {
+                *c = it % kc;
+                *tr = blockIdx.x + (it / kc) * gridDim.x;
+              },
+              maps, false)) {
+        timed_out = true;
+        *S.acc.abort_flag = 1;
+      }
+    }
+  } else if (warp == 5) {
+    if (lane == 0) {
+      int it = 0;
+      for (int tile = blockIdx.x; tile < a.ntile1 && !timed_out; tile += gridDim.x)
+        for (int c = 0; c < a.kchunks1 && !timed_out; ++c, ++it)
+          if (!tc_fused_mma<NPAD, false>(S, tmem, it, kIdesc)) {
+            timed_out = true;
+            *S.acc.abort_flag = 1;
+          }
+    }
+  } else if (warp >= 6) {  // converters
+    int it = 0;
+    for (int tile = blockIdx.x; tile < a.ntile1 && !timed_out; tile += gridDim.x)
+      for (int c = 0; c < a.kchunks1 && !timed_out; ++c, ++it)
+        if (tc_aborted(S.acc) || !tc_convert_chunk<NPAD, false>(S, it)) {
+          timed_out = true;
+          *S.acc.abort_flag = 1;
+        }
+  } else {  // epilogue
+    const uint32_t tlane = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+    float* Tout = static_cast<float*>(io->T);
+    __nv_bfloat16* G3 = static_cast<__nv_bfloat16*>(io->tc_g3);
+    const int64_t gs = a.n_pad;
+    int it = 0;
+    for (int tile = blockIdx.x; tile < a.ntile1 && !timed_out; tile += gridDim.x) {
+      float t[MPAD];
+#pragma unroll
+      for (int j = 0; j < MPAD; ++j) t[j] = 0.0f;
+      for (int c = 0; c < a.kchunks1; ++c, ++it)
+        if (!tc_drain<NPAD, 3>(S.acc, tlane, it, t)) {
+          timed_out = true;
+          *S.acc.abort_flag = 1;
+          break;
+        }
+      if (timed_out) break;
+      const int i = tile * kTcTile1 + warp * 32 + lane;
+      if (i < a.n) {
+#pragma unroll
+        for (int j = 0; j < MPAD; ++j) {
+          float g = 0.0f;
+          if (j < a.m) {
+            if (!sketch && act_s[j]) Tout[static_cast<int64_t>(j) * a.n + i] = t[j];
+            g = grad_factor<float>(form, t[j], gam_s[j], mu_s[j]);
+          }
+          __nv_bfloat16 b0, b1, b2;
+          split3(g, b0, b1, b2);
+          G3[(0 * MPAD + j) * gs + i] = b0;
+          G3[(1 * MPAD + j) * gs + i] = b1;
+          G3[(2 * MPAD + j) * gs + i] = b2;
+        }
+      }
+    }
+  }
+  if (timed_out) atomicOr(&st->error, static_cast<int>(kErrTimeout));
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, Cfg::kCols);
+  }
+}
+
+// fused Y pass (float A)
+template <int NPAD>
+__global__ void __launch_bounds__(kTcFusedThreads, 1) tc_y_fused_kernel(const TcArgs a) {
+  using Cfg = TcFusedCfg<NPAD>;
+  constexpr int MPAD = Cfg::MPAD;
+  constexpr uint32_t kIdesc = idesc_bf16_f32(NPAD, 1, 0);
+  extern __shared__ unsigned char smem_raw[];
+  const TcFusedSmem S = tc_fused_smem<NPAD>(smem_raw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const IO* io = a.io;
+  State* st = a.st;
+  const TcMaps* maps = static_cast<const TcMaps*>(io->tc_maps);
+  const int rb = blockIdx.x, sp = blockIdx.y;
+  const int cb = sp * a.kps2, ce = min(a.nchunks2, cb + a.kps2);
+  const uint32_t tmem = tc_fused_setup<NPAD>(S);
+  bool timed_out = false;
+  if (warp == 4) {
+    if (lane == 0) {
+      tmap_acquire(&maps->a2f);
+      tmap_acquire(&maps->g3);
+      if (!tc_fused_producer<NPAD>(
+              S, max(0, ce - cb),
+              [&](int it, int* c, int* tr) {
+                *c = cb + it;
+                *tr = rb;
+              },
+              maps, true)) {
+        timed_out = true;
+        *S.acc.abort_flag = 1;
+      }
+    }
+  } else if (warp == 5) {
+    if (lane == 0) {
+      for (int c = cb, it = 0; c < ce && !timed_out; ++c, ++it)
+        if (!tc_fused_mma<NPAD, true>(S, tmem, it, kIdesc)) {
+          timed_out = true;
+          *S.acc.abort_flag = 1;
+        }
+    }
+  } else if (warp >= 6) {
+    for (int c = cb, it = 0; c < ce && !timed_out; ++c, ++it)
+      if (tc_aborted(S.acc) || !tc_convert_chunk<NPAD, true>(S, it)) {
+        timed_out = true;
+        *S.acc.abort_flag = 1;
+      }
+  } else {
+    const uint32_t tlane = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+    float y[MPAD];
+#pragma unroll
+    for (int j = 0; j < MPAD; ++j) y[j] = 0.0f;
+    for (int c = cb, it = 0; c < ce; ++c, ++it)
+      if (!tc_drain<NPAD, 3>(S.acc, tlane, it, y)) {
+        timed_out = true;
+        *S.acc.abort_flag = 1;
+        break;
+      }
+    const int r = rb * kTcRows2 + warp * 32 + lane;
+    if (!timed_out && r < a.p) {
+      float* yp = static_cast<float*>(io->ypart);
+#pragma unroll
+      for (int j = 0; j < MPAD; ++j)
+        if (j < a.m) yp[(static_cast<int64_t>(sp) * a.m + j) * a.p + r] = y[j];
+    }
+  }
+  if (timed_out) atomicOr(&st->error, static_cast<int>(kErrTimeout));
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, Cfg::kCols);
+  }
+}
+
 // ---------------------------------------------------------------- host
 
 int tc_smem_bytes(int npad, int na) {
@@ -446,6 +880,29 @@ static bool encode_bf16(CUtensorMap* m, const void* base, int64_t inner, int64_t
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+static bool encode_f32(CUtensorMap* m, const void* base, int64_t inner, int64_t outer, int64_t stride_elems,
+                       int box_outer) {
+  const EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {static_cast<cuuint64_t>(inner), static_cast<cuuint64_t>(outer)};
+  const cuuint64_t strides[1] = {static_cast<cuuint64_t>(stride_elems) * 4};
+  const cuuint32_t box[2] = {32u, static_cast<cuuint32_t>(box_outer)};
+  const cuuint32_t estr[2] = {1u, 1u};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int tc_encode_maps_f32(TcMaps* maps, const void* A, int64_t p, int64_t n, int64_t ld, const void* x3, int p_pad,
+                       const void* g3, int n_pad, int npad) {
+  if (!encode_bf16(&maps->x3, x3, p, npad, p_pad, npad) || !encode_bf16(&maps->g3, g3, n, npad, n_pad, npad) ||
+      !encode_f32(&maps->a1f, A, p, n, ld, kTcTile1) || !encode_f32(&maps->a2f, A, p, n, ld, 64))
+    return record_error(GPSPCA_ECUDA, "cuTensorMapEncodeTiled failed for the fused tensor-core sweep");
+  return GPSPCA_OK;
+}
+
+int tc_fused_smem_bytes(int npad) { return tc_fused_smem(npad); }
+
 int tc_encode_maps(TcMaps* maps, const void* planes, int na, int64_t plane, int64_t p, int64_t n, int64_t ld,
                    const void* x3, int p_pad, const void* g3, int n_pad, int npad) {
   bool ok = encode_bf16(&maps->x3, x3, p, npad, p_pad, npad) && encode_bf16(&maps->g3, g3, n, npad, n_pad, npad);
@@ -459,16 +916,16 @@ int tc_encode_maps(TcMaps* maps, const void* planes, int na, int64_t plane, int6
 
 // float A -> three bf16 planes (a = a0 + a1 + a2 exactly); fp8 -> its values
 // in bf16 (exact; the column scale stays separate); bf16 with a layout TMA
-// cannot read -> a copy with the padded column stride.  Grid-stride over A.
+// cannot read -> a copy with the padded column stride.  Block (x, y): columns
+// y, y + gridDim.y, ...; rows by the threads of x (coalesced along a column).
 template <typename TA>
 __global__ void tc_convert_kernel(const IO* io, int64_t p, int64_t n, int64_t ld, int64_t ldc) {
   const TA* A = static_cast<const TA*>(io->A);
   __nv_bfloat16* planes = static_cast<__nv_bfloat16*>(io->tc_planes);
   const int64_t plane = n * ldc;
-  const int64_t total = n * p;
-  for (int64_t q = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; q < total;
-       q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t i = q / p, r = q - i * p;
+  const int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (r >= p) return;
+  for (int64_t i = blockIdx.y; i < n; i += gridDim.y) {
     const float v = to_tc<TA>(A[i * ld + r]);
     if constexpr (sizeof(TA) == 4) {
       __nv_bfloat16 b0, b1, b2;
@@ -486,12 +943,15 @@ void launch_tc_convert(int dtype, const IO* io, int64_t p, int64_t n, int64_t ld
   int dev = 0, nsm = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const unsigned bx = static_cast<unsigned>((p + 255) / 256);
+  const unsigned by = static_cast<unsigned>(std::min<int64_t>(n, std::max<int64_t>(1, (nsm * 16) / bx)));
+  const dim3 grid(bx, by);
   if (dtype == GPSPCA_F32)
-    tc_convert_kernel<float><<<nsm * 8, 256, 0, s>>>(io, p, n, ld, ldc);
+    tc_convert_kernel<float><<<grid, 256, 0, s>>>(io, p, n, ld, ldc);
   else if (dtype == GPSPCA_FP8_E4M3)
-    tc_convert_kernel<__nv_fp8_e4m3><<<nsm * 8, 256, 0, s>>>(io, p, n, ld, ldc);
+    tc_convert_kernel<__nv_fp8_e4m3><<<grid, 256, 0, s>>>(io, p, n, ld, ldc);
   else if (dtype == GPSPCA_BF16)  // a layout TMA cannot read in place: padded copy
-    tc_convert_kernel<__nv_bfloat16><<<nsm * 8, 256, 0, s>>>(io, p, n, ld, ldc);
+    tc_convert_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(io, p, n, ld, ldc);
 }
 
 template <int NPAD, int NA>
@@ -508,6 +968,20 @@ static void launch_tc_npad(const TcArgs& a, int nsm, cudaStream_t s) {
   tc_y_kernel<NPAD, NA><<<dim3(a.nrow2, a.nsplit2), kTcThreads, smem, s>>>(a);
 }
 
+template <int NPAD>
+static void launch_tc_fused_npad(const TcArgs& a, int nsm, cudaStream_t s) {
+  static bool once = [] {
+    cudaFuncSetAttribute(tc_t_fused_kernel<NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_fused_smem(NPAD));
+    cudaFuncSetAttribute(tc_y_fused_kernel<NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_fused_smem(NPAD));
+    return true;
+  }();
+  (void)once;
+  const int smem = tc_fused_smem(NPAD);
+  tc_prep_kernel<<<(a.p + 255) / 256, 256, 0, s>>>(a);
+  tc_t_fused_kernel<NPAD><<<std::max(1, std::min(a.ntile1, nsm)), kTcFusedThreads, smem, s>>>(a);
+  tc_y_fused_kernel<NPAD><<<dim3(a.nrow2, a.nsplit2), kTcFusedThreads, smem, s>>>(a);
+}
+
 template <int NA>
 static void launch_tc_na(const TcArgs& a, int npad, int nsm, cudaStream_t s) {
   switch (npad) {
@@ -522,10 +996,18 @@ void launch_tc_sweep(const TcArgs& a, int npad, cudaStream_t s) {
   int dev = 0, nsm = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (a.na == 3)
+  if (a.fused) {
+    switch (npad) {
+      case 48: launch_tc_fused_npad<48>(a, nsm, s); break;
+      case 96: launch_tc_fused_npad<96>(a, nsm, s); break;
+      case 144: launch_tc_fused_npad<144>(a, nsm, s); break;
+      default: launch_tc_fused_npad<192>(a, nsm, s); break;
+    }
+  } else if (a.na == 3) {
     launch_tc_na<3>(a, npad, nsm, s);
-  else
+  } else {
     launch_tc_na<1>(a, npad, nsm, s);
+  }
 }
 
 }  // namespace gpspca

@@ -50,6 +50,8 @@ struct TcMaps {
   CUtensorMap x3;     // X3^T, box 64 x N
   CUtensorMap a2[3];  // bf16 planes of A, box 64 rows x 64 columns (Y pass)
   CUtensorMap g3;     // G3^T, box 64 x N
+  CUtensorMap a1f;    // float A, box 32 rows x 128 columns (fused T pass)
+  CUtensorMap a2f;    // float A, box 32 rows x 64 columns (fused Y pass)
 };
 
 struct TcArgs {
@@ -57,6 +59,7 @@ struct TcArgs {
   State* st;
   int p, n, m, mpad, form, sketch;
   int na;             // bf16 planes of A: 1 (bf16 storage, or the fp8 values), 3 (float A = a0 + a1 + a2)
+  int fused;          // float A read as float by TMA and split into its 3 planes in shared memory
   int scaled;         // fp8 storage: a_i = s_i q_i, the column scale applied to t and g
   int p_pad, n_pad;   // row strides (elements) of X3^T and G3^T
   int ntile1;         // ceil(n / 128)
@@ -73,6 +76,10 @@ bool tc_supported(int device);
 // planes: na bf16 matrices (p x n, column stride ld elements, `plane` elements apart)
 int tc_encode_maps(TcMaps* maps, const void* planes, int na, int64_t plane, int64_t p, int64_t n, int64_t ld,
                    const void* x3, int p_pad, const void* g3, int n_pad, int npad);
+// float A read in place by the fused passes (16-byte aligned base, ld % 4 == 0)
+int tc_encode_maps_f32(TcMaps* maps, const void* A, int64_t p, int64_t n, int64_t ld, const void* x3, int p_pad,
+                       const void* g3, int n_pad, int npad);
+int tc_fused_smem_bytes(int npad);
 // float / fp8 / unaligned bf16 A -> bf16 planes in the workspace (once per
 // solve); ldc = p_pad
 void launch_tc_convert(int dtype, const IO* io, int64_t p, int64_t n, int64_t ld, int64_t ldc, cudaStream_t s);
