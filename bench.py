@@ -459,7 +459,10 @@ def run_gamma_path(args):
                       "planted spikes 10000x50000 fp32 (3 spikes, theta_j=40/j, 2% supports), 64 gammas log-spaced "
                       "[0.001,0.5]*max||a_i||, SL1/SL0 batched vs separate; BL1 m=32 gamma=0.01*max||a_i||", "f32",
                       {"results": res,
-                       "roofline": {"bound": "hbm", "kernel": "sweep_kernel<float,8,*> x 8 passes (64 columns)",
+                       "roofline": {"bound": "hbm",
+                                    "kernel": "tc_t_fused_kernel<192> + tc_y_fused_kernel<192> (tcgen05, float A "
+                                              "split into exact bf16 planes in shared memory; two reads of A)",
+                                    "frac_of_two_reads": round(2 * nbytes / (ms_sw / 1e3) / 1e9 / peak, 4),
                                     "achieved": round(nbytes / (ms_sw / 1e3) / 1e9, 1), "peak": peak,
                                     "unit": "GB/s", "frac": round(nbytes / (ms_sw / 1e3) / 1e9 / peak, 4),
                                     "peak_source": kind, "traffic": None, "ms_per_sweep": round(ms_sw, 4),
