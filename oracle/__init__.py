@@ -26,3 +26,4 @@ from .gpower import (  # noqa: F401
     POWER_STEPS,
     gpower,
 )
+from .deflation import gpower_deflated  # noqa: F401,E402
