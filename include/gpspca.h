@@ -182,6 +182,30 @@ typedef struct {
  * solve returned GPSPCA_OK or GPSPCA_EDEGENERATE, else the first other code. */
 int gpspca_solve_batch(gpspca_ctx* ctx, int32_t count, const gpspca_request* reqs, int32_t* rcs);
 
+/* Several sparse components with a single-unit formulation (form SL1 or
+ * SL0), by projection deflation: component j (0 <= j < m) is the single-unit
+ * solve with gamma[j] (as gpspca_solve with one gamma value, same start and
+ * stopping rule) on the deflated matrix
+ *   A_0 = A,   A_j = A_{j-1} - u_j z_j^T,   u_j = A_{j-1} z_j,
+ * i.e. A_j = A_{j-1} (I - z_j z_j^T) with z_j the unit loading (Z column) of
+ * component j, so that A_j z_j = 0.  The paper extracts several single-unit
+ * components (Section 4.1, Fig. 3, m = 5) without naming the deflation; this
+ * is the reading taken.  With GPSPCA_GAMMA_RELATIVE, gamma[j] is relative to
+ * the largest column norm of A_{j-1}.
+ *
+ * A is not modified.  The library deflates a working copy (float; double for
+ * F64 storage, whose solves compute in double; bf16 / fp8 storage is widened
+ * to float, fp8 times its column scale), held only during the call and
+ * counted against the budget (p x n elements of the working type), touching
+ * only the support columns of each z_j.  Results as for gpspca_solve with m
+ * entries: column j of X, Z and support, objective[j] (f of component j on
+ * A_{j-1}), iters[j], status[j] and gamma_abs[j] belong to component j.  A
+ * component with status ZERO deflates nothing.  Flags: GPSPCA_GAMMA_RELATIVE,
+ * GPSPCA_EAGER, GPSPCA_NO_TENSOR_CORES.  Returns when every component is done
+ * (GPSPCA_EINVAL for a block form). */
+int gpspca_solve_deflated(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form, const double* gamma, int32_t m,
+                          double tol, int32_t maxit, uint32_t flags, gpspca_out* out);
+
 /* Asynchronous form of gpspca_solve for many concurrent requests.  The
  * request is queued; a scheduler thread admits it when its workspace fits the
  * budget next to the solves already running, and advances every admitted

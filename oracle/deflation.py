@@ -33,8 +33,9 @@ def gpower_deflated(A, form: str, gamma, tol: float = 1e-6, maxit: int = 1000, r
     on the deflated matrix A_{j-1} (module docstring).
 
     Returns an ``OracleResult`` whose column j holds component j (objective[j]
-    is f of component j on A_{j-1}; gamma the absolute values used), and with
-    ``return_deflated`` also the final deflated matrix A_m.
+    is f of component j on A_{j-1}; gamma the absolute values used; the extra
+    attribute ``cnorms``, n x m, holds the column norms of each matrix solved,
+    A_{j-1}), and with ``return_deflated`` also the final deflated matrix A_m.
     """
     _check_form(form)
     if _is_block(form):
@@ -53,7 +54,9 @@ def gpower_deflated(A, form: str, gamma, tol: float = 1e-6, maxit: int = 1000, r
     status = np.zeros(m, dtype=np.int64)
     gabs = np.zeros(m)
     history = []
+    cnorms = np.zeros((n, m))
     for j in range(m):
+        cnorms[:, j] = np.linalg.norm(Aj, axis=0)
         gj = float(gamma_from_rho(Aj, form, gamma[j])[0]) if relative else float(gamma[j])
         r = gpower(Aj, form, [gj], tol=tol, maxit=maxit)
         X[:, j] = r.X[:, 0]
@@ -68,4 +71,5 @@ def gpower_deflated(A, form: str, gamma, tol: float = 1e-6, maxit: int = 1000, r
         u = Aj @ z  # u_j = A_{j-1} z_j
         Aj = Aj - np.outer(u, z)  # A_j = A_{j-1} (I - z_j z_j^T)
     res = OracleResult(X, Z, objective, iters, status, gabs, np.ones(m), history, T)
+    res.cnorms = cnorms
     return (res, Aj) if return_deflated else res

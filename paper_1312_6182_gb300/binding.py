@@ -39,7 +39,7 @@ ERROR_NAMES = {
 
 EXPORTED = ("gpspca_create", "gpspca_solve", "gpspca_submit", "gpspca_poll", "gpspca_destroy",
             "gpspca_last_error", "gpspca_time_sweep", "gpspca_sweep_static", "gpspca_synth_spikes",
-            "gpspca_solve_batch")
+            "gpspca_solve_batch", "gpspca_solve_deflated")
 
 
 class Matrix(ctypes.Structure):
@@ -100,6 +100,9 @@ def load(path: str = LIB_PATH):
     lib.gpspca_solve.argtypes = [P, ctypes.POINTER(Matrix), ctypes.c_int, D, ctypes.c_int32, D, ctypes.c_double,
                                  ctypes.c_int32, P, ctypes.c_uint32, ctypes.POINTER(Out)]
     lib.gpspca_solve.restype = ctypes.c_int
+    lib.gpspca_solve_deflated.argtypes = [P, ctypes.POINTER(Matrix), ctypes.c_int, D, ctypes.c_int32,
+                                          ctypes.c_double, ctypes.c_int32, ctypes.c_uint32, ctypes.POINTER(Out)]
+    lib.gpspca_solve_deflated.restype = ctypes.c_int
     lib.gpspca_submit.argtypes = [P, ctypes.POINTER(Matrix), ctypes.c_int, D, ctypes.c_int32, D, ctypes.c_double,
                                   ctypes.c_int32, ctypes.c_uint32, ctypes.POINTER(Out),
                                   ctypes.POINTER(ctypes.c_uint64)]
@@ -284,6 +287,29 @@ class Context:
                                    | (0 if tensor_cores else NO_TENSOR_CORES), ctypes.byref(o))
         allow = (OK, EDEGENERATE) if allow_degenerate else (OK,)
         _check(rc, allow)
+        out.rc = rc
+        return out
+
+    def solve_deflated(self, At, form: str, gamma, tol: float = 1e-6, maxit: int = 1000,
+                       gamma_relative: bool = False, p: Optional[int] = None, col_scale=None,
+                       out: Optional[Result] = None, eager: bool = False) -> Result:
+        """Several single-unit components (form SL1 or SL0) by projection
+        deflation (gpspca_solve_deflated): component j solves with gamma[j] on
+        A_{j-1} = A_{j-2} (I - z_{j-1} z_{j-1}^T).  A is not modified."""
+        import torch
+
+        gamma = [float(g) for g in (gamma if hasattr(gamma, "__len__") else [gamma])]
+        m = len(gamma)
+        M = matrix(At, p, col_scale)
+        tc = torch.float64 if At.dtype == torch.float64 else torch.float32
+        if out is None:
+            out = alloc_result(m, int(M.p), int(M.n), At.device, tc)
+        o = out_struct(out)
+        self._sync_torch(At, None, out.X)
+        rc = self.lib.gpspca_solve_deflated(self.ptr, ctypes.byref(M), FORMS[form], _darr(gamma, m), m, float(tol),
+                                            int(maxit), (GAMMA_RELATIVE if gamma_relative else 0)
+                                            | (EAGER if eager else 0), ctypes.byref(o))
+        _check(rc, (OK, EDEGENERATE))
         out.rc = rc
         return out
 

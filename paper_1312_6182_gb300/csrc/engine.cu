@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "aux.cuh"
+#include "deflate.cuh"
 #include "plan.h"
 #include "tc_sweep.cuh"
 
@@ -342,6 +343,7 @@ struct Slot {
   TcMaps* maps_host = nullptr;  // pinned: the tensor maps copied to b_maps before a solve
   // staging for host-located inputs/outputs
   DevBuf s_A, s_scale, s_x0, s_X, s_Z, s_sup, s_obj, s_it, s_stat, s_gam;
+  DevBuf d_W;  // deflation: the working copy of A
   struct GraphEntry {
     cudaGraph_t g = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -353,7 +355,7 @@ struct Slot {
     for (const DevBuf* b : {&b_cnorm, &b_P, &b_Y, &b_ypart, &b_T, &b_fpart, &b_gpart, &b_x3, &b_g3, &b_maps,
                             &b_planes, &s_A,
                             &s_scale, &s_x0, &s_X,
-                            &s_Z, &s_sup, &s_obj, &s_it, &s_stat, &s_gam})
+                            &s_Z, &s_sup, &s_obj, &s_it, &s_stat, &s_gam, &d_W})
       s += b->bytes;
     return s;
   }
@@ -397,7 +399,8 @@ static void release(Slot* s, DevBuf* b) {
 static void release_workspace(Slot* s) {
   for (DevBuf* b : {&s->b_cnorm, &s->b_P, &s->b_Y, &s->b_ypart, &s->b_T, &s->b_fpart, &s->b_gpart, &s->b_x3,
                     &s->b_g3, &s->b_maps, &s->b_planes, &s->s_A,
-                    &s->s_scale, &s->s_x0, &s->s_X, &s->s_Z, &s->s_sup, &s->s_obj, &s->s_it, &s->s_stat, &s->s_gam})
+                    &s->s_scale, &s->s_x0, &s->s_X, &s->s_Z, &s->s_sup, &s->s_obj, &s->s_it, &s->s_stat, &s->s_gam,
+                    &s->d_W})
     release(s, b);
 }
 
@@ -1068,6 +1071,117 @@ int gpspca_solve(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form, cons
   rc = launch_solve(&ctx->sync_slot, r, ctx->nsm, &empty);
   if (rc != GPSPCA_OK || empty) return rc;
   return solve_result(&ctx->sync_slot);
+}
+
+int gpspca_solve_deflated(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form, const double* gamma, int32_t m,
+                          double tol, int32_t maxit, uint32_t flags, gpspca_out* out) {
+  if (!ctx) return fail(GPSPCA_EINVAL, "ctx is NULL");
+  if (form != GPSPCA_SL1 && form != GPSPCA_SL0)
+    return fail(GPSPCA_EINVAL, "deflation extracts single-unit components (SL1 or SL0)");
+  Request r;
+  int rc = request_from(&r, A, form, gamma, m, nullptr, tol, maxit, nullptr, flags, out);
+  if (rc != GPSPCA_OK) return rc;
+  if ((rc = validate(r)) != GPSPCA_OK) return rc;
+  std::lock_guard<std::mutex> lk(ctx->solve_mu);
+  GP_CUDA(cudaSetDevice(ctx->device));
+  Slot* s = &ctx->sync_slot;
+  if (r.A.p == 0 || r.A.n == 0) return solve_empty(s, r);
+  const int64_t p = r.A.p, n = r.A.n;
+  const int wdt = r.A.dtype == GPSPCA_F64 ? GPSPCA_F64 : GPSPCA_F32;
+  const size_t tcs = wdt == GPSPCA_F64 ? sizeof(double) : sizeof(float);
+  const int64_t ldw = deflate_ld(wdt, p);
+  const size_t nw = static_cast<size_t>((n + 31) / 32);
+  // A on the device (host input staged), then the working copy
+  const DInfo d = dinfo(r.A.dtype);
+  const void* A_dev = r.A.data;
+  const float* scale_dev = r.A.col_scale;
+  if (r.A.location == GPSPCA_HOST) {
+    const size_t a_bytes = static_cast<size_t>(r.A.ld) * n * d.esize;
+    if ((rc = ensure(s, &s->s_A, a_bytes))) return rc;
+    GP_CUDA(cudaMemcpyAsync(s->s_A.p, r.A.data, a_bytes, cudaMemcpyHostToDevice, s->stream));
+    A_dev = s->s_A.p;
+    if (r.A.dtype == GPSPCA_FP8_E4M3) {
+      if ((rc = ensure(s, &s->s_scale, sizeof(float) * n))) return rc;
+      GP_CUDA(cudaMemcpyAsync(s->s_scale.p, r.A.col_scale, sizeof(float) * n, cudaMemcpyHostToDevice, s->stream));
+      scale_dev = static_cast<const float*>(s->s_scale.p);
+    }
+  }
+  if ((rc = ensure(s, &s->d_W, tcs * static_cast<size_t>(ldw) * n))) return rc;
+  struct WGuard {  // the working copy is as large as A: never kept after the call
+    Slot* s;
+    ~WGuard() {
+      cudaStreamSynchronize(s->stream);
+      release(s, &s->d_W);
+    }
+  } wguard{s};
+  launch_deflate_copy(r.A.dtype, A_dev, r.A.ld, r.A.dtype == GPSPCA_FP8_E4M3 ? scale_dev : nullptr, s->d_W.p, ldw, p, n,
+                      s->stream);
+  GP_CUDA(cudaGetLastError());
+  if (r.A.location == GPSPCA_HOST) release(s, &s->s_A);  // only the working copy is read from here on
+  // results on the device: the caller's buffers, or staging for host outputs
+  const bool staged = r.out.location == GPSPCA_HOST;
+  gpspca_out o = r.out;
+  if (staged) {
+    if ((rc = ensure(s, &s->s_X, tcs * p * m))) return rc;
+    if ((rc = ensure(s, &s->s_Z, tcs * n * m))) return rc;
+    if ((rc = ensure(s, &s->s_sup, sizeof(uint32_t) * nw * m))) return rc;
+    if ((rc = ensure(s, &s->s_obj, sizeof(double) * m))) return rc;
+    if ((rc = ensure(s, &s->s_it, sizeof(int32_t) * m))) return rc;
+    if ((rc = ensure(s, &s->s_stat, sizeof(int32_t) * m))) return rc;
+    if ((rc = ensure(s, &s->s_gam, sizeof(double) * m))) return rc;
+    o.location = GPSPCA_DEVICE;
+    o.X = s->s_X.p;
+    o.Z = s->s_Z.p;
+    o.support = r.out.support ? static_cast<uint32_t*>(s->s_sup.p) : nullptr;
+    o.objective = static_cast<double*>(s->s_obj.p);
+    o.iters = static_cast<int32_t*>(s->s_it.p);
+    o.status = static_cast<int32_t*>(s->s_stat.p);
+    o.gamma_abs = r.out.gamma_abs ? static_cast<double*>(s->s_gam.p) : nullptr;
+  }
+  int first_err = GPSPCA_OK;
+  for (int j = 0; j < m; ++j) {
+    Request rj;
+    rj.A = gpspca_matrix{s->d_W.p, static_cast<gpspca_dtype>(wdt), GPSPCA_DEVICE, p, n, ldw, nullptr};
+    rj.form = r.form;
+    rj.m = 1;
+    rj.gamma.assign(1, r.gamma[j]);
+    rj.mu.assign(1, 1.0);
+    rj.tol = r.tol;
+    rj.maxit = r.maxit;
+    rj.flags = r.flags;
+    rj.out = o;
+    rj.out.X = static_cast<char*>(o.X) + tcs * p * j;
+    rj.out.Z = static_cast<char*>(o.Z) + tcs * n * j;
+    rj.out.support = o.support ? o.support + nw * j : nullptr;
+    rj.out.objective = o.objective + j;
+    rj.out.iters = o.iters + j;
+    rj.out.status = o.status + j;
+    rj.out.gamma_abs = o.gamma_abs ? o.gamma_abs + j : nullptr;
+    bool empty = false;
+    rc = launch_solve(s, rj, ctx->nsm, &empty);
+    if (rc == GPSPCA_OK && !empty) rc = solve_result(s);
+    if (rc != GPSPCA_OK && rc != GPSPCA_EDEGENERATE) return rc;
+    if (first_err == GPSPCA_OK) first_err = rc;
+    // A_j = A_{j-1} - (A_{j-1} z_j) z_j^T (z_j = 0 leaves it unchanged)
+    if (j + 1 < m) {
+      launch_deflate(wdt, s->d_W.p, ldw, p, n, rj.out.Z, s->stream);
+      GP_CUDA(cudaGetLastError());
+    }
+  }
+  if (staged) {
+    GP_CUDA(cudaMemcpyAsync(r.out.X, o.X, tcs * p * m, cudaMemcpyDeviceToHost, s->stream));
+    GP_CUDA(cudaMemcpyAsync(r.out.Z, o.Z, tcs * n * m, cudaMemcpyDeviceToHost, s->stream));
+    if (r.out.support)
+      GP_CUDA(cudaMemcpyAsync(r.out.support, o.support, sizeof(uint32_t) * nw * m, cudaMemcpyDeviceToHost, s->stream));
+    GP_CUDA(cudaMemcpyAsync(r.out.objective, o.objective, sizeof(double) * m, cudaMemcpyDeviceToHost, s->stream));
+    GP_CUDA(cudaMemcpyAsync(r.out.iters, o.iters, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, s->stream));
+    GP_CUDA(cudaMemcpyAsync(r.out.status, o.status, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, s->stream));
+    if (r.out.gamma_abs)
+      GP_CUDA(cudaMemcpyAsync(r.out.gamma_abs, o.gamma_abs, sizeof(double) * m, cudaMemcpyDeviceToHost, s->stream));
+  }
+  GP_CUDA(cudaStreamSynchronize(s->stream));
+  if (first_err != GPSPCA_OK) return fail(first_err, "a component's polar step was degenerate (status DEGENERATE)");
+  return GPSPCA_OK;
 }
 
 int gpspca_time_sweep(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form, const double* gamma, int32_t m,
