@@ -472,6 +472,152 @@ def run_gamma_path(args):
     print(json.dumps(line), flush=True)
 
 
+def run_deflation(args):
+    """Several single-unit components by projection deflation on the 5000 x
+    20000 FP32 planted-spike matrix (five spikes): SL1 and SL0, m = 5
+    components, relative gamma 0.05 of each deflated matrix's largest column.
+    Units: power iterations (sweeps t = A^T x, all components) per second over
+    the whole extraction (working copy, five solves, four deflations).  With
+    --oracle, the FP64 oracle's extraction of the same components is timed on
+    the host cores and its objectives compared."""
+    import time
+
+    import numpy as np
+    import torch
+
+    from paper_1312_6182_gb300 import binding, synth
+
+    p, n, m = 5000, 20000, 5
+    At = synth.workload_spikes_5000x20000(0)
+    dA = torch.from_numpy(At).cuda()
+    stream = torch.cuda.Stream()
+    ctx = binding.Context(0, stream=stream)
+    res = {}
+    clk = Clocks(0)
+    clocks = None
+    for form in ("SL1", "SL0"):
+        out = binding.alloc_result(m, p, n, "cuda", torch.float32)
+        for _ in range(args.warmup):
+            ctx.solve_deflated(dA, form, [0.05] * m, gamma_relative=True, out=out)
+        if form == "SL1":
+            clk.start()
+        ms, r = _event_ms(stream, lambda: ctx.solve_deflated(dA, form, [0.05] * m, gamma_relative=True, out=out),
+                          args.steps)
+        if form == "SL1":
+            clocks = clk.stop()
+        iters = [int(v) for v in r.iters.tolist()]
+        one = binding.alloc_result(1, p, n, "cuda", torch.float32)
+        ms1, r1 = _event_ms(stream, lambda: ctx.solve(dA, form, [0.05], gamma_relative=True, out=one), args.steps)
+        res[form] = {"iters_per_s": round(sum(iters) / (ms / 1e3), 1), "ms_per_extraction": round(ms, 3),
+                     "iters": iters, "status": [int(v) for v in r.status.tolist()],
+                     "support_sizes": [int(v) for v in (r.Z != 0).sum(dim=1).tolist()],
+                     "objective": [float(v) for v in r.objective.tolist()],
+                     "first_component_alone_ms": round(ms1, 3)}
+        if args.oracle:
+            import oracle
+
+            A = At.astype(np.float64).T
+            t0 = time.perf_counter()
+            ref = oracle.gpower_deflated(A, form, [0.05] * m, tol=1e-6, maxit=1000, relative=True)
+            sec = time.perf_counter() - t0
+            obj = np.array(res[form]["objective"])
+            res[form]["oracle"] = {"seconds": round(sec, 2), "iters": [int(v) for v in ref.iters],
+                                   "objective_rel_err_max": float(np.max(np.abs(obj - ref.objective)
+                                                                         / np.abs(ref.objective))),
+                                   "cores": os.cpu_count()}
+    ctx.close()
+    value = res["SL1"]["iters_per_s"]
+    extra = {"results": res, "clocks": clocks}
+    if args.oracle:
+        o = res["SL1"]["oracle"]
+        extra["cpu_baseline"] = {"value": round(sum(o["iters"]) / o["seconds"], 3), "unit": "iters/s",
+                                 "cores": os.cpu_count(), "kind": "oracle",
+                                 "sample": "the full SL1 extraction (5 components) once"}
+    line = _base_line("deflation power iterations/s (5 single-unit components)", "iters/s", value,
+                      res["SL1"]["ms_per_extraction"], args,
+                      "planted spikes 5000x20000 fp32 (5 spikes), SL1/SL0, m=5 components by projection deflation, "
+                      "gamma=0.05*max||a_i|| of each deflated matrix", "f32", extra)
+    print(json.dumps(line), flush=True)
+
+
+SCALING_FORMS = (("SL0", 0.01), ("BL0", 0.01), ("SL1", 0.05), ("BL1", 0.05))
+
+
+def run_scaling(args):
+    """The paper's efficiency experiment (Section 4.1, Fig. 3) on synthetic
+    inputs: A is P x N i.i.d. N(0,1) (the paper's random instances; float32
+    here), N from 500 to 32000, P = N / 10, m = 5 components, the four
+    formulations at the paper's gamma values (read as relative to the largest
+    column norm): SL0 / BL0 at 0.01, SL1 / BL1 at 0.05.  Single-unit forms
+    extract their five components by deflation, block forms solve for all
+    five at once.  Reported: mean GPU milliseconds per solve (CUDA events,
+    A resident), and with --oracle the FP64 oracle's time on the host cores
+    for the sizes up to --oracle-max-n (one instance each) and the ratio.
+    value = the mean GPU time per solve at the largest N (over forms and
+    instances)."""
+    import time
+
+    import numpy as np
+    import torch
+
+    from paper_1312_6182_gb300 import binding, synth
+
+    sizes = [500, 1000, 2000, 4000, 8000, 16000, 32000]
+    stream = torch.cuda.Stream()
+    ctx = binding.Context(0, stream=stream)
+    table = []
+    clk = Clocks(0)
+    clk.start()
+    for N in sizes:
+        P = N // 10
+        row = {"N": N, "P": P}
+        out = binding.alloc_result(5, P, N, "cuda", torch.float32)
+        ms_all = {f: [] for f, _ in SCALING_FORMS}
+        iters_all = {f: [] for f, _ in SCALING_FORMS}
+        for inst in range(args.instances):
+            dA = torch.from_numpy(synth.gaussian(P, N, seed=100000 + 100 * N + inst, dtype=np.float32)).cuda()
+            for form, rho in SCALING_FORMS:
+                def run():
+                    if form.startswith("S"):
+                        return ctx.solve_deflated(dA, form, [rho] * 5, gamma_relative=True, out=out)
+                    return ctx.solve(dA, form, [rho] * 5, mu=[1.0] * 5, gamma_relative=True, out=out)
+
+                if inst == 0:
+                    run()  # warm: graphs and workspace
+                ms, r = _event_ms(stream, run, 1)
+                ms_all[form].append(ms)
+                iters_all[form].append(int(r.iters.sum().item()) if form.startswith("S")
+                                       else int(r.iters.max().item()))
+            del dA
+        for form, rho in SCALING_FORMS:
+            cell = {"gpu_ms": round(float(np.mean(ms_all[form])), 3),
+                    "iters_mean": round(float(np.mean(iters_all[form])), 1)}
+            if args.oracle and N <= args.oracle_max_n:
+                import oracle
+
+                A = synth.gaussian(P, N, seed=100000 + 100 * N, dtype=np.float32).astype(np.float64).T
+                t0 = time.perf_counter()
+                if form.startswith("S"):
+                    oracle.gpower_deflated(A, form, [rho] * 5, tol=1e-6, maxit=1000, relative=True)
+                else:
+                    gam = oracle.gamma_from_rho(A, form, [rho] * 5)
+                    oracle.gpower(A, form, gam, tol=1e-6, maxit=1000)
+                cell["oracle_ms"] = round((time.perf_counter() - t0) * 1e3, 1)
+                cell["oracle_over_gpu"] = round(cell["oracle_ms"] / ms_all[form][0], 1)
+            row[form] = cell
+        table.append(row)
+        print(json.dumps({"scaling_row": row}), file=sys.stderr, flush=True)
+    clocks = clk.stop()
+    ctx.close()
+    last = table[-1]
+    value = float(np.mean([last[f]["gpu_ms"] for f, _ in SCALING_FORMS]))
+    line = _base_line("GP-SPCA ms per solve, m=5 (Fig. 3 sweep, largest N)", "ms/solve", value, value, args,
+                      f"i.i.d. N(0,1) P x N fp32, N in {sizes}, P=N/10, {args.instances} instances, m=5, "
+                      "SL0/BL0 gamma=0.01, SL1/BL1 gamma=0.05 (relative), single-unit by deflation", "f32",
+                      {"higher_is_better": False, "results": table, "clocks": clocks})
+    print(json.dumps(line), flush=True)
+
+
 def _fp8_columns(dA32):
     """FP8 E4M3 storage with per-column scales s_i = max_r |A_ri| / 448."""
     import torch
@@ -707,10 +853,15 @@ def main():
     ap.add_argument("--sweep-m", type=int, default=None, help="sweep-only: components or gammas (default 1 / 5)")
     ap.add_argument("--sweep-dtype", default="f32", choices=["f32", "bf16"])
     ap.add_argument("--reps", type=int, default=20)
-    ap.add_argument("--workload", default="spikes5000", choices=["spikes5000", "gamma-path", "precision", "serving"],
-                    help="spikes5000: the headline step; the others measure the sparsity-path batch and the "
-                         "BF16/FP8 precision path (one JSON line each)")
-    ap.add_argument("--oracle", action="store_true", help="precision workload: errors against the FP64 oracle")
+    ap.add_argument("--workload", default="spikes5000",
+                    choices=["spikes5000", "gamma-path", "precision", "serving", "deflation", "scaling"],
+                    help="spikes5000: the headline step; the others measure the sparsity-path batch, the "
+                         "BF16/FP8 precision path, the serving mix, deflated multi-component extraction and the "
+                         "size sweep of the paper's efficiency experiment (one JSON line each)")
+    ap.add_argument("--oracle", action="store_true",
+                    help="precision / deflation / scaling workloads: also run (and time) the FP64 oracle")
+    ap.add_argument("--instances", type=int, default=4, help="scaling workload: random instances per size")
+    ap.add_argument("--oracle-max-n", type=int, default=8000, help="scaling workload: largest N the oracle runs")
     ap.add_argument("--requests", type=int, default=2000, help="serving workload: number of requests")
     ap.add_argument("--eager", action="store_true",
                     help="launch each solve's kernels one by one (profilers cannot follow the CUDA graph's "
@@ -723,7 +874,8 @@ def main():
         args.steps = 100 if args.workload == "spikes5000" else 4
     if args.workload != "spikes5000":
         args.warmup = max(args.warmup, 1)
-        {"gamma-path": run_gamma_path, "precision": run_precision, "serving": run_serving}[args.workload](args)
+        {"gamma-path": run_gamma_path, "precision": run_precision, "serving": run_serving,
+         "deflation": run_deflation, "scaling": run_scaling}[args.workload](args)
         return
     if args.warmup < 3 and args.impl == "gpu":
         args.warmup = 3

@@ -343,7 +343,7 @@ struct Slot {
   TcMaps* maps_host = nullptr;  // pinned: the tensor maps copied to b_maps before a solve
   // staging for host-located inputs/outputs
   DevBuf s_A, s_scale, s_x0, s_X, s_Z, s_sup, s_obj, s_it, s_stat, s_gam;
-  DevBuf d_W;  // deflation: the working copy of A
+  DevBuf d_W, d_list;  // deflation: the working copy of A, the support list of z_j
   struct GraphEntry {
     cudaGraph_t g = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -355,7 +355,7 @@ struct Slot {
     for (const DevBuf* b : {&b_cnorm, &b_P, &b_Y, &b_ypart, &b_T, &b_fpart, &b_gpart, &b_x3, &b_g3, &b_maps,
                             &b_planes, &s_A,
                             &s_scale, &s_x0, &s_X,
-                            &s_Z, &s_sup, &s_obj, &s_it, &s_stat, &s_gam, &d_W})
+                            &s_Z, &s_sup, &s_obj, &s_it, &s_stat, &s_gam, &d_W, &d_list})
       s += b->bytes;
     return s;
   }
@@ -400,7 +400,7 @@ static void release_workspace(Slot* s) {
   for (DevBuf* b : {&s->b_cnorm, &s->b_P, &s->b_Y, &s->b_ypart, &s->b_T, &s->b_fpart, &s->b_gpart, &s->b_x3,
                     &s->b_g3, &s->b_maps, &s->b_planes, &s->s_A,
                     &s->s_scale, &s->s_x0, &s->s_X, &s->s_Z, &s->s_sup, &s->s_obj, &s->s_it, &s->s_stat, &s->s_gam,
-                    &s->d_W})
+                    &s->d_W, &s->d_list})
     release(s, b);
 }
 
@@ -1106,14 +1106,9 @@ int gpspca_solve_deflated(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form f
       scale_dev = static_cast<const float*>(s->s_scale.p);
     }
   }
+  // workspace like the solves' own (kept for the next call, counted against the budget)
   if ((rc = ensure(s, &s->d_W, tcs * static_cast<size_t>(ldw) * n))) return rc;
-  struct WGuard {  // the working copy is as large as A: never kept after the call
-    Slot* s;
-    ~WGuard() {
-      cudaStreamSynchronize(s->stream);
-      release(s, &s->d_W);
-    }
-  } wguard{s};
+  if ((rc = ensure(s, &s->d_list, deflate_list_bytes(wdt, n)))) return rc;
   launch_deflate_copy(r.A.dtype, A_dev, r.A.ld, r.A.dtype == GPSPCA_FP8_E4M3 ? scale_dev : nullptr, s->d_W.p, ldw, p, n,
                       s->stream);
   GP_CUDA(cudaGetLastError());
@@ -1164,7 +1159,7 @@ int gpspca_solve_deflated(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form f
     if (first_err == GPSPCA_OK) first_err = rc;
     // A_j = A_{j-1} - (A_{j-1} z_j) z_j^T (z_j = 0 leaves it unchanged)
     if (j + 1 < m) {
-      launch_deflate(wdt, s->d_W.p, ldw, p, n, rj.out.Z, s->stream);
+      launch_deflate(wdt, s->d_W.p, ldw, p, n, rj.out.Z, s->d_list.p, s->stream);
       GP_CUDA(cudaGetLastError());
     }
   }
