@@ -440,23 +440,37 @@ __device__ __forceinline__ dd shfl_xor_dd(dd v, int off) {
   return dd{__shfl_xor_sync(0xffffffffu, v.hi, off), __shfl_xor_sync(0xffffffffu, v.lo, off)};
 }
 
+// Whether entry t is active: the decision the sweep took for its gradient
+// factor, in the same precision (float compute: float t against float gamma
+// and mu), so that the objective, the loadings and the iterate's g agree on
+// the active set even for t within rounding of the threshold (otherwise an
+// entry could count in f while its g is zero, and an all-zero g with f > 0
+// would look like a degenerate step).
+__device__ __forceinline__ bool active_entry(int form, float t, double gam, double mu) {
+  return grad_factor<float>(form, t, static_cast<float>(gam), static_cast<float>(mu)) != 0.0f;
+}
+__device__ __forceinline__ bool active_entry(int form, double t, double gam, double mu) {
+  return grad_factor<double>(form, t, gam, mu) != 0.0;
+}
+
 // Table 1 summand and squared unnormalised loading of one entry t: the rule
-// of threshold(), for float t evaluated in double-float against the double
-// gamma and mu given as dd (no double arithmetic), for double t in double.
-__device__ __forceinline__ void objective_terms(int form, float t, double, double, dd gam, dd mu, dd* term,
-                                                dd* z2) {
+// of threshold() on the active set of active_entry(), for float t evaluated
+// in double-float against the double gamma and mu given as dd (no double
+// arithmetic), for double t in double.  An active entry whose value rounds
+// to the threshold contributes zero.
+__device__ __forceinline__ void objective_terms(int form, float t, double gam_x, double mu_x, dd gam, dd mu,
+                                                dd* term, dd* z2) {
+  const bool act = active_entry(form, t, gam_x, mu_x);
   if ((form & 1) == 0) {  // L1: s = [mu |t| - gamma]_+, term = s^2 = z^2
     const dd s = dd_sub(dd_mul_f(mu, fabsf(t)), gam);
     const dd sq = dd_mul(s, s);
-    const bool act = s.hi > 0.0f;
-    *term = act ? sq : dd{0.0f, 0.0f};
+    *term = (act && s.hi > 0.0f) ? sq : dd{0.0f, 0.0f};
     *z2 = *term;
   } else {  // L0: u = mu t, active when u^2 > gamma: term = u^2 - gamma, z = u
     const dd u = dd_mul_f(mu, t);
     const dd u2 = dd_mul(u, u);
     const dd d = dd_sub(u2, gam);
-    const bool act = d.hi > 0.0f;
-    *term = act ? d : dd{0.0f, 0.0f};
+    *term = (act && d.hi > 0.0f) ? d : dd{0.0f, 0.0f};
     *z2 = act ? u2 : dd{0.0f, 0.0f};
   }
 }
@@ -750,8 +764,11 @@ __global__ void finalize_kernel(const IO* io, const State* st, int p, int n, int
   const TC* T = static_cast<const TC*>(io->T);
   TC z = 0;
   if (i < n && it > 0) {
-    const Thr th = threshold(form, static_cast<double>(T[static_cast<int64_t>(j) * n + i]), gam, mu);
-    z = static_cast<TC>(th.zr * inv);
+    const TC t = T[static_cast<int64_t>(j) * n + i];
+    if (active_entry(form, t, gam, mu)) {  // the active set of the objective and of g
+      const Thr th = threshold(form, static_cast<double>(t), gam, mu);
+      z = static_cast<TC>(th.zr * inv);
+    }
   }
   if (i < n) static_cast<TC*>(io->Z)[static_cast<int64_t>(j) * n + i] = z;
   const unsigned bits = __ballot_sync(0xffffffffu, i < n && z != TC(0));
