@@ -203,8 +203,9 @@ def run_gpu(args):
     ms, total_sweeps_all = reduce_over_ranks(ms, total_sweeps, "cuda")
     value = total_sweeps_all / (ms / 1e3)
 
-    # end to end through the C ABI with host (pinned) buffers: A copied in and
-    # every result copied out inside the timed region, each solve
+    # end to end through the C ABI with host (pinned) buffers: A copied in
+    # (once per step: the batch stages a host matrix its requests share) and
+    # every result copied out inside the timed region
     for _ in range(1):
         step(host=True)
     torch.cuda.synchronize()
@@ -218,7 +219,7 @@ def run_gpu(args):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
-    h2d = len(CASES) * P * N * 4
+    h2d = P * N * 4  # the six requests share the host matrix: the batch copies it once
     d2h = sum((P + N) * 4 * (1 if mu is None else len(mu)) + ((N + 31) // 32) * 4 * (1 if mu is None else len(mu))
               + 24 * (1 if mu is None else len(mu)) for _, mu in CASES)
 
@@ -246,15 +247,17 @@ def run_gpu(args):
         "config": {"workload": WORKLOAD, "p": P, "n": N, "solves_per_step": len(CASES),
                    "sweeps_per_step": round(total_sweeps / args.steps, 2),
                    "l2": "inputs larger than L2 (A is 400 MB)", "parallelism": "replicas" if ws > 1 else "1 gpu"},
-        "roofline": {"bound": "hbm", "kernel": "sweep_kernel<float,1,*> (single-unit fused sweep)",
-                     "achieved": round(ach_su, 1), "peak": peak, "unit": "GB/s", "frac": round(ach_su / peak, 4),
-                     "peak_source": peak_kind, "traffic": TRAFFIC_SL1, "ms_per_launch": round(ms_su, 5),
+        # the dominant kernel of the step by launch time (about 58%): the
+        # block m = 5 sweep; the single-unit sweep beside it
+        "roofline": {"bound": "hbm", "kernel": "sweep_kernel<float,5,2> (block m=5 fused sweep)",
+                     "achieved": round(ach_blk, 1), "peak": peak, "unit": "GB/s", "frac": round(ach_blk / peak, 4),
+                     "peak_source": peak_kind, "traffic": TRAFFIC_BL1, "ms_per_launch": round(ms_blk, 5),
                      "algorithmic_bytes_per_launch": bytes_a,
                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch"},
-        "roofline_block": {"bound": "hbm", "kernel": "sweep_kernel<float,5,*> (block m=5 fused sweep)",
-                           "achieved": round(ach_blk, 1), "peak": peak, "unit": "GB/s",
-                           "frac": round(ach_blk / peak, 4), "ms_per_launch": round(ms_blk, 5),
-                           "traffic": TRAFFIC_BL1},
+        "roofline_single_unit": {"bound": "hbm", "kernel": "sweep_kernel<float,1,2> (single-unit fused sweep)",
+                                 "achieved": round(ach_su, 1), "peak": peak, "unit": "GB/s",
+                                 "frac": round(ach_su / peak, 4), "ms_per_launch": round(ms_su, 5),
+                                 "traffic": TRAFFIC_SL1},
         "e2e": {"value": round(e2e_sweeps / (e2e_ms / 1e3), 2), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": total_launches,

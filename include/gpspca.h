@@ -179,7 +179,11 @@ typedef struct {
  * and work enqueued on it afterwards starts after the whole batch.  Returns
  * when every solve has finished; rcs[i] (count entries, caller-owned)
  * receives solve i's result code.  The return value is GPSPCA_OK when every
- * solve returned GPSPCA_OK or GPSPCA_EDEGENERATE, else the first other code. */
+ * solve returned GPSPCA_OK or GPSPCA_EDEGENERATE, else the first other code.
+ * A host matrix shared by several requests of the batch (same data pointer,
+ * dtype, shape, ld and col_scale) is copied to the device once, on the
+ * context's stream before the batch starts, into a buffer the context keeps
+ * (counted against the budget) for later batches. */
 int gpspca_solve_batch(gpspca_ctx* ctx, int32_t count, const gpspca_request* reqs, int32_t* rcs);
 
 /* Several sparse components with a single-unit formulation (form SL1 or

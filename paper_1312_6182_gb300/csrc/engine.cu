@@ -904,6 +904,7 @@ struct gpspca_ctx {
   // batches (gpspca_solve_batch), under solve_mu
   std::vector<std::unique_ptr<Slot>> batch_slots;
   cudaEvent_t batch_start = nullptr;
+  std::vector<DevBuf> batch_stage;  // host matrices shared by several requests, copied once
 };
 
 static constexpr int kServeSlots = 8;
@@ -1036,6 +1037,45 @@ int gpspca_solve_batch(gpspca_ctx* ctx, int32_t count, const gpspca_request* req
     ctx->batch_slots.push_back(std::move(s));
   }
   cudaStream_t cs = ctx->sync_slot.stream;
+  // A host matrix that several requests share (same buffer, type, shape,
+  // stride and scales) is copied to the device once, on the context's stream
+  // before the batch starts, and those requests read the device copy.
+  {
+    size_t nstage = 0;
+    for (int i = 0; i < count; ++i) {
+      const gpspca_matrix& Ai = R[i].A;
+      if (Ai.location != GPSPCA_HOST || Ai.p <= 0 || Ai.n <= 0 || !Ai.data) continue;
+      int users = 0;
+      for (int k = i; k < count; ++k) {
+        const gpspca_matrix& Ak = R[k].A;
+        users += Ak.location == GPSPCA_HOST && Ak.data == Ai.data && Ak.dtype == Ai.dtype && Ak.p == Ai.p &&
+                 Ak.n == Ai.n && Ak.ld == Ai.ld && Ak.col_scale == Ai.col_scale;
+      }
+      if (users < 2) continue;
+      const gpspca_matrix host = Ai;
+      const size_t a_bytes = static_cast<size_t>(host.ld) * host.n * dinfo(host.dtype).esize;
+      const size_t s_bytes = host.dtype == GPSPCA_FP8_E4M3 ? sizeof(float) * host.n : 0;
+      if (ctx->batch_stage.size() <= nstage) ctx->batch_stage.resize(nstage + 1);
+      DevBuf* buf = &ctx->batch_stage[nstage++];
+      int rc = ensure(&ctx->sync_slot, buf, a_bytes + s_bytes + 256);
+      if (rc != GPSPCA_OK) return rc;
+      GP_CUDA(cudaMemcpyAsync(buf->p, host.data, a_bytes, cudaMemcpyHostToDevice, cs));
+      float* scale = nullptr;
+      if (s_bytes) {
+        scale = reinterpret_cast<float*>(static_cast<char*>(buf->p) + (a_bytes + 255) / 256 * 256);
+        GP_CUDA(cudaMemcpyAsync(scale, host.col_scale, s_bytes, cudaMemcpyHostToDevice, cs));
+      }
+      for (int k = i; k < count; ++k) {
+        gpspca_matrix& Ak = R[k].A;
+        if (Ak.location == GPSPCA_HOST && Ak.data == host.data && Ak.dtype == host.dtype && Ak.p == host.p &&
+            Ak.n == host.n && Ak.ld == host.ld && Ak.col_scale == host.col_scale) {
+          Ak.location = GPSPCA_DEVICE;
+          Ak.data = buf->p;
+          Ak.col_scale = scale;
+        }
+      }
+    }
+  }
   GP_CUDA(cudaEventRecord(ctx->batch_start, cs));
   std::vector<char> running(static_cast<size_t>(count), 0);
   auto collect = [&](int i) {
@@ -1284,6 +1324,7 @@ int gpspca_destroy(gpspca_ctx* ctx) {
   for (auto& s : ctx->serve_slots) slot_free(s.get());
   for (auto& s : ctx->batch_slots) slot_free(s.get());
   if (ctx->batch_start) cudaEventDestroy(ctx->batch_start);
+  for (DevBuf& b : ctx->batch_stage) release(&ctx->sync_slot, &b);
   slot_free(&ctx->sync_slot);
   delete ctx;
   return GPSPCA_OK;

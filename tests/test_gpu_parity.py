@@ -480,6 +480,29 @@ def test_batch_equals_solo_solves(ctx):
         ctx.solve_batch([dict(At=items[0]["At"], form="SL1", gamma=[-1.0])])
 
 
+def test_batch_shares_host_matrix(ctx):
+    """Requests of a batch that share one pinned host matrix (the library copies
+    it once) give the device batch's bits, with host or device outputs, for
+    float and fp8 (host scales) storage."""
+    At = synth.planted_spike(900, 3100, 3, [30.0, 20.0, 12.0], support_frac=0.05, seed=31, dtype=np.float32)
+    s = np.abs(At).max(axis=1).astype(np.float32) / 448.0
+    q = torch.from_numpy(At / s[:, None]).to(torch.float8_e4m3fn)
+    for hA, hs in ((torch.from_numpy(At).pin_memory(), None), (q.pin_memory(), torch.from_numpy(s).pin_memory())):
+        cases = [("SL1", None), ("BL0", [1.0] * 3), ("SL0", None), ("BL1", [1.0, 0.9, 0.8])]
+        dev_items, host_items = [], []
+        for k, (form, mu) in enumerate(cases):
+            m = 1 if mu is None else 3
+            common = dict(form=form, gamma=[0.05] * m, mu=mu, gamma_relative=True)
+            dev_items.append(dict(At=hA.cuda(), col_scale=None if hs is None else hs.cuda(), **common))
+            out = binding.alloc_result(m, 900, 3100, "cpu", torch.float32, pin=True) if k % 2 else None
+            host_items.append(dict(At=hA, col_scale=hs, out=out, **common))
+        dev = ctx.solve_batch(dev_items)
+        host = ctx.solve_batch(host_items)
+        for a, b in zip(dev, host):
+            assert torch.equal(a.Z.cpu(), b.Z.cpu()) and torch.equal(a.X.cpu(), b.X.cpu())
+            assert torch.equal(a.objective.cpu(), b.objective.cpu()) and torch.equal(a.iters.cpu(), b.iters.cpu())
+
+
 def test_submitted_requests_equal_solo_solves(ctx):
     """Requests of different shapes and formulations submitted together (and so
     overlapping on the device) give the bit-identical results of solo solves."""
