@@ -27,3 +27,4 @@ from .gpower import (  # noqa: F401
     gpower,
 )
 from .deflation import gpower_deflated  # noqa: F401,E402
+from .projection import project  # noqa: F401,E402
