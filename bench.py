@@ -511,6 +511,15 @@ def run_deflation(args):
         iters = [int(v) for v in r.iters.tolist()]
         one = binding.alloc_result(1, p, n, "cuda", torch.float32)
         ms1, r1 = _event_ms(stream, lambda: ctx.solve(dA, form, [0.05], gamma_relative=True, out=one), args.steps)
+        # scores of the 5000 samples on the five loadings (gpspca_project):
+        # reads the support columns only
+        Zc = r.Z.contiguous()
+        Sc = torch.empty((m, p), dtype=torch.float32, device="cuda")
+        ctx.project(dA, Zc, out=Sc)
+        ms_proj, _ = _event_ms(stream, lambda: ctx.project(dA, Zc, out=Sc), args.steps)
+        proj_bytes = int((r.Z != 0).sum().item()) * p * 4
+        res[form + "_projection"] = {"ms": round(ms_proj, 4), "bytes_read": proj_bytes,
+                                     "GB/s": round(proj_bytes / (ms_proj / 1e3) / 1e9, 1)}
         res[form] = {"iters_per_s": round(sum(iters) / (ms / 1e3), 1), "ms_per_extraction": round(ms, 3),
                      "iters": iters, "status": [int(v) for v in r.status.tolist()],
                      "support_sizes": [int(v) for v in (r.Z != 0).sum(dim=1).tolist()],

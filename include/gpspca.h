@@ -210,6 +210,20 @@ int gpspca_solve_batch(gpspca_ctx* ctx, int32_t count, const gpspca_request* req
 int gpspca_solve_deflated(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form, const double* gamma, int32_t m,
                           double tol, int32_t maxit, uint32_t flags, gpspca_out* out);
 
+/* Scores of samples on sparse loadings: S = B Z.  The paper maps every
+ * sample (training and test) into the subspace of the learned components
+ * before classifying (Section 4.2); with the loadings Z of a solve (n x m,
+ * column-major, ld n) and samples B (q x n: q samples of the same n
+ * variables, column-major like A, any storage type; fp8 with its column
+ * scales), S (q x m, column-major, ld q) gets column j = sum_i Z[i, j] b_i.
+ * Only the columns of B in the support of each loading are read, so the cost
+ * is q * |supp z_j| elements per component.  Z and S are double for F64
+ * storage and float otherwise; sums in double-float (double for F64).
+ * B, Z and S are all in B's location (device, or host: copied by the
+ * library).  Returns when S is written.  GPSPCA_EINVAL for m outside
+ * [1, GPSPCA_MAX_M], NULL pointers or a bad shape. */
+int gpspca_project(gpspca_ctx* ctx, const gpspca_matrix* B, const void* Z, int32_t m, void* S);
+
 /* Asynchronous form of gpspca_solve for many concurrent requests.  The
  * request is queued; a scheduler thread admits it when its workspace fits the
  * budget next to the solves already running, and advances every admitted

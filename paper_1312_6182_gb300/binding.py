@@ -39,7 +39,7 @@ ERROR_NAMES = {
 
 EXPORTED = ("gpspca_create", "gpspca_solve", "gpspca_submit", "gpspca_poll", "gpspca_destroy",
             "gpspca_last_error", "gpspca_time_sweep", "gpspca_sweep_static", "gpspca_synth_spikes",
-            "gpspca_solve_batch", "gpspca_solve_deflated")
+            "gpspca_solve_batch", "gpspca_solve_deflated", "gpspca_project")
 
 
 class Matrix(ctypes.Structure):
@@ -103,6 +103,8 @@ def load(path: str = LIB_PATH):
     lib.gpspca_solve_deflated.argtypes = [P, ctypes.POINTER(Matrix), ctypes.c_int, D, ctypes.c_int32,
                                           ctypes.c_double, ctypes.c_int32, ctypes.c_uint32, ctypes.POINTER(Out)]
     lib.gpspca_solve_deflated.restype = ctypes.c_int
+    lib.gpspca_project.argtypes = [P, ctypes.POINTER(Matrix), P, ctypes.c_int32, P]
+    lib.gpspca_project.restype = ctypes.c_int
     lib.gpspca_submit.argtypes = [P, ctypes.POINTER(Matrix), ctypes.c_int, D, ctypes.c_int32, D, ctypes.c_double,
                                   ctypes.c_int32, ctypes.c_uint32, ctypes.POINTER(Out),
                                   ctypes.POINTER(ctypes.c_uint64)]
@@ -311,6 +313,25 @@ class Context:
                                             | (EAGER if eager else 0), ctypes.byref(o))
         _check(rc, (OK, EDEGENERATE))
         out.rc = rc
+        return out
+
+    def project(self, Bt, Z, col_scale=None, p: Optional[int] = None, out=None):
+        """Scores S = B Z (gpspca_project).  Bt: (q, ld) tensor holding B
+        column-major like At; Z: (m, n) tensor, row j = loading j (a solve's
+        Result.Z); returns (m, q), row j = column j of S, in Z's device."""
+        import torch
+
+        M = matrix(Bt, p, col_scale)
+        m = int(Z.shape[0])
+        tc = torch.float64 if Bt.dtype == torch.float64 else torch.float32
+        if Z.dtype != tc or not Z.is_contiguous() or Z.shape[1] != M.n:
+            raise ValueError(f"Z must be a contiguous ({m}, {int(M.n)}) {tc} tensor")
+        if (Z.device.type == "cuda") != (M.location == DEVICE):
+            raise ValueError("Z must be in the same location as B")
+        if out is None:
+            out = torch.empty((m, int(M.p)), dtype=tc, device=Z.device)
+        self._sync_torch(Bt, Z, out)
+        _check(self.lib.gpspca_project(self.ptr, ctypes.byref(M), Z.data_ptr(), m, out.data_ptr()), (OK,))
         return out
 
     def solve_batch(self, items, allow_degenerate: bool = True):

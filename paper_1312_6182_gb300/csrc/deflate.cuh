@@ -20,4 +20,13 @@ size_t deflate_list_bytes(int dtype, int64_t n);
 void launch_deflate(int dtype, void* W, int64_t ldw, int64_t p, int64_t n, const void* z, void* list,
                     cudaStream_t s);
 
+// S[:, j] = B z_j for j < m: B (q x n, column-major, ld; dtype as the
+// matrix descriptor, fp8 with its column scales), Z (n x m, ld n) and S
+// (q x m, ld q) in the working type (double for GPSPCA_F64, float
+// otherwise), all device memory; reads only the support columns of each z_j.
+// list: m * deflate_list_bytes(dtype, n) of device scratch (one support
+// list per column).
+void launch_project(int dtype, const void* B, int64_t ld, const float* scale, int64_t q, int64_t n, const void* Z,
+                    int m, void* S, void* list, cudaStream_t s);
+
 }  // namespace gpspca

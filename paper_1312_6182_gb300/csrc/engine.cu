@@ -1219,6 +1219,64 @@ int gpspca_solve_deflated(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form f
   return GPSPCA_OK;
 }
 
+int gpspca_project(gpspca_ctx* ctx, const gpspca_matrix* B, const void* Z, int32_t m, void* S) {
+  if (!ctx || !B || !Z || !S) return fail(GPSPCA_EINVAL, "ctx, B, Z and S must not be NULL");
+  if (m < 1 || m > kMaxM) return fail(GPSPCA_EINVAL, "m = %d outside [1, %d]", m, kMaxM);
+  if (B->dtype < GPSPCA_F32 || B->dtype > GPSPCA_F64) return fail(GPSPCA_EINVAL, "unknown dtype %d", (int)B->dtype);
+  if (B->location != GPSPCA_DEVICE && B->location != GPSPCA_HOST) return fail(GPSPCA_EINVAL, "bad B location");
+  const int64_t q = B->p, n = B->n;
+  if (q < 0 || n < 0 || q > (1 << 30) || n > (1 << 30)) return fail(GPSPCA_EINVAL, "bad shape");
+  if (q > 0 && n > 0) {
+    if (!B->data) return fail(GPSPCA_EINVAL, "B.data is NULL");
+    if (B->ld < q) return fail(GPSPCA_EINVAL, "ld (%lld) < rows (%lld)", (long long)B->ld, (long long)q);
+    if (B->dtype == GPSPCA_FP8_E4M3 && !B->col_scale) return fail(GPSPCA_EINVAL, "FP8 storage needs col_scale");
+  }
+  std::lock_guard<std::mutex> lk(ctx->solve_mu);
+  GP_CUDA(cudaSetDevice(ctx->device));
+  Slot* s = &ctx->sync_slot;
+  const int wdt = B->dtype == GPSPCA_F64 ? GPSPCA_F64 : GPSPCA_F32;
+  const size_t tcs = wdt == GPSPCA_F64 ? sizeof(double) : sizeof(float);
+  const bool host = B->location == GPSPCA_HOST;
+  if (q == 0) return GPSPCA_OK;
+  if (n == 0) {  // no variables: every score is zero
+    if (host) {
+      std::memset(S, 0, tcs * q * m);
+      return GPSPCA_OK;
+    }
+    GP_CUDA(cudaMemsetAsync(S, 0, tcs * q * m, s->stream));
+    GP_CUDA(cudaStreamSynchronize(s->stream));
+    return GPSPCA_OK;
+  }
+  int rc;
+  const void* Bd = B->data;
+  const float* scale = B->col_scale;
+  const void* Zd = Z;
+  void* Sd = S;
+  if (host) {
+    const size_t b_bytes = static_cast<size_t>(B->ld) * n * dinfo(B->dtype).esize;
+    if ((rc = ensure(s, &s->s_A, b_bytes))) return rc;
+    GP_CUDA(cudaMemcpyAsync(s->s_A.p, B->data, b_bytes, cudaMemcpyHostToDevice, s->stream));
+    Bd = s->s_A.p;
+    if (B->dtype == GPSPCA_FP8_E4M3) {
+      if ((rc = ensure(s, &s->s_scale, sizeof(float) * n))) return rc;
+      GP_CUDA(cudaMemcpyAsync(s->s_scale.p, B->col_scale, sizeof(float) * n, cudaMemcpyHostToDevice, s->stream));
+      scale = static_cast<const float*>(s->s_scale.p);
+    }
+    if ((rc = ensure(s, &s->s_Z, tcs * n * m))) return rc;
+    GP_CUDA(cudaMemcpyAsync(s->s_Z.p, Z, tcs * n * m, cudaMemcpyHostToDevice, s->stream));
+    Zd = s->s_Z.p;
+    if ((rc = ensure(s, &s->s_X, tcs * q * m))) return rc;
+    Sd = s->s_X.p;
+  }
+  if ((rc = ensure(s, &s->d_list, deflate_list_bytes(wdt, n) * m))) return rc;
+  launch_project(B->dtype, Bd, B->ld, B->dtype == GPSPCA_FP8_E4M3 ? scale : nullptr, q, n, Zd, m, Sd, s->d_list.p,
+                 s->stream);
+  GP_CUDA(cudaGetLastError());
+  if (host) GP_CUDA(cudaMemcpyAsync(S, Sd, tcs * q * m, cudaMemcpyDeviceToHost, s->stream));
+  GP_CUDA(cudaStreamSynchronize(s->stream));
+  return GPSPCA_OK;
+}
+
 int gpspca_time_sweep(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form, const double* gamma, int32_t m,
                       const double* mu, uint32_t flags, int32_t reps, double* ms_per_sweep) {
   if (!ctx || !ms_per_sweep) return fail(GPSPCA_EINVAL, "ctx and ms_per_sweep must not be NULL");
