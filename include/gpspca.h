@@ -225,10 +225,11 @@ int gpspca_solve_deflated(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form f
 int gpspca_project(gpspca_ctx* ctx, const gpspca_matrix* B, const void* Z, int32_t m, void* S);
 
 /* Asynchronous form of gpspca_solve for many concurrent requests.  The
- * request is queued; a scheduler thread admits it when its workspace fits the
- * budget next to the solves already running, and advances every admitted
- * solve one sweep per scheduling tick, so requests that arrive while others
- * run join them on the device.  Same arguments and ownership as gpspca_solve
+ * request is queued; a scheduler thread admits it into one of 8 slots (each
+ * with its own stream and workspace) when its workspace fits the budget next
+ * to the solves already running, and launches it there as a whole solve (the
+ * cached CUDA graph of its geometry), so requests that arrive while others
+ * run overlap with them on the device.  Same arguments and ownership as gpspca_solve
  * (A and out must be in device memory); *ticket receives the request id. */
 int gpspca_submit(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form, const double* gamma, int32_t m,
                   const double* mu, double tol, int32_t maxit, uint32_t flags, gpspca_out* out,
