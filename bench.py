@@ -33,8 +33,8 @@ RHO32 = 0.01
 # dram bytes (read + write) of one launch of the fused sweeps on this matrix,
 # from an ncu capture of the current kernels (dram__bytes_read.sum +
 # dram__bytes_write.sum)
-TRAFFIC_SL1 = 403.20e6
-TRAFFIC_BL1 = 403.93e6
+TRAFFIC_SL1 = 403.40e6
+TRAFFIC_BL1 = 404.11e6
 METRIC = "GPower iters/s"
 UNIT = "iters/s"
 WORKLOAD = "planted spikes 5000x20000 fp32 (5 spikes, theta_j=40/j, 5% supports), SL1+SL0+BL1+BL0 (m=5, mu=1 and mu=[1,.9,.8,.7,.6]), gamma=0.05*max||a_i||, tol 1e-6"
