@@ -170,11 +170,12 @@ def test_tensor_core_gamma_path_64(ctx, form):
 
 
 @pytest.mark.parametrize("form", ["BL1", "SL0"])
-def test_tensor_core_sweep_fp8_storage(ctx, form):
+@pytest.mark.parametrize("p", [1200, 1204])  # aligned and unaligned column strides
+def test_tensor_core_sweep_fp8_storage(ctx, form, p):
     """FP8 E4M3 storage with per-column scales and 16 components / gamma
     values: the tensor cores read the fp8 values as bf16 (exact) and the
     scales enter the threshold; oracle on the dequantised matrix."""
-    At = synth.planted_spike(1200, 5000, 16, [100.0 / np.sqrt(j) for j in range(1, 17)], support_frac=0.01, seed=13,
+    At = synth.planted_spike(p, 5000, 16, [100.0 / np.sqrt(j) for j in range(1, 17)], support_frac=0.01, seed=13,
                              dtype=np.float32)
     q, sc, deq = _fp8(At)
     A = deq.astype(np.float64).T
