@@ -481,6 +481,32 @@ __device__ __forceinline__ void objective_terms(int form, double t, double gam, 
   *z2 = dd_from_double(th.zr * th.zr);
 }
 
+// The per-cluster partials of rows `row` of Y columns j0 .. j0+NJ-1 (those
+// below m), splits g, g + G, g + 2G, ... (G = kReduceGroups) added in that
+// order into s; the loads of KS splits x NJ columns are issued before any of
+// their adds (the partials' latency, not their bytes, bounds small solves).
+template <typename TC, int NJ, int KS, int JY>
+__device__ __forceinline__ void sum_split_partials(const TC* __restrict__ yp, int nsplit, int64_t stride, int p,
+                                                   int row, int g, int j0, int m, YAcc<TC> (&s)[JY]) {
+  for (int sp0 = g; sp0 < nsplit; sp0 += KS * kReduceGroups) {
+    TC v[KS][NJ];
+#pragma unroll
+    for (int k = 0; k < KS; ++k) {
+      const int sp = sp0 + k * kReduceGroups;
+#pragma unroll
+      for (int u = 0; u < NJ; ++u) {
+        const int j = j0 + u;
+        v[k][u] = (sp < nsplit && j < m) ? yp[sp * stride + static_cast<int64_t>(j) * p + row] : TC(0);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < KS; ++k)
+#pragma unroll
+      for (int u = 0; u < NJ; ++u)
+        if (sp0 + k * kReduceGroups < nsplit) s[u].add(v[k][u]);
+  }
+}
+
 // One reduction launch after a sweep.  Blocks [0, nyb): Y = sum of the
 // per-cluster partials (fixed order) for kReduceRows rows, and those rows'
 // contribution to the Gram matrix Y^T Y (packed j <= l, or the diagonal), in
@@ -555,23 +581,10 @@ __global__ void __launch_bounds__(kReduceRows* kReduceGroups) reduce_kernel(cons
   for (int j0 = 0; j0 < m; j0 += JY) {
     YAcc<TC> s[JY];
     if (row < p) {
-      // loads of JY columns x 2 splits issued before any of their adds
-      for (int sp = g; sp < a.nsplit; sp += 2 * kReduceGroups) {
-        const bool two = sp + kReduceGroups < a.nsplit;
-        TC v0[JY], v1[JY];
-#pragma unroll
-        for (int u = 0; u < JY; ++u) {
-          const int j = min(j0 + u, m - 1);
-          const TC* src = yp + static_cast<int64_t>(j) * p + row;
-          v0[u] = src[sp * stride];
-          v1[u] = two ? src[(sp + kReduceGroups) * stride] : TC(0);
-        }
-#pragma unroll
-        for (int u = 0; u < JY; ++u) {
-          s[u].add(v0[u]);
-          if (two) s[u].add(v1[u]);
-        }
-      }
+      if (m == 1)
+        sum_split_partials<TC, 1, 8>(yp, a.nsplit, stride, p, row, g, j0, m, s);
+      else
+        sum_split_partials<TC, JY, 2>(yp, a.nsplit, stride, p, row, g, j0, m, s);
     }
 #pragma unroll
     for (int u = 0; u < JY; ++u) part[g][u][rl] = s[u];
