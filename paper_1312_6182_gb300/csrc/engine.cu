@@ -39,6 +39,10 @@ const void* sweep_kernel_f32(int mg, int nch);
 const void* sweep_kernel_f64(int mg, int nch);
 const void* sweep_kernel_bf16(int mg, int nch);
 const void* sweep_kernel_fp8(int mg, int nch);
+const void* sweep_kernel_f32_nrm(int mg, int nch);
+const void* sweep_kernel_f64_nrm(int mg, int nch);
+const void* sweep_kernel_bf16_nrm(int mg, int nch);
+const void* sweep_kernel_fp8_nrm(int mg, int nch);
 
 // ---------------------------------------------------------------- errors
 
@@ -76,12 +80,13 @@ static DInfo dinfo(int dt) {
   }
 }
 
-static const void* sweep_ptr(int dt, int mg, int nch) {
+// nrm: the variant that also forms the column norms
+static const void* sweep_ptr(int dt, int mg, int nch, bool nrm = false) {
   switch (dt) {
-    case GPSPCA_F32: return sweep_kernel_f32(mg, nch);
-    case GPSPCA_F64: return sweep_kernel_f64(mg, nch);
-    case GPSPCA_BF16: return sweep_kernel_bf16(mg, nch);
-    default: return sweep_kernel_fp8(mg, nch);
+    case GPSPCA_F32: return nrm ? sweep_kernel_f32_nrm(mg, nch) : sweep_kernel_f32(mg, nch);
+    case GPSPCA_F64: return nrm ? sweep_kernel_f64_nrm(mg, nch) : sweep_kernel_f64(mg, nch);
+    case GPSPCA_BF16: return nrm ? sweep_kernel_bf16_nrm(mg, nch) : sweep_kernel_bf16(mg, nch);
+    default: return nrm ? sweep_kernel_fp8_nrm(mg, nch) : sweep_kernel_fp8(mg, nch);
   }
 }
 
@@ -144,11 +149,11 @@ static std::vector<std::pair<int, int>> split_components(int m, int gmax) {
 
 // Pick threads / rows per thread / tile width / stages for one pass with
 // cluster size C.  Returns false if this C does not fit.
-static bool fit_pass(int dt, int mg, int C, int ps, int m, Pass* out) {
+static bool fit_pass(int dt, int mg, int C, int ps, int m, Pass* out, bool nrm = false) {
   const DInfo d = dinfo(dt);
   static const int kNch[] = {1, 2, 3, 4};
   for (int nch : kNch) {
-    const void* k = sweep_ptr(dt, mg, nch);
+    const void* k = sweep_ptr(dt, mg, nch, nrm);
     if (!k) continue;
     const KAttr at = kattr(k);
     if (!at.ok || at.local > 0) continue;  // spilling variants are not used
@@ -156,7 +161,7 @@ static bool fit_pass(int dt, int mg, int C, int ps, int m, Pass* out) {
     threads = std::max(64, (threads + 31) / 32 * 32);
     if (threads > at.max_threads) continue;
     const int colbytes = ps * d.esize;
-    const int wb = sweep_kb(mg) / mg;  // the kernel's tile width limit
+    const int wb = sweep_kb(mg) / (mg + (nrm ? 1 : 0));  // the kernel's tile width limit
     const int nw = threads / 32;
     const SweepSmem base = sweep_smem_layout(0, 0, ps, d.esize, d.tcsize, nw, m, mg);
     const int room = kSmemBudget - base.total;
@@ -288,6 +293,17 @@ int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fa
     if (cudaOccupancyMaxActiveClusters(&nc, q.k, &cfg) == cudaSuccess && nc > 0) ncl = std::min(ncl, nc);
   }
   if (!pl.tc) ncl = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ncl, n)));
+  // block forms on the CUDA cores: the start's first power step reads A and
+  // can form the column norms too (no pass of their own)
+  if (!pl.tc && form >= 2 && !pl.passes.empty()) {
+    Pass q;
+    if (fit_pass(dt, pl.passes[0].mg, pl.C, pl.ps, m, &q, true)) {
+      q.j0 = pl.passes[0].j0;
+      q.mgv = pl.passes[0].mgv;
+      pl.norm_pass = q;
+      pl.norms_in_sweep = 1;
+    }
+  }
   pl.ncl = ncl;
   pl.cols_per_cl = static_cast<int>((n + ncl - 1) / ncl);
   pl.nred = static_cast<int>((p + kReduceRows - 1) / kReduceRows);
@@ -456,7 +472,7 @@ static void slot_free(Slot* s) {
 
 // ---------------------------------------------------------------- graph
 
-static cudaError_t launch_sweeps(const Plan& pl, Slot* s, cudaStream_t cs, int sketch = 0);
+static cudaError_t launch_sweeps(const Plan& pl, Slot* s, cudaStream_t cs, int sketch = 0, int norms = 0);
 
 // Start of the solve: norms, gamma, the start directions and their
 // projection.  Block forms without a caller start then take kPowerSteps
@@ -466,9 +482,14 @@ static cudaError_t launch_prologue(const Plan& pl, Slot* s, cudaStream_t cs, cud
   if (pl.tc && pl.tc_convert)  // bf16 planes of a float / fp8 A for the tensor cores
     launch_tc_convert(pl.dtype, s->io_dev, pl.p, pl.n, pl.ld, pl.p_pad, cs);
   launch_reset(s->io_dev, s->st_dev, pl.m, pl.form, cs);
-  launch_colnorm(pl.dtype, s->io_dev, s->st_dev, pl.ld, pl.p, pl.n, pl.fast, cs);
+  // the block start's first power step forms the column norms itself; the
+  // start selection (gamma scale, non-finite check) then follows that step
+  const bool late_norms = pca && pl.norms_in_sweep;
   StartArgs sa{s->io_dev, s->st_dev, pl.ld, pl.p, pl.n, pl.m, pl.form};
-  launch_select_start(pl.dtype, sa, cs);
+  if (!late_norms) {
+    launch_colnorm(pl.dtype, s->io_dev, s->st_dev, pl.ld, pl.p, pl.n, pl.fast, cs);
+    launch_select_start(pl.dtype, sa, cs);
+  }
   launch_gather_start(pl.dtype, sa, cs);
   const int gram_pairs = pl.full_gram ? pl.m * (pl.m + 1) / 2 : pl.m;
   ReduceArgs ra{s->io_dev, s->st_dev, 1, pl.m, pl.p, pl.full_gram, gram_pairs, 1, 0, 0, pl.n, pl.form, pl.nred, 0};
@@ -479,11 +500,12 @@ static cudaError_t launch_prologue(const Plan& pl, Slot* s, cudaStream_t cs, cud
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !pca) return e;
   for (int step = 0; step < kPowerSteps; ++step) {
-    if ((e = launch_sweeps(pl, s, cs, 1)) != cudaSuccess) return e;
+    if ((e = launch_sweeps(pl, s, cs, 1, late_norms && step == 0)) != cudaSuccess) return e;
     ReduceArgs rp{s->io_dev, s->st_dev, pl.ncl, pl.m, pl.p, 1, gram_pairs, 0, 0, 0, pl.n, pl.form, pl.nred, 0};
     launch_reduce(pl.tcsize, rp, cs);
     FinishArgs fp{s->io_dev, s->st_dev, pl.ncl, pl.nred, gram_pairs, pl.m, pl.form, kFinishPolar, 0, h, use_cond};
     launch_finish(fp, pl.finish_smem, cs);
+    if (late_norms && step == 0) launch_select_start(pl.dtype, sa, cs);
   }
   if ((e = launch_sweeps(pl, s, cs, 1)) != cudaSuccess) return e;
   ReduceArgs rc{s->io_dev, s->st_dev, pl.ncl, pl.m, pl.p, 1, pl.m * pl.m, 0, 1, 0, pl.n, pl.form, pl.nred, 0};
@@ -493,7 +515,7 @@ static cudaError_t launch_prologue(const Plan& pl, Slot* s, cudaStream_t cs, cud
   return cudaGetLastError();
 }
 
-static cudaError_t launch_sweeps(const Plan& pl, Slot* s, cudaStream_t cs, int sketch) {
+static cudaError_t launch_sweeps(const Plan& pl, Slot* s, cudaStream_t cs, int sketch, int norms) {
   if (pl.tc) {
     TcArgs a{s->io_dev,  s->st_dev, pl.p,     pl.n,       pl.m,        pl.mpad,     pl.form,
              sketch,     pl.tc_na,  pl.tc_fused, pl.dtype == GPSPCA_FP8_E4M3 ? 1 : 0, pl.p_pad, pl.n_pad,
@@ -501,7 +523,8 @@ static cudaError_t launch_sweeps(const Plan& pl, Slot* s, cudaStream_t cs, int s
     launch_tc_sweep(a, pl.npad, cs);
     return cudaGetLastError();
   }
-  for (const Pass& q : pl.passes) {
+  for (size_t pi = 0; pi < pl.passes.size(); ++pi) {
+    const Pass& q = (norms && pi == 0) ? pl.norm_pass : pl.passes[pi];
     SweepArgs a{s->io_dev, s->st_dev, pl.ld, pl.p, pl.n, pl.m, pl.form, q.j0, q.mgv, pl.ps, q.W, q.S,
                 pl.cols_per_cl, pl.fast, sketch};
     cudaLaunchConfig_t cfg = {};

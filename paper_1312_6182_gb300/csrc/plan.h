@@ -22,6 +22,10 @@ struct Plan {
   int pca = 0;  // block start by power steps + Rayleigh-Ritz (no caller x0)
   int C = 1, ps = 0, ncl = 0, cols_per_cl = 0;
   std::vector<Pass> passes;
+  // block start: the first power step's pass with the column norms (its
+  // first pass of components; the others as in `passes`)
+  Pass norm_pass{};
+  int norms_in_sweep = 0;
   int nred = 0, nobj = 0, npairs = 0, full_gram = 0;
   int finish_smem = 0;
   int tcsize = 4, esize = 4;
@@ -45,6 +49,10 @@ struct Plan {
     }
     for (const Pass& q : passes) {
       snprintf(b, sizeof(b), "|%d,%d,%d,%d,%d,%d,%d", q.j0, q.mgv, q.mg, q.nch, q.threads, q.W, q.S);
+      s += b;
+    }
+    if (norms_in_sweep) {
+      snprintf(b, sizeof(b), "|n%d,%d,%d,%d", norm_pass.nch, norm_pass.threads, norm_pass.W, norm_pass.S);
       s += b;
     }
     return s;

@@ -220,13 +220,17 @@ __host__ __device__ inline SweepSmem sweep_smem_layout(int W, int S, int ps, int
 // function.
 __host__ __device__ constexpr int sweep_kb(int mg) { return mg == 1 ? 8 : 32; }
 
-template <typename TA, int MG, int NCH>
+// NRM: the sweep also forms each column's squared norm (one more reduction
+// slot per column), for the block start's first power step, which reads A
+// anyway: the column norms then need no pass of their own.
+template <typename TA, int MG, int NCH, bool NRM = false>
 struct SweepCfg {
   using TC = typename Elem<TA>::TC;
   static constexpr int VEC = Elem<TA>::VEC;
   static constexpr int R = NCH * VEC;
   static constexpr int KB = sweep_kb(MG);
-  static constexpr int WB = KB / MG;  // most columns one tile can hold
+  static constexpr int SL = MG + (NRM ? 1 : 0);  // reduction slots per column
+  static constexpr int WB = KB / SL;             // most columns one tile can hold
   // registers per thread: x and y tiles, the reduction slots, and a fixed
   // part (addresses, loop state, loads in flight) measured with -Xptxas -v
   static constexpr int REGS = static_cast<int>(sizeof(TC) / 4) * (2 * R * MG + KB + (MG == 1 ? 64 : (MG == 2 ? 60 : 40)));
@@ -239,9 +243,10 @@ struct SweepCfg {
   static constexpr int MAXT = MAXT_RAW >= 1024 ? 1024 : (MAXT_RAW < 128 ? 128 : MAXT_RAW);
 };
 
-template <typename TA, int MG, int NCH>
-__global__ void __launch_bounds__(SweepCfg<TA, MG, NCH>::MAXT, 1) sweep_kernel(const SweepArgs a) {
-  using Cfg = SweepCfg<TA, MG, NCH>;
+template <typename TA, int MG, int NCH, bool NRM = false>
+__global__ void __launch_bounds__(SweepCfg<TA, MG, NCH, NRM>::MAXT, 1) sweep_kernel(const SweepArgs a) {
+  using Cfg = SweepCfg<TA, MG, NCH, NRM>;
+  constexpr int SL = Cfg::SL;
   using TC = typename Cfg::TC;
   constexpr int VEC = Cfg::VEC;
   constexpr int WB = Cfg::WB;
@@ -407,7 +412,7 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH>::MAXT, 1) sweep_kernel(c
   TC* Tout = static_cast<TC*>(io->T);
   const float* cscale = io->col_scale;
   // lane L of every warp owns slot L = (column w = L / MG, component j = L % MG)
-  const int wq = lane / MG, jq = lane % MG;
+  const int wq = lane / SL, jq = lane % SL;
 
   // Tiles run in order: phase A (partial dots, CTA total, push to the
   // cluster peers), then phase B (the peers' totals, threshold, rank update).
@@ -441,9 +446,9 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH>::MAXT, 1) sweep_kernel(c
       for (int w = 0; w < WB; ++w) {
         if (w < wv) {
           const TA* colp = sb + w * ps;
-          uint64_t acc[MG];
+          uint64_t acc[SL];
 #pragma unroll
-          for (int j = 0; j < MG; ++j) acc[j] = 0;
+          for (int j = 0; j < SL; ++j) acc[j] = 0;
 #pragma unroll
           for (int c = 0; c < NCH; ++c) {
             uint64_t a2[2];
@@ -455,11 +460,15 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH>::MAXT, 1) sweep_kernel(c
               acc[j] = ffma2(a2[0], xp[c][0][j], acc[j]);
               acc[j] = ffma2(a2[1], xp[c][1][j], acc[j]);
             }
+            if constexpr (NRM) {  // the column's squared norm
+              acc[MG] = ffma2(a2[0], a2[0], acc[MG]);
+              acc[MG] = ffma2(a2[1], a2[1], acc[MG]);
+            }
           }
 #pragma unroll
-          for (int j = 0; j < MG; ++j) {  // even + odd rows of column w
+          for (int j = 0; j < SL; ++j) {  // even + odd rows of column w
             const float2 f = f2unpack(acc[j]);
-            pd[w * MG + j] = f.x + f.y;
+            pd[w * SL + j] = f.x + f.y;
           }
         }
       }
@@ -476,7 +485,8 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH>::MAXT, 1) sweep_kernel(c
           for (int v = 0; v < VEC; ++v) {
             const TC aval = (vmask & (1u << (c * VEC + v))) ? av[v] : TC(0);
 #pragma unroll
-            for (int j = 0; j < MG; ++j) pd[w * MG + j] += aval * x[c][v][j];
+            for (int j = 0; j < MG; ++j) pd[w * SL + j] += aval * x[c][v][j];
+            if constexpr (NRM) pd[w * SL + MG] += aval * aval;
           }
         }
       }
@@ -511,7 +521,8 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH>::MAXT, 1) sweep_kernel(c
     const TA* sb = stage + buf * stage_elems;
     const int c0 = col_begin + tile * W;
     const int wv = min(W, col_end - c0);
-    const bool mine_valid = lane < WB * MG && wq < wv && jq < a.mg_valid;
+    const bool norm_slot = NRM && jq == MG;  // this lane's slot is a column's squared norm
+    const bool mine_valid = lane < WB * SL && wq < wv && !norm_slot && jq < a.mg_valid;
     if (C > 1) {  // wait for the peers' totals, add all C in rank order
       const int xs = tile % kXSlots;
       TC* slot = xrecv + xs * kMaxCluster * 32;
@@ -527,6 +538,14 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH>::MAXT, 1) sweep_kernel(c
       t *= scl;
       g = grad_factor<TC>(form, t, gam_c[jq], mu_c[jq]) * scl;
     }
+    if constexpr (NRM) {  // ||a_i|| (the column-norm pass's output and its non-finite check)
+      if (norm_slot && warp == 0 && cr == 0 && lane < WB * SL && wq < wv) {
+        double c = sqrt(static_cast<double>(t));
+        if (kFP8) c *= static_cast<double>(cscale[c0 + wq]);
+        if (!isfinite(c)) atomicOr(&st->error, static_cast<int>(kErrNonFinite));
+        io->cnorm[c0 + wq] = c;
+      }
+    }
     // T for the objective (formed by the reduction) and the loadings
     if (warp == 0 && mine_valid && cr == 0 && !sketch && act[jq])
       Tout[static_cast<int64_t>(a.j0 + jq) * n + c0 + wq] = t;
@@ -536,7 +555,7 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH>::MAXT, 1) sweep_kernel(c
       if (w < wv) {
         TC gw[MG];
 #pragma unroll
-        for (int j = 0; j < MG; ++j) gw[j] = __shfl_sync(0xffffffffu, g, w * MG + j);
+        for (int j = 0; j < MG; ++j) gw[j] = __shfl_sync(0xffffffffu, g, w * SL + j);
         const TA* colp = sb + w * ps;
         if constexpr (kPair) {
           uint64_t g2[MG];
@@ -598,10 +617,10 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH>::MAXT, 1) sweep_kernel(c
   if (C > 1) cluster_sync_all();  // no CTA leaves while a peer may read its shared memory
 }
 
-template <typename TA, int MG, int NCH>
+template <typename TA, int MG, int NCH, bool NRM = false>
 const void* sweep_kernel_ptr() {
-  if constexpr (SweepCfg<TA, MG, NCH>::kBuilt) {
-    return reinterpret_cast<const void*>(&sweep_kernel<TA, MG, NCH>);
+  if constexpr (SweepCfg<TA, MG, NCH, NRM>::kBuilt) {
+    return reinterpret_cast<const void*>(&sweep_kernel<TA, MG, NCH, NRM>);
   } else {
     return nullptr;
   }

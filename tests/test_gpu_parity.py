@@ -415,15 +415,22 @@ def test_empty_matrix(ctx):
     assert res.status.item() == binding.ZERO and res.iters.item() == 0
 
 
-def test_nonfinite_input_is_reported(ctx):
+@pytest.mark.parametrize("form", ["SL1", "BL1", "BL0"])
+def test_nonfinite_input_is_reported(ctx, form):
+    """A NaN entry (or one whose square overflows) is reported as ENONFINITE:
+    by the column-norm pass, or for block starts on the CUDA cores by the
+    first power step, which forms the column norms."""
     At = np.random.default_rng(2).standard_normal((100, 40)).astype(np.float32)
-    At[17, 3] = np.nan
-    with pytest.raises(binding.GpspcaError) as e:
-        ctx.solve(torch.from_numpy(At).cuda(), "SL1", [0.1])
-    assert e.value.code == binding.ENONFINITE
+    m = 1 if form.startswith("S") else 2
+    mu = None if m == 1 else [1.0] * m
+    for bad in (np.nan, 3e19):
+        At[17, 3] = bad
+        with pytest.raises(binding.GpspcaError) as e:
+            ctx.solve(torch.from_numpy(At).cuda(), form, [0.1] * m, mu=mu)
+        assert e.value.code == binding.ENONFINITE
     # the context stays usable
     At[17, 3] = 0.0
-    ctx.solve(torch.from_numpy(At).cuda(), "SL1", [0.1])
+    ctx.solve(torch.from_numpy(At).cuda(), form, [0.1] * m, mu=mu)
 
 
 def test_degenerate_polar_status(ctx):
