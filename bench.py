@@ -552,6 +552,55 @@ def run_deflation(args):
     print(json.dumps(line), flush=True)
 
 
+def run_latency(args):
+    """The latency-bound case: 200 x 1000 i.i.d. N(0,1) with centred columns,
+    FP64, SL1 at gamma = 0.1 max||a_i||, tol 1e-6, maxit 1000 (the matrix is
+    1.6 MB, L2-resident).  Reported: microseconds per power iteration through
+    the cached CUDA graph (stopping test on the device) and with the same
+    kernels launched one by one from the host (one read-back of the active
+    count per iteration): their difference is what the graph saves per
+    iteration.  With --oracle, the FP64 oracle's time per iteration."""
+    import time
+
+    import numpy as np
+    import torch
+
+    from paper_1312_6182_gb300 import binding, synth
+
+    At = synth.workload_fp64_200x1000(0)
+    dA = torch.from_numpy(At).cuda()
+    stream = torch.cuda.Stream()
+    ctx = binding.Context(0, stream=stream)
+    out = binding.alloc_result(1, 200, 1000, "cuda", torch.float64)
+    res = {}
+    for eager in (False, True):
+        for _ in range(args.warmup):
+            ctx.solve(dA, "SL1", [0.1], gamma_relative=True, tol=1e-6, maxit=1000, out=out, eager=eager)
+        ms, r = _event_ms(stream, lambda: ctx.solve(dA, "SL1", [0.1], gamma_relative=True, tol=1e-6, maxit=1000,
+                                                    out=out, eager=eager), args.steps)
+        it = int(r.iters.item())
+        res["eager" if eager else "graph"] = {"ms_per_solve": round(ms, 4), "iters": it,
+                                              "us_per_iter": round(ms * 1e3 / it, 2)}
+    ctx.close()
+    res["graph_saves_us_per_iter"] = round(res["eager"]["us_per_iter"] - res["graph"]["us_per_iter"], 2)
+    extra = {"results": res}
+    if args.oracle:
+        import oracle
+
+        A = At.T
+        g = oracle.gamma_from_rho(A, "SL1", 0.1)
+        t0 = time.perf_counter()
+        ref = oracle.gpower(A, "SL1", g, tol=1e-6, maxit=1000)
+        sec = time.perf_counter() - t0
+        extra["cpu_baseline"] = {"value": round(int(ref.iters[0]) / sec, 1), "unit": "iters/s",
+                                 "cores": os.cpu_count(), "kind": "oracle", "sample": "the whole solve once",
+                                 "us_per_iter": round(sec * 1e6 / int(ref.iters[0]), 2)}
+    value = res["graph"]["iters"] / (res["graph"]["ms_per_solve"] / 1e3)
+    line = _base_line("GPower iters/s, latency-bound case", "iters/s", value, res["graph"]["ms_per_solve"], args,
+                      "200x1000 N(0,1) centred fp64, SL1 gamma=0.1*max||a_i||, tol 1e-6 (L2-resident)", "f64", extra)
+    print(json.dumps(line), flush=True)
+
+
 SCALING_FORMS = (("SL0", 0.01), ("BL0", 0.01), ("SL1", 0.05), ("BL1", 0.05))
 
 
@@ -866,7 +915,7 @@ def main():
     ap.add_argument("--sweep-dtype", default="f32", choices=["f32", "bf16"])
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--workload", default="spikes5000",
-                    choices=["spikes5000", "gamma-path", "precision", "serving", "deflation", "scaling"],
+                    choices=["spikes5000", "gamma-path", "precision", "serving", "deflation", "scaling", "latency"],
                     help="spikes5000: the headline step; the others measure the sparsity-path batch, the "
                          "BF16/FP8 precision path, the serving mix, deflated multi-component extraction and the "
                          "size sweep of the paper's efficiency experiment (one JSON line each)")
@@ -887,7 +936,7 @@ def main():
     if args.workload != "spikes5000":
         args.warmup = max(args.warmup, 1)
         {"gamma-path": run_gamma_path, "precision": run_precision, "serving": run_serving,
-         "deflation": run_deflation, "scaling": run_scaling}[args.workload](args)
+         "deflation": run_deflation, "scaling": run_scaling, "latency": run_latency}[args.workload](args)
         return
     if args.warmup < 3 and args.impl == "gpu":
         args.warmup = 3
