@@ -275,6 +275,75 @@ __device__ void jacobi_dd(const EigWs& ws, int mm) {
   }
 }
 
+// The CTA form of jacobi_dd for larger mm: each round applies J^T H J as
+// independent 2 x 2 block updates (rows p_i, q_i of the pair i rotation,
+// columns p_j, q_j of pair j, one block per thread) together with V <- V J,
+// so a round has two block barriers (rotations; updates).  Every element
+// gets the same double-float operations in the same order as jacobi_dd
+// (rows, then columns): the results are identical.
+__device__ inline void jacobi_dd_blocks(const EigWs& ws, int mm) {
+  dd* H = ws.H;
+  dd* V = ws.V;
+  const int tid = static_cast<int>(threadIdx.x);
+  const int nthr = static_cast<int>(blockDim.x);
+  for (int idx = tid; idx < mm * mm; idx += nthr) V[idx] = dd{(idx / mm == idx % mm) ? 1.0f : 0.0f, 0.0f};
+  __syncthreads();
+  const int half = mm / 2;
+  float off_prev = -1.0f;
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    float off = 0.0f, dg = 0.0f;
+    for (int idx = tid; idx < mm * mm; idx += nthr) {
+      const int r = idx / mm, c = idx % mm;
+      const float h = H[idx].hi;
+      if (r < c) off += h * h;
+      if (r == c) dg += h * h;
+    }
+    off = group_sum<false>(off, ws.red);
+    dg = group_sum<false>(dg, ws.red);
+    if (jacobi_done(off, dg, off_prev)) break;
+    off_prev = off;
+#pragma unroll 1
+    for (int round = 0; round < mm - 1; ++round) {
+      if (tid < half) {
+        const int k = tid;
+        const int a = (k == 0) ? 0 : ((k - 1 + round) % (mm - 1)) + 1;
+        const int b = ((mm - 2 - k + round) % (mm - 1)) + 1;
+        const int pp = min(a, b), qq = max(a, b);
+        dd c, s;
+        rotation(H[pp * mm + pp], H[qq * mm + qq], H[pp * mm + qq], &c, &s);
+        ws.rp[k] = pp;
+        ws.rq[k] = qq;
+        ws.rc[k] = c;
+        ws.rs[k] = s;
+      }
+      __syncthreads();
+      for (int t = tid; t < half * half; t += nthr) {  // block (i, j): H <- J_i^T H J_j
+        const int i = t / half, j = t % half;
+        const int pi = ws.rp[i], qi = ws.rq[i], pj = ws.rp[j], qj = ws.rq[j];
+        const dd ci = ws.rc[i], si = ws.rs[i], cj = ws.rc[j], sj = ws.rs[j];
+        const dd h00 = H[pi * mm + pj], h01 = H[pi * mm + qj], h10 = H[qi * mm + pj], h11 = H[qi * mm + qj];
+        // rows
+        const dd r00 = dd_sub(dd_mul(ci, h00), dd_mul(si, h10)), r01 = dd_sub(dd_mul(ci, h01), dd_mul(si, h11));
+        const dd r10 = dd_add(dd_mul(si, h00), dd_mul(ci, h10)), r11 = dd_add(dd_mul(si, h01), dd_mul(ci, h11));
+        // columns
+        H[pi * mm + pj] = dd_sub(dd_mul(cj, r00), dd_mul(sj, r01));
+        H[pi * mm + qj] = dd_add(dd_mul(sj, r00), dd_mul(cj, r01));
+        H[qi * mm + pj] = dd_sub(dd_mul(cj, r10), dd_mul(sj, r11));
+        H[qi * mm + qj] = dd_add(dd_mul(sj, r10), dd_mul(cj, r11));
+      }
+      for (int t = tid; t < half * mm; t += nthr) {  // V <- V J
+        const int k = t % half, l = t / half;
+        const int pp = ws.rp[k], qq = ws.rq[k];
+        const dd c = ws.rc[k], s = ws.rs[k];
+        const dd vp = V[l * mm + pp], vq = V[l * mm + qq];
+        V[l * mm + pp] = dd_sub(dd_mul(c, vp), dd_mul(s, vq));
+        V[l * mm + qq] = dd_add(dd_mul(s, vp), dd_mul(c, vq));
+      }
+      __syncthreads();
+    }
+  }
+}
+
 // Runs the Jacobi sweeps on the group that suits mm; all threads of the CTA
 // call it and leave it together.
 __device__ inline void jacobi_dd_cta(const EigWs& ws, int mm) {
@@ -292,7 +361,7 @@ __device__ inline void jacobi_dd_cta(const EigWs& ws, int mm) {
       }
     }
   } else {
-    jacobi_dd<false>(ws, mm);
+    jacobi_dd_blocks(ws, mm);
   }
   __syncthreads();
 }
