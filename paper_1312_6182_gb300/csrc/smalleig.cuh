@@ -66,23 +66,10 @@ __device__ inline EigWs eig_ws(double* base, int m) {
   return w;
 }
 
-// Barrier of the group that runs the generic Jacobi sweeps (mm > 16: the
-// whole CTA; the one-warp form for mm <= 16 is jacobi_small).
-template <bool kWarp>
-__device__ __forceinline__ void group_sync() {
-  if (kWarp) {
-    __syncwarp();
-  } else {
-    __syncthreads();
-  }
-}
-
-// Sum of v over the group, the same value in every thread, added in a fixed
+// Sum of v over the CTA, the same value in every thread, added in a fixed
 // order (xor tree within a warp, then the warps in index order).
-template <bool kWarp>
-__device__ __forceinline__ float group_sum(float v, float* red) {
+__device__ __forceinline__ float cta_sum(float v, float* red) {
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-  if (kWarp) return v;
   const int nw = blockDim.x >> 5;
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
@@ -131,7 +118,7 @@ __device__ __forceinline__ bool jacobi_done(float off, float dg, float off_prev)
 // arithmetic divides by constants, each lane owns (pair, index) slots of the
 // row and column updates (up to four), and the rotation of each pair,
 // computed by lane k, is broadcast by shuffles.  Same rotations, order and
-// stopping rule as jacobi_dd.  The kernel runs once per launch with a cold
+// stopping rule as jacobi_dd_blocks.  The kernel runs once per launch with a cold
 // instruction cache, so loops stay rolled: code size, not arithmetic, sets
 // its time.
 template <int MM>
@@ -210,77 +197,14 @@ __device__ void jacobi_small(dd* H, dd* V) {
   }
 }
 
-// Cyclic Jacobi on the symmetric mm x mm dd matrix H (mm even); on return
-// diag(H) holds the eigenvalues and V the eigenvectors (columns).  Stops by
-// jacobi_done, or after 30 sweeps.
-template <bool kWarp>
-__device__ void jacobi_dd(const EigWs& ws, int mm) {
-  dd* H = ws.H;
-  dd* V = ws.V;
-  const int tid = kWarp ? static_cast<int>(threadIdx.x & 31) : static_cast<int>(threadIdx.x);
-  const int nthr = kWarp ? 32 : static_cast<int>(blockDim.x);
-  for (int idx = tid; idx < mm * mm; idx += nthr) V[idx] = dd{(idx / mm == idx % mm) ? 1.0f : 0.0f, 0.0f};
-  group_sync<kWarp>();
-  const int half = mm / 2;
-  float off_prev = -1.0f;
-  for (int sweep = 0; sweep < 30; ++sweep) {
-    float off = 0.0f, dg = 0.0f;
-    for (int idx = tid; idx < mm * mm; idx += nthr) {
-      const int r = idx / mm, c = idx % mm;
-      const float h = H[idx].hi;
-      if (r < c) off += h * h;
-      if (r == c) dg += h * h;
-    }
-    off = group_sum<kWarp>(off, ws.red);
-    dg = group_sum<kWarp>(dg, ws.red);
-    if (jacobi_done(off, dg, off_prev)) break;
-    off_prev = off;
-#pragma unroll 1
-    for (int round = 0; round < mm - 1; ++round) {
-      if (tid < half) {
-        const int k = tid;
-        const int a = (k == 0) ? 0 : ((k - 1 + round) % (mm - 1)) + 1;
-        const int b = ((mm - 2 - k + round) % (mm - 1)) + 1;
-        const int pp = min(a, b), qq = max(a, b);
-        dd c, s;
-        rotation(H[pp * mm + pp], H[qq * mm + qq], H[pp * mm + qq], &c, &s);
-        ws.rp[k] = pp;
-        ws.rq[k] = qq;
-        ws.rc[k] = c;
-        ws.rs[k] = s;
-      }
-      group_sync<kWarp>();
-      for (int idx = tid; idx < half * mm; idx += nthr) {  // rows: H <- J^T H
-        const int k = idx / mm, l = idx % mm;
-        const int pp = ws.rp[k], qq = ws.rq[k];
-        const dd c = ws.rc[k], s = ws.rs[k];
-        const dd hp = H[pp * mm + l], hq = H[qq * mm + l];
-        H[pp * mm + l] = dd_sub(dd_mul(c, hp), dd_mul(s, hq));
-        H[qq * mm + l] = dd_add(dd_mul(s, hp), dd_mul(c, hq));
-      }
-      group_sync<kWarp>();
-      for (int idx = tid; idx < half * mm; idx += nthr) {  // columns: H <- H J, V <- V J
-        const int k = idx / mm, l = idx % mm;
-        const int pp = ws.rp[k], qq = ws.rq[k];
-        const dd c = ws.rc[k], s = ws.rs[k];
-        const dd hp = H[l * mm + pp], hq = H[l * mm + qq];
-        H[l * mm + pp] = dd_sub(dd_mul(c, hp), dd_mul(s, hq));
-        H[l * mm + qq] = dd_add(dd_mul(s, hp), dd_mul(c, hq));
-        const dd vp = V[l * mm + pp], vq = V[l * mm + qq];
-        V[l * mm + pp] = dd_sub(dd_mul(c, vp), dd_mul(s, vq));
-        V[l * mm + qq] = dd_add(dd_mul(s, vp), dd_mul(c, vq));
-      }
-      group_sync<kWarp>();
-    }
-  }
-}
-
-// The CTA form of jacobi_dd for larger mm: each round applies J^T H J as
+// Cyclic Jacobi on the symmetric mm x mm dd matrix H (mm even) by the whole
+// CTA; on return diag(H) holds the eigenvalues and V the eigenvectors
+// (columns).  The mm - 1 rounds of a sweep rotate the mm / 2 disjoint pairs
+// of a round-robin ordering at once; each round applies J^T H J as
 // independent 2 x 2 block updates (rows p_i, q_i of the pair i rotation,
-// columns p_j, q_j of pair j, one block per thread) together with V <- V J,
-// so a round has two block barriers (rotations; updates).  Every element
-// gets the same double-float operations in the same order as jacobi_dd
-// (rows, then columns): the results are identical.
+// columns p_j, q_j of pair j: one block per thread, the rows' update first,
+// then the columns') together with V <- V J, so a round has two block
+// barriers (rotations; updates).  Stops by jacobi_done, or after 30 sweeps.
 __device__ inline void jacobi_dd_blocks(const EigWs& ws, int mm) {
   dd* H = ws.H;
   dd* V = ws.V;
@@ -298,8 +222,8 @@ __device__ inline void jacobi_dd_blocks(const EigWs& ws, int mm) {
       if (r < c) off += h * h;
       if (r == c) dg += h * h;
     }
-    off = group_sum<false>(off, ws.red);
-    dg = group_sum<false>(dg, ws.red);
+    off = cta_sum(off, ws.red);
+    dg = cta_sum(dg, ws.red);
     if (jacobi_done(off, dg, off_prev)) break;
     off_prev = off;
 #pragma unroll 1
