@@ -208,6 +208,41 @@ static void plan_tc(Plan* pl, int m, int64_t p, int64_t n, int nsm) {
   pl->nsplit2 = (pl->nchunks2 + pl->kps2 - 1) / pl->kps2;
 }
 
+// Row ranges per column tile of the T pass.  With ntile1 tiles on one
+// persistent CTA per SM the last wave runs only ntile1 mod nsm of them (157
+// tiles on 152 SMs: two waves for 1.03 of work); splitting each tile's rows
+// into s ranges evens the waves at the cost of the partial sums (s * mpad
+// floats per column, written by the T pass and read back by the combine
+// step).  Cost in units of one 64-row chunk streamed by every CTA: the
+// largest CTA's chunks plus one per item (its pipeline fill and epilogue),
+// the partials' traffic at twice that streaming rate (the combine step
+// streams at the HBM rate), and two for the combine launch.  Geometries with
+// two CTAs per SM already absorb the tail and stay unsplit.  Fitted on GB300
+// over p x n in {5000 x 20000, 10000 x 50000, 20000 x 100000, 2000 x 60000,
+// 8000 x 8000}, m in {16, 32, 64}, float and bf16 storage.
+static void plan_tc_ksplit(Plan* pl, int nsm) {
+  pl->ksplit1 = 1;
+  pl->kcs1 = pl->kchunks1;
+  if (tc_t_ctas_per_sm(pl->npad, pl->tc_na, pl->tc_fused != 0) > 1) return;
+  const double chunk_bytes = static_cast<double>(kTcBK) * kTcTile1 * (pl->tc_fused ? 4 : 2 * pl->tc_na) * nsm;
+  const double part_bytes = 2.0 * 4.0 * pl->mpad * pl->n_pad;
+  int best = 1;
+  double best_cost = 0.0;
+  for (int sp = 1; sp <= kTcMaxSplit1; ++sp) {
+    const int kcs = (pl->kchunks1 + sp - 1) / sp;
+    if (sp > 1 && kcs < 4) break;
+    const int items = pl->ntile1 * sp;
+    const double cost = static_cast<double>((items + nsm - 1) / nsm) * (kcs + 1) +
+                        (sp > 1 ? 0.5 * sp * part_bytes / chunk_bytes + 2.0 : 0.0);
+    if (sp == 1 || cost < best_cost * 0.99) {
+      best_cost = cost;
+      best = sp;
+    }
+  }
+  pl->kcs1 = (pl->kchunks1 + best - 1) / best;
+  pl->ksplit1 = (pl->kchunks1 + pl->kcs1 - 1) / pl->kcs1;
+}
+
 int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fast, int nsm, Plan* P,
               bool allow_tc) {
   const DInfo d = dinfo(dt);
@@ -241,6 +276,7 @@ int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fa
     // layouts are copied once per solve
     pl.tc_fused = (dt == GPSPCA_F32 && fast && ld % 4 == 0) ? 1 : 0;
     pl.tc_convert = (native_bf16 || pl.tc_fused) ? 0 : 1;
+    plan_tc_ksplit(&pl, nsm);
     pl.C = 1;
     pl.ps = static_cast<int>(p);
     found = true;
@@ -324,6 +360,8 @@ int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fa
     pl.ws_x3 = 2 * static_cast<size_t>(pl.npad) * pl.p_pad;
     pl.ws_g3 = 2 * static_cast<size_t>(pl.npad) * pl.n_pad;
     if (pl.tc_convert) pl.ws_planes = 2 * static_cast<size_t>(pl.tc_na) * n * pl.p_pad;
+    if (pl.ksplit1 > 1)
+      pl.ws_tpart = sizeof(float) * static_cast<size_t>(pl.ksplit1) * pl.mpad * pl.n_pad;
   }
   *P = pl;
   return GPSPCA_OK;
@@ -355,7 +393,7 @@ struct Slot {
   cudaEvent_t done = nullptr;
   Budget* budget = nullptr;
   // workspace buffers, grown on demand
-  DevBuf b_cnorm, b_P, b_Y, b_ypart, b_T, b_fpart, b_gpart, b_x3, b_g3, b_maps, b_planes;
+  DevBuf b_cnorm, b_P, b_Y, b_ypart, b_T, b_fpart, b_gpart, b_x3, b_g3, b_maps, b_planes, b_tpart;
   TcMaps* maps_host = nullptr;  // pinned: the tensor maps copied to b_maps before a solve
   // staging for host-located inputs/outputs
   DevBuf s_A, s_scale, s_x0, s_X, s_Z, s_sup, s_obj, s_it, s_stat, s_gam;
@@ -369,7 +407,7 @@ struct Slot {
   size_t held() const {
     size_t s = 0;
     for (const DevBuf* b : {&b_cnorm, &b_P, &b_Y, &b_ypart, &b_T, &b_fpart, &b_gpart, &b_x3, &b_g3, &b_maps,
-                            &b_planes, &s_A,
+                            &b_planes, &b_tpart, &s_A,
                             &s_scale, &s_x0, &s_X,
                             &s_Z, &s_sup, &s_obj, &s_it, &s_stat, &s_gam, &d_W, &d_list})
       s += b->bytes;
@@ -414,7 +452,7 @@ static void release(Slot* s, DevBuf* b) {
 
 static void release_workspace(Slot* s) {
   for (DevBuf* b : {&s->b_cnorm, &s->b_P, &s->b_Y, &s->b_ypart, &s->b_T, &s->b_fpart, &s->b_gpart, &s->b_x3,
-                    &s->b_g3, &s->b_maps, &s->b_planes, &s->s_A,
+                    &s->b_g3, &s->b_maps, &s->b_planes, &s->b_tpart, &s->s_A,
                     &s->s_scale, &s->s_x0, &s->s_X, &s->s_Z, &s->s_sup, &s->s_obj, &s->s_it, &s->s_stat, &s->s_gam,
                     &s->d_W, &s->d_list})
     release(s, b);
@@ -519,7 +557,7 @@ static cudaError_t launch_sweeps(const Plan& pl, Slot* s, cudaStream_t cs, int s
   if (pl.tc) {
     TcArgs a{s->io_dev,  s->st_dev, pl.p,     pl.n,       pl.m,        pl.mpad,     pl.form,
              sketch,     pl.tc_na,  pl.tc_fused, pl.dtype == GPSPCA_FP8_E4M3 ? 1 : 0, pl.p_pad, pl.n_pad,
-             pl.ntile1,  pl.kchunks1, pl.nchunks2, pl.kps2, pl.nsplit2, pl.nrow2};
+             pl.ntile1,  pl.kchunks1, pl.ksplit1, pl.kcs1, pl.nchunks2, pl.kps2, pl.nsplit2, pl.nrow2};
     launch_tc_sweep(a, pl.npad, cs);
     return cudaGetLastError();
   }
@@ -747,6 +785,7 @@ static int prepare_solve(Slot* s, const Request& r, int nsm, bool scratch_out, P
     if ((rc = ensure(s, &s->b_g3, pl.ws_g3))) return rc;
     if ((rc = ensure(s, &s->b_maps, sizeof(TcMaps)))) return rc;
     if (pl.tc_convert && (rc = ensure(s, &s->b_planes, pl.ws_planes))) return rc;
+    if (pl.ksplit1 > 1 && (rc = ensure(s, &s->b_tpart, pl.ws_tpart))) return rc;
     // the host copy of the maps is reused only after this solve's copy has run
     GP_CUDA(cudaStreamSynchronize(s->stream));
     if (pl.tc_fused) {
@@ -804,6 +843,7 @@ static int prepare_solve(Slot* s, const Request& r, int nsm, bool scratch_out, P
     io.tc_g3 = s->b_g3.p;
     io.tc_maps = s->b_maps.p;
     io.tc_planes = pl.tc_convert ? s->b_planes.p : nullptr;
+    io.tc_tpart = pl.ksplit1 > 1 ? s->b_tpart.p : nullptr;
   }
   for (int j = 0; j < m; ++j) {
     io.gamma_in[j] = r.gamma[j];

@@ -37,6 +37,7 @@ struct IO {
   void* tc_g3;    // tensor-core path: [3 mpad][n_pad] bf16 split of the gradient factors G (transposed)
   const void* tc_maps;  // tensor-core path: the TMA tensor maps of A, X3 and G3 (TcMaps)
   void* tc_planes;      // tensor-core path: bf16 planes of a float / fp8 A ([na][n][p_pad])
+  void* tc_tpart;       // tensor-core path: T partials of the row ranges ([ksplit][mpad][n_pad] float)
   double gamma_in[kMaxM];  // as passed (absolute, or relative with the flag)
   double mu[kMaxM];
   double tol;

@@ -35,8 +35,9 @@ struct Plan {
   int tc_na = 1;       // bf16 planes of A the contractions read (3 for float A)
   int tc_convert = 0;  // the planes are a workspace copy made once per solve (float / fp8 A)
   int tc_fused = 0;    // float A read in place, split into planes in shared memory
+  int ksplit1 = 1, kcs1 = 0;  // T pass: row ranges per column tile, 64-row chunks per range
   size_t ws_cnorm = 0, ws_P = 0, ws_ypart = 0, ws_T = 0, ws_fpart = 0, ws_gpart = 0, ws_x3 = 0, ws_g3 = 0,
-         ws_planes = 0;
+         ws_planes = 0, ws_tpart = 0;
 
   std::string key() const {
     char b[256];
@@ -44,7 +45,7 @@ struct Plan {
              ps, ncl, cols_per_cl);
     std::string s(b);
     if (tc) {
-      snprintf(b, sizeof(b), "|tc%d,%d,%d,%d,%d,%d", npad, kps2, nsplit2, tc_na, tc_convert, tc_fused);
+      snprintf(b, sizeof(b), "|tc%d,%d,%d,%d,%d,%d,%d", npad, kps2, nsplit2, tc_na, tc_convert, tc_fused, ksplit1);
       s += b;
     }
     for (const Pass& q : passes) {
@@ -58,7 +59,7 @@ struct Plan {
     return s;
   }
   size_t workspace_bytes() const {
-    return ws_cnorm + ws_P + ws_ypart + ws_T + ws_fpart + ws_gpart + ws_x3 + ws_g3 + ws_planes + 11 * 256 + 1024;
+    return ws_cnorm + ws_P + ws_ypart + ws_T + ws_fpart + ws_gpart + ws_x3 + ws_g3 + ws_planes + ws_tpart + 12 * 256 + 1024;
   }
 };
 

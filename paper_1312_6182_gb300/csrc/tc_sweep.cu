@@ -24,39 +24,36 @@ __device__ __forceinline__ void split3(float v, __nv_bfloat16& b0, __nv_bfloat16
 }
 
 // X = Y W (the iterate this sweep evaluates, as the fused sweep forms it),
-// written out for the active components and split into X3^T for the T pass.
+// written out for the active components and split into X3^T for the T pass;
+// one thread per (row, component), blockIdx.y the component.
 __global__ void tc_prep_kernel(const TcArgs a) {
-  __shared__ float Ws[kMaxM * kMaxM];
-  __shared__ int act[kMaxM];
+  __shared__ float wj[kMaxM];
   const IO* io = a.io;
   const State* st = a.st;
-  const int m = a.m, p = a.p;
+  const int m = a.m, p = a.p, j = blockIdx.y;
   const bool block = a.form >= 2;
-  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) Ws[idx] = static_cast<float>(st->W[idx]);
-  if (threadIdx.x < kMaxM) act[threadIdx.x] = threadIdx.x < m ? st->active[threadIdx.x] : 0;
+  // column j of W (its diagonal entry alone for the single-unit forms)
+  if (threadIdx.x < m) wj[threadIdx.x] = j < m ? static_cast<float>(st->W[threadIdx.x * m + j]) : 0.0f;
   __syncthreads();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= p) return;
   const float* Y = static_cast<const float*>(io->Y);
-  float* Xo = static_cast<float*>(io->X);
+  float x = 0.0f;
+  if (j < m) {
+    if (block) {
+      for (int l = 0; l < m; ++l) x += Y[static_cast<int64_t>(l) * p + r] * wj[l];
+    } else {
+      x = Y[static_cast<int64_t>(j) * p + r] * wj[j];
+    }
+    if (!a.sketch && st->active[j]) static_cast<float*>(io->X)[static_cast<int64_t>(j) * p + r] = x;
+  }
   __nv_bfloat16* X3 = static_cast<__nv_bfloat16*>(io->tc_x3);
   const int64_t rs = a.p_pad;
-  for (int j = 0; j < a.mpad; ++j) {
-    float x = 0.0f;
-    if (j < m) {
-      if (block) {
-        for (int l = 0; l < m; ++l) x += Y[static_cast<int64_t>(l) * p + r] * Ws[l * m + j];
-      } else {
-        x = Y[static_cast<int64_t>(j) * p + r] * Ws[j * m + j];
-      }
-      if (!a.sketch && act[j]) Xo[static_cast<int64_t>(j) * p + r] = x;
-    }
-    __nv_bfloat16 b0, b1, b2;
-    split3(x, b0, b1, b2);
-    X3[(0 * a.mpad + j) * rs + r] = b0;
-    X3[(1 * a.mpad + j) * rs + r] = b1;
-    X3[(2 * a.mpad + j) * rs + r] = b2;
-  }
+  __nv_bfloat16 b0, b1, b2;
+  split3(x, b0, b1, b2);
+  X3[(0 * a.mpad + j) * rs + r] = b0;
+  X3[(1 * a.mpad + j) * rs + r] = b1;
+  X3[(2 * a.mpad + j) * rs + r] = b2;
 }
 
 __host__ __device__ constexpr int tc_stages(int npad, int na) { return na == 3 ? 3 : (npad <= 48 ? 4 : (npad <= 96 ? 3 : 5)); }
@@ -221,6 +218,118 @@ __device__ __forceinline__ bool tc_drain(const TcSmem& S, uint32_t tlane, int it
   return true;
 }
 
+// ---- the T pass's work: items blockIdx.x, blockIdx.x + gridDim.x, ... of
+// ntile1 * ksplit1, item = (column tile, range of kcs1 64-row chunks); with
+// one range per tile the item is the whole tile.  Splitting the rows fills
+// the last wave of CTAs when the tiles do not divide evenly among them.
+struct TItem {
+  int tile, ks, cb, ce;  // tile, range index, its chunks [cb, ce)
+};
+__device__ __forceinline__ TItem t_item(const TcArgs& a, int item) {
+  TItem r;
+  r.tile = item / a.ksplit1;
+  r.ks = item - r.tile * a.ksplit1;
+  r.cb = r.ks * a.kcs1;
+  r.ce = min(a.kchunks1, r.cb + a.kcs1);
+  return r;
+}
+// Walks this CTA's chunks in order (the TMA, MMA and converter roles).
+struct TCursor {
+  int item, c;
+  TItem cur;
+  __device__ void start(const TcArgs& a) {
+    item = blockIdx.x;
+    if (valid(a)) {
+      cur = t_item(a, item);
+      c = cur.cb;
+    }
+  }
+  __device__ bool valid(const TcArgs& a) const { return item < a.ntile1 * a.ksplit1; }
+  __device__ void next(const TcArgs& a) {
+    if (++c >= cur.ce) {
+      item += gridDim.x;
+      if (valid(a)) {
+        cur = t_item(a, item);
+        c = cur.cb;
+      }
+    }
+  }
+};
+
+// Entry (component j, column i) of the finished T (the sum of the column's
+// products, before the fp8 column scale scl): the Table 1 threshold, T out,
+// G split into bf16 thirds.
+template <int MPAD>
+__device__ __forceinline__ void tc_t_finish(const TcArgs& a, int i, int j, float t, float scl, int form,
+                                            const float* gam_s, const float* mu_s, const int* act_s) {
+  float g = 0.0f;
+  if (j < a.m) {
+    const float tj = t * scl;
+    if (!a.sketch && act_s[j]) static_cast<float*>(a.io->T)[static_cast<int64_t>(j) * a.n + i] = tj;
+    g = grad_factor<float>(form, tj, gam_s[j], mu_s[j]) * scl;
+  }
+  __nv_bfloat16* G3 = static_cast<__nv_bfloat16*>(a.io->tc_g3);
+  const int64_t gs = a.n_pad;
+  __nv_bfloat16 b0, b1, b2;
+  split3(g, b0, b1, b2);
+  G3[(0 * MPAD + j) * gs + i] = b0;
+  G3[(1 * MPAD + j) * gs + i] = b1;
+  G3[(2 * MPAD + j) * gs + i] = b2;
+}
+
+// The epilogue of one T-pass item for column `col` of its tile: the column's
+// finish, or, with several row ranges, its partial for tc_t_combine_kernel.
+template <int MPAD>
+__device__ __forceinline__ void tc_t_store(const TcArgs& a, const TItem& ti, int col, const float (&t)[MPAD],
+                                           int form, const float* gam_s, const float* mu_s, const int* act_s) {
+  const int i = ti.tile * kTcTile1 + col;
+  if (i >= a.n) return;
+  if (a.ksplit1 > 1) {
+    float* tp = static_cast<float*>(a.io->tc_tpart);
+#pragma unroll
+    for (int j = 0; j < MPAD; ++j)
+      if (j < a.m) tp[(static_cast<int64_t>(ti.ks) * MPAD + j) * a.n_pad + i] = t[j];
+    return;
+  }
+  const float scl = a.scaled ? a.io->col_scale[i] : 1.0f;
+#pragma unroll
+  for (int j = 0; j < MPAD; ++j) tc_t_finish<MPAD>(a, i, j, t[j], scl, form, gam_s, mu_s, act_s);
+}
+
+// T from the row ranges' partials, summed in range order, and its finish:
+// one thread per (column, component), blockIdx.y the component.
+template <int MPAD>
+__global__ void tc_t_combine_kernel(const TcArgs a) {
+  __shared__ float gam_s[kMaxM], mu_s[kMaxM];
+  __shared__ int act_s[kMaxM];
+  const IO* io = a.io;
+  const State* st = a.st;
+  const bool sketch = a.sketch != 0;
+  const int tid = threadIdx.x, j = blockIdx.y;
+  if (tid < kMaxM) {
+    const bool v = tid < a.m && !sketch;
+    gam_s[tid] = v ? static_cast<float>(st->gamma[tid]) : 0.0f;
+    mu_s[tid] = v ? static_cast<float>(io->mu[tid]) : 1.0f;
+    act_s[tid] = tid < a.m ? st->active[tid] : 0;
+  }
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + tid;
+  if (i >= a.n) return;
+  float sum = 0.0f;
+  if (j < a.m) {
+    const float* tp = static_cast<const float*>(io->tc_tpart) + static_cast<int64_t>(j) * a.n_pad + i;
+    const int64_t ks_stride = static_cast<int64_t>(MPAD) * a.n_pad;
+    float v[kTcMaxSplit1];
+#pragma unroll
+    for (int ks = 0; ks < kTcMaxSplit1; ++ks) v[ks] = ks < a.ksplit1 ? tp[ks * ks_stride] : 0.0f;
+#pragma unroll
+    for (int ks = 0; ks < kTcMaxSplit1; ++ks)
+      if (ks < a.ksplit1) sum += v[ks];
+  }
+  const float scl = a.scaled ? io->col_scale[i] : 1.0f;
+  tc_t_finish<MPAD>(a, i, j, sum, scl, sketch ? GPSPCA_SL0 : a.form, gam_s, mu_s, act_s);
+}
+
 // ---- pass 1: T = A^T X for 128-column tiles (persistent CTAs), threshold,
 // G3^T for pass 2.  Tensor-memory lane = column of the tile.
 template <int NPAD, int NA>
@@ -251,49 +360,42 @@ __global__ void __launch_bounds__(kTcThreads) tc_t_kernel(const TcArgs a) {
     if (lane == 0) {
       for (int pl = 0; pl < NA; ++pl) tmap_acquire(&maps->a1[pl]);
       tmap_acquire(&maps->x3);
-      int it = 0;
-      for (int tile = blockIdx.x; tile < a.ntile1 && !timed_out; tile += gridDim.x) {
-        for (int c = 0; c < a.kchunks1; ++c, ++it) {
-          const bool ok = tc_produce<NPAD, NA>(S, it, c, [&](int cc, uint32_t sa, uint32_t bar) {
-            for (int pl = 0; pl < NA; ++pl) tma_load_2d(sa + pl * kTcA, &maps->a1[pl], cc * kTcBK, tile * kTcTile1, bar);
-            tma_load_2d(sa + Cfg::kAll, &maps->x3, cc * kTcBK, 0, bar);
-          });
-          if (!ok) {
-            timed_out = true;
-            break;
-          }
-        }
+      TCursor cu;
+      cu.start(a);
+      for (int it = 0; cu.valid(a) && !timed_out; ++it, cu.next(a)) {
+        const int tile = cu.cur.tile;
+        const bool ok = tc_produce<NPAD, NA>(S, it, cu.c, [&](int cc, uint32_t sa, uint32_t bar) {
+          for (int pl = 0; pl < NA; ++pl) tma_load_2d(sa + pl * kTcA, &maps->a1[pl], cc * kTcBK, tile * kTcTile1, bar);
+          tma_load_2d(sa + Cfg::kAll, &maps->x3, cc * kTcBK, 0, bar);
+        });
+        if (!ok) timed_out = true;
       }
     }
   } else if (warp == 5) {  // MMA issuer
     if (lane == 0) {
-      int it = 0;
-      for (int tile = blockIdx.x; tile < a.ntile1 && !timed_out; tile += gridDim.x) {
-        for (int c = 0; c < a.kchunks1; ++c, ++it) {
-          const bool ok =
-              tc_mma_chunk<NPAD, NA>(S, tmem, it, kIdesc, [](uint32_t sa, int pl, int kk, uint64_t* ad, uint64_t* bd) {
-                *ad = sdesc_sw128(sa + pl * kTcA + kk * 32, 16, 1024);
-                *bd = sdesc_sw128(sa + Cfg::kAll + kk * 32, 16, 1024);
-              });
-          if (!ok) {
-            timed_out = true;
-            *S.abort_flag = 1;
-            break;
-          }
+      TCursor cu;
+      cu.start(a);
+      for (int it = 0; cu.valid(a) && !timed_out; ++it, cu.next(a)) {
+        const bool ok =
+            tc_mma_chunk<NPAD, NA>(S, tmem, it, kIdesc, [](uint32_t sa, int pl, int kk, uint64_t* ad, uint64_t* bd) {
+              *ad = sdesc_sw128(sa + pl * kTcA + kk * 32, 16, 1024);
+              *bd = sdesc_sw128(sa + Cfg::kAll + kk * 32, 16, 1024);
+            });
+        if (!ok) {
+          timed_out = true;
+          *S.abort_flag = 1;
         }
       }
     }
   } else {  // epilogue, warps 0-3: thread = tensor-memory lane = column of the tile
     const uint32_t tlane = tmem + (static_cast<uint32_t>(warp * 32) << 16);
-    float* Tout = static_cast<float*>(io->T);
-    __nv_bfloat16* G3 = static_cast<__nv_bfloat16*>(io->tc_g3);
-    const int64_t gs = a.n_pad;
     int it = 0;
-    for (int tile = blockIdx.x; tile < a.ntile1 && !timed_out; tile += gridDim.x) {
+    for (int item = blockIdx.x; item < a.ntile1 * a.ksplit1 && !timed_out; item += gridDim.x) {
+      const TItem ti = t_item(a, item);
       float t[MPAD];
 #pragma unroll
       for (int j = 0; j < MPAD; ++j) t[j] = 0.0f;
-      for (int c = 0; c < a.kchunks1; ++c, ++it) {
+      for (int c = ti.cb; c < ti.ce; ++c, ++it) {
         if (!tc_drain<NPAD, NA>(S, tlane, it, t)) {
           timed_out = true;
           *S.abort_flag = 1;
@@ -301,24 +403,7 @@ __global__ void __launch_bounds__(kTcThreads) tc_t_kernel(const TcArgs a) {
         }
       }
       if (timed_out) break;
-      const int i = tile * kTcTile1 + warp * 32 + lane;
-      if (i < a.n) {
-        const float scl = a.scaled ? io->col_scale[i] : 1.0f;
-#pragma unroll
-        for (int j = 0; j < MPAD; ++j) {
-          float g = 0.0f;
-          if (j < a.m) {
-            const float tj = t[j] * scl;
-            if (!sketch && act_s[j]) Tout[static_cast<int64_t>(j) * a.n + i] = tj;
-            g = grad_factor<float>(form, tj, gam_s[j], mu_s[j]) * scl;
-          }
-          __nv_bfloat16 b0, b1, b2;
-          split3(g, b0, b1, b2);
-          G3[(0 * MPAD + j) * gs + i] = b0;
-          G3[(1 * MPAD + j) * gs + i] = b1;
-          G3[(2 * MPAD + j) * gs + i] = b2;
-        }
-      }
+      tc_t_store<MPAD>(a, ti, warp * 32 + lane, t, form, gam_s, mu_s, act_s);
     }
   }
   tc_teardown<NPAD, NA>(S, tmem, timed_out, st);
@@ -606,11 +691,13 @@ __device__ __forceinline__ bool tc_fused_mma(const TcFusedSmem& S, uint32_t tmem
 // converters have read the stage's previous tile, the X3 / G3 tile once the
 // MMAs of the ring-2 stage's previous chunk have completed.  The two streams
 // are polled without blocking, so neither waits behind the other.
-// coord(it, &c, &tr): the chunk's 64-deep index c and its tile (T pass) or
-// 128-row block (Y pass).  false on a timeout or an abort.
-template <int NPAD, typename Coord>
-__device__ __forceinline__ bool tc_fused_producer(const TcFusedSmem& S, int total, Coord coord, const TcMaps* maps,
-                                                  bool y_pass) {
+// coordf / coordb(it, &c, &tr): the chunk's 64-deep index c and its tile (T
+// pass) or 128-row block (Y pass), for the stored-tile and the X3 / G3
+// streams; each is called with it = 0, 1, 2, ... in turn.  false on a
+// timeout or an abort.
+template <int NPAD, typename CoordF, typename CoordB>
+__device__ __forceinline__ bool tc_fused_producer(const TcFusedSmem& S, int total, CoordF coordf, CoordB coordb,
+                                                  const TcMaps* maps, bool y_pass) {
   using Cfg = TcFusedCfg<NPAD>;
   int itf = 0, itb = 0;
   uint32_t idle = 0;
@@ -622,7 +709,7 @@ __device__ __forceinline__ bool tc_fused_producer(const TcFusedSmem& S, int tota
       const uint32_t u1 = static_cast<uint32_t>(itf / Cfg::S1);
       if (u1 == 0 || mbar_test(smem_u32(&S.empty1[s1]), (u1 - 1) & 1)) {
         int c, tr;
-        coord(itf, &c, &tr);
+        coordf(itf, &c, &tr);
         const uint32_t sa = S.base1 + s1 * Cfg::kStage1;
         const uint32_t bar = smem_u32(&S.full1[s1]);
         mbar_arrive_expect_tx(bar, kTcF);
@@ -641,7 +728,7 @@ __device__ __forceinline__ bool tc_fused_producer(const TcFusedSmem& S, int tota
       const uint32_t u2 = static_cast<uint32_t>(itb / Cfg::S2);
       if (u2 == 0 || mbar_test(smem_u32(&S.empty2[s2]), (u2 - 1) & 1)) {
         int c, tr;
-        coord(itb, &c, &tr);
+        coordb(itb, &c, &tr);
         const uint32_t bar = smem_u32(&S.full2[s2]);
         mbar_arrive_expect_tx(bar, Cfg::kB);
         tma_load_2d(S.base2 + s2 * Cfg::kStage2 + 3 * kTcA, y_pass ? &maps->g3 : &maps->x3, c * kTcBK, 0, bar);
@@ -687,13 +774,25 @@ __global__ void __launch_bounds__(kTcFusedThreads, 1) tc_t_fused_kernel(const Tc
     if (lane == 0) {
       tmap_acquire(&maps->a1f);
       tmap_acquire(&maps->x3);
-      const int ntiles = blockIdx.x < a.ntile1 ? (a.ntile1 - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-      const int kc = a.kchunks1;
+      int total = 0;
+      for (int item = blockIdx.x; item < a.ntile1 * a.ksplit1; item += gridDim.x) {
+        const TItem ti = t_item(a, item);
+        total += ti.ce - ti.cb;
+      }
+      TCursor cf, cb;  // the stored-tile and the X3 streams, each called with consecutive indices
+      cf.start(a);
+      cb.start(a);
       if (!tc_fused_producer<NPAD>(
-              S, ntiles * kc,
-              [&](int it, int* c, int* tr) {
-                *c = it % kc;
-                *tr = blockIdx.x + (it / kc) * gridDim.x;
+              S, total,
+              [&](int, int* c, int* tr) {
+                *c = cf.c;
+                *tr = cf.cur.tile;
+                cf.next(a);
+              },
+              [&](int, int* c, int* tr) {
+                *c = cb.c;
+                *tr = cb.cur.tile;
+                cb.next(a);
               },
               maps, false)) {
         timed_out = true;
@@ -702,55 +801,38 @@ __global__ void __launch_bounds__(kTcFusedThreads, 1) tc_t_fused_kernel(const Tc
     }
   } else if (warp == 5) {
     if (lane == 0) {
-      int it = 0;
-      for (int tile = blockIdx.x; tile < a.ntile1 && !timed_out; tile += gridDim.x)
-        for (int c = 0; c < a.kchunks1 && !timed_out; ++c, ++it)
-          if (!tc_fused_mma<NPAD, false>(S, tmem, it, kIdesc)) {
-            timed_out = true;
-            *S.acc.abort_flag = 1;
-          }
-    }
-  } else if (warp >= 6) {  // converters
-    int it = 0;
-    for (int tile = blockIdx.x; tile < a.ntile1 && !timed_out; tile += gridDim.x)
-      for (int c = 0; c < a.kchunks1 && !timed_out; ++c, ++it)
-        if (tc_aborted(S.acc) || !tc_convert_chunk<NPAD, false>(S, it)) {
+      TCursor cu;
+      cu.start(a);
+      for (int it = 0; cu.valid(a) && !timed_out; ++it, cu.next(a))
+        if (!tc_fused_mma<NPAD, false>(S, tmem, it, kIdesc)) {
           timed_out = true;
           *S.acc.abort_flag = 1;
         }
+    }
+  } else if (warp >= 6) {  // converters
+    TCursor cu;
+    cu.start(a);
+    for (int it = 0; cu.valid(a) && !timed_out; ++it, cu.next(a))
+      if (tc_aborted(S.acc) || !tc_convert_chunk<NPAD, false>(S, it)) {
+        timed_out = true;
+        *S.acc.abort_flag = 1;
+      }
   } else {  // epilogue
     const uint32_t tlane = tmem + (static_cast<uint32_t>(warp * 32) << 16);
-    float* Tout = static_cast<float*>(io->T);
-    __nv_bfloat16* G3 = static_cast<__nv_bfloat16*>(io->tc_g3);
-    const int64_t gs = a.n_pad;
     int it = 0;
-    for (int tile = blockIdx.x; tile < a.ntile1 && !timed_out; tile += gridDim.x) {
+    for (int item = blockIdx.x; item < a.ntile1 * a.ksplit1 && !timed_out; item += gridDim.x) {
+      const TItem ti = t_item(a, item);
       float t[MPAD];
 #pragma unroll
       for (int j = 0; j < MPAD; ++j) t[j] = 0.0f;
-      for (int c = 0; c < a.kchunks1; ++c, ++it)
+      for (int c = ti.cb; c < ti.ce; ++c, ++it)
         if (!tc_drain<NPAD, 3>(S.acc, tlane, it, t)) {
           timed_out = true;
           *S.acc.abort_flag = 1;
           break;
         }
       if (timed_out) break;
-      const int i = tile * kTcTile1 + warp * 32 + lane;
-      if (i < a.n) {
-#pragma unroll
-        for (int j = 0; j < MPAD; ++j) {
-          float g = 0.0f;
-          if (j < a.m) {
-            if (!sketch && act_s[j]) Tout[static_cast<int64_t>(j) * a.n + i] = t[j];
-            g = grad_factor<float>(form, t[j], gam_s[j], mu_s[j]);
-          }
-          __nv_bfloat16 b0, b1, b2;
-          split3(g, b0, b1, b2);
-          G3[(0 * MPAD + j) * gs + i] = b0;
-          G3[(1 * MPAD + j) * gs + i] = b1;
-          G3[(2 * MPAD + j) * gs + i] = b2;
-        }
-      }
+      tc_t_store<MPAD>(a, ti, warp * 32 + lane, t, form, gam_s, mu_s, act_s);
     }
   }
   if (timed_out) atomicOr(&st->error, static_cast<int>(kErrTimeout));
@@ -782,13 +864,11 @@ __global__ void __launch_bounds__(kTcFusedThreads, 1) tc_y_fused_kernel(const Tc
     if (lane == 0) {
       tmap_acquire(&maps->a2f);
       tmap_acquire(&maps->g3);
-      if (!tc_fused_producer<NPAD>(
-              S, max(0, ce - cb),
-              [&](int it, int* c, int* tr) {
-                *c = cb + it;
-                *tr = rb;
-              },
-              maps, true)) {
+      const auto coord = [&](int it, int* c, int* tr) {
+        *c = cb + it;
+        *tr = rb;
+      };
+      if (!tc_fused_producer<NPAD>(S, max(0, ce - cb), coord, coord, maps, true)) {
         timed_out = true;
         *S.acc.abort_flag = 1;
       }
@@ -836,6 +916,8 @@ __global__ void __launch_bounds__(kTcFusedThreads, 1) tc_y_fused_kernel(const Tc
 }
 
 // ---------------------------------------------------------------- host
+
+int tc_t_ctas_per_sm(int npad, int na, bool fused) { return fused ? 1 : tc_ctas_per_sm(npad, na); }
 
 int tc_smem_bytes(int npad, int na) {
   return tc_stages(npad, na) * (na * static_cast<int>(kTcA) + npad * 128) + 1024 + 512;
@@ -963,8 +1045,10 @@ static void launch_tc_npad(const TcArgs& a, int nsm, cudaStream_t s) {
   }();
   (void)once;
   const int smem = tc_smem_bytes(NPAD, NA);
-  tc_prep_kernel<<<(a.p + 255) / 256, 256, 0, s>>>(a);
-  tc_t_kernel<NPAD, NA><<<std::max(1, std::min(a.ntile1, tc_ctas_per_sm(NPAD, NA) * nsm)), kTcThreads, smem, s>>>(a);
+  tc_prep_kernel<<<dim3((a.p + 255) / 256, a.mpad), 256, 0, s>>>(a);
+  tc_t_kernel<NPAD, NA><<<std::max(1, std::min(a.ntile1 * a.ksplit1, tc_ctas_per_sm(NPAD, NA) * nsm)), kTcThreads,
+                          smem, s>>>(a);
+  if (a.ksplit1 > 1) tc_t_combine_kernel<NPAD / 3><<<dim3((a.n + 255) / 256, NPAD / 3), 256, 0, s>>>(a);
   tc_y_kernel<NPAD, NA><<<dim3(a.nrow2, a.nsplit2), kTcThreads, smem, s>>>(a);
 }
 
@@ -977,8 +1061,9 @@ static void launch_tc_fused_npad(const TcArgs& a, int nsm, cudaStream_t s) {
   }();
   (void)once;
   const int smem = tc_fused_smem(NPAD);
-  tc_prep_kernel<<<(a.p + 255) / 256, 256, 0, s>>>(a);
-  tc_t_fused_kernel<NPAD><<<std::max(1, std::min(a.ntile1, nsm)), kTcFusedThreads, smem, s>>>(a);
+  tc_prep_kernel<<<dim3((a.p + 255) / 256, a.mpad), 256, 0, s>>>(a);
+  tc_t_fused_kernel<NPAD><<<std::max(1, std::min(a.ntile1 * a.ksplit1, nsm)), kTcFusedThreads, smem, s>>>(a);
+  if (a.ksplit1 > 1) tc_t_combine_kernel<NPAD / 3><<<dim3((a.n + 255) / 256, NPAD / 3), 256, 0, s>>>(a);
   tc_y_fused_kernel<NPAD><<<dim3(a.nrow2, a.nsplit2), kTcFusedThreads, smem, s>>>(a);
 }
 

@@ -54,6 +54,8 @@ struct TcMaps {
   CUtensorMap a2f;    // float A, box 32 rows x 64 columns (fused Y pass)
 };
 
+constexpr int kTcMaxSplit1 = 8;  // T pass: at most this many row ranges per column tile
+
 struct TcArgs {
   const IO* io;
   State* st;
@@ -64,6 +66,8 @@ struct TcArgs {
   int p_pad, n_pad;   // row strides (elements) of X3^T and G3^T
   int ntile1;         // ceil(n / 128)
   int kchunks1;       // ceil(p / 64)
+  int ksplit1;        // T pass: row ranges per column tile (partial T summed by a combine step when > 1)
+  int kcs1;           // 64-row chunks per row range
   int nchunks2;       // ceil(n / 64)
   int kps2;           // 64-column chunks per Y-pass split
   int nsplit2;        // Y-pass splits of the columns
@@ -84,5 +88,7 @@ int tc_fused_smem_bytes(int npad);
 // solve); ldc = p_pad
 void launch_tc_convert(int dtype, const IO* io, int64_t p, int64_t n, int64_t ld, int64_t ldc, cudaStream_t s);
 void launch_tc_sweep(const TcArgs& a, int npad, cudaStream_t s);
+// CTAs of the T pass resident per SM (1 or 2) for a geometry.
+int tc_t_ctas_per_sm(int npad, int na, bool fused);
 
 }  // namespace gpspca

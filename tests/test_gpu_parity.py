@@ -223,6 +223,42 @@ def test_tensor_core_sweep_edge_shapes(ctx, dtype, form, p, n, m):
                        iters_slack=0)
 
 
+@pytest.mark.parametrize("dtype,form,p,n,m", [
+    ("f32", "BL1", 2100, 3000, 16),     # float read in place; 4 row ranges, the last one shorter
+    ("f32", "SL1", 8000, 2000, 16),     # 8 row ranges (the most)
+    ("f32-ld", "SL0", 2100, 3000, 16),  # float with an odd column stride: planes copied once per solve
+    ("bf16", "SL1", 3000, 2500, 64),    # N = 192 on bf16 storage
+])
+def test_tensor_core_t_pass_row_ranges(ctx, dtype, form, p, n, m):
+    """Long columns on few 128-column tiles: the T pass splits each tile's rows
+    into ranges (partial T summed in range order before the threshold).
+    Against the oracle on the stored values, 4 sweeps from the start; two runs
+    give the same bits."""
+    block = form.startswith("B")
+    k = m if block else 3
+    At = synth.planted_spike(p, n, k, [100.0 / np.sqrt(j) for j in range(1, k + 1)], support_frac=0.02, seed=41,
+                             dtype=np.float32)
+    if dtype == "bf16":
+        tA, deq = _bf16(At)
+        tA = tA.cuda()
+    elif dtype == "f32-ld":
+        wide = torch.zeros(n, p + 1)
+        wide[:, :p] = torch.from_numpy(At)
+        tA, deq = wide.cuda()[:, :p], At
+    else:
+        tA, deq = torch.from_numpy(At).cuda(), At
+    A = deq.astype(np.float64).T
+    rho = [0.02] * m if block else list(synth.log_spaced_rho(m, 0.005, 0.2))
+    gam = _gammas(A, form, rho)
+    mu = [1.0] * m if block else None
+    ref = oracle.gpower(A, form, gam, mu=mu, tol=0.0, maxit=4)
+    res = ctx.solve(tA, form, list(gam), mu=mu, tol=0.0, maxit=4)
+    assert_matches(form, gpu_arrays(res), ref, oracle.column_norms(A), tol_z=5e-5, tol_f=1e-6, tol_x=5e-5,
+                   iters_slack=0)
+    again = ctx.solve(tA, form, list(gam), mu=mu, tol=0.0, maxit=4)
+    assert torch.equal(res.Z, again.Z) and torch.equal(res.X, again.X)
+
+
 def test_tensor_core_and_cuda_core_sweeps_agree(ctx):
     """The same solve with and without the tensor cores: float-rounding
     differences only, on the well-determined quantities (the objective, and
