@@ -34,7 +34,7 @@ RHO32 = 0.01
 # from an ncu capture of the current kernels (dram__bytes_read.sum +
 # dram__bytes_write.sum)
 TRAFFIC_SL1 = 403.40e6
-TRAFFIC_BL1 = 404.11e6
+TRAFFIC_BL1 = None
 METRIC = "GPower iters/s"
 UNIT = "iters/s"
 WORKLOAD = "planted spikes 5000x20000 fp32 (5 spikes, theta_j=40/j, 5% supports), SL1+SL0+BL1+BL0 (m=5, mu=1 and mu=[1,.9,.8,.7,.6]), gamma=0.05*max||a_i||, tol 1e-6"
@@ -249,7 +249,7 @@ def run_gpu(args):
                    "l2": "inputs larger than L2 (A is 400 MB)", "parallelism": "replicas" if ws > 1 else "1 gpu"},
         # the dominant kernel of the step by launch time (about 58%): the
         # block m = 5 sweep; the single-unit sweep beside it
-        "roofline": {"bound": "hbm", "kernel": "sweep_kernel<float,5,2> (block m=5 fused sweep)",
+        "roofline": {"bound": "hbm", "kernel": "sweep_kernel<float,5,3,full-width> (block m=5 fused sweep)",
                      "achieved": round(ach_blk, 1), "peak": peak, "unit": "GB/s", "frac": round(ach_blk / peak, 4),
                      "peak_source": peak_kind, "traffic": TRAFFIC_BL1, "ms_per_launch": round(ms_blk, 5),
                      "algorithmic_bytes_per_launch": bytes_a,
