@@ -34,7 +34,7 @@ RHO32 = 0.01
 # from an ncu capture of the current kernels (dram__bytes_read.sum +
 # dram__bytes_write.sum)
 TRAFFIC_SL1 = 403.40e6
-TRAFFIC_BL1 = None
+TRAFFIC_BL1 = 404.02e6
 METRIC = "GPower iters/s"
 UNIT = "iters/s"
 WORKLOAD = "planted spikes 5000x20000 fp32 (5 spikes, theta_j=40/j, 5% supports), SL1+SL0+BL1+BL0 (m=5, mu=1 and mu=[1,.9,.8,.7,.6]), gamma=0.05*max||a_i||, tol 1e-6"
@@ -247,7 +247,8 @@ def run_gpu(args):
         "config": {"workload": WORKLOAD, "p": P, "n": N, "solves_per_step": len(CASES),
                    "sweeps_per_step": round(total_sweeps / args.steps, 2),
                    "l2": "inputs larger than L2 (A is 400 MB)", "parallelism": "replicas" if ws > 1 else "1 gpu"},
-        # the dominant kernel of the step by launch time (about 58%): the
+        # the dominant kernel of the step by launch time (about 57% with its
+        # norm-forming variant): the
         # block m = 5 sweep; the single-unit sweep beside it
         "roofline": {"bound": "hbm", "kernel": "sweep_kernel<float,5,3,full-width> (block m=5 fused sweep)",
                      "achieved": round(ach_blk, 1), "peak": peak, "unit": "GB/s", "frac": round(ach_blk / peak, 4),
