@@ -248,8 +248,8 @@ def run_gpu(args):
                    "sweeps_per_step": round(total_sweeps / args.steps, 2),
                    "l2": "inputs larger than L2 (A is 400 MB)", "parallelism": "replicas" if ws > 1 else "1 gpu"},
         # the dominant kernel of the step by launch time (about 57% with its
-        # norm-forming variant): the
-        # block m = 5 sweep; the single-unit sweep beside it
+        # norm-forming variant): the block m = 5 sweep; the single-unit sweep
+        # beside it
         "roofline": {"bound": "hbm", "kernel": "sweep_kernel<float,5,3,full-width> (block m=5 fused sweep)",
                      "achieved": round(ach_blk, 1), "peak": peak, "unit": "GB/s", "frac": round(ach_blk / peak, 4),
                      "peak_source": peak_kind, "traffic": TRAFFIC_BL1, "ms_per_launch": round(ms_blk, 5),
