@@ -33,7 +33,7 @@ RHO32 = 0.01
 # dram bytes (read + write) of one launch of the fused sweeps on this matrix,
 # from an ncu capture of the current kernels (dram__bytes_read.sum +
 # dram__bytes_write.sum)
-TRAFFIC_SL1 = 403.40e6
+TRAFFIC_SL1 = None
 TRAFFIC_BL1 = 404.02e6
 METRIC = "GPower iters/s"
 UNIT = "iters/s"
@@ -255,7 +255,7 @@ def run_gpu(args):
                      "peak_source": peak_kind, "traffic": TRAFFIC_BL1, "ms_per_launch": round(ms_blk, 5),
                      "algorithmic_bytes_per_launch": bytes_a,
                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch"},
-        "roofline_single_unit": {"bound": "hbm", "kernel": "sweep_kernel<float,1,2> (single-unit fused sweep)",
+        "roofline_single_unit": {"bound": "hbm", "kernel": "sweep_kernel<float,1,2,fixed-width 3> (single-unit fused sweep)",
                                  "achieved": round(ach_su, 1), "peak": peak, "unit": "GB/s",
                                  "frac": round(ach_su / peak, 4), "ms_per_launch": round(ms_su, 5),
                                  "traffic": TRAFFIC_SL1},

@@ -223,7 +223,7 @@ __host__ __device__ constexpr int sweep_kb(int mg) { return mg == 1 ? 8 : 32; }
 // NRM: the sweep also forms each column's squared norm (one more reduction
 // slot per column), for the block start's first power step, which reads A
 // anyway: the column norms then need no pass of their own.
-template <typename TA, int MG, int NCH, bool NRM = false, bool FULLW = false>
+template <typename TA, int MG, int NCH, bool NRM = false, int FW = 0>
 struct SweepCfg {
   using TC = typename Elem<TA>::TC;
   static constexpr int VEC = Elem<TA>::VEC;
@@ -235,9 +235,9 @@ struct SweepCfg {
   // part (addresses, loop state, loads in flight) measured with -Xptxas -v
   static constexpr int REGS = static_cast<int>(sizeof(TC) / 4) * (2 * R * MG + KB + (MG == 1 ? 64 : (MG == 2 ? 60 : 40)));
   // register arrays of x and y beyond this spill; such variants are not built;
-  // the full-width form exists for the float pairs only
-  static constexpr bool kBuilt =
-      static_cast<int>(sizeof(TC) / 4) * 2 * R * MG <= 160 && (!FULLW || (sizeof(TC) == 4 && VEC == 4));
+  // the fixed-width form exists for the float pairs only
+  static constexpr bool kBuilt = static_cast<int>(sizeof(TC) / 4) * 2 * R * MG <= 160 &&
+                                 (FW == 0 || (sizeof(TC) == 4 && VEC == 4 && FW >= 1 && FW <= WB));
   // each of the 4 SM sub-partitions holds a quarter of the CTA's warps in its
   // own 16K-register file: whole warps per sub-partition, times four
   static constexpr int WARPS_PER_SMSP = 16384 / (32 * REGS);
@@ -245,14 +245,14 @@ struct SweepCfg {
   static constexpr int MAXT = MAXT_RAW >= 1024 ? 1024 : (MAXT_RAW < 128 ? 128 : MAXT_RAW);
 };
 
-// FULLW: tiles are WB columns wide (a.W == WB).  The dot products and the
-// rank update then run every column slot of a tile without a test on the
-// tile's width, so the columns' chains interleave; the last tile's empty
+// FW > 0: tiles are exactly FW columns wide (a.W == FW).  The dot products
+// and the rank update then run every column slot of a tile without a test on
+// the tile's width, so the columns' chains interleave; the last tile's empty
 // slots hold zeros or earlier columns of A (the ring starts zeroed) and get
-// g = 0.
-template <typename TA, int MG, int NCH, bool NRM = false, bool FULLW = false>
-__global__ void __launch_bounds__(SweepCfg<TA, MG, NCH, NRM, FULLW>::MAXT, 1) sweep_kernel(const SweepArgs a) {
-  using Cfg = SweepCfg<TA, MG, NCH, NRM, FULLW>;
+// g = 0.  FW = 0: any width up to WB, each slot tested.
+template <typename TA, int MG, int NCH, bool NRM = false, int FW = 0>
+__global__ void __launch_bounds__(SweepCfg<TA, MG, NCH, NRM, FW>::MAXT, 1) sweep_kernel(const SweepArgs a) {
+  using Cfg = SweepCfg<TA, MG, NCH, NRM, FW>;
   constexpr int SL = Cfg::SL;
   using TC = typename Cfg::TC;
   constexpr int VEC = Cfg::VEC;
@@ -262,7 +262,8 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH, NRM, FULLW>::MAXT, 1) sw
 
   State* st = a.st;
   if (st->n_active == 0) return;  // uniform across the grid
-  if (a.W > WB || a.W < 1 || (FULLW && a.W != WB)) {  // a tile width this variant does not run: refuse
+  constexpr int WL = FW > 0 ? FW : WB;  // column slots a tile loop runs
+  if (a.W > WB || a.W < 1 || (FW > 0 && a.W != FW)) {  // a tile width this variant does not run: refuse
     if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(&st->error, static_cast<int>(kErrLaunch));
     return;
   }
@@ -320,7 +321,7 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH, NRM, FULLW>::MAXT, 1) sw
     wsm[idx] = (j < a.mg_valid) ? static_cast<TC>(st->W[l * m + a.j0 + j]) : TC(0);
   }
   const uint32_t bytes_per_col = static_cast<uint32_t>(align_up(rows_valid * static_cast<int>(sizeof(TA)), 16));
-  if constexpr (FULLW) {  // zero the ring before the first bulk copy lands in it
+  if constexpr (FW > 0) {  // zero the ring before the first bulk copy lands in it
     uint4* z = reinterpret_cast<uint4*>(smem);
     for (int i = tid; i < (S * L.stage_bytes + kRingSlack) / 16; i += nthr) z[i] = make_uint4(0u, 0u, 0u, 0u);
     fence_async_smem();
@@ -455,8 +456,8 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH, NRM, FULLW>::MAXT, 1) sw
     for (int i = 0; i < KB; ++i) pd[i] = 0;
     if constexpr (kPair) {
 #pragma unroll
-      for (int w = 0; w < WB; ++w) {
-        if (FULLW || w < wv) {
+      for (int w = 0; w < WL; ++w) {
+        if (FW > 0 || w < wv) {
           const TA* colp = sb + w * ps;
           uint64_t acc[SL];
 #pragma unroll
@@ -563,8 +564,8 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH, NRM, FULLW>::MAXT, 1) sw
       Tout[static_cast<int64_t>(a.j0 + jq) * n + c0 + wq] = t;
     // rank update y += g a over this thread's rows of the tile
 #pragma unroll
-    for (int w = 0; w < WB; ++w) {
-      if (FULLW || w < wv) {
+    for (int w = 0; w < WL; ++w) {
+      if (FW > 0 || w < wv) {
         TC gw[MG];
 #pragma unroll
         for (int j = 0; j < MG; ++j) gw[j] = __shfl_sync(0xffffffffu, g, w * SL + j);
@@ -629,10 +630,10 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH, NRM, FULLW>::MAXT, 1) sw
   if (C > 1) cluster_sync_all();  // no CTA leaves while a peer may read its shared memory
 }
 
-template <typename TA, int MG, int NCH, bool NRM = false, bool FULLW = false>
+template <typename TA, int MG, int NCH, bool NRM = false, int FW = 0>
 const void* sweep_kernel_ptr() {
-  if constexpr (SweepCfg<TA, MG, NCH, NRM, FULLW>::kBuilt) {
-    return reinterpret_cast<const void*>(&sweep_kernel<TA, MG, NCH, NRM, FULLW>);
+  if constexpr (SweepCfg<TA, MG, NCH, NRM, FW>::kBuilt) {
+    return reinterpret_cast<const void*>(&sweep_kernel<TA, MG, NCH, NRM, FW>);
   } else {
     return nullptr;
   }

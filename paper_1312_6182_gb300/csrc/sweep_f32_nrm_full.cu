@@ -7,9 +7,11 @@ namespace gpspca {
 
 #define GPSPCA_K(MG, NCH) \
   case MG * 10 + NCH:     \
-    return sweep_kernel_ptr<float, MG, NCH, true, true>();
+    return sweep_kernel_ptr<float, MG, NCH, true, sweep_kb(MG) / (MG + 1)>();
 
-const void* sweep_kernel_f32_nrm_full(int mg, int nch) {
+// fw: the tile width the pass runs; nullptr unless it is the variant's width
+const void* sweep_kernel_f32_nrm_full(int mg, int nch, int fw) {
+  if (fw != sweep_kb(mg) / (mg + 1)) return nullptr;
   switch (mg * 10 + nch) {
     GPSPCA_K(1, 1) GPSPCA_K(1, 2) GPSPCA_K(1, 3) GPSPCA_K(1, 4)
     GPSPCA_K(2, 1) GPSPCA_K(2, 2) GPSPCA_K(2, 3) GPSPCA_K(2, 4)
