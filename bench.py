@@ -33,7 +33,7 @@ RHO32 = 0.01
 # dram bytes (read + write) of one launch of the fused sweeps on this matrix,
 # from an ncu capture of the current kernels (dram__bytes_read.sum +
 # dram__bytes_write.sum)
-TRAFFIC_SL1 = None
+TRAFFIC_SL1 = 403.32e6
 TRAFFIC_BL1 = 404.02e6
 METRIC = "GPower iters/s"
 UNIT = "iters/s"
