@@ -1,16 +1,16 @@
-// Instantiations of the single-component fused sweep for A stored as float
-// with fixed-width tiles (every tile slot run without a width test), one per
-// tile width 1..8: the width of a single-unit pass follows the column length.
+// Instantiations of the fused sweep for A stored as float with fixed-width
+// tiles (every tile slot run without a width test), one component, tile widths 1-8 (a single-unit
+// pass's width follows the column length).
 #include "sweep.cuh"
 
 namespace gpspca {
 
 #define GPSPCA_K(NCH, FW) \
-  case NCH * 10 + FW:     \
+  case NCH * 100 + FW:    \
     return sweep_kernel_ptr<float, 1, NCH, false, FW>();
 
 const void* sweep_kernel_f32_full1(int nch, int fw) {
-  switch (nch * 10 + fw) {
+  switch (nch * 100 + fw) {
     GPSPCA_K(1, 1) GPSPCA_K(1, 2) GPSPCA_K(1, 3) GPSPCA_K(1, 4) GPSPCA_K(1, 5) GPSPCA_K(1, 6) GPSPCA_K(1, 7) GPSPCA_K(1, 8)
     GPSPCA_K(2, 1) GPSPCA_K(2, 2) GPSPCA_K(2, 3) GPSPCA_K(2, 4) GPSPCA_K(2, 5) GPSPCA_K(2, 6) GPSPCA_K(2, 7) GPSPCA_K(2, 8)
     GPSPCA_K(3, 1) GPSPCA_K(3, 2) GPSPCA_K(3, 3) GPSPCA_K(3, 4) GPSPCA_K(3, 5) GPSPCA_K(3, 6) GPSPCA_K(3, 7) GPSPCA_K(3, 8)
