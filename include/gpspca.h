@@ -66,7 +66,7 @@ typedef enum { GPSPCA_DEVICE = 0, GPSPCA_HOST = 1 } gpspca_location;
 #define GPSPCA_ETIMEDOUT (-4)     /* a device-side wait gave up; the context stays usable */
 #define GPSPCA_EDEGENERATE (-5)   /* block polar step met a rank-deficient Y; outputs hold the last valid X */
 #define GPSPCA_ECUDA (-6)         /* a CUDA runtime call failed */
-#define GPSPCA_ENOTFOUND (-7)     /* gpspca_poll: unknown or already collected ticket */
+#define GPSPCA_ENOTFOUND (-7)     /* gpspca_poll: unknown or already collected ticket; gpspca_tune_load: no file */
 
 /* Per-solve termination status, written to out->status[j]. */
 #define GPSPCA_CONVERGED 0   /* |f_k - f_{k-1}| < tol * f_{k-1} */
@@ -239,6 +239,34 @@ int gpspca_submit(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form, con
  * ticket.  Returns GPSPCA_PENDING, or the ticket's result code (as
  * gpspca_solve would return it) once, after which the ticket is forgotten. */
 int gpspca_poll(gpspca_ctx* ctx, uint64_t ticket, int32_t wait_us);
+
+/* Autotuner.  Times every candidate sweep layout for this problem (the
+ * tensor-core sweep where its storage type allows it, and every grouping of
+ * the components into CUDA-core passes of at most 8, 5, 4, 2 or 1 in
+ * clusters of 1, 2, 4 or 8 CTAs that fits on chip): for each, the start and
+ * projection as gpspca_solve runs them, one warm-up sweep, then `reps`
+ * sweeps between CUDA events.  The fastest layout is remembered for this
+ * shape (storage type, single-unit or block form, m, p, n, ld, alignment,
+ * tensor-core permission, SM count) by the context, and later solves of the
+ * shape use it; results are discarded.  *n_candidates receives the number of
+ * layouts timed, *ms_best the fastest one's milliseconds per sweep and
+ * *ms_default the planner's own choice's.  Arguments as gpspca_time_sweep.
+ * The tuned layout changes only the order of the float partial sums, not the
+ * iteration. */
+int gpspca_tune(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form, const double* gamma, int32_t m,
+                const double* mu, uint32_t flags, int32_t reps, int32_t* n_candidates, double* ms_best,
+                double* ms_default);
+
+/* Write the context's tuned layouts to a text file (a "gpspca-tune 1" line,
+ * then one "shape TAB layout TAB milliseconds" line per shape).  GPSPCA_EINVAL
+ * if the file cannot be written. */
+int gpspca_tune_save(gpspca_ctx* ctx, const char* path);
+
+/* Merge the tuned layouts of a file written by gpspca_tune_save into the
+ * context.  A layout is used only where the planner still offers it on this
+ * device (otherwise the default plan runs).  GPSPCA_ENOTFOUND if the file
+ * cannot be read, GPSPCA_EINVAL if it is not such a table (nothing merged). */
+int gpspca_tune_load(gpspca_ctx* ctx, const char* path);
 
 /* Measurement aid: prepare a solve (start and projection, as gpspca_solve
  * does), then time `reps` back-to-back launches of the fused sweep of one

@@ -39,7 +39,8 @@ ERROR_NAMES = {
 
 EXPORTED = ("gpspca_create", "gpspca_solve", "gpspca_submit", "gpspca_poll", "gpspca_destroy",
             "gpspca_last_error", "gpspca_time_sweep", "gpspca_sweep_static", "gpspca_synth_spikes",
-            "gpspca_solve_batch", "gpspca_solve_deflated", "gpspca_project")
+            "gpspca_solve_batch", "gpspca_solve_deflated", "gpspca_project", "gpspca_tune", "gpspca_tune_save",
+            "gpspca_tune_load")
 
 
 class Matrix(ctypes.Structure):
@@ -125,6 +126,13 @@ def load(path: str = LIB_PATH):
     lib.gpspca_synth_spikes.restype = ctypes.c_int
     lib.gpspca_solve_batch.argtypes = [P, ctypes.c_int32, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_int32)]
     lib.gpspca_solve_batch.restype = ctypes.c_int
+    lib.gpspca_tune.argtypes = [P, ctypes.POINTER(Matrix), ctypes.c_int, D, ctypes.c_int32, D, ctypes.c_uint32,
+                                ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), D, D]
+    lib.gpspca_tune.restype = ctypes.c_int
+    lib.gpspca_tune_save.argtypes = [P, ctypes.c_char_p]
+    lib.gpspca_tune_save.restype = ctypes.c_int
+    lib.gpspca_tune_load.argtypes = [P, ctypes.c_char_p]
+    lib.gpspca_tune_load.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -412,6 +420,30 @@ class Context:
                                           | (0 if tensor_cores else NO_TENSOR_CORES), int(reps),
                                           ctypes.byref(ms)))
         return ms.value
+
+
+    def tune(self, At, form: str, gamma, mu=None, reps: int = 10, gamma_relative: bool = False,
+             p: Optional[int] = None, col_scale=None, tensor_cores: bool = True):
+        """Time every candidate sweep layout for this shape and keep the fastest
+        (gpspca_tune).  Returns (layouts timed, best ms per sweep, default ms)."""
+        gamma = [float(g) for g in (gamma if hasattr(gamma, "__len__") else [gamma])]
+        m = len(gamma)
+        M = matrix(At, p, col_scale)
+        self._sync_torch(At)
+        nc, best, dflt = ctypes.c_int32(), ctypes.c_double(), ctypes.c_double()
+        _check(self.lib.gpspca_tune(self.ptr, ctypes.byref(M), FORMS[form], _darr(gamma, m), m, _darr(mu, m),
+                                    (GAMMA_RELATIVE if gamma_relative else 0)
+                                    | (0 if tensor_cores else NO_TENSOR_CORES), int(reps), ctypes.byref(nc),
+                                    ctypes.byref(best), ctypes.byref(dflt)))
+        return nc.value, best.value, dflt.value
+
+    def tune_save(self, path: str):
+        """Write the tuned layouts to a file (gpspca_tune_save)."""
+        _check(self.lib.gpspca_tune_save(self.ptr, str(path).encode()))
+
+    def tune_load(self, path: str):
+        """Merge the tuned layouts of a file into this context (gpspca_tune_load)."""
+        _check(self.lib.gpspca_tune_load(self.ptr, str(path).encode()))
 
 
 def sweep_static(At, form: str, gamma: float, x, x_next, t, objective, p: Optional[int] = None, stream=None) -> int:

@@ -265,8 +265,37 @@ static void plan_tc_ksplit(Plan* pl, int nsm) {
   pl->ksplit1 = (pl->kchunks1 + pl->kcs1 - 1) / pl->kcs1;
 }
 
+// The CUDA-core passes of `m` components in groups of at most gmax, each
+// pass in clusters of C CTAs; false if some pass does not fit.
+static bool cuda_layout(int dt, int m, int64_t p, int unit, int gmax, int C, int* ps_out, std::vector<Pass>* out) {
+  const int ps = static_cast<int>(((p + C - 1) / C + unit - 1) / unit * unit);
+  if (C > 1 && static_cast<int64_t>(C - 1) * ps >= p) return false;
+  std::vector<Pass> passes;
+  int j0 = 0;
+  for (auto g : split_components(m, gmax)) {
+    Pass q;
+    if (!fit_pass(dt, g.first, C, ps, m, &q)) return false;
+    q.j0 = j0;
+    q.mgv = g.second;
+    j0 += g.second;
+    passes.push_back(q);
+  }
+  *ps_out = ps;
+  *out = passes;
+  return true;
+}
+
+static bool same_passes(const std::vector<Pass>& a, const std::vector<Pass>& b) {
+  if (a.size() != b.size()) return false;
+  for (size_t i = 0; i < a.size(); ++i)
+    if (a[i].mg != b[i].mg || a[i].mgv != b[i].mgv || a[i].k != b[i].k || a[i].threads != b[i].threads ||
+        a[i].W != b[i].W || a[i].S != b[i].S)
+      return false;
+  return true;
+}
+
 int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fast, int nsm, Plan* P,
-              bool allow_tc) {
+              bool allow_tc, int cand, int* ncand) {
   const DInfo d = dinfo(dt);
   Plan pl;
   pl.dtype = dt;
@@ -279,59 +308,76 @@ int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fa
   pl.tcsize = d.tcsize;
   pl.esize = d.esize;
   const int unit = std::max(d.align, d.vec);
-  bool found = false;
-  // the tensor-core sweep where the CUDA-core passes become compute-bound:
-  // bf16 storage from 6 components (or gamma values) on, read in place when
-  // its layout suits TMA (16-byte aligned base and column stride) and copied
-  // once per solve into a padded layout otherwise; float A as three bf16
-  // planes and fp8 A as one, copied once per solve, from 9 on (one CUDA-core
-  // pass covers up to 8).  Crossovers measured on GB300 over p x n in
-  // {5000 x 20000, 2000 x 60000, 8000 x 8000}.
-  const bool native_bf16 = dt == GPSPCA_BF16 && fast && ld % 8 == 0;
+  // Candidate layouts, the planner's default first: the tensor-core sweep
+  // where the CUDA-core passes become compute-bound: bf16 storage from 6
+  // components (or gamma values) on, read in place when its layout suits TMA
+  // (16-byte aligned base and column stride) and copied once per solve into
+  // a padded layout otherwise; float A as three bf16 planes and fp8 A as one,
+  // from 9 on (one CUDA-core pass covers up to 8).  Crossovers measured on
+  // GB300 over p x n in {5000 x 20000, 2000 x 60000, 8000 x 8000}.  Otherwise
+  // the widest CUDA-core passes first (fewest reads of A) in the smallest
+  // clusters that fit; long columns (large p) may only fit narrower passes,
+  // whose per-thread register tiles are smaller.  The other candidates (the
+  // autotuner times them all): the tensor-core sweep from 2 components, and
+  // every pass grouping of at most 8, 5, 4, 2 or 1 components in clusters of
+  // 1, 2, 4 or 8 that fits.
+  struct Layout {
+    bool tc;
+    int C, ps;
+    std::vector<Pass> passes;
+  };
+  std::vector<Layout> lay;
+  const bool tc_type = dt == GPSPCA_BF16 || dt == GPSPCA_F32 || dt == GPSPCA_FP8_E4M3;
   const int tc_min_m = dt == GPSPCA_BF16 ? 6 : 9;
-  if (allow_tc && m >= tc_min_m && p >= 1 && n >= 1 &&
-      (dt == GPSPCA_BF16 || dt == GPSPCA_F32 || dt == GPSPCA_FP8_E4M3)) {
+  const bool tc_default = allow_tc && tc_type && m >= tc_min_m && p >= 1 && n >= 1;
+  if (tc_default) lay.push_back({true, 1, static_cast<int>(p), {}});
+  for (int gmax : {8, 4, 2, 1}) {
+    if (!lay.empty()) break;
+    for (int C : {1, 2, 4, 8}) {
+      Layout L{false, C, 0, {}};
+      if (cuda_layout(dt, m, p, unit, gmax, C, &L.ps, &L.passes)) {
+        lay.push_back(L);
+        break;
+      }
+    }
+  }
+  if (lay.empty())
+    return fail(GPSPCA_EINVAL, "no sweep configuration fits p=%lld (rows too long for the on-chip tile ring)",
+                (long long)p);
+  if (cand > 0 || ncand) {  // the alternatives, only when asked for (they cost a fit per variant)
+    if (!tc_default && allow_tc && tc_type && m >= 2 && p >= 1 && n >= 1)
+      lay.push_back({true, 1, static_cast<int>(p), {}});
+    for (int gmax : {8, 5, 4, 2, 1})
+      for (int C : {1, 2, 4, 8}) {
+        Layout L{false, C, 0, {}};
+        if (!cuda_layout(dt, m, p, unit, gmax, C, &L.ps, &L.passes)) continue;
+        bool dup = false;
+        for (const Layout& o : lay) dup = dup || (!o.tc && o.C == L.C && same_passes(o.passes, L.passes));
+        if (!dup) lay.push_back(L);
+      }
+  }
+  if (ncand) *ncand = static_cast<int>(lay.size());
+  const int pick = cand < 0 ? 0 : cand;
+  if (pick >= static_cast<int>(lay.size()))
+    return fail(GPSPCA_EINVAL, "plan candidate %d of %d", pick, static_cast<int>(lay.size()));
+  const Layout& L = lay[pick];
+  if (L.tc) {
     plan_tc(&pl, m, p, n, nsm);
     pl.tc_na = dt == GPSPCA_F32 ? 3 : 1;
     // float A that TMA can read (16-byte aligned base and column stride) is
     // split into its planes in shared memory; other float / fp8 / bf16
     // layouts are copied once per solve
+    const bool native_bf16 = dt == GPSPCA_BF16 && fast && ld % 8 == 0;
     pl.tc_fused = (dt == GPSPCA_F32 && fast && ld % 4 == 0) ? 1 : 0;
     pl.tc_convert = (native_bf16 || pl.tc_fused) ? 0 : 1;
     plan_tc_ksplit(&pl, nsm);
     pl.C = 1;
     pl.ps = static_cast<int>(p);
-    found = true;
+  } else {
+    pl.C = L.C;
+    pl.ps = L.ps;
+    pl.passes = L.passes;
   }
-  // widest passes first (fewest reads of A); long columns (large p) may only
-  // fit narrower passes, whose per-thread register tiles are smaller
-  for (int gmax : {8, 4, 2, 1}) {
-    if (found) break;
-    const auto groups = split_components(m, gmax);
-    for (int C : {1, 2, 4, 8}) {
-      const int ps = static_cast<int>(((p + C - 1) / C + unit - 1) / unit * unit);
-      if (C > 1 && static_cast<int64_t>(C - 1) * ps >= p) break;
-      std::vector<Pass> passes;
-      bool ok = true;
-      int j0 = 0;
-      for (auto g : groups) {
-        Pass q;
-        if (!fit_pass(dt, g.first, C, ps, m, &q)) { ok = false; break; }
-        q.j0 = j0;
-        q.mgv = g.second;
-        j0 += g.second;
-        passes.push_back(q);
-      }
-      if (!ok) continue;
-      pl.C = C;
-      pl.ps = ps;
-      pl.passes = passes;
-      found = true;
-      break;
-    }
-    if (found) break;
-  }
-  if (!found) return fail(GPSPCA_EINVAL, "no sweep configuration fits p=%lld (rows too long for the on-chip tile ring)", (long long)p);
   // clusters: as many as can be co-resident for the heaviest pass (the
   // tensor-core sweep's Y-pass splits play their part)
   int ncl = pl.tc ? pl.nsplit2 : nsm / pl.C;
@@ -403,6 +449,21 @@ struct Budget {
   size_t limit = 0, used = 0;
 };
 
+// Autotuned sweep layouts of a context: problem shape (tune_shape) -> the
+// key (Plan::key) of the candidate layout that timed fastest, and its time.
+struct TuneTable {
+  std::mutex mu;
+  std::unordered_map<std::string, std::pair<std::string, double>> best;
+};
+
+static std::string tune_shape(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fast, bool allow_tc,
+                              int nsm) {
+  char b[160];
+  snprintf(b, sizeof(b), "d%d/%s/m%d/p%lld/n%lld/ld%lld/f%d/tc%d/sm%d", dt, form >= 2 ? "block" : "single", m,
+           (long long)p, (long long)n, (long long)ld, fast ? 1 : 0, allow_tc ? 1 : 0, nsm);
+  return b;
+}
+
 struct Slot {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -414,6 +475,7 @@ struct Slot {
   State* st_host = nullptr;  // pinned
   cudaEvent_t done = nullptr;
   Budget* budget = nullptr;
+  TuneTable* tune = nullptr;  // the context's autotuned layouts
   // workspace buffers, grown on demand
   DevBuf b_cnorm, b_P, b_Y, b_ypart, b_T, b_fpart, b_gpart, b_x3, b_g3, b_maps, b_planes, b_tpart;
   TcMaps* maps_host = nullptr;  // pinned: the tensor maps copied to b_maps before a solve
@@ -480,9 +542,10 @@ static void release_workspace(Slot* s) {
     release(s, b);
 }
 
-static int slot_init(Slot* s, int device, cudaStream_t user_stream, Budget* budget) {
+static int slot_init(Slot* s, int device, cudaStream_t user_stream, Budget* budget, TuneTable* tune) {
   s->device = device;
   s->budget = budget;
+  s->tune = tune;
   if (user_stream) {
     s->stream = user_stream;
   } else {
@@ -757,7 +820,11 @@ static int solve_empty(Slot* s, const Request& r) {
 // Validate, plan, size the workspace and write the IO record for one solve
 // (asynchronous, on the slot's stream).  scratch_out: results go to library
 // staging buffers and are not copied anywhere (used by the sweep timer).
-static int prepare_solve(Slot* s, const Request& r, int nsm, bool scratch_out, Plan* plan, bool* empty) {
+// cand >= 0: candidate layout `cand` of the autotuner's list (*ncand its
+// length); cand < 0: the tuned layout of this shape if the context has one,
+// else the planner's default.  *shape (if given): the shape's tuning key.
+static int prepare_solve(Slot* s, const Request& r, int nsm, bool scratch_out, Plan* plan, bool* empty,
+                         int cand = -1, int* ncand = nullptr, std::string* shape = nullptr) {
   *empty = false;
   int rc = validate(r);
   if (rc != GPSPCA_OK) return rc;
@@ -793,8 +860,31 @@ static int prepare_solve(Slot* s, const Request& r, int nsm, bool scratch_out, P
   const bool fast = (reinterpret_cast<uintptr_t>(A_dev) % 16 == 0) && ((ld * d.esize) % 16 == 0);
   Plan& pl = *plan;
   const bool allow_tc = !(r.flags & GPSPCA_NO_TENSOR_CORES) && tc_supported(s->device);
-  if ((rc = make_plan(r.A.dtype, r.form, m, p, n, ld, fast, nsm, &pl, allow_tc))) return rc;
-  pl.pca = (r.form >= GPSPCA_BL1 && !r.x0) ? 1 : 0;
+  const int pca = (r.form >= GPSPCA_BL1 && !r.x0) ? 1 : 0;
+  const std::string shape_key = tune_shape(r.A.dtype, r.form, m, p, n, ld, fast, allow_tc, nsm);
+  if (shape) *shape = shape_key;
+  std::string tuned;
+  if (cand < 0 && s->tune) {
+    std::lock_guard<std::mutex> lk(s->tune->mu);
+    auto it = s->tune->best.find(shape_key);
+    if (it != s->tune->best.end()) tuned = it->second.first;
+  }
+  bool picked = false;
+  if (!tuned.empty()) {  // the candidate whose plan key was stored (the default if none matches)
+    int nc = 0;
+    if (make_plan(r.A.dtype, r.form, m, p, n, ld, fast, nsm, &pl, allow_tc, 0, &nc) == GPSPCA_OK)
+      for (int c = 0; c < nc && !picked; ++c) {
+        Plan q;
+        if (make_plan(r.A.dtype, r.form, m, p, n, ld, fast, nsm, &q, allow_tc, c) != GPSPCA_OK) continue;
+        q.pca = pca;
+        if (q.key() == tuned) {
+          pl = q;
+          picked = true;
+        }
+      }
+  }
+  if (!picked && (rc = make_plan(r.A.dtype, r.form, m, p, n, ld, fast, nsm, &pl, allow_tc, cand, ncand))) return rc;
+  pl.pca = pca;
   if ((rc = ensure(s, &s->b_cnorm, pl.ws_cnorm))) return rc;
   if ((rc = ensure(s, &s->b_P, pl.ws_P))) return rc;
   if ((rc = ensure(s, &s->b_Y, pl.ws_P))) return rc;
@@ -973,6 +1063,7 @@ struct gpspca_ctx {
   int device = 0;
   int nsm = 0;
   Budget budget;
+  TuneTable tune;
   Slot sync_slot;
   std::mutex solve_mu;  // one synchronous solve at a time on sync_slot
   // serving
@@ -1086,7 +1177,7 @@ int gpspca_create(gpspca_ctx** out, int device, size_t hbm_budget_bytes, void* c
   size_t fr = 0, tot = 0;
   cudaMemGetInfo(&fr, &tot);
   ctx->budget.limit = hbm_budget_bytes ? hbm_budget_bytes : static_cast<size_t>(0.9 * fr);
-  int rc = slot_init(&ctx->sync_slot, device, static_cast<cudaStream_t>(cuda_stream), &ctx->budget);
+  int rc = slot_init(&ctx->sync_slot, device, static_cast<cudaStream_t>(cuda_stream), &ctx->budget, &ctx->tune);
   if (rc != GPSPCA_OK) {
     slot_free(&ctx->sync_slot);
     delete ctx;
@@ -1114,7 +1205,7 @@ int gpspca_solve_batch(gpspca_ctx* ctx, int32_t count, const gpspca_request* req
   const int nb = std::min(count, kBatchSlots);
   while (static_cast<int>(ctx->batch_slots.size()) < nb) {
     auto s = std::make_unique<Slot>();
-    const int rc = slot_init(s.get(), ctx->device, nullptr, &ctx->budget);
+    const int rc = slot_init(s.get(), ctx->device, nullptr, &ctx->budget, &ctx->tune);
     if (rc != GPSPCA_OK) {
       slot_free(s.get());
       return rc;
@@ -1403,6 +1494,129 @@ int gpspca_time_sweep(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form,
   return GPSPCA_OK;
 }
 
+// Time one prepared plan's sweep: start and projection as a solve does,
+// one warm-up sweep, then `reps` sweeps between CUDA events.
+static int time_plan(Slot* s, const Plan& pl, int reps, double* ms_per_sweep) {
+  GP_CUDA(launch_prologue(pl, s, s->stream, cudaGraphConditionalHandle{}, pl.pca != 0, 0));
+  cudaEvent_t e0, e1;
+  GP_CUDA(cudaEventCreate(&e0));
+  GP_CUDA(cudaEventCreate(&e1));
+  GP_CUDA(launch_sweeps(pl, s, s->stream));  // warm-up
+  GP_CUDA(cudaEventRecord(e0, s->stream));
+  for (int i = 0; i < reps; ++i) GP_CUDA(launch_sweeps(pl, s, s->stream));
+  GP_CUDA(cudaEventRecord(e1, s->stream));
+  GP_CUDA(cudaEventSynchronize(e1));
+  GP_CUDA(cudaGetLastError());
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  GP_CUDA(cudaMemcpy(s->st_host, s->st_dev, sizeof(State), cudaMemcpyDeviceToHost));
+  if (s->st_host->error & kErrTimeout) return fail(GPSPCA_ETIMEDOUT, "a device-side wait for a tile copy gave up");
+  if (s->st_host->error & kErrLaunch) return fail(GPSPCA_ECUDA, "a sweep refused its launch geometry");
+  if (s->st_host->n_active == 0) return fail(GPSPCA_EINVAL, "the start is degenerate or A is zero: nothing to time");
+  *ms_per_sweep = static_cast<double>(ms) / reps;
+  return GPSPCA_OK;
+}
+
+int gpspca_tune(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form, const double* gamma, int32_t m,
+                const double* mu, uint32_t flags, int32_t reps, int32_t* n_candidates, double* ms_best,
+                double* ms_default) {
+  if (!ctx || !n_candidates || !ms_best || !ms_default)
+    return fail(GPSPCA_EINVAL, "ctx and the result pointers must not be NULL");
+  if (reps < 1) return fail(GPSPCA_EINVAL, "reps must be >= 1");
+  gpspca_out dummy = {};
+  dummy.location = GPSPCA_DEVICE;
+  double one = 0.0;
+  dummy.X = dummy.Z = dummy.objective = &one;  // replaced by staging buffers
+  dummy.iters = dummy.status = reinterpret_cast<int32_t*>(&one);
+  Request r;
+  int rc = request_from(&r, A, form, gamma, m, mu, 0.0, 1 << 30, nullptr, flags, &dummy);
+  if (rc != GPSPCA_OK) return rc;
+  std::lock_guard<std::mutex> lk(ctx->solve_mu);
+  GP_CUDA(cudaSetDevice(ctx->device));
+  Slot* s = &ctx->sync_slot;
+  int nc = 0;
+  double best = 0.0, def = 0.0;
+  std::string best_key, shape;
+  for (int c = 0; c == 0 || c < nc; ++c) {
+    Plan pl;
+    bool empty = false;
+    rc = prepare_solve(s, r, ctx->nsm, true, &pl, &empty, c, c == 0 ? &nc : nullptr, c == 0 ? &shape : nullptr);
+    if (rc == GPSPCA_ENOMEM && c > 0) continue;  // a candidate whose workspace does not fit the budget
+    if (rc != GPSPCA_OK) return rc;
+    if (empty) return fail(GPSPCA_EINVAL, "empty matrix");
+    double ms = 0.0;
+    if ((rc = time_plan(s, pl, reps, &ms)) != GPSPCA_OK) return rc;
+    if (c == 0) def = ms;
+    if (c == 0 || ms < best) {
+      best = ms;
+      best_key = pl.key();
+    }
+  }
+  {
+    std::lock_guard<std::mutex> tl(ctx->tune.mu);
+    ctx->tune.best[shape] = {best_key, best};
+  }
+  *n_candidates = nc;
+  *ms_best = best;
+  *ms_default = def;
+  return GPSPCA_OK;
+}
+
+int gpspca_tune_save(gpspca_ctx* ctx, const char* path) {
+  if (!ctx || !path) return fail(GPSPCA_EINVAL, "ctx and path must not be NULL");
+  FILE* f = fopen(path, "w");
+  if (!f) return fail(GPSPCA_EINVAL, "cannot write %s", path);
+  fprintf(f, "gpspca-tune 1\n");
+  {
+    std::lock_guard<std::mutex> tl(ctx->tune.mu);
+    for (const auto& kv : ctx->tune.best)
+      fprintf(f, "%s\t%s\t%.6f\n", kv.first.c_str(), kv.second.first.c_str(), kv.second.second);
+  }
+  const bool ok = fclose(f) == 0;
+  return ok ? GPSPCA_OK : fail(GPSPCA_EINVAL, "cannot write %s", path);
+}
+
+int gpspca_tune_load(gpspca_ctx* ctx, const char* path) {
+  if (!ctx || !path) return fail(GPSPCA_EINVAL, "ctx and path must not be NULL");
+  FILE* f = fopen(path, "r");
+  if (!f) return fail(GPSPCA_ENOTFOUND, "cannot read %s", path);
+  std::vector<std::pair<std::string, std::pair<std::string, double>>> rows;
+  char line[4096];
+  bool header = false, bad = false;
+  while (fgets(line, sizeof(line), f)) {
+    std::string l(line);
+    while (!l.empty() && (l.back() == '\n' || l.back() == '\r')) l.pop_back();
+    if (!header) {
+      header = true;
+      if (l != "gpspca-tune 1") {
+        bad = true;
+        break;
+      }
+      continue;
+    }
+    if (l.empty()) continue;
+    const size_t t1 = l.find('\t'), t2 = t1 == std::string::npos ? t1 : l.find('\t', t1 + 1);
+    if (t1 == std::string::npos || t2 == std::string::npos || t1 == 0 || t2 == t1 + 1) {
+      bad = true;
+      break;
+    }
+    char* end = nullptr;
+    const double ms = strtod(l.c_str() + t2 + 1, &end);
+    if (end == l.c_str() + t2 + 1) {
+      bad = true;
+      break;
+    }
+    rows.push_back({l.substr(0, t1), {l.substr(t1 + 1, t2 - t1 - 1), ms}});
+  }
+  fclose(f);
+  if (bad || !header) return fail(GPSPCA_EINVAL, "%s is not a tuned-layout table", path);
+  std::lock_guard<std::mutex> tl(ctx->tune.mu);
+  for (auto& row : rows) ctx->tune.best[row.first] = row.second;
+  return GPSPCA_OK;
+}
+
 int gpspca_submit(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form, const double* gamma, int32_t m,
                   const double* mu, double tol, int32_t maxit, uint32_t flags, gpspca_out* out, uint64_t* ticket) {
   if (!ctx || !ticket) return fail(GPSPCA_EINVAL, "ctx and ticket must not be NULL");
@@ -1418,7 +1632,7 @@ int gpspca_submit(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form, con
     cudaSetDevice(ctx->device);
     for (int i = 0; i < kServeSlots; ++i) {
       auto s = std::make_unique<Slot>();
-      rc = slot_init(s.get(), ctx->device, nullptr, &ctx->budget);
+      rc = slot_init(s.get(), ctx->device, nullptr, &ctx->budget, &ctx->tune);
       if (rc != GPSPCA_OK) return rc;
       ctx->serve_slots.push_back(std::move(s));
     }

@@ -64,9 +64,11 @@ struct Plan {
 };
 
 // Plan a solve: cluster size, per-pass kernel variant, threads, tile ring;
-// or, with allow_tc and a wide bf16 problem, the tensor-core sweep.
+// or, with allow_tc and a wide problem, the tensor-core sweep.  cand < 0:
+// the planner's default; cand >= 0: candidate layout `cand` of the list the
+// autotuner times (0 is the default; *ncand receives the list's length).
 int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fast, int nsm, Plan* P,
-              bool allow_tc = false);
+              bool allow_tc = false, int cand = -1, int* ncand = nullptr);
 
 // Record `msg` as the calling thread's last error (gpspca_last_error) and return code.
 int record_error(int code, const char* msg);
