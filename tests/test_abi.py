@@ -59,3 +59,8 @@ def test_null_arguments_are_rejected_without_a_gpu(lib_path):
     assert lib.gpspca_poll(None, 1, 0) == binding.EINVAL
     assert lib.gpspca_destroy(None) == binding.OK
     assert b"NULL" in lib.gpspca_last_error()
+    nc, best, dflt = ctypes.c_int32(), ctypes.c_double(), ctypes.c_double()
+    assert lib.gpspca_tune(None, None, 0, None, 1, None, 0, 3, ctypes.byref(nc), ctypes.byref(best),
+                           ctypes.byref(dflt)) == binding.EINVAL
+    assert lib.gpspca_tune_save(None, b"/nonexistent/x") == binding.EINVAL
+    assert lib.gpspca_tune_load(None, b"/nonexistent/x") == binding.EINVAL
