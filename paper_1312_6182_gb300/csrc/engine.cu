@@ -450,10 +450,13 @@ struct Budget {
 };
 
 // Autotuned sweep layouts of a context: problem shape (tune_shape) -> the
-// key (Plan::key) of the candidate layout that timed fastest, and its time.
+// key (Plan::key) of the candidate layout that timed fastest, and its time;
+// and, once a solve has found that candidate among the planner's, its plan
+// (so later solves of the shape skip the search).
 struct TuneTable {
   std::mutex mu;
   std::unordered_map<std::string, std::pair<std::string, double>> best;
+  std::unordered_map<std::string, Plan> resolved;
 };
 
 static std::string tune_shape(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fast, bool allow_tc,
@@ -864,13 +867,20 @@ static int prepare_solve(Slot* s, const Request& r, int nsm, bool scratch_out, P
   const std::string shape_key = tune_shape(r.A.dtype, r.form, m, p, n, ld, fast, allow_tc, nsm);
   if (shape) *shape = shape_key;
   std::string tuned;
+  bool picked = false;
   if (cand < 0 && s->tune) {
     std::lock_guard<std::mutex> lk(s->tune->mu);
     auto it = s->tune->best.find(shape_key);
-    if (it != s->tune->best.end()) tuned = it->second.first;
+    if (it != s->tune->best.end()) {
+      tuned = it->second.first;
+      auto rv = s->tune->resolved.find(shape_key);
+      if (rv != s->tune->resolved.end() && rv->second.pca == pca && rv->second.key() == tuned) {
+        pl = rv->second;
+        picked = true;
+      }
+    }
   }
-  bool picked = false;
-  if (!tuned.empty()) {  // the candidate whose plan key was stored (the default if none matches)
+  if (!picked && !tuned.empty()) {  // the candidate whose plan key was stored (the default if none matches)
     int nc = 0;
     if (make_plan(r.A.dtype, r.form, m, p, n, ld, fast, nsm, &pl, allow_tc, 0, &nc) == GPSPCA_OK)
       for (int c = 0; c < nc && !picked; ++c) {
@@ -882,6 +892,10 @@ static int prepare_solve(Slot* s, const Request& r, int nsm, bool scratch_out, P
           picked = true;
         }
       }
+    if (picked) {
+      std::lock_guard<std::mutex> lk(s->tune->mu);
+      s->tune->resolved[shape_key] = pl;
+    }
   }
   if (!picked && (rc = make_plan(r.A.dtype, r.form, m, p, n, ld, fast, nsm, &pl, allow_tc, cand, ncand))) return rc;
   pl.pca = pca;
@@ -1557,6 +1571,7 @@ int gpspca_tune(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form, const
   {
     std::lock_guard<std::mutex> tl(ctx->tune.mu);
     ctx->tune.best[shape] = {best_key, best};
+    ctx->tune.resolved.erase(shape);
   }
   *n_candidates = nc;
   *ms_best = best;
@@ -1613,7 +1628,10 @@ int gpspca_tune_load(gpspca_ctx* ctx, const char* path) {
   fclose(f);
   if (bad || !header) return fail(GPSPCA_EINVAL, "%s is not a tuned-layout table", path);
   std::lock_guard<std::mutex> tl(ctx->tune.mu);
-  for (auto& row : rows) ctx->tune.best[row.first] = row.second;
+  for (auto& row : rows) {
+    ctx->tune.best[row.first] = row.second;
+    ctx->tune.resolved.erase(row.first);
+  }
   return GPSPCA_OK;
 }
 
