@@ -240,10 +240,12 @@ int gpspca_submit(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form, con
  * gpspca_solve would return it) once, after which the ticket is forgotten. */
 int gpspca_poll(gpspca_ctx* ctx, uint64_t ticket, int32_t wait_us);
 
-/* Autotuner.  Times every candidate sweep layout for this problem (the
- * tensor-core sweep where its storage type allows it, and every grouping of
- * the components into CUDA-core passes of at most 8, 5, 4, 2 or 1 in
- * clusters of 1, 2, 4 or 8 CTAs that fits on chip): for each, the start and
+/* Autotuner (the paper has no counterpart; it picks how the sweep of
+ * Section 2 / Table 1 is laid out on the GPU, not what it computes).  Times
+ * every candidate sweep layout for this problem (the tensor-core sweep where
+ * its storage type allows it, and every grouping of the components into
+ * CUDA-core passes of at most 8, 5, 4, 2 or 1 in clusters of 1, 2, 4 or 8
+ * CTAs that fits on chip): for each, the start and
  * projection as gpspca_solve runs them, one warm-up sweep, then `reps`
  * sweeps between CUDA events.  The fastest layout is remembered for this
  * shape (storage type, single-unit or block form, m, p, n, ld, alignment,
@@ -268,7 +270,8 @@ int gpspca_tune_save(gpspca_ctx* ctx, const char* path);
  * cannot be read, GPSPCA_EINVAL if it is not such a table (nothing merged). */
 int gpspca_tune_load(gpspca_ctx* ctx, const char* path);
 
-/* Measurement aid: prepare a solve (start and projection, as gpspca_solve
+/* Measurement aid (the paper has no counterpart): prepare a solve (start
+ * and projection, as gpspca_solve
  * does), then time `reps` back-to-back launches of the fused sweep of one
  * iteration (every component pass) on the context's stream with CUDA events.
  * *ms_per_sweep receives the mean milliseconds per sweep.  A must be on the
