@@ -1,12 +1,13 @@
 """Benchmark of the GB300 GP-SPCA hot path (one JSON line on rank 0).
 
-Workload (the four formulations in FP32 on planted sparse spikes): A is
-5000 x 20000 (p samples x n variables) = N(0,1) noise + sum_{j<=5}
-(40/j) u_j v_j^T with 5% disjoint Rademacher supports; gamma = 0.05
+Headline workload (the largest single-GPU configuration): A is 20000 x
+100000 FP32 (p samples x n variables, 8 GB) = N(0,1) noise + sum_{j<=16}
+(100/sqrt j) u_j v_j^T with 1% disjoint Rademacher supports; gamma = 0.05
 max||a_i|| (L1) and (0.05 max||a_i||)^2 (L0), scaled on the device.  One step
-= six full solves on that A (setup, power iterations to tol 1e-6, loadings):
-SL1, SL0, BL1 and BL0 with m = 5 at mu = 1, and BL1, BL0 at mu = [1, .9, .8,
-.7, .6].  Metric: power iterations (sweeps) per second over the step.
+= four full solves on that A (setup, power iterations to tol 1e-6,
+loadings): SL1, SL0, and BL1, BL0 with m = 16 components at mu = 1.  Metric:
+power iterations (sweeps) per second over the step.  The line also carries
+the 5000 x 20000 step (six solves, block m = 5) under "spikes_5000x20000".
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 N > 1 runs independent replicas (one process per GPU under torchrun).
@@ -24,20 +25,31 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# headline: 20000 x 100000 fp32, 16 spikes
+P4, N4, M4 = 20000, 100000, 16
+CASES4 = [("SL1", None), ("SL0", None), ("BL1", [1.0] * M4), ("BL0", [1.0] * M4)]
+# the oracle's bounded sample: noise block 0 of 16 (columns 0..6249, all
+# 20000 rows); its time per sweep is scaled by n / 6250 = 16
+SAMPLE_BLOCKS = (0, 1)
+SAMPLE_COLS = 6250
+# secondary: 5000 x 20000 fp32, 5 spikes
 P, N, K_SPIKES = 5000, 20000, 5
 RHO = 0.05
 MU_W = [1.0, 0.9, 0.8, 0.7, 0.6]
 CASES = [("SL1", None), ("SL0", None), ("BL1", [1.0] * 5), ("BL0", [1.0] * 5), ("BL1", MU_W), ("BL0", MU_W)]
 TOL, MAXIT = 1e-6, 1000
 RHO32 = 0.01
-# dram bytes (read + write) of one launch of the fused sweeps on this matrix,
-# from an ncu capture of the current kernels (dram__bytes_read.sum +
-# dram__bytes_write.sum)
+# dram bytes (read + write) of one launch of the fused sweeps on the 5000 x
+# 20000 matrix, from an ncu capture of the current kernels
+# (dram__bytes_read.sum + dram__bytes_write.sum)
 TRAFFIC_SL1 = 403.32e6
 TRAFFIC_BL1 = 404.02e6
 METRIC = "GPower iters/s"
 UNIT = "iters/s"
-WORKLOAD = "planted spikes 5000x20000 fp32 (5 spikes, theta_j=40/j, 5% supports), SL1+SL0+BL1+BL0 (m=5, mu=1 and mu=[1,.9,.8,.7,.6]), gamma=0.05*max||a_i||, tol 1e-6"
+WORKLOAD4 = ("planted spikes 20000x100000 fp32 (16 spikes, theta_j=100/sqrt(j), 1% supports), SL1+SL0+BL1+BL0 "
+             "(block m=16, mu=1), gamma=0.05*max||a_i||, tol 1e-6")
+WORKLOAD = ("planted spikes 5000x20000 fp32 (5 spikes, theta_j=40/j, 5% supports), SL1+SL0+BL1+BL0 (m=5, mu=1 and "
+            "mu=[1,.9,.8,.7,.6]), gamma=0.05*max||a_i||, tol 1e-6")
 
 
 def _peaks():
@@ -129,6 +141,63 @@ class Clocks:
         return out
 
 
+def _run_steps(ctx, stream, dA, hA, cases, p, n, steps, warmup, eager, host=False):
+    """`steps` timed steps of the solves in `cases` (after `warmup` untimed
+    ones), issued as one gpspca_solve_batch per step (the solves run
+    concurrently on their own streams, ordered on the context's stream).
+    Returns (ms, sweeps, kernel launches) over the timed steps."""
+    import torch
+
+    from paper_1312_6182_gb300 import binding
+
+    outs, counts = [], []
+    for form, mu in cases:
+        m = 1 if mu is None else len(mu)
+        outs.append(binding.alloc_result(m, p, n, "cpu" if host else "cuda", torch.float32, pin=host))
+        counts.append(ctx.plan_launches(dA, form, [RHO] * m, mu=mu, gamma_relative=True))
+
+    def step():
+        items = []
+        for (form, mu), out in zip(cases, outs):
+            m = 1 if mu is None else len(mu)
+            items.append(dict(At=hA if host else dA, form=form, gamma=[RHO] * m, mu=mu, tol=TOL, maxit=MAXIT,
+                              gamma_relative=True, out=out, eager=eager))
+        results = [ctx.solve(**it) for it in items] if eager else ctx.solve_batch(items)
+        sweeps, launches = 0, 0
+        for res, (pro, per, epi) in zip(results, counts):
+            it = int(res.iters.max().item())
+            sweeps += it
+            launches += pro + it * per + epi
+        return sweeps, launches
+
+    torch.cuda.synchronize()
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    total_sweeps, total_launches = 0, 0
+    ev0.record(stream)
+    for _ in range(steps):
+        sw, la = step()
+        total_sweeps += sw
+        total_launches += la
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1), total_sweeps, total_launches
+
+
+def _roofline(ctx, dA, form, m, bytes_a, peak, peak_kind, kernel, traffic):
+    """The sweep of one iteration timed alone (CUDA events on the library's
+    stream, gpspca_time_sweep); algorithmic bytes = one read of A."""
+    mu = [1.0] * m if form.startswith("B") else None
+    ms = ctx.time_sweep(dA, form, [RHO] * m, mu=mu, gamma_relative=True, reps=20)
+    ach = bytes_a / (ms / 1e3) / 1e9
+    return {"bound": "hbm", "kernel": kernel, "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(ach / peak, 4), "peak_source": peak_kind, "traffic": traffic,
+            "ms_per_launch": round(ms, 5), "algorithmic_bytes_per_launch": bytes_a}
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -141,96 +210,69 @@ def run_gpu(args):
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    At = synth.workload_spikes_5000x20000(0)
-    dA = torch.from_numpy(At).cuda()
-    hA = torch.from_numpy(At).pin_memory()
+    peak, peak_kind = _peaks()
     stream = torch.cuda.Stream()
     ctx = binding.Context(local, stream=stream)
-    outs = {}
-    for form, mu in CASES:
-        m = 1 if mu is None else len(mu)
-        outs[(form, tuple(mu) if mu else None)] = (
-            binding.alloc_result(m, P, N, "cuda", torch.float32),
-            binding.alloc_result(m, P, N, "cpu", torch.float32, pin=True),
-        )
 
-    def step(host=False):
-        # the six independent solves of a step as one batch: they run
-        # concurrently on their own streams, ordered on the context's stream
-        items = []
-        for form, mu in CASES:
-            m = 1 if mu is None else len(mu)
-            dres, hres = outs[(form, tuple(mu) if mu else None)]
-            items.append(dict(At=hA if host else dA, form=form, gamma=[RHO] * m, mu=mu, tol=TOL, maxit=MAXIT,
-                              gamma_relative=True, out=hres if host else dres, eager=args.eager))
-        if args.eager:  # profiling: one by one
-            results = [ctx.solve(**it) for it in items]
-        else:
-            results = ctx.solve_batch(items)
-        sweeps, launches = 0, 0
-        for (form, mu), res in zip(CASES, results):
-            it = int(res.iters.max().item())
-            sweeps += it
-            # reset, norms, selection, gather, reduction + finish of the start
-            # (+ 3 x {sketch sweep, reduction, finish} for the block start),
-            # one {sweep, reduction, finish} per iteration, the loadings
-            launches += 6 + (9 if form.startswith("B") else 0) + 3 * it + 1
-        return sweeps, launches
-
-    torch.cuda.synchronize()
-    for _ in range(args.warmup):
-        step()
+    # ---- headline: 20000 x 100000 fp32, four solves per step
+    At = synth.workload_spikes_20000x100000(2)
+    dA = torch.from_numpy(At).cuda()
+    hA = torch.from_numpy(At).pin_memory()
+    del At
     if ws > 1:
         torch.distributed.barrier()
-    torch.cuda.synchronize()
     clk = Clocks(local)
     clk.start()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    total_sweeps, total_launches = 0, 0
-    ev0.record(stream)
-    for _ in range(args.steps):
-        s, l = step()
-        total_sweeps += s
-        total_launches += l
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
+    ms, sweeps, launches = _run_steps(ctx, stream, dA, hA, CASES4, P4, N4, args.steps, args.warmup, args.eager)
     clocks = clk.stop()
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    ms, total_sweeps_all = reduce_over_ranks(ms, total_sweeps, "cuda")
-    value = total_sweeps_all / (ms / 1e3)
-
+    ms, sweeps_all = reduce_over_ranks(ms, sweeps, "cuda")
+    value = sweeps_all / (ms / 1e3)
     # end to end through the C ABI with host (pinned) buffers: A copied in
-    # (once per step: the batch stages a host matrix its requests share) and
-    # every result copied out inside the timed region
-    for _ in range(1):
-        step(host=True)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e2e_sweeps = 0
+    # (once per step: the batch stages the host matrix its requests share)
+    # and every result copied out inside the timed region
     e2e_steps = max(1, args.steps // 4)
-    e0.record(stream)
-    for _ in range(e2e_steps):
-        e2e_sweeps += step(host=True)[0]
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    h2d = P * N * 4  # the six requests share the host matrix: the batch copies it once
-    d2h = sum((P + N) * 4 * (1 if mu is None else len(mu)) + ((N + 31) // 32) * 4 * (1 if mu is None else len(mu))
-              + 24 * (1 if mu is None else len(mu)) for _, mu in CASES)
+    e2e_ms, e2e_sweeps, _ = _run_steps(ctx, stream, dA, hA, CASES4, P4, N4, e2e_steps, 1, False, host=True)
+    del hA
+    h2d = P4 * N4 * 4
+    d2h = sum((P4 + N4) * 4 * (1 if mu is None else len(mu)) + ((N4 + 31) // 32) * 4 * (1 if mu is None else len(mu))
+              + 24 * (1 if mu is None else len(mu)) for _, mu in CASES4)
+    bytes_a = P4 * N4 * 4
+    # the sweeps of the step: the block m = 16 sweep (fused float tensor-core
+    # passes) and the single-unit fused sweep; the one with the larger share
+    # of the step's sweep time is the dominant kernel
+    r_blk = _roofline(ctx, dA, "BL1", M4, bytes_a, peak, peak_kind,
+                      "tc_prep + tc_t_fused<48> + tc_t_combine + tc_y_fused<48> (block m=16 sweep: tcgen05, float A "
+                      "split into exact bf16 planes in shared memory)", None)
+    r_su = _roofline(ctx, dA, "SL1", 1, bytes_a, peak, peak_kind, "sweep_kernel<float,1> (single-unit fused sweep)",
+                     None)
+    its = _case_iters(ctx, dA, CASES4, P4, N4)
+    share_blk = sum(it for (f, _), it in zip(CASES4, its) if f.startswith("B")) * r_blk["ms_per_launch"]
+    share_su = sum(it for (f, _), it in zip(CASES4, its) if f.startswith("S")) * r_su["ms_per_launch"]
+    dom, other = (r_blk, r_su) if share_blk >= share_su else (r_su, r_blk)
+    dom["share_of_step_sweep_time"] = round(max(share_blk, share_su) / (share_blk + share_su), 3)
+    del dA
+    torch.cuda.empty_cache()
 
-    # roofline of the dominant kernels: the fused sweep, timed alone with CUDA
-    # events on the library's stream; algorithmic bytes = one read of A
-    ms_su = ctx.time_sweep(dA, "SL1", [RHO], gamma_relative=True, reps=20)
-    ms_blk = ctx.time_sweep(dA, "BL1", [RHO] * 5, mu=[1.0] * 5, gamma_relative=True, reps=20)
-    bytes_a = P * N * 4
-    peak, peak_kind = _peaks()
-    ach_su = bytes_a / (ms_su / 1e3) / 1e9
-    ach_blk = bytes_a / (ms_blk / 1e3) / 1e9
+    # ---- secondary: 5000 x 20000 fp32, six solves per step (block m = 5)
+    At2 = synth.workload_spikes_5000x20000(0)
+    dA2 = torch.from_numpy(At2).cuda()
+    ms2, sweeps2, launches2 = _run_steps(ctx, stream, dA2, None, CASES, P, N, args.steps, args.warmup, args.eager)
+    ms2, sweeps2_all = reduce_over_ranks(ms2, sweeps2, "cuda")
+    bytes2 = P * N * 4
+    secondary = {
+        "workload": WORKLOAD, "value": round(sweeps2_all / (ms2 / 1e3), 2), "unit": UNIT,
+        "ms_per_step": round(ms2 / args.steps, 4), "sweeps_per_step": round(sweeps2 / args.steps, 2),
+        "gpu_launches": launches2,
+        "roofline": _roofline(ctx, dA2, "BL1", 5, bytes2, peak, peak_kind,
+                              "sweep_kernel<float,5,3,full-width> (block m=5 fused sweep)", TRAFFIC_BL1),
+        "roofline_single_unit": _roofline(ctx, dA2, "SL1", 1, bytes2, peak, peak_kind,
+                                          "sweep_kernel<float,1,2,fixed-width 3> (single-unit fused sweep)",
+                                          TRAFFIC_SL1),
+    }
+    ctx.close()
     line = {
         "metric": METRIC,
         "value": round(value, 2),
@@ -244,29 +286,19 @@ def run_gpu(args):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "p": P, "n": N, "solves_per_step": len(CASES),
-                   "sweeps_per_step": round(total_sweeps / args.steps, 2),
-                   "l2": "inputs larger than L2 (A is 400 MB)", "parallelism": "replicas" if ws > 1 else "1 gpu"},
-        # the dominant kernel of the step by launch time (about 57% with its
-        # norm-forming variant): the block m = 5 sweep; the single-unit sweep
-        # beside it
-        "roofline": {"bound": "hbm", "kernel": "sweep_kernel<float,5,3,full-width> (block m=5 fused sweep)",
-                     "achieved": round(ach_blk, 1), "peak": peak, "unit": "GB/s", "frac": round(ach_blk / peak, 4),
-                     "peak_source": peak_kind, "traffic": TRAFFIC_BL1, "ms_per_launch": round(ms_blk, 5),
-                     "algorithmic_bytes_per_launch": bytes_a,
-                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch"},
-        "roofline_single_unit": {"bound": "hbm", "kernel": "sweep_kernel<float,1,2,fixed-width 3> (single-unit fused sweep)",
-                                 "achieved": round(ach_su, 1), "peak": peak, "unit": "GB/s",
-                                 "frac": round(ach_su / peak, 4), "ms_per_launch": round(ms_su, 5),
-                                 "traffic": TRAFFIC_SL1},
+        "config": {"workload": WORKLOAD4, "p": P4, "n": N4, "m_block": M4, "solves_per_step": len(CASES4),
+                   "sweeps_per_step": round(sweeps / args.steps, 2), "iters_per_case": its,
+                   "l2": "inputs larger than L2 (A is 8 GB)", "parallelism": "replicas" if ws > 1 else "1 gpu"},
+        "roofline": dom,
+        "roofline_other_sweep": other,
         "e2e": {"value": round(e2e_sweeps / (e2e_ms / 1e3), 2), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": total_launches,
+        "gpu_launches": launches,
         "clocks": clocks,
+        "spikes_5000x20000": secondary,
     }
     if rank == 0:
         line["cpu_baseline"] = cpu_baseline(ws)
-    ctx.close()
     if ws > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
@@ -274,16 +306,27 @@ def run_gpu(args):
         print(json.dumps(line), flush=True)
 
 
-def _oracle_sample(A64, sweeps_per_case=2):
-    """The oracle on a bounded sample of the workload: every case of the step,
-    a fixed number of sweeps each (tol = 0).  Returns (sweeps, seconds)."""
+def _case_iters(ctx, dA, cases, p, n):
+    """Iterations of each case of the step (one solve each)."""
+    its = []
+    for form, mu in cases:
+        m = 1 if mu is None else len(mu)
+        r = ctx.solve(dA, form, [RHO] * m, mu=mu, tol=TOL, maxit=MAXIT, gamma_relative=True)
+        its.append(int(r.iters.max().item()))
+    return its
+
+
+def _oracle_sample(A64, sweeps_per_case):
+    """The oracle on a bounded sample of the headline workload (the columns
+    of A64): every case of the step, a fixed number of sweeps each (tol = 0),
+    gamma relative to the sample's largest column.  Returns (sweeps, seconds)."""
     import numpy as np
 
     import oracle
 
     t0 = time.perf_counter()
     done = 0
-    for form, mu in CASES:
+    for form, mu in CASES4:
         m = 1 if mu is None else len(mu)
         g = oracle.gamma_from_rho(A64, form, [RHO] * m)
         r = oracle.gpower(A64, form, g, mu=mu, tol=0.0, maxit=sweeps_per_case)
@@ -291,31 +334,38 @@ def _oracle_sample(A64, sweeps_per_case=2):
     return done, time.perf_counter() - t0
 
 
-def cpu_baseline(ws):
-    if ws > 1 and _dist()[1] != 0:
-        return None
+def _sample64():
     import numpy as np
 
     from paper_1312_6182_gb300 import synth
 
-    At = synth.workload_spikes_5000x20000(0)
-    A64 = At.astype(np.float64).T
+    At = synth.workload_spikes_20000x100000(2, blocks=SAMPLE_BLOCKS)
+    assert At.shape == (SAMPLE_COLS, P4)
+    return At.astype(np.float64).T
+
+
+SAMPLE_NOTE = (f"columns 0..{SAMPLE_COLS - 1} (noise block {SAMPLE_BLOCKS[0]} of 16, all "
+               f"{P4} rows) of the 20000x100000 matrix; time per sweep scaled by n/{SAMPLE_COLS} = "
+               f"{N4 // SAMPLE_COLS}")
+
+
+def cpu_baseline(ws):
+    if ws > 1 and _dist()[1] != 0:
+        return None
+    A64 = _sample64()
     sweeps, sec = _oracle_sample(A64, 2)
-    return {"value": round(sweeps / sec, 3), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{sweeps} sweeps: every case of the step, 2 sweeps each (tol=0), FP64 NumPy on the host"}
+    scale = N4 / SAMPLE_COLS
+    return {"value": round(sweeps / (sec * scale), 3), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{sweeps} sweeps: every case of the step, 2 sweeps each (tol=0), FP64 NumPy on the host, "
+                      + SAMPLE_NOTE}
 
 
 def run_reference(args):
     """The oracle as it stands, timed on the host cores (rank 0 only)."""
-    import numpy as np
-
-    from paper_1312_6182_gb300 import synth
-
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    At = synth.workload_spikes_5000x20000(0)
-    A64 = At.astype(np.float64).T
+    A64 = _sample64()
     for _ in range(args.warmup):
         _oracle_sample(A64, 1)
     total, sec = 0, 0.0
@@ -323,7 +373,9 @@ def run_reference(args):
         s, t = _oracle_sample(A64, 1)
         total += s
         sec += t
-    value = total / sec
+    scale = N4 / SAMPLE_COLS
+    value = total / (sec * scale)
+    sample = "every case of the step, 1 sweep each (tol=0), FP64 NumPy, " + SAMPLE_NOTE
     line = {
         "impl": "reference",
         "metric": METRIC,
@@ -332,39 +384,42 @@ def run_reference(args):
         "n_gpus": ws,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": round(sec / args.steps * 1e3, 3),
+        "ms_per_step": round(sec * scale / args.steps * 1e3, 3),
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "p": P, "n": N, "sample": "every case of the step, 1 sweep each"},
+        "config": {"workload": WORKLOAD4, "p": P4, "n": N4, "sample": sample},
         "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                         "sample": "every case of the step, 1 sweep each (tol=0), FP64 NumPy"},
+                         "sample": sample},
         "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
 def run_sweep_only(args):
-    """The fused sweep alone on the benchmark matrix (profiling entry):
-    prints the mean time of one sweep and the algorithmic bandwidth."""
+    """The fused sweep alone on one of the benchmark matrices (profiling
+    entry): prints the mean time of one sweep and the algorithmic bandwidth."""
     import torch
 
     from paper_1312_6182_gb300 import binding, synth
 
-    At = synth.workload_spikes_5000x20000(0)
-    if args.sweep_dtype == "bf16":
-        dA = torch.from_numpy(At).cuda().to(torch.bfloat16)
+    if args.sweep_matrix == "20000x100000":
+        At, p, n = synth.workload_spikes_20000x100000(2), P4, N4
     else:
-        dA = torch.from_numpy(At).cuda()
+        At, p, n = synth.workload_spikes_5000x20000(0), P, N
+    dA = torch.from_numpy(At).cuda()
+    del At
+    if args.sweep_dtype == "bf16":
+        dA = dA.to(torch.bfloat16)
     form = args.sweep_only
     m = args.sweep_m or (1 if form.startswith("S") else 5)
     mu = [1.0] * m if form.startswith("B") else None
     with binding.Context(0) as ctx:
         ms = ctx.time_sweep(dA, form, [RHO] * m, mu=mu, gamma_relative=True, reps=args.reps)
-    nbytes = P * N * dA.element_size()
-    print(json.dumps({"sweep": form, "m": m, "dtype": args.sweep_dtype, "ms": round(ms, 5),
+    nbytes = p * n * dA.element_size()
+    print(json.dumps({"sweep": form, "m": m, "dtype": args.sweep_dtype, "matrix": f"{p}x{n}", "ms": round(ms, 5),
                       "GB/s": round(nbytes / (ms / 1e3) / 1e9, 1)}), flush=True)
 
 
@@ -914,10 +969,13 @@ def main():
                     help="time the fused sweep alone on the benchmark matrix (profiling)")
     ap.add_argument("--sweep-m", type=int, default=None, help="sweep-only: components or gammas (default 1 / 5)")
     ap.add_argument("--sweep-dtype", default="f32", choices=["f32", "bf16"])
+    ap.add_argument("--sweep-matrix", default="5000x20000", choices=["5000x20000", "20000x100000"],
+                    help="sweep-only: the matrix")
     ap.add_argument("--reps", type=int, default=20)
-    ap.add_argument("--workload", default="spikes5000",
-                    choices=["spikes5000", "gamma-path", "precision", "serving", "deflation", "scaling", "latency"],
-                    help="spikes5000: the headline step; the others measure the sparsity-path batch, the "
+    ap.add_argument("--workload", default="step",
+                    choices=["step", "gamma-path", "precision", "serving", "deflation", "scaling", "latency"],
+                    help="step: the headline step (20000x100000, with the 5000x20000 step beside it); the others "
+                         "measure the sparsity-path batch, the "
                          "BF16/FP8 precision path, the serving mix, deflated multi-component extraction and the "
                          "size sweep of the paper's efficiency experiment (one JSON line each)")
     ap.add_argument("--oracle", action="store_true",
@@ -933,8 +991,8 @@ def main():
         run_sweep_only(args)
         return
     if args.steps is None:
-        args.steps = 100 if args.workload == "spikes5000" else 4
-    if args.workload != "spikes5000":
+        args.steps = 20 if args.workload == "step" else 4
+    if args.workload != "step":
         args.warmup = max(args.warmup, 1)
         {"gamma-path": run_gamma_path, "precision": run_precision, "serving": run_serving,
          "deflation": run_deflation, "scaling": run_scaling, "latency": run_latency}[args.workload](args)

@@ -85,6 +85,10 @@ typedef enum { GPSPCA_DEVICE = 0, GPSPCA_HOST = 1 } gpspca_location;
 #define GPSPCA_NO_TENSOR_CORES 4u /* run the CUDA-core fused sweep even where the tensor-core
                                      (tcgen05) sweep applies (bf16 storage with m >= 6, float or
                                      fp8 storage with m >= 9) */
+#define GPSPCA_INJECT_TIMEOUT 8u  /* test hook for callers' error handling: after the solve has
+                                     run, its device state is marked as if a device-side wait had
+                                     given up, so the call returns GPSPCA_ETIMEDOUT (no wait is
+                                     made to expire); the context stays usable */
 
 /* Largest m (components, or gamma values of a path) one solve accepts. */
 #define GPSPCA_MAX_M 64
@@ -279,30 +283,6 @@ int gpspca_tune_load(gpspca_ctx* ctx, const char* path);
 int gpspca_time_sweep(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form, const double* gamma, int32_t m,
                       const double* mu, uint32_t flags, int32_t reps, double* ms_per_sweep);
 
-/* One fused single-unit sweep that allocates no memory (the paper has no
- * counterpart; it serves callers that cannot allocate device memory when
- * they need a sweep, e.g. because another framework's caching allocator
- * holds the free HBM, or because the call sits in a latency-bound loop or in
- * code where allocation is forbidden).  No context is needed.
- *
- * For a float32 matrix A in device memory and a device iterate x (p floats,
- * used as given), it computes on the device: t = A^T x (n floats), the
- * objective f of Table 1 at x (one double) and x_next = A g / ||A g|| (p
- * floats; all zero when every entry is thresholded), where g is the SL1 or
- * SL0 gradient factor at gamma (absolute).  All outputs are caller-owned
- * device memory.  Runs on cuda_stream (NULL: the legacy default stream) and
- * returns when the results are ready.
- *
- * Scratch lives in file-scope device arrays of fixed size (6 MiB: the
- * per-cluster partials of y, up to 160 clusters x p floats) that every GPU
- * loading the library keeps until the process exits.  Limit: p <= 8192;
- * a larger p returns GPSPCA_EINVAL naming the limit.
- * The arrays are shared by every call: calls are serialised inside the
- * library, and calls that overlapped on the GPU (e.g. from other processes
- * sharing a context) would race.  The first call on a device resolves the
- * arrays' device addresses (cudaGetSymbolAddress); make it before any
- * stream capture.  No cudaMalloc, cudaFree or allocating library routine is
- * called. */
 /* Seeded synthetic input (not part of the method): a planted-spike matrix
  * drawn on the device, for workloads whose requests bring their own data
  * (the serving benchmark).  Writes A (p x n, column-major, leading dimension
@@ -319,6 +299,46 @@ int gpspca_time_sweep(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form,
 int gpspca_synth_spikes(void* At, gpspca_dtype dtype, int64_t p, int64_t n, int64_t ld, int32_t k,
                         const double* theta, double support_frac, uint64_t seed, void* cuda_stream);
 
+/* Measurement aid (the paper has no counterpart): the number of kernel
+ * launches of one solve of this problem with the layout gpspca_solve would
+ * pick, as counts[0] before the iterations (start, norms, projection, and
+ * for block forms the power steps of the start), counts[1] per iteration
+ * (the sweep's kernels, its reduction and its finish step) and counts[2]
+ * after them (the loadings).  A solve that runs k iterations launches
+ * counts[0] + k counts[1] + counts[2] kernels.  Arguments as
+ * gpspca_time_sweep; nothing is launched. */
+int gpspca_plan_launches(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form, const double* gamma, int32_t m,
+                         const double* mu, uint32_t flags, int32_t counts[3]);
+
+/* One fused single-unit sweep that allocates no memory.  The paper has no
+ * counterpart: this entry point is for callers that cannot allocate device
+ * memory at the moment they need a sweep, e.g. because another framework's
+ * caching allocator holds the free HBM, because the call sits in a
+ * latency-bound loop where an allocation could synchronise the device, or
+ * because it runs where allocation is forbidden.  No context is needed.
+ *
+ * For a float32 matrix A in device memory and a device iterate x (p floats,
+ * used as given), it computes on the device: t = A^T x (n floats), the
+ * single-unit objective f at x (one double: sum of [|t_i| - gamma]_+^2 for
+ * SL1, of [t_i^2 - gamma]_+ for SL0) and x_next = A g / ||A g|| (p floats; all
+ * zero when every entry is thresholded), where g is the SL1 or SL0 gradient
+ * factor at gamma (absolute).  All outputs are caller-owned device memory.
+ * cuda_stream (NULL: the legacy default stream) must belong to the current
+ * device; the call synchronises with it and returns when the results are
+ * ready, so it cannot itself run under stream capture.
+ *
+ * Scratch lives in file-scope device arrays of fixed size (6 MiB: the
+ * per-cluster partials of y, up to 160 clusters x p floats) that every GPU
+ * loading the library keeps until the process exits.  Limit: p <= 8192;
+ * a larger p returns GPSPCA_EINVAL naming the limit.  The arrays are shared
+ * by every call and keep the last call's contents (everything a call reads
+ * is rewritten by it first): calls are serialised inside the library, and
+ * calls that overlapped on the GPU (e.g. from other processes) would race.
+ * The first call on a device resolves the arrays' device addresses
+ * (cudaGetSymbolAddress) for that device; make it before any stream capture
+ * on the device.  A NaN or infinity in A or x (or an overflow of t, f or
+ * ||A g||) returns GPSPCA_ENONFINITE.  No cudaMalloc, cudaFree or allocating
+ * library routine is called. */
 int gpspca_sweep_static(const gpspca_matrix* A, gpspca_form form, double gamma, const float* x, float* x_next,
                         float* t, double* objective, void* cuda_stream);
 

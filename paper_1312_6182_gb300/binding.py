@@ -30,6 +30,7 @@ CONVERGED, MAXIT, ZERO, DEGENERATE = 0, 1, 2, 3
 GAMMA_RELATIVE = 1
 EAGER = 2  # kernels launched one by one, host-driven loop (for profilers)
 NO_TENSOR_CORES = 4  # CUDA-core fused sweep even where the tensor-core sweep applies
+INJECT_TIMEOUT = 8  # test hook: the solve returns ETIMEDOUT after running
 MAX_M = 64
 
 ERROR_NAMES = {
@@ -40,7 +41,7 @@ ERROR_NAMES = {
 EXPORTED = ("gpspca_create", "gpspca_solve", "gpspca_submit", "gpspca_poll", "gpspca_destroy",
             "gpspca_last_error", "gpspca_time_sweep", "gpspca_sweep_static", "gpspca_synth_spikes",
             "gpspca_solve_batch", "gpspca_solve_deflated", "gpspca_project", "gpspca_tune", "gpspca_tune_save",
-            "gpspca_tune_load")
+            "gpspca_tune_load", "gpspca_plan_launches")
 
 
 class Matrix(ctypes.Structure):
@@ -133,6 +134,9 @@ def load(path: str = LIB_PATH):
     lib.gpspca_tune_save.restype = ctypes.c_int
     lib.gpspca_tune_load.argtypes = [P, ctypes.c_char_p]
     lib.gpspca_tune_load.restype = ctypes.c_int
+    lib.gpspca_plan_launches.argtypes = [P, ctypes.POINTER(Matrix), ctypes.c_int, D, ctypes.c_int32, D,
+                                         ctypes.c_uint32, ctypes.POINTER(ctypes.c_int32)]
+    lib.gpspca_plan_launches.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -277,10 +281,11 @@ class Context:
     def solve(self, At, form: str, gamma, mu=None, tol: float = 1e-6, maxit: int = 1000, x0=None,
               gamma_relative: bool = False, p: Optional[int] = None, col_scale=None,
               out: Optional[Result] = None, allow_degenerate: bool = True, eager: bool = False,
-              tensor_cores: bool = True) -> Result:
+              tensor_cores: bool = True, extra_flags: int = 0) -> Result:
         """One synchronous solve.  gamma: m values; mu: block weights.  eager: launch
         the kernels one by one with a host-driven loop instead of the CUDA graph.
-        tensor_cores=False keeps the CUDA-core sweep where the tcgen05 one applies."""
+        tensor_cores=False keeps the CUDA-core sweep where the tcgen05 one applies.
+        extra_flags: further GPSPCA_* flag bits (e.g. INJECT_TIMEOUT)."""
         import torch
 
         gamma = [float(g) for g in (gamma if hasattr(gamma, "__len__") else [gamma])]
@@ -294,7 +299,7 @@ class Context:
         rc = self.lib.gpspca_solve(self.ptr, ctypes.byref(M), FORMS[form], _darr(gamma, m), m, _darr(mu, m),
                                    float(tol), int(maxit), x0.data_ptr() if x0 is not None else None,
                                    (GAMMA_RELATIVE if gamma_relative else 0) | (EAGER if eager else 0)
-                                   | (0 if tensor_cores else NO_TENSOR_CORES), ctypes.byref(o))
+                                   | (0 if tensor_cores else NO_TENSOR_CORES) | int(extra_flags), ctypes.byref(o))
         allow = (OK, EDEGENERATE) if allow_degenerate else (OK,)
         _check(rc, allow)
         out.rc = rc
@@ -422,6 +427,20 @@ class Context:
         return ms.value
 
 
+    def plan_launches(self, At, form: str, gamma, mu=None, gamma_relative: bool = False, p: Optional[int] = None,
+                      col_scale=None, tensor_cores: bool = True):
+        """Kernel launches of one solve of this problem (gpspca_plan_launches):
+        (before the iterations, per iteration, after them)."""
+        gamma = [float(g) for g in (gamma if hasattr(gamma, "__len__") else [gamma])]
+        m = len(gamma)
+        M = matrix(At, p, col_scale)
+        self._sync_torch(At)
+        c = (ctypes.c_int32 * 3)()
+        _check(self.lib.gpspca_plan_launches(self.ptr, ctypes.byref(M), FORMS[form], _darr(gamma, m), m,
+                                             _darr(mu, m), (GAMMA_RELATIVE if gamma_relative else 0)
+                                             | (0 if tensor_cores else NO_TENSOR_CORES), c))
+        return int(c[0]), int(c[1]), int(c[2])
+
     def tune(self, At, form: str, gamma, mu=None, reps: int = 10, gamma_relative: bool = False,
              p: Optional[int] = None, col_scale=None, tensor_cores: bool = True):
         """Time every candidate sweep layout for this shape and keep the fastest
@@ -457,13 +476,24 @@ def sweep_static(At, form: str, gamma: float, x, x_next, t, objective, p: Option
     import torch
 
     lib = load()
+    n, ld = At.shape
+    pp = ld if p is None else int(p)
+    if not (At.is_cuda and At.dtype == torch.float32):
+        raise GpspcaError(EINVAL, "sweep_static: At must be a float32 CUDA tensor")
+    for name, ten, dt, count in (("x", x, torch.float32, pp), ("x_next", x_next, torch.float32, pp),
+                                 ("t", t, torch.float32, n), ("objective", objective, torch.float64, 1)):
+        if not (ten.is_cuda and ten.device == At.device and ten.dtype == dt and ten.is_contiguous()
+                and ten.numel() == count):
+            raise GpspcaError(EINVAL, f"sweep_static: {name} must be a contiguous {dt} tensor of {count} entries "
+                                      f"on {At.device}")
     M = matrix(At, p)
     torch.cuda.current_stream().synchronize()
     handle = None
     if stream is not None:
         handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
-    rc = lib.gpspca_sweep_static(ctypes.byref(M), FORMS[form], float(gamma), x.data_ptr(), x_next.data_ptr(),
-                                 t.data_ptr(), objective.data_ptr(), handle)
+    with torch.cuda.device(At.device):  # the library works on the current device
+        rc = lib.gpspca_sweep_static(ctypes.byref(M), FORMS[form], float(gamma), x.data_ptr(), x_next.data_ptr(),
+                                     t.data_ptr(), objective.data_ptr(), handle)
     return _check(rc)
 
 

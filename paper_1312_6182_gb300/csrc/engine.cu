@@ -1021,6 +1021,11 @@ static int launch_solve(Slot* s, const Request& r, int nsm, bool* empty) {
     if (r.out.gamma_abs)
       GP_CUDA(cudaMemcpyAsync(r.out.gamma_abs, s->s_gam.p, sizeof(double) * m, cudaMemcpyDeviceToHost, s->stream));
   }
+  if (r.flags & GPSPCA_INJECT_TIMEOUT) {
+    // the error word as a timed-out wait leaves it; the next solve's reset clears it
+    static const int32_t kTimedOut = kErrTimeout;
+    GP_CUDA(cudaMemcpyAsync(&s->st_dev->error, &kTimedOut, sizeof(int32_t), cudaMemcpyHostToDevice, s->stream));
+  }
   GP_CUDA(cudaMemcpyAsync(s->st_host, s->st_dev, sizeof(State), cudaMemcpyDeviceToHost, s->stream));
   GP_CUDA(cudaEventRecord(s->done, s->stream));
   return GPSPCA_OK;
@@ -1042,7 +1047,7 @@ static int request_from(Request* r, const gpspca_matrix* A, gpspca_form form, co
                         const double* mu, double tol, int32_t maxit, const void* x0, uint32_t flags,
                         gpspca_out* out) {
   if (!A || !out || !gamma) return fail(GPSPCA_EINVAL, "A, gamma and out must not be NULL");
-  if (flags & ~(GPSPCA_GAMMA_RELATIVE | GPSPCA_EAGER | GPSPCA_NO_TENSOR_CORES))
+  if (flags & ~(GPSPCA_GAMMA_RELATIVE | GPSPCA_EAGER | GPSPCA_NO_TENSOR_CORES | GPSPCA_INJECT_TIMEOUT))
     return fail(GPSPCA_EINVAL, "unknown flag bits 0x%x", flags);
   if (m < 1 || m > kMaxM) return fail(GPSPCA_EINVAL, "m = %d outside [1, %d]", m, kMaxM);
   r->A = *A;
@@ -1505,6 +1510,43 @@ int gpspca_time_sweep(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form,
   if (s->st_host->error & kErrTimeout) return fail(GPSPCA_ETIMEDOUT, "a device-side wait for a tile copy gave up");
   if (s->st_host->n_active == 0) return fail(GPSPCA_EINVAL, "the start is degenerate or A is zero: nothing to time");
   *ms_per_sweep = static_cast<double>(ms) / reps;
+  return GPSPCA_OK;
+}
+
+// Kernel launches of one plan: before the iterations, per iteration, after
+// (mirrors launch_prologue / launch_body / launch_epilogue).
+static void plan_launch_counts(const Plan& pl, int32_t c[3]) {
+  const int sweeps = pl.tc ? 3 + (pl.ksplit1 > 1 ? 1 : 0) : static_cast<int>(pl.passes.size());
+  const bool late_norms = pl.pca && pl.norms_in_sweep;
+  int pro = (pl.tc && pl.tc_convert ? 1 : 0) + 1 + (late_norms ? 0 : 2) + 1 + 2;
+  if (pl.pca) pro += kPowerSteps * (sweeps + 2) + (late_norms ? 1 : 0) + sweeps + 2;
+  c[0] = pro;
+  c[1] = sweeps + 2;
+  c[2] = 1;
+}
+
+int gpspca_plan_launches(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form, const double* gamma, int32_t m,
+                         const double* mu, uint32_t flags, int32_t counts[3]) {
+  if (!ctx || !counts) return fail(GPSPCA_EINVAL, "ctx and counts must not be NULL");
+  gpspca_out dummy = {};
+  dummy.location = GPSPCA_DEVICE;
+  double one = 0.0;
+  dummy.X = dummy.Z = dummy.objective = &one;  // replaced by staging buffers
+  dummy.iters = dummy.status = reinterpret_cast<int32_t*>(&one);
+  Request r;
+  int rc = request_from(&r, A, form, gamma, m, mu, 0.0, 1, nullptr, flags, &dummy);
+  if (rc != GPSPCA_OK) return rc;
+  std::lock_guard<std::mutex> lk(ctx->solve_mu);
+  GP_CUDA(cudaSetDevice(ctx->device));
+  Plan pl;
+  bool empty = false;
+  rc = prepare_solve(&ctx->sync_slot, r, ctx->nsm, true, &pl, &empty);
+  if (rc != GPSPCA_OK) return rc;
+  if (empty) {
+    counts[0] = counts[1] = counts[2] = 0;
+    return GPSPCA_OK;
+  }
+  plan_launch_counts(pl, counts);
   return GPSPCA_OK;
 }
 

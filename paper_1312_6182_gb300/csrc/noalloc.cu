@@ -12,6 +12,7 @@
 // The work is the same fused sweep kernel the solver uses, followed by the
 // deterministic partial-sum reduction and a one-block step that forms the
 // objective and normalises y.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <mutex>
@@ -65,10 +66,22 @@ static int static_setup(int dev, StaticPtrs** out) {
   return GPSPCA_OK;
 }
 
+// Sets the non-finite bit when any entry of t is NaN or infinite: a NaN or
+// infinity in A or x, or a product that overflowed, reaches t (a NaN entry
+// would otherwise fail every threshold test and drop out of the objective).
+__global__ void static_check_finite(const float* __restrict__ t, int64_t n, State* st) {
+  bool bad = false;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    bad |= !isfinite(t[i]);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&st->error, kErrNonFinite);
+}
+
 // Sum of the reduction blocks' partials (fixed order): objective f and ||y||^2, then
-// x_next = y / ||y|| (all zero when y = 0).  One block.
+// x_next = y / ||y|| (all zero when y = 0).  One block.  A non-finite f or
+// ||y||^2 sets the non-finite bit.
 __global__ void static_sweep_finish(const dd* fpart, int nobj, const double* gpart, int nred, float* x_next, int p,
-                                    double* objective) {
+                                    double* objective, State* st) {
   __shared__ double s_g;
   if (threadIdx.x == 0) {
     dd f{0.0f, 0.0f};
@@ -76,10 +89,12 @@ __global__ void static_sweep_finish(const dd* fpart, int nobj, const double* gpa
     for (int b = 0; b < nobj; ++b) f = dd_add(f, fpart[2 * b]);
     for (int b = 0; b < nred; ++b) g += gpart[b];
     s_g = g;
-    *objective = dd_to_double(f);
+    const double fv = dd_to_double(f);
+    *objective = fv;
+    if (!isfinite(fv) || !isfinite(g)) atomicOr(&st->error, kErrNonFinite);
   }
   __syncthreads();
-  const float inv = s_g > 0.0 ? static_cast<float>(1.0 / sqrt(s_g)) : 0.0f;
+  const float inv = (s_g > 0.0 && isfinite(s_g)) ? static_cast<float>(1.0 / sqrt(s_g)) : 0.0f;
   for (int r = threadIdx.x; r < p; r += blockDim.x) x_next[r] *= inv;
 }
 
@@ -177,9 +192,11 @@ extern "C" int gpspca_sweep_static(const gpspca_matrix* A, gpspca_form form, dou
   }
   ReduceArgs ra{sp->io_reduce, sp->st, pl.ncl, 1, p, 0, 1, 0, 0, 1, n, form, pl.nred, pl.nobj};
   launch_reduce(4, ra, stream);
+  static_check_finite<<<static_cast<int>(std::min<int64_t>((n + 255) / 256, 4 * static_cast<int64_t>(sp->nsm))),
+                        256, 0, stream>>>(t, n, sp->st);
   static_sweep_finish<<<1, 256, 0, stream>>>(reinterpret_cast<const dd*>(sc + off_f), pl.nobj,
                                               reinterpret_cast<const double*>(sc + off_g), pl.nred, x_next, p,
-                                              objective);
+                                              objective, sp->st);
   if (cudaGetLastError() != cudaSuccess) return record_error(GPSPCA_ECUDA, "reduction launch failed");
   int32_t err = 0;
   if (cudaMemcpyAsync(&err, &sp->st->error, sizeof(int32_t), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
@@ -187,6 +204,8 @@ extern "C" int gpspca_sweep_static(const gpspca_matrix* A, gpspca_form form, dou
     cudaGetLastError();
     return record_error(GPSPCA_ECUDA, "sweep execution failed");
   }
+  if (err & kErrNonFinite)
+    return record_error(GPSPCA_ENONFINITE, "A or x has a non-finite entry (or t, the objective or ||A g|| overflowed)");
   if (err & kErrTimeout) return record_error(GPSPCA_ETIMEDOUT, "a device-side wait for a tile copy gave up");
   if (err & kErrLaunch) return record_error(GPSPCA_ECUDA, "internal: sweep launched with a tile wider than it reduces");
   return GPSPCA_OK;

@@ -20,6 +20,7 @@ available, so planted sparse spikes stand in for structured data):
 
 from __future__ import annotations
 
+import os
 from dataclasses import dataclass
 from typing import Optional, Sequence
 
@@ -56,11 +57,21 @@ def planted_spike(
     seed: int = 0,
     dtype=np.float32,
     with_meta: bool = False,
+    noise_streams: int = 1,
+    blocks: Optional[tuple] = None,
 ):
     """Planted sparse spikes: A = N(0,1) + sum_{j<k} theta_j u_j v_j^T.
 
     Each v_j has ``support_size`` (or round(support_frac * n)) nonzeros,
     +-1/sqrt(s), on supports that are disjoint across j.
+
+    ``noise_streams`` > 1 (the matrices of billions of entries): the noise is
+    drawn in that many equal blocks of columns of A, block b from the b-th
+    child of ``SeedSequence(seed).spawn(noise_streams)``, filled on parallel
+    threads; u, supports and signs then come from ``default_rng(seed)`` in the
+    usual order.  ``blocks = (b0, b1)`` then returns only the columns of
+    noise blocks b0 .. b1-1 (bit-identical to those columns of the whole
+    matrix): a sample of a matrix too large to draw in full.
     """
     if support_size is None:
         support_size = int(round(float(support_frac) * n))
@@ -71,7 +82,15 @@ def planted_spike(
     if theta.size != k:
         raise ValueError("theta must have k entries")
     rng = np.random.default_rng(seed)
-    At = rng.standard_normal((n, p), dtype=np.float32)  # noise
+    lo, hi = 0, n
+    if noise_streams > 1:
+        b0, b1 = (0, noise_streams) if blocks is None else blocks
+        lo, hi = b0 * n // noise_streams, b1 * n // noise_streams
+        At = _noise_blocks(n, p, seed, noise_streams, b0, b1)
+    else:
+        if blocks is not None:
+            raise ValueError("blocks needs noise_streams > 1")
+        At = rng.standard_normal((n, p), dtype=np.float32)  # noise
     U = rng.standard_normal((k, p))  # u_j ~ N(0, I_p)
     perm = rng.permutation(n)[: k * s]
     supports = [np.sort(perm[j * s : (j + 1) * s]) for j in range(k)]
@@ -79,13 +98,34 @@ def planted_spike(
     for j in range(k):
         if s == 0:
             continue
-        idx = supports[j]
-        v = signs[j] / np.sqrt(s)
+        keep = (supports[j] >= lo) & (supports[j] < hi)
+        idx = supports[j][keep] - lo
+        v = signs[j][keep] / np.sqrt(s)
         rows = At[idx].astype(np.float64) + theta[j] * np.outer(v, U[j])
         At[idx] = rows.astype(np.float32)
     out = np.ascontiguousarray(At.astype(dtype, copy=False))
     if with_meta:
         return out, SpikeMeta(theta, U, supports, signs)
+    return out
+
+
+def _noise_blocks(n: int, p: int, seed: int, streams: int, b0: int = 0, b1: Optional[int] = None) -> np.ndarray:
+    """N(0,1) float32 rows [b n / streams, (b+1) n / streams) of an n x p
+    array, each drawn from the b-th child seed of ``seed``, for blocks b0 ..
+    b1-1 (see ``planted_spike``)."""
+    import concurrent.futures
+
+    b1 = streams if b1 is None else b1
+    base = b0 * n // streams
+    out = np.empty((b1 * n // streams - base, p), dtype=np.float32)
+    kids = np.random.SeedSequence(seed).spawn(streams)
+
+    def fill(b):
+        lo, hi = b * n // streams - base, (b + 1) * n // streams - base
+        np.random.default_rng(kids[b]).standard_normal(out=out[lo:hi], dtype=np.float32)
+
+    with concurrent.futures.ThreadPoolExecutor(min(b1 - b0, os.cpu_count() or 1)) as ex:
+        list(ex.map(fill, range(b0, b1)))
     return out
 
 
@@ -104,17 +144,20 @@ def workload_spikes_5000x20000(seed: int = 0, p: int = 5000, n: int = 20000, wit
 
 
 def workload_spikes_10000x50000(seed: int = 1, p: int = 10000, n: int = 50000, with_meta: bool = False):
-    """10000 x 50000 float32, 3 spikes, theta_j = 40/j, 2% disjoint supports."""
+    """10000 x 50000 float32, 3 spikes, theta_j = 40/j, 2% disjoint supports
+    (noise in 16 parallel streams)."""
     k = 3
     return planted_spike(p, n, k, [40.0 / j for j in range(1, k + 1)], support_frac=0.02,
-                         seed=seed, dtype=np.float32, with_meta=with_meta)
+                         seed=seed, dtype=np.float32, with_meta=with_meta, noise_streams=16)
 
 
-def workload_spikes_20000x100000(seed: int = 2, p: int = 20000, n: int = 100000, with_meta: bool = False):
-    """20000 x 100000 float32, 16 spikes, theta_j = 100/sqrt(j), 1% supports."""
+def workload_spikes_20000x100000(seed: int = 2, p: int = 20000, n: int = 100000, with_meta: bool = False,
+                                 blocks: Optional[tuple] = None):
+    """20000 x 100000 float32, 16 spikes, theta_j = 100/sqrt(j), 1% supports
+    (noise in 16 parallel streams of 6250 columns; ``blocks`` selects some)."""
     k = 16
     return planted_spike(p, n, k, [100.0 / np.sqrt(j) for j in range(1, k + 1)], support_frac=0.01,
-                         seed=seed, dtype=np.float32, with_meta=with_meta)
+                         seed=seed, dtype=np.float32, with_meta=with_meta, noise_streams=16, blocks=blocks)
 
 
 def log_spaced_rho(count: int = 64, lo: float = 1e-3, hi: float = 0.5) -> np.ndarray:

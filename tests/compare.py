@@ -1,26 +1,49 @@
 """Comparison of a GPU result with the FP64 oracle.
 
 Stated tolerances (float32 compute): loadings 1e-5 relative per column,
-objective 1e-6 relative (per gamma for single-unit forms, the total for block
-forms), support identical outside a band of 1e-6 * gamma around the
-threshold.  Where the float32 accuracy of t = a_i^T x itself is coarser than
-the stated figure (small gamma, objectives made of near-threshold entries),
-the bound derived from that accuracy is used instead:
+objective 1e-6 relative (per gamma for single-unit forms; per component and
+in total for block forms), support identical outside a band of 1e-6 * gamma
+around the threshold.  These are the limits by default.
+
+A per-column limit is raised above the stated figure only where the float32
+accuracy of t = a_i^T x itself is coarser than that figure (a small gamma,
+loadings made of entries close to the threshold).  The bound derived from that
+accuracy is
 
   dt_i   = 4 * eps * ||a_i||                (eps = 2^-24 for float32 compute,
                                              blocked/tree accumulation of t)
   band_i = max(1e-6 gamma, 3 mu dt_i)       L1: margin |mu |t| - gamma|
          = max(1e-6 gamma, 6 mu^2 |t| dt_i) L0: margin |(mu t)^2 - gamma|
-  loadings: max(1e-5, 3 ||mu dt||_active / ||z_unnormalised||)
-  objective: max(1e-6, 3 sqrt(sum_active (df/dt_i dt_i)^2) / f)
+  loadings:  3 ||mu dt||_active / ||z_unnormalised||
+  objective: 3 sqrt(sum_active (df/dt_i dt_i)^2) / f
 
-Per-component objectives of block forms (f_j) are checked at max(1e-5, the
-derived bound); the total at max(1e-6, derived).
+Every check records which limit decided it (``stated`` or ``derived``) and
+prints one line per call; a derived limit more than ``MAX_DERIVED_RATIO``
+times the stated figure fails the check (the case is then too ill-conditioned
+for float32 to say anything at the stated figure, and the test must pick a
+better-posed case instead).
+
+Stopping index.  A converged solve stops at the first sweep k whose relative
+objective change falls below tol; the GPU decides that in double from its
+float32 objective, the oracle from its float64 one, so near the boundary the
+two can stop a sweep apart.  ``align_to_gpu_stop`` checks that every sweep at
+which the two decisions differ has an oracle relative change within
+``STOP_MARGIN`` * tol of tol, and then compares the GPU result with the
+oracle's own state after the GPU's number of sweeps (the oracle run with
+tol = 0 for that many sweeps: a state of the oracle, not an input from the
+GPU).
 """
 
 import numpy as np
 
+import oracle
+
 EPS32 = 2.0 ** -24
+MAX_DERIVED_RATIO = 10.0
+STOP_MARGIN = 0.5
+
+# every check of the session: (label, quantity, error, limit, stated, binding)
+LOG = []
 
 
 def unpack_support(words, n):
@@ -42,22 +65,26 @@ def gpu_arrays(res):
     )
 
 
-def derived_bounds(form, ref, cnorm, eps):
-    """Per-column bounds implied by the accuracy of t (see module docstring)."""
+def derived_bounds(form, ref, cnorm, eps, dx=None):
+    """Per-column bounds implied by the accuracy of t (see module docstring).
+    ``dx`` (per column, optional): a difference of the iterate itself, which
+    moves t_i by up to ||a_i|| dx_j and so widens the support band (the
+    refinement path starts from a low-precision iterate)."""
     T, gam, mu = ref.T, ref.gamma, ref.mu
-    dt = 4.0 * eps * cnorm[:, None]  # n x 1
+    dt = 4.0 * eps * np.asarray(cnorm)[:, None]  # n x 1
+    dtb = dt if dx is None else dt + np.asarray(cnorm)[:, None] * np.asarray(dx)[None, :]
     l1 = form.endswith("1")
     if l1:
         s = np.maximum(mu * np.abs(T) - gam, 0.0)
         active = s > 0
         dfdt = 2.0 * s * mu
-        band = np.maximum(1e-6 * gam, 3.0 * mu * dt)
+        band = np.maximum(1e-6 * gam, 3.0 * mu * dtb)
         zr = s
     else:
         u = mu * T
         active = u * u > gam
         dfdt = 2.0 * mu * mu * np.abs(T)
-        band = np.maximum(1e-6 * gam, 6.0 * mu * mu * np.abs(T) * dt)
+        band = np.maximum(1e-6 * gam, 6.0 * mu * mu * np.abs(T) * dtb)
         zr = np.abs(u) * active
     df = np.sqrt(np.sum(np.where(active, (dfdt * dt) ** 2, 0.0), axis=0))
     dz = np.sqrt(np.sum(np.where(active, (mu * dt) ** 2, 0.0), axis=0))
@@ -68,11 +95,42 @@ def derived_bounds(form, ref, cnorm, eps):
     return dict(df=3.0 * df, rel_z=rel_z, near=margin <= band)
 
 
-def assert_matches(form, g, ref, cnorm, tol_z=1e-5, tol_f=1e-6, tol_x=1e-5, iters_slack=1, check_support=True,
-                   check_status=True, eps=EPS32):
+class _Checker:
+    def __init__(self, label):
+        self.label = label
+        self.worst = {}
+        self.fail = []
+
+    def check(self, quantity, err, stated, derived=0.0):
+        derived = float(derived)
+        limit = max(stated, derived)
+        binding = "derived" if derived > stated else "stated"
+        LOG.append((self.label, quantity, float(err), limit, stated, binding))
+        if derived > MAX_DERIVED_RATIO * stated:
+            self.fail.append(f"{quantity}: derived limit {derived:.2e} is more than {MAX_DERIVED_RATIO:g}x the "
+                             f"stated {stated:.0e}")
+        if not err <= limit:
+            self.fail.append(f"{quantity}: error {err:.3e} > {limit:.2e} ({binding})")
+        key = quantity.split("[")[0]
+        r = err / limit if limit > 0 else 0.0
+        if key not in self.worst or r > self.worst[key][0]:
+            self.worst[key] = (r, err, limit, binding)
+
+    def report(self):
+        parts = [f"{k} {e:.2e}/{lim:.1e}({b[0]})" for k, (_, e, lim, b) in sorted(self.worst.items())]
+        print(f"[parity] {self.label}: " + "  ".join(parts))
+        assert not self.fail, f"{self.label}: " + "; ".join(self.fail[:6])
+
+
+def assert_matches(form, g, ref, cnorm, tol_z=1e-5, tol_f=1e-6, tol_x=1e-5, iters_slack=0, check_support=True,
+                   check_status=True, eps=EPS32, label=None, dx=None):
+    """Element-by-element comparison of a GPU result ``g`` with an oracle
+    result ``ref`` at the stated limits (derived ones where larger, module
+    docstring).  ``iters_slack`` > 0 is for results compared after
+    ``align_to_gpu_stop``, which has already checked the stopping index."""
     n, m = ref.Z.shape
-    b = derived_bounds(form, ref, cnorm, eps)
-    block = form.startswith("B")
+    b = derived_bounds(form, ref, cnorm, eps, dx)
+    c = _Checker(label or f"{form} m={m}")
     if check_status:
         np.testing.assert_array_equal(g["status"], ref.status)
     assert np.all(np.abs(g["iters"] - ref.iters) <= iters_slack), (g["iters"], ref.iters)
@@ -82,24 +140,76 @@ def assert_matches(form, g, ref, cnorm, tol_z=1e-5, tol_f=1e-6, tol_x=1e-5, iter
         if nz == 0:
             assert np.all(g["Z"][:, j] == 0), f"column {j}: oracle zero, gpu not"
         else:
-            err = np.linalg.norm(g["Z"][:, j] - zr) / nz
-            tz = max(tol_z, b["rel_z"][j])
-            assert err <= tz, f"column {j}: loadings rel err {err:.3e} > {tz:.1e}"
+            c.check(f"loadings[{j}]", np.linalg.norm(g["Z"][:, j] - zr) / nz, tol_z, b["rel_z"][j])
         fr = ref.objective[j]
         if fr != 0:
-            ef = abs(g["objective"][j] - fr) / abs(fr)
-            tf = max(10 * tol_f if block else tol_f, b["df"][j] / abs(fr))
-            assert ef <= tf, f"column {j}: objective rel err {ef:.3e} > {tf:.1e}"
+            c.check(f"objective[{j}]", abs(g["objective"][j] - fr) / abs(fr), tol_f, b["df"][j] / abs(fr))
         else:
-            assert g["objective"][j] == 0
-    if ref.total != 0:
-        et = abs(np.sum(g["objective"]) - ref.total) / abs(ref.total)
-        tt = max(tol_f, np.sqrt(np.sum(b["df"] ** 2)) / abs(ref.total))
-        assert et <= tt, f"total objective rel err {et:.3e} > {tt:.1e}"
-    ex = np.linalg.norm(g["X"] - ref.X) / np.sqrt(m)
-    assert ex <= tol_x, f"iterate err {ex:.3e} > {tol_x:.1e}"
+            assert g["objective"][j] == 0, f"column {j}: oracle objective 0, gpu {g['objective'][j]}"
+    if ref.total != 0 and m > 1:
+        c.check("total", abs(np.sum(g["objective"]) - ref.total) / abs(ref.total), tol_f,
+                np.sqrt(np.sum(b["df"] ** 2)) / abs(ref.total))
+    c.check("iterate", np.linalg.norm(g["X"] - ref.X) / np.sqrt(m), tol_x)
     if check_support:
         sup = unpack_support(g["support"], n)
         diff = (sup != (ref.Z != 0)) & ~b["near"]
         assert not diff.any(), f"support differs at {np.argwhere(diff)[:5].tolist()}"
         assert np.array_equal(sup, g["Z"] != 0)
+        LOG.append((c.label, "support", float(np.sum(sup != (ref.Z != 0))), 0.0, 0.0, "band"))
+    c.report()
+
+
+def _rel_changes(hist):
+    h = np.asarray(hist, dtype=np.float64)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        return np.abs(np.diff(h)) / h[:-1]  # r[k-1] = |f_k - f_{k-1}| / f_{k-1}, k >= 1
+
+
+def align_to_gpu_stop(A, form, gamma, mu, ref, g, tol, x0=None, slack=2):
+    """Oracle state at the GPU's stopping sweep where the two stop apart.
+
+    For each solve whose GPU sweep count differs from the oracle's (by at
+    most ``slack``), runs the oracle for the larger count with tol = 0,
+    checks that each sweep where the decisions differ sits on the boundary
+    (oracle relative change within STOP_MARGIN * tol of tol), and returns an
+    oracle result holding, for that solve, the oracle's state after the GPU's
+    number of sweeps (status copied from the GPU's).  Other solves keep the
+    oracle's own result.
+    """
+    gi = np.asarray(g["iters"]).astype(np.int64)
+    if np.array_equal(gi, ref.iters):
+        return ref
+    assert np.all(np.abs(gi - ref.iters) <= slack), (gi, ref.iters)
+    block = form.startswith("B")
+    out = oracle.OracleResult(ref.X.copy(), ref.Z.copy(), ref.objective.copy(), ref.iters.copy(),
+                              ref.status.copy(), ref.gamma, ref.mu, list(ref.history), ref.T.copy())
+    cols = [list(range(len(gi)))] if block else [[j] for j in range(len(gi)) if gi[j] != ref.iters[j]]
+    for js in cols:
+        j0 = js[0]
+        kg, ko = int(gi[j0]), int(ref.iters[j0])
+        if kg == ko:
+            continue
+        kmax = max(kg, ko)
+        sub_x0 = None if x0 is None else (x0 if block else np.asarray(x0)[:, js])
+        long = oracle.gpower(A, form, np.asarray(gamma)[js], mu=None if not block else mu, tol=0.0,
+                             maxit=kmax, x0=sub_x0)
+        r = _rel_changes(long.history[0])
+        for k in range(min(kg, ko), kg + 1):
+            # the decision after the k-th sweep: stop when r[k-2] < tol (k >= 2)
+            if k - 2 < 0 or k - 2 >= r.size:
+                continue
+            rk = r[k - 2]
+            if (k == kg) == (rk < tol):
+                continue  # both decide alike here
+            assert abs(rk - tol) <= STOP_MARGIN * tol, (
+                f"solve {js}: GPU stopped after {kg} sweeps, oracle after {ko}; oracle relative change "
+                f"{rk:.3e} after sweep {k} is not on the boundary tol = {tol:g}")
+        at = oracle.gpower(A, form, np.asarray(gamma)[js], mu=None if not block else mu, tol=0.0, maxit=kg,
+                           x0=sub_x0)
+        out.X[:, js] = at.X
+        out.Z[:, js] = at.Z
+        out.T[:, js] = at.T
+        out.objective[js] = at.objective
+        out.iters[js] = at.iters
+        out.status[js] = np.asarray(g["status"])[js]
+    return out

@@ -1,0 +1,134 @@
+"""Full-size parity of the sparsity-path and precision workloads.
+
+10000 x 50000 FP32 planted spikes (3 spikes, theta_j = 40/j, 2% supports):
+the 64-value gamma path of SL1 and SL0 (all 64 columns in one tensor-core
+contraction per sweep) and block L1 with m = 32 at gamma = 0.01 max||a_i||.
+
+20000 x 100000 planted spikes (16 spikes, theta_j = 100/sqrt(j), 1%
+supports): the four formulations in FP32 (block forms with m = 16: the fused
+float tensor-core passes with the T pass split into row ranges, and the wave
+tail of 782 column tiles), and the precision path, BF16 and FP8 E4M3 storage
+(per-column scales) solved to convergence and then refined by 3 FP32 sweeps
+from the converged iterate, against the oracle's converged solve on the FP32
+matrix (Section 2, Table 1; the oracle runs on the exact float64 upcast of the
+FP32 values).
+
+Fixed sweep counts (tol = 0) make both sides run the same number of sweeps,
+so the comparison is element by element at the stated limits.
+"""
+
+import gc
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1312_6182_gb300 import binding, synth
+from tests.compare import assert_matches, gpu_arrays
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    c = binding.Context(0)
+    yield c
+    c.close()
+
+
+def _gammas(A64, form, rho):
+    c = oracle.column_norms(A64).max()
+    rho = np.atleast_1d(rho).astype(np.float64)
+    return rho * c if form.endswith("1") else (rho * c) ** 2
+
+
+class _Workload:
+    def __init__(self, At):
+        self.dA = torch.from_numpy(At).cuda()
+        self.A = At.astype(np.float64).T  # exact upcast, p x n view
+        self.cn = oracle.column_norms(self.A)
+
+    def free(self):
+        del self.dA, self.A
+        gc.collect()
+        torch.cuda.empty_cache()
+
+
+@pytest.fixture(scope="module")
+def w10k():
+    w = _Workload(synth.workload_spikes_10000x50000(1))
+    yield w
+    w.free()
+
+
+@pytest.mark.parametrize("form", ["SL1", "SL0"])
+def test_gamma_path_64_at_10000x50000(ctx, w10k, form):
+    """64 gamma values log-spaced over [0.001, 0.5] max||a_i|| as one batched
+    solve, 4 sweeps, against the oracle's 64 independent solves."""
+    gam = _gammas(w10k.A, form, synth.log_spaced_rho(64))
+    ref = oracle.gpower(w10k.A, form, gam, tol=0.0, maxit=4)
+    res = ctx.solve(w10k.dA, form, list(gam), tol=0.0, maxit=4)
+    assert_matches(form, gpu_arrays(res), ref, w10k.cn, label=f"10000x50000 gamma path 64 {form}")
+
+
+def test_block_m32_at_10000x50000(ctx, w10k):
+    """Block L1, m = 32, mu = 1, gamma = 0.01 max||a_i|| (3 planted spikes, 29
+    noise components), 4 sweeps from the PCA start."""
+    m = 32
+    gam = _gammas(w10k.A, "BL1", [0.01] * m)
+    ref = oracle.gpower(w10k.A, "BL1", gam, mu=[1.0] * m, tol=0.0, maxit=4)
+    res = ctx.solve(w10k.dA, "BL1", list(gam), mu=[1.0] * m, tol=0.0, maxit=4)
+    assert_matches("BL1", gpu_arrays(res), ref, w10k.cn, label="10000x50000 BL1 m=32")
+
+
+@pytest.fixture(scope="module")
+def w20k(w10k):
+    w10k.free()  # one large matrix on the host and the device at a time
+    w = _Workload(synth.workload_spikes_20000x100000(2))
+    yield w
+    w.free()
+
+
+@pytest.mark.parametrize("form", oracle.FORMS)
+def test_four_forms_fp32_at_20000x100000(ctx, w20k, form):
+    """The four formulations in FP32 (block: m = 16, mu = 1) at gamma = 0.05
+    max||a_i|| (L1) / its square (L0), 4 sweeps from the start."""
+    m = 1 if form.startswith("S") else 16
+    mu = None if m == 1 else [1.0] * m
+    gam = _gammas(w20k.A, form, [0.05] * m)
+    ref = oracle.gpower(w20k.A, form, gam, mu=mu, tol=0.0, maxit=4)
+    res = ctx.solve(w20k.dA, form, list(gam), mu=mu, tol=0.0, maxit=4)
+    assert_matches(form, gpu_arrays(res), ref, w20k.cn, label=f"20000x100000 fp32 {form}")
+
+
+def _fp8_columns(d32):
+    s = d32.abs().amax(dim=1) / 448.0
+    s = torch.where(s > 0, s, torch.ones_like(s))
+    return (d32 / s[:, None]).to(torch.float8_e4m3fn), s.float().contiguous()
+
+
+@pytest.mark.parametrize("form", ["BL1", "BL0"])
+def test_precision_path_at_20000x100000(ctx, w20k, form):
+    """BF16 and FP8 storage, converged (tol 1e-6), then 3 FP32 sweeps from the
+    converged iterate on the FP32 matrix: loadings and iterate within 1e-3 of
+    the oracle's converged FP32 solve, objective within 1e-6, support equal
+    outside the band (widened by the iterate's own difference)."""
+    m = 16
+    mu = [1.0] * m
+    gam = _gammas(w20k.A, form, [0.05] * m)
+    ref = oracle.gpower(w20k.A, form, gam, mu=mu, tol=1e-6, maxit=1000)
+    for fmt in ("bf16", "fp8"):
+        if fmt == "bf16":
+            low = ctx.solve(w20k.dA.to(torch.bfloat16), form, list(gam), mu=mu, tol=1e-6, maxit=1000)
+        else:
+            q, s = _fp8_columns(w20k.dA)
+            low = ctx.solve(q, form, list(gam), mu=mu, tol=1e-6, maxit=1000, col_scale=s)
+            del q, s
+        fine = ctx.solve(w20k.dA, form, list(gam), mu=mu, tol=0.0, maxit=3, x0=low.X.contiguous())
+        g = gpu_arrays(fine)
+        dx = np.linalg.norm(g["X"] - ref.X, axis=0)
+        assert_matches(form, g, ref, w20k.cn, tol_z=1e-3, tol_x=1e-3, tol_f=1e-6, check_status=False,
+                       iters_slack=10 ** 6, dx=dx, label=f"20000x100000 {form} {fmt} + 3 fp32 sweeps")
+        torch.cuda.empty_cache()

@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 from paper_1312_6182_gb300 import binding, synth
-from tests.compare import assert_matches, gpu_arrays
+from tests.compare import align_to_gpu_stop, assert_matches, gpu_arrays
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -45,6 +45,14 @@ def _run(ctx, At, form, gam, mu=None, tol=1e-6, maxit=1000, ld=None, x0=None, **
     p = At.shape[1]
     res = ctx.solve(dA, form, list(gam), mu=mu, tol=tol, maxit=maxit, p=p, x0=x0, **kw)
     return gpu_arrays(res), res
+
+
+def _converged(form, g, A, gam, mu, ref, tol, label, slack=2, **kw):
+    """A solve run to convergence: where GPU and oracle stop a sweep apart
+    (the decision sits on the tol boundary), compare with the oracle's state
+    after the GPU's sweep count; then the stated limits."""
+    ref = align_to_gpu_stop(A, form, gam, mu, ref, g, tol, slack=slack)
+    assert_matches(form, g, ref, oracle.column_norms(A), label=label, **kw)
 
 
 # ---------------------------------------------------------------- workload sizes
@@ -84,7 +92,7 @@ def test_spikes_5000x20000_fp32(ctx, spikes_full, form, mu):
     gam = _gammas(A, form, [0.05] * m)
     ref = oracle.gpower(A, form, gam, mu=mu, tol=1e-6, maxit=1000)
     g, _ = _run(ctx, At, form, gam, mu=mu, tol=1e-6, maxit=1000)
-    assert_matches(form, g, ref, oracle.column_norms(A), tol_z=1e-5, tol_f=1e-6, tol_x=1e-5)
+    _converged(form, g, A, gam, mu, ref, 1e-6, f"5000x20000 {form} mu={mu}")
 
 
 # ---------------------------------------------------------------- fixed sweep counts
@@ -107,7 +115,7 @@ def test_fixed_sweeps_ragged(ctx, form, ld):
         gam = _gammas(A, form, [0.03] * 3) * (np.array(mu) if form.endswith("1") else np.array(mu) ** 2)
     ref = oracle.gpower(A, form, gam, mu=mu, tol=0.0, maxit=15)
     g, _ = _run(ctx, At, form, gam, mu=mu, tol=0.0, maxit=15, ld=ld)
-    assert_matches(form, g, ref, oracle.column_norms(A), tol_z=2e-5, tol_f=1e-6, tol_x=2e-5, iters_slack=0)
+    assert_matches(form, g, ref, oracle.column_norms(A), label=f"ragged {form} ld={ld}")
 
 
 @pytest.mark.parametrize("form", ["SL1", "SL0"])
@@ -119,7 +127,7 @@ def test_gamma_path_64(ctx, form):
     gam = _gammas(A, form, synth.log_spaced_rho(64))
     ref = oracle.gpower(A, form, gam, tol=1e-6, maxit=300)
     g, _ = _run(ctx, At, form, gam, tol=1e-6, maxit=300)
-    assert_matches(form, g, ref, oracle.column_norms(A), tol_z=1e-4, tol_f=1e-6, tol_x=1e-4, iters_slack=2)
+    _converged(form, g, A, gam, None, ref, 1e-6, f"gamma path 64 {form} (CUDA cores)")
 
 
 @pytest.mark.parametrize("p,n,m", [(1500, 8000, 16), (2000, 12000, 32)])
@@ -133,7 +141,7 @@ def test_block_many_components(ctx, p, n, m):
     gam = _gammas(A, "BL1", [0.02] * m)
     ref = oracle.gpower(A, "BL1", gam, mu=[1.0] * m, tol=0.0, maxit=8)
     g, _ = _run(ctx, At, "BL1", gam, mu=[1.0] * m, tol=0.0, maxit=8)
-    assert_matches("BL1", g, ref, oracle.column_norms(A), tol_z=5e-5, tol_f=1e-6, tol_x=5e-5, iters_slack=0)
+    assert_matches("BL1", g, ref, oracle.column_norms(A), label=f"BL1 m={m} {p}x{n}")
 
 
 # ---------------------------------------------------------------- tensor-core (tcgen05) sweep
@@ -151,8 +159,7 @@ def test_tensor_core_sweep_block_matches_oracle(ctx, form, p, n, m):
     mu = [1.0] * m
     ref = oracle.gpower(A, form, gam, mu=mu, tol=0.0, maxit=8)
     res = ctx.solve(tb.cuda(), form, list(gam), mu=mu, tol=0.0, maxit=8)
-    assert_matches(form, gpu_arrays(res), ref, oracle.column_norms(A), tol_z=5e-5, tol_f=1e-6, tol_x=5e-5,
-                   iters_slack=0)
+    assert_matches(form, gpu_arrays(res), ref, oracle.column_norms(A), label=f"tc bf16 {form} m={m} {p}x{n}")
 
 
 @pytest.mark.parametrize("form", ["SL1", "SL0"])
@@ -165,8 +172,7 @@ def test_tensor_core_gamma_path_64(ctx, form):
     gam = _gammas(A, form, synth.log_spaced_rho(64))
     ref = oracle.gpower(A, form, gam, tol=1e-6, maxit=300)
     res = ctx.solve(tb.cuda(), form, list(gam), tol=1e-6, maxit=300)
-    assert_matches(form, gpu_arrays(res), ref, oracle.column_norms(A), tol_z=1e-4, tol_f=1e-6, tol_x=1e-4,
-                   iters_slack=2)
+    _converged(form, gpu_arrays(res), A, gam, None, ref, 1e-6, f"tc gamma path 64 {form} bf16")
 
 
 @pytest.mark.parametrize("form", ["BL1", "SL0"])
@@ -185,8 +191,7 @@ def test_tensor_core_sweep_fp8_storage(ctx, form, p):
     mu = [1.0] * m if form.startswith("B") else None
     ref = oracle.gpower(A, form, gam, mu=mu, tol=0.0, maxit=6)
     res = ctx.solve(q.cuda(), form, list(gam), mu=mu, tol=0.0, maxit=6, col_scale=sc.cuda())
-    assert_matches(form, gpu_arrays(res), ref, oracle.column_norms(A), tol_z=5e-5, tol_f=1e-6, tol_x=5e-5,
-                   iters_slack=0)
+    assert_matches(form, gpu_arrays(res), ref, oracle.column_norms(A), label=f"tc fp8 {form} p={p}")
 
 
 @pytest.mark.parametrize("dtype,form,p,n,m", [
@@ -215,12 +220,11 @@ def test_tensor_core_sweep_edge_shapes(ctx, dtype, form, p, n, m):
     res = ctx.solve(tA, form, list(gam), mu=mu, tol=0.0, maxit=3, allow_degenerate=True)
     if block and m > 4:
         # more components than spikes: compare only the well-determined objective
-        assert abs(res.objective.sum().item() - ref.total) / ref.total < 1e-5
+        assert abs(res.objective.sum().item() - ref.total) / ref.total < 1e-6
         X = res.X.double().cpu().numpy().T
         assert np.abs(X.T @ X - np.eye(m)).max() < 1e-5
     else:
-        assert_matches(form, gpu_arrays(res), ref, oracle.column_norms(A), tol_z=5e-5, tol_f=1e-6, tol_x=5e-5,
-                       iters_slack=0)
+        assert_matches(form, gpu_arrays(res), ref, oracle.column_norms(A), label=f"tc edge {dtype} {form} m={m}")
 
 
 @pytest.mark.parametrize("dtype,form,p,n,m", [
@@ -253,8 +257,7 @@ def test_tensor_core_t_pass_row_ranges(ctx, dtype, form, p, n, m):
     mu = [1.0] * m if block else None
     ref = oracle.gpower(A, form, gam, mu=mu, tol=0.0, maxit=4)
     res = ctx.solve(tA, form, list(gam), mu=mu, tol=0.0, maxit=4)
-    assert_matches(form, gpu_arrays(res), ref, oracle.column_norms(A), tol_z=5e-5, tol_f=1e-6, tol_x=5e-5,
-                   iters_slack=0)
+    assert_matches(form, gpu_arrays(res), ref, oracle.column_norms(A), label=f"tc row ranges {dtype} {form} {p}x{n}")
     again = ctx.solve(tA, form, list(gam), mu=mu, tol=0.0, maxit=4)
     assert torch.equal(res.Z, again.Z) and torch.equal(res.X, again.X)
 
@@ -303,7 +306,7 @@ def test_bf16_storage_matches_oracle_on_stored_values(ctx, form):
     gam = _gammas(A, form, [0.05] * m)
     ref = oracle.gpower(A, form, gam, mu=mu, tol=1e-6, maxit=500)
     res = ctx.solve(tb.cuda(), form, list(gam), mu=mu, tol=1e-6, maxit=500)
-    assert_matches(form, gpu_arrays(res), ref, oracle.column_norms(A), tol_z=1e-5, tol_f=1e-6, tol_x=1e-5)
+    _converged(form, gpu_arrays(res), A, gam, mu, ref, 1e-6, f"bf16 storage {form}")
 
 
 @pytest.mark.parametrize("form", ["SL0", "BL1"])
@@ -317,7 +320,7 @@ def test_fp8_storage_matches_oracle_on_stored_values(ctx, form):
     gam = _gammas(A, form, [0.05] * m)
     ref = oracle.gpower(A, form, gam, mu=mu, tol=1e-6, maxit=500)
     res = ctx.solve(q.cuda(), form, list(gam), mu=mu, tol=1e-6, maxit=500, col_scale=s.cuda())
-    assert_matches(form, gpu_arrays(res), ref, oracle.column_norms(A), tol_z=1e-5, tol_f=1e-6, tol_x=1e-5)
+    _converged(form, gpu_arrays(res), A, gam, mu, ref, 1e-6, f"fp8 storage {form}")
 
 
 @pytest.mark.parametrize("fmt", ["bf16", "fp8"])
@@ -339,10 +342,13 @@ def test_low_precision_then_fp32_refinement(ctx, fmt):
     x0 = low.X.contiguous()
     fine = ctx.solve(torch.from_numpy(At).cuda(), "BL1", list(gam), mu=mu, tol=0.0, maxit=3, x0=x0)
     g = gpu_arrays(fine)
-    for j in range(4):
-        err = np.linalg.norm(g["Z"][:, j] - ref.Z[:, j]) / np.linalg.norm(ref.Z[:, j])
-        assert err < 1e-3, (fmt, j, err)
-    assert abs(np.sum(g["objective"]) - ref.total) / ref.total < 1e-4
+    # stated: loadings and iterate 1e-3 after the low-precision solve and the
+    # refinement, objective 1e-6, support outside the band; the band and the
+    # objective limit also carry the iterate's own difference (each t_i moves
+    # by at most ||a_i|| ||x_j - x_j^oracle||)
+    dx = np.linalg.norm(g["X"] - ref.X, axis=0)
+    assert_matches("BL1", g, ref, oracle.column_norms(A), tol_z=1e-3, tol_x=1e-3, tol_f=1e-6, check_status=False,
+                   iters_slack=10 ** 6, dx=dx, label=f"{fmt} + 3 fp32 sweeps")
 
 
 # ---------------------------------------------------------------- API behaviour
@@ -370,8 +376,9 @@ def test_relative_gamma_is_scaled_on_device(ctx):
                         gamma_relative=True)
         ga = res.gamma_abs.cpu().numpy()
         np.testing.assert_allclose(ga, oracle.gamma_from_rho(A, form, rho), rtol=1e-12)
-        ref = oracle.gpower(A, form, ga, mu=None if m == 1 else [1.0, 1.0])
-        assert_matches(form, gpu_arrays(res), ref, oracle.column_norms(A))
+        mu = None if m == 1 else [1.0, 1.0]
+        ref = oracle.gpower(A, form, ga, mu=mu)
+        _converged(form, gpu_arrays(res), A, ga, mu, ref, 1e-6, f"relative gamma {form}")
 
 
 def test_warm_start_x0(ctx):
@@ -383,10 +390,41 @@ def test_warm_start_x0(ctx):
     ref = oracle.gpower(A, "BL0", gam, mu=[1.0, 1.0], tol=0.0, maxit=10, x0=x0)
     g, _ = _run(ctx, At, "BL0", gam, mu=[1.0, 1.0], tol=0.0, maxit=10,
                 x0=torch.from_numpy(x0.T.astype(np.float32).copy()).cuda())
-    # ten sweeps from a random start stop on an unconverged trajectory that
-    # amplifies per-sweep float rounding: loadings, iterate and per-component
-    # objectives at 2e-5 (the converged cases hold the stated 1e-5 / 1e-6)
-    assert_matches("BL0", g, ref, oracle.column_norms(A), tol_z=2e-5, tol_f=2e-6, tol_x=2e-5, iters_slack=0)
+    assert_matches("BL0", g, ref, oracle.column_norms(A), label="warm start x0 BL0")
+
+
+@pytest.mark.parametrize("cond", [1e6, 1e8, 1e10])
+def test_polar_factor_of_ill_conditioned_start(ctx, cond):
+    """The block polar step X = Y (Y^T Y)^{-1/2} (Section 2, Stiefel
+    projection) on a caller's start Y whose Gram matrix has condition `cond`
+    (up to 1e10; the degenerate limit is 1e12).  The GPU forms Y^T Y in double
+    and solves the m x m eigenproblem by Jacobi in double-float (about 48
+    significant bits), so its smallest eigenvalue carries an error of about
+    2^-48 cond relative to itself; the bound below is that, with a float32
+    output, against the FP64 polar factor (SVD).  An FP64 Gram + eigh polar
+    factor is printed beside it for scale."""
+    p, m = 1200, 4
+    rng = np.random.default_rng(27)
+    Q, _ = np.linalg.qr(rng.standard_normal((p, m)))
+    R, _ = np.linalg.qr(rng.standard_normal((m, m)))
+    s = np.geomspace(1.0, cond ** -0.5, m)
+    Y = ((Q * s) @ R.T).astype(np.float32)  # p x m
+    Y64 = Y.astype(np.float64)
+    X_svd, degenerate = oracle.polar(Y64)
+    assert not degenerate
+    w, V = np.linalg.eigh(Y64.T @ Y64)
+    X_eigh = Y64 @ (V / np.sqrt(w)) @ V.T
+    At = synth.planted_spike(p, 3000, 2, [30.0, 15.0], support_frac=0.05, seed=28, dtype=np.float32)
+    gam = list(_gammas(At.astype(np.float64).T, "BL1", [0.05] * m))
+    res = ctx.solve(torch.from_numpy(At).cuda(), "BL1", gam, mu=[1.0] * m, tol=0.0, maxit=1,
+                    x0=torch.from_numpy(np.ascontiguousarray(Y.T)).cuda())
+    X = res.X.double().cpu().numpy().T
+    err = np.abs(X - X_svd).max()
+    orth = np.abs(X.T @ X - np.eye(m)).max()
+    bound = 4.0 * (2.0 ** -24 * np.sqrt(m) + 2.0 ** -46 * cond)
+    print(f"[polar] cond {cond:.0e}: gpu {err:.2e}, orthogonality {orth:.2e}, fp64 gram+eigh "
+          f"{np.abs(X_eigh - X_svd).max():.2e}, bound {bound:.1e}")
+    assert err <= bound and orth <= bound
 
 
 def test_deterministic(ctx):
@@ -424,7 +462,7 @@ def test_tiny_shapes(ctx):
         gam = _gammas(A, form, [0.1] * m)
         ref = oracle.gpower(A, form, gam, mu=mu, tol=0.0, maxit=6)
         g, _ = _run(ctx, At, form, gam, mu=mu, tol=0.0, maxit=6)
-        assert_matches(form, g, ref, oracle.column_norms(A), tol_z=1e-5, tol_x=1e-5, iters_slack=0)
+        assert_matches(form, g, ref, oracle.column_norms(A), label=f"tiny {p}x{n} {form}")
 
 
 def test_zero_matrix_and_large_gamma(ctx):
@@ -469,6 +507,25 @@ def test_nonfinite_input_is_reported(ctx, form):
     ctx.solve(torch.from_numpy(At).cuda(), form, [0.1] * m, mu=mu)
 
 
+@pytest.mark.parametrize("eager", [False, True])
+def test_timeout_status_maps_to_etimedout(ctx, eager):
+    """A solve whose device state carries the timeout bit (set on the host
+    after the solve ran: the INJECT_TIMEOUT test hook; no device wait is made
+    to expire) returns GPSPCA_ETIMEDOUT, and the context's next solve is the
+    one it would have been without it."""
+    At = synth.planted_spike(600, 2000, 2, [30.0, 15.0], support_frac=0.05, seed=26, dtype=np.float32)
+    dA = torch.from_numpy(At).cuda()
+    with pytest.raises(binding.GpspcaError) as e:
+        ctx.solve(dA, "BL1", [0.05, 0.05], mu=[1.0, 1.0], gamma_relative=True, eager=eager,
+                  extra_flags=binding.INJECT_TIMEOUT)
+    assert e.value.code == binding.ETIMEDOUT and "gave up" in str(e.value)
+    after = ctx.solve(dA, "BL1", [0.05, 0.05], mu=[1.0, 1.0], gamma_relative=True, eager=eager)
+    with binding.Context(0) as fresh:
+        ref = fresh.solve(dA, "BL1", [0.05, 0.05], mu=[1.0, 1.0], gamma_relative=True, eager=eager)
+    assert after.rc == binding.OK
+    assert torch.equal(after.Z, ref.Z) and torch.equal(after.X, ref.X) and torch.equal(after.iters, ref.iters)
+
+
 def test_degenerate_polar_status(ctx):
     At = np.random.default_rng(20).standard_normal((30, 12)).astype(np.float32)
     A = At.astype(np.float64).T
@@ -478,7 +535,7 @@ def test_degenerate_polar_status(ctx):
     res = ctx.solve(torch.from_numpy(At).cuda(), "BL1", gam, mu=[1.0, 1.0])
     assert res.rc == binding.EDEGENERATE
     g = gpu_arrays(res)
-    assert_matches("BL1", g, ref, oracle.column_norms(A), iters_slack=0)
+    assert_matches("BL1", g, ref, oracle.column_norms(A), label="degenerate polar")
 
 
 def test_invalid_arguments(ctx):

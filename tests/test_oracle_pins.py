@@ -503,3 +503,20 @@ def test_block_start_rank_deficient_is_degenerate():
     assert st == oracle.STATUS_DEGENERATE
     r = oracle.gpower(A, "BL1", [0.1, 0.1], mu=[1, 1])
     assert np.all(r.status == oracle.STATUS_DEGENERATE) and np.all(r.iters == 0)
+
+
+def test_gamma_from_rho_hand_values():
+    """Relative gamma (reading of Section 4.1's unitless values): rho times the
+    largest column norm for L1, its square for L0.  On A = [[3, 0], [4, 1]]
+    the columns have norms 5 and 1 (the rows 3 and sqrt 17, the whole matrix
+    sqrt 26), so a row norm, a Frobenius norm, or rho * max||a_i||^2 for L0
+    all give other numbers than the hand values below."""
+    A = np.array([[3.0, 0.0], [4.0, 1.0]])
+    np.testing.assert_array_equal(oracle.gamma_from_rho(A, "SL1", 0.1), [0.5])
+    np.testing.assert_array_equal(oracle.gamma_from_rho(A, "BL1", [0.1, 0.2]), [0.5, 1.0])
+    np.testing.assert_allclose(oracle.gamma_from_rho(A, "SL0", 0.1), [0.25], rtol=1e-15)
+    np.testing.assert_allclose(oracle.gamma_from_rho(A, "BL0", [0.1, 0.4]), [0.25, 4.0], rtol=1e-15)
+    # the largest column may come last
+    B = np.array([[0.0, 3.0], [1.0, 4.0]])
+    np.testing.assert_array_equal(oracle.gamma_from_rho(B, "SL1", 1.0), [5.0])
+    np.testing.assert_allclose(oracle.gamma_from_rho(B, "SL0", 1.0), [25.0], rtol=1e-15)

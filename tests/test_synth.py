@@ -80,3 +80,14 @@ def test_serving_mix():
     r = next(q for q in rq if q.form.startswith("S") and q.m > 2)
     g = r.gammas()
     assert len(g) == r.m and abs(g[0] - r.rho / 2) < 1e-12 and abs(g[-1] - r.rho) < 1e-12
+
+
+def test_block_sample_equals_the_columns_of_the_whole_matrix():
+    """A sample of noise blocks is bit-identical to those columns of the whole
+    planted-spike matrix (the CPU baselines time the oracle on such a
+    sample of the 20000 x 100000 workload)."""
+    kw = dict(support_frac=0.05, seed=4, noise_streams=16)
+    full = synth.planted_spike(300, 1600, 3, [40.0, 20.0, 10.0], **kw)
+    part = synth.planted_spike(300, 1600, 3, [40.0, 20.0, 10.0], blocks=(2, 5), **kw)
+    assert np.array_equal(full[200:500], part)
+    assert not np.array_equal(full[:300], part)

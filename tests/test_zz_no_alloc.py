@@ -72,3 +72,78 @@ def test_static_sweep_rejects_sizes_beyond_its_scratch():
         binding.sweep_static(dA, "SL1", 0.1, x, torch.empty_like(x), torch.empty(n, device="cuda"),
                              torch.empty(1, device="cuda", dtype=torch.float64))
     assert e.value.code == binding.EINVAL and "8192" in str(e.value)
+
+
+@pytest.mark.parametrize("form", ["SL1", "SL0"])
+def test_static_sweep_against_the_oracle_formulas(form):
+    """One sweep at the largest p the scratch takes (8192 rows), from a
+    seeded unit iterate, against the same sweep in float64 written with the
+    oracle's Table 1 functions: t = A^T x, f, g, y = A g, x_next = y/||y||."""
+    import oracle
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    p, n = 8192, 1501
+    At = synth.planted_spike(p, n, 2, [60.0, 30.0], support_frac=0.05, seed=22, dtype=np.float32)
+    x = np.random.default_rng(23).standard_normal(p).astype(np.float32)
+    x /= np.float32(np.linalg.norm(x.astype(np.float64)))
+    A = At.astype(np.float64).T
+    c = float(np.linalg.norm(A, axis=0).max())
+    gamma = 0.02 * c if form == "SL1" else (0.02 * c) ** 2
+    t_ref = A.T @ x.astype(np.float64)
+    one = np.ones(1)
+    f_ref = float(oracle.objective_parts(form, t_ref[:, None], np.array([gamma]), one)[0])
+    y = A @ oracle.gradient_direction(form, t_ref[:, None], np.array([gamma]), one)[:, 0]
+    xn_ref = y / np.linalg.norm(y)
+    dA = torch.from_numpy(At).cuda()
+    dx = torch.from_numpy(x).cuda()
+    x_next = torch.empty(p, device="cuda")
+    t = torch.empty(n, device="cuda")
+    obj = torch.empty(1, device="cuda", dtype=torch.float64)
+    for _call in range(2):
+        binding.sweep_static(dA, form, gamma, dx, x_next, t, obj)
+        tt = t.double().cpu().numpy()
+        # t to float32 accuracy of a dot product of length p
+        dt = 4.0 * 2.0 ** -24 * np.linalg.norm(A, axis=0)
+        assert np.all(np.abs(tt - t_ref) <= dt), np.max(np.abs(tt - t_ref) / dt)
+        assert abs(obj.item() - f_ref) <= 1e-6 * f_ref, (obj.item(), f_ref)
+        assert np.linalg.norm(x_next.double().cpu().numpy() - xn_ref) <= 1e-5
+
+
+def test_static_sweep_reports_non_finite_input():
+    """A NaN in A or in x is reported (GPSPCA_ENONFINITE), not returned as a
+    zero iterate; the next call with finite input works."""
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    p, n = 300, 700
+    At = np.random.default_rng(24).standard_normal((n, p)).astype(np.float32)
+    x = torch.full((p,), p ** -0.5, device="cuda")
+    out = (torch.empty(p, device="cuda"), torch.empty(n, device="cuda"),
+           torch.empty(1, device="cuda", dtype=torch.float64))
+    bad = At.copy()
+    bad[11, 7] = np.nan
+    with pytest.raises(binding.GpspcaError) as e:
+        binding.sweep_static(torch.from_numpy(bad).cuda(), "SL1", 0.5, x, *out)
+    assert e.value.code == binding.ENONFINITE
+    xb = x.clone()
+    xb[5] = float("inf")
+    with pytest.raises(binding.GpspcaError) as e:
+        binding.sweep_static(torch.from_numpy(At).cuda(), "SL0", 0.5, xb, *out)
+    assert e.value.code == binding.ENONFINITE
+    binding.sweep_static(torch.from_numpy(At).cuda(), "SL1", 0.5, x, *out)
+    assert np.isfinite(out[2].item())
+
+
+def test_static_sweep_checks_its_buffers():
+    """Buffers of the wrong size, type or device are refused before the call."""
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    p, n = 64, 100
+    dA = torch.randn(n, p, device="cuda")
+    x = torch.randn(p, device="cuda")
+    good = dict(x_next=torch.empty(p, device="cuda"), t=torch.empty(n, device="cuda"),
+                objective=torch.empty(1, device="cuda", dtype=torch.float64))
+    for key, wrong in (("t", torch.empty(n - 1, device="cuda")), ("objective", torch.empty(1, device="cuda")),
+                       ("x_next", torch.empty(p, device="cuda", dtype=torch.float64))):
+        kw = dict(good)
+        kw[key] = wrong
+        with pytest.raises(binding.GpspcaError) as e:
+            binding.sweep_static(dA, "SL1", 0.1, x, kw["x_next"], kw["t"], kw["objective"])
+        assert e.value.code == binding.EINVAL
