@@ -27,13 +27,18 @@ __device__ __forceinline__ void split3(float v, __nv_bfloat16& b0, __nv_bfloat16
 // written out for the active components and split into X3^T for the T pass;
 // one thread per (row, component), blockIdx.y the component.
 __global__ void tc_prep_kernel(const TcArgs a) {
-  __shared__ float wj[kMaxM];
+  __shared__ float wj[kMaxM], wlo[kMaxM];
   const IO* io = a.io;
   const State* st = a.st;
   const int m = a.m, p = a.p, j = blockIdx.y;
   const bool block = a.form >= 2;
-  // column j of W (its diagonal entry alone for the single-unit forms)
-  if (threadIdx.x < m) wj[threadIdx.x] = j < m ? static_cast<float>(st->W[threadIdx.x * m + j]) : 0.0f;
+  // column j of W (its diagonal entry alone for the single-unit forms), as
+  // a high and a low float part
+  if (threadIdx.x < m) {
+    const double w = j < m ? st->W[threadIdx.x * m + j] : 0.0;
+    wj[threadIdx.x] = static_cast<float>(w);
+    wlo[threadIdx.x] = static_cast<float>(w - static_cast<double>(wj[threadIdx.x]));
+  }
   __syncthreads();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= p) return;
@@ -41,7 +46,21 @@ __global__ void tc_prep_kernel(const TcArgs a) {
   float x = 0.0f;
   if (j < m) {
     if (block) {
-      for (int l = 0; l < m; ++l) x += Y[static_cast<int64_t>(l) * p + r] * wj[l];
+      // Y W with every product's and sum's rounding error carried in a second
+      // accumulator (Dekker's exact product by fma, Knuth's two-sum): X is Y W
+      // rounded once to float even where W's large entries make the sum cancel
+      float xe = 0.0f;
+      for (int l = 0; l < m; ++l) {
+        const float yv = Y[static_cast<int64_t>(l) * p + r];
+        const float pr = __fmul_rn(yv, wj[l]);
+        const float pe = fmaf(yv, wj[l], -pr);
+        const float s2 = __fadd_rn(x, pr);
+        const float bb = __fsub_rn(s2, x);
+        const float se = __fadd_rn(__fsub_rn(x, __fsub_rn(s2, bb)), __fsub_rn(pr, bb));
+        x = s2;
+        xe += pe + se + yv * wlo[l];
+      }
+      x = __fadd_rn(x, xe);
     } else {
       x = Y[static_cast<int64_t>(j) * p + r] * wj[j];
     }

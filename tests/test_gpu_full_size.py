@@ -51,7 +51,7 @@ class _Workload:
         self.cn = oracle.column_norms(self.A)
 
     def free(self):
-        del self.dA, self.A
+        self.dA = self.A = None
         gc.collect()
         torch.cuda.empty_cache()
 

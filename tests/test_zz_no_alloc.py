@@ -76,19 +76,20 @@ def test_static_sweep_rejects_sizes_beyond_its_scratch():
 
 @pytest.mark.parametrize("form", ["SL1", "SL0"])
 def test_static_sweep_against_the_oracle_formulas(form):
-    """One sweep at the largest p the scratch takes (8192 rows), from a
-    seeded unit iterate, against the same sweep in float64 written with the
-    oracle's Table 1 functions: t = A^T x, f, g, y = A g, x_next = y/||y||."""
+    """One sweep at the largest p the scratch takes (8192 rows), from the
+    single-unit start (the largest column, normalised), against the same
+    sweep in float64 written with the oracle's Table 1 functions: t = A^T x,
+    f, g, y = A g, x_next = y/||y||."""
     import oracle
 
     assert torch.cuda.is_available(), "GPU tests need a CUDA device"
     p, n = 8192, 1501
     At = synth.planted_spike(p, n, 2, [60.0, 30.0], support_frac=0.05, seed=22, dtype=np.float32)
-    x = np.random.default_rng(23).standard_normal(p).astype(np.float32)
-    x /= np.float32(np.linalg.norm(x.astype(np.float64)))
     A = At.astype(np.float64).T
-    c = float(np.linalg.norm(A, axis=0).max())
-    gamma = 0.02 * c if form == "SL1" else (0.02 * c) ** 2
+    cn = np.linalg.norm(A, axis=0)
+    x = (A[:, int(np.argmax(cn))] / cn.max()).astype(np.float32)
+    c = float(cn.max())
+    gamma = 0.05 * c if form == "SL1" else (0.05 * c) ** 2
     t_ref = A.T @ x.astype(np.float64)
     one = np.ones(1)
     f_ref = float(oracle.objective_parts(form, t_ref[:, None], np.array([gamma]), one)[0])
@@ -107,6 +108,7 @@ def test_static_sweep_against_the_oracle_formulas(form):
         assert np.all(np.abs(tt - t_ref) <= dt), np.max(np.abs(tt - t_ref) / dt)
         assert abs(obj.item() - f_ref) <= 1e-6 * f_ref, (obj.item(), f_ref)
         assert np.linalg.norm(x_next.double().cpu().numpy() - xn_ref) <= 1e-5
+        assert np.count_nonzero(oracle.gradient_direction(form, t_ref[:, None], np.array([gamma]), one)) > 10
 
 
 def test_static_sweep_reports_non_finite_input():
