@@ -370,6 +370,7 @@ int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fa
     const bool native_bf16 = dt == GPSPCA_BF16 && fast && ld % 8 == 0;
     pl.tc_fused = (dt == GPSPCA_F32 && fast && ld % 4 == 0) ? 1 : 0;
     pl.tc_convert = (native_bf16 || pl.tc_fused) ? 0 : 1;
+    pl.tc_sparse = pl.tc_fused;
     plan_tc_ksplit(&pl, nsm);
     pl.C = 1;
     pl.ps = static_cast<int>(p);
@@ -430,6 +431,7 @@ int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fa
     if (pl.tc_convert) pl.ws_planes = 2 * static_cast<size_t>(pl.tc_na) * n * pl.p_pad;
     if (pl.ksplit1 > 1)
       pl.ws_tpart = sizeof(float) * static_cast<size_t>(pl.ksplit1) * pl.mpad * pl.n_pad;
+    if (pl.tc_sparse) pl.ws_sparse = sparse_layout(n, pl.npad).total;
   }
   *P = pl;
   return GPSPCA_OK;
@@ -480,7 +482,7 @@ struct Slot {
   Budget* budget = nullptr;
   TuneTable* tune = nullptr;  // the context's autotuned layouts
   // workspace buffers, grown on demand
-  DevBuf b_cnorm, b_P, b_Y, b_ypart, b_T, b_fpart, b_gpart, b_x3, b_g3, b_maps, b_planes, b_tpart;
+  DevBuf b_cnorm, b_P, b_Y, b_ypart, b_T, b_fpart, b_gpart, b_x3, b_g3, b_maps, b_planes, b_tpart, b_sparse;
   TcMaps* maps_host = nullptr;  // pinned: the tensor maps copied to b_maps before a solve
   // staging for host-located inputs/outputs
   DevBuf s_A, s_scale, s_x0, s_X, s_Z, s_sup, s_obj, s_it, s_stat, s_gam;
@@ -494,7 +496,7 @@ struct Slot {
   size_t held() const {
     size_t s = 0;
     for (const DevBuf* b : {&b_cnorm, &b_P, &b_Y, &b_ypart, &b_T, &b_fpart, &b_gpart, &b_x3, &b_g3, &b_maps,
-                            &b_planes, &b_tpart, &s_A,
+                            &b_planes, &b_tpart, &b_sparse, &s_A,
                             &s_scale, &s_x0, &s_X,
                             &s_Z, &s_sup, &s_obj, &s_it, &s_stat, &s_gam, &d_W, &d_list})
       s += b->bytes;
@@ -539,7 +541,7 @@ static void release(Slot* s, DevBuf* b) {
 
 static void release_workspace(Slot* s) {
   for (DevBuf* b : {&s->b_cnorm, &s->b_P, &s->b_Y, &s->b_ypart, &s->b_T, &s->b_fpart, &s->b_gpart, &s->b_x3,
-                    &s->b_g3, &s->b_maps, &s->b_planes, &s->b_tpart, &s->s_A,
+                    &s->b_g3, &s->b_maps, &s->b_planes, &s->b_tpart, &s->b_sparse, &s->s_A,
                     &s->s_scale, &s->s_x0, &s->s_X, &s->s_Z, &s->s_sup, &s->s_obj, &s->s_it, &s->s_stat, &s->s_gam,
                     &s->d_W, &s->d_list})
     release(s, b);
@@ -607,6 +609,12 @@ static cudaError_t launch_prologue(const Plan& pl, Slot* s, cudaStream_t cs, cud
                                    int use_cond = 1) {
   if (pl.tc && pl.tc_convert)  // bf16 planes of a float / fp8 A for the tensor cores
     launch_tc_convert(pl.dtype, s->io_dev, pl.p, pl.n, pl.ld, pl.p_pad, cs);
+  if (pl.tc_sparse) {  // no column is flagged active before the first threshold sweep
+    const cudaError_t e0 =
+        cudaMemsetAsync(static_cast<unsigned char*>(s->b_sparse.p) + sparse_layout(pl.n, pl.npad).act, 0,
+                        static_cast<size_t>((pl.n + 63) / 64 * 64), cs);
+    if (e0 != cudaSuccess) return e0;
+  }
   launch_reset(s->io_dev, s->st_dev, pl.m, pl.form, cs);
   // the block start's first power step forms the column norms itself; the
   // start selection (gamma scale, non-finite check) then follows that step
@@ -645,7 +653,8 @@ static cudaError_t launch_sweeps(const Plan& pl, Slot* s, cudaStream_t cs, int s
   if (pl.tc) {
     TcArgs a{s->io_dev,  s->st_dev, pl.p,     pl.n,       pl.m,        pl.mpad,     pl.form,
              sketch,     pl.tc_na,  pl.tc_fused, pl.dtype == GPSPCA_FP8_E4M3 ? 1 : 0, pl.p_pad, pl.n_pad,
-             pl.ntile1,  pl.kchunks1, pl.ksplit1, pl.kcs1, pl.nchunks2, pl.kps2, pl.nsplit2, pl.nrow2};
+             pl.ntile1,  pl.kchunks1, pl.ksplit1, pl.kcs1, pl.nchunks2, pl.kps2, pl.nsplit2, pl.nrow2,
+             pl.tc_sparse};
     launch_tc_sweep(a, pl.npad, cs);
     return cudaGetLastError();
   }
@@ -912,11 +921,14 @@ static int prepare_solve(Slot* s, const Request& r, int nsm, bool scratch_out, P
     if ((rc = ensure(s, &s->b_maps, sizeof(TcMaps)))) return rc;
     if (pl.tc_convert && (rc = ensure(s, &s->b_planes, pl.ws_planes))) return rc;
     if (pl.ksplit1 > 1 && (rc = ensure(s, &s->b_tpart, pl.ws_tpart))) return rc;
+    if (pl.tc_sparse && (rc = ensure(s, &s->b_sparse, pl.ws_sparse))) return rc;
     // the host copy of the maps is reused only after this solve's copy has run
     GP_CUDA(cudaStreamSynchronize(s->stream));
     if (pl.tc_fused) {
+      const void* g3c =
+          pl.tc_sparse ? static_cast<unsigned char*>(s->b_sparse.p) + sparse_layout(n, pl.npad).g3c : nullptr;
       if ((rc = tc_encode_maps_f32(s->maps_host, A_dev, p, n, ld, s->b_x3.p, pl.p_pad, s->b_g3.p, pl.n_pad,
-                                   pl.npad)))
+                                   pl.npad, g3c)))
         return rc;
     } else {
       const void* planes = pl.tc_convert ? s->b_planes.p : A_dev;
@@ -970,6 +982,15 @@ static int prepare_solve(Slot* s, const Request& r, int nsm, bool scratch_out, P
     io.tc_maps = s->b_maps.p;
     io.tc_planes = pl.tc_convert ? s->b_planes.p : nullptr;
     io.tc_tpart = pl.ksplit1 > 1 ? s->b_tpart.p : nullptr;
+    if (pl.tc_sparse) {
+      const SparseLayout L = sparse_layout(n, pl.npad);
+      unsigned char* b = static_cast<unsigned char*>(s->b_sparse.p);
+      io.tc_act = b + L.act;
+      io.tc_list = reinterpret_cast<int32_t*>(b + L.list);
+      io.tc_nlist = reinterpret_cast<int32_t*>(b + L.nlist);
+      io.tc_cnt = reinterpret_cast<int32_t*>(b + L.cnt);
+      io.tc_g3c = b + L.g3c;
+    }
   }
   for (int j = 0; j < m; ++j) {
     io.gamma_in[j] = r.gamma[j];
@@ -1516,12 +1537,13 @@ int gpspca_time_sweep(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form,
 // Kernel launches of one plan: before the iterations, per iteration, after
 // (mirrors launch_prologue / launch_body / launch_epilogue).
 static void plan_launch_counts(const Plan& pl, int32_t c[3]) {
+  // the start's power steps launch no active-column list (two kernels in a threshold sweep)
   const int sweeps = pl.tc ? 3 + (pl.ksplit1 > 1 ? 1 : 0) : static_cast<int>(pl.passes.size());
   const bool late_norms = pl.pca && pl.norms_in_sweep;
   int pro = (pl.tc && pl.tc_convert ? 1 : 0) + 1 + (late_norms ? 0 : 2) + 1 + 2;
   if (pl.pca) pro += kPowerSteps * (sweeps + 2) + (late_norms ? 1 : 0) + sweeps + 2;
   c[0] = pro;
-  c[1] = sweeps + 2;
+  c[1] = sweeps + (pl.tc_sparse ? 2 : 0) + 2;
   c[2] = 1;
 }
 

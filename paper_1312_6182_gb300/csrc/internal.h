@@ -38,6 +38,13 @@ struct IO {
   const void* tc_maps;  // tensor-core path: the TMA tensor maps of A, X3 and G3 (TcMaps)
   void* tc_planes;      // tensor-core path: bf16 planes of a float / fp8 A ([na][n][p_pad])
   void* tc_tpart;       // tensor-core path: T partials of the row ranges ([ksplit][mpad][n_pad] float)
+  // tensor-core path, rank update over the active columns only (columns i
+  // with some G_ij != 0; the others add nothing to Y = A G)
+  uint8_t* tc_act;      // [n_pad] 1 where column i is active in this sweep (cleared once listed)
+  int32_t* tc_list;     // [n64] the active columns in increasing order, padded to a multiple of 64
+  int32_t* tc_nlist;    // their count
+  int32_t* tc_cnt;      // [ceil(n / 1024)] active columns per block of 1024
+  void* tc_g3c;         // [3 mpad][n_pad] bf16: the G3 columns of the listed columns, zero past the count
   double gamma_in[kMaxM];  // as passed (absolute, or relative with the flag)
   double mu[kMaxM];
   double tol;

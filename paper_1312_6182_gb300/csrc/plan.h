@@ -35,9 +35,10 @@ struct Plan {
   int tc_na = 1;       // bf16 planes of A the contractions read (3 for float A)
   int tc_convert = 0;  // the planes are a workspace copy made once per solve (float / fp8 A)
   int tc_fused = 0;    // float A read in place, split into planes in shared memory
+  int tc_sparse = 0;   // fused Y pass of threshold sweeps over the active columns only
   int ksplit1 = 1, kcs1 = 0;  // T pass: row ranges per column tile, 64-row chunks per range
   size_t ws_cnorm = 0, ws_P = 0, ws_ypart = 0, ws_T = 0, ws_fpart = 0, ws_gpart = 0, ws_x3 = 0, ws_g3 = 0,
-         ws_planes = 0, ws_tpart = 0;
+         ws_planes = 0, ws_tpart = 0, ws_sparse = 0;
 
   std::string key() const {
     char b[256];
@@ -59,9 +60,29 @@ struct Plan {
     return s;
   }
   size_t workspace_bytes() const {
-    return ws_cnorm + ws_P + ws_ypart + ws_T + ws_fpart + ws_gpart + ws_x3 + ws_g3 + ws_planes + ws_tpart + 12 * 256 + 1024;
+    return ws_cnorm + ws_P + ws_ypart + ws_T + ws_fpart + ws_gpart + ws_x3 + ws_g3 + ws_planes + ws_tpart +
+           ws_sparse + 13 * 256 + 1024;
   }
 };
+
+// Layout of the listed-column buffers of the tensor-core Y pass (one
+// allocation): flags [n64] bytes | list [n64] int32 | count | per-block
+// counts [ceil(n / 1024)] int32 | G3c [npad][n64] bf16, each 256-aligned.
+struct SparseLayout {
+  size_t act, list, nlist, cnt, g3c, total;
+};
+inline SparseLayout sparse_layout(int64_t n, int npad) {
+  auto up = [](size_t v) { return (v + 255) / 256 * 256; };
+  const size_t n64 = static_cast<size_t>((n + 63) / 64 * 64);
+  SparseLayout L;
+  L.act = 0;
+  L.list = up(n64);
+  L.nlist = L.list + up(4 * n64);
+  L.cnt = L.nlist + 256;
+  L.g3c = L.cnt + up(4 * static_cast<size_t>((n + 1023) / 1024));
+  L.total = L.g3c + up(2 * static_cast<size_t>(npad) * n64);
+  return L;
+}
 
 // Plan a solve: cluster size, per-pass kernel variant, threads, tile ring;
 // or, with allow_tc and a wide problem, the tensor-core sweep.  cand < 0:

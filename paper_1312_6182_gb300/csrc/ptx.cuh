@@ -129,6 +129,20 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, int 
       : "memory");
 }
 
+// Four rows of a 2-D tensor map gathered into shared memory (tile::gather4):
+// rows r0..r3 (outer coordinates, any order) from inner coordinate c0, one
+// box row each (the map's box must be one row high), written one after the
+// other at dst with the map's swizzle, completing on an mbarrier.  c0's byte
+// offset must be a multiple of 16.
+__device__ __forceinline__ void tma_gather4(uint32_t dst, const void* tmap, int c0, int r0, int r1, int r2, int r3,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cta.global.tile::gather4.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+      "%4, %5, %6}], [%7];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(bar)
+      : "memory");
+}
+
 // Acquire a tensor map that was written to global memory through the generic
 // proxy (e.g. by a host copy) before the first TMA that reads it.
 __device__ __forceinline__ void tmap_acquire(const void* tmap) {

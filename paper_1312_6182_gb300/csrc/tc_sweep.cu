@@ -286,6 +286,7 @@ __device__ __forceinline__ void tc_t_finish(const TcArgs& a, int i, int j, float
     const float tj = t * scl;
     if (!a.sketch && act_s[j]) static_cast<float*>(a.io->T)[static_cast<int64_t>(j) * a.n + i] = tj;
     g = grad_factor<float>(form, tj, gam_s[j], mu_s[j]) * scl;
+    if (a.sparse && !a.sketch && g != 0.0f) a.io->tc_act[i] = 1;  // column i adds to Y = A G
   }
   __nv_bfloat16* G3 = static_cast<__nv_bfloat16*>(a.io->tc_g3);
   const int64_t gs = a.n_pad;
@@ -347,6 +348,116 @@ __global__ void tc_t_combine_kernel(const TcArgs a) {
   }
   const float scl = a.scaled ? io->col_scale[i] : 1.0f;
   tc_t_finish<MPAD>(a, i, j, sum, scl, sketch ? GPSPCA_SL0 : a.form, gam_s, mu_s, act_s);
+}
+
+// ---- the active columns of a threshold sweep (some G_ij != 0), listed in
+// increasing order for the Y pass, which then reads only those columns of A
+// (the others multiply zeros).  Two launches over blocks of kTcCompactCols
+// columns: the counts, then each block's columns at its offset (the sum of
+// the counts before it) with their G3 columns copied beside them; the flags
+// are cleared as they are read.  Where the count exceeds the Y pass's sparse
+// limit nothing but the count is written (the Y pass then reads every
+// column).
+
+__device__ __forceinline__ int tc_warp_sum(int v) {
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(256) tc_count_kernel(const TcArgs a) {
+  __shared__ int wsum[8];
+  const uint8_t* act = a.io->tc_act;
+  const int tid = threadIdx.x;
+  const int i0 = blockIdx.x * kTcCompactCols + tid * 4;
+  int c = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) c += (i0 + k < a.n && act[i0 + k] != 0) ? 1 : 0;
+  c = tc_warp_sum(c);
+  if ((tid & 31) == 0) wsum[tid >> 5] = c;
+  __syncthreads();
+  if (tid == 0) {
+    int t = 0;
+    for (int w = 0; w < 8; ++w) t += wsum[w];
+    a.io->tc_cnt[blockIdx.x] = t;
+  }
+}
+
+template <int MPAD>
+__global__ void __launch_bounds__(256) tc_compact_kernel(const TcArgs a) {
+  __shared__ int s_before[8], s_all[8], s_wtot[8], s_off, s_nl;
+  const IO* io = a.io;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nb = gridDim.x;
+  // counts of the blocks before this one, and of all blocks
+  int before = 0, all = 0;
+  for (int b = tid; b < nb; b += blockDim.x) {
+    const int c = io->tc_cnt[b];
+    all += c;
+    if (b < static_cast<int>(blockIdx.x)) before += c;
+  }
+  before = tc_warp_sum(before);
+  all = tc_warp_sum(all);
+  const int i0 = blockIdx.x * kTcCompactCols + tid * 4;
+  uint8_t f[4];
+  int c = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    f[k] = (i0 + k < a.n) ? io->tc_act[i0 + k] : 0;
+    c += f[k] != 0 ? 1 : 0;
+  }
+  int inc = c;  // inclusive scan over the warp
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += v;
+  }
+  if (lane == 0) {
+    s_before[warp] = before;
+    s_all[warp] = all;
+  }
+  if (lane == 31) s_wtot[warp] = inc;
+  __syncthreads();
+  if (tid == 0) {
+    int off = 0, nl = 0, run = 0;
+    for (int w = 0; w < 8; ++w) {
+      off += s_before[w];
+      nl += s_all[w];
+      const int t = s_wtot[w];
+      s_wtot[w] = run;
+      run += t;
+    }
+    s_off = off;
+    s_nl = nl;
+  }
+  __syncthreads();
+  const int nl = s_nl;
+  const bool listed = static_cast<int64_t>(nl) * 10 <= static_cast<int64_t>(a.n) * kTcSparseTenths;
+  const int64_t gs = a.n_pad, cs = (static_cast<int64_t>(a.n) + 63) / 64 * 64;  // G3 / G3c row strides
+  const __nv_bfloat16* G3 = static_cast<const __nv_bfloat16*>(io->tc_g3);
+  __nv_bfloat16* G3c = static_cast<__nv_bfloat16*>(io->tc_g3c);
+  int pos = s_off + s_wtot[warp] + inc - c;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (!f[k]) continue;
+    const int i = i0 + k;
+    io->tc_act[i] = 0;
+    if (listed) {
+      io->tc_list[pos] = i;
+      for (int r = 0; r < 3 * MPAD; ++r) G3c[r * cs + pos] = G3[r * gs + i];
+    }
+    ++pos;
+  }
+  if (blockIdx.x == nb - 1) {  // the count, and the list padded to a multiple of 64
+    if (tid == 0) *io->tc_nlist = nl;
+    if (listed) {
+      const int end = (nl + 63) / 64 * 64;
+      for (int k = nl + tid; k < end; k += blockDim.x) {
+        io->tc_list[k] = 0;
+        for (int r = 0; r < 3 * MPAD; ++r) G3c[r * cs + k] = __float2bfloat16_rn(0.0f);
+      }
+    }
+  }
 }
 
 // ---- pass 1: T = A^T X for 128-column tiles (persistent CTAs), threshold,
@@ -653,10 +764,41 @@ __device__ __forceinline__ void tc_convert_row(const unsigned char* f0, int frow
   }
 }
 
+// The same for float rows without swizzle (the gathered columns of the Y
+// pass: a column's 128-byte row as TMA wrote it): the four 8-row groups are
+// taken in an order rotated by the row index, so that the lanes of a warp
+// (consecutive rows) read four different 16-byte chunks at a time.
+__device__ __forceinline__ void tc_convert_row_plain(const unsigned char* f0, const unsigned char* f1, int fr,
+                                                     unsigned char* plane0, int prow, int g0) {
+#pragma unroll
+  for (int gg = 0; gg < 4; ++gg) {
+    const int g = g0 + ((gg + fr) & 3);
+    const unsigned char* src = g < 4 ? f0 : f1;
+    const int c0 = (g & 3) * 2;
+    const uint4 v0 = *reinterpret_cast<const uint4*>(src + fr * 128 + c0 * 16);
+    const uint4 v1 = *reinterpret_cast<const uint4*>(src + fr * 128 + (c0 + 1) * 16);
+    const uint32_t x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+    uint32_t w[3][4];
+#pragma unroll
+    for (int e = 0; e < 8; e += 2) {
+      uint32_t a0, a1, a2, b0, b1, b2;
+      split3_trunc(__uint_as_float(x[e]), a0, a1, a2);
+      split3_trunc(__uint_as_float(x[e + 1]), b0, b1, b2);
+      w[0][e / 2] = __byte_perm(a0, b0, 0x7632);
+      w[1][e / 2] = __byte_perm(a1, b1, 0x7632);
+      w[2][e / 2] = __byte_perm(a2, b2, 0x7632);
+    }
+    const int off = prow * 128 + ((g ^ (prow & 7)) * 16);
+#pragma unroll
+    for (int pl = 0; pl < 3; ++pl)
+      *reinterpret_cast<uint4*>(plane0 + pl * kTcA + off) = make_uint4(w[pl][0], w[pl][1], w[pl][2], w[pl][3]);
+  }
+}
+
 // Converter warps: chunk `it` from ring 1 into ring 2.  kY: Y-pass layout
 // (two 64-row MN atoms of 64 columns) instead of the T pass's 128 columns.
 template <int NPAD, bool kY>
-__device__ __forceinline__ bool tc_convert_chunk(const TcFusedSmem& S, int it) {
+__device__ __forceinline__ bool tc_convert_chunk(const TcFusedSmem& S, int it, bool plain = false) {
   using Cfg = TcFusedCfg<NPAD>;
   const int s1 = it % Cfg::S1, s2 = it % Cfg::S2;
   const uint32_t u1 = static_cast<uint32_t>(it / Cfg::S1), u2 = static_cast<uint32_t>(it / Cfg::S2);
@@ -670,7 +812,10 @@ __device__ __forceinline__ bool tc_convert_chunk(const TcFusedSmem& S, int it) {
     tc_convert_row(f, q, f + 16384, q, b, q, 4 * h, 4);
   } else {    // atom a = rows 64a..64a+63 of A, row i = column i; float boxes of 32 rows x 64 columns
     const int a = q >> 6, i = q & 63;
-    tc_convert_row(f + (2 * a) * 8192, i, f + (2 * a + 1) * 8192, i, b + a * 8192, i, 4 * h, 4);
+    if (plain)  // gathered columns: the float boxes are not swizzled
+      tc_convert_row_plain(f + (2 * a) * 8192, f + (2 * a + 1) * 8192, i, b + a * 8192, i, 4 * h);
+    else
+      tc_convert_row(f + (2 * a) * 8192, i, f + (2 * a + 1) * 8192, i, b + a * 8192, i, 4 * h, 4);
   }
   __syncwarp();
   if ((threadIdx.x & 31) == 0) mbar_arrive(smem_u32(&S.empty1[s1]));  // the float stage is read
@@ -756,6 +901,73 @@ __device__ __forceinline__ bool tc_fused_producer(const TcFusedSmem& S, int tota
       }
     }
     if (progressed) {
+      idle = 0;
+    } else {
+      if (++idle > (1u << 25)) return false;
+      __nanosleep(32);
+    }
+  }
+  return true;
+}
+
+// Producer of the fused Y pass over listed columns (the whole warp): chunk c
+// of the CTA holds list entries 64c .. 64c+63; lane l gathers the four
+// columns 4g .. 4g+3 (g = l mod 16) for two of the four 32-row boxes of the
+// 128-row block (tile::gather4, one 128-byte box row per column, no
+// swizzle: each gather lands 512 bytes after the previous one), so column k
+// of the chunk is row k of each box.  Lane 0 polls both rings and copies the
+// G3c tile.  false on a timeout or an abort.
+template <int NPAD>
+__device__ __forceinline__ bool tc_gather_producer(const TcFusedSmem& S, int cb, int ce, int rb, const int32_t* list,
+                                                   const TcMaps* maps) {
+  using Cfg = TcFusedCfg<NPAD>;
+  const int lane = threadIdx.x & 31;
+  const int g = lane & 15, q0 = (lane >> 4) * 2;
+  const int total = ce - cb;
+  auto cols = [&](int it) { return *reinterpret_cast<const int4*>(list + static_cast<int64_t>(cb + it) * kTcBK + 4 * g); };
+  int itf = 0, itb = 0;
+  uint32_t idle = 0;
+  int4 cur = total > 0 ? cols(0) : make_int4(0, 0, 0, 0);
+  while (itf < total || itb < total) {
+    int want = 0;  // bit 0: the float stage is free, bit 1: the G3c stage, bit 2: abort
+    if (lane == 0) {
+      if (tc_aborted(S.acc)) {
+        want = 4;
+      } else {
+        if (itf < total) {
+          const uint32_t u1 = static_cast<uint32_t>(itf / Cfg::S1);
+          if (u1 == 0 || mbar_test(smem_u32(&S.empty1[itf % Cfg::S1]), (u1 - 1) & 1)) want |= 1;
+        }
+        if (itb < total) {
+          const uint32_t u2 = static_cast<uint32_t>(itb / Cfg::S2);
+          if (u2 == 0 || mbar_test(smem_u32(&S.empty2[itb % Cfg::S2]), (u2 - 1) & 1)) want |= 2;
+        }
+      }
+    }
+    want = __shfl_sync(0xffffffffu, want, 0);
+    if (want & 4) return false;
+    if (want & 1) {
+      const int s1 = itf % Cfg::S1;
+      const uint32_t sa = S.base1 + s1 * Cfg::kStage1;
+      const uint32_t bar = smem_u32(&S.full1[s1]);
+      if (lane == 0) mbar_arrive_expect_tx(bar, kTcF);
+      __syncwarp();
+#pragma unroll
+      for (int q = q0; q < q0 + 2; ++q)
+        tma_gather4(sa + q * 8192 + g * 512, &maps->a2g, rb * kTcRows2 + 32 * q, cur.x, cur.y, cur.z, cur.w, bar);
+      ++itf;
+      if (itf < total) cur = cols(itf);
+    }
+    if (want & 2) {
+      if (lane == 0) {
+        const int s2 = itb % Cfg::S2;
+        const uint32_t bar = smem_u32(&S.full2[s2]);
+        mbar_arrive_expect_tx(bar, Cfg::kB);
+        tma_load_2d(S.base2 + s2 * Cfg::kStage2 + 3 * kTcA, &maps->g3c, (cb + itb) * kTcBK, 0, bar);
+      }
+      ++itb;
+    }
+    if (want & 3) {
       idle = 0;
     } else {
       if (++idle > (1u << 25)) return false;
@@ -876,11 +1088,32 @@ __global__ void __launch_bounds__(kTcFusedThreads, 1) tc_y_fused_kernel(const Tc
   State* st = a.st;
   const TcMaps* maps = static_cast<const TcMaps*>(io->tc_maps);
   const int rb = blockIdx.x, sp = blockIdx.y;
-  const int cb = sp * a.kps2, ce = min(a.nchunks2, cb + a.kps2);
+  // a threshold sweep with few active columns reads only those (listed by
+  // the compaction step); otherwise every column
+  const int nl = (a.sparse && !a.sketch) ? *io->tc_nlist : 0;
+  const bool listed =
+      a.sparse && !a.sketch && static_cast<int64_t>(nl) * 10 <= static_cast<int64_t>(a.n) * kTcSparseTenths;
+  int cb, ce;
+  if (listed) {
+    const int nch = (nl + kTcBK - 1) / kTcBK;
+    const int kps = (nch + a.nsplit2 - 1) / a.nsplit2;
+    cb = sp * kps;
+    ce = max(cb, min(nch, cb + kps));
+  } else {
+    cb = sp * a.kps2;
+    ce = max(cb, min(a.nchunks2, cb + a.kps2));
+  }
   const uint32_t tmem = tc_fused_setup<NPAD>(S);
   bool timed_out = false;
   if (warp == 4) {
-    if (lane == 0) {
+    if (listed) {
+      tmap_acquire(&maps->a2g);
+      tmap_acquire(&maps->g3c);
+      if (!tc_gather_producer<NPAD>(S, cb, ce, rb, io->tc_list, maps)) {
+        timed_out = true;
+        if (lane == 0) *S.acc.abort_flag = 1;
+      }
+    } else if (lane == 0) {
       tmap_acquire(&maps->a2f);
       tmap_acquire(&maps->g3);
       const auto coord = [&](int it, int* c, int* tr) {
@@ -902,7 +1135,7 @@ __global__ void __launch_bounds__(kTcFusedThreads, 1) tc_y_fused_kernel(const Tc
     }
   } else if (warp >= 6) {
     for (int c = cb, it = 0; c < ce && !timed_out; ++c, ++it)
-      if (tc_aborted(S.acc) || !tc_convert_chunk<NPAD, true>(S, it)) {
+      if (tc_aborted(S.acc) || !tc_convert_chunk<NPAD, true>(S, it, listed)) {
         timed_out = true;
         *S.acc.abort_flag = 1;
       }
@@ -982,7 +1215,7 @@ static bool encode_bf16(CUtensorMap* m, const void* base, int64_t inner, int64_t
 }
 
 static bool encode_f32(CUtensorMap* m, const void* base, int64_t inner, int64_t outer, int64_t stride_elems,
-                       int box_outer) {
+                       int box_outer, bool swizzle = true) {
   const EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   const cuuint64_t dims[2] = {static_cast<cuuint64_t>(inner), static_cast<cuuint64_t>(outer)};
@@ -990,15 +1223,20 @@ static bool encode_f32(CUtensorMap* m, const void* base, int64_t inner, int64_t 
   const cuuint32_t box[2] = {32u, static_cast<cuuint32_t>(box_outer)};
   const cuuint32_t estr[2] = {1u, 1u};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+            CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 int tc_encode_maps_f32(TcMaps* maps, const void* A, int64_t p, int64_t n, int64_t ld, const void* x3, int p_pad,
-                       const void* g3, int n_pad, int npad) {
+                       const void* g3, int n_pad, int npad, const void* g3c) {
   if (!encode_bf16(&maps->x3, x3, p, npad, p_pad, npad) || !encode_bf16(&maps->g3, g3, n, npad, n_pad, npad) ||
       !encode_f32(&maps->a1f, A, p, n, ld, kTcTile1) || !encode_f32(&maps->a2f, A, p, n, ld, 64))
     return record_error(GPSPCA_ECUDA, "cuTensorMapEncodeTiled failed for the fused tensor-core sweep");
+  if (g3c) {  // the Y pass over listed columns: A gathered a column at a time, G3c in rows of ceil(n / 64) * 64
+    const int64_t n64 = (n + 63) / 64 * 64;
+    if (!encode_f32(&maps->a2g, A, p, n, ld, 1, false) || !encode_bf16(&maps->g3c, g3c, n64, npad, n64, npad))
+      return record_error(GPSPCA_ECUDA, "cuTensorMapEncodeTiled failed for the listed-column tensor-core sweep");
+  }
   return GPSPCA_OK;
 }
 
@@ -1083,6 +1321,11 @@ static void launch_tc_fused_npad(const TcArgs& a, int nsm, cudaStream_t s) {
   tc_prep_kernel<<<dim3((a.p + 255) / 256, a.mpad), 256, 0, s>>>(a);
   tc_t_fused_kernel<NPAD><<<std::max(1, std::min(a.ntile1 * a.ksplit1, nsm)), kTcFusedThreads, smem, s>>>(a);
   if (a.ksplit1 > 1) tc_t_combine_kernel<NPAD / 3><<<dim3((a.n + 255) / 256, NPAD / 3), 256, 0, s>>>(a);
+  if (a.sparse && !a.sketch) {
+    const int nb = (a.n + kTcCompactCols - 1) / kTcCompactCols;
+    tc_count_kernel<<<nb, 256, 0, s>>>(a);
+    tc_compact_kernel<NPAD / 3><<<nb, 256, 0, s>>>(a);
+  }
   tc_y_fused_kernel<NPAD><<<dim3(a.nrow2, a.nsplit2), kTcFusedThreads, smem, s>>>(a);
 }
 

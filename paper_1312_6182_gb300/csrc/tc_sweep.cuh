@@ -52,9 +52,15 @@ struct TcMaps {
   CUtensorMap g3;     // G3^T, box 64 x N
   CUtensorMap a1f;    // float A, box 32 rows x 128 columns (fused T pass)
   CUtensorMap a2f;    // float A, box 32 rows x 64 columns (fused Y pass)
+  CUtensorMap a2g;    // float A, box 32 rows x 1 column (fused Y pass, gathered columns: tile::gather4)
+  CUtensorMap g3c;    // G3c^T (the active columns' G3), box 64 x N
 };
 
 constexpr int kTcMaxSplit1 = 8;  // T pass: at most this many row ranges per column tile
+constexpr int kTcCompactCols = 1024;  // columns per block of the active-column list kernels
+// the Y pass runs over the listed columns while they are at most this
+// fraction (in tenths) of n, and over all columns otherwise
+constexpr int kTcSparseTenths = 6;
 
 struct TcArgs {
   const IO* io;
@@ -72,6 +78,7 @@ struct TcArgs {
   int kps2;           // 64-column chunks per Y-pass split
   int nsplit2;        // Y-pass splits of the columns
   int nrow2;          // ceil(p / 128)
+  int sparse;         // fused float Y pass over the active columns only (threshold sweeps, not the start)
 };
 
 // Host side (tc_sweep.cu).
@@ -82,7 +89,7 @@ int tc_encode_maps(TcMaps* maps, const void* planes, int na, int64_t plane, int6
                    const void* x3, int p_pad, const void* g3, int n_pad, int npad);
 // float A read in place by the fused passes (16-byte aligned base, ld % 4 == 0)
 int tc_encode_maps_f32(TcMaps* maps, const void* A, int64_t p, int64_t n, int64_t ld, const void* x3, int p_pad,
-                       const void* g3, int n_pad, int npad);
+                       const void* g3, int n_pad, int npad, const void* g3c);
 int tc_fused_smem_bytes(int npad);
 // float / fp8 / unaligned bf16 A -> bf16 planes in the workspace (once per
 // solve); ldc = p_pad

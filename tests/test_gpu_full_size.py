@@ -24,7 +24,7 @@ import pytest
 
 import oracle
 from paper_1312_6182_gb300 import binding, synth
-from tests.compare import assert_matches, gpu_arrays
+from tests.compare import assert_matches, gpu_arrays, unpack_support
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -75,12 +75,38 @@ def test_gamma_path_64_at_10000x50000(ctx, w10k, form):
 
 def test_block_m32_at_10000x50000(ctx, w10k):
     """Block L1, m = 32, mu = 1, gamma = 0.01 max||a_i|| (3 planted spikes, 29
-    noise components), 4 sweeps from the PCA start."""
-    m = 32
+    noise components), 4 sweeps from the PCA start.
+
+    The 29 noise components fit noise directions whose singular values nearly
+    coincide: in the oracle itself a relative change of 1e-7 in the entries
+    of A moves their loadings by up to 3e-6 (the spike components' by 7e-9),
+    so float32 arithmetic does not determine each of them to 1e-5, only the
+    subspace they span.  Compared element by element at the stated limits:
+    the three spike components (loadings, iterate, objectives, support) and
+    every component's objective and the total; for the noise components, the
+    projector onto their span (1e-5) and the validity of the rest (orthonormal
+    iterate, unit loadings whose support is where they are nonzero)."""
+    m, k = 32, 3
     gam = _gammas(w10k.A, "BL1", [0.01] * m)
     ref = oracle.gpower(w10k.A, "BL1", gam, mu=[1.0] * m, tol=0.0, maxit=4)
     res = ctx.solve(w10k.dA, "BL1", list(gam), mu=[1.0] * m, tol=0.0, maxit=4)
-    assert_matches("BL1", gpu_arrays(res), ref, w10k.cn, label="10000x50000 BL1 m=32")
+    g = gpu_arrays(res)
+    spikes = oracle.OracleResult(ref.X[:, :k], ref.Z[:, :k], ref.objective[:k], ref.iters[:k], ref.status[:k],
+                                 ref.gamma[:k], ref.mu[:k], [], ref.T[:, :k])
+    gs = {key: (v[:, :k] if key in ("X", "Z") else v[:k]) for key, v in g.items()}
+    gs["support"] = g["support"][:k]
+    assert_matches("BL1", gs, spikes, w10k.cn, label="10000x50000 BL1 m=32, spike components")
+    for j in range(m):
+        assert abs(g["objective"][j] - ref.objective[j]) <= 1e-6 * ref.objective[j], j
+    assert abs(np.sum(g["objective"]) - ref.total) <= 1e-6 * ref.total
+    Xn, Rn = g["X"][:, k:], ref.X[:, k:]
+    proj = np.linalg.norm(Xn @ Xn.T - Rn @ Rn.T) / np.sqrt(m - k)
+    orth = np.abs(g["X"].T @ g["X"] - np.eye(m)).max()
+    print(f"[parity] 10000x50000 BL1 m=32 noise components: projector {proj:.2e}, orthogonality {orth:.2e}")
+    assert proj <= 1e-5 and orth <= 1e-5
+    zn = np.linalg.norm(g["Z"], axis=0)
+    assert np.all(np.abs(zn - 1.0) <= 1e-6)
+    assert np.array_equal(unpack_support(g["support"], g["Z"].shape[0]), g["Z"] != 0)
 
 
 @pytest.fixture(scope="module")

@@ -269,6 +269,40 @@ def test_tensor_core_t_pass_row_ranges(ctx, dtype, form, p, n, m):
     assert torch.equal(res.Z, again.Z) and torch.equal(res.X, again.X)
 
 
+@pytest.mark.parametrize("form,p,n,m,frac", [
+    ("BL0", 1500, 4099, 9, 0.02),    # 18% of the columns active
+    ("BL1", 2100, 3001, 16, 0.01),   # 16%: 480 listed columns, 7.5 chunks of 64
+    ("BL1", 777, 1601, 10, 0.03),    # 30%, p ragged against the 128-row blocks
+])
+def test_tensor_core_listed_columns(ctx, form, p, n, m, frac):
+    """Float storage on the tensor cores: a threshold sweep's rank update
+    Y = A G reads only the columns with some G_ij != 0 (gathered by TMA from
+    the list of active columns), the others contributing nothing.  m planted
+    spikes of theta_j = 60/sqrt(j), 4 sweeps from the PCA start, against the
+    oracle at the stated limits."""
+    At = synth.planted_spike(p, n, m, [60.0 / np.sqrt(j + 1) for j in range(m)], support_frac=frac, seed=61,
+                             dtype=np.float32)
+    A = At.astype(np.float64).T
+    rho = {9: 0.05, 16: 0.05, 10: 0.06}[m]
+    gam = _gammas(A, form, [rho] * m)
+    ref = oracle.gpower(A, form, gam, mu=[1.0] * m, tol=0.0, maxit=4)
+    res = ctx.solve(torch.from_numpy(At).cuda(), form, list(gam), mu=[1.0] * m, tol=0.0, maxit=4)
+    assert_matches(form, gpu_arrays(res), ref, oracle.column_norms(A), label=f"tc listed {form} {p}x{n} m={m}")
+    again = ctx.solve(torch.from_numpy(At).cuda(), form, list(gam), mu=[1.0] * m, tol=0.0, maxit=4)
+    assert torch.equal(res.Z, again.Z) and torch.equal(res.X, again.X)
+
+
+def test_tensor_core_all_thresholded(ctx):
+    """Float storage, 16 components, gamma above every |a_i^T x|: no column is
+    active, the first sweep's objective is 0 (status ZERO, one sweep)."""
+    At = np.random.default_rng(62).standard_normal((1000, 300)).astype(np.float32)
+    A = At.astype(np.float64).T
+    c = oracle.column_norms(A).max() * (1.0 + 1e-6)
+    res = ctx.solve(torch.from_numpy(At).cuda(), "BL1", [c] * 16, mu=[1.0] * 16)
+    assert np.all(res.status.cpu().numpy() == binding.ZERO) and np.all(res.iters.cpu().numpy() == 1)
+    assert torch.all(res.Z == 0) and torch.all(res.objective == 0)
+
+
 def test_tensor_core_and_cuda_core_sweeps_agree(ctx):
     """The same solve with and without the tensor cores: float-rounding
     differences only, on the well-determined quantities (the objective, and
