@@ -855,6 +855,54 @@ void launch_finish(const FinishArgs& a, int smem, cudaStream_t s) {
   finish_kernel<<<1, kFinishThreads, smem, s>>>(a);
 }
 
+// Block forms on the CUDA cores: the iterate X = Y W of the next sweep (the
+// projection of Section 2: Y (Y^T Y)^{-1/2} for the polar step, the
+// Rayleigh-Ritz rotation after the start), one thread per (row, component).
+// Float compute carries W as a high and a low float part and every
+// product's and sum's rounding error in a second accumulator (Dekker's
+// exact product by fma, Knuth's two-sum), so X is Y W rounded once to float
+// even where W's entries (up to lambda_min(Y^T Y)^{-1/2}) make the sum
+// cancel; double compute sums in double.
+template <typename TC>
+__global__ void form_x_kernel(const IO* io, const State* st, int p, int m) {
+  __shared__ double wj[kMaxM];
+  const int j = blockIdx.y;
+  if (threadIdx.x < m) wj[threadIdx.x] = st->W[threadIdx.x * m + j];
+  __syncthreads();
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= p) return;
+  const TC* Y = static_cast<const TC*>(io->Y);
+  TC* X = static_cast<TC*>(io->Xf);
+  if constexpr (sizeof(TC) == 8) {
+    double x = 0.0;
+    for (int l = 0; l < m; ++l) x += Y[static_cast<int64_t>(l) * p + r] * wj[l];
+    X[static_cast<int64_t>(j) * p + r] = x;
+  } else {
+    float x = 0.0f, xe = 0.0f;
+    for (int l = 0; l < m; ++l) {
+      const float yv = Y[static_cast<int64_t>(l) * p + r];
+      const float wh = static_cast<float>(wj[l]);
+      const float wl = static_cast<float>(wj[l] - static_cast<double>(wh));
+      const float pr = __fmul_rn(yv, wh);
+      const float pe = fmaf(yv, wh, -pr);  // y w_hi = pr + pe exactly
+      const float s2 = __fadd_rn(x, pr);
+      const float bb = __fsub_rn(s2, x);
+      const float se = __fadd_rn(__fsub_rn(x, __fsub_rn(s2, bb)), __fsub_rn(pr, bb));  // x + pr = s2 + se
+      x = s2;
+      xe += pe + se + yv * wl;
+    }
+    X[static_cast<int64_t>(j) * p + r] = __fadd_rn(x, xe);
+  }
+}
+
+void launch_form_x(int tcsize, const IO* io, const State* st, int p, int m, cudaStream_t s) {
+  const dim3 grid((p + 255) / 256, m);
+  if (tcsize == 8)
+    form_x_kernel<double><<<grid, 256, 0, s>>>(io, st, p, m);
+  else
+    form_x_kernel<float><<<grid, 256, 0, s>>>(io, st, p, m);
+}
+
 void launch_finalize(int tcsize, const IO* io, const State* st, int p, int n, int m, int form, cudaStream_t s) {
   const int len = std::max(n, p);
   const dim3 grid((len + 255) / 256, m);

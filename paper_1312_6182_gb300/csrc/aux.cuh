@@ -72,5 +72,6 @@ void launch_gather_start(int dtype, const StartArgs& a, cudaStream_t s);
 void launch_reduce(int tcsize, const ReduceArgs& a, cudaStream_t s);
 void launch_finish(const FinishArgs& a, int smem, cudaStream_t s);
 void launch_finalize(int tcsize, const IO* io, const State* st, int p, int n, int m, int form, cudaStream_t s);
+void launch_form_x(int tcsize, const IO* io, const State* st, int p, int m, cudaStream_t s);
 
 }  // namespace gpspca

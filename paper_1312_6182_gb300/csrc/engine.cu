@@ -421,6 +421,7 @@ int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fa
                 pl.finish_smem, kFinishMaxSmem);
   pl.ws_cnorm = sizeof(double) * n;
   pl.ws_P = static_cast<size_t>(d.tcsize) * m * p;
+  if (!pl.tc && form >= 2) pl.ws_Xf = static_cast<size_t>(d.tcsize) * m * p;
   pl.ws_ypart = static_cast<size_t>(d.tcsize) * ncl * m * p;
   pl.ws_T = static_cast<size_t>(d.tcsize) * m * n;
   pl.ws_fpart = sizeof(dd) * static_cast<size_t>(pl.nobj) * 2 * m;
@@ -482,7 +483,7 @@ struct Slot {
   Budget* budget = nullptr;
   TuneTable* tune = nullptr;  // the context's autotuned layouts
   // workspace buffers, grown on demand
-  DevBuf b_cnorm, b_P, b_Y, b_ypart, b_T, b_fpart, b_gpart, b_x3, b_g3, b_maps, b_planes, b_tpart, b_sparse;
+  DevBuf b_cnorm, b_P, b_Y, b_Xf, b_ypart, b_T, b_fpart, b_gpart, b_x3, b_g3, b_maps, b_planes, b_tpart, b_sparse;
   TcMaps* maps_host = nullptr;  // pinned: the tensor maps copied to b_maps before a solve
   // staging for host-located inputs/outputs
   DevBuf s_A, s_scale, s_x0, s_X, s_Z, s_sup, s_obj, s_it, s_stat, s_gam;
@@ -495,7 +496,7 @@ struct Slot {
 
   size_t held() const {
     size_t s = 0;
-    for (const DevBuf* b : {&b_cnorm, &b_P, &b_Y, &b_ypart, &b_T, &b_fpart, &b_gpart, &b_x3, &b_g3, &b_maps,
+    for (const DevBuf* b : {&b_cnorm, &b_P, &b_Y, &b_Xf, &b_ypart, &b_T, &b_fpart, &b_gpart, &b_x3, &b_g3, &b_maps,
                             &b_planes, &b_tpart, &b_sparse, &s_A,
                             &s_scale, &s_x0, &s_X,
                             &s_Z, &s_sup, &s_obj, &s_it, &s_stat, &s_gam, &d_W, &d_list})
@@ -540,7 +541,7 @@ static void release(Slot* s, DevBuf* b) {
 }
 
 static void release_workspace(Slot* s) {
-  for (DevBuf* b : {&s->b_cnorm, &s->b_P, &s->b_Y, &s->b_ypart, &s->b_T, &s->b_fpart, &s->b_gpart, &s->b_x3,
+  for (DevBuf* b : {&s->b_cnorm, &s->b_P, &s->b_Y, &s->b_Xf, &s->b_ypart, &s->b_T, &s->b_fpart, &s->b_gpart, &s->b_x3,
                     &s->b_g3, &s->b_maps, &s->b_planes, &s->b_tpart, &s->b_sparse, &s->s_A,
                     &s->s_scale, &s->s_x0, &s->s_X, &s->s_Z, &s->s_sup, &s->s_obj, &s->s_it, &s->s_stat, &s->s_gam,
                     &s->d_W, &s->d_list})
@@ -658,6 +659,7 @@ static cudaError_t launch_sweeps(const Plan& pl, Slot* s, cudaStream_t cs, int s
     launch_tc_sweep(a, pl.npad, cs);
     return cudaGetLastError();
   }
+  if (pl.form >= 2) launch_form_x(pl.tcsize, s->io_dev, s->st_dev, pl.p, pl.m, cs);  // X = Y W for the passes
   for (size_t pi = 0; pi < pl.passes.size(); ++pi) {
     const Pass& q = (norms && pi == 0) ? pl.norm_pass : pl.passes[pi];
     SweepArgs a{s->io_dev, s->st_dev, pl.ld, pl.p, pl.n, pl.m, pl.form, q.j0, q.mgv, pl.ps, q.W, q.S,
@@ -911,6 +913,7 @@ static int prepare_solve(Slot* s, const Request& r, int nsm, bool scratch_out, P
   if ((rc = ensure(s, &s->b_cnorm, pl.ws_cnorm))) return rc;
   if ((rc = ensure(s, &s->b_P, pl.ws_P))) return rc;
   if ((rc = ensure(s, &s->b_Y, pl.ws_P))) return rc;
+  if (pl.ws_Xf && (rc = ensure(s, &s->b_Xf, pl.ws_Xf))) return rc;
   if ((rc = ensure(s, &s->b_ypart, pl.ws_ypart))) return rc;
   if ((rc = ensure(s, &s->b_T, pl.ws_T))) return rc;
   if ((rc = ensure(s, &s->b_fpart, pl.ws_fpart))) return rc;
@@ -972,6 +975,7 @@ static int prepare_solve(Slot* s, const Request& r, int nsm, bool scratch_out, P
   io.cnorm = static_cast<double*>(s->b_cnorm.p);
   io.P = s->b_P.p;
   io.Y = s->b_Y.p;
+  io.Xf = pl.ws_Xf ? s->b_Xf.p : nullptr;
   io.ypart = s->b_ypart.p;
   io.T = s->b_T.p;
   io.fpart = static_cast<dd*>(s->b_fpart.p);
@@ -1538,7 +1542,8 @@ int gpspca_time_sweep(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form,
 // (mirrors launch_prologue / launch_body / launch_epilogue).
 static void plan_launch_counts(const Plan& pl, int32_t c[3]) {
   // the start's power steps launch no active-column list (two kernels in a threshold sweep)
-  const int sweeps = pl.tc ? 3 + (pl.ksplit1 > 1 ? 1 : 0) : static_cast<int>(pl.passes.size());
+  const int sweeps = pl.tc ? 3 + (pl.ksplit1 > 1 ? 1 : 0)
+                          : static_cast<int>(pl.passes.size()) + (pl.form >= 2 ? 1 : 0);  // + form_x
   const bool late_norms = pl.pca && pl.norms_in_sweep;
   int pro = (pl.tc && pl.tc_convert ? 1 : 0) + 1 + (late_norms ? 0 : 2) + 1 + 2;
   if (pl.pca) pro += kPowerSteps * (sweeps + 2) + (late_norms ? 1 : 0) + sweeps + 2;

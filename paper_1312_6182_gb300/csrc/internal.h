@@ -29,6 +29,7 @@ struct IO {
   double* cnorm;  // n approximate column norms
   void* P;        // [m][p] start directions
   void* Y;        // [m][p] last unnormalised direction
+  void* Xf;       // [m][p] block forms on the CUDA cores: the iterate X = Y W the next sweep evaluates
   void* ypart;    // [nsplit][m][p] per-cluster partials of Y = A G
   void* T;        // [m][n] dot products of the last sweep
   dd* fpart;      // [nobj][2][m] objective / loading-norm partials (double-float)

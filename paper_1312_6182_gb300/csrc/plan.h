@@ -38,7 +38,7 @@ struct Plan {
   int tc_sparse = 0;   // fused Y pass of threshold sweeps over the active columns only
   int ksplit1 = 1, kcs1 = 0;  // T pass: row ranges per column tile, 64-row chunks per range
   size_t ws_cnorm = 0, ws_P = 0, ws_ypart = 0, ws_T = 0, ws_fpart = 0, ws_gpart = 0, ws_x3 = 0, ws_g3 = 0,
-         ws_planes = 0, ws_tpart = 0, ws_sparse = 0;
+         ws_planes = 0, ws_tpart = 0, ws_sparse = 0, ws_Xf = 0;
 
   std::string key() const {
     char b[256];
@@ -60,8 +60,8 @@ struct Plan {
     return s;
   }
   size_t workspace_bytes() const {
-    return ws_cnorm + ws_P + ws_ypart + ws_T + ws_fpart + ws_gpart + ws_x3 + ws_g3 + ws_planes + ws_tpart +
-           ws_sparse + 13 * 256 + 1024;
+    return ws_cnorm + 2 * ws_P + ws_Xf + ws_ypart + ws_T + ws_fpart + ws_gpart + ws_x3 + ws_g3 + ws_planes +
+           ws_tpart + ws_sparse + 14 * 256 + 1024;
   }
 };
 

@@ -209,7 +209,7 @@ __host__ __device__ inline SweepSmem sweep_smem_layout(int W, int S, int ps, int
   o = align_up(o, 16);
   L.red = o; o += 2 * nwarps * 32 * tcsize;          // warp partials, by tile parity
   L.xrecv = o; o += kXSlots * kMaxCluster * 32 * tcsize;  // partials pushed by cluster peers
-  L.wsm = o; o += 2 * m * mg * tcsize;  // polar weights: high parts, then the low parts
+  L.wsm = o; o += m * mg * tcsize;
   L.total = align_up(o, 128);
   return L;
 }
@@ -318,10 +318,7 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH, NRM, FW>::MAXT, 1) sweep
   }
   for (int idx = tid; idx < m * MG; idx += nthr) {
     const int l = idx / MG, j = idx % MG;
-    const double w = (j < a.mg_valid) ? st->W[l * m + a.j0 + j] : 0.0;
-    const TC hi = static_cast<TC>(w);
-    wsm[idx] = hi;
-    wsm[m * MG + idx] = static_cast<TC>(w - static_cast<double>(hi));  // 0 for double compute
+    wsm[idx] = (j < a.mg_valid) ? static_cast<TC>(st->W[l * m + a.j0 + j]) : TC(0);
   }
   const uint32_t bytes_per_col = static_cast<uint32_t>(align_up(rows_valid * static_cast<int>(sizeof(TA)), 16));
   if constexpr (FW > 0) {  // zero the ring before the first bulk copy lands in it
@@ -375,58 +372,28 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH, NRM, FW>::MAXT, 1) sweep
   // block: all m columns of Y contribute; single-unit: only column j0+j
   const int lbeg = block ? 0 : a.j0;
   const int lend = block ? m : a.j0 + a.mg_valid;
-  if (sizeof(TC) == 4 && block) {
-    // float compute, block forms: X = Y W with W to about 48 bits (high +
-    // low float parts) and every product's and sum's rounding error carried
-    // in a second accumulator (Dekker's exact product by fma, Knuth's
-    // two-sum), so that X is Y W rounded once to float even where W's
-    // entries (up to lambda_min(Y^T Y)^{-1/2}) make the sum cancel
-    TC xe[NCH][VEC][MG];
+  if (block) {
+    // block forms: X = Y W was formed before this launch (form_x_kernel,
+    // float-accurate however large W's entries); its rows are loaded here
+    const TC* xf = static_cast<const TC*>(io->Xf);
 #pragma unroll
-    for (int c = 0; c < NCH; ++c)
+    for (int j = 0; j < MG; ++j) {
+      if (j >= a.mg_valid) continue;
+      const TC* xl = xf + static_cast<int64_t>(a.j0 + j) * p + row0;
 #pragma unroll
-      for (int v = 0; v < VEC; ++v)
-#pragma unroll
-        for (int j = 0; j < MG; ++j) xe[c][v][j] = 0;
-    for (int l = lbeg; l < lend; ++l) {
-      float wl[MG], wlo[MG];
-#pragma unroll
-      for (int j = 0; j < MG; ++j) {
-        wl[j] = static_cast<float>(wsm[l * MG + j]);
-        wlo[j] = static_cast<float>(wsm[m * MG + l * MG + j]);
-      }
-      const TC* yl = Yp + static_cast<int64_t>(l) * p + row0;
-#pragma unroll
-      for (int c = 0; c < NCH; ++c) {
+      for (int c = 0; c < NCH; ++c)
 #pragma unroll
         for (int v = 0; v < VEC; ++v) {
           const int rl = (c * nthr + tid) * VEC + v;
-          const float yv = (vmask & (1u << (c * VEC + v))) ? static_cast<float>(yl[rl]) : 0.0f;
-#pragma unroll
-          for (int j = 0; j < MG; ++j) {
-            const float xs = static_cast<float>(x[c][v][j]);
-            const float pr = __fmul_rn(yv, wl[j]);
-            const float pe = fmaf(yv, wl[j], -pr);  // exact: y w_hi = pr + pe
-            const float s2 = __fadd_rn(xs, pr);
-            const float bb = __fsub_rn(s2, xs);
-            const float se = __fadd_rn(__fsub_rn(xs, __fsub_rn(s2, bb)), __fsub_rn(pr, bb));  // xs + pr = s2 + se
-            x[c][v][j] = s2;
-            xe[c][v][j] = static_cast<float>(xe[c][v][j]) + (pe + se + yv * wlo[j]);
-          }
+          x[c][v][j] = (vmask & (1u << (c * VEC + v))) ? xl[rl] : TC(0);
         }
-      }
     }
-#pragma unroll
-    for (int c = 0; c < NCH; ++c)
-#pragma unroll
-      for (int v = 0; v < VEC; ++v)
-#pragma unroll
-        for (int j = 0; j < MG; ++j) x[c][v][j] = __fadd_rn(static_cast<float>(x[c][v][j]), static_cast<float>(xe[c][v][j]));
   } else {
+    // single-unit forms: column j0+j of Y times its own weight
     for (int l = lbeg; l < lend; ++l) {
       TC wl[MG];
 #pragma unroll
-      for (int j = 0; j < MG; ++j) wl[j] = (block || l == a.j0 + j) ? wsm[l * MG + j] : TC(0);
+      for (int j = 0; j < MG; ++j) wl[j] = (l == a.j0 + j) ? wsm[l * MG + j] : TC(0);
       const TC* yl = Yp + static_cast<int64_t>(l) * p + row0;
 #pragma unroll
       for (int c = 0; c < NCH; ++c) {
