@@ -398,8 +398,11 @@ int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fa
     if (cudaOccupancyMaxActiveClusters(&nc, q.k, &cfg) == cudaSuccess && nc > 0) ncl = std::min(ncl, nc);
   }
   if (!pl.tc) ncl = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ncl, n)));
-  // block forms on the CUDA cores: the start's first power step reads A and
-  // can form the column norms too (no pass of their own)
+  // block forms: the start's first power step reads A and can form the
+  // column norms too (no pass of their own): the fused float tensor-core
+  // sweep sums them in its T pass
+  if (pl.tc && pl.tc_fused && form >= 2) pl.norms_in_sweep = 1;
+  // on the CUDA cores, the first pass runs a variant that forms them
   if (!pl.tc && form >= 2 && !pl.passes.empty()) {
     Pass q;
     if (fit_pass(dt, pl.passes[0].mg, pl.C, pl.ps, m, &q, true)) {
@@ -616,6 +619,11 @@ static cudaError_t launch_prologue(const Plan& pl, Slot* s, cudaStream_t cs, cud
                         static_cast<size_t>((pl.n + 63) / 64 * 64), cs);
     if (e0 != cudaSuccess) return e0;
   }
+  if (pl.tc && pca && pl.norms_in_sweep) {  // the squared norms the first power step sums
+    const cudaError_t e1 = cudaMemsetAsync(
+        static_cast<unsigned char*>(s->b_sparse.p) + sparse_layout(pl.n, pl.npad).nsq, 0, sizeof(double) * pl.n, cs);
+    if (e1 != cudaSuccess) return e1;
+  }
   launch_reset(s->io_dev, s->st_dev, pl.m, pl.form, cs);
   // the block start's first power step forms the column norms itself; the
   // start selection (gamma scale, non-finite check) then follows that step
@@ -655,7 +663,7 @@ static cudaError_t launch_sweeps(const Plan& pl, Slot* s, cudaStream_t cs, int s
     TcArgs a{s->io_dev,  s->st_dev, pl.p,     pl.n,       pl.m,        pl.mpad,     pl.form,
              sketch,     pl.tc_na,  pl.tc_fused, pl.dtype == GPSPCA_FP8_E4M3 ? 1 : 0, pl.p_pad, pl.n_pad,
              pl.ntile1,  pl.kchunks1, pl.ksplit1, pl.kcs1, pl.nchunks2, pl.kps2, pl.nsplit2, pl.nrow2,
-             pl.tc_sparse};
+             pl.tc_sparse, norms};
     launch_tc_sweep(a, pl.npad, cs);
     return cudaGetLastError();
   }
@@ -994,6 +1002,7 @@ static int prepare_solve(Slot* s, const Request& r, int nsm, bool scratch_out, P
       io.tc_nlist = reinterpret_cast<int32_t*>(b + L.nlist);
       io.tc_cnt = reinterpret_cast<int32_t*>(b + L.cnt);
       io.tc_g3c = b + L.g3c;
+      io.tc_nsq = reinterpret_cast<double*>(b + L.nsq);
     }
   }
   for (int j = 0; j < m; ++j) {
@@ -1546,7 +1555,7 @@ static void plan_launch_counts(const Plan& pl, int32_t c[3]) {
                           : static_cast<int>(pl.passes.size()) + (pl.form >= 2 ? 1 : 0);  // + form_x
   const bool late_norms = pl.pca && pl.norms_in_sweep;
   int pro = (pl.tc && pl.tc_convert ? 1 : 0) + 1 + (late_norms ? 0 : 2) + 1 + 2;
-  if (pl.pca) pro += kPowerSteps * (sweeps + 2) + (late_norms ? 1 : 0) + sweeps + 2;
+  if (pl.pca) pro += kPowerSteps * (sweeps + 2) + (late_norms ? 1 : 0) + (late_norms && pl.tc ? 1 : 0) + sweeps + 2;
   c[0] = pro;
   c[1] = sweeps + (pl.tc_sparse ? 2 : 0) + 2;
   c[2] = 1;

@@ -46,6 +46,7 @@ struct IO {
   int32_t* tc_nlist;    // their count
   int32_t* tc_cnt;      // [ceil(n / 1024)] active columns per block of 1024
   void* tc_g3c;         // [3 mpad][n_pad] bf16: the G3 columns of the listed columns, zero past the count
+  double* tc_nsq;       // [n] squared column norms summed by the block start's first T pass
   double gamma_in[kMaxM];  // as passed (absolute, or relative with the flag)
   double mu[kMaxM];
   double tol;

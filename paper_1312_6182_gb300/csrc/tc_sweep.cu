@@ -460,6 +460,21 @@ __global__ void __launch_bounds__(256) tc_compact_kernel(const TcArgs a) {
   }
 }
 
+// Column norms from the squared norms the first power step's T pass summed
+// (the block start): ||a_i|| for the start selection and a relative gamma; a
+// non-finite one (a NaN or infinity in A, or a square that overflowed)
+// flags the solve.
+__global__ void tc_norms_kernel(const TcArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  bool bad = false;
+  if (i < a.n) {
+    const double c = sqrt(a.io->tc_nsq[i]);
+    a.io->cnorm[i] = c;
+    bad = !isfinite(c);
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&a.st->error, static_cast<int>(kErrNonFinite));
+}
+
 // ---- pass 1: T = A^T X for 128-column tiles (persistent CTAs), threshold,
 // G3^T for pass 2.  Tensor-memory lane = column of the tile.
 template <int NPAD, int NA>
@@ -736,8 +751,12 @@ __device__ __forceinline__ void split3_trunc(float x, uint32_t& h0, uint32_t& h1
 // two float rows (32 rows of A each) at f0 / f1 in ring 1; all layouts
 // swizzle the 16-byte chunks of a row by (row % 8), the float rows by their
 // own index.
+// NORM: also adds the squares of the converted values to ss (a share of the
+// column's squared norm, for the block start's first power step).
+template <bool NORM = false>
 __device__ __forceinline__ void tc_convert_row(const unsigned char* f0, int frow0, const unsigned char* f1,
-                                               int frow1, unsigned char* plane0, int prow, int g0, int ng) {
+                                               int frow1, unsigned char* plane0, int prow, int g0, int ng,
+                                               float* ss = nullptr) {
 #pragma unroll 4
   for (int g = g0; g < g0 + ng; ++g) {  // 8 rows of A -> one 16-byte chunk per plane
     const unsigned char* src = g < 4 ? f0 : f1;
@@ -746,6 +765,10 @@ __device__ __forceinline__ void tc_convert_row(const unsigned char* f0, int frow
     const uint4 v0 = *reinterpret_cast<const uint4*>(src + fr * 128 + ((c0 ^ (fr & 7)) * 16));
     const uint4 v1 = *reinterpret_cast<const uint4*>(src + fr * 128 + (((c0 + 1) ^ (fr & 7)) * 16));
     const uint32_t x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+    if constexpr (NORM) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) *ss = fmaf(__uint_as_float(x[e]), __uint_as_float(x[e]), *ss);
+    }
     uint32_t w[3][4];
 #pragma unroll
     for (int e = 0; e < 8; e += 2) {
@@ -797,8 +820,9 @@ __device__ __forceinline__ void tc_convert_row_plain(const unsigned char* f0, co
 
 // Converter warps: chunk `it` from ring 1 into ring 2.  kY: Y-pass layout
 // (two 64-row MN atoms of 64 columns) instead of the T pass's 128 columns.
-template <int NPAD, bool kY>
-__device__ __forceinline__ bool tc_convert_chunk(const TcFusedSmem& S, int it, bool plain = false) {
+template <int NPAD, bool kY, bool NORM = false>
+__device__ __forceinline__ bool tc_convert_chunk(const TcFusedSmem& S, int it, bool plain = false,
+                                                 float* ss = nullptr) {
   using Cfg = TcFusedCfg<NPAD>;
   const int s1 = it % Cfg::S1, s2 = it % Cfg::S2;
   const uint32_t u1 = static_cast<uint32_t>(it / Cfg::S1), u2 = static_cast<uint32_t>(it / Cfg::S2);
@@ -809,7 +833,7 @@ __device__ __forceinline__ bool tc_convert_chunk(const TcFusedSmem& S, int it, b
   const int c = static_cast<int>(threadIdx.x) - 192;  // 0..255: (half of the 64 rows, plane row)
   const int h = c >> 7, q = c & 127;
   if (!kY) {  // row q = column q of the tile; float boxes: rows 0-31 | 32-63 of A
-    tc_convert_row(f, q, f + 16384, q, b, q, 4 * h, 4);
+    tc_convert_row<NORM>(f, q, f + 16384, q, b, q, 4 * h, 4, ss);
   } else {    // atom a = rows 64a..64a+63 of A, row i = column i; float boxes of 32 rows x 64 columns
     const int a = q >> 6, i = q & 63;
     if (plain)  // gathered columns: the float boxes are not swizzled
@@ -1043,11 +1067,30 @@ __global__ void __launch_bounds__(kTcFusedThreads, 1) tc_t_fused_kernel(const Tc
   } else if (warp >= 6) {  // converters
     TCursor cu;
     cu.start(a);
-    for (int it = 0; cu.valid(a) && !timed_out; ++it, cu.next(a))
-      if (tc_aborted(S.acc) || !tc_convert_chunk<NPAD, false>(S, it)) {
+    // with a.norms (the block start's first power step): the squares of the
+    // column's 32 rows each thread converts, summed per chunk in float, per
+    // item in double, and added to the column's squared norm at the item's
+    // end (two halves of the rows, and the row ranges, add up by atomics)
+    const int q = (tid - 192) & 127;
+    double nacc = 0.0;
+    for (int it = 0; cu.valid(a) && !timed_out; ++it, cu.next(a)) {
+      float ss = 0.0f;
+      const bool ok = a.norms ? tc_convert_chunk<NPAD, false, true>(S, it, false, &ss)
+                              : tc_convert_chunk<NPAD, false>(S, it);
+      if (tc_aborted(S.acc) || !ok) {
         timed_out = true;
         *S.acc.abort_flag = 1;
+        break;
       }
+      if (a.norms) {
+        nacc += static_cast<double>(ss);
+        if (cu.c + 1 >= cu.cur.ce) {
+          const int col = cu.cur.tile * kTcTile1 + q;
+          if (col < a.n) atomicAdd(&a.io->tc_nsq[col], nacc);
+          nacc = 0.0;
+        }
+      }
+    }
   } else {  // epilogue
     const uint32_t tlane = tmem + (static_cast<uint32_t>(warp * 32) << 16);
     int it = 0;
@@ -1321,6 +1364,7 @@ static void launch_tc_fused_npad(const TcArgs& a, int nsm, cudaStream_t s) {
   tc_prep_kernel<<<dim3((a.p + 255) / 256, a.mpad), 256, 0, s>>>(a);
   tc_t_fused_kernel<NPAD><<<std::max(1, std::min(a.ntile1 * a.ksplit1, nsm)), kTcFusedThreads, smem, s>>>(a);
   if (a.ksplit1 > 1) tc_t_combine_kernel<NPAD / 3><<<dim3((a.n + 255) / 256, NPAD / 3), 256, 0, s>>>(a);
+  if (a.norms) tc_norms_kernel<<<(a.n + 255) / 256, 256, 0, s>>>(a);
   if (a.sparse && !a.sketch) {
     const int nb = (a.n + kTcCompactCols - 1) / kTcCompactCols;
     tc_count_kernel<<<nb, 256, 0, s>>>(a);

@@ -79,6 +79,7 @@ struct TcArgs {
   int nsplit2;        // Y-pass splits of the columns
   int nrow2;          // ceil(p / 128)
   int sparse;         // fused float Y pass over the active columns only (threshold sweeps, not the start)
+  int norms;          // fused float T pass also sums the columns' squared norms (the start's first step)
 };
 
 // Host side (tc_sweep.cu).

@@ -422,6 +422,24 @@ def test_relative_gamma_is_scaled_on_device(ctx):
         _converged(form, gpu_arrays(res), A, ga, mu, ref, 1e-6, f"relative gamma {form}")
 
 
+def test_relative_gamma_on_the_tensor_cores(ctx):
+    """The fused float tensor-core sweep sums the column norms in the start's
+    first power step (no pass of its own); the largest is then re-normed
+    exactly, so a relative gamma matches the oracle's scale to rounding, and
+    the solve matches the oracle at the stated limits."""
+    m = 16
+    At = synth.planted_spike(900, 3100, m, [60.0 / np.sqrt(j + 1) for j in range(m)], support_frac=0.01, seed=63,
+                             dtype=np.float32)
+    A = At.astype(np.float64).T
+    for form in ("BL1", "BL0"):
+        res = ctx.solve(torch.from_numpy(At).cuda(), form, [0.05] * m, mu=[1.0] * m, gamma_relative=True, tol=0.0,
+                        maxit=4)
+        ga = res.gamma_abs.cpu().numpy()
+        np.testing.assert_allclose(ga, oracle.gamma_from_rho(A, form, [0.05] * m), rtol=1e-12)
+        ref = oracle.gpower(A, form, ga, mu=[1.0] * m, tol=0.0, maxit=4)
+        assert_matches(form, gpu_arrays(res), ref, oracle.column_norms(A), label=f"tc relative gamma {form}")
+
+
 def test_warm_start_x0(ctx):
     """A caller's start near the solution (the planted directions u_j plus
     noise of the same norm), projected on the Stiefel manifold, then 12
@@ -575,6 +593,21 @@ def test_timeout_status_maps_to_etimedout(ctx, eager):
         ref = fresh.solve(dA, "BL1", [0.05, 0.05], mu=[1.0, 1.0], gamma_relative=True, eager=eager)
     assert after.rc == binding.OK
     assert torch.equal(after.Z, ref.Z) and torch.equal(after.X, ref.X) and torch.equal(after.iters, ref.iters)
+
+
+def test_nonfinite_input_on_the_tensor_cores(ctx):
+    """Float storage with 16 components runs the fused tensor-core sweep,
+    whose first power step of the start sums the column norms: a NaN (or an
+    entry whose square overflows) is reported as ENONFINITE there, and the
+    context stays usable."""
+    At = np.random.default_rng(3).standard_normal((700, 200)).astype(np.float32)
+    for bad in (np.nan, 3e19):
+        At[301, 77] = bad
+        with pytest.raises(binding.GpspcaError) as e:
+            ctx.solve(torch.from_numpy(At).cuda(), "BL0", [0.1] * 16, mu=[1.0] * 16, gamma_relative=True)
+        assert e.value.code == binding.ENONFINITE
+    At[301, 77] = 0.0
+    ctx.solve(torch.from_numpy(At).cuda(), "BL0", [0.1] * 16, mu=[1.0] * 16, gamma_relative=True)
 
 
 def test_degenerate_polar_status(ctx):
