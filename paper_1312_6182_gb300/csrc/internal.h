@@ -44,7 +44,7 @@ struct IO {
   uint8_t* tc_act;      // [n_pad] 1 where column i is active in this sweep (cleared once listed)
   int32_t* tc_list;     // [n64] the active columns in increasing order, padded to a multiple of 64
   int32_t* tc_nlist;    // their count
-  int32_t* tc_cnt;      // [ceil(n / 1024)] active columns per block of 1024
+  int32_t* tc_cnt;      // [ceil(n / 256)] active columns per block of 256
   void* tc_g3c;         // [3 mpad][n_pad] bf16: the G3 columns of the listed columns, zero past the count
   double* tc_nsq;       // [n] squared column norms summed by the block start's first T pass
   double gamma_in[kMaxM];  // as passed (absolute, or relative with the flag)

@@ -67,7 +67,7 @@ struct Plan {
 
 // Layout of the buffers of the fused float tensor-core sweep (one
 // allocation): the listed-column rank update's flags [n64] bytes | list
-// [n64] int32 | count | per-block counts [ceil(n / 1024)] int32 | G3c
+// [n64] int32 | count | per-block counts [ceil(n / 256)] int32 | G3c
 // [npad][n64] bf16, and the start's squared column norms [n] double, each
 // 256-aligned.
 struct SparseLayout {
@@ -81,7 +81,7 @@ inline SparseLayout sparse_layout(int64_t n, int npad) {
   L.list = up(n64);
   L.nlist = L.list + up(4 * n64);
   L.cnt = L.nlist + 256;
-  L.g3c = L.cnt + up(4 * static_cast<size_t>((n + 1023) / 1024));
+  L.g3c = L.cnt + up(4 * static_cast<size_t>((n + 255) / 256));
   L.nsq = L.g3c + up(2 * static_cast<size_t>(npad) * n64);
   L.total = L.nsq + up(8 * static_cast<size_t>(n));
   return L;

@@ -353,7 +353,7 @@ __global__ void tc_t_combine_kernel(const TcArgs a) {
 // ---- the active columns of a threshold sweep (some G_ij != 0), listed in
 // increasing order for the Y pass, which then reads only those columns of A
 // (the others multiply zeros).  Two launches over blocks of kTcCompactCols
-// columns: the counts, then each block's columns at its offset (the sum of
+// columns, one per thread: the counts, then each block's columns at its offset (the sum of
 // the counts before it) with their G3 columns copied beside them; the flags
 // are cleared as they are read.  Where the count exceeds the Y pass's sparse
 // limit nothing but the count is written (the Y pass then reads every
@@ -369,10 +369,8 @@ __global__ void __launch_bounds__(256) tc_count_kernel(const TcArgs a) {
   __shared__ int wsum[8];
   const uint8_t* act = a.io->tc_act;
   const int tid = threadIdx.x;
-  const int i0 = blockIdx.x * kTcCompactCols + tid * 4;
-  int c = 0;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) c += (i0 + k < a.n && act[i0 + k] != 0) ? 1 : 0;
+  const int i = blockIdx.x * kTcCompactCols + tid;
+  int c = (i < a.n && act[i] != 0) ? 1 : 0;
   c = tc_warp_sum(c);
   if ((tid & 31) == 0) wsum[tid >> 5] = c;
   __syncthreads();
@@ -385,7 +383,8 @@ __global__ void __launch_bounds__(256) tc_count_kernel(const TcArgs a) {
 
 template <int MPAD>
 __global__ void __launch_bounds__(256) tc_compact_kernel(const TcArgs a) {
-  __shared__ int s_before[8], s_all[8], s_wtot[8], s_off, s_nl;
+  __shared__ int s_before[8], s_all[8], s_wtot[8], s_off, s_nl, s_tot;
+  __shared__ int s_col[kTcCompactCols];
   const IO* io = a.io;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nb = gridDim.x;
@@ -398,14 +397,8 @@ __global__ void __launch_bounds__(256) tc_compact_kernel(const TcArgs a) {
   }
   before = tc_warp_sum(before);
   all = tc_warp_sum(all);
-  const int i0 = blockIdx.x * kTcCompactCols + tid * 4;
-  uint8_t f[4];
-  int c = 0;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    f[k] = (i0 + k < a.n) ? io->tc_act[i0 + k] : 0;
-    c += f[k] != 0 ? 1 : 0;
-  }
+  const int i0 = blockIdx.x * kTcCompactCols + tid;  // this thread's column
+  const int c = (i0 < a.n && io->tc_act[i0] != 0) ? 1 : 0;
   int inc = c;  // inclusive scan over the warp
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -429,35 +422,37 @@ __global__ void __launch_bounds__(256) tc_compact_kernel(const TcArgs a) {
     }
     s_off = off;
     s_nl = nl;
+    s_tot = run;
   }
   __syncthreads();
-  const int nl = s_nl;
+  const int nl = s_nl, tot = s_tot, off = s_off;
   const bool listed = static_cast<int64_t>(nl) * 10 <= static_cast<int64_t>(a.n) * kTcSparseTenths;
-  const int64_t gs = a.n_pad, cs = (static_cast<int64_t>(a.n) + 63) / 64 * 64;  // G3 / G3c row strides
-  const __nv_bfloat16* G3 = static_cast<const __nv_bfloat16*>(io->tc_g3);
-  __nv_bfloat16* G3c = static_cast<__nv_bfloat16*>(io->tc_g3c);
-  int pos = s_off + s_wtot[warp] + inc - c;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    if (!f[k]) continue;
-    const int i = i0 + k;
-    io->tc_act[i] = 0;
-    if (listed) {
-      io->tc_list[pos] = i;
-      for (int r = 0; r < 3 * MPAD; ++r) G3c[r * cs + pos] = G3[r * gs + i];
-    }
-    ++pos;
+  // this block's active columns in order, then the flags cleared
+  if (c) {
+    s_col[s_wtot[warp] + inc - 1] = i0;
+    io->tc_act[i0] = 0;
   }
-  if (blockIdx.x == nb - 1) {  // the count, and the list padded to a multiple of 64
-    if (tid == 0) *io->tc_nlist = nl;
-    if (listed) {
+  __syncthreads();
+  if (listed) {  // the list, and the G3 columns beside it (consecutive threads: consecutive columns of a row)
+    const int64_t gs = a.n_pad, cs = (static_cast<int64_t>(a.n) + 63) / 64 * 64;  // G3 / G3c row strides
+    const __nv_bfloat16* G3 = static_cast<const __nv_bfloat16*>(io->tc_g3);
+    __nv_bfloat16* G3c = static_cast<__nv_bfloat16*>(io->tc_g3c);
+    for (int k = tid; k < tot; k += blockDim.x) io->tc_list[off + k] = s_col[k];
+#pragma unroll 4
+    for (int idx = tid; idx < 3 * MPAD * tot; idx += blockDim.x) {
+      const int r = idx / tot, k = idx - r * tot;
+      G3c[r * cs + off + k] = G3[r * gs + s_col[k]];
+    }
+    if (blockIdx.x == nb - 1) {  // the list padded to a multiple of 64
       const int end = (nl + 63) / 64 * 64;
-      for (int k = nl + tid; k < end; k += blockDim.x) {
-        io->tc_list[k] = 0;
-        for (int r = 0; r < 3 * MPAD; ++r) G3c[r * cs + k] = __float2bfloat16_rn(0.0f);
+      for (int k = nl + tid; k < end; k += blockDim.x) io->tc_list[k] = 0;
+      for (int idx = tid; idx < 3 * MPAD * (end - nl); idx += blockDim.x) {
+        const int r = idx / (end - nl), k = nl + idx % (end - nl);
+        G3c[r * cs + k] = __float2bfloat16_rn(0.0f);
       }
     }
   }
+  if (blockIdx.x == nb - 1 && tid == 0) *io->tc_nlist = nl;
 }
 
 // Column norms from the squared norms the first power step's T pass summed
@@ -787,19 +782,18 @@ __device__ __forceinline__ void tc_convert_row(const unsigned char* f0, int frow
   }
 }
 
-// The same for float rows without swizzle (the gathered columns of the Y
-// pass: a column's 128-byte row as TMA wrote it): the four 8-row groups are
-// taken in an order rotated by the row index, so that the lanes of a warp
-// (consecutive rows) read four different 16-byte chunks at a time.
-__device__ __forceinline__ void tc_convert_row_plain(const unsigned char* f0, const unsigned char* f1, int fr,
-                                                     unsigned char* plane0, int prow, int g0) {
+// The same for the gathered columns of the Y pass: col points at the 64
+// rows of one MN atom of one column (256 contiguous bytes, no swizzle); the
+// four 8-row groups are taken in an order rotated by the column, so that the
+// lanes of a warp (consecutive columns, 512 bytes apart) read four different
+// 32-byte pieces at a time.
+__device__ __forceinline__ void tc_convert_row_plain(const unsigned char* col, int rot, unsigned char* plane0,
+                                                     int prow, int g0) {
 #pragma unroll
   for (int gg = 0; gg < 4; ++gg) {
-    const int g = g0 + ((gg + fr) & 3);
-    const unsigned char* src = g < 4 ? f0 : f1;
-    const int c0 = (g & 3) * 2;
-    const uint4 v0 = *reinterpret_cast<const uint4*>(src + fr * 128 + c0 * 16);
-    const uint4 v1 = *reinterpret_cast<const uint4*>(src + fr * 128 + (c0 + 1) * 16);
+    const int g = g0 + ((gg + rot) & 3);
+    const uint4 v0 = *reinterpret_cast<const uint4*>(col + g * 32);
+    const uint4 v1 = *reinterpret_cast<const uint4*>(col + g * 32 + 16);
     const uint32_t x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
     uint32_t w[3][4];
 #pragma unroll
@@ -836,8 +830,8 @@ __device__ __forceinline__ bool tc_convert_chunk(const TcFusedSmem& S, int it, b
     tc_convert_row<NORM>(f, q, f + 16384, q, b, q, 4 * h, 4, ss);
   } else {    // atom a = rows 64a..64a+63 of A, row i = column i; float boxes of 32 rows x 64 columns
     const int a = q >> 6, i = q & 63;
-    if (plain)  // gathered columns: the float boxes are not swizzled
-      tc_convert_row_plain(f + (2 * a) * 8192, f + (2 * a + 1) * 8192, i, b + a * 8192, i, 4 * h);
+    if (plain)  // gathered columns: column i's 128 rows at byte 512 i, not swizzled
+      tc_convert_row_plain(f + i * 512 + a * 256, i, b + a * 8192, i, 4 * h);
     else
       tc_convert_row(f + (2 * a) * 8192, i, f + (2 * a + 1) * 8192, i, b + a * 8192, i, 4 * h, 4);
   }
@@ -935,23 +929,26 @@ __device__ __forceinline__ bool tc_fused_producer(const TcFusedSmem& S, int tota
 }
 
 // Producer of the fused Y pass over listed columns (the whole warp): chunk c
-// of the CTA holds list entries 64c .. 64c+63; lane l gathers the four
-// columns 4g .. 4g+3 (g = l mod 16) for two of the four 32-row boxes of the
-// 128-row block (tile::gather4, one 128-byte box row per column, no
-// swizzle: each gather lands 512 bytes after the previous one), so column k
-// of the chunk is row k of each box.  Lane 0 polls both rings and copies the
-// G3c tile.  false on a timeout or an abort.
+// of the CTA holds list entries 64c .. 64c+63; lane g < 16 gathers the four
+// columns 4g .. 4g+3, all 128 rows of the block (tile::gather4, one 512-byte
+// box row per column, no swizzle), so column k of the chunk lands at byte
+// 512 k of the float stage.  Lane 0 polls both rings and copies the G3c
+// tile.  false on a timeout or an abort.
 template <int NPAD>
 __device__ __forceinline__ bool tc_gather_producer(const TcFusedSmem& S, int cb, int ce, int rb, const int32_t* list,
                                                    const TcMaps* maps) {
   using Cfg = TcFusedCfg<NPAD>;
   const int lane = threadIdx.x & 31;
-  const int g = lane & 15, q0 = (lane >> 4) * 2;
+  const int g = lane & 15;  // lanes 0-15: columns 4g .. 4g+3 of the chunk, all 128 rows
   const int total = ce - cb;
   auto cols = [&](int it) { return *reinterpret_cast<const int4*>(list + static_cast<int64_t>(cb + it) * kTcBK + 4 * g); };
   int itf = 0, itb = 0;
   uint32_t idle = 0;
-  int4 cur = total > 0 ? cols(0) : make_int4(0, 0, 0, 0);
+  // the list entries of the next four chunks are loaded ahead (registers,
+  // rotated as chunks are issued), so no chunk waits for its list
+  const int4 z = make_int4(0, 0, 0, 0);
+  int4 cur = total > 0 ? cols(0) : z, n1 = total > 1 ? cols(1) : z, n2 = total > 2 ? cols(2) : z,
+       n3 = total > 3 ? cols(3) : z;
   while (itf < total || itb < total) {
     int want = 0;  // bit 0: the float stage is free, bit 1: the G3c stage, bit 2: abort
     if (lane == 0) {
@@ -976,11 +973,12 @@ __device__ __forceinline__ bool tc_gather_producer(const TcFusedSmem& S, int cb,
       const uint32_t bar = smem_u32(&S.full1[s1]);
       if (lane == 0) mbar_arrive_expect_tx(bar, kTcF);
       __syncwarp();
-#pragma unroll
-      for (int q = q0; q < q0 + 2; ++q)
-        tma_gather4(sa + q * 8192 + g * 512, &maps->a2g, rb * kTcRows2 + 32 * q, cur.x, cur.y, cur.z, cur.w, bar);
+      if (lane < 16) tma_gather4(sa + g * 2048, &maps->a2g, rb * kTcRows2, cur.x, cur.y, cur.z, cur.w, bar);
       ++itf;
-      if (itf < total) cur = cols(itf);
+      cur = n1;
+      n1 = n2;
+      n2 = n3;
+      if (itf + 3 < total) n3 = cols(itf + 3);
     }
     if (want & 2) {
       if (lane == 0) {
@@ -1258,12 +1256,12 @@ static bool encode_bf16(CUtensorMap* m, const void* base, int64_t inner, int64_t
 }
 
 static bool encode_f32(CUtensorMap* m, const void* base, int64_t inner, int64_t outer, int64_t stride_elems,
-                       int box_outer, bool swizzle = true) {
+                       int box_outer, bool swizzle = true, int box_inner = 32) {
   const EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   const cuuint64_t dims[2] = {static_cast<cuuint64_t>(inner), static_cast<cuuint64_t>(outer)};
   const cuuint64_t strides[1] = {static_cast<cuuint64_t>(stride_elems) * 4};
-  const cuuint32_t box[2] = {32u, static_cast<cuuint32_t>(box_outer)};
+  const cuuint32_t box[2] = {static_cast<cuuint32_t>(box_inner), static_cast<cuuint32_t>(box_outer)};
   const cuuint32_t estr[2] = {1u, 1u};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -1277,7 +1275,8 @@ int tc_encode_maps_f32(TcMaps* maps, const void* A, int64_t p, int64_t n, int64_
     return record_error(GPSPCA_ECUDA, "cuTensorMapEncodeTiled failed for the fused tensor-core sweep");
   if (g3c) {  // the Y pass over listed columns: A gathered a column at a time, G3c in rows of ceil(n / 64) * 64
     const int64_t n64 = (n + 63) / 64 * 64;
-    if (!encode_f32(&maps->a2g, A, p, n, ld, 1, false) || !encode_bf16(&maps->g3c, g3c, n64, npad, n64, npad))
+    if (!encode_f32(&maps->a2g, A, p, n, ld, 1, false, kTcRows2) ||
+        !encode_bf16(&maps->g3c, g3c, n64, npad, n64, npad))
       return record_error(GPSPCA_ECUDA, "cuTensorMapEncodeTiled failed for the listed-column tensor-core sweep");
   }
   return GPSPCA_OK;

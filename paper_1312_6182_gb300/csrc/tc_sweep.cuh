@@ -52,12 +52,12 @@ struct TcMaps {
   CUtensorMap g3;     // G3^T, box 64 x N
   CUtensorMap a1f;    // float A, box 32 rows x 128 columns (fused T pass)
   CUtensorMap a2f;    // float A, box 32 rows x 64 columns (fused Y pass)
-  CUtensorMap a2g;    // float A, box 32 rows x 1 column (fused Y pass, gathered columns: tile::gather4)
+  CUtensorMap a2g;    // float A, box 128 rows x 1 column, no swizzle (fused Y pass, gathered columns: tile::gather4)
   CUtensorMap g3c;    // G3c^T (the active columns' G3), box 64 x N
 };
 
 constexpr int kTcMaxSplit1 = 8;  // T pass: at most this many row ranges per column tile
-constexpr int kTcCompactCols = 1024;  // columns per block of the active-column list kernels
+constexpr int kTcCompactCols = 256;  // columns per block of the active-column list kernels (one per thread)
 // the Y pass runs over the listed columns while they are at most this
 // fraction (in tenths) of n, and over all columns otherwise
 constexpr int kTcSparseTenths = 6;
