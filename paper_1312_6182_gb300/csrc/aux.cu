@@ -652,8 +652,8 @@ __global__ void __launch_bounds__(kFinishThreads, 1) finish_kernel(const FinishA
     sum_partials(io->gpart, a.nblk, a.npairs, a.npairs, gsum);
     if (a.mode == kFinishIterate) sum_partials(io->fpart, a.nsplit, 2 * m, 2 * m, fz);
   }
-  if (proceed && a.mode == kFinishRitz) {
-    ritz_weights(gsum, m, st->W, Wt, jac);
+  if (proceed && (a.mode == kFinishRitz || a.mode == kFinishRitzT)) {
+    ritz_weights(gsum, m, st->W, Wt, jac, a.mode == kFinishRitzT);
     for (int idx = tid; idx < m * m; idx += blockDim.x) st->W[idx] = Wt[idx];
   } else if (proceed && a.mode == kFinishPolar) {
     if (block) {
@@ -901,6 +901,54 @@ void launch_form_x(int tcsize, const IO* io, const State* st, int p, int m, cuda
     form_x_kernel<double><<<grid, 256, 0, s>>>(io, st, p, m);
   else
     form_x_kernel<float><<<grid, 256, 0, s>>>(io, st, p, m);
+}
+
+// T^T T, block b over columns [kGramTCols b, kGramTCols (b+1)) of T: the
+// block's columns of every component in shared memory (rows padded by one
+// float against bank conflicts), one (j, l >= j) pair per thread at a time,
+// each product exact (Dekker) and the sum in double-float; written to both
+// halves of the m x m partial.
+__global__ void __launch_bounds__(256) gram_t_kernel(const IO* io, const State* st, int m, int n) {
+  extern __shared__ float ts[];
+  constexpr int W = kGramTCols, LD = kGramTCols + 1;
+  if (st->n_active == 0) return;
+  const int i0 = blockIdx.x * W, w = min(W, n - i0);
+  const float* T = static_cast<const float*>(io->T);
+  for (int idx = threadIdx.x; idx < m * W; idx += blockDim.x) {
+    const int j = idx / W, i = idx - j * W;
+    ts[j * LD + i] = i < w ? T[static_cast<int64_t>(j) * n + i0 + i] : 0.0f;
+  }
+  __syncthreads();
+  const int npairs = m * (m + 1) / 2;
+  double* out = io->gpart + static_cast<int64_t>(blockIdx.x) * m * m;
+  for (int q = threadIdx.x; q < npairs; q += blockDim.x) {
+    int j = 0, rem = q;
+    while (rem >= m - j) {
+      rem -= m - j;
+      ++j;
+    }
+    const int l = j + rem;
+    const float* a = ts + j * LD;
+    const float* b = ts + l * LD;
+    dd s{0.0f, 0.0f};
+    for (int i = 0; i < w; ++i) {
+      const float pr = __fmul_rn(a[i], b[i]);
+      s = dd_add(s, dd{pr, fmaf(a[i], b[i], -pr)});
+    }
+    const double v = dd_to_double(s);
+    out[j * m + l] = v;
+    out[l * m + j] = v;
+  }
+}
+
+void launch_gram_t(const IO* io, const State* st, int m, int n, cudaStream_t s) {
+  const int smem = static_cast<int>(sizeof(float)) * m * (kGramTCols + 1);
+  static bool once = [] {
+    cudaFuncSetAttribute(gram_t_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * (kGramTCols + 1) * 4);
+    return true;
+  }();
+  (void)once;
+  gram_t_kernel<<<gram_t_blocks(n), 256, smem, s>>>(io, st, m, n);
 }
 
 void launch_finalize(int tcsize, const IO* io, const State* st, int p, int n, int m, int form, cudaStream_t s) {

@@ -31,13 +31,13 @@ struct FinishArgs {
   int nblk;    // Gram partials in io->gpart
   int npairs;
   int m, form;
-  int mode;  // kFinishIterate, kFinishPolar (project the start), kFinishRitz (rotate the start)
+  int mode;  // kFinishIterate, kFinishPolar (project the start), kFinishRitz / kFinishRitzT (rotate the start)
   int last;  // 1: the start is complete after this step (sweep counter k = 0)
   cudaGraphConditionalHandle cond;
   int use_cond;
 };
 
-enum : int { kFinishIterate = 0, kFinishPolar = 1, kFinishRitz = 2 };
+enum : int { kFinishIterate = 0, kFinishPolar = 1, kFinishRitz = 2, kFinishRitzT = 3 };
 
 // Fixed sketch of the block start: SplitMix64 (Steele, Lea & Flood 2014),
 // entry (r, j) = sign from the top bit of output k = j * 2^32 + r + 1 of the
@@ -73,5 +73,10 @@ void launch_reduce(int tcsize, const ReduceArgs& a, cudaStream_t s);
 void launch_finish(const FinishArgs& a, int smem, cudaStream_t s);
 void launch_finalize(int tcsize, const IO* io, const State* st, int p, int n, int m, int form, cudaStream_t s);
 void launch_form_x(int tcsize, const IO* io, const State* st, int p, int m, cudaStream_t s);
+// T^T T of the float T = A^T Q in io->T ([m][n]) as Gram partials (gpart,
+// [blocks][m*m], full), for the start's Rayleigh-Ritz rotation.
+constexpr int kGramTCols = 256;  // columns of T per block
+inline int gram_t_blocks(int64_t n) { return static_cast<int>((n + kGramTCols - 1) / kGramTCols); }
+void launch_gram_t(const IO* io, const State* st, int m, int n, cudaStream_t s);
 
 }  // namespace gpspca

@@ -428,7 +428,8 @@ int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fa
   pl.ws_ypart = static_cast<size_t>(d.tcsize) * ncl * m * p;
   pl.ws_T = static_cast<size_t>(d.tcsize) * m * n;
   pl.ws_fpart = sizeof(dd) * static_cast<size_t>(pl.nobj) * 2 * m;
-  pl.ws_gpart = sizeof(double) * static_cast<size_t>(pl.nred) * pl.npairs;
+  // Gram partials: per reduction block, or per T^T T block of the tensor-core start
+  pl.ws_gpart = sizeof(double) * static_cast<size_t>(std::max(pl.nred, pl.tc ? gram_t_blocks(n) : 0)) * pl.npairs;
   if (pl.tc) {
     pl.ws_x3 = 2 * static_cast<size_t>(pl.npad) * pl.p_pad;
     pl.ws_g3 = 2 * static_cast<size_t>(pl.npad) * pl.n_pad;
@@ -604,7 +605,8 @@ static void slot_free(Slot* s) {
 
 // ---------------------------------------------------------------- graph
 
-static cudaError_t launch_sweeps(const Plan& pl, Slot* s, cudaStream_t cs, int sketch = 0, int norms = 0);
+static cudaError_t launch_sweeps(const Plan& pl, Slot* s, cudaStream_t cs, int sketch = 0, int norms = 0,
+                                 int keep_t = 0);
 
 // Start of the solve: norms, gamma, the start directions and their
 // projection.  Block forms without a caller start then take kPowerSteps
@@ -650,6 +652,16 @@ static cudaError_t launch_prologue(const Plan& pl, Slot* s, cudaStream_t cs, cud
     launch_finish(fp, pl.finish_smem, cs);
     if (late_norms && step == 0) launch_select_start(pl.dtype, sa, cs);
   }
+  if (pl.tc) {
+    // Rayleigh-Ritz from T = A^T Q alone: Q^T A A^T Q = T^T T, so this step
+    // needs the T pass but no rank update (one read of A instead of two)
+    if ((e = launch_sweeps(pl, s, cs, 1, 0, 1)) != cudaSuccess) return e;
+    launch_gram_t(s->io_dev, s->st_dev, pl.m, pl.n, cs);
+    FinishArgs fr{s->io_dev, s->st_dev, pl.ncl, gram_t_blocks(pl.n), pl.m * pl.m, pl.m, pl.form, kFinishRitzT, 1, h,
+                  use_cond};
+    launch_finish(fr, pl.finish_smem, cs);
+    return cudaGetLastError();
+  }
   if ((e = launch_sweeps(pl, s, cs, 1)) != cudaSuccess) return e;
   ReduceArgs rc{s->io_dev, s->st_dev, pl.ncl, pl.m, pl.p, 1, pl.m * pl.m, 0, 1, 0, pl.n, pl.form, pl.nred, 0};
   launch_reduce(pl.tcsize, rc, cs);
@@ -658,13 +670,15 @@ static cudaError_t launch_prologue(const Plan& pl, Slot* s, cudaStream_t cs, cud
   return cudaGetLastError();
 }
 
-static cudaError_t launch_sweeps(const Plan& pl, Slot* s, cudaStream_t cs, int sketch, int norms) {
+// keep_t (tensor-core sweep, start only): X3 and the T pass alone, T = A^T Q
+// written to io->T for the Rayleigh-Ritz step's T^T T.
+static cudaError_t launch_sweeps(const Plan& pl, Slot* s, cudaStream_t cs, int sketch, int norms, int keep_t) {
   if (pl.tc) {
     TcArgs a{s->io_dev,  s->st_dev, pl.p,     pl.n,       pl.m,        pl.mpad,     pl.form,
              sketch,     pl.tc_na,  pl.tc_fused, pl.dtype == GPSPCA_FP8_E4M3 ? 1 : 0, pl.p_pad, pl.n_pad,
              pl.ntile1,  pl.kchunks1, pl.ksplit1, pl.kcs1, pl.nchunks2, pl.kps2, pl.nsplit2, pl.nrow2,
-             pl.tc_sparse, norms};
-    launch_tc_sweep(a, pl.npad, cs);
+             pl.tc_sparse, norms, keep_t};
+    launch_tc_sweep(a, pl.npad, cs, keep_t != 0);
     return cudaGetLastError();
   }
   if (pl.form >= 2) launch_form_x(pl.tcsize, s->io_dev, s->st_dev, pl.p, pl.m, cs);  // X = Y W for the passes
@@ -1555,7 +1569,10 @@ static void plan_launch_counts(const Plan& pl, int32_t c[3]) {
                           : static_cast<int>(pl.passes.size()) + (pl.form >= 2 ? 1 : 0);  // + form_x
   const bool late_norms = pl.pca && pl.norms_in_sweep;
   int pro = (pl.tc && pl.tc_convert ? 1 : 0) + 1 + (late_norms ? 0 : 2) + 1 + 2;
-  if (pl.pca) pro += kPowerSteps * (sweeps + 2) + (late_norms ? 1 : 0) + (late_norms && pl.tc ? 1 : 0) + sweeps + 2;
+  // the Rayleigh-Ritz step: a sweep, its reduction and finish; on the tensor
+  // cores X3 and the T pass (+ combine), T^T T and the finish
+  const int ritz = pl.tc ? 2 + (pl.ksplit1 > 1 ? 1 : 0) + 2 : sweeps + 2;
+  if (pl.pca) pro += kPowerSteps * (sweeps + 2) + (late_norms ? 1 : 0) + (late_norms && pl.tc ? 1 : 0) + ritz;
   c[0] = pro;
   c[1] = sweeps + (pl.tc_sparse ? 2 : 0) + 2;
   c[2] = 1;

@@ -407,7 +407,10 @@ __device__ inline bool polar_weights(const double* gsum, int m, double* W, doubl
 // by decreasing Ritz value, each signed so that its largest-magnitude entry
 // (first on ties) is positive, rotate the start: new weights W V.
 // All threads of the CTA call it.
-__device__ inline void ritz_weights(const double* C, int m, const double* Wcur, double* Wout, double* wsbase) {
+// direct: C is already the projected matrix Q^T A A^T Q (= T^T T for T = A^T
+// Q) rather than the cross Gram of the two directions, and H = sym(C).
+__device__ inline void ritz_weights(const double* C, int m, const double* Wcur, double* Wout, double* wsbase,
+                                    bool direct = false) {
   const int mm = m + (m & 1);
   const EigWs ws = eig_ws(wsbase, m);
   __shared__ int ord[kMaxM];
@@ -430,14 +433,19 @@ __device__ inline void ritz_weights(const double* C, int m, const double* Wcur, 
     ws.E[idx] = dd_from_double(Wcur[idx] * sw);
   }
   __syncthreads();
-  for (int idx = tid; idx < mm * mm; idx += nthr) {  // H = sym(W C) (scaled)
+  for (int idx = tid; idx < mm * mm; idx += nthr) {  // H = sym(W C), or sym(C) when direct (scaled)
     const int r = idx / mm, c = idx % mm;
     dd v{0.0f, 0.0f};
     if (r < m && c < m) {
       dd brc{0.0f, 0.0f}, bcr{0.0f, 0.0f};
-      for (int k = 0; k < m; ++k) {
-        brc = dd_fma(ws.E[r * m + k], ws.T[k * m + c], brc);
-        bcr = dd_fma(ws.E[c * m + k], ws.T[k * m + r], bcr);
+      if (direct) {
+        brc = ws.T[r * m + c];
+        bcr = ws.T[c * m + r];
+      } else {
+        for (int k = 0; k < m; ++k) {
+          brc = dd_fma(ws.E[r * m + k], ws.T[k * m + c], brc);
+          bcr = dd_fma(ws.E[c * m + k], ws.T[k * m + r], bcr);
+        }
       }
       const dd sum = dd_add(brc, bcr);
       v = dd{sum.hi * 0.5f, sum.lo * 0.5f};

@@ -284,7 +284,7 @@ __device__ __forceinline__ void tc_t_finish(const TcArgs& a, int i, int j, float
   float g = 0.0f;
   if (j < a.m) {
     const float tj = t * scl;
-    if (!a.sketch && act_s[j]) static_cast<float*>(a.io->T)[static_cast<int64_t>(j) * a.n + i] = tj;
+    if ((!a.sketch && act_s[j]) || a.keep_t) static_cast<float*>(a.io->T)[static_cast<int64_t>(j) * a.n + i] = tj;
     g = grad_factor<float>(form, tj, gam_s[j], mu_s[j]) * scl;
     if (a.sparse && !a.sketch && g != 0.0f) a.io->tc_act[i] = 1;  // column i adds to Y = A G
   }
@@ -1336,7 +1336,7 @@ void launch_tc_convert(int dtype, const IO* io, int64_t p, int64_t n, int64_t ld
 }
 
 template <int NPAD, int NA>
-static void launch_tc_npad(const TcArgs& a, int nsm, cudaStream_t s) {
+static void launch_tc_npad(const TcArgs& a, int nsm, cudaStream_t s, bool t_only) {
   static bool once = [] {
     cudaFuncSetAttribute(tc_t_kernel<NPAD, NA>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem_bytes(NPAD, NA));
     cudaFuncSetAttribute(tc_y_kernel<NPAD, NA>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem_bytes(NPAD, NA));
@@ -1348,11 +1348,12 @@ static void launch_tc_npad(const TcArgs& a, int nsm, cudaStream_t s) {
   tc_t_kernel<NPAD, NA><<<std::max(1, std::min(a.ntile1 * a.ksplit1, tc_ctas_per_sm(NPAD, NA) * nsm)), kTcThreads,
                           smem, s>>>(a);
   if (a.ksplit1 > 1) tc_t_combine_kernel<NPAD / 3><<<dim3((a.n + 255) / 256, NPAD / 3), 256, 0, s>>>(a);
+  if (t_only) return;
   tc_y_kernel<NPAD, NA><<<dim3(a.nrow2, a.nsplit2), kTcThreads, smem, s>>>(a);
 }
 
 template <int NPAD>
-static void launch_tc_fused_npad(const TcArgs& a, int nsm, cudaStream_t s) {
+static void launch_tc_fused_npad(const TcArgs& a, int nsm, cudaStream_t s, bool t_only) {
   static bool once = [] {
     cudaFuncSetAttribute(tc_t_fused_kernel<NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_fused_smem(NPAD));
     cudaFuncSetAttribute(tc_y_fused_kernel<NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_fused_smem(NPAD));
@@ -1364,6 +1365,7 @@ static void launch_tc_fused_npad(const TcArgs& a, int nsm, cudaStream_t s) {
   tc_t_fused_kernel<NPAD><<<std::max(1, std::min(a.ntile1 * a.ksplit1, nsm)), kTcFusedThreads, smem, s>>>(a);
   if (a.ksplit1 > 1) tc_t_combine_kernel<NPAD / 3><<<dim3((a.n + 255) / 256, NPAD / 3), 256, 0, s>>>(a);
   if (a.norms) tc_norms_kernel<<<(a.n + 255) / 256, 256, 0, s>>>(a);
+  if (t_only) return;
   if (a.sparse && !a.sketch) {
     const int nb = (a.n + kTcCompactCols - 1) / kTcCompactCols;
     tc_count_kernel<<<nb, 256, 0, s>>>(a);
@@ -1373,30 +1375,31 @@ static void launch_tc_fused_npad(const TcArgs& a, int nsm, cudaStream_t s) {
 }
 
 template <int NA>
-static void launch_tc_na(const TcArgs& a, int npad, int nsm, cudaStream_t s) {
+static void launch_tc_na(const TcArgs& a, int npad, int nsm, cudaStream_t s, bool t_only) {
   switch (npad) {
-    case 48: launch_tc_npad<48, NA>(a, nsm, s); break;
-    case 96: launch_tc_npad<96, NA>(a, nsm, s); break;
-    case 144: launch_tc_npad<144, NA>(a, nsm, s); break;
-    default: launch_tc_npad<192, NA>(a, nsm, s); break;
+    case 48: launch_tc_npad<48, NA>(a, nsm, s, t_only); break;
+    case 96: launch_tc_npad<96, NA>(a, nsm, s, t_only); break;
+    case 144: launch_tc_npad<144, NA>(a, nsm, s, t_only); break;
+    default: launch_tc_npad<192, NA>(a, nsm, s, t_only); break;
   }
 }
 
-void launch_tc_sweep(const TcArgs& a, int npad, cudaStream_t s) {
+// t_only: the X3 preparation and the T pass (with its combine step) alone.
+void launch_tc_sweep(const TcArgs& a, int npad, cudaStream_t s, bool t_only) {
   int dev = 0, nsm = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (a.fused) {
     switch (npad) {
-      case 48: launch_tc_fused_npad<48>(a, nsm, s); break;
-      case 96: launch_tc_fused_npad<96>(a, nsm, s); break;
-      case 144: launch_tc_fused_npad<144>(a, nsm, s); break;
-      default: launch_tc_fused_npad<192>(a, nsm, s); break;
+      case 48: launch_tc_fused_npad<48>(a, nsm, s, t_only); break;
+      case 96: launch_tc_fused_npad<96>(a, nsm, s, t_only); break;
+      case 144: launch_tc_fused_npad<144>(a, nsm, s, t_only); break;
+      default: launch_tc_fused_npad<192>(a, nsm, s, t_only); break;
     }
   } else if (a.na == 3) {
-    launch_tc_na<3>(a, npad, nsm, s);
+    launch_tc_na<3>(a, npad, nsm, s, t_only);
   } else {
-    launch_tc_na<1>(a, npad, nsm, s);
+    launch_tc_na<1>(a, npad, nsm, s, t_only);
   }
 }
 

@@ -80,6 +80,7 @@ struct TcArgs {
   int nrow2;          // ceil(p / 128)
   int sparse;         // fused float Y pass over the active columns only (threshold sweeps, not the start)
   int norms;          // fused float T pass also sums the columns' squared norms (the start's first step)
+  int keep_t;         // start: the T pass writes T = A^T Q to io->T (the Rayleigh-Ritz step's T^T T)
 };
 
 // Host side (tc_sweep.cu).
@@ -95,7 +96,7 @@ int tc_fused_smem_bytes(int npad);
 // float / fp8 / unaligned bf16 A -> bf16 planes in the workspace (once per
 // solve); ldc = p_pad
 void launch_tc_convert(int dtype, const IO* io, int64_t p, int64_t n, int64_t ld, int64_t ldc, cudaStream_t s);
-void launch_tc_sweep(const TcArgs& a, int npad, cudaStream_t s);
+void launch_tc_sweep(const TcArgs& a, int npad, cudaStream_t s, bool t_only = false);
 // CTAs of the T pass resident per SM (1 or 2) for a geometry.
 int tc_t_ctas_per_sm(int npad, int na, bool fused);
 
