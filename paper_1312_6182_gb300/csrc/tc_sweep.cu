@@ -928,27 +928,69 @@ __device__ __forceinline__ bool tc_fused_producer(const TcFusedSmem& S, int tota
   return true;
 }
 
+// ---- the fused Y pass's work: items k = blockIdx.x, blockIdx.x + gridDim.x,
+// ... of nrow2 * nsplit2 (persistent CTAs), item k = (128-row block k mod
+// nrow2, column split k / nrow2), a split = kps consecutive 64-column chunks
+// (of all columns, or of the listed ones).  Walks the chunks of this CTA's
+// items in order, skipping empty items.
+struct YCursor {
+  int item, c, cb, ce, rb, sp;
+  int nrow2, nitems, nch, kps;
+  __device__ void set(int k) {
+    rb = k % nrow2;
+    sp = k / nrow2;
+    cb = sp * kps;
+    ce = max(cb, min(nch, cb + kps));
+    c = cb;
+  }
+  __device__ void seek(int k) {
+    for (item = k; item < nitems; item += gridDim.x) {
+      set(item);
+      if (cb < ce) return;
+    }
+  }
+  __device__ void start(int nrow2_, int nsplit, int nch_, int kps_) {
+    nrow2 = nrow2_;
+    nitems = nrow2_ * nsplit;
+    nch = nch_;
+    kps = kps_;
+    seek(blockIdx.x);
+  }
+  __device__ bool valid() const { return item < nitems; }
+  __device__ void next() {
+    if (++c >= ce) seek(item + gridDim.x);
+  }
+};
+
 // Producer of the fused Y pass over listed columns (the whole warp): chunk c
-// of the CTA holds list entries 64c .. 64c+63; lane g < 16 gathers the four
-// columns 4g .. 4g+3, all 128 rows of the block (tile::gather4, one 512-byte
-// box row per column, no swizzle), so column k of the chunk lands at byte
-// 512 k of the float stage.  Lane 0 polls both rings and copies the G3c
-// tile.  false on a timeout or an abort.
+// holds list entries 64c .. 64c+63; lane g < 16 gathers the four columns 4g
+// .. 4g+3, all 128 rows of the chunk's row block (tile::gather4, one
+// 512-byte box row per column, no swizzle), so column k of the chunk lands
+// at byte 512 k of the float stage.  The list entries of the next four
+// chunks are loaded ahead into registers.  Lane 0 polls both rings and
+// copies the G3c tile.  false on a timeout or an abort.
 template <int NPAD>
-__device__ __forceinline__ bool tc_gather_producer(const TcFusedSmem& S, int cb, int ce, int rb, const int32_t* list,
-                                                   const TcMaps* maps) {
+__device__ __forceinline__ bool tc_gather_producer(const TcFusedSmem& S, int total, YCursor ca, YCursor cg,
+                                                   const int32_t* list, const TcMaps* maps) {
   using Cfg = TcFusedCfg<NPAD>;
   const int lane = threadIdx.x & 31;
-  const int g = lane & 15;  // lanes 0-15: columns 4g .. 4g+3 of the chunk, all 128 rows
-  const int total = ce - cb;
-  auto cols = [&](int it) { return *reinterpret_cast<const int4*>(list + static_cast<int64_t>(cb + it) * kTcBK + 4 * g); };
+  const int g = lane & 15;
   int itf = 0, itb = 0;
   uint32_t idle = 0;
-  // the list entries of the next four chunks are loaded ahead (registers,
-  // rotated as chunks are issued), so no chunk waits for its list
   const int4 z = make_int4(0, 0, 0, 0);
-  int4 cur = total > 0 ? cols(0) : z, n1 = total > 1 ? cols(1) : z, n2 = total > 2 ? cols(2) : z,
-       n3 = total > 3 ? cols(3) : z;
+  int4 q0 = z, q1 = z, q2 = z, q3 = z;
+  int r0 = 0, r1 = 0, r2 = 0, r3 = 0;
+  auto pull = [&](int4& q, int& r) {
+    if (ca.valid()) {
+      q = *reinterpret_cast<const int4*>(list + static_cast<int64_t>(ca.c) * kTcBK + 4 * g);
+      r = ca.rb;
+      ca.next();
+    }
+  };
+  pull(q0, r0);
+  pull(q1, r1);
+  pull(q2, r2);
+  pull(q3, r3);
   while (itf < total || itb < total) {
     int want = 0;  // bit 0: the float stage is free, bit 1: the G3c stage, bit 2: abort
     if (lane == 0) {
@@ -973,21 +1015,25 @@ __device__ __forceinline__ bool tc_gather_producer(const TcFusedSmem& S, int cb,
       const uint32_t bar = smem_u32(&S.full1[s1]);
       if (lane == 0) mbar_arrive_expect_tx(bar, kTcF);
       __syncwarp();
-      if (lane < 16) tma_gather4(sa + g * 2048, &maps->a2g, rb * kTcRows2, cur.x, cur.y, cur.z, cur.w, bar);
+      if (lane < 16) tma_gather4(sa + g * 2048, &maps->a2g, r0 * kTcRows2, q0.x, q0.y, q0.z, q0.w, bar);
       ++itf;
-      cur = n1;
-      n1 = n2;
-      n2 = n3;
-      if (itf + 3 < total) n3 = cols(itf + 3);
+      q0 = q1;
+      r0 = r1;
+      q1 = q2;
+      r1 = r2;
+      q2 = q3;
+      r2 = r3;
+      pull(q3, r3);
     }
     if (want & 2) {
       if (lane == 0) {
         const int s2 = itb % Cfg::S2;
         const uint32_t bar = smem_u32(&S.full2[s2]);
         mbar_arrive_expect_tx(bar, Cfg::kB);
-        tma_load_2d(S.base2 + s2 * Cfg::kStage2 + 3 * kTcA, &maps->g3c, (cb + itb) * kTcBK, 0, bar);
+        tma_load_2d(S.base2 + s2 * Cfg::kStage2 + 3 * kTcA, &maps->g3c, cg.c * kTcBK, 0, bar);
       }
       ++itb;
+      cg.next();
     }
     if (want & 3) {
       idle = 0;
@@ -1116,7 +1162,7 @@ __global__ void __launch_bounds__(kTcFusedThreads, 1) tc_t_fused_kernel(const Tc
   }
 }
 
-// fused Y pass (float A)
+// fused Y pass (float A), persistent CTAs over (row block, split) items
 template <int NPAD>
 __global__ void __launch_bounds__(kTcFusedThreads, 1) tc_y_fused_kernel(const TcArgs a) {
   using Cfg = TcFusedCfg<NPAD>;
@@ -1128,75 +1174,84 @@ __global__ void __launch_bounds__(kTcFusedThreads, 1) tc_y_fused_kernel(const Tc
   const IO* io = a.io;
   State* st = a.st;
   const TcMaps* maps = static_cast<const TcMaps*>(io->tc_maps);
-  const int rb = blockIdx.x, sp = blockIdx.y;
   // a threshold sweep with few active columns reads only those (listed by
   // the compaction step); otherwise every column
   const int nl = (a.sparse && !a.sketch) ? *io->tc_nlist : 0;
   const bool listed =
       a.sparse && !a.sketch && static_cast<int64_t>(nl) * 10 <= static_cast<int64_t>(a.n) * kTcSparseTenths;
-  int cb, ce;
-  if (listed) {
-    const int nch = (nl + kTcBK - 1) / kTcBK;
-    const int kps = (nch + a.nsplit2 - 1) / a.nsplit2;
-    cb = sp * kps;
-    ce = max(cb, min(nch, cb + kps));
-  } else {
-    cb = sp * a.kps2;
-    ce = max(cb, min(a.nchunks2, cb + a.kps2));
-  }
+  const int nch = listed ? (nl + kTcBK - 1) / kTcBK : a.nchunks2;
+  const int kps = listed ? (nch + a.nsplit2 - 1) / a.nsplit2 : a.kps2;
+  YCursor cur;
+  cur.start(a.nrow2, a.nsplit2, nch, kps);
+  int total = 0;  // chunks of this CTA's items
+  for (YCursor t = cur; t.valid(); t.seek(t.item + gridDim.x)) total += t.ce - t.cb;
   const uint32_t tmem = tc_fused_setup<NPAD>(S);
   bool timed_out = false;
   if (warp == 4) {
     if (listed) {
       tmap_acquire(&maps->a2g);
       tmap_acquire(&maps->g3c);
-      if (!tc_gather_producer<NPAD>(S, cb, ce, rb, io->tc_list, maps)) {
+      if (!tc_gather_producer<NPAD>(S, total, cur, cur, io->tc_list, maps)) {
         timed_out = true;
         if (lane == 0) *S.acc.abort_flag = 1;
       }
     } else if (lane == 0) {
       tmap_acquire(&maps->a2f);
       tmap_acquire(&maps->g3);
-      const auto coord = [&](int it, int* c, int* tr) {
-        *c = cb + it;
-        *tr = rb;
-      };
-      if (!tc_fused_producer<NPAD>(S, max(0, ce - cb), coord, coord, maps, true)) {
+      YCursor cf = cur, cb = cur;  // the stored-tile and the G3 streams
+      if (!tc_fused_producer<NPAD>(
+              S, total,
+              [&](int, int* c, int* tr) {
+                *c = cf.c;
+                *tr = cf.rb;
+                cf.next();
+              },
+              [&](int, int* c, int* tr) {
+                *c = cb.c;
+                *tr = cb.rb;
+                cb.next();
+              },
+              maps, true)) {
         timed_out = true;
         *S.acc.abort_flag = 1;
       }
     }
   } else if (warp == 5) {
     if (lane == 0) {
-      for (int c = cb, it = 0; c < ce && !timed_out; ++c, ++it)
+      for (int it = 0; it < total && !timed_out; ++it)
         if (!tc_fused_mma<NPAD, true>(S, tmem, it, kIdesc)) {
           timed_out = true;
           *S.acc.abort_flag = 1;
         }
     }
   } else if (warp >= 6) {
-    for (int c = cb, it = 0; c < ce && !timed_out; ++c, ++it)
+    for (int it = 0; it < total && !timed_out; ++it)
       if (tc_aborted(S.acc) || !tc_convert_chunk<NPAD, true>(S, it, listed)) {
         timed_out = true;
         *S.acc.abort_flag = 1;
       }
-  } else {
+  } else {  // epilogue: every item of this CTA, empty ones included, writes its rows
     const uint32_t tlane = tmem + (static_cast<uint32_t>(warp * 32) << 16);
-    float y[MPAD];
+    float* yp = static_cast<float*>(io->ypart);
+    YCursor t = cur;
+    int it = 0;
+    for (int k = blockIdx.x; k < t.nitems && !timed_out; k += gridDim.x) {
+      t.set(k);
+      float y[MPAD];
 #pragma unroll
-    for (int j = 0; j < MPAD; ++j) y[j] = 0.0f;
-    for (int c = cb, it = 0; c < ce; ++c, ++it)
-      if (!tc_drain<NPAD, 3>(S.acc, tlane, it, y)) {
-        timed_out = true;
-        *S.acc.abort_flag = 1;
-        break;
+      for (int j = 0; j < MPAD; ++j) y[j] = 0.0f;
+      for (int c = t.cb; c < t.ce; ++c, ++it)
+        if (!tc_drain<NPAD, 3>(S.acc, tlane, it, y)) {
+          timed_out = true;
+          *S.acc.abort_flag = 1;
+          break;
+        }
+      const int r = t.rb * kTcRows2 + warp * 32 + lane;
+      if (!timed_out && r < a.p) {
+#pragma unroll
+        for (int j = 0; j < MPAD; ++j)
+          if (j < a.m) yp[(static_cast<int64_t>(t.sp) * a.m + j) * a.p + r] = y[j];
       }
-    const int r = rb * kTcRows2 + warp * 32 + lane;
-    if (!timed_out && r < a.p) {
-      float* yp = static_cast<float*>(io->ypart);
-#pragma unroll
-      for (int j = 0; j < MPAD; ++j)
-        if (j < a.m) yp[(static_cast<int64_t>(sp) * a.m + j) * a.p + r] = y[j];
     }
   }
   if (timed_out) atomicOr(&st->error, static_cast<int>(kErrTimeout));
@@ -1371,7 +1426,7 @@ static void launch_tc_fused_npad(const TcArgs& a, int nsm, cudaStream_t s, bool 
     tc_count_kernel<<<nb, 256, 0, s>>>(a);
     tc_compact_kernel<NPAD / 3><<<nb, 256, 0, s>>>(a);
   }
-  tc_y_fused_kernel<NPAD><<<dim3(a.nrow2, a.nsplit2), kTcFusedThreads, smem, s>>>(a);
+  tc_y_fused_kernel<NPAD><<<std::max(1, std::min(a.nrow2 * a.nsplit2, nsm)), kTcFusedThreads, smem, s>>>(a);
 }
 
 template <int NA>
