@@ -44,6 +44,9 @@ RHO32 = 0.01
 # (dram__bytes_read.sum + dram__bytes_write.sum)
 TRAFFIC_SL1 = 403.32e6
 TRAFFIC_BL1 = 404.02e6
+# the same for the tensor-core T pass on the 20000 x 100000 matrix (m = 16);
+# None until captured for the current kernel
+TRAFFIC_T4 = None
 METRIC = "GPower iters/s"
 UNIT = "iters/s"
 WORKLOAD4 = ("planted spikes 20000x100000 fp32 (16 spikes, theta_j=100/sqrt(j), 1% supports), SL1+SL0+BL1+BL0 "
@@ -187,11 +190,12 @@ def _run_steps(ctx, stream, dA, hA, cases, p, n, steps, warmup, eager, host=Fals
     return ev0.elapsed_time(ev1), total_sweeps, total_launches
 
 
-def _roofline(ctx, dA, form, m, bytes_a, peak, peak_kind, kernel, traffic):
-    """The sweep of one iteration timed alone (CUDA events on the library's
-    stream, gpspca_time_sweep); algorithmic bytes = one read of A."""
+def _roofline(ctx, dA, form, m, bytes_a, peak, peak_kind, kernel, traffic, t_pass=False):
+    """The sweep of one iteration (or, with t_pass, the tensor-core sweep's T
+    pass) timed alone (CUDA events on the library's stream,
+    gpspca_time_sweep); algorithmic bytes = one read of A."""
     mu = [1.0] * m if form.startswith("B") else None
-    ms = ctx.time_sweep(dA, form, [RHO] * m, mu=mu, gamma_relative=True, reps=20)
+    ms = ctx.time_sweep(dA, form, [RHO] * m, mu=mu, gamma_relative=True, reps=20, t_pass=t_pass)
     ach = bytes_a / (ms / 1e3) / 1e9
     return {"bound": "hbm", "kernel": kernel, "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
             "frac": round(ach / peak, 4), "peak_source": peak_kind, "traffic": traffic,
@@ -240,19 +244,28 @@ def run_gpu(args):
     d2h = sum((P4 + N4) * 4 * (1 if mu is None else len(mu)) + ((N4 + 31) // 32) * 4 * (1 if mu is None else len(mu))
               + 24 * (1 if mu is None else len(mu)) for _, mu in CASES4)
     bytes_a = P4 * N4 * 4
-    # the sweeps of the step: the block m = 16 sweep (fused float tensor-core
-    # passes) and the single-unit fused sweep; the one with the larger share
-    # of the step's sweep time is the dominant kernel
+    # the kernels of the step: the block solves' T pass (T = A^T X on the
+    # tensor cores; every sweep of a block solve, the start's three included,
+    # runs one), the block threshold sweep as a whole (T pass, listing of the
+    # active columns, rank update over them) and the single-unit fused sweep;
+    # algorithmic bytes = one read of A per launch for each.  The dominant
+    # one by its share of the step's kernel time is the roofline line.
+    r_t = _roofline(ctx, dA, "BL1", M4, bytes_a, peak, peak_kind,
+                    "tc_t_fused_kernel<48> (+ tc_prep, tc_t_combine): T = A^T X on tcgen05, float A split into exact "
+                    "bf16 planes in shared memory", TRAFFIC_T4, t_pass=True)
     r_blk = _roofline(ctx, dA, "BL1", M4, bytes_a, peak, peak_kind,
-                      "tc_prep + tc_t_fused<48> + tc_t_combine + tc_y_fused<48> (block m=16 sweep: tcgen05, float A "
-                      "split into exact bf16 planes in shared memory)", None)
+                      "block m=16 threshold sweep: tc_prep + tc_t_fused<48> + tc_t_combine + tc_count + "
+                      "tc_compact + tc_y_fused<48> over the active columns", None)
     r_su = _roofline(ctx, dA, "SL1", 1, bytes_a, peak, peak_kind, "sweep_kernel<float,1> (single-unit fused sweep)",
                      None)
     its = _case_iters(ctx, dA, CASES4, P4, N4)
-    share_blk = sum(it for (f, _), it in zip(CASES4, its) if f.startswith("B")) * r_blk["ms_per_launch"]
-    share_su = sum(it for (f, _), it in zip(CASES4, its) if f.startswith("S")) * r_su["ms_per_launch"]
-    dom, other = (r_blk, r_su) if share_blk >= share_su else (r_su, r_blk)
-    dom["share_of_step_sweep_time"] = round(max(share_blk, share_su) / (share_blk + share_su), 3)
+    t_ms = sum(3 + it for (f, _), it in zip(CASES4, its) if f.startswith("B")) * r_t["ms_per_launch"]
+    su_ms = sum(it for (f, _), it in zip(CASES4, its) if f.startswith("S")) * r_su["ms_per_launch"]
+    step_ms = ms / args.steps
+    r_t["share_of_step"] = round(t_ms / step_ms, 3)
+    r_su["share_of_step"] = round(su_ms / step_ms, 3)
+    r_blk["launches_per_step"] = sum(it for (f, _), it in zip(CASES4, its) if f.startswith("B"))
+    dom, other = (r_t, r_su) if t_ms >= su_ms else (r_su, r_t)
     del dA
     torch.cuda.empty_cache()
 
@@ -290,7 +303,8 @@ def run_gpu(args):
                    "sweeps_per_step": round(sweeps / args.steps, 2), "iters_per_case": its,
                    "l2": "inputs larger than L2 (A is 8 GB)", "parallelism": "replicas" if ws > 1 else "1 gpu"},
         "roofline": dom,
-        "roofline_other_sweep": other,
+        "roofline_other": other,
+        "roofline_block_sweep": r_blk,
         "e2e": {"value": round(e2e_sweeps / (e2e_ms / 1e3), 2), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,

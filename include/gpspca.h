@@ -85,6 +85,10 @@ typedef enum { GPSPCA_DEVICE = 0, GPSPCA_HOST = 1 } gpspca_location;
 #define GPSPCA_NO_TENSOR_CORES 4u /* run the CUDA-core fused sweep even where the tensor-core
                                      (tcgen05) sweep applies (bf16 storage with m >= 6, float or
                                      fp8 storage with m >= 9) */
+#define GPSPCA_TIME_T_PASS 16u    /* gpspca_time_sweep only: time the tensor-core sweep's first
+                                     pass (T = A^T X with its X3 preparation and row-range
+                                     combine) without the rank update; GPSPCA_EINVAL where the
+                                     problem does not run the tensor-core sweep */
 #define GPSPCA_INJECT_TIMEOUT 8u  /* test hook for callers' error handling: after the solve has
                                      run, its device state is marked as if a device-side wait had
                                      given up, so the call returns GPSPCA_ETIMEDOUT (no wait is

@@ -31,6 +31,7 @@ GAMMA_RELATIVE = 1
 EAGER = 2  # kernels launched one by one, host-driven loop (for profilers)
 NO_TENSOR_CORES = 4  # CUDA-core fused sweep even where the tensor-core sweep applies
 INJECT_TIMEOUT = 8  # test hook: the solve returns ETIMEDOUT after running
+TIME_T_PASS = 16  # time_sweep: the tensor-core sweep's T pass alone
 MAX_M = 64
 
 ERROR_NAMES = {
@@ -413,8 +414,9 @@ class Context:
         return self.lib.gpspca_poll(self.ptr, ctypes.c_uint64(ticket), int(wait_us))
 
     def time_sweep(self, At, form: str, gamma, mu=None, reps: int = 20, gamma_relative: bool = False,
-                   p: Optional[int] = None, col_scale=None, tensor_cores: bool = True) -> float:
-        """Mean milliseconds of one fused sweep (all component passes), CUDA events."""
+                   p: Optional[int] = None, col_scale=None, tensor_cores: bool = True, t_pass: bool = False) -> float:
+        """Mean milliseconds of one fused sweep (all component passes), CUDA events;
+        t_pass: the tensor-core sweep's T pass alone."""
         gamma = [float(g) for g in (gamma if hasattr(gamma, "__len__") else [gamma])]
         m = len(gamma)
         M = matrix(At, p, col_scale)
@@ -422,8 +424,8 @@ class Context:
         ms = ctypes.c_double()
         _check(self.lib.gpspca_time_sweep(self.ptr, ctypes.byref(M), FORMS[form], _darr(gamma, m), m,
                                           _darr(mu, m), (GAMMA_RELATIVE if gamma_relative else 0)
-                                          | (0 if tensor_cores else NO_TENSOR_CORES), int(reps),
-                                          ctypes.byref(ms)))
+                                          | (0 if tensor_cores else NO_TENSOR_CORES)
+                                          | (TIME_T_PASS if t_pass else 0), int(reps), ctypes.byref(ms)))
         return ms.value
 
 

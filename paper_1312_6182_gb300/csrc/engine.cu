@@ -172,9 +172,14 @@ static bool fit_variant(int dt, int mg, int nch, const void* k, int ps, int m, b
     --W;
   }
   if (W < 1 || S < 2) return false;
-  const SweepSmem L = sweep_smem_layout(W, S, ps, d.esize, d.tcsize, nw, m, mg);
+  // single-column tiles (long columns): the per-tile chain of dot products,
+  // block barrier and cluster exchange is the latency, so tiles overlap
+  // (phase A of the next before phase B of this one; four exchange slots,
+  // one stage less of prefetch)
+  const int ov = (W == 1 && S >= 3) ? 1 : 0;
+  const SweepSmem L = sweep_smem_layout(W, S, ps, d.esize, d.tcsize, nw, m, mg, ov ? 4 : kXSlots);
   if (L.total > at.max_dyn_smem) return false;
-  *out = Pass{0, 0, mg, nch, threads, W, S, L.total, k};
+  *out = Pass{0, 0, mg, nch, threads, W, S, L.total, k, ov};
   return true;
 }
 
@@ -685,7 +690,7 @@ static cudaError_t launch_sweeps(const Plan& pl, Slot* s, cudaStream_t cs, int s
   for (size_t pi = 0; pi < pl.passes.size(); ++pi) {
     const Pass& q = (norms && pi == 0) ? pl.norm_pass : pl.passes[pi];
     SweepArgs a{s->io_dev, s->st_dev, pl.ld, pl.p, pl.n, pl.m, pl.form, q.j0, q.mgv, pl.ps, q.W, q.S,
-                pl.cols_per_cl, pl.fast, sketch};
+                pl.cols_per_cl, pl.fast, sketch, q.ov};
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -1095,7 +1100,8 @@ static int request_from(Request* r, const gpspca_matrix* A, gpspca_form form, co
                         const double* mu, double tol, int32_t maxit, const void* x0, uint32_t flags,
                         gpspca_out* out) {
   if (!A || !out || !gamma) return fail(GPSPCA_EINVAL, "A, gamma and out must not be NULL");
-  if (flags & ~(GPSPCA_GAMMA_RELATIVE | GPSPCA_EAGER | GPSPCA_NO_TENSOR_CORES | GPSPCA_INJECT_TIMEOUT))
+  if (flags & ~(GPSPCA_GAMMA_RELATIVE | GPSPCA_EAGER | GPSPCA_NO_TENSOR_CORES | GPSPCA_INJECT_TIMEOUT |
+                GPSPCA_TIME_T_PASS))
     return fail(GPSPCA_EINVAL, "unknown flag bits 0x%x", flags);
   if (m < 1 || m > kMaxM) return fail(GPSPCA_EINVAL, "m = %d outside [1, %d]", m, kMaxM);
   r->A = *A;
@@ -1540,13 +1546,15 @@ int gpspca_time_sweep(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form,
   rc = prepare_solve(s, r, ctx->nsm, true, &pl, &empty);
   if (rc != GPSPCA_OK) return rc;
   if (empty) return fail(GPSPCA_EINVAL, "empty matrix");
+  const int t_only = (flags & GPSPCA_TIME_T_PASS) ? 1 : 0;
+  if (t_only && !pl.tc) return fail(GPSPCA_EINVAL, "GPSPCA_TIME_T_PASS: this problem runs the CUDA-core sweep");
   GP_CUDA(launch_prologue(pl, s, s->stream, cudaGraphConditionalHandle{}, pl.pca != 0, 0));
   cudaEvent_t e0, e1;
   GP_CUDA(cudaEventCreate(&e0));
   GP_CUDA(cudaEventCreate(&e1));
-  GP_CUDA(launch_sweeps(pl, s, s->stream));  // warm-up
+  GP_CUDA(launch_sweeps(pl, s, s->stream, 0, 0, t_only));  // warm-up
   GP_CUDA(cudaEventRecord(e0, s->stream));
-  for (int i = 0; i < reps; ++i) GP_CUDA(launch_sweeps(pl, s, s->stream));
+  for (int i = 0; i < reps; ++i) GP_CUDA(launch_sweeps(pl, s, s->stream, 0, 0, t_only));
   GP_CUDA(cudaEventRecord(e1, s->stream));
   GP_CUDA(cudaEventSynchronize(e1));
   GP_CUDA(cudaGetLastError());

@@ -118,6 +118,22 @@ def test_fixed_sweeps_ragged(ctx, form, ld):
     assert_matches(form, g, ref, oracle.column_norms(A), label=f"ragged {form} ld={ld}")
 
 
+@pytest.mark.parametrize("form", oracle.FORMS)
+def test_long_columns_overlapped_tiles(ctx, form):
+    """Columns longer than 8192 rows per CTA make single-column tiles, where
+    the fused sweep overlaps the next tile's dot products with this tile's
+    cluster exchange (four exchange slots, one stage less of prefetch):
+    12001 x 2003 planted spikes, 6 sweeps against the oracle."""
+    At = synth.planted_spike(12001, 2003, 2, [60.0, 35.0], support_frac=0.03, seed=64, dtype=np.float32)
+    A = At.astype(np.float64).T
+    m = 1 if form.startswith("S") else 2
+    mu = None if m == 1 else [1.0, 0.8]
+    gam = _gammas(A, form, [0.05] * m)
+    ref = oracle.gpower(A, form, gam, mu=mu, tol=0.0, maxit=6)
+    g, _ = _run(ctx, At, form, gam, mu=mu, tol=0.0, maxit=6)
+    assert_matches(form, g, ref, oracle.column_norms(A), label=f"long columns {form}")
+
+
 @pytest.mark.parametrize("form", ["SL1", "SL0"])
 def test_gamma_path_64(ctx, form):
     """A 64-value gamma path (log-spaced over [0.001, 0.5] max||a_i||) on one
