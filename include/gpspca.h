@@ -135,7 +135,8 @@ typedef struct {
 typedef struct gpspca_ctx gpspca_ctx;
 
 /* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the
- * library's own workspace (0 = 90% of the device's free memory).
+ * library's own workspace, and for gpspca_submit also the admitted
+ * requests' matrices and outputs (0 = 90% of the device's free memory).
  * cuda_stream: a cudaStream_t to run on, or NULL for a stream the context
  * creates.  Section 3's host/device flow: the context owns device workspace
  * and launches every step on that stream. */
@@ -234,11 +235,17 @@ int gpspca_project(gpspca_ctx* ctx, const gpspca_matrix* B, const void* Z, int32
 
 /* Asynchronous form of gpspca_solve for many concurrent requests.  The
  * request is queued; a scheduler thread admits it into one of 8 slots (each
- * with its own stream and workspace) when its workspace fits the budget next
- * to the solves already running, and launches it there as a whole solve (the
- * cached CUDA graph of its geometry), so requests that arrive while others
- * run overlap with them on the device.  Same arguments and ownership as gpspca_solve
- * (A and out must be in device memory); *ticket receives the request id. */
+ * with its own stream and workspace) when its HBM footprint fits the context
+ * budget next to the solves already running, and launches it there as a
+ * whole solve (the cached CUDA graph of its geometry), so requests that
+ * arrive while others run overlap with them on the device.  The footprint is
+ * the request's own device bytes (its matrix, fp8 scales and outputs) plus
+ * the workspace of its solve; both stay reserved until the request
+ * completes.  A request that does not fit waits for running ones to finish;
+ * one whose matrix and outputs alone exceed the budget returns GPSPCA_ENOMEM
+ * here (one that cannot fit even alone, workspace included, completes with
+ * GPSPCA_ENOMEM).  Same arguments and ownership as gpspca_solve (A and out
+ * must be in device memory); *ticket receives the request id. */
 int gpspca_submit(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form, const double* gamma, int32_t m,
                   const double* mu, double tol, int32_t maxit, uint32_t flags, gpspca_out* out,
                   uint64_t* ticket);

@@ -1130,7 +1130,32 @@ struct Ticket {
   int rc = GPSPCA_PENDING;
   bool done = false;
   std::chrono::steady_clock::time_point t_submit;
+  size_t foot = 0;  // the request's own device bytes (A, its scales, the outputs), reserved while it runs
 };
+
+// Device bytes a submitted request holds while it is solved: its matrix (and
+// fp8 scales) and its outputs; the solve's workspace comes on top.
+static size_t request_footprint(const Request& r) {
+  const DInfo d = dinfo(r.A.dtype);
+  const size_t m = static_cast<size_t>(r.m), p = static_cast<size_t>(r.A.p), n = static_cast<size_t>(r.A.n);
+  size_t f = static_cast<size_t>(r.A.ld) * n * d.esize;
+  if (r.A.dtype == GPSPCA_FP8_E4M3) f += sizeof(float) * n;
+  f += static_cast<size_t>(d.tcsize) * (p + n) * m + sizeof(uint32_t) * ((n + 31) / 32) * m +
+       (2 * sizeof(double) + 2 * sizeof(int32_t)) * m;
+  return f;
+}
+
+// Reserve (or return) bytes of the context budget; false if they do not fit.
+static bool budget_take(Budget* b, size_t bytes) {
+  std::lock_guard<std::mutex> lk(b->mu);
+  if (b->used + bytes > b->limit) return false;
+  b->used += bytes;
+  return true;
+}
+static void budget_give(Budget* b, size_t bytes) {
+  std::lock_guard<std::mutex> lk(b->mu);
+  b->used -= std::min(b->used, bytes);
+}
 
 struct gpspca_ctx {
   int device = 0;
@@ -1159,9 +1184,12 @@ struct gpspca_ctx {
 static constexpr int kServeSlots = 8;
 
 // Scheduler: admits queued requests into free slots (each slot has its own
-// stream and workspace, counted against the context budget), so solves that
-// arrive while others run overlap on the device; completion is detected per
-// slot with events and reported to gpspca_poll.
+// stream and workspace), so solves that arrive while others run overlap on
+// the device; completion is detected per slot with events and reported to
+// gpspca_poll.  Admission is by HBM footprint: a request starts when its own
+// device bytes (matrix, scales, outputs) and its solve's workspace fit in the
+// context budget next to the running solves, and waits for one to finish
+// otherwise; both are returned when it completes.
 static void scheduler_main(gpspca_ctx* ctx) {
   cudaSetDevice(ctx->device);
   std::vector<uint64_t> running(ctx->serve_slots.size(), 0);
@@ -1177,6 +1205,7 @@ static void scheduler_main(gpspca_ctx* ctx) {
       std::lock_guard<std::mutex> lk(ctx->q_mu);
       auto it = ctx->tickets.find(running[i]);
       if (it != ctx->tickets.end()) {
+        budget_give(&ctx->budget, it->second->foot);
         it->second->rc = rc;
         it->second->msg = rc == GPSPCA_OK ? "" : t_last_error;
         it->second->done = true;
@@ -1197,15 +1226,21 @@ static void scheduler_main(gpspca_ctx* ctx) {
         t = ctx->tickets[id].get();
       }
       Slot* s = ctx->serve_slots[i].get();
+      bool any = false;
+      for (uint64_t r2 : running) any = any || r2;
       bool empty = false;
-      const int rc = launch_solve(s, t->req, ctx->nsm, &empty);
+      int rc = GPSPCA_ENOMEM;
+      if (budget_take(&ctx->budget, t->foot)) {
+        rc = launch_solve(s, t->req, ctx->nsm, &empty);
+        if (rc != GPSPCA_OK || empty) budget_give(&ctx->budget, t->foot);
+      }
       if (rc == GPSPCA_ENOMEM) {
         // does not fit next to the running solves: wait for one to finish,
         // unless nothing runs (then it can never fit)
         release_workspace(s);
-        bool any = false;
-        for (uint64_t r2 : running) any = any || r2;
         if (any) break;
+        fail(GPSPCA_ENOMEM, "request of %zu bytes (matrix and outputs) and its workspace exceed the budget of %zu",
+             t->foot, ctx->budget.limit);
       }
       std::lock_guard<std::mutex> lk(ctx->q_mu);
       ctx->queue.pop_front();
@@ -1747,6 +1782,10 @@ int gpspca_submit(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form, con
   if ((rc = validate(t->req)) != GPSPCA_OK) return rc;
   if (A->location != GPSPCA_DEVICE || out->location != GPSPCA_DEVICE)
     return fail(GPSPCA_EINVAL, "gpspca_submit takes device buffers only");
+  t->foot = request_footprint(t->req);
+  if (t->foot > ctx->budget.limit)
+    return fail(GPSPCA_ENOMEM, "request of %zu bytes (matrix and outputs) exceeds the context budget of %zu", t->foot,
+                ctx->budget.limit);
   t->t_submit = std::chrono::steady_clock::now();
   std::lock_guard<std::mutex> lk(ctx->q_mu);
   if (!ctx->sched_started) {

@@ -729,3 +729,33 @@ def test_submitted_requests_equal_solo_solves(ctx):
         assert torch.equal(out.Z, ref.Z) and torch.equal(out.X, ref.X)
         assert torch.equal(out.objective, ref.objective) and torch.equal(out.iters, ref.iters)
     assert ctx.poll(tickets[0][0], 0) == binding.ENOTFOUND
+
+
+def test_submit_admission_by_footprint():
+    """Requests are admitted by their HBM footprint (matrix, outputs and the
+    solve's workspace) under the context budget: with a budget that holds
+    one 24 MB request at a time, four submitted requests wait for each other
+    and each result equals its solo solve; a request whose own matrix and
+    outputs exceed the budget is refused with ENOMEM."""
+    reqs = []
+    for i in range(4):
+        At = synth.planted_spike(1500, 4000, 2, [30.0, 15.0], support_frac=0.05, seed=300 + i, dtype=np.float32)
+        reqs.append((torch.from_numpy(At).cuda(), oracle.FORMS[i % 4]))
+    solo = []
+    with binding.Context(0) as big:
+        for dA, form in reqs:
+            m = 1 if form.startswith("S") else 2
+            solo.append(big.solve(dA, form, [0.05] * m, mu=None if m == 1 else [1.0, 1.0], gamma_relative=True))
+    with binding.Context(0, budget_bytes=40 << 20) as small:
+        tickets = []
+        for dA, form in reqs:
+            m = 1 if form.startswith("S") else 2
+            tickets.append(small.submit(dA, form, [0.05] * m, mu=None if m == 1 else [1.0, 1.0], gamma_relative=True))
+        for (t, out), ref in zip(tickets, solo):
+            assert small.poll(t, wait_us=-1) == binding.OK
+            assert torch.equal(out.Z, ref.Z) and torch.equal(out.X, ref.X)
+            assert torch.equal(out.objective, ref.objective)
+        huge = torch.zeros((6000, 2000), device="cuda")  # 48 MB
+        with pytest.raises(binding.GpspcaError) as e:
+            small.submit(huge, "SL1", [0.05], gamma_relative=True)
+        assert e.value.code == binding.ENOMEM
