@@ -144,7 +144,7 @@ class Clocks:
         return out
 
 
-def _run_steps(ctx, stream, dA, hA, cases, p, n, steps, warmup, eager, host=False):
+def _run_steps(ctx, stream, dA, hA, cases, p, n, steps, warmup, eager, host=False, label="gpspca_step"):
     """`steps` timed steps of the solves in `cases` (after `warmup` untimed
     ones), issued as one gpspca_solve_batch per step (the solves run
     concurrently on their own streams, ordered on the context's stream).
@@ -180,6 +180,13 @@ def _run_steps(ctx, stream, dA, hA, cases, p, n, steps, warmup, eager, host=Fals
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     total_sweeps, total_launches = 0, 0
+    # an NVTX range around the timed steps (profilers filter the step's
+    # kernels with it, e.g. ncu --nvtx --nvtx-include "gpspca_step/")
+    try:
+        torch.cuda.nvtx.range_push(label)
+        nvtx = True
+    except Exception:
+        nvtx = False
     ev0.record(stream)
     for _ in range(steps):
         sw, la = step()
@@ -187,6 +194,8 @@ def _run_steps(ctx, stream, dA, hA, cases, p, n, steps, warmup, eager, host=Fals
         total_launches += la
     ev1.record(stream)
     torch.cuda.synchronize()
+    if nvtx:
+        torch.cuda.nvtx.range_pop()
     return ev0.elapsed_time(ev1), total_sweeps, total_launches
 
 
@@ -238,7 +247,8 @@ def run_gpu(args):
     # (once per step: the batch stages the host matrix its requests share)
     # and every result copied out inside the timed region
     e2e_steps = max(1, args.steps // 4)
-    e2e_ms, e2e_sweeps, _ = _run_steps(ctx, stream, dA, hA, CASES4, P4, N4, e2e_steps, 1, False, host=True)
+    e2e_ms, e2e_sweeps, _ = _run_steps(ctx, stream, dA, hA, CASES4, P4, N4, e2e_steps, 1, False, host=True,
+                                       label="gpspca_step_e2e")
     del hA
     h2d = P4 * N4 * 4
     d2h = sum((P4 + N4) * 4 * (1 if mu is None else len(mu)) + ((N4 + 31) // 32) * 4 * (1 if mu is None else len(mu))
@@ -272,7 +282,8 @@ def run_gpu(args):
     # ---- secondary: 5000 x 20000 fp32, six solves per step (block m = 5)
     At2 = synth.workload_spikes_5000x20000(0)
     dA2 = torch.from_numpy(At2).cuda()
-    ms2, sweeps2, launches2 = _run_steps(ctx, stream, dA2, None, CASES, P, N, args.steps, args.warmup, args.eager)
+    ms2, sweeps2, launches2 = _run_steps(ctx, stream, dA2, None, CASES, P, N, args.steps, args.warmup, args.eager,
+                                         label="gpspca_step_5000x20000")
     ms2, sweeps2_all = reduce_over_ranks(ms2, sweeps2, "cuda")
     bytes2 = P * N * 4
     secondary = {

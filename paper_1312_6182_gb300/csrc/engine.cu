@@ -294,7 +294,7 @@ static bool same_passes(const std::vector<Pass>& a, const std::vector<Pass>& b) 
   if (a.size() != b.size()) return false;
   for (size_t i = 0; i < a.size(); ++i)
     if (a[i].mg != b[i].mg || a[i].mgv != b[i].mgv || a[i].k != b[i].k || a[i].threads != b[i].threads ||
-        a[i].W != b[i].W || a[i].S != b[i].S)
+        a[i].W != b[i].W || a[i].S != b[i].S || a[i].ov != b[i].ov)
       return false;
   return true;
 }
@@ -360,6 +360,30 @@ int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fa
         for (const Layout& o : lay) dup = dup || (!o.tc && o.C == L.C && same_passes(o.passes, L.passes));
         if (!dup) lay.push_back(L);
       }
+    // each CUDA-core layout also with its tiles overlapped the other way
+    // (phase A of the next tile before phase B of this one, or not)
+    const size_t base = lay.size();
+    for (size_t li = 0; li < base; ++li) {
+      if (lay[li].tc) continue;
+      Layout L = lay[li];
+      bool ok = true;
+      for (Pass& q : L.passes) {
+        if (q.S < 3) {
+          ok = false;
+          break;
+        }
+        q.ov = q.ov ? 0 : 1;
+        const DInfo d = dinfo(dt);
+        const SweepSmem S2 = sweep_smem_layout(q.W, q.S, L.ps, d.esize, d.tcsize, q.threads / 32, m, q.mg,
+                                               q.ov ? 4 : kXSlots);
+        if (S2.total > kattr(q.k).max_dyn_smem) {
+          ok = false;
+          break;
+        }
+        q.smem = S2.total;
+      }
+      if (ok) lay.push_back(L);
+    }
   }
   if (ncand) *ncand = static_cast<int>(lay.size());
   const int pick = cand < 0 ? 0 : cand;
