@@ -39,14 +39,16 @@ MU_W = [1.0, 0.9, 0.8, 0.7, 0.6]
 CASES = [("SL1", None), ("SL0", None), ("BL1", [1.0] * 5), ("BL0", [1.0] * 5), ("BL1", MU_W), ("BL0", MU_W)]
 TOL, MAXIT = 1e-6, 1000
 RHO32 = 0.01
-# dram bytes (read + write) of one launch of the fused sweeps on the 5000 x
-# 20000 matrix, from an ncu capture of the current kernels
-# (dram__bytes_read.sum + dram__bytes_write.sum)
-TRAFFIC_SL1 = 403.32e6
-TRAFFIC_BL1 = 404.02e6
-# the same for the tensor-core T pass on the 20000 x 100000 matrix (m = 16);
-# None until captured for the current kernel
-TRAFFIC_T4 = None
+# dram bytes (read + write) per launch from ncu captures of the current
+# kernels (dram__bytes_read.sum + dram__bytes_write.sum): the fused sweeps on
+# the 5000 x 20000 matrix, and on the 20000 x 100000 matrix the tensor-core T
+# pass, the whole block threshold sweep (its six kernels) and the
+# single-unit sweep
+TRAFFIC_SL1 = 400.3e6
+TRAFFIC_BL1 = 400.7e6
+TRAFFIC_T4 = 8114.9e6
+TRAFFIC_BLK4 = 9456.2e6
+TRAFFIC_SU4 = 8000.9e6
 METRIC = "GPower iters/s"
 UNIT = "iters/s"
 WORKLOAD4 = ("planted spikes 20000x100000 fp32 (16 spikes, theta_j=100/sqrt(j), 1% supports), SL1+SL0+BL1+BL0 "
@@ -265,9 +267,10 @@ def run_gpu(args):
                     "bf16 planes in shared memory", TRAFFIC_T4, t_pass=True)
     r_blk = _roofline(ctx, dA, "BL1", M4, bytes_a, peak, peak_kind,
                       "block m=16 threshold sweep: tc_prep + tc_t_fused<48> + tc_t_combine + tc_count + "
-                      "tc_compact + tc_y_fused<48> over the active columns", None)
-    r_su = _roofline(ctx, dA, "SL1", 1, bytes_a, peak, peak_kind, "sweep_kernel<float,1> (single-unit fused sweep)",
-                     None)
+                      "tc_compact + tc_y_fused<48> over the active columns", TRAFFIC_BLK4)
+    r_su = _roofline(ctx, dA, "SL1", 1, bytes_a, peak, peak_kind,
+                     "sweep_kernel<float,1,2,0,3> (single-unit fused sweep, overlapped single-column tiles)",
+                     TRAFFIC_SU4)
     its = _case_iters(ctx, dA, CASES4, P4, N4)
     t_ms = sum(3 + it for (f, _), it in zip(CASES4, its) if f.startswith("B")) * r_t["ms_per_launch"]
     su_ms = sum(it for (f, _), it in zip(CASES4, its) if f.startswith("S")) * r_su["ms_per_launch"]
