@@ -786,7 +786,11 @@ def run_precision(args):
     from paper_1312_6182_gb300 import binding, synth
 
     p, n, m = 20000, 100000, 16
-    At = synth.workload_spikes_20000x100000(2)
+    if args.theta_scale == 1.0:
+        At = synth.workload_spikes_20000x100000(2)
+    else:  # the same draw with weaker spikes (slower convergence)
+        At = synth.planted_spike(p, n, 16, [100.0 * args.theta_scale / np.sqrt(j) for j in range(1, 17)],
+                                 support_frac=0.01, seed=2, dtype=np.float32, noise_streams=16)
     d32 = torch.from_numpy(At).cuda()
     if not args.oracle:
         del At
@@ -858,8 +862,9 @@ def run_precision(args):
     value = res["BL1_bf16"]["solves_per_s"]
     line = _base_line("precision-path solves/s (BF16 + 3 FP32 refinement sweeps)", "solves/s", value,
                       res["BL1_bf16"]["ms_total"], args,
-                      "planted spikes 20000x100000 (16 spikes, theta_j=100/sqrt(j), 1% supports), BL1/BL0 m=16 mu=1, "
-                      "gamma=0.05*max||a_i||; BF16 and FP8-E4M3 (per-column scales) storage + 3 FP32 sweeps vs FP32",
+                      f"planted spikes 20000x100000 (16 spikes, theta_j={100 * args.theta_scale:g}/sqrt(j), 1% "
+                      "supports), BL1/BL0 m=16 mu=1, gamma=0.05*max||a_i||; BF16 and FP8-E4M3 (per-column scales) "
+                      "storage + 3 FP32 sweeps vs FP32",
                       "bf16",
                       {"results": res, "roofline": {"bound": "hbm", "peak": peak, "peak_source": kind, "unit": "GB/s",
                                                     "sweeps_m16": roof}, "clocks": clocks})
@@ -1011,6 +1016,8 @@ def main():
     ap.add_argument("--instances", type=int, default=4, help="scaling workload: random instances per size")
     ap.add_argument("--oracle-max-n", type=int, default=8000, help="scaling workload: largest N the oracle runs")
     ap.add_argument("--requests", type=int, default=2000, help="serving workload: number of requests")
+    ap.add_argument("--theta-scale", type=float, default=1.0,
+                    help="precision workload: spike strengths theta_j = 100 * scale / sqrt(j) (1 = the workload)")
     ap.add_argument("--eager", action="store_true",
                     help="launch each solve's kernels one by one (profilers cannot follow the CUDA graph's "
                          "conditional node); slower, for launch lists only")

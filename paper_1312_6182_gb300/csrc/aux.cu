@@ -63,7 +63,20 @@ __device__ void sum_partials(const P* __restrict__ src, int nb, int stride, int 
     const int q = q0 + static_cast<int>(threadIdx.x) / tpp;
     P s0 = sp_zero(src), s1 = sp_zero(src);
     if (q < nq) {
+      // sixteen partials' loads in flight per step (hundreds of partials
+      // per entry: the sum is bound by the load latency), added in a fixed
+      // order
       int b = sub;
+      for (; b + 15 * tpp < nb; b += 16 * tpp) {
+        P v[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) v[u] = src[static_cast<int64_t>(b + u * tpp) * stride + q];
+#pragma unroll
+        for (int u = 0; u < 8; u += 2) {
+          s0 = sp_add(s0, sp_add(v[u], v[u + 8]));
+          s1 = sp_add(s1, sp_add(v[u + 1], v[u + 9]));
+        }
+      }
       for (; b + 3 * tpp < nb; b += 4 * tpp) {
         const P v0 = src[static_cast<int64_t>(b) * stride + q];
         const P v1 = src[static_cast<int64_t>(b + tpp) * stride + q];
