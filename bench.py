@@ -777,8 +777,10 @@ def run_precision(args):
     """Precision path: block L1 and L0, m = 16, on a 20000 x 100000
     planted-spike A (16 spikes, 1% supports, theta_j = 100/sqrt j) stored in
     BF16 and in FP8 E4M3 with per-column scales, each solved to convergence
-    and then refined by 3 FP32 sweeps from the converged X on the FP32 copy;
-    against the plain FP32 solve.  With --oracle, errors of every variant
+    and then refined by --refine-sweeps FP32 sweeps (default 3) from the
+    converged X on the FP32 copy; against the plain FP32 solve.  --rho sets
+    gamma (default 0.05 max||a_i||); a smaller rho or --theta-scale < 1 gives
+    a slower-converging instance.  With --oracle, errors of every variant
     against the FP64 oracle on the FP32 matrix (objective, loadings, support)."""
     import numpy as np
     import torch
@@ -808,7 +810,7 @@ def run_precision(args):
     for form in ("BL1", "BL0"):
         for fmt, dA, cs in (("f32", d32, None), ("bf16", dbf, None), ("fp8", d8, s8)):
             def solve():
-                return ctx.solve(dA, form, [0.05] * m, mu=mu, gamma_relative=True, out=out, col_scale=cs)
+                return ctx.solve(dA, form, [args.rho] * m, mu=mu, gamma_relative=True, out=out, col_scale=cs)
 
             for _ in range(args.warmup):
                 solve()
@@ -818,13 +820,14 @@ def run_precision(args):
             if clocks is None:
                 clocks = clk.stop()
             iters = int(r.iters.max().item())
-            entry = {"ms_per_solve": round(ms, 3), "iters": iters, "iters_per_s": round(iters / (ms / 1e3), 1)}
+            entry = {"ms_per_solve": round(ms, 3), "iters": iters, "iters_per_s": round(iters / (ms / 1e3), 1),
+                     "status": int(r.status.max().item())}
             if fmt != "f32":
                 x0 = r.X.contiguous().clone()
 
                 def refine():
-                    return ctx.solve(d32, form, [0.05] * m, mu=mu, gamma_relative=True, tol=0.0, maxit=3, x0=x0,
-                                     out=out2)
+                    return ctx.solve(d32, form, [args.rho] * m, mu=mu, gamma_relative=True, tol=0.0,
+                                     maxit=args.refine_sweeps, x0=x0, out=out2)
 
                 ms_r, rr = _event_ms(stream, refine, max(1, args.steps // 4))
                 entry["refine_ms"] = round(ms_r, 3)
@@ -835,7 +838,7 @@ def run_precision(args):
                 keep[(form, fmt)] = {k: getattr(r, k).clone() for k in ("X", "Z", "objective", "support")}
             entry["solves_per_s"] = round(1e3 / entry["ms_total"], 2)
             res[f"{form}_{fmt}"] = entry
-    sweep_ms = {fmt: ctx.time_sweep(dA, "BL1", [0.05] * m, mu=mu, gamma_relative=True, reps=5, col_scale=cs)
+    sweep_ms = {fmt: ctx.time_sweep(dA, "BL1", [args.rho] * m, mu=mu, gamma_relative=True, reps=5, col_scale=cs)
                 for fmt, dA, cs in (("f32", d32, None), ("bf16", dbf, None), ("fp8", d8, s8))}
     ctx.close()
     if args.oracle:
@@ -844,7 +847,7 @@ def run_precision(args):
         A64 = At.astype(np.float64).T
         del At
         for form in ("BL1", "BL0"):
-            gam = oracle.gamma_from_rho(A64, form, [0.05] * m)
+            gam = oracle.gamma_from_rho(A64, form, [args.rho] * m)
             ref = oracle.gpower(A64, form, gam, mu=np.array(mu), tol=1e-6, maxit=1000)
             for fmt in ("f32", "bf16", "fp8"):
                 g = keep[(form, fmt)]
@@ -854,17 +857,18 @@ def run_precision(args):
                 ferr = abs(float(g["objective"].sum().item()) - ref.total) / ref.total
                 sup = (Z != 0) != (ref.Z != 0)
                 res[f"{form}_{fmt}"]["oracle"] = {"loadings_rel_err_max": max(zerr), "objective_rel_err": ferr,
-                                                 "support_mismatches": int(sup.sum()), "oracle_iters": int(ref.iters[0])}
+                                                 "support_mismatches": int(sup.sum()),
+                                                 "oracle_iters": int(ref.iters[0]), "oracle_status": int(ref.status[0])}
     peak, kind = _peaks()
     bytes_of = {"f32": p * n * 4, "bf16": p * n * 2, "fp8": p * n + n * 4}
     roof = {fmt: {"ms_per_sweep": round(ms_, 4), "GB/s": round(bytes_of[fmt] / (ms_ / 1e3) / 1e9, 1),
                   "frac": round(bytes_of[fmt] / (ms_ / 1e3) / 1e9 / peak, 4)} for fmt, ms_ in sweep_ms.items()}
     value = res["BL1_bf16"]["solves_per_s"]
-    line = _base_line("precision-path solves/s (BF16 + 3 FP32 refinement sweeps)", "solves/s", value,
-                      res["BL1_bf16"]["ms_total"], args,
+    line = _base_line(f"precision-path solves/s (BF16 + {args.refine_sweeps} FP32 refinement sweeps)", "solves/s",
+                      value, res["BL1_bf16"]["ms_total"], args,
                       f"planted spikes 20000x100000 (16 spikes, theta_j={100 * args.theta_scale:g}/sqrt(j), 1% "
-                      "supports), BL1/BL0 m=16 mu=1, gamma=0.05*max||a_i||; BF16 and FP8-E4M3 (per-column scales) "
-                      "storage + 3 FP32 sweeps vs FP32",
+                      f"supports), BL1/BL0 m=16 mu=1, gamma={args.rho:g}*max||a_i||; BF16 and FP8-E4M3 (per-column "
+                      f"scales) storage + {args.refine_sweeps} FP32 sweeps vs FP32",
                       "bf16",
                       {"results": res, "roofline": {"bound": "hbm", "peak": peak, "peak_source": kind, "unit": "GB/s",
                                                     "sweeps_m16": roof}, "clocks": clocks})
@@ -1016,6 +1020,9 @@ def main():
     ap.add_argument("--instances", type=int, default=4, help="scaling workload: random instances per size")
     ap.add_argument("--oracle-max-n", type=int, default=8000, help="scaling workload: largest N the oracle runs")
     ap.add_argument("--requests", type=int, default=2000, help="serving workload: number of requests")
+    ap.add_argument("--rho", type=float, default=0.05,
+                    help="precision workload: gamma = rho max||a_i|| (L1) / its square (L0)")
+    ap.add_argument("--refine-sweeps", type=int, default=3, help="precision workload: FP32 refinement sweeps")
     ap.add_argument("--theta-scale", type=float, default=1.0,
                     help="precision workload: spike strengths theta_j = 100 * scale / sqrt(j) (1 = the workload)")
     ap.add_argument("--eager", action="store_true",
