@@ -150,6 +150,11 @@ def _run_steps(ctx, stream, dA, hA, cases, p, n, steps, warmup, eager, host=Fals
     """`steps` timed steps of the solves in `cases` (after `warmup` untimed
     ones), issued as one gpspca_solve_batch per step (the solves run
     concurrently on their own streams, ordered on the context's stream).
+    host: end to end from the pinned host matrix hA, with the results
+    written to pinned host buffers: each step's A is copied in by
+    gpspca_upload into one of two device buffers, the copy for step k + 1
+    issued before the solves of step k so that it overlaps them (the solves
+    of step k + 1 wait for it on the device).
     Returns (ms, sweeps, kernel launches) over the timed steps."""
     import torch
 
@@ -160,13 +165,19 @@ def _run_steps(ctx, stream, dA, hA, cases, p, n, steps, warmup, eager, host=Fals
         m = 1 if mu is None else len(mu)
         outs.append(binding.alloc_result(m, p, n, "cpu" if host else "cuda", torch.float32, pin=host))
         counts.append(ctx.plan_launches(dA, form, [RHO] * m, mu=mu, gamma_relative=True))
+    bufs = [torch.empty_like(dA), torch.empty_like(dA)] if host else None
 
-    def step():
+    def step(k, last):
+        if host:
+            if k == 0:
+                ctx.upload(hA, bufs[0])
+            if k + 1 < last:
+                ctx.upload(hA, bufs[(k + 1) % 2])
         items = []
         for (form, mu), out in zip(cases, outs):
             m = 1 if mu is None else len(mu)
-            items.append(dict(At=hA if host else dA, form=form, gamma=[RHO] * m, mu=mu, tol=TOL, maxit=MAXIT,
-                              gamma_relative=True, out=out, eager=eager))
+            items.append(dict(At=bufs[k % 2] if host else dA, form=form, gamma=[RHO] * m, mu=mu, tol=TOL,
+                              maxit=MAXIT, gamma_relative=True, out=out, eager=eager))
         results = [ctx.solve(**it) for it in items] if eager else ctx.solve_batch(items)
         sweeps, launches = 0, 0
         for res, (pro, per, epi) in zip(results, counts):
@@ -176,8 +187,8 @@ def _run_steps(ctx, stream, dA, hA, cases, p, n, steps, warmup, eager, host=Fals
         return sweeps, launches
 
     torch.cuda.synchronize()
-    for _ in range(warmup):
-        step()
+    for k in range(warmup):
+        step(k, warmup)
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -190,14 +201,15 @@ def _run_steps(ctx, stream, dA, hA, cases, p, n, steps, warmup, eager, host=Fals
     except Exception:
         nvtx = False
     ev0.record(stream)
-    for _ in range(steps):
-        sw, la = step()
+    for k in range(steps):
+        sw, la = step(k, steps)
         total_sweeps += sw
         total_launches += la
     ev1.record(stream)
     torch.cuda.synchronize()
     if nvtx:
         torch.cuda.nvtx.range_pop()
+    del bufs
     return ev0.elapsed_time(ev1), total_sweeps, total_launches
 
 
@@ -245,11 +257,11 @@ def run_gpu(args):
     torch.cuda.synchronize()
     ms, sweeps_all = reduce_over_ranks(ms, sweeps, "cuda")
     value = sweeps_all / (ms / 1e3)
-    # end to end through the C ABI with host (pinned) buffers: A copied in
-    # (once per step: the batch stages the host matrix its requests share)
+    # end to end through the C ABI from host (pinned) buffers: every step's
+    # A copied in (gpspca_upload, overlapping the previous step's solves)
     # and every result copied out inside the timed region
-    e2e_steps = max(1, args.steps // 4)
-    e2e_ms, e2e_sweeps, _ = _run_steps(ctx, stream, dA, hA, CASES4, P4, N4, e2e_steps, 1, False, host=True,
+    e2e_steps = args.steps
+    e2e_ms, e2e_sweeps, _ = _run_steps(ctx, stream, dA, hA, CASES4, P4, N4, e2e_steps, args.warmup, False, host=True,
                                        label="gpspca_step_e2e")
     del hA
     h2d = P4 * N4 * 4

@@ -83,8 +83,9 @@ typedef enum { GPSPCA_DEVICE = 0, GPSPCA_HOST = 1 } gpspca_location;
                                      node: for profilers and debuggers that cannot follow
                                      conditional graph nodes.  Results are identical. */
 #define GPSPCA_NO_TENSOR_CORES 4u /* run the CUDA-core fused sweep even where the tensor-core
-                                     (tcgen05) sweep applies (bf16 storage with m >= 6, float or
-                                     fp8 storage with m >= 9) */
+                                     (tcgen05) sweep applies (bf16 storage, or float storage with
+                                     a 16-byte aligned base and column stride, with m >= 6; other
+                                     float layouts and fp8 storage with m >= 9) */
 #define GPSPCA_TIME_T_PASS 16u    /* gpspca_time_sweep only: time the tensor-core sweep's first
                                      pass (T = A^T X with its X3 preparation and row-range
                                      combine) without the rank update; GPSPCA_EINVAL where the
@@ -194,6 +195,29 @@ typedef struct {
  * context's stream before the batch starts, into a buffer the context keeps
  * (counted against the budget) for later batches. */
 int gpspca_solve_batch(gpspca_ctx* ctx, int32_t count, const gpspca_request* reqs, int32_t* rcs);
+
+/* Asynchronous copy of a host matrix to device memory the caller owns, so
+ * that the copy of the next problem overlaps the solves of this one (no
+ * counterpart in the paper: its host/device flow of Section 3 copies A before
+ * the iterations).
+ *   host  GPSPCA_HOST matrix (page-locked memory for the copy to overlap
+ *         anything; pageable memory is copied too, without overlap)
+ *   dst   GPSPCA_DEVICE matrix of the same dtype, p and n; its own ld >= p
+ *         (the copy re-strides when the two ld differ); FP8 storage: both
+ *         col_scale arrays (host / device, n floats) are copied as well
+ * The copy runs on a stream of the context's own, after the work already
+ * enqueued on the context's stream, and the call returns at once.  Every
+ * later gpspca_solve, gpspca_solve_batch, gpspca_submit, gpspca_solve_deflated,
+ * gpspca_project, gpspca_time_sweep and gpspca_tune of this context whose
+ * matrix has dst's data pointer waits on the device for the copy of the
+ * latest upload to that pointer (gpspca_sweep_static, which has no context,
+ * does not).  The host memory must stay unchanged until the copy has
+ * finished: a synchronous call that reads dst has returned, or a submitted
+ * one has been polled to completion.  dst must not be written to again, by
+ * an upload or otherwise, while a solve that reads it is still running.  The context remembers the last 16
+ * destinations.  Returns GPSPCA_OK, GPSPCA_EINVAL (locations, shapes or types
+ * that do not match, NULL pointers) or GPSPCA_ECUDA. */
+int gpspca_upload(gpspca_ctx* ctx, const gpspca_matrix* host, const gpspca_matrix* dst);
 
 /* Several sparse components with a single-unit formulation (form SL1 or
  * SL0), by projection deflation: component j (0 <= j < m) is the single-unit

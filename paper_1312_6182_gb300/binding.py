@@ -42,7 +42,7 @@ ERROR_NAMES = {
 EXPORTED = ("gpspca_create", "gpspca_solve", "gpspca_submit", "gpspca_poll", "gpspca_destroy",
             "gpspca_last_error", "gpspca_time_sweep", "gpspca_sweep_static", "gpspca_synth_spikes",
             "gpspca_solve_batch", "gpspca_solve_deflated", "gpspca_project", "gpspca_tune", "gpspca_tune_save",
-            "gpspca_tune_load", "gpspca_plan_launches")
+            "gpspca_tune_load", "gpspca_plan_launches", "gpspca_upload")
 
 
 class Matrix(ctypes.Structure):
@@ -138,6 +138,8 @@ def load(path: str = LIB_PATH):
     lib.gpspca_plan_launches.argtypes = [P, ctypes.POINTER(Matrix), ctypes.c_int, D, ctypes.c_int32, D,
                                          ctypes.c_uint32, ctypes.POINTER(ctypes.c_int32)]
     lib.gpspca_plan_launches.restype = ctypes.c_int
+    lib.gpspca_upload.argtypes = [P, ctypes.POINTER(Matrix), ctypes.POINTER(Matrix)]
+    lib.gpspca_upload.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -388,6 +390,20 @@ class Context:
             _check(rcs[k], allow)
             outs[k].rc = rcs[k]
         return outs
+
+    def upload(self, hA, dA, p: Optional[int] = None, host_scale=None, dev_scale=None):
+        """Asynchronous copy of the host tensor hA (page-locked for overlap)
+        into the device tensor dA of the same dtype and shape (gpspca_upload);
+        returns at once.  Later solves of this context on dA wait for the
+        copy on the device.  FP8: host_scale / dev_scale, the n column
+        scales on either side."""
+        H = matrix(hA, p, host_scale)
+        D = matrix(dA, p, dev_scale)
+        if H.location != HOST or D.location != DEVICE:
+            raise ValueError("upload copies a host tensor into a device tensor")
+        self._sync_torch(dA, dev_scale)
+        _check(self.lib.gpspca_upload(self.ptr, ctypes.byref(H), ctypes.byref(D)))
+        return dA
 
     def submit(self, At, form: str, gamma, mu=None, tol: float = 1e-6, maxit: int = 1000,
                gamma_relative: bool = False, p: Optional[int] = None, col_scale=None,

@@ -317,9 +317,13 @@ int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fa
   // where the CUDA-core passes become compute-bound: bf16 storage from 6
   // components (or gamma values) on, read in place when its layout suits TMA
   // (16-byte aligned base and column stride) and copied once per solve into
-  // a padded layout otherwise; float A as three bf16 planes and fp8 A as one,
-  // from 9 on (one CUDA-core pass covers up to 8).  Crossovers measured on
-  // GB300 over p x n in {5000 x 20000, 2000 x 60000, 8000 x 8000}.  Otherwise
+  // a padded layout otherwise; float A that TMA can read (split into three
+  // bf16 planes in shared memory) also from 6; other float layouts and fp8
+  // (copied once per solve) from 9 (one CUDA-core pass covers up to 8).
+  // Crossovers measured on GB300 over p x n in {5000 x 20000, 2000 x 60000,
+  // 8000 x 8000}: at 6-8 float components the fused tensor-core sweep takes
+  // 0.15 / 0.15 / 0.10 ms against 0.30 / 0.19 / 0.13 ms for one CUDA-core
+  // pass; at 5 the CUDA-core pass is as fast or faster.  Otherwise
   // the widest CUDA-core passes first (fewest reads of A) in the smallest
   // clusters that fit; long columns (large p) may only fit narrower passes,
   // whose per-thread register tiles are smaller.  The other candidates (the
@@ -333,7 +337,8 @@ int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fa
   };
   std::vector<Layout> lay;
   const bool tc_type = dt == GPSPCA_BF16 || dt == GPSPCA_F32 || dt == GPSPCA_FP8_E4M3;
-  const int tc_min_m = dt == GPSPCA_BF16 ? 6 : 9;
+  const bool f32_in_place = dt == GPSPCA_F32 && fast && ld % 4 == 0;
+  const int tc_min_m = (dt == GPSPCA_BF16 || f32_in_place) ? 6 : 9;
   const bool tc_default = allow_tc && tc_type && m >= tc_min_m && p >= 1 && n >= 1;
   if (tc_default) lay.push_back({true, 1, static_cast<int>(p), {}});
   for (int gmax : {8, 4, 2, 1}) {
@@ -397,7 +402,7 @@ int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fa
     // split into its planes in shared memory; other float / fp8 / bf16
     // layouts are copied once per solve
     const bool native_bf16 = dt == GPSPCA_BF16 && fast && ld % 8 == 0;
-    pl.tc_fused = (dt == GPSPCA_F32 && fast && ld % 4 == 0) ? 1 : 0;
+    pl.tc_fused = f32_in_place ? 1 : 0;
     pl.tc_convert = (native_bf16 || pl.tc_fused) ? 0 : 1;
     pl.tc_sparse = pl.tc_fused;
     plan_tc_ksplit(&pl, nsm);
@@ -1203,7 +1208,32 @@ struct gpspca_ctx {
   std::vector<std::unique_ptr<Slot>> batch_slots;
   cudaEvent_t batch_start = nullptr;
   std::vector<DevBuf> batch_stage;  // host matrices shared by several requests, copied once
+  // uploads (gpspca_upload), under up_mu: copies on their own stream, each
+  // destination with the event its copy recorded, oldest first
+  std::mutex up_mu;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t up_tail = nullptr;
+  struct Upload {
+    const void* data;
+    cudaEvent_t done;
+  };
+  std::vector<Upload> uploads;
 };
+
+static constexpr size_t kUploads = 16;
+
+// Make stream s wait (on the device) for the copy of the latest upload whose
+// destination is A's data, if there is one.
+static int wait_upload(gpspca_ctx* ctx, cudaStream_t s, const gpspca_matrix& A) {
+  if (A.location != GPSPCA_DEVICE || !A.data) return GPSPCA_OK;
+  std::lock_guard<std::mutex> lk(ctx->up_mu);
+  for (const gpspca_ctx::Upload& u : ctx->uploads)
+    if (u.data == A.data) {
+      GP_CUDA(cudaStreamWaitEvent(s, u.done, 0));
+      break;
+    }
+  return GPSPCA_OK;
+}
 
 static constexpr int kServeSlots = 8;
 
@@ -1255,7 +1285,8 @@ static void scheduler_main(gpspca_ctx* ctx) {
       bool empty = false;
       int rc = GPSPCA_ENOMEM;
       if (budget_take(&ctx->budget, t->foot)) {
-        rc = launch_solve(s, t->req, ctx->nsm, &empty);
+        rc = wait_upload(ctx, s->stream, t->req.A);
+        if (rc == GPSPCA_OK) rc = launch_solve(s, t->req, ctx->nsm, &empty);
         if (rc != GPSPCA_OK || empty) budget_give(&ctx->budget, t->foot);
       }
       if (rc == GPSPCA_ENOMEM) {
@@ -1384,6 +1415,10 @@ int gpspca_solve_batch(gpspca_ctx* ctx, int32_t count, const gpspca_request* req
       }
     }
   }
+  for (int i = 0; i < count; ++i) {
+    const int rc = wait_upload(ctx, cs, R[i].A);
+    if (rc != GPSPCA_OK) return rc;
+  }
   GP_CUDA(cudaEventRecord(ctx->batch_start, cs));
   std::vector<char> running(static_cast<size_t>(count), 0);
   auto collect = [&](int i) {
@@ -1407,6 +1442,66 @@ int gpspca_solve_batch(gpspca_ctx* ctx, int32_t count, const gpspca_request* req
   return GPSPCA_OK;
 }
 
+int gpspca_upload(gpspca_ctx* ctx, const gpspca_matrix* host, const gpspca_matrix* dst) {
+  if (!ctx || !host || !dst) return fail(GPSPCA_EINVAL, "ctx, host and dst must not be NULL");
+  const gpspca_matrix& H = *host;
+  const gpspca_matrix& D = *dst;
+  if (H.location != GPSPCA_HOST) return fail(GPSPCA_EINVAL, "upload source must be a host matrix");
+  if (D.location != GPSPCA_DEVICE) return fail(GPSPCA_EINVAL, "upload destination must be a device matrix");
+  if (H.dtype < GPSPCA_F32 || H.dtype > GPSPCA_F64) return fail(GPSPCA_EINVAL, "unknown dtype %d", (int)H.dtype);
+  if (H.dtype != D.dtype || H.p != D.p || H.n != D.n)
+    return fail(GPSPCA_EINVAL, "upload source and destination differ in dtype or shape");
+  const int64_t p = H.p, n = H.n;
+  if (p < 0 || n < 0 || p > (1 << 30) || n > (1 << 30)) return fail(GPSPCA_EINVAL, "bad shape");
+  if (p == 0 || n == 0) return GPSPCA_OK;
+  if (!H.data || !D.data) return fail(GPSPCA_EINVAL, "upload data pointer is NULL");
+  if (H.ld < p || D.ld < p) return fail(GPSPCA_EINVAL, "ld < rows");
+  const bool fp8 = H.dtype == GPSPCA_FP8_E4M3;
+  if (fp8 && (!H.col_scale || !D.col_scale)) return fail(GPSPCA_EINVAL, "FP8 storage needs col_scale on both sides");
+  std::lock_guard<std::mutex> lk(ctx->up_mu);
+  GP_CUDA(cudaSetDevice(ctx->device));
+  if (!ctx->copy_stream) GP_CUDA(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+  if (!ctx->up_tail) GP_CUDA(cudaEventCreateWithFlags(&ctx->up_tail, cudaEventDisableTiming));
+  // after the work already enqueued on the context's stream
+  GP_CUDA(cudaEventRecord(ctx->up_tail, ctx->sync_slot.stream));
+  GP_CUDA(cudaStreamWaitEvent(ctx->copy_stream, ctx->up_tail, 0));
+  const size_t es = dinfo(H.dtype).esize;
+  void* dd = const_cast<void*>(D.data);  // the descriptor's pointer is const for the solves' reads
+  if (H.ld == D.ld) {
+    const size_t bytes = (static_cast<size_t>(n - 1) * H.ld + p) * es;
+    GP_CUDA(cudaMemcpyAsync(dd, H.data, bytes, cudaMemcpyHostToDevice, ctx->copy_stream));
+  } else {
+    GP_CUDA(cudaMemcpy2DAsync(dd, D.ld * es, H.data, H.ld * es, p * es, n, cudaMemcpyHostToDevice,
+                              ctx->copy_stream));
+  }
+  if (fp8)
+    GP_CUDA(cudaMemcpyAsync(const_cast<float*>(D.col_scale), H.col_scale, sizeof(float) * n, cudaMemcpyHostToDevice,
+                            ctx->copy_stream));
+  // the destination's entry (moved to the back), or a new one; the oldest
+  // is dropped when the table is full, once its copy has finished (later
+  // solves of that destination need not wait for it)
+  std::vector<gpspca_ctx::Upload>& U = ctx->uploads;
+  gpspca_ctx::Upload e{D.data, nullptr};
+  for (size_t i = 0; i < U.size(); ++i)
+    if (U[i].data == D.data) {
+      e = U[i];
+      U.erase(U.begin() + static_cast<std::ptrdiff_t>(i));
+      break;
+    }
+  if (!e.done) {
+    if (U.size() >= kUploads) {
+      GP_CUDA(cudaEventSynchronize(U.front().done));
+      e.done = U.front().done;
+      U.erase(U.begin());
+    } else {
+      GP_CUDA(cudaEventCreateWithFlags(&e.done, cudaEventDisableTiming));
+    }
+  }
+  U.push_back(e);
+  GP_CUDA(cudaEventRecord(e.done, ctx->copy_stream));
+  return GPSPCA_OK;
+}
+
 int gpspca_solve(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form, const double* gamma, int32_t m,
                  const double* mu, double tol, int32_t maxit, const void* x0, uint32_t flags, gpspca_out* out) {
   if (!ctx) return fail(GPSPCA_EINVAL, "ctx is NULL");
@@ -1415,6 +1510,7 @@ int gpspca_solve(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form, cons
   if (rc != GPSPCA_OK) return rc;
   std::lock_guard<std::mutex> lk(ctx->solve_mu);
   GP_CUDA(cudaSetDevice(ctx->device));
+  if ((rc = wait_upload(ctx, ctx->sync_slot.stream, r.A)) != GPSPCA_OK) return rc;
   bool empty = false;
   rc = launch_solve(&ctx->sync_slot, r, ctx->nsm, &empty);
   if (rc != GPSPCA_OK || empty) return rc;
@@ -1434,6 +1530,7 @@ int gpspca_solve_deflated(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form f
   GP_CUDA(cudaSetDevice(ctx->device));
   Slot* s = &ctx->sync_slot;
   if (r.A.p == 0 || r.A.n == 0) return solve_empty(s, r);
+  if ((rc = wait_upload(ctx, s->stream, r.A)) != GPSPCA_OK) return rc;
   const int64_t p = r.A.p, n = r.A.n;
   const int wdt = r.A.dtype == GPSPCA_F64 ? GPSPCA_F64 : GPSPCA_F32;
   const size_t tcs = wdt == GPSPCA_F64 ? sizeof(double) : sizeof(float);
@@ -1556,6 +1653,7 @@ int gpspca_project(gpspca_ctx* ctx, const gpspca_matrix* B, const void* Z, int32
     return GPSPCA_OK;
   }
   int rc;
+  if ((rc = wait_upload(ctx, s->stream, *B)) != GPSPCA_OK) return rc;
   const void* Bd = B->data;
   const float* scale = B->col_scale;
   const void* Zd = Z;
@@ -1600,6 +1698,7 @@ int gpspca_time_sweep(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form,
   std::lock_guard<std::mutex> lk(ctx->solve_mu);
   GP_CUDA(cudaSetDevice(ctx->device));
   Slot* s = &ctx->sync_slot;
+  if ((rc = wait_upload(ctx, s->stream, r.A)) != GPSPCA_OK) return rc;
   Plan pl;
   bool empty = false;
   rc = prepare_solve(s, r, ctx->nsm, true, &pl, &empty);
@@ -1712,6 +1811,7 @@ int gpspca_tune(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form, const
   std::lock_guard<std::mutex> lk(ctx->solve_mu);
   GP_CUDA(cudaSetDevice(ctx->device));
   Slot* s = &ctx->sync_slot;
+  if ((rc = wait_upload(ctx, s->stream, r.A)) != GPSPCA_OK) return rc;
   int nc = 0;
   double best = 0.0, def = 0.0;
   std::string best_key, shape;
@@ -1865,6 +1965,10 @@ int gpspca_destroy(gpspca_ctx* ctx) {
   for (auto& s : ctx->serve_slots) slot_free(s.get());
   for (auto& s : ctx->batch_slots) slot_free(s.get());
   if (ctx->batch_start) cudaEventDestroy(ctx->batch_start);
+  if (ctx->copy_stream) cudaStreamSynchronize(ctx->copy_stream);
+  for (gpspca_ctx::Upload& u : ctx->uploads) cudaEventDestroy(u.done);
+  if (ctx->up_tail) cudaEventDestroy(ctx->up_tail);
+  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
   for (DevBuf& b : ctx->batch_stage) release(&ctx->sync_slot, &b);
   slot_free(&ctx->sync_slot);
   delete ctx;

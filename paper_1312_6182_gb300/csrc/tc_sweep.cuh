@@ -1,6 +1,7 @@
 // The wide sweep on the 5th-generation tensor cores (tcgen05): for many
 // components (or gamma values; the planner's crossover is m >= 6 for bf16
-// storage, m >= 9 otherwise), one power iteration is two tall-skinny
+// storage and for float storage read in place, m >= 9 otherwise), one power
+// iteration is two tall-skinny
 // contractions over A,
 //
 //   T = A^T X   (n x m; then the Table 1 threshold gives G, per entry)

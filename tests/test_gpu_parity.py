@@ -160,6 +160,29 @@ def test_block_many_components(ctx, p, n, m):
     assert_matches("BL1", g, ref, oracle.column_norms(A), label=f"BL1 m={m} {p}x{n}")
 
 
+@pytest.mark.parametrize("m", [6, 8])
+@pytest.mark.parametrize("tensor_cores", [True, False])
+def test_block_six_to_eight_float_components(ctx, m, tensor_cores):
+    """Float block L1 with 6 and 8 components on as many planted spikes: by
+    default on the tensor cores (float read in place and split into bf16
+    planes), and with tensor_cores=False in one 8-wide CUDA-core pass; both
+    against the oracle, 6 sweeps from the PCA start.  The two plans differ
+    (their per-iteration kernel counts are not the same)."""
+    p, n = 1500, 8000
+    At = synth.planted_spike(p, n, m, [80.0 / np.sqrt(j) for j in range(1, m + 1)], support_frac=0.02, seed=71,
+                             dtype=np.float32)
+    A = At.astype(np.float64).T
+    gam = _gammas(A, "BL1", [0.03] * m)
+    mu = [1.0] * m
+    dA = torch.from_numpy(At).cuda()
+    plans = [ctx.plan_launches(dA, "BL1", list(gam), mu=mu, tensor_cores=tc) for tc in (True, False)]
+    assert plans[0][1] != plans[1][1], plans
+    ref = oracle.gpower(A, "BL1", gam, mu=mu, tol=0.0, maxit=6)
+    res = ctx.solve(dA, "BL1", list(gam), mu=mu, tol=0.0, maxit=6, tensor_cores=tensor_cores)
+    assert_matches("BL1", gpu_arrays(res), ref, oracle.column_norms(A),
+                   label=f"BL1 m={m} {p}x{n} {'tensor cores' if tensor_cores else 'CUDA cores'}")
+
+
 # ---------------------------------------------------------------- tensor-core (tcgen05) sweep
 
 @pytest.mark.parametrize("form,p,n,m", [("BL1", 1496, 8008, 16), ("BL0", 2048, 6000, 16), ("BL1", 1504, 9000, 32)])
@@ -705,6 +728,77 @@ def test_batch_shares_host_matrix(ctx):
         for a, b in zip(dev, host):
             assert torch.equal(a.Z.cpu(), b.Z.cpu()) and torch.equal(a.X.cpu(), b.X.cpu())
             assert torch.equal(a.objective.cpu(), b.objective.cpu()) and torch.equal(a.iters.cpu(), b.iters.cpu())
+
+
+def test_upload_then_solve_equals_device_solve(ctx):
+    """gpspca_upload copies a pinned host matrix into a device tensor (same
+    stride; a wider stride, re-strided by the copy; fp8 with its scales);
+    a solve on the destination gives the bits of a solve on a device copy
+    made by PyTorch."""
+    p, n = 900, 3100
+    At = synth.planted_spike(p, n, 3, [30.0, 20.0, 12.0], support_frac=0.05, seed=32, dtype=np.float32)
+    ref = ctx.solve(torch.from_numpy(At).cuda(), "BL1", [0.05] * 3, mu=[1.0] * 3, gamma_relative=True)
+    for ld in (p, p + 36):
+        dst = torch.zeros((n, ld), device="cuda")
+        ctx.upload(torch.from_numpy(At).pin_memory(), dst, p=p)
+        got = ctx.solve(dst, "BL1", [0.05] * 3, mu=[1.0] * 3, gamma_relative=True, p=p)
+        assert torch.equal(got.Z, ref.Z) and torch.equal(got.X, ref.X), ld
+        assert torch.equal(got.objective, ref.objective)
+    s = np.abs(At).max(axis=1).astype(np.float32) / 448.0
+    q = torch.from_numpy(At / s[:, None]).to(torch.float8_e4m3fn)
+    ref8 = ctx.solve(q.cuda(), "SL0", [0.05], gamma_relative=True, col_scale=torch.from_numpy(s).cuda())
+    dq = torch.empty((n, p), dtype=torch.float8_e4m3fn, device="cuda")
+    ds = torch.zeros(n, device="cuda")
+    ctx.upload(q.pin_memory(), dq, host_scale=torch.from_numpy(s).pin_memory(), dev_scale=ds)
+    got8 = ctx.solve(dq, "SL0", [0.05], gamma_relative=True, col_scale=ds)
+    assert torch.equal(got8.Z, ref8.Z) and torch.equal(got8.objective, ref8.objective)
+
+
+def test_upload_double_buffered_batches(ctx):
+    """The pattern of a pipelined loop: the copy of step k + 1's matrix is
+    issued before the batch of step k, into the other of two device buffers,
+    and the matrices alternate between two different ones, so a solve that
+    did not wait for its copy would read the previous matrix (or part of
+    it).  Every step's results equal those of its matrix solved from a
+    device copy; outputs go to pinned host buffers."""
+    p, n = 2000, 25000  # 200 MB per copy
+    mats = [synth.planted_spike(p, n, 2, [40.0, 20.0], support_frac=0.02, seed=33 + k, dtype=np.float32)
+            for k in range(2)]
+    hosts = [torch.from_numpy(a).pin_memory() for a in mats]
+    cases = [("SL1", None), ("BL1", [1.0, 1.0])]
+    refs = []
+    for a in mats:
+        dA = torch.from_numpy(a).cuda()
+        refs.append([ctx.solve(dA, f, [0.05] * (1 if mu is None else 2), mu=mu, gamma_relative=True)
+                     for f, mu in cases])
+        del dA
+    bufs = [torch.zeros((n, p), device="cuda") for _ in range(2)]
+    steps = 6
+    ctx.upload(hosts[0], bufs[0])
+    for k in range(steps):
+        if k + 1 < steps:
+            ctx.upload(hosts[(k + 1) % 2], bufs[(k + 1) % 2])
+        items = []
+        for f, mu in cases:
+            m = 1 if mu is None else 2
+            out = binding.alloc_result(m, p, n, "cpu", torch.float32, pin=True)
+            items.append(dict(At=bufs[k % 2], form=f, gamma=[0.05] * m, mu=mu, gamma_relative=True, out=out))
+        res = ctx.solve_batch(items)
+        for a, b in zip(res, refs[k % 2]):
+            assert torch.equal(a.Z, b.Z.cpu()) and torch.equal(a.X, b.X.cpu()), k
+            assert torch.equal(a.objective, b.objective.cpu()), k
+
+
+def test_upload_rejects_mismatched_descriptors(ctx):
+    h = torch.zeros((10, 8)).pin_memory()
+    with pytest.raises(binding.GpspcaError) as e:
+        ctx.upload(h, torch.zeros((10, 7), device="cuda"))
+    assert e.value.code == binding.EINVAL
+    with pytest.raises(binding.GpspcaError) as e:
+        ctx.upload(h, torch.zeros((10, 8), device="cuda", dtype=torch.float64))
+    assert e.value.code == binding.EINVAL
+    with pytest.raises(ValueError):
+        ctx.upload(h, torch.zeros((10, 8)))
 
 
 def test_submitted_requests_equal_solo_solves(ctx):
