@@ -42,13 +42,13 @@ RHO32 = 0.01
 # dram bytes (read + write) per launch from ncu captures of the current
 # kernels (dram__bytes_read.sum + dram__bytes_write.sum): the fused sweeps on
 # the 5000 x 20000 matrix, and on the 20000 x 100000 matrix the tensor-core T
-# pass, the whole block threshold sweep (its six kernels) and the
-# single-unit sweep
+# pass and the whole block and single-unit threshold sweeps (their six
+# kernels each); None where the kernels changed since the last capture
 TRAFFIC_SL1 = 400.3e6
 TRAFFIC_BL1 = 400.7e6
 TRAFFIC_T4 = 8114.9e6
 TRAFFIC_BLK4 = 9456.2e6
-TRAFFIC_SU4 = 8000.9e6
+TRAFFIC_SU4 = None  # the single-unit sweep on the tensor cores: not captured yet
 METRIC = "GPower iters/s"
 UNIT = "iters/s"
 WORKLOAD4 = ("planted spikes 20000x100000 fp32 (16 spikes, theta_j=100/sqrt(j), 1% supports), SL1+SL0+BL1+BL0 "
@@ -263,17 +263,28 @@ def run_gpu(args):
     e2e_steps = args.steps
     e2e_ms, e2e_sweeps, _ = _run_steps(ctx, stream, dA, hA, CASES4, P4, N4, e2e_steps, args.warmup, False, host=True,
                                        label="gpspca_step_e2e")
-    del hA
+    # the host link alone: uploads of the matrix with nothing else running
+    # (the copies run on the library's copy stream: timed on the host around
+    # a device synchronisation)
+    buf = torch.empty_like(dA)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(3):
+        ctx.upload(hA, buf)
+    torch.cuda.synchronize()
+    h2d_ms = (time.perf_counter() - t0) * 1e3 / 3
+    del buf, hA
     h2d = P4 * N4 * 4
     d2h = sum((P4 + N4) * 4 * (1 if mu is None else len(mu)) + ((N4 + 31) // 32) * 4 * (1 if mu is None else len(mu))
               + 24 * (1 if mu is None else len(mu)) for _, mu in CASES4)
     bytes_a = P4 * N4 * 4
-    # the kernels of the step: the block solves' T pass (T = A^T X on the
-    # tensor cores; every sweep of a block solve, the start's three included,
-    # runs one), the block threshold sweep as a whole (T pass, listing of the
-    # active columns, rank update over them) and the single-unit fused sweep;
-    # algorithmic bytes = one read of A per launch for each.  The dominant
-    # one by its share of the step's kernel time is the roofline line.
+    # the kernels of the step: the T pass (T = A^T X on the tensor cores:
+    # every sweep of every solve runs one, the block starts' three included;
+    # the 20000-row single-unit solves run the tensor-core sweep too), and the
+    # threshold sweeps as a whole (T pass, listing of the active columns,
+    # rank update over them) of the block and the single-unit solves;
+    # algorithmic bytes = one read of A per launch for each.  The T pass, by
+    # its share of the step, is the roofline line.
     r_t = _roofline(ctx, dA, "BL1", M4, bytes_a, peak, peak_kind,
                     "tc_t_fused_kernel<48> (+ tc_prep, tc_t_combine): T = A^T X on tcgen05, float A split into exact "
                     "bf16 planes in shared memory", TRAFFIC_T4, t_pass=True)
@@ -281,16 +292,17 @@ def run_gpu(args):
                       "block m=16 threshold sweep: tc_prep + tc_t_fused<48> + tc_t_combine + tc_count + "
                       "tc_compact + tc_y_fused<48> over the active columns", TRAFFIC_BLK4)
     r_su = _roofline(ctx, dA, "SL1", 1, bytes_a, peak, peak_kind,
-                     "sweep_kernel<float,1,2,0,3> (single-unit fused sweep, overlapped single-column tiles)",
-                     TRAFFIC_SU4)
+                     "single-unit threshold sweep on the tensor cores: tc_prep + tc_t_fused<48> + tc_t_combine + "
+                     "tc_count + tc_compact + tc_y_fused<48> over the active columns", TRAFFIC_SU4)
     its = _case_iters(ctx, dA, CASES4, P4, N4)
-    t_ms = sum(3 + it for (f, _), it in zip(CASES4, its) if f.startswith("B")) * r_t["ms_per_launch"]
-    su_ms = sum(it for (f, _), it in zip(CASES4, its) if f.startswith("S")) * r_su["ms_per_launch"]
+    # block: the start's two power steps and rotation step, and every sweep
+    # but the first (its T comes from the rotation step's); single-unit: every sweep
+    n_t = sum((2 + it) if f.startswith("B") else it for (f, _), it in zip(CASES4, its))
     step_ms = ms / args.steps
-    r_t["share_of_step"] = round(t_ms / step_ms, 3)
-    r_su["share_of_step"] = round(su_ms / step_ms, 3)
+    r_t["launches_per_step"] = n_t
+    r_t["share_of_step"] = round(n_t * r_t["ms_per_launch"] / step_ms, 3)
     r_blk["launches_per_step"] = sum(it for (f, _), it in zip(CASES4, its) if f.startswith("B"))
-    dom, other = (r_t, r_su) if t_ms >= su_ms else (r_su, r_t)
+    r_su["launches_per_step"] = sum(it for (f, _), it in zip(CASES4, its) if f.startswith("S"))
     del dA
     torch.cuda.empty_cache()
 
@@ -328,11 +340,12 @@ def run_gpu(args):
         "config": {"workload": WORKLOAD4, "p": P4, "n": N4, "m_block": M4, "solves_per_step": len(CASES4),
                    "sweeps_per_step": round(sweeps / args.steps, 2), "iters_per_case": its,
                    "l2": "inputs larger than L2 (A is 8 GB)", "parallelism": "replicas" if ws > 1 else "1 gpu"},
-        "roofline": dom,
-        "roofline_other": other,
+        "roofline": r_t,
         "roofline_block_sweep": r_blk,
+        "roofline_single_unit_sweep": r_su,
         "e2e": {"value": round(e2e_sweeps / (e2e_ms / 1e3), 2), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms / e2e_steps, 3),
+                "h2d_alone_gbs": round(h2d / (h2d_ms / 1e3) / 1e9, 1)},
         "gpu_launches": launches,
         "clocks": clocks,
         "spikes_5000x20000": secondary,
@@ -447,6 +460,9 @@ def run_sweep_only(args):
 
     if args.sweep_matrix == "20000x100000":
         At, p, n = synth.workload_spikes_20000x100000(2), P4, N4
+    elif args.sweep_matrix == "20000x25000":  # column blocks 0-3 of 16 of the 20000 x 100000 matrix (2 GB)
+        At = synth.workload_spikes_20000x100000(2, blocks=(0, 4))
+        p, n = At.shape[1], At.shape[0]
     else:
         At, p, n = synth.workload_spikes_5000x20000(0), P, N
     dA = torch.from_numpy(At).cuda()
@@ -1018,7 +1034,7 @@ def main():
                     help="time the fused sweep alone on the benchmark matrix (profiling)")
     ap.add_argument("--sweep-m", type=int, default=None, help="sweep-only: components or gammas (default 1 / 5)")
     ap.add_argument("--sweep-dtype", default="f32", choices=["f32", "bf16"])
-    ap.add_argument("--sweep-matrix", default="5000x20000", choices=["5000x20000", "20000x100000"],
+    ap.add_argument("--sweep-matrix", default="5000x20000", choices=["5000x20000", "20000x100000", "20000x25000"],
                     help="sweep-only: the matrix")
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--workload", default="step",

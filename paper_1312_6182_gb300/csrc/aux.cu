@@ -666,7 +666,7 @@ __global__ void __launch_bounds__(kFinishThreads, 1) finish_kernel(const FinishA
     if (a.mode == kFinishIterate) sum_partials(io->fpart, a.nsplit, 2 * m, 2 * m, fz);
   }
   if (proceed && (a.mode == kFinishRitz || a.mode == kFinishRitzT)) {
-    ritz_weights(gsum, m, st->W, Wt, jac, a.mode == kFinishRitzT);
+    ritz_weights(gsum, m, st->W, Wt, jac, a.mode == kFinishRitzT, a.mode == kFinishRitzT ? st->R : nullptr);
     for (int idx = tid; idx < m * m; idx += blockDim.x) st->W[idx] = Wt[idx];
   } else if (proceed && a.mode == kFinishPolar) {
     if (block) {

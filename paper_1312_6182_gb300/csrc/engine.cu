@@ -129,6 +129,7 @@ static KAttr kattr(const void* f) {
 // ---------------------------------------------------------------- planning
 
 constexpr int kSmemBudget = 200 * 1024;  // stage ring + bookkeeping, per CTA
+constexpr int64_t kTcLongRows = 9000;     // float columns this long take the tensor-core sweep for any m
 
 static const int kMGs[] = {1, 2, 4, 5, 8};
 
@@ -172,14 +173,9 @@ static bool fit_variant(int dt, int mg, int nch, const void* k, int ps, int m, b
     --W;
   }
   if (W < 1 || S < 2) return false;
-  // single-column tiles (long columns): the per-tile chain of dot products,
-  // block barrier and cluster exchange is the latency, so tiles overlap
-  // (phase A of the next before phase B of this one; four exchange slots,
-  // one stage less of prefetch)
-  const int ov = (W == 1 && S >= 3) ? 1 : 0;
-  const SweepSmem L = sweep_smem_layout(W, S, ps, d.esize, d.tcsize, nw, m, mg, ov ? 4 : kXSlots);
+  const SweepSmem L = sweep_smem_layout(W, S, ps, d.esize, d.tcsize, nw, m, mg);
   if (L.total > at.max_dyn_smem) return false;
-  *out = Pass{0, 0, mg, nch, threads, W, S, L.total, k, ov};
+  *out = Pass{0, 0, mg, nch, threads, W, S, L.total, k};
   return true;
 }
 
@@ -294,7 +290,7 @@ static bool same_passes(const std::vector<Pass>& a, const std::vector<Pass>& b) 
   if (a.size() != b.size()) return false;
   for (size_t i = 0; i < a.size(); ++i)
     if (a[i].mg != b[i].mg || a[i].mgv != b[i].mgv || a[i].k != b[i].k || a[i].threads != b[i].threads ||
-        a[i].W != b[i].W || a[i].S != b[i].S || a[i].ov != b[i].ov)
+        a[i].W != b[i].W || a[i].S != b[i].S)
       return false;
   return true;
 }
@@ -323,11 +319,18 @@ int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fa
   // Crossovers measured on GB300 over p x n in {5000 x 20000, 2000 x 60000,
   // 8000 x 8000}: at 6-8 float components the fused tensor-core sweep takes
   // 0.15 / 0.15 / 0.10 ms against 0.30 / 0.19 / 0.13 ms for one CUDA-core
-  // pass; at 5 the CUDA-core pass is as fast or faster.  Otherwise
+  // pass; at 5 the CUDA-core pass is as fast or faster.  Float read in place
+  // with columns of kTcLongRows rows or more takes the tensor-core sweep for
+  // any m: a CUDA-core CTA holds at most 5000-8000 float rows in registers,
+  // so such columns are split over clusters whose per-tile exchange (and
+  // idle SMs) cost more than the tensor-core sweep's two passes (single-unit
+  // at 10000 x 40000 / 12000 x 30000 / 20000 x 25000: 0.327 / 0.288 / 0.392
+  // ms against 0.363 / 0.318 / 0.441 ms; a tie at 16000 x 30000; block m = 5
+  // at 20000 x 25000: 0.71 ms on the CUDA cores).  Otherwise
   // the widest CUDA-core passes first (fewest reads of A) in the smallest
   // clusters that fit; long columns (large p) may only fit narrower passes,
   // whose per-thread register tiles are smaller.  The other candidates (the
-  // autotuner times them all): the tensor-core sweep from 2 components, and
+  // autotuner times them all): the tensor-core sweep for any m, and
   // every pass grouping of at most 8, 5, 4, 2 or 1 components in clusters of
   // 1, 2, 4 or 8 that fits.
   struct Layout {
@@ -339,7 +342,8 @@ int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fa
   const bool tc_type = dt == GPSPCA_BF16 || dt == GPSPCA_F32 || dt == GPSPCA_FP8_E4M3;
   const bool f32_in_place = dt == GPSPCA_F32 && fast && ld % 4 == 0;
   const int tc_min_m = (dt == GPSPCA_BF16 || f32_in_place) ? 6 : 9;
-  const bool tc_default = allow_tc && tc_type && m >= tc_min_m && p >= 1 && n >= 1;
+  const bool long_cols = f32_in_place && p >= kTcLongRows;
+  const bool tc_default = allow_tc && tc_type && (m >= tc_min_m || long_cols) && p >= 1 && n >= 1;
   if (tc_default) lay.push_back({true, 1, static_cast<int>(p), {}});
   for (int gmax : {8, 4, 2, 1}) {
     if (!lay.empty()) break;
@@ -355,8 +359,7 @@ int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fa
     return fail(GPSPCA_EINVAL, "no sweep configuration fits p=%lld (rows too long for the on-chip tile ring)",
                 (long long)p);
   if (cand > 0 || ncand) {  // the alternatives, only when asked for (they cost a fit per variant)
-    if (!tc_default && allow_tc && tc_type && m >= 2 && p >= 1 && n >= 1)
-      lay.push_back({true, 1, static_cast<int>(p), {}});
+    if (!tc_default && allow_tc && tc_type && p >= 1 && n >= 1) lay.push_back({true, 1, static_cast<int>(p), {}});
     for (int gmax : {8, 5, 4, 2, 1})
       for (int C : {1, 2, 4, 8}) {
         Layout L{false, C, 0, {}};
@@ -365,30 +368,6 @@ int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fa
         for (const Layout& o : lay) dup = dup || (!o.tc && o.C == L.C && same_passes(o.passes, L.passes));
         if (!dup) lay.push_back(L);
       }
-    // each CUDA-core layout also with its tiles overlapped the other way
-    // (phase A of the next tile before phase B of this one, or not)
-    const size_t base = lay.size();
-    for (size_t li = 0; li < base; ++li) {
-      if (lay[li].tc) continue;
-      Layout L = lay[li];
-      bool ok = true;
-      for (Pass& q : L.passes) {
-        if (q.S < 3) {
-          ok = false;
-          break;
-        }
-        q.ov = q.ov ? 0 : 1;
-        const DInfo d = dinfo(dt);
-        const SweepSmem S2 = sweep_smem_layout(q.W, q.S, L.ps, d.esize, d.tcsize, q.threads / 32, m, q.mg,
-                                               q.ov ? 4 : kXSlots);
-        if (S2.total > kattr(q.k).max_dyn_smem) {
-          ok = false;
-          break;
-        }
-        q.smem = S2.total;
-      }
-      if (ok) lay.push_back(L);
-    }
   }
   if (ncand) *ncand = static_cast<int>(lay.size());
   const int pick = cand < 0 ? 0 : cand;
@@ -404,7 +383,7 @@ int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fa
     const bool native_bf16 = dt == GPSPCA_BF16 && fast && ld % 8 == 0;
     pl.tc_fused = f32_in_place ? 1 : 0;
     pl.tc_convert = (native_bf16 || pl.tc_fused) ? 0 : 1;
-    pl.tc_sparse = pl.tc_fused;
+    pl.tc_sparse = 1;  // threshold sweeps' rank update over the listed active columns
     plan_tc_ksplit(&pl, nsm);
     pl.C = 1;
     pl.ps = static_cast<int>(p);
@@ -640,7 +619,14 @@ static void slot_free(Slot* s) {
 // ---------------------------------------------------------------- graph
 
 static cudaError_t launch_sweeps(const Plan& pl, Slot* s, cudaStream_t cs, int sketch = 0, int norms = 0,
-                                 int keep_t = 0);
+                                 int keep_t = 0, int from_ritz = 0);
+static cudaError_t launch_body(const Plan& pl, Slot* s, cudaStream_t cs, cudaGraphConditionalHandle h,
+                               int use_cond = 1, int from_ritz = 0);
+
+// The first sweep after a block start on the tensor cores can form T from
+// the T = A^T Q its Rayleigh-Ritz step kept (T = (A^T Q) R) instead of a T
+// pass; unscaled storage (the kept T of fp8 storage carries the scales).
+static bool first_sweep_from_ritz(const Plan& pl) { return pl.tc && pl.pca && pl.dtype != GPSPCA_FP8_E4M3; }
 
 // Start of the solve: norms, gamma, the start directions and their
 // projection.  Block forms without a caller start then take kPowerSteps
@@ -694,7 +680,10 @@ static cudaError_t launch_prologue(const Plan& pl, Slot* s, cudaStream_t cs, cud
     FinishArgs fr{s->io_dev, s->st_dev, pl.ncl, gram_t_blocks(pl.n), pl.m * pl.m, pl.m, pl.form, kFinishRitzT, 1, h,
                   use_cond};
     launch_finish(fr, pl.finish_smem, cs);
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // the first sweep, its T from the kept A^T Q and the rotation
+    if (first_sweep_from_ritz(pl)) return launch_body(pl, s, cs, h, use_cond, 1);
+    return cudaSuccess;
   }
   if ((e = launch_sweeps(pl, s, cs, 1)) != cudaSuccess) return e;
   ReduceArgs rc{s->io_dev, s->st_dev, pl.ncl, pl.m, pl.p, 1, pl.m * pl.m, 0, 1, 0, pl.n, pl.form, pl.nred, 0};
@@ -705,13 +694,15 @@ static cudaError_t launch_prologue(const Plan& pl, Slot* s, cudaStream_t cs, cud
 }
 
 // keep_t (tensor-core sweep, start only): X3 and the T pass alone, T = A^T Q
-// written to io->T for the Rayleigh-Ritz step's T^T T.
-static cudaError_t launch_sweeps(const Plan& pl, Slot* s, cudaStream_t cs, int sketch, int norms, int keep_t) {
+// written to io->T for the Rayleigh-Ritz step's T^T T.  from_ritz
+// (tensor-core sweep, the first sweep after the start): T from that kept T.
+static cudaError_t launch_sweeps(const Plan& pl, Slot* s, cudaStream_t cs, int sketch, int norms, int keep_t,
+                                 int from_ritz) {
   if (pl.tc) {
     TcArgs a{s->io_dev,  s->st_dev, pl.p,     pl.n,       pl.m,        pl.mpad,     pl.form,
              sketch,     pl.tc_na,  pl.tc_fused, pl.dtype == GPSPCA_FP8_E4M3 ? 1 : 0, pl.p_pad, pl.n_pad,
              pl.ntile1,  pl.kchunks1, pl.ksplit1, pl.kcs1, pl.nchunks2, pl.kps2, pl.nsplit2, pl.nrow2,
-             pl.tc_sparse, norms, keep_t};
+             pl.tc_sparse, norms, keep_t, pl.tc_convert ? static_cast<int64_t>(pl.p_pad) : pl.ld, from_ritz};
     launch_tc_sweep(a, pl.npad, cs, keep_t != 0);
     return cudaGetLastError();
   }
@@ -719,7 +710,7 @@ static cudaError_t launch_sweeps(const Plan& pl, Slot* s, cudaStream_t cs, int s
   for (size_t pi = 0; pi < pl.passes.size(); ++pi) {
     const Pass& q = (norms && pi == 0) ? pl.norm_pass : pl.passes[pi];
     SweepArgs a{s->io_dev, s->st_dev, pl.ld, pl.p, pl.n, pl.m, pl.form, q.j0, q.mgv, pl.ps, q.W, q.S,
-                pl.cols_per_cl, pl.fast, sketch, q.ov};
+                pl.cols_per_cl, pl.fast, sketch};
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -740,8 +731,8 @@ static cudaError_t launch_sweeps(const Plan& pl, Slot* s, cudaStream_t cs, int s
 }
 
 static cudaError_t launch_body(const Plan& pl, Slot* s, cudaStream_t cs, cudaGraphConditionalHandle h,
-                               int use_cond = 1) {
-  cudaError_t e = launch_sweeps(pl, s, cs);
+                               int use_cond, int from_ritz) {
+  cudaError_t e = launch_sweeps(pl, s, cs, 0, 0, 0, from_ritz);
   if (e != cudaSuccess) return e;
   const int gram_pairs = pl.full_gram ? pl.m * (pl.m + 1) / 2 : pl.m;
   ReduceArgs ra{s->io_dev, s->st_dev, pl.ncl, pl.m, pl.p, pl.full_gram, gram_pairs, 0, 0, 1, pl.n, pl.form, pl.nred,
@@ -992,8 +983,10 @@ static int prepare_solve(Slot* s, const Request& r, int nsm, bool scratch_out, P
     } else {
       const void* planes = pl.tc_convert ? s->b_planes.p : A_dev;
       const int64_t pld = pl.tc_convert ? pl.p_pad : ld;
+      const void* g3c =
+          pl.tc_sparse ? static_cast<unsigned char*>(s->b_sparse.p) + sparse_layout(n, pl.npad).g3c : nullptr;
       if ((rc = tc_encode_maps(s->maps_host, planes, pl.tc_na, pld * n, p, n, pld, s->b_x3.p, pl.p_pad, s->b_g3.p,
-                               pl.n_pad, pl.npad)))
+                               pl.n_pad, pl.npad, g3c)))
         return rc;
     }
     GP_CUDA(cudaMemcpyAsync(s->b_maps.p, s->maps_host, sizeof(TcMaps), cudaMemcpyHostToDevice, s->stream));
@@ -1739,6 +1732,9 @@ static void plan_launch_counts(const Plan& pl, int32_t c[3]) {
   // cores X3 and the T pass (+ combine), T^T T and the finish
   const int ritz = pl.tc ? 2 + (pl.ksplit1 > 1 ? 1 : 0) + 2 : sweeps + 2;
   if (pl.pca) pro += kPowerSteps * (sweeps + 2) + (late_norms ? 1 : 0) + (late_norms && pl.tc ? 1 : 0) + ritz;
+  // the first sweep runs with the start, its T pass (and combine) replaced
+  // by one kernel: counted as an iteration, less the difference
+  if (first_sweep_from_ritz(pl)) pro -= (pl.ksplit1 > 1 ? 1 : 0);
   c[0] = pro;
   c[1] = sweeps + (pl.tc_sparse ? 2 : 0) + 2;
   c[2] = 1;

@@ -73,6 +73,7 @@ struct State {
   double f[kMaxM];
   double znorm2[kMaxM];  // squared norm of the unnormalised loading column of the last sweep
   double W[kMaxM * kMaxM];  // projection weights: X_k = Y_{k-1} W, [l * m + j]
+  double R[kMaxM * kMaxM];  // the block start's Rayleigh-Ritz rotation: X_0 = Q R, [k * m + j]
   dd V[kMaxM * kMaxM];      // eigenvectors of the last Gram matrix, double-float (warm start of the next eigensolve)
   int32_t has_v;
   double cmax;              // max_i ||a_i||
@@ -104,7 +105,6 @@ struct SweepArgs {
   int j0, mg_valid;
   int ps, W, S, cols_per_cl, fast;
   int sketch;  // 1: power step of the block start (no threshold, no outputs)
-  int overlap; // 1: phase A of tile t+1 before phase B of tile t (single-column tiles)
 };
 
 }  // namespace gpspca

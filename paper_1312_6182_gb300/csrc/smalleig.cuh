@@ -409,8 +409,9 @@ __device__ inline bool polar_weights(const double* gsum, int m, double* W, doubl
 // All threads of the CTA call it.
 // direct: C is already the projected matrix Q^T A A^T Q (= T^T T for T = A^T
 // Q) rather than the cross Gram of the two directions, and H = sym(C).
+// Rout (optional): the rotation itself, ordered and signed (Wout = Wcur Rout).
 __device__ inline void ritz_weights(const double* C, int m, const double* Wcur, double* Wout, double* wsbase,
-                                    bool direct = false) {
+                                    bool direct = false, double* Rout = nullptr) {
   const int mm = m + (m & 1);
   const EigWs ws = eig_ws(wsbase, m);
   __shared__ int ord[kMaxM];
@@ -495,6 +496,7 @@ __device__ inline void ritz_weights(const double* C, int m, const double* Wcur, 
     dd s{0.0f, 0.0f};
     for (int k = 0; k < m; ++k) s = dd_fma(ws.E[l * m + k], ws.V[k * mm + c], s);
     Wout[l * m + j] = sgn[j] * dd_to_double(s) * back;
+    if (Rout) Rout[l * m + j] = sgn[j] * dd_to_double(ws.V[l * mm + c]);
   }
   __syncthreads();
 }

@@ -350,6 +350,45 @@ __global__ void tc_t_combine_kernel(const TcArgs a) {
   tc_t_finish<MPAD>(a, i, j, sum, scl, sketch ? GPSPCA_SL0 : a.form, gam_s, mu_s, act_s);
 }
 
+// The first sweep after the block start: T = A^T X_0 for X_0 = Q R, the
+// start's last iterate Q rotated by the Rayleigh-Ritz step, is (A^T Q) R,
+// and the rotation step kept A^T Q in io->T; so this sweep forms T from it
+// (double sums of m products per entry) instead of reading A, and finishes
+// each entry as the T pass does.  One thread per column: its m entries of
+// A^T Q are read before any entry of T is overwritten.  Unscaled storage
+// only (the kept T already carries an fp8 column scale).
+template <int MPAD>
+__global__ void tc_t_from_ritz_kernel(const TcArgs a) {
+  __shared__ float gam_s[kMaxM], mu_s[kMaxM];
+  __shared__ int act_s[kMaxM];
+  __shared__ double R[MPAD * MPAD];
+  const IO* io = a.io;
+  const State* st = a.st;
+  if (st->n_active == 0) return;  // uniform across the grid
+  const int tid = threadIdx.x, m = a.m;
+  if (tid < kMaxM) {
+    const bool v = tid < m;
+    gam_s[tid] = v ? static_cast<float>(st->gamma[tid]) : 0.0f;
+    mu_s[tid] = v ? static_cast<float>(io->mu[tid]) : 1.0f;
+    act_s[tid] = v ? st->active[tid] : 0;
+  }
+  for (int idx = tid; idx < m * m; idx += blockDim.x) R[idx] = st->R[idx];
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + tid;
+  if (i >= a.n) return;
+  float* T = static_cast<float*>(io->T);
+  float q[MPAD];
+#pragma unroll
+  for (int k = 0; k < MPAD; ++k) q[k] = k < m ? T[static_cast<int64_t>(k) * a.n + i] : 0.0f;
+#pragma unroll 4
+  for (int j = 0; j < MPAD; ++j) {
+    double t = 0.0;
+    if (j < m)
+      for (int k = 0; k < m; ++k) t = fma(static_cast<double>(q[k]), R[k * m + j], t);
+    tc_t_finish<MPAD>(a, i, j, static_cast<float>(t), 1.0f, a.form, gam_s, mu_s, act_s);
+  }
+}
+
 // ---- the active columns of a threshold sweep (some G_ij != 0), listed in
 // increasing order for the Y pass, which then reads only those columns of A
 // (the others multiply zeros).  Two launches over blocks of kTcCompactCols
@@ -549,9 +588,92 @@ __global__ void __launch_bounds__(kTcThreads) tc_t_kernel(const TcArgs a) {
   tc_teardown<NPAD, NA>(S, tmem, timed_out, st);
 }
 
+// Producer of the Y pass over listed columns, bf16 planes (the whole warp):
+// chunk c holds list entries 64c .. 64c+63 of this block's 128 rows.  Lanes
+// 0-15 copy the sixteen 16-byte pieces of one listed column's rows, lanes
+// 16-31 those of the next, by cp.async into the place a TMA tile load with
+// the 128-byte swizzle would put them (half h = rows 64h .. 64h+63, column k
+// of the chunk at byte 128 k, piece q at 16 (q xor k mod 8)), so the MMA
+// reads the stage as in the dense pass; rows past p are zero-filled.  Lane 0
+// copies the G3c tile by TMA.  A stage is handed to the MMA (one arrival,
+// the G3c bytes expected) once the warp's copies into it have completed,
+// kLag chunks later, after a proxy fence.  false on a timeout or an abort.
+template <int NPAD, int NA>
+__device__ __forceinline__ bool tc_list_producer(const TcSmem& S, const TcArgs& a, int rb, int cb, int ce,
+                                                 const TcMaps* maps) {
+  using Cfg = TcCfg<NPAD, NA>;
+  constexpr int kS = Cfg::kStages;
+  constexpr int kLag = kS >= 3 ? 2 : 1;  // chunks whose copies are in flight before their arrival
+  static_assert(kLag < kS, "a stage's arrival precedes the wait for its next use");
+  const int lane = threadIdx.x & 31;
+  const int qp = lane & 15, half = qp >> 3, qq = qp & 7;
+  const int32_t* list = a.io->tc_list;
+  const __nv_bfloat16* base =
+      static_cast<const __nv_bfloat16*>(a.io->tc_planes ? a.io->tc_planes : a.io->A);
+  const int64_t ld = a.yld, plane = a.yld * a.n;
+  const int r = rb * kTcRows2 + qp * 8;  // first row of this lane's pieces
+  const uint32_t nbytes = static_cast<uint32_t>(max(0, min(8, a.p - r)) * 2);
+  const int64_t roff = nbytes ? r : 0;
+  int l0 = 0, l1 = 0;  // list entries 64c + lane and 64c + 32 + lane of the next chunk
+  auto pull = [&](int c) {
+    if (c < ce) {
+      l0 = list[static_cast<int64_t>(c) * kTcBK + lane];
+      l1 = list[static_cast<int64_t>(c) * kTcBK + 32 + lane];
+    }
+  };
+  auto hand_over = [&](int it) {  // chunk it's copies are complete and visible to the MMA
+    fence_async_smem();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(smem_u32(&S.full[it % kS]));
+  };
+  pull(cb);
+  const int n_it = ce - cb;
+  for (int it = 0; it < n_it; ++it) {
+    const int c = cb + it;
+    const int s = it % kS;
+    const uint32_t u = static_cast<uint32_t>(it / kS);
+    int ok = 1;
+    if (lane == 0)
+      ok = !tc_aborted(S) && (u == 0 || mbar_wait_bounded(smem_u32(&S.empty[s]), (u - 1) & 1)) ? 1 : 0;
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (!ok) {
+      cp_async_wait<0>();
+      if (lane == 0) *S.abort_flag = 1;
+      return false;
+    }
+    const uint32_t sa = S.base + s * Cfg::kStage;
+    if (lane == 0) {
+      const uint32_t bar = smem_u32(&S.full[s]);
+      mbar_expect_tx(bar, Cfg::kB);
+      tma_load_2d(sa + Cfg::kAll, &maps->g3c, c * kTcBK, 0, bar);
+    }
+    const int c0 = l0, c1 = l1;
+    pull(c + 1);
+#pragma unroll 8
+    for (int q = 0; q < 32; ++q) {
+      const int k = 2 * q + (lane >> 4);
+      const int col = __shfl_sync(0xffffffffu, q < 16 ? c0 : c1, k & 31);
+      const uint32_t dst = sa + half * (kTcA / 2) + k * 128 + ((qq ^ (k & 7)) << 4);
+      const __nv_bfloat16* src = base + static_cast<int64_t>(col) * ld + roff;
+#pragma unroll
+      for (int pl = 0; pl < NA; ++pl) cp_async_16(dst + pl * kTcA, src + pl * plane, nbytes);
+    }
+    cp_async_commit();
+    if (it >= kLag) {
+      cp_async_wait<kLag>();
+      hand_over(it - kLag);
+    }
+  }
+  cp_async_wait<0>();
+  for (int it = max(0, n_it - kLag); it < n_it; ++it) hand_over(it);
+  return true;
+}
+
 // ---- pass 2: Y = A G for 128-row blocks, the columns split over gridDim.y;
 // partial sums to ypart[split].  Tensor-memory lane = row of the block.  The
 // A tile is the operand in MN-major form (64 rows contiguous per column).
+// A threshold sweep with few active columns reads only those (listed by the
+// compaction step, copied by tc_list_producer); otherwise every column.
 template <int NPAD, int NA>
 __global__ void __launch_bounds__(kTcThreads) tc_y_kernel(const TcArgs a) {
   using Cfg = TcCfg<NPAD, NA>;
@@ -564,11 +686,20 @@ __global__ void __launch_bounds__(kTcThreads) tc_y_kernel(const TcArgs a) {
   State* st = a.st;
   const TcMaps* maps = static_cast<const TcMaps*>(io->tc_maps);
   const int rb = blockIdx.x, sp = blockIdx.y;
-  const int cb = sp * a.kps2, ce = min(a.nchunks2, cb + a.kps2);
+  const int nl = (a.sparse && !a.sketch) ? *io->tc_nlist : 0;
+  const bool listed =
+      a.sparse && !a.sketch && static_cast<int64_t>(nl) * 10 <= static_cast<int64_t>(a.n) * kTcSparseTenths;
+  const int nch = listed ? (nl + kTcBK - 1) / kTcBK : a.nchunks2;
+  const int kps = listed ? (nch + static_cast<int>(gridDim.y) - 1) / static_cast<int>(gridDim.y) : a.kps2;
+  const int cb = sp * kps, ce = max(cb, min(nch, cb + kps));
   const uint32_t tmem = tc_setup<NPAD, NA>(S);
   bool timed_out = false;
 
-  if (warp == 4) {  // TMA producer
+  if (warp == 4 && listed) {  // copies of the listed columns
+    if (lane == 0) tmap_acquire(&maps->g3c);
+    __syncwarp();
+    if (!tc_list_producer<NPAD, NA>(S, a, rb, cb, ce, maps)) timed_out = true;
+  } else if (warp == 4) {  // TMA producer
     if (lane == 0) {
       for (int pl = 0; pl < NA; ++pl) tmap_acquire(&maps->a2[pl]);
       tmap_acquire(&maps->g3);
@@ -1340,11 +1471,15 @@ int tc_encode_maps_f32(TcMaps* maps, const void* A, int64_t p, int64_t n, int64_
 int tc_fused_smem_bytes(int npad) { return tc_fused_smem(npad); }
 
 int tc_encode_maps(TcMaps* maps, const void* planes, int na, int64_t plane, int64_t p, int64_t n, int64_t ld,
-                   const void* x3, int p_pad, const void* g3, int n_pad, int npad) {
+                   const void* x3, int p_pad, const void* g3, int n_pad, int npad, const void* g3c) {
   bool ok = encode_bf16(&maps->x3, x3, p, npad, p_pad, npad) && encode_bf16(&maps->g3, g3, n, npad, n_pad, npad);
   for (int pl = 0; pl < na && ok; ++pl) {
     const void* base = static_cast<const __nv_bfloat16*>(planes) + pl * plane;
     ok = encode_bf16(&maps->a1[pl], base, p, n, ld, kTcTile1) && encode_bf16(&maps->a2[pl], base, p, n, ld, 64);
+  }
+  if (ok && g3c) {  // the Y pass over listed columns: G3c in rows of ceil(n / 64) * 64
+    const int64_t n64 = (n + 63) / 64 * 64;
+    ok = encode_bf16(&maps->g3c, g3c, n64, npad, n64, npad);
   }
   if (!ok) return record_error(GPSPCA_ECUDA, "cuTensorMapEncodeTiled failed for the tensor-core sweep");
   return GPSPCA_OK;
@@ -1400,10 +1535,19 @@ static void launch_tc_npad(const TcArgs& a, int nsm, cudaStream_t s, bool t_only
   (void)once;
   const int smem = tc_smem_bytes(NPAD, NA);
   tc_prep_kernel<<<dim3((a.p + 255) / 256, a.mpad), 256, 0, s>>>(a);
-  tc_t_kernel<NPAD, NA><<<std::max(1, std::min(a.ntile1 * a.ksplit1, tc_ctas_per_sm(NPAD, NA) * nsm)), kTcThreads,
-                          smem, s>>>(a);
-  if (a.ksplit1 > 1) tc_t_combine_kernel<NPAD / 3><<<dim3((a.n + 255) / 256, NPAD / 3), 256, 0, s>>>(a);
+  if (a.from_ritz) {
+    tc_t_from_ritz_kernel<NPAD / 3><<<(a.n + 255) / 256, 256, 0, s>>>(a);
+  } else {
+    tc_t_kernel<NPAD, NA><<<std::max(1, std::min(a.ntile1 * a.ksplit1, tc_ctas_per_sm(NPAD, NA) * nsm)), kTcThreads,
+                            smem, s>>>(a);
+    if (a.ksplit1 > 1) tc_t_combine_kernel<NPAD / 3><<<dim3((a.n + 255) / 256, NPAD / 3), 256, 0, s>>>(a);
+  }
   if (t_only) return;
+  if (a.sparse && !a.sketch) {
+    const int nb = (a.n + kTcCompactCols - 1) / kTcCompactCols;
+    tc_count_kernel<<<nb, 256, 0, s>>>(a);
+    tc_compact_kernel<NPAD / 3><<<nb, 256, 0, s>>>(a);
+  }
   tc_y_kernel<NPAD, NA><<<dim3(a.nrow2, a.nsplit2), kTcThreads, smem, s>>>(a);
 }
 
@@ -1417,8 +1561,12 @@ static void launch_tc_fused_npad(const TcArgs& a, int nsm, cudaStream_t s, bool 
   (void)once;
   const int smem = tc_fused_smem(NPAD);
   tc_prep_kernel<<<dim3((a.p + 255) / 256, a.mpad), 256, 0, s>>>(a);
-  tc_t_fused_kernel<NPAD><<<std::max(1, std::min(a.ntile1 * a.ksplit1, nsm)), kTcFusedThreads, smem, s>>>(a);
-  if (a.ksplit1 > 1) tc_t_combine_kernel<NPAD / 3><<<dim3((a.n + 255) / 256, NPAD / 3), 256, 0, s>>>(a);
+  if (a.from_ritz) {
+    tc_t_from_ritz_kernel<NPAD / 3><<<(a.n + 255) / 256, 256, 0, s>>>(a);
+  } else {
+    tc_t_fused_kernel<NPAD><<<std::max(1, std::min(a.ntile1 * a.ksplit1, nsm)), kTcFusedThreads, smem, s>>>(a);
+    if (a.ksplit1 > 1) tc_t_combine_kernel<NPAD / 3><<<dim3((a.n + 255) / 256, NPAD / 3), 256, 0, s>>>(a);
+  }
   if (a.norms) tc_norms_kernel<<<(a.n + 255) / 256, 256, 0, s>>>(a);
   if (t_only) return;
   if (a.sparse && !a.sketch) {

@@ -79,9 +79,11 @@ struct TcArgs {
   int kps2;           // 64-column chunks per Y-pass split
   int nsplit2;        // Y-pass splits of the columns
   int nrow2;          // ceil(p / 128)
-  int sparse;         // fused float Y pass over the active columns only (threshold sweeps, not the start)
+  int sparse;         // Y pass over the active columns only (threshold sweeps, not the start)
   int norms;          // fused float T pass also sums the columns' squared norms (the start's first step)
   int keep_t;         // start: the T pass writes T = A^T Q to io->T (the Rayleigh-Ritz step's T^T T)
+  int64_t yld;        // bf16 planes: column stride (elements) of the planes the Y pass reads
+  int from_ritz;      // first sweep after the block start: T = (A^T Q) R from the kept T, no T pass
 };
 
 // Host side (tc_sweep.cu).
@@ -89,7 +91,7 @@ int tc_smem_bytes(int npad, int na);
 bool tc_supported(int device);
 // planes: na bf16 matrices (p x n, column stride ld elements, `plane` elements apart)
 int tc_encode_maps(TcMaps* maps, const void* planes, int na, int64_t plane, int64_t p, int64_t n, int64_t ld,
-                   const void* x3, int p_pad, const void* g3, int n_pad, int npad);
+                   const void* x3, int p_pad, const void* g3, int n_pad, int npad, const void* g3c);
 // float A read in place by the fused passes (16-byte aligned base, ld % 4 == 0)
 int tc_encode_maps_f32(TcMaps* maps, const void* A, int64_t p, int64_t n, int64_t ld, const void* x3, int p_pad,
                        const void* g3, int n_pad, int npad, const void* g3c);

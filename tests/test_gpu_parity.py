@@ -119,19 +119,27 @@ def test_fixed_sweeps_ragged(ctx, form, ld):
 
 
 @pytest.mark.parametrize("form", oracle.FORMS)
-def test_long_columns_overlapped_tiles(ctx, form):
-    """Columns longer than 8192 rows per CTA make single-column tiles, where
-    the fused sweep overlaps the next tile's dot products with this tile's
-    cluster exchange (four exchange slots, one stage less of prefetch):
-    12001 x 2003 planted spikes, 6 sweeps against the oracle."""
-    At = synth.planted_spike(12001, 2003, 2, [60.0, 35.0], support_frac=0.03, seed=64, dtype=np.float32)
+@pytest.mark.parametrize("tensor_cores", [True, False])
+def test_long_columns(ctx, form, tensor_cores):
+    """Float columns of 9000 rows or more: by default the tensor-core sweep
+    for any m (here one or two components); with tensor_cores=False the
+    CUDA-core sweep, which splits each column's rows over a cluster of CTAs
+    whose partial dot products meet through distributed shared memory before
+    the threshold.  12004 x 2003 planted spikes (rows ragged against the
+    CTAs' slices and the 64-row chunks), 6 sweeps against the oracle; the two
+    plans differ."""
+    At = synth.planted_spike(12004, 2003, 2, [60.0, 35.0], support_frac=0.03, seed=64, dtype=np.float32)
     A = At.astype(np.float64).T
     m = 1 if form.startswith("S") else 2
     mu = None if m == 1 else [1.0, 0.8]
     gam = _gammas(A, form, [0.05] * m)
+    dA = torch.from_numpy(At).cuda()
+    plans = [ctx.plan_launches(dA, form, list(gam), mu=mu, tensor_cores=tc) for tc in (True, False)]
+    assert plans[0][1] != plans[1][1], plans
     ref = oracle.gpower(A, form, gam, mu=mu, tol=0.0, maxit=6)
-    g, _ = _run(ctx, At, form, gam, mu=mu, tol=0.0, maxit=6)
-    assert_matches(form, g, ref, oracle.column_norms(A), label=f"long columns {form}")
+    res = ctx.solve(dA, form, list(gam), mu=mu, tol=0.0, maxit=6, tensor_cores=tensor_cores)
+    assert_matches(form, gpu_arrays(res), ref, oracle.column_norms(A),
+                   label=f"long columns {form} {'tensor cores' if tensor_cores else 'CUDA cores'}")
 
 
 @pytest.mark.parametrize("form", ["SL1", "SL0"])
@@ -329,6 +337,79 @@ def test_tensor_core_listed_columns(ctx, form, p, n, m, frac):
     assert_matches(form, gpu_arrays(res), ref, oracle.column_norms(A), label=f"tc listed {form} {p}x{n} m={m}")
     again = ctx.solve(torch.from_numpy(At).cuda(), form, list(gam), mu=[1.0] * m, tol=0.0, maxit=4)
     assert torch.equal(res.Z, again.Z) and torch.equal(res.X, again.X)
+
+
+@pytest.mark.parametrize("storage,form,p,n,m", [
+    ("bf16", "BL1", 2100, 3001, 16),      # bf16 read in place (column stride a multiple of 8)
+    ("bf16", "BL0", 777, 1601, 10),       # p ragged: the last pieces of each column zero-filled
+    ("bf16-odd", "BL1", 1501, 2999, 12),  # unaligned stride: the padded bf16 copy
+    ("fp8", "BL1", 1200, 3001, 16),       # fp8 values (bf16 copy), column scales in G
+    ("f32-odd", "BL0", 1203, 2501, 16),   # float with an unaligned stride: three bf16 planes copied
+])
+def test_tensor_core_listed_columns_bf16_planes(ctx, storage, form, p, n, m):
+    """The rank update over the listed active columns in the tensor-core
+    sweep that reads bf16 planes (bf16 storage, fp8 values, copied float
+    planes): the listed columns are copied piece by piece into the swizzled
+    layout of a tile load.  m planted spikes (theta_j = 60/sqrt(j), 2%
+    supports: 20-32% of the columns active, below the 60% up to which the
+    sweep lists them), 4 sweeps from the PCA start, against the oracle on the
+    stored values; a second solve gives the same bits."""
+    At = synth.planted_spike(p, n, m, [60.0 / np.sqrt(j + 1) for j in range(m)], support_frac=0.02, seed=63,
+                             dtype=np.float32)
+    scale = None
+    if storage.startswith("bf16"):
+        tb, deq = _bf16(At)
+        if storage == "bf16-odd":
+            wide = torch.zeros((n, p + 2), dtype=torch.bfloat16)  # stride 1503: not a multiple of 8
+            wide[:, :p] = tb
+            dA = wide.cuda()
+        else:
+            dA = tb.cuda()
+    elif storage == "fp8":
+        q, sc, deq = _fp8(At)
+        dA, scale = q.cuda(), sc.cuda()
+    else:
+        deq = At
+        wide = torch.zeros((n, p + 2), dtype=torch.float32)  # stride 1205: not a multiple of 4
+        wide[:, :p] = torch.from_numpy(At)
+        dA = wide.cuda()
+    A = deq.astype(np.float64).T
+    gam = _gammas(A, form, [0.05] * m)
+    mu = [1.0] * m
+    ref = oracle.gpower(A, form, gam, mu=mu, tol=0.0, maxit=4)
+    res = ctx.solve(dA, form, list(gam), mu=mu, tol=0.0, maxit=4, p=p, col_scale=scale)
+    active = np.count_nonzero(np.any(ref.Z != 0, axis=1)) / n
+    assert active <= 0.4, active
+    assert_matches(form, gpu_arrays(res), ref, oracle.column_norms(A),
+                   label=f"tc listed {storage} {form} {p}x{n} m={m} ({active:.0%} active)")
+    again = ctx.solve(dA, form, list(gam), mu=mu, tol=0.0, maxit=4, p=p, col_scale=scale)
+    assert torch.equal(res.Z, again.Z) and torch.equal(res.X, again.X)
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+@pytest.mark.parametrize("maxit", [1, 2])
+def test_first_sweep_from_the_rotation_step(ctx, storage, maxit):
+    """The first sweep after a block start on the tensor cores forms T from
+    the A^T Q its Rayleigh-Ritz step kept, times the rotation (no read of A
+    for T): one and two sweeps from the PCA start against the oracle, and
+    the host-driven launches give the graph's bits."""
+    p, n, m = 1500, 4099, 16
+    At = synth.planted_spike(p, n, m, [60.0 / np.sqrt(j + 1) for j in range(m)], support_frac=0.01, seed=65,
+                             dtype=np.float32)
+    if storage == "bf16":
+        tb, deq = _bf16(At)
+        dA, A = tb.cuda(), deq.astype(np.float64).T
+    else:
+        dA, A = torch.from_numpy(At).cuda(), At.astype(np.float64).T
+    gam = _gammas(A, "BL1", [0.05] * m)
+    mu = [1.0] * m
+    ref = oracle.gpower(A, "BL1", gam, mu=mu, tol=0.0, maxit=maxit)
+    res = ctx.solve(dA, "BL1", list(gam), mu=mu, tol=0.0, maxit=maxit)
+    assert_matches("BL1", gpu_arrays(res), ref, oracle.column_norms(A),
+                   label=f"first sweep from the rotation {storage} maxit={maxit}")
+    eager = ctx.solve(dA, "BL1", list(gam), mu=mu, tol=0.0, maxit=maxit, eager=True)
+    assert torch.equal(res.Z, eager.Z) and torch.equal(res.X, eager.X)
+    assert torch.equal(res.objective, eager.objective) and torch.equal(res.iters, eager.iters)
 
 
 def test_tensor_core_all_thresholded(ctx):
