@@ -48,7 +48,7 @@ TRAFFIC_SL1 = 400.3e6
 TRAFFIC_BL1 = 400.7e6
 TRAFFIC_T4 = 8114.9e6
 TRAFFIC_BLK4 = 9456.2e6
-TRAFFIC_SU4 = None  # the single-unit sweep on the tensor cores: not captured yet
+TRAFFIC_SU4 = 8173.4e6
 METRIC = "GPower iters/s"
 UNIT = "iters/s"
 WORKLOAD4 = ("planted spikes 20000x100000 fp32 (16 spikes, theta_j=100/sqrt(j), 1% supports), SL1+SL0+BL1+BL0 "
@@ -713,6 +713,86 @@ def run_latency(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args):
+    """Many small instances: 256 independent single-unit L1 solves of the
+    latency-bound shape (200 x 1000 N(0,1), centred columns, FP64, gamma =
+    0.1 max||a_i||, tol 1e-6; each its own seeded matrix) and 256 of 512 x
+    4096 FP32 planted spikes (2 spikes, 5% supports, gamma = 0.05
+    max||a_i||).  Each set three ways: one gpspca_solve_batch (same-shape
+    requests run as groups: one launch per step for all members), the same
+    requests queued with gpspca_submit (up to 8 solves in flight on their
+    own streams), and one gpspca_solve after another.  Reported: solves/s
+    and power iterations/s per way, and that every grouped result equals its
+    one-by-one solve bit for bit."""
+    import time
+
+    import numpy as np
+    import torch
+
+    from paper_1312_6182_gb300 import binding, synth
+
+    count = 256
+    sets = []
+    mats = [synth.workload_fp64_200x1000(1000 + i) for i in range(count)]
+    sets.append(("fp64 200x1000 SL1", [torch.from_numpy(a).cuda() for a in mats], 0.1, torch.float64))
+    mats = [synth.planted_spike(512, 4096, 2, [30.0, 15.0], support_frac=0.05, seed=2000 + i, dtype=np.float32)
+            for i in range(count)]
+    sets.append(("fp32 512x4096 SL1", [torch.from_numpy(a).cuda() for a in mats], 0.05, torch.float32))
+    del mats
+    ctx = binding.Context(0)
+    res = {}
+    for name, dAs, rho, tc in sets:
+        p, n = int(dAs[0].shape[1]), int(dAs[0].shape[0])
+        outs = [binding.alloc_result(1, p, n, "cuda", tc) for _ in dAs]
+        items = [dict(At=d, form="SL1", gamma=[rho], gamma_relative=True, out=o) for d, o in zip(dAs, outs)]
+
+        def batch():
+            return ctx.solve_batch(items)
+
+        def serial():
+            return [ctx.solve(d, "SL1", [rho], gamma_relative=True, out=o) for d, o in zip(dAs, outs)]
+
+        def submitted():
+            tickets = [ctx.submit(d, "SL1", [rho], gamma_relative=True, out=o)[0] for d, o in zip(dAs, outs)]
+            for t in tickets:
+                while ctx.poll(t, 1000) == binding.PENDING:
+                    pass
+            return outs
+
+        entry = {}
+        for way, fn in (("batch_grouped", batch), ("submit_8_in_flight", submitted), ("one_by_one", serial)):
+            for _ in range(args.warmup):
+                fn()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                fn()
+            torch.cuda.synchronize()
+            sec = (time.perf_counter() - t0) / args.steps
+            iters = int(sum(int(o.iters[0]) for o in outs))
+            entry[way] = {"ms_per_set": round(sec * 1e3, 3), "solves_per_s": round(count / sec, 1),
+                          "iters_per_s": round(iters / sec, 1)}
+            if way == "batch_grouped":
+                keep = [(o.Z.clone(), o.X.clone(), o.objective.clone()) for o in outs]
+        serial()
+        torch.cuda.synchronize()
+        same = sum(torch.equal(z, o.Z) and torch.equal(x, o.X) and torch.equal(f, o.objective)
+                   for (z, x, f), o in zip(keep, outs))
+        entry["grouped_equal_one_by_one"] = f"{same}/{count}"
+        entry["iters_mean"] = round(float(np.mean([int(o.iters[0]) for o in outs])), 1)
+        entry["speedup_grouped_vs_one_by_one"] = round(
+            entry["one_by_one"]["ms_per_set"] / entry["batch_grouped"]["ms_per_set"], 2)
+        res[name] = entry
+    ctx.close()
+    value = res["fp64 200x1000 SL1"]["batch_grouped"]["solves_per_s"]
+    line = _base_line("grouped small solves/s (256 x 200x1000 fp64 SL1)", "solves/s", value,
+                      res["fp64 200x1000 SL1"]["batch_grouped"]["ms_per_set"], args,
+                      "256 independent single-unit solves per set: 200x1000 N(0,1) centred fp64 (gamma 0.1) and "
+                      "512x4096 fp32 planted spikes (gamma 0.05); grouped batch vs submit/poll vs one by one",
+                      "f64|f32", {"results": res})
+    print(json.dumps(line), flush=True)
+
+
 SCALING_FORMS = (("SL0", 0.01), ("BL0", 0.01), ("SL1", 0.05), ("BL1", 0.05))
 
 
@@ -1038,7 +1118,7 @@ def main():
                     help="sweep-only: the matrix")
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--workload", default="step",
-                    choices=["step", "gamma-path", "precision", "serving", "deflation", "scaling", "latency"],
+                    choices=["step", "gamma-path", "precision", "serving", "deflation", "scaling", "latency", "batch"],
                     help="step: the headline step (20000x100000, with the 5000x20000 step beside it); the others "
                          "measure the sparsity-path batch, the "
                          "BF16/FP8 precision path, the serving mix, deflated multi-component extraction and the "
@@ -1065,7 +1145,8 @@ def main():
     if args.workload != "step":
         args.warmup = max(args.warmup, 1)
         {"gamma-path": run_gamma_path, "precision": run_precision, "serving": run_serving,
-         "deflation": run_deflation, "scaling": run_scaling, "latency": run_latency}[args.workload](args)
+         "deflation": run_deflation, "scaling": run_scaling, "latency": run_latency,
+         "batch": run_batch}[args.workload](args)
         return
     if args.warmup < 3 and args.impl == "gpu":
         args.warmup = 3

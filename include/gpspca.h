@@ -194,7 +194,13 @@ typedef struct {
  * A host matrix shared by several requests of the batch (same data pointer,
  * dtype, shape, ld and col_scale) is copied to the device once, on the
  * context's stream before the batch starts, into a buffer the context keeps
- * (counted against the budget) for later batches. */
+ * (counted against the budget) for later batches.  Four or more single-unit
+ * requests with one component and the same storage type, form, shape,
+ * column stride and alignment (device matrices; not GPSPCA_EAGER) run as a
+ * group of up to 256: each step of their solves is one kernel launch for
+ * all of them.  A member's sweep sums over fewer column slabs than a solo
+ * solve's, so it agrees with a solo solve to float rounding; its bits do
+ * not depend on the group's size or other members. */
 int gpspca_solve_batch(gpspca_ctx* ctx, int32_t count, const gpspca_request* reqs, int32_t* rcs);
 
 /* Asynchronous copy of a host matrix to device memory the caller owns, so

@@ -96,7 +96,7 @@ __device__ void sum_partials(const P* __restrict__ src, int nb, int stride, int 
 
 // ---------------------------------------------------------------- kernels
 
-__global__ void reset_state_kernel(const IO* io, State* st, int m, int form) {
+__device__ __forceinline__ void reset_state_body(const IO* io, State* st, int m, int form) {
   const int j = threadIdx.x;
   if (j == 0) {
     st->k = -1;
@@ -166,7 +166,7 @@ struct Wide<__nv_fp8_e4m3> {
 // candidates are recomputed by select_start_kernel before any decision is
 // taken on them.  One warp per column.  A non-finite norm flags the solve.
 template <typename TA>
-__global__ void colnorm_kernel(const IO* io, State* st, int64_t ld, int p, int n, int fast) {
+__device__ __forceinline__ void colnorm_body(const IO* io, State* st, int64_t ld, int p, int n, int fast) {
   double* cnorm = io->cnorm;
   using TC = typename Elem<TA>::TC;
   constexpr int NW = Wide<TA>::N;
@@ -293,7 +293,7 @@ __device__ __forceinline__ bool better(double v, int i, double bv, int bi) {
 // ties to the lower index, decided on accurate norms; gamma scaled by
 // max_i ||a_i|| when relative.  One CTA.
 template <typename TA>
-__global__ void __launch_bounds__(kStartThreads) select_start_kernel(const StartArgs a) {
+__device__ __forceinline__ void select_start_body(const StartArgs& a) {
   const IO* io = a.io;
   State* st = a.st;
   const int tid = threadIdx.x, nthr = blockDim.x;
@@ -404,7 +404,7 @@ __global__ void __launch_bounds__(kStartThreads) select_start_kernel(const Start
 
 // P[j][r] = start column (converted, scaled) or the caller's x0.
 template <typename TA>
-__global__ void gather_start_kernel(const StartArgs a) {
+__device__ __forceinline__ void gather_start_body(const StartArgs& a) {
   using TC = typename Elem<TA>::TC;
   const IO* io = a.io;
   const State* st = a.st;
@@ -526,7 +526,7 @@ __device__ __forceinline__ void sum_split_partials(const TC* __restrict__ yp, in
 // double.  Blocks [nyb, nyb + nobj) (with `objective`): a share of the Table 1
 // objective and of the loadings' squared norms from T, in double-float.
 template <typename TC>
-__global__ void __launch_bounds__(kReduceRows* kReduceGroups) reduce_kernel(const ReduceArgs a) {
+__device__ __forceinline__ void reduce_body(const ReduceArgs& a) {
   if (a.st->n_active == 0) return;
   const int tid = threadIdx.x;
   const int m = a.m, p = a.p;
@@ -648,7 +648,7 @@ __global__ void __launch_bounds__(kReduceRows* kReduceGroups) reduce_kernel(cons
 // Objective, stopping test and projection weights after a sweep, or one step
 // of the start (projection of the start, Rayleigh-Ritz rotation).  One CTA:
 // sums and stopping test in double, the m x m eigenproblems in double-float.
-__global__ void __launch_bounds__(kFinishThreads, 1) finish_kernel(const FinishArgs a) {
+__device__ __forceinline__ void finish_body(const FinishArgs& a) {
   extern __shared__ double fsm[];
   State* st = a.st;
   const IO* io = a.io;
@@ -779,7 +779,7 @@ __global__ void __launch_bounds__(kFinishThreads, 1) finish_kernel(const FinishA
 // Loadings from the last sweep's T (Table 1, original form): threshold,
 // scale each column to unit norm, support bitmap; plus the scalar outputs.
 template <typename TC>
-__global__ void finalize_kernel(const IO* io, const State* st, int p, int n, int m, int form) {
+__device__ __forceinline__ void finalize_body(const IO* io, const State* st, int p, int n, int m, int form) {
   const int j = blockIdx.y;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int it = st->iters[j];
@@ -809,6 +809,79 @@ __global__ void finalize_kernel(const IO* io, const State* st, int p, int n, int
     io->status[j] = st->status[j];
     if (io->gamma_abs) io->gamma_abs[j] = st->gamma[j];
   }
+}
+
+// ---------------------------------------------------------------- launchers
+
+// ---------------------------------------------------------------- entry kernels
+//
+// Each step as a kernel of one solve, and as a kernel of a group of
+// same-shape solves (`*_grouped`): instance blockIdx.z of the group, its IO
+// and State from the group's pointer arrays, the rest of the arguments shared.
+
+__global__ void reset_state_kernel(const IO* io, State* st, int m, int form) { reset_state_body(io, st, m, form); }
+__global__ void reset_state_grouped(GroupPtrs g, int m, int form) {
+  reset_state_body(g.io[blockIdx.z], g.st[blockIdx.z], m, form);
+}
+
+template <typename TA>
+__global__ void colnorm_kernel(const IO* io, State* st, int64_t ld, int p, int n, int fast) {
+  colnorm_body<TA>(io, st, ld, p, n, fast);
+}
+template <typename TA>
+__global__ void colnorm_grouped(GroupPtrs g, int64_t ld, int p, int n, int fast) {
+  colnorm_body<TA>(g.io[blockIdx.z], g.st[blockIdx.z], ld, p, n, fast);
+}
+
+template <typename TA>
+__global__ void __launch_bounds__(kStartThreads) select_start_kernel(const StartArgs a) { select_start_body<TA>(a); }
+template <typename TA>
+__global__ void __launch_bounds__(kStartThreads) select_start_grouped(StartArgs a, GroupPtrs g) {
+  a.io = g.io[blockIdx.z];
+  a.st = g.st[blockIdx.z];
+  select_start_body<TA>(a);
+}
+
+template <typename TA>
+__global__ void gather_start_kernel(const StartArgs a) { gather_start_body<TA>(a); }
+template <typename TA>
+__global__ void gather_start_grouped(StartArgs a, GroupPtrs g) {
+  a.io = g.io[blockIdx.z];
+  a.st = g.st[blockIdx.z];
+  gather_start_body<TA>(a);
+}
+
+template <typename TC>
+__global__ void __launch_bounds__(kReduceRows* kReduceGroups) reduce_kernel(const ReduceArgs a) { reduce_body<TC>(a); }
+template <typename TC>
+__global__ void __launch_bounds__(kReduceRows* kReduceGroups) reduce_grouped(ReduceArgs a, GroupPtrs g) {
+  a.io = g.io[blockIdx.z];
+  a.st = g.st[blockIdx.z];
+  reduce_body<TC>(a);
+}
+
+__global__ void __launch_bounds__(kFinishThreads, 1) finish_kernel(const FinishArgs a) { finish_body(a); }
+__global__ void __launch_bounds__(kFinishThreads, 1) finish_grouped(FinishArgs a, GroupPtrs g) {
+  a.io = g.io[blockIdx.z];
+  a.st = g.st[blockIdx.z];
+  finish_body(a);
+}
+
+template <typename TC>
+__global__ void finalize_kernel(const IO* io, const State* st, int p, int n, int m, int form) {
+  finalize_body<TC>(io, st, p, n, m, form);
+}
+template <typename TC>
+__global__ void finalize_grouped(GroupPtrs g, int p, int n, int m, int form) {
+  finalize_body<TC>(g.io[blockIdx.z], g.st[blockIdx.z], p, n, m, form);
+}
+
+// The loop condition of a group: another sweep while any instance is active.
+__global__ void group_cond_kernel(GroupPtrs g, int count, cudaGraphConditionalHandle h) {
+  int any = 0;
+  for (int i = threadIdx.x; i < count; i += 32) any |= g.st[i]->n_active > 0 ? 1 : 0;
+  any = __any_sync(0xffffffffu, any);
+  if (threadIdx.x == 0) cudaGraphSetConditional(h, any ? 1u : 0u);
 }
 
 // ---------------------------------------------------------------- launchers
@@ -971,6 +1044,77 @@ void launch_finalize(int tcsize, const IO* io, const State* st, int p, int n, in
     finalize_kernel<double><<<grid, 256, 0, s>>>(io, st, p, n, m, form);
   else
     finalize_kernel<float><<<grid, 256, 0, s>>>(io, st, p, n, m, form);
+}
+
+// ---- the same launches for a group of `count` same-shape solves
+
+void launch_reset_g(GroupPtrs g, int count, int m, int form, cudaStream_t s) {
+  reset_state_grouped<<<dim3(1, 1, count), kMaxM, 0, s>>>(g, m, form);
+}
+
+template <typename TA>
+static void colnorm_g_t(GroupPtrs g, int count, int64_t ld, int p, int n, int fast, cudaStream_t s) {
+  const int blocks = std::max(1, std::min((n + 7) / 8, 4096));
+  colnorm_grouped<TA><<<dim3(blocks, 1, count), 256, 0, s>>>(g, ld, p, n, fast);
+}
+
+void launch_colnorm_g(int dtype, GroupPtrs g, int count, int64_t ld, int p, int n, int fast, cudaStream_t s) {
+  switch (dtype) {
+    case GPSPCA_F32: colnorm_g_t<float>(g, count, ld, p, n, fast, s); break;
+    case GPSPCA_F64: colnorm_g_t<double>(g, count, ld, p, n, fast, s); break;
+    case GPSPCA_BF16: colnorm_g_t<__nv_bfloat16>(g, count, ld, p, n, fast, s); break;
+    default: colnorm_g_t<__nv_fp8_e4m3>(g, count, ld, p, n, fast, s); break;
+  }
+}
+
+void launch_select_start_g(int dtype, const StartArgs& a, GroupPtrs g, int count, cudaStream_t s) {
+  const dim3 grid(1, 1, count);
+  switch (dtype) {
+    case GPSPCA_F32: select_start_grouped<float><<<grid, kStartThreads, 0, s>>>(a, g); break;
+    case GPSPCA_F64: select_start_grouped<double><<<grid, kStartThreads, 0, s>>>(a, g); break;
+    case GPSPCA_BF16: select_start_grouped<__nv_bfloat16><<<grid, kStartThreads, 0, s>>>(a, g); break;
+    default: select_start_grouped<__nv_fp8_e4m3><<<grid, kStartThreads, 0, s>>>(a, g); break;
+  }
+}
+
+void launch_gather_start_g(int dtype, const StartArgs& a, GroupPtrs g, int count, cudaStream_t s) {
+  const dim3 grid((a.p + 255) / 256, a.m, count);
+  switch (dtype) {
+    case GPSPCA_F32: gather_start_grouped<float><<<grid, 256, 0, s>>>(a, g); break;
+    case GPSPCA_F64: gather_start_grouped<double><<<grid, 256, 0, s>>>(a, g); break;
+    case GPSPCA_BF16: gather_start_grouped<__nv_bfloat16><<<grid, 256, 0, s>>>(a, g); break;
+    default: gather_start_grouped<__nv_fp8_e4m3><<<grid, 256, 0, s>>>(a, g); break;
+  }
+}
+
+void launch_reduce_g(int tcsize, const ReduceArgs& a, GroupPtrs g, int count, cudaStream_t s) {
+  const dim3 grid(a.nyb + (a.objective ? a.nobj : 0), 1, count);
+  if (tcsize == 8)
+    reduce_grouped<double><<<grid, kReduceRows * kReduceGroups, 0, s>>>(a, g);
+  else
+    reduce_grouped<float><<<grid, kReduceRows * kReduceGroups, 0, s>>>(a, g);
+}
+
+void launch_finish_g(const FinishArgs& a, int smem, GroupPtrs g, int count, cudaStream_t s) {
+  static bool once = [] {
+    cudaFuncSetAttribute(finish_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize, kFinishMaxSmem);
+    return true;
+  }();
+  (void)once;
+  finish_grouped<<<dim3(1, 1, count), kFinishThreads, smem, s>>>(a, g);
+}
+
+void launch_finalize_g(int tcsize, GroupPtrs g, int count, int p, int n, int m, int form, cudaStream_t s) {
+  const int len = std::max(n, p);
+  const dim3 grid((len + 255) / 256, m, count);
+  if (tcsize == 8)
+    finalize_grouped<double><<<grid, 256, 0, s>>>(g, p, n, m, form);
+  else
+    finalize_grouped<float><<<grid, 256, 0, s>>>(g, p, n, m, form);
+}
+
+void launch_group_cond(GroupPtrs g, int count, cudaGraphConditionalHandle h, cudaStream_t s) {
+  group_cond_kernel<<<1, 32, 0, s>>>(g, count, h);
 }
 
 }  // namespace gpspca

@@ -79,4 +79,16 @@ constexpr int kGramTCols = 256;  // columns of T per block
 inline int gram_t_blocks(int64_t n) { return static_cast<int>((n + kGramTCols - 1) / kGramTCols); }
 void launch_gram_t(const IO* io, const State* st, int m, int n, cudaStream_t s);
 
+// The same steps for a group of `count` same-shape solves, one launch each
+// (grid z = instance; the IO and State pointers of `a` are replaced by the
+// group's); the loop condition of a group: any instance still active.
+void launch_reset_g(GroupPtrs g, int count, int m, int form, cudaStream_t s);
+void launch_colnorm_g(int dtype, GroupPtrs g, int count, int64_t ld, int p, int n, int fast, cudaStream_t s);
+void launch_select_start_g(int dtype, const StartArgs& a, GroupPtrs g, int count, cudaStream_t s);
+void launch_gather_start_g(int dtype, const StartArgs& a, GroupPtrs g, int count, cudaStream_t s);
+void launch_reduce_g(int tcsize, const ReduceArgs& a, GroupPtrs g, int count, cudaStream_t s);
+void launch_finish_g(const FinishArgs& a, int smem, GroupPtrs g, int count, cudaStream_t s);
+void launch_finalize_g(int tcsize, GroupPtrs g, int count, int p, int n, int m, int form, cudaStream_t s);
+void launch_group_cond(GroupPtrs g, int count, cudaGraphConditionalHandle h, cudaStream_t s);
+
 }  // namespace gpspca

@@ -17,6 +17,7 @@
 #include <cmath>
 #include <condition_variable>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <deque>
@@ -45,6 +46,7 @@ const void* sweep_kernel_f32_nrm_full(int mg, int nch, int fw);
 const void* sweep_kernel_f64_nrm(int mg, int nch);
 const void* sweep_kernel_bf16_nrm(int mg, int nch);
 const void* sweep_kernel_fp8_nrm(int mg, int nch);
+const void* sweep_kernel_grouped_su(int dtype, int nch);
 
 // ---------------------------------------------------------------- errors
 
@@ -565,7 +567,10 @@ static void release_workspace(Slot* s) {
     release(s, b);
 }
 
-static int slot_init(Slot* s, int device, cudaStream_t user_stream, Budget* budget, TuneTable* tune) {
+// graphs = false: a member of a group (its solve launched by the group's
+// graph), so no capture streams.
+static int slot_init(Slot* s, int device, cudaStream_t user_stream, Budget* budget, TuneTable* tune,
+                     bool graphs = true) {
   s->device = device;
   s->budget = budget;
   s->tune = tune;
@@ -575,8 +580,10 @@ static int slot_init(Slot* s, int device, cudaStream_t user_stream, Budget* budg
     GP_CUDA(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
     s->own_stream = true;
   }
-  GP_CUDA(cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking));
-  GP_CUDA(cudaStreamCreateWithFlags(&s->cap2, cudaStreamNonBlocking));
+  if (graphs) {
+    GP_CUDA(cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking));
+    GP_CUDA(cudaStreamCreateWithFlags(&s->cap2, cudaStreamNonBlocking));
+  }
   GP_CUDA(cudaMalloc(&s->io_dev, sizeof(IO)));
   GP_CUDA(cudaMalloc(&s->st_dev, sizeof(State)));
   GP_CUDA(cudaMallocHost(&s->io_host, sizeof(IO)));
@@ -630,9 +637,11 @@ static bool first_sweep_from_ritz(const Plan& pl) { return pl.tc && pl.pca && pl
 
 // Start of the solve: norms, gamma, the start directions and their
 // projection.  Block forms without a caller start then take kPowerSteps
-// power steps (A A^T Q, projected) and a Rayleigh-Ritz rotation.
+// power steps (A A^T Q, projected) and a Rayleigh-Ritz rotation; on the
+// tensor cores the first sweep follows here (first_sweep), its T formed
+// from the rotation step's.
 static cudaError_t launch_prologue(const Plan& pl, Slot* s, cudaStream_t cs, cudaGraphConditionalHandle h, bool pca,
-                                   int use_cond = 1) {
+                                   int use_cond = 1, bool first_sweep = true) {
   if (pl.tc && pl.tc_convert)  // bf16 planes of a float / fp8 A for the tensor cores
     launch_tc_convert(pl.dtype, s->io_dev, pl.p, pl.n, pl.ld, pl.p_pad, cs);
   if (pl.tc_sparse) {  // no column is flagged active before the first threshold sweep
@@ -682,7 +691,7 @@ static cudaError_t launch_prologue(const Plan& pl, Slot* s, cudaStream_t cs, cud
     launch_finish(fr, pl.finish_smem, cs);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // the first sweep, its T from the kept A^T Q and the rotation
-    if (first_sweep_from_ritz(pl)) return launch_body(pl, s, cs, h, use_cond, 1);
+    if (first_sweep && first_sweep_from_ritz(pl)) return launch_body(pl, s, cs, h, use_cond, 1);
     return cudaSuccess;
   }
   if ((e = launch_sweeps(pl, s, cs, 1)) != cudaSuccess) return e;
@@ -748,7 +757,12 @@ static cudaError_t launch_epilogue(const Plan& pl, Slot* s, cudaStream_t cs) {
   return cudaGetLastError();
 }
 
-static int build_graph(const Plan& pl, Slot* s, Slot::GraphEntry* out) {
+// A graph of the start (pro), a conditional WHILE node over the loop body
+// (body; the condition set by its kernels) and the end (epi), captured on
+// the streams cap (outer) and cap2 (body).
+template <typename Pro, typename Body, typename Epi>
+static int capture_loop_graph(cudaStream_t cap, cudaStream_t cap2, Pro pro, Body body, Epi epi,
+                              Slot::GraphEntry* out) {
   cudaGraph_t g = nullptr;
   GP_CUDA(cudaGraphCreate(&g, 0));
   bool outer = false, inner = false;
@@ -756,8 +770,8 @@ static int build_graph(const Plan& pl, Slot* s, Slot::GraphEntry* out) {
   // on any failure: end the open captures (so the streams leave capture
   // mode), drop the partial graph and report the first error
   auto abort_with = [&](cudaError_t e, const char* what) {
-    if (inner) cudaStreamEndCapture(s->cap2, &tmp);
-    if (outer) cudaStreamEndCapture(s->cap, &tmp);
+    if (inner) cudaStreamEndCapture(cap2, &tmp);
+    if (outer) cudaStreamEndCapture(cap, &tmp);
     cudaGetLastError();
     cudaGraphDestroy(g);
     return fail(GPSPCA_ECUDA, "graph build (%s): %s", what, cudaGetErrorString(e));
@@ -765,14 +779,14 @@ static int build_graph(const Plan& pl, Slot* s, Slot::GraphEntry* out) {
   cudaGraphConditionalHandle h;
   cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
   if (e != cudaSuccess) return abort_with(e, "conditional handle");
-  if ((e = cudaStreamBeginCaptureToGraph(s->cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)))
+  if ((e = cudaStreamBeginCaptureToGraph(cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)))
     return abort_with(e, "begin capture");
   outer = true;
-  if ((e = launch_prologue(pl, s, s->cap, h, pl.pca != 0))) return abort_with(e, "start kernels");
+  if ((e = pro(cap, h))) return abort_with(e, "start kernels");
   cudaStreamCaptureStatus cst;
   const cudaGraphNode_t* deps = nullptr;
   size_t ndeps = 0;
-  if ((e = cudaStreamGetCaptureInfo(s->cap, &cst, nullptr, nullptr, &deps, nullptr, &ndeps)))
+  if ((e = cudaStreamGetCaptureInfo(cap, &cst, nullptr, nullptr, &deps, nullptr, &ndeps)))
     return abort_with(e, "capture info");
   cudaGraphNodeParams cp = {};
   cp.type = cudaGraphNodeTypeConditional;
@@ -781,23 +795,31 @@ static int build_graph(const Plan& pl, Slot* s, Slot::GraphEntry* out) {
   cp.conditional.size = 1;
   cudaGraphNode_t cnode;
   if ((e = cudaGraphAddNode(&cnode, g, deps, nullptr, ndeps, &cp))) return abort_with(e, "while node");
-  cudaGraph_t body = cp.conditional.phGraph_out[0];
-  if ((e = cudaStreamUpdateCaptureDependencies(s->cap, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies)))
+  cudaGraph_t bodyg = cp.conditional.phGraph_out[0];
+  if ((e = cudaStreamUpdateCaptureDependencies(cap, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies)))
     return abort_with(e, "capture dependencies");
-  if ((e = cudaStreamBeginCaptureToGraph(s->cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)))
+  if ((e = cudaStreamBeginCaptureToGraph(cap2, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)))
     return abort_with(e, "begin body capture");
   inner = true;
-  if ((e = launch_body(pl, s, s->cap2, h))) return abort_with(e, "loop body kernels");
+  if ((e = body(cap2, h))) return abort_with(e, "loop body kernels");
   inner = false;
-  if ((e = cudaStreamEndCapture(s->cap2, &tmp))) return abort_with(e, "end body capture");
-  if ((e = launch_epilogue(pl, s, s->cap))) return abort_with(e, "loadings kernel");
+  if ((e = cudaStreamEndCapture(cap2, &tmp))) return abort_with(e, "end body capture");
+  if ((e = epi(cap))) return abort_with(e, "loadings kernel");
   outer = false;
-  if ((e = cudaStreamEndCapture(s->cap, &tmp))) return abort_with(e, "end capture");
+  if ((e = cudaStreamEndCapture(cap, &tmp))) return abort_with(e, "end capture");
   cudaGraphExec_t exec = nullptr;
   if ((e = cudaGraphInstantiate(&exec, g, 0))) return abort_with(e, "instantiate");
   out->g = g;
   out->exec = exec;
   return GPSPCA_OK;
+}
+
+static int build_graph(const Plan& pl, Slot* s, Slot::GraphEntry* out) {
+  return capture_loop_graph(
+      s->cap, s->cap2,
+      [&](cudaStream_t cs, cudaGraphConditionalHandle h) { return launch_prologue(pl, s, cs, h, pl.pca != 0); },
+      [&](cudaStream_t cs, cudaGraphConditionalHandle h) { return launch_body(pl, s, cs, h); },
+      [&](cudaStream_t cs) { return launch_epilogue(pl, s, cs); }, out);
 }
 
 static int get_graph(const Plan& pl, Slot* s, cudaGraphExec_t* exec) {
@@ -884,8 +906,11 @@ static int solve_empty(Slot* s, const Request& r) {
 // cand >= 0: candidate layout `cand` of the autotuner's list (*ncand its
 // length); cand < 0: the tuned layout of this shape if the context has one,
 // else the planner's default.  *shape (if given): the shape's tuning key.
+// fixed: a plan made for the same shape and storage (a group's members
+// share their first member's), used as it is.
 static int prepare_solve(Slot* s, const Request& r, int nsm, bool scratch_out, Plan* plan, bool* empty,
-                         int cand = -1, int* ncand = nullptr, std::string* shape = nullptr) {
+                         int cand = -1, int* ncand = nullptr, std::string* shape = nullptr,
+                         const Plan* fixed = nullptr) {
   *empty = false;
   int rc = validate(r);
   if (rc != GPSPCA_OK) return rc;
@@ -926,7 +951,11 @@ static int prepare_solve(Slot* s, const Request& r, int nsm, bool scratch_out, P
   if (shape) *shape = shape_key;
   std::string tuned;
   bool picked = false;
-  if (cand < 0 && s->tune) {
+  if (fixed) {
+    pl = *fixed;
+    picked = true;
+  }
+  if (!picked && cand < 0 && s->tune) {
     std::lock_guard<std::mutex> lk(s->tune->mu);
     auto it = s->tune->best.find(shape_key);
     if (it != s->tune->best.end()) {
@@ -1060,13 +1089,41 @@ static int prepare_solve(Slot* s, const Request& r, int nsm, bool scratch_out, P
 
 // Enqueue one solve on the slot's stream (asynchronous).  *empty is set when
 // nothing was launched.
+// After a solve's kernels on stream cs: host outputs copied from the slot's
+// staging, the state read back, the slot's done event recorded.
+static int solve_tail(Slot* s, const Request& r, cudaStream_t cs) {
+  const DInfo d = dinfo(r.A.dtype);
+  const int64_t p = r.A.p, n = r.A.n;
+  const int m = r.m;
+  if (r.out.location == GPSPCA_HOST) {
+    const size_t nw = (n + 31) / 32;
+    GP_CUDA(cudaMemcpyAsync(r.out.X, s->s_X.p, static_cast<size_t>(d.tcsize) * p * m, cudaMemcpyDeviceToHost, cs));
+    GP_CUDA(cudaMemcpyAsync(r.out.Z, s->s_Z.p, static_cast<size_t>(d.tcsize) * n * m, cudaMemcpyDeviceToHost, cs));
+    if (r.out.support)
+      GP_CUDA(cudaMemcpyAsync(r.out.support, s->s_sup.p, sizeof(uint32_t) * nw * m, cudaMemcpyDeviceToHost, cs));
+    GP_CUDA(cudaMemcpyAsync(r.out.objective, s->s_obj.p, sizeof(double) * m, cudaMemcpyDeviceToHost, cs));
+    GP_CUDA(cudaMemcpyAsync(r.out.iters, s->s_it.p, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, cs));
+    GP_CUDA(cudaMemcpyAsync(r.out.status, s->s_stat.p, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, cs));
+    if (r.out.gamma_abs)
+      GP_CUDA(cudaMemcpyAsync(r.out.gamma_abs, s->s_gam.p, sizeof(double) * m, cudaMemcpyDeviceToHost, cs));
+  }
+  if (r.flags & GPSPCA_INJECT_TIMEOUT) {
+    // the error word as a timed-out wait leaves it; the next solve's reset clears it
+    static const int32_t kTimedOut = kErrTimeout;
+    GP_CUDA(cudaMemcpyAsync(&s->st_dev->error, &kTimedOut, sizeof(int32_t), cudaMemcpyHostToDevice, cs));
+  }
+  // the host reads the state's leading words only (counter, active count,
+  // error bits, degenerate flag): the rest stays on the device
+  static_assert(offsetof(State, active) == 4 * sizeof(int32_t), "the state's host-read words lead it");
+  GP_CUDA(cudaMemcpyAsync(s->st_host, s->st_dev, offsetof(State, active), cudaMemcpyDeviceToHost, cs));
+  GP_CUDA(cudaEventRecord(s->done, cs));
+  return GPSPCA_OK;
+}
+
 static int launch_solve(Slot* s, const Request& r, int nsm, bool* empty) {
   Plan pl;
   int rc = prepare_solve(s, r, nsm, false, &pl, empty);
   if (rc != GPSPCA_OK || *empty) return rc;
-  const DInfo d = dinfo(r.A.dtype);
-  const int64_t p = r.A.p, n = r.A.n;
-  const int m = r.m;
   if (r.flags & GPSPCA_EAGER) {
     // the graph's kernels, launched one by one; the host reads the active
     // count after each finish step in place of the WHILE node
@@ -1084,26 +1141,7 @@ static int launch_solve(Slot* s, const Request& r, int nsm, bool* empty) {
     if ((rc = get_graph(pl, s, &exec))) return rc;
     GP_CUDA(cudaGraphLaunch(exec, s->stream));
   }
-  if (r.out.location == GPSPCA_HOST) {
-    const size_t nw = (n + 31) / 32;
-    GP_CUDA(cudaMemcpyAsync(r.out.X, s->s_X.p, static_cast<size_t>(d.tcsize) * p * m, cudaMemcpyDeviceToHost, s->stream));
-    GP_CUDA(cudaMemcpyAsync(r.out.Z, s->s_Z.p, static_cast<size_t>(d.tcsize) * n * m, cudaMemcpyDeviceToHost, s->stream));
-    if (r.out.support)
-      GP_CUDA(cudaMemcpyAsync(r.out.support, s->s_sup.p, sizeof(uint32_t) * nw * m, cudaMemcpyDeviceToHost, s->stream));
-    GP_CUDA(cudaMemcpyAsync(r.out.objective, s->s_obj.p, sizeof(double) * m, cudaMemcpyDeviceToHost, s->stream));
-    GP_CUDA(cudaMemcpyAsync(r.out.iters, s->s_it.p, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, s->stream));
-    GP_CUDA(cudaMemcpyAsync(r.out.status, s->s_stat.p, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, s->stream));
-    if (r.out.gamma_abs)
-      GP_CUDA(cudaMemcpyAsync(r.out.gamma_abs, s->s_gam.p, sizeof(double) * m, cudaMemcpyDeviceToHost, s->stream));
-  }
-  if (r.flags & GPSPCA_INJECT_TIMEOUT) {
-    // the error word as a timed-out wait leaves it; the next solve's reset clears it
-    static const int32_t kTimedOut = kErrTimeout;
-    GP_CUDA(cudaMemcpyAsync(&s->st_dev->error, &kTimedOut, sizeof(int32_t), cudaMemcpyHostToDevice, s->stream));
-  }
-  GP_CUDA(cudaMemcpyAsync(s->st_host, s->st_dev, sizeof(State), cudaMemcpyDeviceToHost, s->stream));
-  GP_CUDA(cudaEventRecord(s->done, s->stream));
-  return GPSPCA_OK;
+  return solve_tail(s, r, s->stream);
 }
 
 // Result code of a finished solve from its device state.
@@ -1201,6 +1239,15 @@ struct gpspca_ctx {
   std::vector<std::unique_ptr<Slot>> batch_slots;
   cudaEvent_t batch_start = nullptr;
   std::vector<DevBuf> batch_stage;  // host matrices shared by several requests, copied once
+  // groups of same-shape single-unit solves (gpspca_solve_batch), under
+  // solve_mu: member slots, the group's stream and capture streams, the
+  // device arrays of the members' IO and State pointers, the group graphs
+  std::vector<std::unique_ptr<Slot>> group_slots;
+  cudaStream_t group_stream = nullptr, group_cap = nullptr, group_cap2 = nullptr;
+  cudaEvent_t group_done = nullptr;
+  void** group_ptrs = nullptr;       // device: kGroupMax IO pointers, then kGroupMax State pointers
+  void** group_ptrs_host = nullptr;  // pinned
+  std::unordered_map<std::string, Slot::GraphEntry> group_graphs;
   // uploads (gpspca_upload), under up_mu: copies on their own stream, each
   // destination with the event its copy recorded, oldest first
   std::mutex up_mu;
@@ -1345,6 +1392,176 @@ int gpspca_create(gpspca_ctx** out, int device, size_t hbm_budget_bytes, void* c
 
 static constexpr int kBatchSlots = 8;
 
+// ---------------------------------------------------------------- groups
+//
+// Same-shape single-unit requests of a batch (one component; same storage
+// type, form, shape, column stride and alignment; a CUDA-core plan of one
+// pass in clusters of one CTA) run as a group: every step of the solve is
+// one launch for all of them, the grid's z dimension the member, and the
+// loop one WHILE node that continues while any member is active.  Each
+// member keeps its own workspace, state, stopping test and outputs and runs
+// the kernel bodies of a solo solve.  Its sweep is planned for about
+// kGroupCols columns per CTA instead of one column slab per SM (the group
+// fills the GPU, not the member), so its partial sums are grouped
+// differently from a solo solve's: the results agree with it to float
+// rounding and do not depend on the group's size or other members.  Many
+// small solves then pay one launch per step, not one per solve per step.
+
+static constexpr int kGroupMin = 4;      // fewer same-shape requests run as ordinary solves
+static constexpr int kGroupMax = 256;    // members per group launch
+static constexpr int64_t kGroupCols = 128;  // columns per CTA of a member's sweep
+
+// The group a request may join ("" for none).
+static std::string group_bucket(const Request& r) {
+  if (r.form >= GPSPCA_BL1 || r.m != 1 || (r.flags & (GPSPCA_EAGER | GPSPCA_INJECT_TIMEOUT)) || r.A.p <= 0 ||
+      r.A.n <= 0 || r.A.location != GPSPCA_DEVICE)
+    return "";
+  const DInfo d = dinfo(r.A.dtype);
+  const bool fast = (reinterpret_cast<uintptr_t>(r.A.data) % 16 == 0) && ((r.A.ld * d.esize) % 16 == 0);
+  char b[192];
+  snprintf(b, sizeof(b), "%d/%d/%lld/%lld/%lld/%d/%u", static_cast<int>(r.A.dtype), static_cast<int>(r.form),
+           (long long)r.A.p, (long long)r.A.n, (long long)r.A.ld, fast ? 1 : 0, r.flags & GPSPCA_NO_TENSOR_CORES);
+  return b;
+}
+
+static bool group_plan_ok(const Plan& pl) {
+  return !pl.tc && !pl.pca && !pl.norms_in_sweep && pl.C == 1 && pl.passes.size() == 1 && pl.passes[0].mg == 1 &&
+         pl.passes[0].mgv == 1 && sweep_kernel_grouped_su(pl.dtype, pl.passes[0].nch) != nullptr;
+}
+
+// The start of a group's solves (as launch_prologue for a single-unit form).
+static cudaError_t group_start(const Plan& pl, GroupPtrs g, int count, cudaStream_t cs,
+                               cudaGraphConditionalHandle h) {
+  launch_reset_g(g, count, pl.m, pl.form, cs);
+  launch_colnorm_g(pl.dtype, g, count, pl.ld, pl.p, pl.n, pl.fast, cs);
+  const StartArgs sa{nullptr, nullptr, pl.ld, pl.p, pl.n, pl.m, pl.form};
+  launch_select_start_g(pl.dtype, sa, g, count, cs);
+  launch_gather_start_g(pl.dtype, sa, g, count, cs);
+  const int gram_pairs = pl.full_gram ? pl.m * (pl.m + 1) / 2 : pl.m;
+  const ReduceArgs ra{nullptr, nullptr, 1, pl.m, pl.p, pl.full_gram, gram_pairs, 1, 0, 0, pl.n, pl.form, pl.nred, 0};
+  launch_reduce_g(pl.tcsize, ra, g, count, cs);
+  const FinishArgs fa{nullptr, nullptr, pl.ncl, pl.nred, gram_pairs, pl.m, pl.form, kFinishPolar, 1, h, 0};
+  launch_finish_g(fa, pl.finish_smem, g, count, cs);
+  launch_group_cond(g, count, h, cs);
+  return cudaGetLastError();
+}
+
+// One sweep of a group (as launch_body for a single-unit form).
+static cudaError_t group_sweep(const Plan& pl, GroupPtrs g, int count, cudaStream_t cs,
+                               cudaGraphConditionalHandle h) {
+  const Pass& q = pl.passes[0];
+  SweepArgs a{nullptr, nullptr, pl.ld, pl.p, pl.n, pl.m, pl.form, q.j0, q.mgv, pl.ps, q.W, q.S, pl.cols_per_cl,
+              pl.fast, 0};
+  void* args[] = {&a, &g};
+  cudaError_t e = cudaLaunchKernel(sweep_kernel_grouped_su(pl.dtype, q.nch), dim3(pl.ncl, 1, count),
+                                   dim3(q.threads), args, static_cast<size_t>(q.smem), cs);
+  if (e != cudaSuccess) return e;
+  const int gram_pairs = pl.full_gram ? pl.m * (pl.m + 1) / 2 : pl.m;
+  const ReduceArgs ra{nullptr, nullptr, pl.ncl, pl.m, pl.p, pl.full_gram, gram_pairs, 0, 0, 1, pl.n, pl.form,
+                      pl.nred, pl.nobj};
+  launch_reduce_g(pl.tcsize, ra, g, count, cs);
+  const FinishArgs fa{nullptr, nullptr, pl.nobj, pl.nred, gram_pairs, pl.m, pl.form, kFinishIterate, 0, h, 0};
+  launch_finish_g(fa, pl.finish_smem, g, count, cs);
+  launch_group_cond(g, count, h, cs);
+  return cudaGetLastError();
+}
+
+static int group_init(gpspca_ctx* ctx) {
+  if (ctx->group_stream) return GPSPCA_OK;
+  GP_CUDA(cudaStreamCreateWithFlags(&ctx->group_stream, cudaStreamNonBlocking));
+  GP_CUDA(cudaStreamCreateWithFlags(&ctx->group_cap, cudaStreamNonBlocking));
+  GP_CUDA(cudaStreamCreateWithFlags(&ctx->group_cap2, cudaStreamNonBlocking));
+  GP_CUDA(cudaEventCreateWithFlags(&ctx->group_done, cudaEventDisableTiming));
+  GP_CUDA(cudaMalloc(&ctx->group_ptrs, 2 * kGroupMax * sizeof(void*)));
+  GP_CUDA(cudaMallocHost(&ctx->group_ptrs_host, 2 * kGroupMax * sizeof(void*)));
+  return GPSPCA_OK;
+}
+
+// Runs requests R[idx[k]] as one group, after the work on the context's
+// stream recorded by ctx->batch_start, and collects each result into
+// rcs[idx[k]].  *ran = false (nothing launched) when their plan cannot run
+// as a group: the caller solves them one by one.
+static int run_group(gpspca_ctx* ctx, const std::vector<Request>& R, const std::vector<int>& idx, int32_t* rcs,
+                     bool* ran) {
+  *ran = false;
+  int rc = group_init(ctx);
+  if (rc != GPSPCA_OK) return rc;
+  const int count = static_cast<int>(idx.size());
+  while (static_cast<int>(ctx->group_slots.size()) < count) {
+    auto sl = std::make_unique<Slot>();
+    rc = slot_init(sl.get(), ctx->device, ctx->group_stream, &ctx->budget, &ctx->tune, false);
+    if (rc != GPSPCA_OK) {
+      slot_free(sl.get());
+      return rc;
+    }
+    ctx->group_slots.push_back(std::move(sl));
+  }
+  cudaStream_t gs = ctx->group_stream;
+  GP_CUDA(cudaStreamWaitEvent(gs, ctx->batch_start, 0));
+  // column slabs of a member's sweep: one per kGroupCols columns
+  const int nsm_g = static_cast<int>(std::max<int64_t>(1, (R[idx[0]].A.n + kGroupCols - 1) / kGroupCols));
+  Plan pl0;
+  std::vector<int> member;  // indices into idx of the members that prepared
+  for (int k = 0; k < count; ++k) {
+    Plan pl;
+    bool empty = false;
+    const int r = prepare_solve(ctx->group_slots[k].get(), R[idx[k]], nsm_g, false, &pl, &empty, -1, nullptr,
+                                nullptr, member.empty() ? nullptr : &pl0);
+    if (r != GPSPCA_OK || empty) {
+      rcs[idx[k]] = r;
+      continue;
+    }
+    if (member.empty()) {
+      if (!group_plan_ok(pl)) return GPSPCA_OK;  // not a group plan: solved one by one
+      pl0 = pl;
+    } else if (pl.key() != pl0.key()) {
+      return GPSPCA_OK;
+    }
+    member.push_back(k);
+  }
+  *ran = true;
+  const int nm = static_cast<int>(member.size());
+  if (nm == 0) return GPSPCA_OK;
+  for (int u = 0; u < nm; ++u) {
+    ctx->group_ptrs_host[u] = ctx->group_slots[member[u]]->io_dev;
+    ctx->group_ptrs_host[kGroupMax + u] = ctx->group_slots[member[u]]->st_dev;
+  }
+  GP_CUDA(cudaMemcpyAsync(ctx->group_ptrs, ctx->group_ptrs_host, 2 * kGroupMax * sizeof(void*),
+                          cudaMemcpyHostToDevice, gs));
+  const GroupPtrs g{reinterpret_cast<const IO* const*>(ctx->group_ptrs),
+                    reinterpret_cast<State* const*>(ctx->group_ptrs + kGroupMax)};
+  kattr(sweep_kernel_grouped_su(pl0.dtype, pl0.passes[0].nch));  // its dynamic shared memory limit
+  const std::string key = pl0.key() + "|group" + std::to_string(nm);
+  auto it = ctx->group_graphs.find(key);
+  if (it == ctx->group_graphs.end()) {
+    Slot::GraphEntry ge;
+    rc = capture_loop_graph(
+        ctx->group_cap, ctx->group_cap2,
+        [&](cudaStream_t cs, cudaGraphConditionalHandle h) { return group_start(pl0, g, nm, cs, h); },
+        [&](cudaStream_t cs, cudaGraphConditionalHandle h) { return group_sweep(pl0, g, nm, cs, h); },
+        [&](cudaStream_t cs) {
+          launch_finalize_g(pl0.tcsize, g, nm, pl0.p, pl0.n, pl0.m, pl0.form, cs);
+          return cudaGetLastError();
+        },
+        &ge);
+    if (rc != GPSPCA_OK) return rc;
+    if (ctx->group_graphs.size() >= 64) {  // bound the cache
+      for (auto& kv : ctx->group_graphs) {
+        cudaGraphExecDestroy(kv.second.exec);
+        cudaGraphDestroy(kv.second.g);
+      }
+      ctx->group_graphs.clear();
+    }
+    it = ctx->group_graphs.emplace(key, ge).first;
+  }
+  GP_CUDA(cudaGraphLaunch(it->second.exec, gs));
+  for (int u = 0; u < nm; ++u)
+    if ((rc = solve_tail(ctx->group_slots[member[u]].get(), R[idx[member[u]]], gs)) != GPSPCA_OK) return rc;
+  GP_CUDA(cudaEventRecord(ctx->group_done, gs));
+  for (int u = 0; u < nm; ++u) rcs[idx[member[u]]] = solve_result(ctx->group_slots[member[u]].get());
+  return GPSPCA_OK;
+}
+
 int gpspca_solve_batch(gpspca_ctx* ctx, int32_t count, const gpspca_request* reqs, int32_t* rcs) {
   if (!ctx) return fail(GPSPCA_EINVAL, "ctx is NULL");
   if (count < 0 || (count > 0 && (!reqs || !rcs))) return fail(GPSPCA_EINVAL, "bad batch arguments");
@@ -1413,23 +1630,63 @@ int gpspca_solve_batch(gpspca_ctx* ctx, int32_t count, const gpspca_request* req
     if (rc != GPSPCA_OK) return rc;
   }
   GP_CUDA(cudaEventRecord(ctx->batch_start, cs));
+  // kGroupMin or more same-shape single-unit requests: grouped launches
+  std::vector<std::vector<int>> groups;
+  std::vector<char> grouped(static_cast<size_t>(count), 0);
+  {
+    std::map<std::string, std::vector<int>> buckets;
+    for (int i = 0; i < count; ++i) {
+      const std::string b = group_bucket(R[i]);
+      if (!b.empty()) buckets[b].push_back(i);
+    }
+    for (auto& kv : buckets)
+      for (size_t o = 0; o < kv.second.size(); o += kGroupMax) {
+        const size_t e = std::min(kv.second.size(), o + kGroupMax);
+        if (e - o < static_cast<size_t>(kGroupMin)) continue;
+        groups.emplace_back(kv.second.begin() + static_cast<std::ptrdiff_t>(o),
+                            kv.second.begin() + static_cast<std::ptrdiff_t>(e));
+        for (size_t q = o; q < e; ++q) grouped[kv.second[q]] = 1;
+      }
+  }
+  std::vector<int> solo;
+  for (int i = 0; i < count; ++i)
+    if (!grouped[i]) solo.push_back(i);
   std::vector<char> running(static_cast<size_t>(count), 0);
-  auto collect = [&](int i) {
-    rcs[i] = solve_result(ctx->batch_slots[i % kBatchSlots].get());
-    running[i] = 0;
+  auto collect = [&](int k) {  // the solo solve at position k
+    rcs[solo[k]] = solve_result(ctx->batch_slots[k % kBatchSlots].get());
+    running[solo[k]] = 0;
   };
-  for (int i = 0; i < count; ++i) {
-    Slot* s = ctx->batch_slots[i % kBatchSlots].get();
-    if (i >= kBatchSlots && running[i - kBatchSlots]) collect(i - kBatchSlots);  // the slot's previous solve
+  for (int k = 0; k < static_cast<int>(solo.size()); ++k) {
+    const int i = solo[k];
+    Slot* s = ctx->batch_slots[k % kBatchSlots].get();
+    if (k >= kBatchSlots && running[solo[k - kBatchSlots]]) collect(k - kBatchSlots);  // the slot's previous solve
     GP_CUDA(cudaStreamWaitEvent(s->stream, ctx->batch_start, 0));
     bool empty = false;
     const int rc = launch_solve(s, R[i], ctx->nsm, &empty);
     rcs[i] = rc;
     running[i] = (rc == GPSPCA_OK && !empty) ? 1 : 0;
   }
+  // the groups, one after the other on the group stream, while the solo
+  // solves run; a group whose plan cannot run grouped is solved one by one
+  // on the context's stream
+  for (const std::vector<int>& gv : groups) {
+    bool ran = false;
+    const int rc = run_group(ctx, R, gv, rcs, &ran);
+    if (rc != GPSPCA_OK) {
+      for (int i : gv) rcs[i] = rc;
+      continue;
+    }
+    if (ran) continue;
+    for (int i : gv) {
+      bool empty = false;
+      rcs[i] = launch_solve(&ctx->sync_slot, R[i], ctx->nsm, &empty);
+      if (rcs[i] == GPSPCA_OK && !empty) rcs[i] = solve_result(&ctx->sync_slot);
+    }
+  }
+  if (!groups.empty() && ctx->group_done) GP_CUDA(cudaStreamWaitEvent(cs, ctx->group_done, 0));
   for (int k = 0; k < nb; ++k) GP_CUDA(cudaStreamWaitEvent(cs, ctx->batch_slots[k]->done, 0));
-  for (int i = 0; i < count; ++i)
-    if (running[i]) collect(i);
+  for (int k = 0; k < static_cast<int>(solo.size()); ++k)
+    if (running[solo[k]]) collect(k);
   for (int i = 0; i < count; ++i)
     if (rcs[i] != GPSPCA_OK && rcs[i] != GPSPCA_EDEGENERATE) return fail(rcs[i], "batch request %d failed", i);
   return GPSPCA_OK;
@@ -1699,7 +1956,8 @@ int gpspca_time_sweep(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form form,
   if (empty) return fail(GPSPCA_EINVAL, "empty matrix");
   const int t_only = (flags & GPSPCA_TIME_T_PASS) ? 1 : 0;
   if (t_only && !pl.tc) return fail(GPSPCA_EINVAL, "GPSPCA_TIME_T_PASS: this problem runs the CUDA-core sweep");
-  GP_CUDA(launch_prologue(pl, s, s->stream, cudaGraphConditionalHandle{}, pl.pca != 0, 0));
+  // the start alone (the sweeps timed are the loop's; its first one stays out)
+  GP_CUDA(launch_prologue(pl, s, s->stream, cudaGraphConditionalHandle{}, pl.pca != 0, 0, false));
   cudaEvent_t e0, e1;
   GP_CUDA(cudaEventCreate(&e0));
   GP_CUDA(cudaEventCreate(&e1));
@@ -1768,7 +2026,8 @@ int gpspca_plan_launches(gpspca_ctx* ctx, const gpspca_matrix* A, gpspca_form fo
 // Time one prepared plan's sweep: start and projection as a solve does,
 // one warm-up sweep, then `reps` sweeps between CUDA events.
 static int time_plan(Slot* s, const Plan& pl, int reps, double* ms_per_sweep) {
-  GP_CUDA(launch_prologue(pl, s, s->stream, cudaGraphConditionalHandle{}, pl.pca != 0, 0));
+  // the start alone (the sweeps timed are the loop's; its first one stays out)
+  GP_CUDA(launch_prologue(pl, s, s->stream, cudaGraphConditionalHandle{}, pl.pca != 0, 0, false));
   cudaEvent_t e0, e1;
   GP_CUDA(cudaEventCreate(&e0));
   GP_CUDA(cudaEventCreate(&e1));
@@ -1960,6 +2219,16 @@ int gpspca_destroy(gpspca_ctx* ctx) {
   cudaSetDevice(ctx->device);
   for (auto& s : ctx->serve_slots) slot_free(s.get());
   for (auto& s : ctx->batch_slots) slot_free(s.get());
+  for (auto& s : ctx->group_slots) slot_free(s.get());
+  for (auto& kv : ctx->group_graphs) {
+    cudaGraphExecDestroy(kv.second.exec);
+    cudaGraphDestroy(kv.second.g);
+  }
+  if (ctx->group_done) cudaEventDestroy(ctx->group_done);
+  if (ctx->group_ptrs) cudaFree(ctx->group_ptrs);
+  if (ctx->group_ptrs_host) cudaFreeHost(ctx->group_ptrs_host);
+  for (cudaStream_t c : {ctx->group_cap2, ctx->group_cap, ctx->group_stream})
+    if (c) cudaStreamDestroy(c);
   if (ctx->batch_start) cudaEventDestroy(ctx->batch_start);
   if (ctx->copy_stream) cudaStreamSynchronize(ctx->copy_stream);
   for (gpspca_ctx::Upload& u : ctx->uploads) cudaEventDestroy(u.done);

@@ -80,6 +80,13 @@ struct State {
   int32_t start_cols[kMaxM];
 };
 
+// A group of same-shape solves launched together (grid z = instance): the
+// device arrays of the instances' IO and State.
+struct GroupPtrs {
+  const IO* const* io;
+  State* const* st;
+};
+
 // Launch geometry of the fused sweep (host-chosen).
 struct SweepGeom {
   int C;       // cluster size: CTAs splitting the rows of a column slab

@@ -251,7 +251,7 @@ struct SweepCfg {
 // slots hold zeros or earlier columns of A (the ring starts zeroed) and get
 // g = 0.  FW = 0: any width up to WB, each slot tested.
 template <typename TA, int MG, int NCH, bool NRM = false, int FW = 0>
-__global__ void __launch_bounds__(SweepCfg<TA, MG, NCH, NRM, FW>::MAXT, 1) sweep_kernel(const SweepArgs a) {
+__device__ __forceinline__ void sweep_body(const SweepArgs& a) {
   using Cfg = SweepCfg<TA, MG, NCH, NRM, FW>;
   constexpr int SL = Cfg::SL;
   using TC = typename Cfg::TC;
@@ -648,6 +648,29 @@ __global__ void __launch_bounds__(SweepCfg<TA, MG, NCH, NRM, FW>::MAXT, 1) sweep
   }
   if (timed_out) atomicOr(&st->error, static_cast<int>(kErrTimeout));
   if (C > 1) cluster_sync_all();  // no CTA leaves while a peer may read its shared memory
+}
+
+template <typename TA, int MG, int NCH, bool NRM = false, int FW = 0>
+__global__ void __launch_bounds__(SweepCfg<TA, MG, NCH, NRM, FW>::MAXT, 1) sweep_kernel(const SweepArgs a) {
+  sweep_body<TA, MG, NCH, NRM, FW>(a);
+}
+
+// The sweep of instance blockIdx.z of a group of same-shape solves (clusters
+// of one CTA; the instance's IO and State from the group's arrays).
+template <typename TA, int MG, int NCH>
+__global__ void __launch_bounds__(SweepCfg<TA, MG, NCH>::MAXT, 1) sweep_kernel_grouped(SweepArgs a, GroupPtrs g) {
+  a.io = g.io[blockIdx.z];
+  a.st = g.st[blockIdx.z];
+  sweep_body<TA, MG, NCH>(a);
+}
+
+template <typename TA, int MG, int NCH>
+const void* sweep_kernel_grouped_ptr() {
+  if constexpr (SweepCfg<TA, MG, NCH>::kBuilt) {
+    return reinterpret_cast<const void*>(&sweep_kernel_grouped<TA, MG, NCH>);
+  } else {
+    return nullptr;
+  }
 }
 
 template <typename TA, int MG, int NCH, bool NRM = false, int FW = 0>

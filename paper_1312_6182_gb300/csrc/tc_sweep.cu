@@ -914,17 +914,20 @@ __device__ __forceinline__ void tc_convert_row(const unsigned char* f0, int frow
 }
 
 // The same for the gathered columns of the Y pass: col points at the 64
-// rows of one MN atom of one column (256 contiguous bytes, no swizzle); the
-// four 8-row groups are taken in an order rotated by the column, so that the
-// lanes of a warp (consecutive columns, 512 bytes apart) read four different
-// 32-byte pieces at a time.
-__device__ __forceinline__ void tc_convert_row_plain(const unsigned char* col, int rot, unsigned char* plane0,
-                                                     int prow, int g0) {
+// rows of one MN atom of column i of the chunk (256 contiguous bytes, no
+// swizzle).  At step gg the thread takes 8-row group (gg xor (i >> 1)) mod 4
+// of its four, and that group's two 16-byte halves (i & 1) first: for the
+// eight lanes of one 16-byte shared-memory phase (columns i .. i+7, 512
+// bytes apart) both the loads and the stores into the swizzled plane rows
+// (chunk g xor (i mod 8)) then touch eight different 16-byte bank slots.
+__device__ __forceinline__ void tc_convert_row_plain(const unsigned char* col, int i, unsigned char* plane0, int g0) {
+  const int hf = i & 1;
 #pragma unroll
   for (int gg = 0; gg < 4; ++gg) {
-    const int g = g0 + ((gg + rot) & 3);
-    const uint4 v0 = *reinterpret_cast<const uint4*>(col + g * 32);
-    const uint4 v1 = *reinterpret_cast<const uint4*>(col + g * 32 + 16);
+    const int g = g0 + ((gg ^ (i >> 1)) & 3);
+    const uint4 va = *reinterpret_cast<const uint4*>(col + g * 32 + hf * 16);
+    const uint4 vb = *reinterpret_cast<const uint4*>(col + g * 32 + (hf ^ 1) * 16);
+    const uint4 v0 = hf ? vb : va, v1 = hf ? va : vb;
     const uint32_t x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
     uint32_t w[3][4];
 #pragma unroll
@@ -936,7 +939,7 @@ __device__ __forceinline__ void tc_convert_row_plain(const unsigned char* col, i
       w[1][e / 2] = __byte_perm(a1, b1, 0x7632);
       w[2][e / 2] = __byte_perm(a2, b2, 0x7632);
     }
-    const int off = prow * 128 + ((g ^ (prow & 7)) * 16);
+    const int off = i * 128 + ((g ^ (i & 7)) * 16);
 #pragma unroll
     for (int pl = 0; pl < 3; ++pl)
       *reinterpret_cast<uint4*>(plane0 + pl * kTcA + off) = make_uint4(w[pl][0], w[pl][1], w[pl][2], w[pl][3]);
@@ -962,7 +965,7 @@ __device__ __forceinline__ bool tc_convert_chunk(const TcFusedSmem& S, int it, b
   } else {    // atom a = rows 64a..64a+63 of A, row i = column i; float boxes of 32 rows x 64 columns
     const int a = q >> 6, i = q & 63;
     if (plain)  // gathered columns: column i's 128 rows at byte 512 i, not swizzled
-      tc_convert_row_plain(f + i * 512 + a * 256, i, b + a * 8192, i, 4 * h);
+      tc_convert_row_plain(f + i * 512 + a * 256, i, b + a * 8192, 4 * h);
     else
       tc_convert_row(f + (2 * a) * 8192, i, f + (2 * a + 1) * 8192, i, b + a * 8192, i, 4 * h, 4);
   }

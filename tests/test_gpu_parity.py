@@ -788,6 +788,75 @@ def test_batch_equals_solo_solves(ctx):
         ctx.solve_batch([dict(At=items[0]["At"], form="SL1", gamma=[-1.0])])
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_batch_groups_same_shape_solves(ctx, dtype):
+    """Same-shape single-unit requests of a batch (here 40 of 300 x 2000, SL1
+    and SL0, each with its own data, gamma, tolerance and sweep limit) run
+    as groups, one launch per step for all members.  Every member against
+    the oracle at the stated limits (members stop on their own tests); the
+    same requests in two groups of another composition give the same bits;
+    a request of another shape in the batch runs on its own (the bits of its
+    solo solve)."""
+    rng = np.random.default_rng(66)
+    p, n = 300, 2000
+    tdt = torch.float32 if dtype == "f32" else torch.float64
+    items, mats = [], []
+    for i in range(40):
+        At = synth.planted_spike(p, n, 2, [30.0, 15.0], support_frac=0.05, seed=300 + i, dtype=np.float32)
+        mats.append(At)
+        items.append(dict(At=torch.from_numpy(At).to(tdt).cuda(), form="SL1" if i % 2 else "SL0",
+                          gamma=[float(rng.uniform(0.03, 0.15))], gamma_relative=True,
+                          tol=1e-6 if i % 5 else 0.0, maxit=1000 if i % 5 else 3 + i % 4))
+    other = synth.planted_spike(400, 1500, 2, [30.0, 15.0], support_frac=0.05, seed=399, dtype=np.float32)
+    items.append(dict(At=torch.from_numpy(other).to(tdt).cuda(), form="SL1", gamma=[0.05], gamma_relative=True))
+    got = ctx.solve_batch(items)
+    solo_other = ctx.solve(**items[40])
+    assert torch.equal(got[40].Z, solo_other.Z) and torch.equal(got[40].X, solo_other.X)
+    # another composition: the odd members first, in a batch of their own, then the even ones
+    again = {}
+    for half in (list(range(1, 40, 2)), list(range(0, 40, 2))):
+        for i, r in zip(half, ctx.solve_batch([items[i] for i in half])):
+            again[i] = r
+    for i in range(40):
+        assert torch.equal(got[i].Z, again[i].Z) and torch.equal(got[i].X, again[i].X), i
+        assert torch.equal(got[i].objective, again[i].objective) and torch.equal(got[i].iters, again[i].iters), i
+    its = np.array([int(r.iters[0]) for r in got[:40]])
+    assert len(set(its.tolist())) > 1  # the members stopped on their own tests
+    for i in range(40):
+        A = mats[i].astype(np.float64).T
+        form = items[i]["form"]
+        gam = _gammas(A, form, items[i]["gamma"])
+        ref = oracle.gpower(A, form, gam, tol=items[i]["tol"], maxit=items[i]["maxit"])
+        g = gpu_arrays(got[i])
+        if items[i]["tol"] > 0:
+            _converged(form, g, A, gam, None, ref, items[i]["tol"], f"group member {i} {dtype}")
+        else:
+            assert_matches(form, g, ref, oracle.column_norms(A), label=f"group member {i} {dtype}")
+
+
+def test_batch_group_with_a_failing_member(ctx):
+    """A member with a NaN in its matrix reports GPSPCA_ENONFINITE; the other
+    members of its group (host outputs for some of them) give the bits they
+    give in a group without it."""
+    p, n = 256, 1024
+    items = []
+    for i in range(6):
+        At = synth.planted_spike(p, n, 1, [25.0], support_frac=0.05, seed=400 + i, dtype=np.float32)
+        if i == 3:
+            At[17, 5] = np.nan
+        out = binding.alloc_result(1, p, n, "cpu" if i % 2 else "cuda", torch.float32, pin=bool(i % 2))
+        items.append(dict(At=torch.from_numpy(At).cuda(), form="SL1", gamma=[0.08], gamma_relative=True, out=out))
+    with pytest.raises(binding.GpspcaError) as e:
+        ctx.solve_batch(items)
+    assert e.value.code == binding.ENONFINITE
+    good = (0, 1, 2, 4, 5)
+    refs = ctx.solve_batch([{k: v for k, v in items[i].items() if k != "out"} for i in good])
+    for i, ref in zip(good, refs):
+        got = items[i]["out"]
+        assert torch.equal(got.Z.cpu(), ref.Z.cpu()) and torch.equal(got.X.cpu(), ref.X.cpu()), i
+        assert torch.equal(got.objective.cpu(), ref.objective.cpu()), i
+
+
 def test_batch_shares_host_matrix(ctx):
     """Requests of a batch that share one pinned host matrix (the library copies
     it once) give the device batch's bits, with host or device outputs, for
