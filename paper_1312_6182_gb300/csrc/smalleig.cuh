@@ -114,7 +114,7 @@ __device__ __forceinline__ bool jacobi_done(float off, float dg, float off_prev)
   return !(off > 1e-24f * dg) || (off_prev >= 0.0f && off > 0.25f * off_prev && off < 1e-20f * dg);
 }
 
-// Cyclic Jacobi for mm = MM <= 16 on warp 0 alone: every round's index
+// Cyclic Jacobi for mm = MM <= 8 on warp 0 alone: every round's index
 // arithmetic divides by constants, each lane owns (pair, index) slots of the
 // row and column updates (up to four), and the rotation of each pair,
 // computed by lane k, is broadcast by shuffles.  Same rotations, order and
@@ -197,6 +197,92 @@ __device__ void jacobi_small(dd* H, dd* V) {
   }
 }
 
+// The same Jacobi for 8 < MM <= 16 on NSLOT / 32 rounded up warps (2-4):
+// each thread owns one (pair, index) slot of a round's row and column
+// updates, the rotations of the round's pairs (computed by the first HALF
+// threads) pass through shared memory, and named barrier 1 joins the
+// participating warps; the other threads of the CTA return at once.  Same
+// rotations, order and updates as jacobi_small; the off-diagonal norm of
+// the stopping rule is summed per warp, then over the warps in order.
+template <int MM>
+__device__ void jacobi_multi(const EigWs& ws) {
+  constexpr int HALF = MM / 2;
+  constexpr int NE = MM * MM;
+  constexpr int NSLOT = HALF * MM;
+  constexpr int NT = (NSLOT + 31) / 32 * 32;
+  constexpr int NW = NT / 32;
+  const int tid = threadIdx.x;
+  if (tid >= NT) return;
+  const unsigned full = 0xffffffffu;
+  const int lane = tid & 31, warp = tid >> 5;
+  dd* H = ws.H;
+  dd* V = ws.V;
+  auto bar = [] { asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory"); };
+  for (int e = tid; e < NE; e += NT) V[e] = dd{(e / MM == e % MM) ? 1.0f : 0.0f, 0.0f};
+  float off_prev = -1.0f;
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    bar();  // the previous sweep's updates (or V's start) are visible
+    float off = 0.0f, dg = 0.0f;
+    for (int e = tid; e < NE; e += NT) {
+      const int r = e / MM, c = e % MM;
+      const float h = H[e].hi;
+      if (r < c) off += h * h;
+      if (r == c) dg += h * h;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(full, off, o);
+      dg += __shfl_xor_sync(full, dg, o);
+    }
+    if (lane == 0) {
+      ws.red[warp] = off;
+      ws.red[16 + warp] = dg;
+    }
+    bar();
+    off = 0.0f;
+    dg = 0.0f;
+    for (int w = 0; w < NW; ++w) {
+      off += ws.red[w];
+      dg += ws.red[16 + w];
+    }
+    if (jacobi_done(off, dg, off_prev)) break;  // the same decision in every thread
+    off_prev = off;
+#pragma unroll 1
+    for (int round = 0; round < MM - 1; ++round) {
+      if (tid < HALF) {
+        const int a = (tid == 0) ? 0 : ((tid - 1 + round) % (MM - 1)) + 1;
+        const int b = ((MM - 2 - tid + round) % (MM - 1)) + 1;
+        const int pp = min(a, b), qq = max(a, b);
+        dd c, s;
+        rotation(H[pp * MM + pp], H[qq * MM + qq], H[pp * MM + qq], &c, &s);
+        ws.rc[tid] = c;
+        ws.rs[tid] = s;
+        ws.rp[tid] = pp;
+        ws.rq[tid] = qq;
+      }
+      bar();
+      const bool own = tid < NSLOT;
+      const int k = own ? tid / MM : 0, l = tid % MM;
+      const dd ck = ws.rc[k], sk = ws.rs[k];
+      const int pp = ws.rp[k], qq = ws.rq[k];
+      if (own) {  // rows: H <- J^T H
+        const dd hp = H[pp * MM + l], hq = H[qq * MM + l];
+        H[pp * MM + l] = dd_sub(dd_mul(ck, hp), dd_mul(sk, hq));
+        H[qq * MM + l] = dd_add(dd_mul(sk, hp), dd_mul(ck, hq));
+      }
+      bar();
+      if (own) {  // columns: H <- H J, V <- V J
+        const dd hp = H[l * MM + pp], hq = H[l * MM + qq];
+        const dd vp = V[l * MM + pp], vq = V[l * MM + qq];
+        H[l * MM + pp] = dd_sub(dd_mul(ck, hp), dd_mul(sk, hq));
+        H[l * MM + qq] = dd_add(dd_mul(sk, hp), dd_mul(ck, hq));
+        V[l * MM + pp] = dd_sub(dd_mul(ck, vp), dd_mul(sk, vq));
+        V[l * MM + qq] = dd_add(dd_mul(sk, vp), dd_mul(ck, vq));
+      }
+      bar();
+    }
+  }
+}
+
 // Cyclic Jacobi on the symmetric mm x mm dd matrix H (mm even) by the whole
 // CTA; on return diag(H) holds the eigenvalues and V the eigenvectors
 // (columns).  The mm - 1 rounds of a sweep rotate the mm / 2 disjoint pairs
@@ -271,18 +357,21 @@ __device__ inline void jacobi_dd_blocks(const EigWs& ws, int mm) {
 // Runs the Jacobi sweeps on the group that suits mm; all threads of the CTA
 // call it and leave it together.
 __device__ inline void jacobi_dd_cta(const EigWs& ws, int mm) {
-  if (mm <= 16) {
+  if (mm <= 8) {
     if (threadIdx.x < 32) {
       switch (mm) {
         case 2: jacobi_small<2>(ws.H, ws.V); break;
         case 4: jacobi_small<4>(ws.H, ws.V); break;
         case 6: jacobi_small<6>(ws.H, ws.V); break;
-        case 8: jacobi_small<8>(ws.H, ws.V); break;
-        case 10: jacobi_small<10>(ws.H, ws.V); break;
-        case 12: jacobi_small<12>(ws.H, ws.V); break;
-        case 14: jacobi_small<14>(ws.H, ws.V); break;
-        default: jacobi_small<16>(ws.H, ws.V); break;
+        default: jacobi_small<8>(ws.H, ws.V); break;
       }
+    }
+  } else if (mm <= 16) {  // one thread per slot of a round: 2-4 warps
+    switch (mm) {
+      case 10: jacobi_multi<10>(ws); break;
+      case 12: jacobi_multi<12>(ws); break;
+      case 14: jacobi_multi<14>(ws); break;
+      default: jacobi_multi<16>(ws); break;
     }
   } else {
     jacobi_dd_blocks(ws, mm);
