@@ -44,10 +44,10 @@ RHO32 = 0.01
 # the 5000 x 20000 matrix, and on the 20000 x 100000 matrix the tensor-core T
 # pass and the whole block and single-unit threshold sweeps (their six
 # kernels each); None where the kernels changed since the last capture
-TRAFFIC_SL1 = 400.3e6
-TRAFFIC_BL1 = 400.7e6
+TRAFFIC_SL1 = 400.2e6
+TRAFFIC_BL1 = 400.6e6
 TRAFFIC_T4 = 8114.9e6
-TRAFFIC_BLK4 = 9456.2e6
+TRAFFIC_BLK4 = 9455.4e6
 TRAFFIC_SU4 = 8173.4e6
 METRIC = "GPower iters/s"
 UNIT = "iters/s"
@@ -318,9 +318,9 @@ def run_gpu(args):
         "ms_per_step": round(ms2 / args.steps, 4), "sweeps_per_step": round(sweeps2 / args.steps, 2),
         "gpu_launches": launches2,
         "roofline": _roofline(ctx, dA2, "BL1", 5, bytes2, peak, peak_kind,
-                              "sweep_kernel<float,5,3,full-width> (block m=5 fused sweep)", TRAFFIC_BL1),
+                              "sweep_kernel<float,5,3,0,6> (block m=5 fused sweep, 6-column tiles)", TRAFFIC_BL1),
         "roofline_single_unit": _roofline(ctx, dA2, "SL1", 1, bytes2, peak, peak_kind,
-                                          "sweep_kernel<float,1,2,fixed-width 3> (single-unit fused sweep)",
+                                          "sweep_kernel<float,1,2,0,3> (single-unit fused sweep, 3-column tiles)",
                                           TRAFFIC_SL1),
     }
     ctx.close()
