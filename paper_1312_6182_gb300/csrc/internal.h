@@ -112,6 +112,7 @@ struct SweepArgs {
   int j0, mg_valid;
   int ps, W, S, cols_per_cl, fast;
   int sketch;  // 1: power step of the block start (no threshold, no outputs)
+  int overlap; // 1: phase A of tile t+1 before phase B of tile t
 };
 
 }  // namespace gpspca

@@ -172,7 +172,7 @@ extern "C" int gpspca_sweep_static(const gpspca_matrix* A, gpspca_form form, dou
     return record_error(GPSPCA_ECUDA, "copying the sweep records failed");
   }
   const Pass& q = pl.passes[0];
-  SweepArgs a{sp->io_sweep, sp->st, pl.ld, p, n, 1, form, 0, 1, pl.ps, q.W, q.S, pl.cols_per_cl, pl.fast, 0};
+  SweepArgs a{sp->io_sweep, sp->st, pl.ld, p, n, 1, form, 0, 1, pl.ps, q.W, q.S, pl.cols_per_cl, pl.fast, 0, q.ov};
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;

@@ -13,6 +13,7 @@ namespace gpspca {
 struct Pass {
   int j0, mgv, mg, nch, threads, W, S, smem;
   const void* k;
+  int ov = 0;  // overlapped tiles (phase A of tile t+1 before phase B of tile t)
 };
 
 struct Plan {
@@ -50,7 +51,8 @@ struct Plan {
       s += b;
     }
     for (const Pass& q : passes) {
-      snprintf(b, sizeof(b), "|%d,%d,%d,%d,%d,%d,%d", q.j0, q.mgv, q.mg, q.nch, q.threads, q.W, q.S);
+      snprintf(b, sizeof(b), "|%d,%d,%d,%d,%d,%d,%d%s", q.j0, q.mgv, q.mg, q.nch, q.threads, q.W, q.S,
+               q.ov ? "o" : "");
       s += b;
     }
     if (norms_in_sweep) {

@@ -194,10 +194,10 @@ struct SweepSmem {
   int stage_bytes, bars, xbars, red, xrecv, wsm, total;
 };
 constexpr int kMaxCluster = 8;
-constexpr int kXSlots = 2;  // cluster-exchange slots, by tile parity
+constexpr int kXSlots = 2;  // cluster-exchange slots, by tile parity (4 when tiles overlap, see the main loop)
 __host__ __device__ inline int align_up(int v, int a) { return (v + a - 1) / a * a; }
 __host__ __device__ inline SweepSmem sweep_smem_layout(int W, int S, int ps, int esize, int tcsize, int nwarps, int m,
-                                                      int mg) {
+                                                      int mg, int xslots = kXSlots) {
   SweepSmem L;
   L.stage_bytes = W * ps * esize;  // ps*esize is a multiple of 16
   // Threads own rows up to NCH*threads*VEC >= ps; rows past the CTA's slice
@@ -205,10 +205,10 @@ __host__ __device__ inline SweepSmem sweep_smem_layout(int W, int S, int ps, int
   // after the ring covers the largest overshoot (< 33 * NCH * VEC elements).
   int o = align_up(S * L.stage_bytes + kRingSlack, 128);
   L.bars = o; o += 8 * S;         // tile-copy mbarriers
-  L.xbars = o; o += 8 * kXSlots;  // cluster-exchange mbarriers (tile parity)
+  L.xbars = o; o += 8 * xslots;  // cluster-exchange mbarriers (tile mod xslots)
   o = align_up(o, 16);
   L.red = o; o += 2 * nwarps * 32 * tcsize;          // warp partials, by tile parity
-  L.xrecv = o; o += kXSlots * kMaxCluster * 32 * tcsize;  // partials pushed by cluster peers
+  L.xrecv = o; o += xslots * kMaxCluster * 32 * tcsize;  // partials pushed by cluster peers
   L.wsm = o; o += m * mg * tcsize;
   L.total = align_up(o, 128);
   return L;
@@ -297,8 +297,13 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a) {
   const TA* __restrict__ A = static_cast<const TA*>(io->A);
   const int64_t ld = a.ld;
 
+  // overlapped tiles (passes whose tile chain waits on a cluster exchange or
+  // a single column): phase A of tile t+1 runs before phase B of tile t,
+  // with four exchange slots
+  const bool ov = a.overlap != 0;
+  const int xsl = ov ? 4 : kXSlots;
   extern __shared__ __align__(128) unsigned char smem[];
-  const SweepSmem L = sweep_smem_layout(W, S, ps, sizeof(TA), sizeof(TC), nwarps, m, MG);
+  const SweepSmem L = sweep_smem_layout(W, S, ps, sizeof(TA), sizeof(TC), nwarps, m, MG, xsl);
   TA* stage = reinterpret_cast<TA*>(smem);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bars);
   uint64_t* xbars = reinterpret_cast<uint64_t*>(smem + L.xbars);
@@ -329,7 +334,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a) {
   if (tid == 0) {
     if (a.fast)
       for (int s = 0; s < S; ++s) mbar_init(smem_u32(&bars[s]), 1);
-    for (int xs = 0; xs < kXSlots; ++xs) mbar_init(smem_u32(&xbars[xs]), 1);
+    for (int xs = 0; xs < xsl; ++xs) mbar_init(smem_u32(&xbars[xs]), 1);
     fence_mbar_init();
   }
   __syncthreads();
@@ -530,12 +535,14 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a) {
     const TC mine = warp_reduce_scatter<KB>(pd, lane);
     TC* redp = red + (tile & 1) * nwarps * 32;
     redp[warp * 32 + lane] = mine;
-    const int xs = tile & 1;
+    const int xs = tile % xsl;
     if (C > 1 && tid == 0)  // this tile's pushes from the C-1 peers
       mbar_arrive_expect_tx(smem_u32(&xbars[xs]), static_cast<uint32_t>((C - 1) * KB * sizeof(TC)));
     __syncthreads();  // (1) warp partials visible; phase B of the previous tile is done everywhere
     // refill the stage whose tile every thread has finished: tile - 1's
-    if (a.fast && tid == 0 && tile >= 1 && tile - 1 + S < ntiles) issue_tile(tile - 1 + S, (tile - 1) % S);
+    // (tile - 2's when tiles overlap: phase B of tile - 1 comes after this)
+    const int lag = ov ? 2 : 1;
+    if (a.fast && tid == 0 && tile >= lag && tile - lag + S < ntiles) issue_tile(tile - lag + S, (tile - lag) % S);
     TC t = 0;
     for (int w2 = 0; w2 < nwarps; ++w2) t += redp[w2 * 32 + lane];
     if (C > 1 && warp == 0 && lane < KB) {  // push this CTA's total to every peer (one-way)
@@ -557,9 +564,9 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a) {
     const bool norm_slot = NRM && jq == MG;  // this lane's slot is a column's squared norm
     const bool mine_valid = lane < WB * SL && wq < wv && !norm_slot && jq < a.mg_valid;
     if (C > 1) {  // wait for the peers' totals, add all C in rank order
-      const int xs = tile & 1;
+      const int xs = tile % xsl;
       TC* slot = xrecv + xs * kMaxCluster * 32;
-      if (!mbar_wait_bounded(smem_u32(&xbars[xs]), static_cast<uint32_t>((tile >> 1) & 1))) timed_out = true;
+      if (!mbar_wait_bounded(smem_u32(&xbars[xs]), static_cast<uint32_t>((tile / xsl) & 1))) timed_out = true;
       TC tot = 0;
       for (uint32_t r = 0; r < C; ++r) tot += (r == cr) ? t : slot[r * 32 + lane];
       t = tot;
@@ -619,7 +626,22 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a) {
     }
   };
 
-  for (int tile = 0; tile < ntiles; ++tile) phase_b(tile, phase_a(tile));
+  if (ov) {
+    // phase A of tile t+1 (its dot products) before phase B of tile t, so the
+    // cluster exchange of tile t overlaps the next tile's arithmetic.  Safe
+    // with four exchange slots: a push for tile t+1 into slot (t+1) mod 4
+    // follows this CTA's phase B of tile t-1, which waited for every peer's
+    // phase A of tile t-1, which each peer runs after its phase B of tile t-3,
+    // the slot's previous reader.  The ring refill lags one more tile.
+    TC t_cur = ntiles > 0 ? phase_a(0) : TC(0);
+    for (int tile = 0; tile < ntiles; ++tile) {
+      const TC t_next = tile + 1 < ntiles ? phase_a(tile + 1) : TC(0);
+      phase_b(tile, t_cur);
+      t_cur = t_next;
+    }
+  } else {
+    for (int tile = 0; tile < ntiles; ++tile) phase_b(tile, phase_a(tile));
+  }
 
   // ---- epilogue: this cluster's partial of Y = A G and of the objective
   if constexpr (kPair) {
