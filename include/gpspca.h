@@ -85,7 +85,7 @@ typedef enum { GPSPCA_DEVICE = 0, GPSPCA_HOST = 1 } gpspca_location;
 #define GPSPCA_NO_TENSOR_CORES 4u /* run the CUDA-core fused sweep even where the tensor-core
                                      (tcgen05) sweep applies (bf16 storage, or float storage with
                                      a 16-byte aligned base and column stride, with m >= 6; such
-                                     float storage with p >= 9000 rows for any m; other float
+                                     float storage with p >= 16384 rows for any m; other float
                                      layouts and fp8 storage with m >= 9) */
 #define GPSPCA_TIME_T_PASS 16u    /* gpspca_time_sweep only: time the tensor-core sweep's first
                                      pass (T = A^T X with its X3 preparation and row-range

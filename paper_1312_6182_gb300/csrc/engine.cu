@@ -131,7 +131,7 @@ static KAttr kattr(const void* f) {
 // ---------------------------------------------------------------- planning
 
 constexpr int kSmemBudget = 200 * 1024;  // stage ring + bookkeeping, per CTA
-constexpr int64_t kTcLongRows = 9000;     // float columns this long take the tensor-core sweep for any m
+constexpr int64_t kTcLongRows = 16384;    // float columns this long take the tensor-core sweep for any m
 
 static const int kMGs[] = {1, 2, 4, 5, 8};
 
@@ -345,9 +345,12 @@ int make_plan(int dt, int form, int m, int64_t p, int64_t n, int64_t ld, bool fa
   // any m: a CUDA-core CTA holds at most 5000-8000 float rows in registers,
   // so such columns are split over clusters whose per-tile exchange (and
   // idle SMs) cost more than the tensor-core sweep's two passes (single-unit
-  // at 10000 x 40000 / 12000 x 30000 / 20000 x 25000: 0.327 / 0.288 / 0.392
-  // ms against 0.363 / 0.318 / 0.441 ms; a tie at 16000 x 30000; block m = 5
-  // at 20000 x 25000: 0.71 ms on the CUDA cores).  Otherwise
+  // sweeps at 10000 x 40000 / 12000 x 30000 / 20000 x 25000: 0.327 / 0.288 /
+  // 0.392 ms against 0.363 / 0.318 / 0.441 ms; a tie at 16000 x 30000; block
+  // m = 5 at 20000 x 25000: 0.71 ms on the CUDA cores).  Below 16384 rows
+  // whole single-unit solves did not gain (64 solves at 10000 x 50000: 155
+  // against 135 ms: the tensor-core sweep's extra launches and tensor maps
+  // per solve).  Otherwise
   // the widest CUDA-core passes first (fewest reads of A) in the smallest
   // clusters that fit; long columns (large p) may only fit narrower passes,
   // whose per-thread register tiles are smaller.  The other candidates (the

@@ -121,14 +121,14 @@ def test_fixed_sweeps_ragged(ctx, form, ld):
 @pytest.mark.parametrize("form", oracle.FORMS)
 @pytest.mark.parametrize("tensor_cores", [True, False])
 def test_long_columns(ctx, form, tensor_cores):
-    """Float columns of 9000 rows or more: by default the tensor-core sweep
+    """Float columns of 16384 rows or more: by default the tensor-core sweep
     for any m (here one or two components); with tensor_cores=False the
     CUDA-core sweep, which splits each column's rows over a cluster of CTAs
     whose partial dot products meet through distributed shared memory before
-    the threshold.  12004 x 2003 planted spikes (rows ragged against the
+    the threshold.  16500 x 2003 planted spikes (rows ragged against the
     CTAs' slices and the 64-row chunks), 6 sweeps against the oracle; the two
     plans differ."""
-    At = synth.planted_spike(12004, 2003, 2, [60.0, 35.0], support_frac=0.03, seed=64, dtype=np.float32)
+    At = synth.planted_spike(16500, 2003, 2, [60.0, 35.0], support_frac=0.03, seed=64, dtype=np.float32)
     A = At.astype(np.float64).T
     m = 1 if form.startswith("S") else 2
     mu = None if m == 1 else [1.0, 0.8]
@@ -832,6 +832,34 @@ def test_batch_groups_same_shape_solves(ctx, dtype):
             _converged(form, g, A, gam, None, ref, items[i]["tol"], f"group member {i} {dtype}")
         else:
             assert_matches(form, g, ref, oracle.column_norms(A), label=f"group member {i} {dtype}")
+
+
+@pytest.mark.parametrize("storage", ["bf16", "fp8"])
+def test_batch_groups_low_precision_storage(ctx, storage):
+    """Groups of bf16 and fp8 (per-column scales) requests: 8 members of
+    256 x 3000, SL1, against the oracle on the stored values; the same
+    requests split over two batches give the same bits."""
+    p, n = 256, 3000
+    items, deqs = [], []
+    for i in range(8):
+        At = synth.planted_spike(p, n, 2, [25.0, 12.0], support_frac=0.05, seed=500 + i, dtype=np.float32)
+        if storage == "bf16":
+            tb, deq = _bf16(At)
+            items.append(dict(At=tb.cuda(), form="SL1", gamma=[0.08], gamma_relative=True, tol=0.0, maxit=5))
+        else:
+            q, sc, deq = _fp8(At)
+            items.append(dict(At=q.cuda(), col_scale=sc.cuda(), form="SL1", gamma=[0.08], gamma_relative=True,
+                              tol=0.0, maxit=5))
+        deqs.append(deq)
+    got = ctx.solve_batch(items)
+    again = ctx.solve_batch(items[4:]) + ctx.solve_batch(items[:4])
+    again = again[4:] + again[:4]
+    for i in range(8):
+        assert torch.equal(got[i].Z, again[i].Z) and torch.equal(got[i].X, again[i].X), i
+        A = deqs[i].astype(np.float64).T
+        gam = _gammas(A, "SL1", [0.08])
+        ref = oracle.gpower(A, "SL1", gam, tol=0.0, maxit=5)
+        assert_matches("SL1", gpu_arrays(got[i]), ref, oracle.column_norms(A), label=f"group {storage} member {i}")
 
 
 def test_batch_group_with_a_failing_member(ctx):
