@@ -46,9 +46,9 @@ RHO32 = 0.01
 # kernels each); None where the kernels changed since the last capture
 TRAFFIC_SL1 = 400.2e6
 TRAFFIC_BL1 = 400.6e6
-TRAFFIC_T4 = 8114.9e6
-TRAFFIC_BLK4 = 9455.4e6
-TRAFFIC_SU4 = 8173.4e6
+TRAFFIC_T4 = None
+TRAFFIC_BLK4 = None
+TRAFFIC_SU4 = None
 METRIC = "GPower iters/s"
 UNIT = "iters/s"
 WORKLOAD4 = ("planted spikes 20000x100000 fp32 (16 spikes, theta_j=100/sqrt(j), 1% supports), SL1+SL0+BL1+BL0 "
@@ -287,7 +287,7 @@ def run_gpu(args):
     # its share of the step, is the roofline line.
     r_t = _roofline(ctx, dA, "BL1", M4, bytes_a, peak, peak_kind,
                     "tc_t_fused_kernel<48> (+ tc_prep, tc_t_combine): T = A^T X on tcgen05, float A split into exact "
-                    "bf16 planes in shared memory", TRAFFIC_T4, t_pass=True)
+                    "bf16 planes in tensor memory (the MMA's A operand)", TRAFFIC_T4, t_pass=True)
     r_blk = _roofline(ctx, dA, "BL1", M4, bytes_a, peak, peak_kind,
                       "block m=16 threshold sweep: tc_prep + tc_t_fused<48> + tc_t_combine + tc_count + "
                       "tc_compact + tc_y_fused<48> over the active columns", TRAFFIC_BLK4)

@@ -783,17 +783,37 @@ __host__ __device__ constexpr int tc_fused_smem(int npad) {
   return tc_fused_s1(npad) * static_cast<int>(kTcF) + 2 * (3 * static_cast<int>(kTcA) + npad * 128) + 1024 + 512;
 }
 
-template <int NPAD>
+// T pass with the bf16 planes in tensor memory (TM): the converters write
+// the three planes of a chunk with tcgen05.st into one of two tensor-memory
+// buffers (lane = column of the tile, two rows of A per 32-bit column) and
+// the MMAs read their A operand from there.  Ring 2 then holds only the X3
+// tile, and the shared memory the planes took (and the bandwidth of writing
+// and reading them there: about half of the pass's shared-memory traffic)
+// goes to float stages.  Tensor memory: the two accumulators in columns
+// [0, 2 NPAD), the plane buffers (3 x 32 columns each) from column kTmACol;
+// up to NPAD = 96 this fits the 512 columns of the SM.
+constexpr int kTmS1 = 6;            // float stages in flight
+constexpr uint32_t kTmACol = 256;   // first tensor-memory column of the plane buffers
+constexpr uint32_t kTmABuf = 96;    // columns per plane buffer: 3 planes x 64 rows / 2
+__host__ __device__ constexpr bool tc_fused_tm(int npad) { return npad <= 96; }
+__host__ __device__ constexpr int tc_fused_tm_smem(int npad) {
+  return kTmS1 * static_cast<int>(kTcF) + 2 * (npad * 128) + 1024 + 512;
+}
+
+template <int NPAD, bool TM = false>
 struct TcFusedCfg {
   static constexpr int MPAD = NPAD / 3;
   static constexpr uint32_t kB = NPAD * 128;
   static constexpr uint32_t kStage1 = kTcF;
-  static constexpr uint32_t kStage2 = 3 * kTcA + kB;
-  static constexpr int S1 = tc_fused_s1(NPAD);
+  static constexpr uint32_t kBOff = TM ? 0 : 3 * kTcA;  // X3 / G3 tile within a ring-2 stage
+  static constexpr uint32_t kStage2 = kBOff + kB;
+  static constexpr int S1 = TM ? kTmS1 : tc_fused_s1(NPAD);
   static constexpr int S2 = 2;
-  static constexpr uint32_t kCols = TcCfg<NPAD, 3>::kCols;
+  static constexpr uint32_t kCols = TM ? 512 : TcCfg<NPAD, 3>::kCols;
   static_assert(kStage1 % 1024 == 0 && kStage2 % 1024 == 0, "1024-byte aligned stages");
-  static_assert(tc_fused_smem(NPAD) <= 227 * 1024, "rings fit the shared memory");
+  static_assert((TM ? tc_fused_tm_smem(NPAD) : tc_fused_smem(NPAD)) <= 227 * 1024, "rings fit the shared memory");
+  static_assert(!TM || (2 * NPAD <= static_cast<int>(kTmACol) && kTmACol + 2 * kTmABuf <= 512),
+                "accumulators and plane buffers fit the tensor memory");
 };
 
 struct TcFusedSmem {
@@ -804,9 +824,9 @@ struct TcFusedSmem {
   TcSmem acc;  // accf / acce / tensor-memory slot / abort flag (the drain uses these)
 };
 
-template <int NPAD>
+template <int NPAD, bool TM = false>
 __device__ __forceinline__ TcFusedSmem tc_fused_smem(unsigned char* raw) {
-  using Cfg = TcFusedCfg<NPAD>;
+  using Cfg = TcFusedCfg<NPAD, TM>;
   TcFusedSmem s;
   const uint32_t r = smem_u32(raw);
   s.base1 = (r + 1023u) & ~1023u;
@@ -828,9 +848,9 @@ __device__ __forceinline__ TcFusedSmem tc_fused_smem(unsigned char* raw) {
   return s;
 }
 
-template <int NPAD>
+template <int NPAD, bool TM = false>
 __device__ __forceinline__ uint32_t tc_fused_setup(const TcFusedSmem& S) {
-  using Cfg = TcFusedCfg<NPAD>;
+  using Cfg = TcFusedCfg<NPAD, TM>;
   const int tid = threadIdx.x;
   if (tid == 0) {
     for (int k = 0; k < Cfg::S1; ++k) {
@@ -1003,6 +1023,93 @@ __device__ __forceinline__ bool tc_fused_mma(const TcFusedSmem& S, uint32_t tmem
   return true;
 }
 
+// Converter warps of the TM T pass: chunk `it` from ring 1 into plane
+// buffer it % 2 of tensor memory.  Warp w (6..13) may write the tensor-memory
+// lanes 32 (w % 4) .. + 31, so its thread for lane L takes tile column
+// q = 32 (w % 4) + L, and rows 32 h .. 32 h + 31 of the chunk with
+// h = (w - 6) / 4: the 128-byte row q of float box h (16-byte chunks
+// swizzled by q), split exactly into three bf16 parts, two rows per 32-bit
+// column: plane pl, row r at column kTmACol + 96 (it % 2) + 32 pl + r / 2.
+// NORM: also adds the squares of the values to ss (see tc_convert_row).
+template <int NPAD, bool NORM = false>
+__device__ __forceinline__ bool tc_convert_chunk_tm(const TcFusedSmem& S, uint32_t tmem, int it,
+                                                    float* ss = nullptr) {
+  using Cfg = TcFusedCfg<NPAD, true>;
+  const int s1 = it % Cfg::S1, s2 = it % Cfg::S2;
+  const uint32_t u1 = static_cast<uint32_t>(it / Cfg::S1), u2 = static_cast<uint32_t>(it / Cfg::S2);
+  if (!mbar_wait_bounded(smem_u32(&S.full1[s1]), u1 & 1)) return false;
+  // the MMAs that read this plane buffer (chunk it - 2) have completed
+  if (u2 > 0 && !mbar_wait_bounded(smem_u32(&S.empty2[s2]), (u2 - 1) & 1)) return false;
+  tc_fence_after();
+  const int warp = static_cast<int>(threadIdx.x >> 5), lane = static_cast<int>(threadIdx.x & 31);
+  const int quad = warp & 3;
+  const int q = 32 * quad + lane;
+  const int h = (warp - 6) >> 2;
+  const unsigned char* row = S.ptr1 + s1 * Cfg::kStage1 + h * 16384 + q * 128;
+  const uint32_t tcol = tmem + (static_cast<uint32_t>(32 * quad) << 16) + kTmACol +
+                        static_cast<uint32_t>(s2) * kTmABuf + static_cast<uint32_t>(16 * h);
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {  // rows 16 half .. + 15 of the thread's 32
+    uint32_t w[3][8];
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {  // 16-byte chunk j: rows 4 j .. 4 j + 3
+      const int j = half * 4 + cc;
+      const uint4 v = *reinterpret_cast<const uint4*>(row + ((j ^ (q & 7)) * 16));
+      const uint32_t x[4] = {v.x, v.y, v.z, v.w};
+      if constexpr (NORM) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) *ss = fmaf(__uint_as_float(x[e]), __uint_as_float(x[e]), *ss);
+      }
+#pragma unroll
+      for (int e = 0; e < 4; e += 2) {
+        uint32_t a0, a1, a2, b0, b1, b2;
+        split3_trunc(__uint_as_float(x[e]), a0, a1, a2);
+        split3_trunc(__uint_as_float(x[e + 1]), b0, b1, b2);
+        // high halves of (even row, odd row) -> one bf16x2 word, even row in the low half
+        w[0][2 * cc + e / 2] = __byte_perm(a0, b0, 0x7632);
+        w[1][2 * cc + e / 2] = __byte_perm(a1, b1, 0x7632);
+        w[2][2 * cc + e / 2] = __byte_perm(a2, b2, 0x7632);
+      }
+    }
+#pragma unroll
+    for (int pl = 0; pl < 3; ++pl) tmem_st8(tcol + static_cast<uint32_t>(32 * pl + 8 * half), w[pl]);
+  }
+  tmem_wait_st();
+  __syncwarp();
+  if (lane == 0) mbar_arrive(smem_u32(&S.empty1[s1]));  // the float stage is read
+  tc_fence_before();
+  mbar_arrive(smem_u32(&S.full2[s2]));
+  return true;
+}
+
+// MMA issuer of the TM T pass: the 12 MMAs of chunk `it` (three planes, four
+// K = 16 steps each, smallest plane first), A from plane buffer it % 2 of
+// tensor memory, B the X3 tile of ring-2 stage it % 2.
+template <int NPAD>
+__device__ __forceinline__ bool tc_fused_mma_tm(const TcFusedSmem& S, uint32_t tmem, int it, uint32_t idesc) {
+  using Cfg = TcFusedCfg<NPAD, true>;
+  const int s2 = it % Cfg::S2, b = it & 1;
+  const uint32_t u2 = static_cast<uint32_t>(it / Cfg::S2);
+  const uint32_t ub = static_cast<uint32_t>(it >> 1);
+  if (ub > 0 && !mbar_wait_bounded(smem_u32(&S.acc.acce[b]), (ub - 1) & 1)) return false;
+  if (!mbar_wait_bounded(smem_u32(&S.full2[s2]), u2 & 1)) return false;
+  tc_fence_after();
+  const uint32_t sb = S.base2 + s2 * Cfg::kStage2 + Cfg::kBOff;
+  const uint32_t d = tmem + static_cast<uint32_t>(b * NPAD);
+  const uint32_t at = tmem + kTmACol + static_cast<uint32_t>(s2) * kTmABuf;
+#pragma unroll
+  for (int pl = 2; pl >= 0; --pl) {
+#pragma unroll
+    for (int kk = 0; kk < kTcBK / 16; ++kk) {
+      const uint64_t bd = sdesc_sw128(sb + kk * 32, 16, 1024);
+      umma_f16_ts(d, at + static_cast<uint32_t>(32 * pl + 8 * kk), bd, idesc, (pl < 2 || kk > 0) ? 1u : 0u);
+    }
+  }
+  umma_commit(smem_u32(&S.empty2[s2]));
+  umma_commit(smem_u32(&S.acc.accf[b]));
+  return true;
+}
+
 // TMA producer of both rings: the float tile of chunk `it` once the
 // converters have read the stage's previous tile, the X3 / G3 tile once the
 // MMAs of the ring-2 stage's previous chunk have completed.  The two streams
@@ -1011,10 +1118,10 @@ __device__ __forceinline__ bool tc_fused_mma(const TcFusedSmem& S, uint32_t tmem
 // pass) or 128-row block (Y pass), for the stored-tile and the X3 / G3
 // streams; each is called with it = 0, 1, 2, ... in turn.  false on a
 // timeout or an abort.
-template <int NPAD, typename CoordF, typename CoordB>
+template <int NPAD, bool TM = false, typename CoordF, typename CoordB>
 __device__ __forceinline__ bool tc_fused_producer(const TcFusedSmem& S, int total, CoordF coordf, CoordB coordb,
                                                   const TcMaps* maps, bool y_pass) {
-  using Cfg = TcFusedCfg<NPAD>;
+  using Cfg = TcFusedCfg<NPAD, TM>;
   int itf = 0, itb = 0;
   uint32_t idle = 0;
   while (itf < total || itb < total) {
@@ -1047,7 +1154,7 @@ __device__ __forceinline__ bool tc_fused_producer(const TcFusedSmem& S, int tota
         coordb(itb, &c, &tr);
         const uint32_t bar = smem_u32(&S.full2[s2]);
         mbar_arrive_expect_tx(bar, Cfg::kB);
-        tma_load_2d(S.base2 + s2 * Cfg::kStage2 + 3 * kTcA, y_pass ? &maps->g3 : &maps->x3, c * kTcBK, 0, bar);
+        tma_load_2d(S.base2 + s2 * Cfg::kStage2 + Cfg::kBOff, y_pass ? &maps->g3 : &maps->x3, c * kTcBK, 0, bar);
         ++itb;
         progressed = true;
       }
@@ -1179,14 +1286,14 @@ __device__ __forceinline__ bool tc_gather_producer(const TcFusedSmem& S, int tot
   return true;
 }
 
-// fused T pass (float A)
-template <int NPAD>
+// fused T pass (float A); TM: the bf16 planes in tensor memory
+template <int NPAD, bool TM>
 __global__ void __launch_bounds__(kTcFusedThreads, 1) tc_t_fused_kernel(const TcArgs a) {
-  using Cfg = TcFusedCfg<NPAD>;
+  using Cfg = TcFusedCfg<NPAD, TM>;
   constexpr int MPAD = Cfg::MPAD;
   constexpr uint32_t kIdesc = idesc_bf16_f32(NPAD, 0, 0);
   extern __shared__ unsigned char smem_raw[];
-  const TcFusedSmem S = tc_fused_smem<NPAD>(smem_raw);
+  const TcFusedSmem S = tc_fused_smem<NPAD, TM>(smem_raw);
   __shared__ float gam_s[kMaxM], mu_s[kMaxM];
   __shared__ int act_s[kMaxM];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1201,7 +1308,7 @@ __global__ void __launch_bounds__(kTcFusedThreads, 1) tc_t_fused_kernel(const Tc
     mu_s[tid] = v ? static_cast<float>(io->mu[tid]) : 1.0f;
     act_s[tid] = tid < a.m ? st->active[tid] : 0;
   }
-  const uint32_t tmem = tc_fused_setup<NPAD>(S);
+  const uint32_t tmem = tc_fused_setup<NPAD, TM>(S);
   bool timed_out = false;
   if (warp == 4) {
     if (lane == 0) {
@@ -1215,7 +1322,7 @@ __global__ void __launch_bounds__(kTcFusedThreads, 1) tc_t_fused_kernel(const Tc
       TCursor cf, cb;  // the stored-tile and the X3 streams, each called with consecutive indices
       cf.start(a);
       cb.start(a);
-      if (!tc_fused_producer<NPAD>(
+      if (!tc_fused_producer<NPAD, TM>(
               S, total,
               [&](int, int* c, int* tr) {
                 *c = cf.c;
@@ -1236,11 +1343,17 @@ __global__ void __launch_bounds__(kTcFusedThreads, 1) tc_t_fused_kernel(const Tc
     if (lane == 0) {
       TCursor cu;
       cu.start(a);
-      for (int it = 0; cu.valid(a) && !timed_out; ++it, cu.next(a))
-        if (!tc_fused_mma<NPAD, false>(S, tmem, it, kIdesc)) {
+      for (int it = 0; cu.valid(a) && !timed_out; ++it, cu.next(a)) {
+        bool ok;
+        if constexpr (TM)
+          ok = tc_fused_mma_tm<NPAD>(S, tmem, it, kIdesc);
+        else
+          ok = tc_fused_mma<NPAD, false>(S, tmem, it, kIdesc);
+        if (!ok) {
           timed_out = true;
           *S.acc.abort_flag = 1;
         }
+      }
     }
   } else if (warp >= 6) {  // converters
     TCursor cu;
@@ -1249,12 +1362,15 @@ __global__ void __launch_bounds__(kTcFusedThreads, 1) tc_t_fused_kernel(const Tc
     // column's 32 rows each thread converts, summed per chunk in float, per
     // item in double, and added to the column's squared norm at the item's
     // end (two halves of the rows, and the row ranges, add up by atomics)
-    const int q = (tid - 192) & 127;
+    const int q = TM ? 32 * (warp & 3) + lane : (tid - 192) & 127;  // the thread's column of the tile
     double nacc = 0.0;
     for (int it = 0; cu.valid(a) && !timed_out; ++it, cu.next(a)) {
       float ss = 0.0f;
-      const bool ok = a.norms ? tc_convert_chunk<NPAD, false, true>(S, it, false, &ss)
-                              : tc_convert_chunk<NPAD, false>(S, it);
+      bool ok;
+      if constexpr (TM)
+        ok = a.norms ? tc_convert_chunk_tm<NPAD, true>(S, tmem, it, &ss) : tc_convert_chunk_tm<NPAD>(S, tmem, it);
+      else
+        ok = a.norms ? tc_convert_chunk<NPAD, false, true>(S, it, false, &ss) : tc_convert_chunk<NPAD, false>(S, it);
       if (tc_aborted(S.acc) || !ok) {
         timed_out = true;
         *S.acc.abort_flag = 1;
@@ -1556,8 +1672,10 @@ static void launch_tc_npad(const TcArgs& a, int nsm, cudaStream_t s, bool t_only
 
 template <int NPAD>
 static void launch_tc_fused_npad(const TcArgs& a, int nsm, cudaStream_t s, bool t_only) {
-  static bool once = [] {
-    cudaFuncSetAttribute(tc_t_fused_kernel<NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_fused_smem(NPAD));
+  constexpr bool kTM = tc_fused_tm(NPAD);  // planes in tensor memory where they fit
+  const int smem_t = kTM ? tc_fused_tm_smem(NPAD) : tc_fused_smem(NPAD);
+  static bool once = [smem_t] {
+    cudaFuncSetAttribute(tc_t_fused_kernel<NPAD, kTM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_t);
     cudaFuncSetAttribute(tc_y_fused_kernel<NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_fused_smem(NPAD));
     return true;
   }();
@@ -1567,7 +1685,8 @@ static void launch_tc_fused_npad(const TcArgs& a, int nsm, cudaStream_t s, bool 
   if (a.from_ritz) {
     tc_t_from_ritz_kernel<NPAD / 3><<<(a.n + 255) / 256, 256, 0, s>>>(a);
   } else {
-    tc_t_fused_kernel<NPAD><<<std::max(1, std::min(a.ntile1 * a.ksplit1, nsm)), kTcFusedThreads, smem, s>>>(a);
+    tc_t_fused_kernel<NPAD, kTM>
+        <<<std::max(1, std::min(a.ntile1 * a.ksplit1, nsm)), kTcFusedThreads, smem_t, s>>>(a);
     if (a.ksplit1 > 1) tc_t_combine_kernel<NPAD / 3><<<dim3((a.n + 255) / 256, NPAD / 3), 256, 0, s>>>(a);
   }
   if (a.norms) tc_norms_kernel<<<(a.n + 255) / 256, 256, 0, s>>>(a);
