@@ -46,9 +46,9 @@ RHO32 = 0.01
 # kernels each); None where the kernels changed since the last capture
 TRAFFIC_SL1 = 400.2e6
 TRAFFIC_BL1 = 400.6e6
-TRAFFIC_T4 = None
-TRAFFIC_BLK4 = None
-TRAFFIC_SU4 = None
+TRAFFIC_T4 = 8115.3e6
+TRAFFIC_BLK4 = 9456.1e6
+TRAFFIC_SU4 = 8173.1e6
 METRIC = "GPower iters/s"
 UNIT = "iters/s"
 WORKLOAD4 = ("planted spikes 20000x100000 fp32 (16 spikes, theta_j=100/sqrt(j), 1% supports), SL1+SL0+BL1+BL0 "

@@ -784,20 +784,42 @@ __host__ __device__ constexpr int tc_fused_smem(int npad) {
 }
 
 // T pass with the bf16 planes in tensor memory (TM): the converters write
-// the three planes of a chunk with tcgen05.st into one of two tensor-memory
+// the three planes of a chunk with tcgen05.st into one of S2 tensor-memory
 // buffers (lane = column of the tile, two rows of A per 32-bit column) and
 // the MMAs read their A operand from there.  Ring 2 then holds only the X3
 // tile, and the shared memory the planes took (and the bandwidth of writing
 // and reading them there: about half of the pass's shared-memory traffic)
 // goes to float stages.  Tensor memory: the two accumulators in columns
-// [0, 2 NPAD), the plane buffers (3 x 32 columns each) from column kTmACol;
+// [0, 2 NPAD), the plane buffers (3 x 32 columns each) from column 2 NPAD;
 // up to NPAD = 96 this fits the 512 columns of the SM.
-constexpr int kTmS1 = 6;            // float stages in flight
-constexpr uint32_t kTmACol = 256;   // first tensor-memory column of the plane buffers
 constexpr uint32_t kTmABuf = 96;    // columns per plane buffer: 3 planes x 64 rows / 2
 __host__ __device__ constexpr bool tc_fused_tm(int npad) { return npad <= 96; }
+// accumulators: the MMAs of one chunk fill one while the epilogue drains the
+// others; three where the tensor memory leaves room for three plane buffers
+// next to them (NPAD = 48), else two.  Measured at 20000 x 100000, m = 16:
+// block sweep 1.655 ms with two accumulators and four plane buffers, 1.607
+// with three and three.
+__host__ __device__ constexpr int tc_tm_nacc(int npad) { return npad <= 48 ? 3 : 2; }
+// first tensor-memory column of the plane buffers: after the accumulators
+__host__ __device__ constexpr uint32_t tc_tm_acol(int npad) {
+  return static_cast<uint32_t>((tc_tm_nacc(npad) * npad + 31) / 32 * 32);
+}
+// plane buffers (and X3 stages): as many as the tensor memory holds next to
+// the accumulators (3 for NPAD = 48 and 96); the converters run that many
+// chunks ahead of the MMAs.  Measured at 20000 x 100000 with two
+// accumulators: single-unit sweep 1.288 / 1.280 / 1.256 ms with 2 / 3 / 4
+// buffers.
+__host__ __device__ constexpr int tc_tm_s2(int npad) {
+  return (512 - static_cast<int>(tc_tm_acol(npad))) / static_cast<int>(kTmABuf);
+}
+// float stages: as many as the shared memory holds next to the X3 stages, at most 6
+__host__ __device__ constexpr int tc_tm_s1(int npad) {
+  return (227 * 1024 - 1024 - 512 - tc_tm_s2(npad) * npad * 128) / static_cast<int>(kTcF) < 6
+             ? (227 * 1024 - 1024 - 512 - tc_tm_s2(npad) * npad * 128) / static_cast<int>(kTcF)
+             : 6;
+}
 __host__ __device__ constexpr int tc_fused_tm_smem(int npad) {
-  return kTmS1 * static_cast<int>(kTcF) + 2 * (npad * 128) + 1024 + 512;
+  return tc_tm_s1(npad) * static_cast<int>(kTcF) + tc_tm_s2(npad) * (npad * 128) + 1024 + 512;
 }
 
 template <int NPAD, bool TM = false>
@@ -807,13 +829,15 @@ struct TcFusedCfg {
   static constexpr uint32_t kStage1 = kTcF;
   static constexpr uint32_t kBOff = TM ? 0 : 3 * kTcA;  // X3 / G3 tile within a ring-2 stage
   static constexpr uint32_t kStage2 = kBOff + kB;
-  static constexpr int S1 = TM ? kTmS1 : tc_fused_s1(NPAD);
-  static constexpr int S2 = 2;
+  static constexpr int S1 = TM ? tc_tm_s1(NPAD) : tc_fused_s1(NPAD);
+  static constexpr int S2 = TM ? tc_tm_s2(NPAD) : 2;
   static constexpr uint32_t kCols = TM ? 512 : TcCfg<NPAD, 3>::kCols;
+  static constexpr uint32_t kACol = tc_tm_acol(NPAD);
+  static constexpr int NACC = TM ? tc_tm_nacc(NPAD) : 2;
   static_assert(kStage1 % 1024 == 0 && kStage2 % 1024 == 0, "1024-byte aligned stages");
   static_assert((TM ? tc_fused_tm_smem(NPAD) : tc_fused_smem(NPAD)) <= 227 * 1024, "rings fit the shared memory");
-  static_assert(!TM || (2 * NPAD <= static_cast<int>(kTmACol) && kTmACol + 2 * kTmABuf <= 512),
-                "accumulators and plane buffers fit the tensor memory");
+  static_assert(!TM || (S1 >= 3 && S2 >= 2 && kACol % 32 == 0 && kACol + S2 * kTmABuf <= 512),
+                "float stages, accumulators and plane buffers fit");
 };
 
 struct TcFusedSmem {
@@ -839,8 +863,8 @@ __device__ __forceinline__ TcFusedSmem tc_fused_smem(unsigned char* raw) {
   s.full2 = s.empty1 + Cfg::S1;
   s.empty2 = s.full2 + Cfg::S2;
   s.acc.accf = s.empty2 + Cfg::S2;
-  s.acc.acce = s.acc.accf + 2;
-  s.acc.tslot = reinterpret_cast<uint32_t*>(s.acc.acce + 2);
+  s.acc.acce = s.acc.accf + Cfg::NACC;
+  s.acc.tslot = reinterpret_cast<uint32_t*>(s.acc.acce + Cfg::NACC);
   s.acc.abort_flag = reinterpret_cast<int*>(s.acc.tslot + 1);
   s.acc.full = s.acc.empty = nullptr;
   s.acc.base = 0;
@@ -861,7 +885,7 @@ __device__ __forceinline__ uint32_t tc_fused_setup(const TcFusedSmem& S) {
       mbar_init(smem_u32(&S.full2[k]), kTcConverters + 1);  // converters + the X3 / G3 copy
       mbar_init(smem_u32(&S.empty2[k]), 1);
     }
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < Cfg::NACC; ++k) {
       mbar_init(smem_u32(&S.acc.accf[k]), 1);
       mbar_init(smem_u32(&S.acc.acce[k]), 128);
     }
@@ -1024,12 +1048,12 @@ __device__ __forceinline__ bool tc_fused_mma(const TcFusedSmem& S, uint32_t tmem
 }
 
 // Converter warps of the TM T pass: chunk `it` from ring 1 into plane
-// buffer it % 2 of tensor memory.  Warp w (6..13) may write the tensor-memory
+// buffer it % S2 of tensor memory.  Warp w (6..13) may write the tensor-memory
 // lanes 32 (w % 4) .. + 31, so its thread for lane L takes tile column
 // q = 32 (w % 4) + L, and rows 32 h .. 32 h + 31 of the chunk with
 // h = (w - 6) / 4: the 128-byte row q of float box h (16-byte chunks
 // swizzled by q), split exactly into three bf16 parts, two rows per 32-bit
-// column: plane pl, row r at column kTmACol + 96 (it % 2) + 32 pl + r / 2.
+// column: plane pl, row r at column 2 NPAD + 96 (it % S2) + 32 pl + r / 2.
 // NORM: also adds the squares of the values to ss (see tc_convert_row).
 template <int NPAD, bool NORM = false>
 __device__ __forceinline__ bool tc_convert_chunk_tm(const TcFusedSmem& S, uint32_t tmem, int it,
@@ -1046,15 +1070,14 @@ __device__ __forceinline__ bool tc_convert_chunk_tm(const TcFusedSmem& S, uint32
   const int q = 32 * quad + lane;
   const int h = (warp - 6) >> 2;
   const unsigned char* row = S.ptr1 + s1 * Cfg::kStage1 + h * 16384 + q * 128;
-  const uint32_t tcol = tmem + (static_cast<uint32_t>(32 * quad) << 16) + kTmACol +
+  const uint32_t tcol = tmem + (static_cast<uint32_t>(32 * quad) << 16) + Cfg::kACol +
                         static_cast<uint32_t>(s2) * kTmABuf + static_cast<uint32_t>(16 * h);
 #pragma unroll
   for (int half = 0; half < 2; ++half) {  // rows 16 half .. + 15 of the thread's 32
     uint32_t w[3][8];
 #pragma unroll
     for (int cc = 0; cc < 4; ++cc) {  // 16-byte chunk j: rows 4 j .. 4 j + 3
-      const int j = half * 4 + cc;
-      const uint4 v = *reinterpret_cast<const uint4*>(row + ((j ^ (q & 7)) * 16));
+      const uint4 v = *reinterpret_cast<const uint4*>(row + (((half * 4 + cc) ^ (q & 7)) * 16));
       const uint32_t x[4] = {v.x, v.y, v.z, v.w};
       if constexpr (NORM) {
 #pragma unroll
@@ -1075,28 +1098,30 @@ __device__ __forceinline__ bool tc_convert_chunk_tm(const TcFusedSmem& S, uint32
     for (int pl = 0; pl < 3; ++pl) tmem_st8(tcol + static_cast<uint32_t>(32 * pl + 8 * half), w[pl]);
   }
   tmem_wait_st();
+  // the float stage is released only now: releasing it as soon as its values
+  // were in registers was measured 2% slower over the whole pass
   __syncwarp();
-  if (lane == 0) mbar_arrive(smem_u32(&S.empty1[s1]));  // the float stage is read
+  if (lane == 0) mbar_arrive(smem_u32(&S.empty1[s1]));
   tc_fence_before();
   mbar_arrive(smem_u32(&S.full2[s2]));
   return true;
 }
 
 // MMA issuer of the TM T pass: the 12 MMAs of chunk `it` (three planes, four
-// K = 16 steps each, smallest plane first), A from plane buffer it % 2 of
-// tensor memory, B the X3 tile of ring-2 stage it % 2.
+// K = 16 steps each, smallest plane first), A from plane buffer it % S2 of
+// tensor memory, B the X3 tile of ring-2 stage it % S2.
 template <int NPAD>
 __device__ __forceinline__ bool tc_fused_mma_tm(const TcFusedSmem& S, uint32_t tmem, int it, uint32_t idesc) {
   using Cfg = TcFusedCfg<NPAD, true>;
-  const int s2 = it % Cfg::S2, b = it & 1;
+  const int s2 = it % Cfg::S2, b = it % Cfg::NACC;
   const uint32_t u2 = static_cast<uint32_t>(it / Cfg::S2);
-  const uint32_t ub = static_cast<uint32_t>(it >> 1);
+  const uint32_t ub = static_cast<uint32_t>(it / Cfg::NACC);
   if (ub > 0 && !mbar_wait_bounded(smem_u32(&S.acc.acce[b]), (ub - 1) & 1)) return false;
   if (!mbar_wait_bounded(smem_u32(&S.full2[s2]), u2 & 1)) return false;
   tc_fence_after();
   const uint32_t sb = S.base2 + s2 * Cfg::kStage2 + Cfg::kBOff;
   const uint32_t d = tmem + static_cast<uint32_t>(b * NPAD);
-  const uint32_t at = tmem + kTmACol + static_cast<uint32_t>(s2) * kTmABuf;
+  const uint32_t at = tmem + Cfg::kACol + static_cast<uint32_t>(s2) * kTmABuf;
 #pragma unroll
   for (int pl = 2; pl >= 0; --pl) {
 #pragma unroll
@@ -1107,6 +1132,31 @@ __device__ __forceinline__ bool tc_fused_mma_tm(const TcFusedSmem& S, uint32_t t
   }
   umma_commit(smem_u32(&S.empty2[s2]));
   umma_commit(smem_u32(&S.acc.accf[b]));
+  return true;
+}
+
+// Epilogue of the TM T pass: as tc_drain, over the NACC accumulators.
+template <int NPAD>
+__device__ __forceinline__ bool tc_drain_tm(const TcSmem& S, uint32_t tlane, int it, float (&acc)[NPAD / 3]) {
+  using Cfg = TcFusedCfg<NPAD, true>;
+  constexpr int MPAD = NPAD / 3;
+  const int b = it % Cfg::NACC;
+  if (!mbar_wait_bounded(smem_u32(&S.accf[b]), static_cast<uint32_t>((it / Cfg::NACC) & 1))) return false;
+  tc_fence_after();
+  const uint32_t col = tlane + static_cast<uint32_t>(b * NPAD);
+#pragma unroll
+  for (int c0 = 0; c0 < MPAD; c0 += 16) {
+    uint32_t h[16], md[16], lo[16];
+    tmem_ld16(col + c0, h);
+    tmem_ld16(col + MPAD + c0, md);
+    tmem_ld16(col + 2 * MPAD + c0, lo);
+    tmem_wait_ld();
+#pragma unroll
+    for (int e = 0; e < 16; ++e)
+      acc[c0 + e] += __uint_as_float(h[e]) + (__uint_as_float(md[e]) + __uint_as_float(lo[e]));
+  }
+  tc_fence_before();
+  mbar_arrive(smem_u32(&S.acce[b]));
   return true;
 }
 
@@ -1393,12 +1443,18 @@ __global__ void __launch_bounds__(kTcFusedThreads, 1) tc_t_fused_kernel(const Tc
       float t[MPAD];
 #pragma unroll
       for (int j = 0; j < MPAD; ++j) t[j] = 0.0f;
-      for (int c = ti.cb; c < ti.ce; ++c, ++it)
-        if (!tc_drain<NPAD, 3>(S.acc, tlane, it, t)) {
+      for (int c = ti.cb; c < ti.ce; ++c, ++it) {
+        bool ok;
+        if constexpr (TM)
+          ok = tc_drain_tm<NPAD>(S.acc, tlane, it, t);
+        else
+          ok = tc_drain<NPAD, 3>(S.acc, tlane, it, t);
+        if (!ok) {
           timed_out = true;
           *S.acc.abort_flag = 1;
           break;
         }
+      }
       if (timed_out) break;
       tc_t_store<MPAD>(a, ti, warp * 32 + lane, t, form, gam_s, mu_s, act_s);
     }
