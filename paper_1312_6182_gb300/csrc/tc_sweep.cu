@@ -1107,6 +1107,62 @@ __device__ __forceinline__ bool tc_convert_chunk_tm(const TcFusedSmem& S, uint32
   return true;
 }
 
+// Converter warps of the TM Y pass: chunk `it` (64 columns of A, 128 rows)
+// from ring 1 into plane buffer it % S2.  The thread for tensor-memory lane
+// r = 32 (w % 4) + L takes row r of the block and columns 32 h .. 32 h + 31
+// of the chunk (h = (w - 6) / 4), one 4-byte load per column: in the stored
+// layout (four boxes of 32 rows x 64 columns, 16-byte chunks swizzled by the
+// column) or, for gathered columns (plain), column i's 128 rows at byte
+// 512 i.  Two columns per 32-bit word, the even one in the low half.
+template <int NPAD>
+__device__ __forceinline__ bool tc_convert_chunk_tm_y(const TcFusedSmem& S, uint32_t tmem, int it, bool plain) {
+  using Cfg = TcFusedCfg<NPAD, true>;
+  const int s1 = it % Cfg::S1, s2 = it % Cfg::S2;
+  const uint32_t u1 = static_cast<uint32_t>(it / Cfg::S1), u2 = static_cast<uint32_t>(it / Cfg::S2);
+  if (!mbar_wait_bounded(smem_u32(&S.full1[s1]), u1 & 1)) return false;
+  if (u2 > 0 && !mbar_wait_bounded(smem_u32(&S.empty2[s2]), (u2 - 1) & 1)) return false;
+  tc_fence_after();
+  const int warp = static_cast<int>(threadIdx.x >> 5), lane = static_cast<int>(threadIdx.x & 31);
+  const int quad = warp & 3;
+  const int h = (warp - 6) >> 2;
+  const unsigned char* f = S.ptr1 + s1 * Cfg::kStage1;
+  // byte offset of (row r, column i): plain i * 512 + 4 r; stored box r / 32,
+  // column row i, 16-byte chunk (r % 32) / 4 swizzled by i
+  const unsigned char* rowp = plain ? f + 4 * (32 * quad + lane) : f + quad * 8192 + (lane & 3) * 4;
+  const uint32_t tcol = tmem + (static_cast<uint32_t>(32 * quad) << 16) + Cfg::kACol +
+                        static_cast<uint32_t>(s2) * kTmABuf + static_cast<uint32_t>(16 * h);
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    uint32_t w[3][8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int i = 32 * h + 16 * half + 2 * e;
+      float v0, v1;
+      if (plain) {
+        v0 = *reinterpret_cast<const float*>(rowp + i * 512);
+        v1 = *reinterpret_cast<const float*>(rowp + (i + 1) * 512);
+      } else {
+        v0 = *reinterpret_cast<const float*>(rowp + i * 128 + (((lane >> 2) ^ (i & 7)) << 4));
+        v1 = *reinterpret_cast<const float*>(rowp + (i + 1) * 128 + (((lane >> 2) ^ ((i + 1) & 7)) << 4));
+      }
+      uint32_t a0, a1, a2, b0, b1, b2;
+      split3_trunc(v0, a0, a1, a2);
+      split3_trunc(v1, b0, b1, b2);
+      w[0][e] = __byte_perm(a0, b0, 0x7632);
+      w[1][e] = __byte_perm(a1, b1, 0x7632);
+      w[2][e] = __byte_perm(a2, b2, 0x7632);
+    }
+#pragma unroll
+    for (int pl = 0; pl < 3; ++pl) tmem_st8(tcol + static_cast<uint32_t>(32 * pl + 8 * half), w[pl]);
+  }
+  tmem_wait_st();
+  __syncwarp();
+  if (lane == 0) mbar_arrive(smem_u32(&S.empty1[s1]));
+  tc_fence_before();
+  mbar_arrive(smem_u32(&S.full2[s2]));
+  return true;
+}
+
 // MMA issuer of the TM T pass: the 12 MMAs of chunk `it` (three planes, four
 // K = 16 steps each, smallest plane first), A from plane buffer it % S2 of
 // tensor memory, B the X3 tile of ring-2 stage it % S2.
@@ -1260,10 +1316,10 @@ struct YCursor {
 // at byte 512 k of the float stage.  The list entries of the next four
 // chunks are loaded ahead into registers.  Lane 0 polls both rings and
 // copies the G3c tile.  false on a timeout or an abort.
-template <int NPAD>
+template <int NPAD, bool TM = false>
 __device__ __forceinline__ bool tc_gather_producer(const TcFusedSmem& S, int total, YCursor ca, YCursor cg,
                                                    const int32_t* list, const TcMaps* maps) {
-  using Cfg = TcFusedCfg<NPAD>;
+  using Cfg = TcFusedCfg<NPAD, TM>;
   const int lane = threadIdx.x & 31;
   const int g = lane & 15;
   int itf = 0, itb = 0;
@@ -1321,7 +1377,7 @@ __device__ __forceinline__ bool tc_gather_producer(const TcFusedSmem& S, int tot
         const int s2 = itb % Cfg::S2;
         const uint32_t bar = smem_u32(&S.full2[s2]);
         mbar_arrive_expect_tx(bar, Cfg::kB);
-        tma_load_2d(S.base2 + s2 * Cfg::kStage2 + 3 * kTcA, &maps->g3c, cg.c * kTcBK, 0, bar);
+        tma_load_2d(S.base2 + s2 * Cfg::kStage2 + Cfg::kBOff, &maps->g3c, cg.c * kTcBK, 0, bar);
       }
       ++itb;
       cg.next();
@@ -1468,14 +1524,15 @@ __global__ void __launch_bounds__(kTcFusedThreads, 1) tc_t_fused_kernel(const Tc
   }
 }
 
-// fused Y pass (float A), persistent CTAs over (row block, split) items
-template <int NPAD>
+// fused Y pass (float A), persistent CTAs over (row block, split) items; TM:
+// the bf16 planes in tensor memory (rows in lanes, so the A operand is K-major)
+template <int NPAD, bool TM>
 __global__ void __launch_bounds__(kTcFusedThreads, 1) tc_y_fused_kernel(const TcArgs a) {
-  using Cfg = TcFusedCfg<NPAD>;
+  using Cfg = TcFusedCfg<NPAD, TM>;
   constexpr int MPAD = Cfg::MPAD;
-  constexpr uint32_t kIdesc = idesc_bf16_f32(NPAD, 1, 0);
+  constexpr uint32_t kIdesc = idesc_bf16_f32(NPAD, TM ? 0 : 1, 0);
   extern __shared__ unsigned char smem_raw[];
-  const TcFusedSmem S = tc_fused_smem<NPAD>(smem_raw);
+  const TcFusedSmem S = tc_fused_smem<NPAD, TM>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const IO* io = a.io;
   State* st = a.st;
@@ -1491,13 +1548,13 @@ __global__ void __launch_bounds__(kTcFusedThreads, 1) tc_y_fused_kernel(const Tc
   cur.start(a.nrow2, a.nsplit2, nch, kps);
   int total = 0;  // chunks of this CTA's items
   for (YCursor t = cur; t.valid(); t.seek(t.item + gridDim.x)) total += t.ce - t.cb;
-  const uint32_t tmem = tc_fused_setup<NPAD>(S);
+  const uint32_t tmem = tc_fused_setup<NPAD, TM>(S);
   bool timed_out = false;
   if (warp == 4) {
     if (listed) {
       tmap_acquire(&maps->a2g);
       tmap_acquire(&maps->g3c);
-      if (!tc_gather_producer<NPAD>(S, total, cur, cur, io->tc_list, maps)) {
+      if (!tc_gather_producer<NPAD, TM>(S, total, cur, cur, io->tc_list, maps)) {
         timed_out = true;
         if (lane == 0) *S.acc.abort_flag = 1;
       }
@@ -1505,7 +1562,7 @@ __global__ void __launch_bounds__(kTcFusedThreads, 1) tc_y_fused_kernel(const Tc
       tmap_acquire(&maps->a2f);
       tmap_acquire(&maps->g3);
       YCursor cf = cur, cb = cur;  // the stored-tile and the G3 streams
-      if (!tc_fused_producer<NPAD>(
+      if (!tc_fused_producer<NPAD, TM>(
               S, total,
               [&](int, int* c, int* tr) {
                 *c = cf.c;
@@ -1524,18 +1581,30 @@ __global__ void __launch_bounds__(kTcFusedThreads, 1) tc_y_fused_kernel(const Tc
     }
   } else if (warp == 5) {
     if (lane == 0) {
-      for (int it = 0; it < total && !timed_out; ++it)
-        if (!tc_fused_mma<NPAD, true>(S, tmem, it, kIdesc)) {
+      for (int it = 0; it < total && !timed_out; ++it) {
+        bool ok;
+        if constexpr (TM)
+          ok = tc_fused_mma_tm<NPAD>(S, tmem, it, kIdesc);
+        else
+          ok = tc_fused_mma<NPAD, true>(S, tmem, it, kIdesc);
+        if (!ok) {
           timed_out = true;
           *S.acc.abort_flag = 1;
         }
+      }
     }
   } else if (warp >= 6) {
-    for (int it = 0; it < total && !timed_out; ++it)
-      if (tc_aborted(S.acc) || !tc_convert_chunk<NPAD, true>(S, it, listed)) {
+    for (int it = 0; it < total && !timed_out; ++it) {
+      bool ok = !tc_aborted(S.acc);
+      if constexpr (TM)
+        ok = ok && tc_convert_chunk_tm_y<NPAD>(S, tmem, it, listed);
+      else
+        ok = ok && tc_convert_chunk<NPAD, true>(S, it, listed);
+      if (!ok) {
         timed_out = true;
         *S.acc.abort_flag = 1;
       }
+    }
   } else {  // epilogue: every item of this CTA, empty ones included, writes its rows
     const uint32_t tlane = tmem + (static_cast<uint32_t>(warp * 32) << 16);
     float* yp = static_cast<float*>(io->ypart);
@@ -1546,12 +1615,18 @@ __global__ void __launch_bounds__(kTcFusedThreads, 1) tc_y_fused_kernel(const Tc
       float y[MPAD];
 #pragma unroll
       for (int j = 0; j < MPAD; ++j) y[j] = 0.0f;
-      for (int c = t.cb; c < t.ce; ++c, ++it)
-        if (!tc_drain<NPAD, 3>(S.acc, tlane, it, y)) {
+      for (int c = t.cb; c < t.ce; ++c, ++it) {
+        bool ok;
+        if constexpr (TM)
+          ok = tc_drain_tm<NPAD>(S.acc, tlane, it, y);
+        else
+          ok = tc_drain<NPAD, 3>(S.acc, tlane, it, y);
+        if (!ok) {
           timed_out = true;
           *S.acc.abort_flag = 1;
           break;
         }
+      }
       const int r = t.rb * kTcRows2 + warp * 32 + lane;
       if (!timed_out && r < a.p) {
 #pragma unroll
@@ -1732,11 +1807,10 @@ static void launch_tc_fused_npad(const TcArgs& a, int nsm, cudaStream_t s, bool 
   const int smem_t = kTM ? tc_fused_tm_smem(NPAD) : tc_fused_smem(NPAD);
   static bool once = [smem_t] {
     cudaFuncSetAttribute(tc_t_fused_kernel<NPAD, kTM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_t);
-    cudaFuncSetAttribute(tc_y_fused_kernel<NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_fused_smem(NPAD));
+    cudaFuncSetAttribute(tc_y_fused_kernel<NPAD, kTM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_t);
     return true;
   }();
   (void)once;
-  const int smem = tc_fused_smem(NPAD);
   tc_prep_kernel<<<dim3((a.p + 255) / 256, a.mpad), 256, 0, s>>>(a);
   if (a.from_ritz) {
     tc_t_from_ritz_kernel<NPAD / 3><<<(a.n + 255) / 256, 256, 0, s>>>(a);
@@ -1752,7 +1826,7 @@ static void launch_tc_fused_npad(const TcArgs& a, int nsm, cudaStream_t s, bool 
     tc_count_kernel<<<nb, 256, 0, s>>>(a);
     tc_compact_kernel<NPAD / 3><<<nb, 256, 0, s>>>(a);
   }
-  tc_y_fused_kernel<NPAD><<<std::max(1, std::min(a.nrow2 * a.nsplit2, nsm)), kTcFusedThreads, smem, s>>>(a);
+  tc_y_fused_kernel<NPAD, kTM><<<std::max(1, std::min(a.nrow2 * a.nsplit2, nsm)), kTcFusedThreads, smem_t, s>>>(a);
 }
 
 template <int NA>
