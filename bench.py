@@ -50,6 +50,7 @@ TRAFFIC_T4 = 8115.3e6
 TRAFFIC_BLK4 = 9456.1e6
 TRAFFIC_SU4 = 8173.1e6
 METRIC = "GPower iters/s"
+SERVING_SAMPLE = 1000  # requests of the serving mix run by the default benchmark
 UNIT = "iters/s"
 WORKLOAD4 = ("planted spikes 20000x100000 fp32 (16 spikes, theta_j=100/sqrt(j), 1% supports), SL1+SL0+BL1+BL0 "
              "(block m=16, mu=1), gamma=0.05*max||a_i||, tol 1e-6")
@@ -324,6 +325,16 @@ def run_gpu(args):
                                           TRAFFIC_SL1),
     }
     ctx.close()
+    del dA2
+    torch.cuda.empty_cache()
+
+    # ---- serving sample (rank 0, after the timed steps): the request mix of
+    # the serving workload with SERVING_SAMPLE requests, for p50 / p99 at the
+    # offered 200 requests/s beside the throughput
+    serving = None
+    if rank == 0:
+        serving, _, _ = _serving(SERVING_SAMPLE, 3)
+        serving = {"workload": f"serving mix: {SERVING_SAMPLE} requests, {SERVING_MIX}", **serving}
     line = {
         "metric": METRIC,
         "value": round(value, 2),
@@ -350,6 +361,8 @@ def run_gpu(args):
         "clocks": clocks,
         "spikes_5000x20000": secondary,
     }
+    if serving is not None:
+        line["serving_sample"] = serving
     if rank == 0:
         line["cpu_baseline"] = cpu_baseline(ws)
     if ws > 1:
@@ -989,22 +1002,23 @@ def _pct(xs, q):
     return float(np.percentile(np.asarray(xs, dtype=np.float64), q)) if len(xs) else None
 
 
-def run_serving(args):
-    """Serving: the request mix (Poisson arrivals at 200/s; p, n log-uniform
+def _serving(nreq, warmup):
+    """The serving mix (Poisson arrivals at 200/s; p, n log-uniform
     over [256, 8192] x [1024, 65536]; FP32 or BF16; the four forms; m in
     1..16; rho ~ U(0.02, 0.2)); each request's planted-spike A is drawn on
     the device (seed 1000 + id, timed as ingest) and submitted to the
-    context's continuous-batching scheduler (admission by workspace under a
-    150 GB budget, up to 8 solves overlapping).  Reported: served solves/s
-    and p50/p99 latency at the offered load, the saturated throughput, and the
-    serial plain per-request solves on the same requests (their latency at the
-    same arrivals from a single-server FIFO queue)."""
+    context's continuous-batching scheduler (admission by HBM footprint:
+    matrix, outputs and workspace under a 150 GB budget; up to 8 solves
+    overlapping).  Measured: served solves/s and p50/p99 latency at the
+    offered load, the saturated throughput, and the serial plain per-request
+    solves on the same requests (their latency at the same arrivals from a
+    single-server FIFO queue).  Returns (summary, clocks, span in seconds)."""
     import numpy as np
     import torch
 
     from paper_1312_6182_gb300 import binding, synth
 
-    reqs = synth.serving_requests(count=args.requests, rate=200.0, seed=3)
+    reqs = synth.serving_requests(count=nreq, rate=200.0, seed=3)
     gen_stream = torch.cuda.Stream()
     ctx = binding.Context(0, budget_bytes=150 << 30)
 
@@ -1052,7 +1066,7 @@ def run_serving(args):
         return time.perf_counter() - t0, lat, lat_solve, ingest, results
 
     # warm-up: a few requests through both paths (graph builds for common shapes are per shape)
-    for r in reqs[: args.warmup]:
+    for r in reqs[:warmup]:
         A = make_input(r)
         ctx.solve(A, r.form, r.gammas(), mu=mu_of(r), tol=TOL, maxit=MAXIT, gamma_relative=True)
     clk = Clocks(0)
@@ -1081,26 +1095,34 @@ def run_serving(args):
         free_at = start + sv
         lat_serial.append(free_at - r.arrival_s)
     ctx.close()
-    nreq = len(reqs)
+    summary = {
+        "offered_rate": 200.0, "requests": nreq,
+        "served_solves_per_s": round(nreq / span, 2),
+        "p50_ms": round(_pct(lat, 50) * 1e3, 3), "p99_ms": round(_pct(lat, 99) * 1e3, 3),
+        "p50_solve_ms": round(_pct(lat_solve, 50) * 1e3, 3),
+        "p99_solve_ms": round(_pct(lat_solve, 99) * 1e3, 3),
+        "ingest_ms_mean": round(float(np.mean(ingest)) * 1e3, 4),
+        "saturated_solves_per_s": round(nreq / span_sat, 2),
+        "saturated_p50_ms": round(_pct(lat_sat, 50) * 1e3, 3),
+        "serial_solves_per_s": round(nreq / sum(svc), 2),
+        "serial_p50_ms_at_offered": round(_pct(lat_serial, 50) * 1e3, 3),
+        "serial_p99_ms_at_offered": round(_pct(lat_serial, 99) * 1e3, 3),
+        "same_alone_and_in_mix": f"{same}/{len(serial_out)}",
+        "mean_p_times_n": float(np.mean([r.p * r.n for r in reqs]))}
+    return summary, clocks, span
+
+
+SERVING_MIX = ("p in [256,8192], n in [1024,65536] log-uniform, fp32|bf16, SL1|SL0|BL1|BL0, m 1..16, rho "
+               "U(0.02,0.2), device-generated planted spikes (Philox4x32-10, seed 1000+id), Poisson arrivals at 200/s")
+
+
+def run_serving(args):
+    """Serving: the request mix of `_serving` with --requests requests."""
+    summary, clocks, span = _serving(args.requests, args.warmup)
+    nreq = summary["requests"]
     line = _base_line("served solves/s", "solves/s", nreq / span, span * 1e3 / nreq, args,
-                      f"serving mix: {nreq} requests, Poisson 200/s, p in [256,8192], n in [1024,65536] "
-                      "log-uniform, fp32|bf16, SL1|SL0|BL1|BL0, m 1..16, rho U(0.02,0.2), device-generated "
-                      "planted spikes (Philox4x32-10, seed 1000+id)", "f32|bf16",
-                      {"serving": {
-                          "offered_rate": 200.0, "requests": nreq,
-                          "served_solves_per_s": round(nreq / span, 2),
-                          "p50_ms": round(_pct(lat, 50) * 1e3, 3), "p99_ms": round(_pct(lat, 99) * 1e3, 3),
-                          "p50_solve_ms": round(_pct(lat_solve, 50) * 1e3, 3),
-                          "p99_solve_ms": round(_pct(lat_solve, 99) * 1e3, 3),
-                          "ingest_ms_mean": round(float(np.mean(ingest)) * 1e3, 4),
-                          "saturated_solves_per_s": round(nreq / span_sat, 2),
-                          "saturated_p50_ms": round(_pct(lat_sat, 50) * 1e3, 3),
-                          "serial_solves_per_s": round(nreq / sum(svc), 2),
-                          "serial_p50_ms_at_offered": round(_pct(lat_serial, 50) * 1e3, 3),
-                          "serial_p99_ms_at_offered": round(_pct(lat_serial, 99) * 1e3, 3),
-                          "same_alone_and_in_mix": f"{same}/{len(serial_out)}",
-                          "mean_p_times_n": float(np.mean([r.p * r.n for r in reqs]))},
-                       "clocks": clocks})
+                      f"serving mix: {nreq} requests, {SERVING_MIX}", "f32|bf16",
+                      {"serving": summary, "clocks": clocks})
     print(json.dumps(line), flush=True)
 
 
