@@ -304,6 +304,23 @@ def run_gpu(args):
     r_t["share_of_step"] = round(n_t * r_t["ms_per_launch"] / step_ms, 3)
     r_blk["launches_per_step"] = sum(it for (f, _), it in zip(CASES4, its) if f.startswith("B"))
     r_su["launches_per_step"] = sum(it for (f, _), it in zip(CASES4, its) if f.startswith("S"))
+
+    # ---- precision sample (rank 0, after the timed steps): BL1 / BL0 with
+    # m = 16 on this matrix in FP32, and on its BF16 and FP8 copies + 3 FP32
+    # refinement sweeps
+    precision = None
+    if rank == 0:
+        pres, _, _, psw = _precision(ctx, stream, dA, P4, N4, RHO, 3, 2, 8)
+        pbytes = {"f32": P4 * N4 * 4, "bf16": P4 * N4 * 2, "fp8": P4 * N4 + N4 * 4}
+        precision = {
+            "workload": "planted spikes 20000x100000 (16 spikes, theta_j=100/sqrt(j), 1% supports), BL1/BL0 m=16 "
+                        f"mu=1, gamma={RHO:g}*max||a_i||; FP32 vs BF16 and FP8-E4M3 (per-column scales) storage + "
+                        "3 FP32 refinement sweeps",
+            "results": pres,
+            "solves_per_s_vs_f32": {k: round(v["solves_per_s"] / pres[k.split("_")[0] + "_f32"]["solves_per_s"], 3)
+                                    for k, v in pres.items() if not k.endswith("f32")},
+            "sweeps_m16": {fmt: {"ms_per_sweep": round(v, 4),
+                                 "frac": round(pbytes[fmt] / (v / 1e3) / 1e9 / peak, 4)} for fmt, v in psw.items()}}
     del dA
     torch.cuda.empty_cache()
 
@@ -324,9 +341,21 @@ def run_gpu(args):
                                           "sweep_kernel<float,1,2,0,3> (single-unit fused sweep, 3-column tiles)",
                                           TRAFFIC_SL1),
     }
-    ctx.close()
     del dA2
     torch.cuda.empty_cache()
+
+    # ---- sparsity-path sample (rank 0): 64 gammas batched vs separate on a
+    # 10000 x 50000 matrix, block L1 with m = 32
+    gamma_path = None
+    if rank == 0:
+        dA3 = torch.from_numpy(synth.workload_spikes_10000x50000(1)).cuda()
+        gres, ms_sw, ms_sw32, _ = _gamma_path(ctx, stream, dA3, 10000, 50000, 2, 4)
+        gamma_path = {"workload": GAMMA_WORKLOAD, "results": gres, "ms_per_64_gamma_sweep": round(ms_sw, 4),
+                      "frac_one_read": round(10000 * 50000 * 4 / (ms_sw / 1e3) / 1e9 / peak, 4),
+                      "block_m32_sweep_ms": round(ms_sw32, 4)}
+        del dA3
+        torch.cuda.empty_cache()
+    ctx.close()
 
     # ---- serving sample (rank 0, after the timed steps): the request mix of
     # the serving workload with SERVING_SAMPLE requests, for p50 / p99 at the
@@ -361,8 +390,10 @@ def run_gpu(args):
         "clocks": clocks,
         "spikes_5000x20000": secondary,
     }
-    if serving is not None:
-        line["serving_sample"] = serving
+    for key, val in (("precision_sample", precision), ("gamma_path_sample", gamma_path),
+                     ("serving_sample", serving)):
+        if val is not None:
+            line[key] = val
     if rank == 0:
         line["cpu_baseline"] = cpu_baseline(ws)
     if ws > 1:
@@ -517,34 +548,27 @@ def _base_line(metric, unit, value, ms_per_step, args, workload, dtype, extra):
     return line
 
 
-def run_gamma_path(args):
-    """Sparsity path: 64 gamma values log-spaced over [0.001, 0.5] max||a_i||,
-    single-unit L1 and L0 on a 10000 x 50000 FP32 planted-spike A (3 spikes,
-    2% supports), as one batched solve (all 64 columns advance in every
-    sweep) against 64 separate solves; plus block L1 with m = 32.  Units:
-    solve-iterations (one gamma value, one sweep) per second."""
-    import numpy as np
+def _gamma_path(ctx, stream, dA, p, n, warmup, steps):
+    """The sparsity-path measurements on dA (10000 x 50000): the 64 gammas of
+    SL1 and SL0 as one batched solve and as 64 separate solves, block L1 with
+    m = 32, and the sweeps alone.  Returns (results, ms per 64-gamma sweep,
+    ms per m = 32 sweep, clocks)."""
     import torch
 
     from paper_1312_6182_gb300 import binding, synth
 
-    p, n = 10000, 50000
-    At = synth.workload_spikes_10000x50000(1)
-    dA = torch.from_numpy(At).cuda()
-    del At
     rho = [float(r) for r in synth.log_spaced_rho(64)]
-    stream = torch.cuda.Stream()
-    ctx = binding.Context(0, stream=stream)
     res = {}
     clk = Clocks(0)
+    clocks = None
     for form in ("SL1", "SL0"):
         out = binding.alloc_result(64, p, n, "cuda", torch.float32)
         one = binding.alloc_result(1, p, n, "cuda", torch.float32)
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             ctx.solve(dA, form, rho, gamma_relative=True, out=out)
         if form == "SL1":
             clk.start()
-        ms_b, r = _event_ms(stream, lambda: ctx.solve(dA, form, rho, gamma_relative=True, out=out), args.steps)
+        ms_b, r = _event_ms(stream, lambda: ctx.solve(dA, form, rho, gamma_relative=True, out=out), steps)
         if form == "SL1":
             clocks = clk.stop()
         it_b = int(r.iters.sum().item())
@@ -567,25 +591,47 @@ def run_gamma_path(args):
     # only 3 spikes, larger gammas threshold whole noise components away)
     rho32 = [RHO32] * 32
     out32 = binding.alloc_result(32, p, n, "cuda", torch.float32)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         ctx.solve(dA, "BL1", rho32, mu=[1.0] * 32, gamma_relative=True, out=out32)
     ms_32, r32 = _event_ms(stream, lambda: ctx.solve(dA, "BL1", rho32, mu=[1.0] * 32, gamma_relative=True,
-                                                    out=out32), max(1, args.steps // 2))
+                                                    out=out32), max(1, steps // 2))
     res["BL1_m32"] = {"iters_per_s": round(int(r32.iters.max().item()) / (ms_32 / 1e3), 1),
                       "ms_per_solve": round(ms_32, 3), "iters": int(r32.iters.max().item()),
                       "status": sorted(set(int(v) for v in r32.status.tolist())), "rho": RHO32}
     # the sweep of the 64-column batch alone: one read of A is the algorithmic minimum
     ms_sw = ctx.time_sweep(dA, "SL1", rho, gamma_relative=True, reps=10)
     ms_sw32 = ctx.time_sweep(dA, "BL1", rho32, mu=[1.0] * 32, gamma_relative=True, reps=10)
+    return res, ms_sw, ms_sw32, clocks
+
+
+GAMMA_WORKLOAD = ("planted spikes 10000x50000 fp32 (3 spikes, theta_j=40/j, 2% supports), 64 gammas log-spaced "
+                  "[0.001,0.5]*max||a_i||, SL1/SL0 batched vs separate; BL1 m=32 gamma=0.01*max||a_i||")
+
+
+def run_gamma_path(args):
+    """Sparsity path: 64 gamma values log-spaced over [0.001, 0.5] max||a_i||,
+    single-unit L1 and L0 on a 10000 x 50000 FP32 planted-spike A (3 spikes,
+    2% supports), as one batched solve (all 64 columns advance in every
+    sweep) against 64 separate solves; plus block L1 with m = 32.  Units:
+    solve-iterations (one gamma value, one sweep) per second."""
+    import torch
+
+    from paper_1312_6182_gb300 import binding, synth
+
+    p, n = 10000, 50000
+    At = synth.workload_spikes_10000x50000(1)
+    dA = torch.from_numpy(At).cuda()
+    del At
+    stream = torch.cuda.Stream()
+    ctx = binding.Context(0, stream=stream)
+    res, ms_sw, ms_sw32, clocks = _gamma_path(ctx, stream, dA, p, n, args.warmup, args.steps)
     peak, kind = _peaks()
     nbytes = p * n * 4
     flops = 4.0 * p * n * 64
     ctx.close()
     value = res["SL1"]["batched_iters_per_s"]
     line = _base_line("gamma-path solve-iters/s (64 gammas batched)", "iters/s", value,
-                      res["SL1"]["batched_ms_per_solve"], args,
-                      "planted spikes 10000x50000 fp32 (3 spikes, theta_j=40/j, 2% supports), 64 gammas log-spaced "
-                      "[0.001,0.5]*max||a_i||, SL1/SL0 batched vs separate; BL1 m=32 gamma=0.01*max||a_i||", "f32",
+                      res["SL1"]["batched_ms_per_solve"], args, GAMMA_WORKLOAD, "f32",
                       {"results": res,
                        "roofline": {"bound": "hbm",
                                     "kernel": "tc_t_fused_kernel<192> + tc_y_fused_kernel<192> (tcgen05, float A "
@@ -894,6 +940,62 @@ def _fp8_columns(dA32):
     return q, s.float().contiguous()
 
 
+def _precision(ctx, stream, d32, p, n, rho, refine_sweeps, warmup, steps):
+    """The precision-path measurements on the float matrix d32 (n x p
+    column-major storage): BL1 and BL0 with m = 16, solved on the FP32
+    matrix, and on its BF16 and FP8 E4M3 (per-column scales) copies followed
+    by `refine_sweeps` FP32 sweeps from the converged X; and each storage's sweep
+    alone.  Returns (results, kept outputs, clocks, ms per sweep by storage)."""
+    import torch
+
+    from paper_1312_6182_gb300 import binding
+
+    m = 16
+    dbf = d32.to(torch.bfloat16)
+    d8, s8 = _fp8_columns(d32)
+    mu = [1.0] * m
+    out = binding.alloc_result(m, p, n, "cuda", torch.float32)
+    out2 = binding.alloc_result(m, p, n, "cuda", torch.float32)
+    res = {}
+    keep = {}
+    clk = Clocks(0)
+    clocks = None
+    for form in ("BL1", "BL0"):
+        for fmt, dA, cs in (("f32", d32, None), ("bf16", dbf, None), ("fp8", d8, s8)):
+            def solve():
+                return ctx.solve(dA, form, [rho] * m, mu=mu, gamma_relative=True, out=out, col_scale=cs)
+
+            for _ in range(warmup):
+                solve()
+            if clocks is None:
+                clk.start()
+            ms, r = _event_ms(stream, solve, max(1, steps // 4))
+            if clocks is None:
+                clocks = clk.stop()
+            iters = int(r.iters.max().item())
+            entry = {"ms_per_solve": round(ms, 3), "iters": iters, "iters_per_s": round(iters / (ms / 1e3), 1),
+                     "status": int(r.status.max().item())}
+            if fmt != "f32":
+                x0 = r.X.contiguous().clone()
+
+                def refine():
+                    return ctx.solve(d32, form, [rho] * m, mu=mu, gamma_relative=True, tol=0.0,
+                                     maxit=refine_sweeps, x0=x0, out=out2)
+
+                ms_r, rr = _event_ms(stream, refine, max(1, steps // 4))
+                entry["refine_ms"] = round(ms_r, 3)
+                entry["ms_total"] = round(ms + ms_r, 3)
+                keep[(form, fmt)] = {k: getattr(rr, k).clone() for k in ("X", "Z", "objective", "support")}
+            else:
+                entry["ms_total"] = round(ms, 3)
+                keep[(form, fmt)] = {k: getattr(r, k).clone() for k in ("X", "Z", "objective", "support")}
+            entry["solves_per_s"] = round(1e3 / entry["ms_total"], 2)
+            res[f"{form}_{fmt}"] = entry
+    sweep_ms = {fmt: ctx.time_sweep(dA, "BL1", [rho] * m, mu=mu, gamma_relative=True, reps=5, col_scale=cs)
+                for fmt, dA, cs in (("f32", d32, None), ("bf16", dbf, None), ("fp8", d8, s8))}
+    return res, keep, clocks, sweep_ms
+
+
 def run_precision(args):
     """Precision path: block L1 and L0, m = 16, on a 20000 x 100000
     planted-spike A (16 spikes, 1% supports, theta_j = 100/sqrt j) stored in
@@ -917,50 +1019,11 @@ def run_precision(args):
     d32 = torch.from_numpy(At).cuda()
     if not args.oracle:
         del At
-    dbf = d32.to(torch.bfloat16)
-    d8, s8 = _fp8_columns(d32)
     stream = torch.cuda.Stream()
     ctx = binding.Context(0, stream=stream)
     mu = [1.0] * m
-    out = binding.alloc_result(m, p, n, "cuda", torch.float32)
-    out2 = binding.alloc_result(m, p, n, "cuda", torch.float32)
-    res = {}
-    keep = {}
-    clk = Clocks(0)
-    clocks = None
-    for form in ("BL1", "BL0"):
-        for fmt, dA, cs in (("f32", d32, None), ("bf16", dbf, None), ("fp8", d8, s8)):
-            def solve():
-                return ctx.solve(dA, form, [args.rho] * m, mu=mu, gamma_relative=True, out=out, col_scale=cs)
-
-            for _ in range(args.warmup):
-                solve()
-            if clocks is None:
-                clk.start()
-            ms, r = _event_ms(stream, solve, max(1, args.steps // 4))
-            if clocks is None:
-                clocks = clk.stop()
-            iters = int(r.iters.max().item())
-            entry = {"ms_per_solve": round(ms, 3), "iters": iters, "iters_per_s": round(iters / (ms / 1e3), 1),
-                     "status": int(r.status.max().item())}
-            if fmt != "f32":
-                x0 = r.X.contiguous().clone()
-
-                def refine():
-                    return ctx.solve(d32, form, [args.rho] * m, mu=mu, gamma_relative=True, tol=0.0,
-                                     maxit=args.refine_sweeps, x0=x0, out=out2)
-
-                ms_r, rr = _event_ms(stream, refine, max(1, args.steps // 4))
-                entry["refine_ms"] = round(ms_r, 3)
-                entry["ms_total"] = round(ms + ms_r, 3)
-                keep[(form, fmt)] = {k: getattr(rr, k).clone() for k in ("X", "Z", "objective", "support")}
-            else:
-                entry["ms_total"] = round(ms, 3)
-                keep[(form, fmt)] = {k: getattr(r, k).clone() for k in ("X", "Z", "objective", "support")}
-            entry["solves_per_s"] = round(1e3 / entry["ms_total"], 2)
-            res[f"{form}_{fmt}"] = entry
-    sweep_ms = {fmt: ctx.time_sweep(dA, "BL1", [args.rho] * m, mu=mu, gamma_relative=True, reps=5, col_scale=cs)
-                for fmt, dA, cs in (("f32", d32, None), ("bf16", dbf, None), ("fp8", d8, s8))}
+    res, keep, clocks, sweep_ms = _precision(ctx, stream, d32, p, n, args.rho, args.refine_sweeps, args.warmup,
+                                             args.steps)
     ctx.close()
     if args.oracle:
         import oracle
