@@ -783,15 +783,17 @@ __host__ __device__ constexpr int tc_fused_smem(int npad) {
   return tc_fused_s1(npad) * static_cast<int>(kTcF) + 2 * (3 * static_cast<int>(kTcA) + npad * 128) + 1024 + 512;
 }
 
-// T pass with the bf16 planes in tensor memory (TM): the converters write
-// the three planes of a chunk with tcgen05.st into one of S2 tensor-memory
-// buffers (lane = column of the tile, two rows of A per 32-bit column) and
-// the MMAs read their A operand from there.  Ring 2 then holds only the X3
-// tile, and the shared memory the planes took (and the bandwidth of writing
-// and reading them there: about half of the pass's shared-memory traffic)
-// goes to float stages.  Tensor memory: the two accumulators in columns
-// [0, 2 NPAD), the plane buffers (3 x 32 columns each) from column 2 NPAD;
-// up to NPAD = 96 this fits the 512 columns of the SM.
+// Both passes with the bf16 planes in tensor memory (TM): the converters
+// write the three planes of a chunk with tcgen05.st into one of S2
+// tensor-memory buffers (lane = the MMA's M index: a column of the tile in
+// the T pass, a row of the block in the Y pass; two K values per 32-bit
+// column) and the MMAs read their A operand from there.  Ring 2 then holds
+// only the X3 / G3 tile, and the shared memory the planes took (and the
+// bandwidth of writing and reading them there: about half of the pass's
+// shared-memory traffic) goes to float stages.  Tensor memory: NACC
+// accumulators from column 0, the plane buffers (3 x 32 columns each) from
+// the next multiple of 32 after them; up to NPAD = 96 this fits the 512
+// columns of the SM.
 constexpr uint32_t kTmABuf = 96;    // columns per plane buffer: 3 planes x 64 rows / 2
 __host__ __device__ constexpr bool tc_fused_tm(int npad) { return npad <= 96; }
 // accumulators: the MMAs of one chunk fill one while the epilogue drains the
