@@ -180,7 +180,11 @@ def _run_steps(ctx, stream, dA, hA, cases, p, n, steps, warmup, eager, host=Fals
             items.append(dict(At=bufs[k % 2] if host else dA, form=form, gamma=[RHO] * m, mu=mu, tol=TOL,
                               maxit=MAXIT, gamma_relative=True, out=out, eager=eager))
         results = [ctx.solve(**it) for it in items] if eager else ctx.solve_batch(items)
-        sweeps, launches = 0, 0
+        # a batch computes the column norms of a matrix that two or more of its
+        # single-unit solves share once (one launch), and those solves copy them
+        # (one launch each, as their own norm pass would have been)
+        sweeps = 0
+        launches = 1 if not eager and sum(1 for f, _ in cases if f.startswith("S")) >= 2 else 0
         for res, (pro, per, epi) in zip(results, counts):
             it = int(res.iters.max().item())
             sweeps += it

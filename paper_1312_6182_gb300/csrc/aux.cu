@@ -166,11 +166,10 @@ struct Wide<__nv_fp8_e4m3> {
 // candidates are recomputed by select_start_kernel before any decision is
 // taken on them.  One warp per column.  A non-finite norm flags the solve.
 template <typename TA>
-__device__ __forceinline__ void colnorm_body(const IO* io, State* st, int64_t ld, int p, int n, int fast) {
-  double* cnorm = io->cnorm;
+__device__ __forceinline__ void colnorm_core(const TA* __restrict__ A, const float* col_scale, double* cnorm,
+                                             int32_t* error, int64_t ld, int p, int n, int fast) {
   using TC = typename Elem<TA>::TC;
   constexpr int NW = Wide<TA>::N;
-  const TA* __restrict__ A = static_cast<const TA*>(io->A);
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -204,12 +203,16 @@ __device__ __forceinline__ void colnorm_body(const IO* io, State* st, int64_t ld
     for (int off = 16; off > 0; off >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, off);
     if (lane == 0) {
       double c = sqrt(tot);
-      if (sizeof(TA) == 1) c *= static_cast<double>(io->col_scale[i]);
+      if (sizeof(TA) == 1) c *= static_cast<double>(col_scale[i]);
       if (!isfinite(c)) bad = true;
       cnorm[i] = c;
     }
   }
-  if (bad) atomicOr(&st->error, static_cast<int>(kErrNonFinite));
+  if (bad) atomicOr(error, static_cast<int>(kErrNonFinite));
+}
+template <typename TA>
+__device__ __forceinline__ void colnorm_body(const IO* io, State* st, int64_t ld, int p, int n, int fast) {
+  colnorm_core<TA>(static_cast<const TA*>(io->A), io->col_scale, io->cnorm, &st->error, ld, p, n, fast);
 }
 
 // Squared norm of column i over the rows [r0, p) step `step`: float data in
@@ -832,6 +835,24 @@ template <typename TA>
 __global__ void colnorm_grouped(GroupPtrs g, int64_t ld, int p, int n, int fast) {
   colnorm_body<TA>(g.io[blockIdx.z], g.st[blockIdx.z], ld, p, n, fast);
 }
+// column norms of a matrix that several solves of a batch share, into out
+// (the same per-column arithmetic as colnorm_kernel, so the same values)
+template <typename TA>
+__global__ void colnorm_shared_kernel(const void* A, const float* col_scale, double* out, int32_t* error,
+                                      int64_t ld, int p, int n, int fast) {
+  colnorm_core<TA>(static_cast<const TA*>(A), col_scale, out, error, ld, p, n, fast);
+}
+// a solve's column norms taken from the batch's shared ones, with the
+// non-finite check its own norm pass would have made
+__global__ void copy_norms_kernel(const IO* io, State* st, int n) {
+  bool bad = false;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double c = io->cnorm_src[i];
+    if (!isfinite(c)) bad = true;
+    io->cnorm[i] = c;
+  }
+  if (bad) atomicOr(&st->error, static_cast<int>(kErrNonFinite));
+}
 
 template <typename TA>
 __global__ void __launch_bounds__(kStartThreads) select_start_kernel(const StartArgs a) { select_start_body<TA>(a); }
@@ -903,6 +924,27 @@ void launch_colnorm(int dtype, const IO* io, State* st, int64_t ld, int p, int n
     case GPSPCA_BF16: colnorm_t<__nv_bfloat16>(io, st, ld, p, n, fast, s); break;
     default: colnorm_t<__nv_fp8_e4m3>(io, st, ld, p, n, fast, s); break;
   }
+}
+
+template <typename TA>
+static void colnorm_shared_t(const void* A, const float* col_scale, double* out, int32_t* error, int64_t ld, int p,
+                             int n, int fast, cudaStream_t s) {
+  const int blocks = std::max(1, std::min((n + 7) / 8, 4096));
+  colnorm_shared_kernel<TA><<<blocks, 256, 0, s>>>(A, col_scale, out, error, ld, p, n, fast);
+}
+
+void launch_colnorm_shared(int dtype, const void* A, const float* col_scale, double* out, int32_t* error,
+                           int64_t ld, int p, int n, int fast, cudaStream_t s) {
+  switch (dtype) {
+    case GPSPCA_F32: colnorm_shared_t<float>(A, col_scale, out, error, ld, p, n, fast, s); break;
+    case GPSPCA_F64: colnorm_shared_t<double>(A, col_scale, out, error, ld, p, n, fast, s); break;
+    case GPSPCA_BF16: colnorm_shared_t<__nv_bfloat16>(A, col_scale, out, error, ld, p, n, fast, s); break;
+    default: colnorm_shared_t<__nv_fp8_e4m3>(A, col_scale, out, error, ld, p, n, fast, s); break;
+  }
+}
+
+void launch_copy_norms(const IO* io, State* st, int n, cudaStream_t s) {
+  copy_norms_kernel<<<std::max(1, std::min((n + 255) / 256, 1024)), 256, 0, s>>>(io, st, n);
 }
 
 void launch_select_start(int dtype, const StartArgs& a, cudaStream_t s) {

@@ -67,6 +67,12 @@ inline int finish_smem_doubles(int m, int npairs) { return npairs + 2 * m + m * 
 // Host-side launchers (each kernel is launched from the file that defines it).
 void launch_reset(const IO* io, State* st, int m, int form, cudaStream_t s);
 void launch_colnorm(int dtype, const IO* io, State* st, int64_t ld, int p, int n, int fast, cudaStream_t s);
+// the column norms of a matrix that several solves of a batch share, once,
+// into out (n doubles; error collects kErrNonFinite)
+void launch_colnorm_shared(int dtype, const void* A, const float* col_scale, double* out, int32_t* error,
+                           int64_t ld, int p, int n, int fast, cudaStream_t s);
+// a solve's column norms copied from io->cnorm_src, with the non-finite check
+void launch_copy_norms(const IO* io, State* st, int n, cudaStream_t s);
 void launch_select_start(int dtype, const StartArgs& a, cudaStream_t s);
 void launch_gather_start(int dtype, const StartArgs& a, cudaStream_t s);
 void launch_reduce(int tcsize, const ReduceArgs& a, cudaStream_t s);

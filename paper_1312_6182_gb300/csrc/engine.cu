@@ -708,7 +708,10 @@ static cudaError_t launch_prologue(const Plan& pl, Slot* s, cudaStream_t cs, cud
   const bool late_norms = pca && pl.norms_in_sweep;
   StartArgs sa{s->io_dev, s->st_dev, pl.ld, pl.p, pl.n, pl.m, pl.form};
   if (!late_norms) {
-    launch_colnorm(pl.dtype, s->io_dev, s->st_dev, pl.ld, pl.p, pl.n, pl.fast, cs);
+    if (pl.norms_given)  // computed once by the batch for its solves of this matrix
+      launch_copy_norms(s->io_dev, s->st_dev, pl.n, cs);
+    else
+      launch_colnorm(pl.dtype, s->io_dev, s->st_dev, pl.ld, pl.p, pl.n, pl.fast, cs);
     launch_select_start(pl.dtype, sa, cs);
   }
   launch_gather_start(pl.dtype, sa, cs);
@@ -903,6 +906,9 @@ struct Request {
   const void* x0 = nullptr;
   uint32_t flags = 0;
   gpspca_out out;
+  // single-unit solves of a batch on one device matrix: the column norms the
+  // batch computed once for them (device, n doubles), or null
+  const double* cnorm_src = nullptr;
 };
 
 static int validate(const Request& r) {
@@ -1033,6 +1039,7 @@ static int prepare_solve(Slot* s, const Request& r, int nsm, bool scratch_out, P
   }
   if (!picked && (rc = make_plan(r.A.dtype, r.form, m, p, n, ld, fast, nsm, &pl, allow_tc, cand, ncand))) return rc;
   pl.pca = pca;
+  pl.norms_given = (r.cnorm_src && r.form < GPSPCA_BL1 && !pl.norms_in_sweep) ? 1 : 0;
   if ((rc = ensure(s, &s->b_cnorm, pl.ws_cnorm))) return rc;
   if ((rc = ensure(s, &s->b_P, pl.ws_P))) return rc;
   if ((rc = ensure(s, &s->b_Y, pl.ws_P))) return rc;
@@ -1098,6 +1105,7 @@ static int prepare_solve(Slot* s, const Request& r, int nsm, bool scratch_out, P
     io.gamma_abs = r.out.gamma_abs;
   }
   io.cnorm = static_cast<double*>(s->b_cnorm.p);
+  io.cnorm_src = pl.norms_given ? r.cnorm_src : nullptr;
   io.P = s->b_P.p;
   io.Y = s->b_Y.p;
   io.Xf = pl.ws_Xf ? s->b_Xf.p : nullptr;
@@ -1286,6 +1294,7 @@ struct gpspca_ctx {
   std::vector<std::unique_ptr<Slot>> batch_slots;
   cudaEvent_t batch_start = nullptr;
   std::vector<DevBuf> batch_stage;  // host matrices shared by several requests, copied once
+  std::vector<DevBuf> batch_norms;  // column norms of device matrices shared by single-unit requests
   // groups of same-shape single-unit solves (gpspca_solve_batch), under
   // solve_mu: member slots, the group's stream and capture streams, the
   // device arrays of the members' IO and State pointers, the group graphs
@@ -1676,7 +1685,6 @@ int gpspca_solve_batch(gpspca_ctx* ctx, int32_t count, const gpspca_request* req
     const int rc = wait_upload(ctx, cs, R[i].A);
     if (rc != GPSPCA_OK) return rc;
   }
-  GP_CUDA(cudaEventRecord(ctx->batch_start, cs));
   // kGroupMin or more same-shape single-unit requests: grouped launches
   std::vector<std::vector<int>> groups;
   std::vector<char> grouped(static_cast<size_t>(count), 0);
@@ -1698,6 +1706,50 @@ int gpspca_solve_batch(gpspca_ctx* ctx, int32_t count, const gpspca_request* req
   std::vector<int> solo;
   for (int i = 0; i < count; ++i)
     if (!grouped[i]) solo.push_back(i);
+  // Single-unit solo requests that share a device matrix (two or more of
+  // them: same buffer, type, shape, stride and scales) take its column norms
+  // from one pass made here, on the context's stream before the batch
+  // starts, instead of one pass each: the norm of a column does not depend on
+  // the launch, so every solve sees the values its own pass would have made
+  // (block solves keep theirs: they form them in their first power step).
+  {
+    auto same = [](const gpspca_matrix& a, const gpspca_matrix& b) {
+      return a.location == b.location && a.data == b.data && a.dtype == b.dtype && a.p == b.p && a.n == b.n &&
+             a.ld == b.ld && a.col_scale == b.col_scale;
+    };
+    auto shares = [](const Request& r) {
+      return r.form < GPSPCA_BL1 && r.A.location == GPSPCA_DEVICE && r.A.p > 0 && r.A.n > 0 && r.A.data &&
+             r.A.ld >= r.A.p && !(r.flags & GPSPCA_INJECT_TIMEOUT);
+    };
+    std::vector<char> taken(static_cast<size_t>(count), 0);
+    size_t nsh = 0;
+    for (size_t a = 0; a < solo.size(); ++a) {
+      const int i = solo[a];
+      if (taken[i] || !shares(R[i])) continue;
+      std::vector<int> users;
+      for (size_t b = a; b < solo.size(); ++b)
+        if (!taken[solo[b]] && shares(R[solo[b]]) && same(R[solo[b]].A, R[i].A)) users.push_back(solo[b]);
+      if (users.size() < 2) continue;
+      const gpspca_matrix& A = R[i].A;
+      const DInfo d = dinfo(A.dtype);
+      const size_t nbytes = (sizeof(double) * static_cast<size_t>(A.n) + 255) / 256 * 256;
+      if (ctx->batch_norms.size() <= nsh) ctx->batch_norms.resize(nsh + 1);
+      DevBuf* nb = &ctx->batch_norms[nsh++];
+      const int rc = ensure(&ctx->sync_slot, nb, nbytes + 256);
+      if (rc != GPSPCA_OK) return rc;
+      double* norms = static_cast<double*>(nb->p);
+      int32_t* err = reinterpret_cast<int32_t*>(static_cast<char*>(nb->p) + nbytes);  // not read: each solve checks
+      const bool fast = (reinterpret_cast<uintptr_t>(A.data) % 16 == 0) && ((A.ld * d.esize) % 16 == 0);
+      launch_colnorm_shared(A.dtype, A.data, A.col_scale, norms, err, A.ld, static_cast<int>(A.p),
+                            static_cast<int>(A.n), fast ? 1 : 0, cs);
+      GP_CUDA(cudaGetLastError());
+      for (int k : users) {
+        taken[k] = 1;
+        R[k].cnorm_src = norms;
+      }
+    }
+  }
+  GP_CUDA(cudaEventRecord(ctx->batch_start, cs));
   std::vector<char> running(static_cast<size_t>(count), 0);
   auto collect = [&](int k) {  // the solo solve at position k
     rcs[solo[k]] = solve_result(ctx->batch_slots[k % kBatchSlots].get());
@@ -2282,6 +2334,7 @@ int gpspca_destroy(gpspca_ctx* ctx) {
   if (ctx->up_tail) cudaEventDestroy(ctx->up_tail);
   if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
   for (DevBuf& b : ctx->batch_stage) release(&ctx->sync_slot, &b);
+  for (DevBuf& b : ctx->batch_norms) release(&ctx->sync_slot, &b);
   slot_free(&ctx->sync_slot);
   delete ctx;
   return GPSPCA_OK;

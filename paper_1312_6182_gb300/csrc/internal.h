@@ -27,6 +27,7 @@ struct IO {
   double* gamma_abs;
   // library workspace (device)
   double* cnorm;  // n approximate column norms
+  const double* cnorm_src;  // the same, computed once for the batch's solves of this matrix (or null)
   void* P;        // [m][p] start directions
   void* Y;        // [m][p] last unnormalised direction
   void* Xf;       // [m][p] block forms on the CUDA cores: the iterate X = Y W the next sweep evaluates

@@ -27,6 +27,9 @@ struct Plan {
   // first pass of components; the others as in `passes`)
   Pass norm_pass{};
   int norms_in_sweep = 0;
+  // the column norms come from a pass the batch made once for several
+  // solves of this matrix (copied in the prologue instead of computed)
+  int norms_given = 0;
   int nred = 0, nobj = 0, npairs = 0, full_gram = 0;
   int finish_smem = 0;
   int tcsize = 4, esize = 4;
@@ -59,6 +62,7 @@ struct Plan {
       snprintf(b, sizeof(b), "|n%d,%d,%d,%d", norm_pass.nch, norm_pass.threads, norm_pass.W, norm_pass.S);
       s += b;
     }
+    if (norms_given) s += "|ng";
     return s;
   }
   size_t workspace_bytes() const {

@@ -908,6 +908,34 @@ def test_batch_shares_host_matrix(ctx):
             assert torch.equal(a.objective.cpu(), b.objective.cpu()) and torch.equal(a.iters.cpu(), b.iters.cpu())
 
 
+def test_batch_shares_column_norms_of_a_device_matrix(ctx):
+    """Single-unit requests of a batch on one device matrix take its column
+    norms from one pass the batch makes for them: their results are
+    bit-identical to solo solves (a block request on the same matrix keeps
+    its own norms), and a non-finite entry is still reported by each of them
+    (each copies the shared norms with the check its own pass would make)."""
+    At = synth.planted_spike(2000, 6000, 3, [30.0, 20.0, 12.0], support_frac=0.05, seed=41, dtype=np.float32)
+    dA = torch.from_numpy(At).cuda()
+    items = [dict(At=dA, form="SL1", gamma=[0.05], gamma_relative=True),
+             dict(At=dA, form="SL0", gamma=[0.05], gamma_relative=True),
+             dict(At=dA, form="BL1", gamma=[0.05] * 3, mu=[1.0] * 3, gamma_relative=True),
+             dict(At=dA, form="SL1", gamma=[0.1], gamma_relative=True)]
+    solo = [ctx.solve(**it) for it in items]
+    got = ctx.solve_batch(items)
+    for ref, out in zip(solo, got):
+        assert torch.equal(out.Z, ref.Z) and torch.equal(out.X, ref.X)
+        assert torch.equal(out.objective, ref.objective) and torch.equal(out.iters, ref.iters)
+    bad = At.copy()
+    bad[17, 3] = np.nan
+    dB = torch.from_numpy(bad).cuda()
+    for order in (("SL1", "SL0"), ("SL0", "SL1")):  # the first request's code is the one raised
+        with pytest.raises(binding.GpspcaError) as e:
+            ctx.solve_batch([dict(At=dB, form=f, gamma=[0.05], gamma_relative=True) for f in order])
+        assert e.value.code == binding.ENONFINITE
+    again = ctx.solve_batch(items[:2])  # the context stays usable
+    assert torch.equal(again[0].Z, solo[0].Z) and torch.equal(again[1].Z, solo[1].Z)
+
+
 def test_upload_then_solve_equals_device_solve(ctx):
     """gpspca_upload copies a pinned host matrix into a device tensor (same
     stride; a wider stride, re-strided by the copy; fp8 with its scales);
