@@ -194,7 +194,12 @@ typedef struct {
  * A host matrix shared by several requests of the batch (same data pointer,
  * dtype, shape, ld and col_scale) is copied to the device once, on the
  * context's stream before the batch starts, into a buffer the context keeps
- * (counted against the budget) for later batches.  Four or more single-unit
+ * (counted against the budget) for later batches.  Two or more single-unit
+ * requests that are not grouped (below) and share one device matrix (same
+ * data pointer, dtype, shape, ld and col_scale, the staged copy included)
+ * take its column norms from one pass the batch makes for them on the
+ * context's stream, each copying them with its own non-finite check; their
+ * results are bit-identical to solo solves.  Four or more single-unit
  * requests with one component and the same storage type, form, shape,
  * column stride and alignment (device matrices; not GPSPCA_EAGER) run as a
  * group of up to 256: each step of their solves is one kernel launch for
